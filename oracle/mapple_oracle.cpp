@@ -1,0 +1,928 @@
+// Plain, slow CPU oracle for the Mapple index-mapping hot path.
+//
+// TEST INFRASTRUCTURE ONLY.  Only tests/, __graft_entry__.smoke() and the
+// cpu_baseline / reference legs of bench.py may load this library.  It shares
+// no code, header, table or helper with the CUDA engine.
+//
+// Every function evaluates the paper's definitions literally, one point and
+// one transform at a time, on explicit coordinate vectors, with exact integer
+// arithmetic (__int128 where a product can exceed 64 bits):
+//
+//   * transforms split / merge / swap: the index formulas of Fig. 4 (Sec. 3.3),
+//     a point of the transformed space is resolved by applying each
+//     transform's formula from the last transform to the first (Sec. 3.3,
+//     "m''[a0,a1] = m'[...] = m[...]", and Sec. 5.2's block1D_x example);
+//   * decompose(i, T): the optimisation problem of Sec. 4.2 (minimise
+//     sum d_m / l_m subject to prod d_m = d_i), solved by the exhaustive
+//     prime-exponent enumeration of Sec. 4.3, then expanded into k-1 splits
+//     as Sec. 4.2 states;
+//   * distributions: block (Fig. 1a / Fig. 3: idx = point * m.size / space),
+//     cyclic and block-cyclic (reading R9), the Cannon hierarchical
+//     block/cyclic mapper (Appendix A.1), the linearised round-robin of
+//     Fig. 5 (reading R8);
+//   * halo volume: every directed nearest-neighbour face whose two endpoints
+//     have different owners (Sec. 4.2, Fig. 10 surface formula; reading R10);
+//   * the greedy grid heuristic of Algorithm A1;
+//   * the matmul moved-bytes cost of a candidate (reading R12) and the
+//     exhaustive lexicographic argmin over (factorisation, chain) candidates
+//     (reading R13).
+//
+// Parity status: the Fig. 5 linearised cyclic distribution (R8) and
+// balance_split (R7) are "parity unpinned" beyond the special cases the tests
+// list (the paper gives no worked numbers for them).
+
+#include <algorithm>
+#include <cstdint>
+#include <cstring>
+#include <thread>
+#include <vector>
+
+namespace {
+
+typedef int64_t i64;
+typedef uint64_t u64;
+typedef __int128 i128;
+
+enum { OP_SPLIT = 0, OP_MERGE = 1, OP_SWAP = 2, OP_DECOMPOSE = 3, OP_BALANCE_SPLIT = 4 };
+enum { D_BLOCK = 0, D_CYCLIC = 1, D_BLOCK_CYCLIC = 2, D_HIER = 3, D_LINEAR_CYCLIC = 4 };
+
+const int MAXR = 32;   // processor-space rank bound inside the oracle
+
+// A user transform as the oracle receives it: 9 int64 per op
+//   [op, i, j, k, d, T0, T1, T2, T3]
+struct UserOp {
+  int op, i, j, k;
+  i64 d;
+  i64 T[4];
+};
+
+// After decompose / balance_split are expanded only these remain.
+struct Prim {
+  int op;        // OP_SPLIT, OP_MERGE, OP_SWAP
+  int p, q;      // split: p = i; merge/swap: p, q
+  i64 d;         // split factor
+  int rank_before;
+  i64 before[MAXR];   // shape of the space the primitive is applied to
+};
+
+struct Plan {
+  int n, g;                 // Machine(GPU) = (nodes, procs per node)
+  int k;                    // task-space rank
+  i64 L[4];                 // task-space extents
+  int dist, b;              // distribution kind and block-cyclic block size
+  std::vector<Prim> prims;  // chain + rank fix-up, in application order
+  int rank;                 // final processor-space rank
+  i64 s[MAXR];              // final processor-space shape
+  i64 P;
+  i64 npoints;
+};
+
+// ---------------------------------------------------------------- numbers
+
+std::vector<std::pair<i64, int>> prime_factorise(i64 d) {
+  std::vector<std::pair<i64, int>> out;
+  for (i64 p = 2; p * p <= d; ++p) {
+    int e = 0;
+    while (d % p == 0) { d /= p; ++e; }
+    if (e) out.push_back({p, e});
+  }
+  if (d > 1) out.push_back({d, 1});
+  return out;
+}
+
+i64 ipow(i64 b, int e) { i64 r = 1; while (e--) r *= b; return r; }
+
+// All non-negative integer solutions of z_1 + ... + z_k = a (Sec. 4.3), by
+// recursion on the first coordinate.
+void stars_and_bars(int a, int k, std::vector<int>& cur, std::vector<std::vector<int>>& out) {
+  if ((int)cur.size() == k - 1) {
+    cur.push_back(a);
+    out.push_back(cur);
+    cur.pop_back();
+    return;
+  }
+  for (int z = 0; z <= a; ++z) {
+    cur.push_back(z);
+    stars_and_bars(a - z, k, cur, out);
+    cur.pop_back();
+  }
+}
+
+// Every ordered k-factorisation of d (Sec. 4.3): per prime p_j distribute its
+// exponent a_j over the k factors, then take the Cartesian product over the
+// primes.  Returned sorted lexicographically ascending (the candidate order).
+std::vector<std::vector<i64>> factorisations(i64 d, int k) {
+  std::vector<std::vector<i64>> result;
+  if (d < 1 || k < 1) return result;
+  auto pf = prime_factorise(d);
+  std::vector<std::vector<std::vector<int>>> per_prime;
+  for (auto& pe : pf) {
+    std::vector<std::vector<int>> sols;
+    std::vector<int> cur;
+    stars_and_bars(pe.second, k, cur, sols);
+    per_prime.push_back(sols);
+  }
+  // Cartesian product
+  std::vector<size_t> idx(per_prime.size(), 0);
+  while (true) {
+    std::vector<i64> f(k, 1);
+    for (size_t j = 0; j < per_prime.size(); ++j)
+      for (int m = 0; m < k; ++m) f[m] *= ipow(pf[j].first, per_prime[j][idx[j]][m]);
+    result.push_back(f);
+    size_t j = 0;
+    while (j < per_prime.size()) {
+      if (++idx[j] < per_prime[j].size()) break;
+      idx[j] = 0;
+      ++j;
+    }
+    if (j == per_prime.size()) break;
+  }
+  std::sort(result.begin(), result.end());
+  return result;
+}
+
+// decompose objective (Sec. 4.2): sum_m d_m / l_m, compared exactly as the
+// integer sum_m d_m * prod_{j != m} l_j (common denominator prod l).
+i128 decompose_objective(const std::vector<i64>& f, const i64* l, int k) {
+  i128 tot = 0;
+  for (int m = 0; m < k; ++m) {
+    i128 term = f[m];
+    for (int j = 0; j < k; ++j)
+      if (j != m) term *= l[j];
+    tot += term;
+  }
+  return tot;
+}
+
+// argmin over all factorisations; ties go to the lexicographically smallest
+// tuple (reading R5) -- the enumeration is lexicographic and only a strictly
+// smaller objective replaces the incumbent.
+std::vector<i64> decompose_factors(i64 d, int k, const i64* l) {
+  auto all = factorisations(d, k);
+  std::vector<i64> best;
+  i128 bestv = 0;
+  for (auto& f : all) {
+    i128 v = decompose_objective(f, l, k);
+    if (best.empty() || v < bestv) { best = f; bestv = v; }
+  }
+  return best;
+}
+
+// ---------------------------------------------------------------- plan
+
+struct Space {
+  int r;
+  i64 s[MAXR];
+};
+
+bool push_split(std::vector<Prim>& prims, Space& sp, int i, i64 d) {
+  if (i < 0 || i >= sp.r || d < 1 || sp.r + 1 > MAXR) return false;
+  if (sp.s[i] % d != 0) return false;
+  Prim pr;
+  pr.op = OP_SPLIT; pr.p = i; pr.q = -1; pr.d = d; pr.rank_before = sp.r;
+  std::memcpy(pr.before, sp.s, sizeof(sp.s));
+  prims.push_back(pr);
+  // Fig. 4 / Sec. 3.3: (s_0, ..., d, s_i / d, ..., s_{n-1})
+  Space nsp;
+  nsp.r = sp.r + 1;
+  for (int t = 0; t < i; ++t) nsp.s[t] = sp.s[t];
+  nsp.s[i] = d;
+  nsp.s[i + 1] = sp.s[i] / d;
+  for (int t = i + 1; t < sp.r; ++t) nsp.s[t + 1] = sp.s[t];
+  sp = nsp;
+  return true;
+}
+
+bool push_merge(std::vector<Prim>& prims, Space& sp, int p, int q) {
+  if (!(0 <= p && p < q && q < sp.r)) return false;
+  Prim pr;
+  pr.op = OP_MERGE; pr.p = p; pr.q = q; pr.d = 0; pr.rank_before = sp.r;
+  std::memcpy(pr.before, sp.s, sizeof(sp.s));
+  prims.push_back(pr);
+  // Sec. 3.3: (s_0, ..., s_p * s_q, ..., s_{n-1}); dimension q removed
+  Space nsp;
+  nsp.r = sp.r - 1;
+  int o = 0;
+  for (int t = 0; t < sp.r; ++t) {
+    if (t == q) continue;
+    nsp.s[o++] = (t == p) ? sp.s[p] * sp.s[q] : sp.s[t];
+  }
+  sp = nsp;
+  return true;
+}
+
+bool push_swap(std::vector<Prim>& prims, Space& sp, int p, int q) {
+  if (p < 0 || q < 0 || p >= sp.r || q >= sp.r || p == q) return false;
+  Prim pr;
+  pr.op = OP_SWAP; pr.p = p; pr.q = q; pr.d = 0; pr.rank_before = sp.r;
+  std::memcpy(pr.before, sp.s, sizeof(sp.s));
+  prims.push_back(pr);
+  std::swap(sp.s[p], sp.s[q]);
+  return true;
+}
+
+// decompose(i, T) = k-1 splits split(i + n - 1, d_n), n = 1..k-1 (Sec. 4.2)
+bool push_decompose(std::vector<Prim>& prims, Space& sp, int i, int k, const i64* T) {
+  if (i < 0 || i >= sp.r || k < 1 || k > 4) return false;
+  for (int m = 0; m < k; ++m)
+    if (T[m] < 1) return false;
+  std::vector<i64> f = decompose_factors(sp.s[i], k, T);
+  for (int n = 1; n < k; ++n)
+    if (!push_split(prims, sp, i + n - 1, f[n - 1])) return false;
+  return true;
+}
+
+void flatten(std::vector<Prim>& prims, Space& sp) {
+  while (sp.r > 1) push_merge(prims, sp, 0, 1);
+}
+
+int target_rank(int dist, int k) {
+  if (dist == D_HIER) return 2 * k;
+  if (dist == D_LINEAR_CYCLIC) return 1;
+  return k;
+}
+
+// Returns 0 on success, 1 on an invalid chain or distribution.
+int build_plan(Plan& pl, const i64* L, int k, int n, int g, const i64* xf, int nxf,
+               int dist, int b) {
+  if (k < 1 || k > 4 || n < 1 || g < 1) return 1;
+  if (dist < 0 || dist > 4) return 1;
+  if (dist == D_BLOCK_CYCLIC && b < 1) return 1;
+  pl.n = n; pl.g = g; pl.k = k; pl.dist = dist; pl.b = b;
+  pl.npoints = 1;
+  for (int t = 0; t < k; ++t) {
+    if (L[t] < 1) return 1;
+    pl.L[t] = L[t];
+    pl.npoints *= L[t];
+  }
+  pl.P = (i64)n * g;
+  Space sp;
+  sp.r = 2;
+  sp.s[0] = n;
+  sp.s[1] = g;
+  pl.prims.clear();
+  for (int o = 0; o < nxf; ++o) {
+    const i64* e = xf + 9 * o;
+    int op = (int)e[0], i = (int)e[1], j = (int)e[2], kk = (int)e[3];
+    i64 d = e[4];
+    bool ok = false;
+    if (op == OP_SPLIT) ok = push_split(pl.prims, sp, i, d);
+    else if (op == OP_MERGE) ok = push_merge(pl.prims, sp, i, j);
+    else if (op == OP_SWAP) ok = push_swap(pl.prims, sp, i, j);
+    else if (op == OP_DECOMPOSE) ok = push_decompose(pl.prims, sp, i, kk, e + 5);
+    else if (op == OP_BALANCE_SPLIT) {
+      // reading R7: balance_split(i, k) = decompose(i, (1, ..., 1))
+      i64 ones[4] = {1, 1, 1, 1};
+      ok = (kk >= 1 && kk <= 4) && push_decompose(pl.prims, sp, i, kk, ones);
+    }
+    if (!ok) return 1;
+  }
+  // rank fix-up so that the final space has the rank the distribution indexes
+  int tr = target_rank(dist, k);
+  if (sp.r != tr) {
+    flatten(pl.prims, sp);
+    if (dist == D_LINEAR_CYCLIC) {
+      // already 1-D
+    } else if (dist == D_HIER) {
+      // Appendix A.1 pattern on the re-split machine (n, g): decompose the
+      // node dimension by the task space, then the processor dimension by the
+      // task space divided elementwise by the node factors (reading R6).
+      if (!push_split(pl.prims, sp, 0, n)) return 1;
+      if (!push_decompose(pl.prims, sp, 0, k, pl.L)) return 1;
+      i64 T2[4];
+      for (int t = 0; t < k; ++t) {
+        T2[t] = pl.L[t] / sp.s[t];
+        if (T2[t] < 1) T2[t] = 1;
+      }
+      if (!push_decompose(pl.prims, sp, k, k, T2)) return 1;
+    } else {
+      if (!push_decompose(pl.prims, sp, 0, k, pl.L)) return 1;
+    }
+  }
+  if (sp.r != tr) return 1;
+  pl.rank = sp.r;
+  std::memcpy(pl.s, sp.s, sizeof(sp.s));
+  return 0;
+}
+
+// Resolve an index of the final space back to Machine(GPU) by applying each
+// primitive's Fig. 4 formula from the last primitive to the first.
+void resolve(const Plan& pl, const i64* a_final, i64& node, i64& proc) {
+  i64 a[MAXR], bidx[MAXR];
+  int r = pl.rank;
+  for (int t = 0; t < r; ++t) a[t] = a_final[t];
+  for (int o = (int)pl.prims.size() - 1; o >= 0; --o) {
+    const Prim& pr = pl.prims[o];
+    int n = pr.rank_before;   // rank of b (the space before the primitive)
+    if (pr.op == OP_SPLIT) {
+      int i = pr.p;
+      for (int t = 0; t < n; ++t) {
+        if (t < i) bidx[t] = a[t];
+        else if (t == i) bidx[t] = a[i] + a[i + 1] * pr.d;
+        else bidx[t] = a[t + 1];
+      }
+    } else if (pr.op == OP_MERGE) {
+      int p = pr.p, q = pr.q;
+      for (int t = 0; t < n; ++t) {
+        if (t < p || (p < t && t < q)) bidx[t] = a[t];
+        else if (t == p) bidx[t] = a[p] % pr.before[p];
+        else if (t == q) bidx[t] = a[p] / pr.before[p];
+        else bidx[t] = a[t - 1];
+      }
+    } else {  // swap
+      for (int t = 0; t < n; ++t) bidx[t] = a[t];
+      bidx[pr.p] = a[pr.q];
+      bidx[pr.q] = a[pr.p];
+    }
+    for (int t = 0; t < n; ++t) a[t] = bidx[t];
+    r = n;
+  }
+  node = a[0];
+  proc = a[1];
+}
+
+// Distribution: task point -> index of the final processor space.
+void distribute(const Plan& pl, const i64* x, i64* a) {
+  int k = pl.k;
+  switch (pl.dist) {
+    case D_BLOCK:   // Fig. 1a: idx = point * m.size / space (floor, exact)
+      for (int t = 0; t < k; ++t) a[t] = (i64)((i128)x[t] * pl.s[t] / pl.L[t]);
+      break;
+    case D_CYCLIC:
+      for (int t = 0; t < k; ++t) a[t] = x[t] % pl.s[t];
+      break;
+    case D_BLOCK_CYCLIC:
+      for (int t = 0; t < k; ++t) a[t] = (x[t] / pl.b) % pl.s[t];
+      break;
+    case D_HIER:    // Appendix A.1: upper = ip * m[:k] / is, lower = ip % m[k:]
+      for (int t = 0; t < k; ++t) {
+        a[t] = (i64)((i128)x[t] * pl.s[t] / pl.L[t]);
+        a[k + t] = x[t] % pl.s[k + t];
+      }
+      break;
+    case D_LINEAR_CYCLIC: {   // Fig. 5: C-order linearisation, round robin
+      i128 lin = 0;
+      for (int t = 0; t < k; ++t) lin = lin * pl.L[t] + x[t];
+      a[0] = (i64)(lin % pl.s[0]);
+      break;
+    }
+  }
+}
+
+i64 owner_of_point(const Plan& pl, const i64* x) {
+  i64 a[MAXR];
+  distribute(pl, x, a);
+  i64 node, proc;
+  resolve(pl, a, node, proc);
+  return node * pl.g + proc;   // reading R1: node-major processor id
+}
+
+void unravel(const Plan& pl, i64 lin, i64* x) {
+  for (int t = pl.k - 1; t >= 0; --t) {
+    x[t] = lin % pl.L[t];
+    lin /= pl.L[t];
+  }
+}
+
+template <class F>
+void parallel_for(i64 n, int threads, F fn) {
+  if (threads <= 1 || n < 4096) { fn(0, n, 0); return; }
+  std::vector<std::thread> th;
+  i64 chunk = (n + threads - 1) / threads;
+  for (int w = 0; w < threads; ++w) {
+    i64 lo = w * chunk, hi = std::min(n, lo + chunk);
+    if (lo >= hi) break;
+    th.emplace_back(fn, lo, hi, w);
+  }
+  for (auto& t : th) t.join();
+}
+
+// ------------------------------------------------- canonical op alphabet
+
+struct COp { int op; int p; int q; i64 d; };
+
+std::vector<i64> nontrivial_divisors(i64 s) {
+  std::vector<i64> out;
+  for (i64 d = 2; d < s; ++d)
+    if (s % d == 0) out.push_back(d);
+  return out;
+}
+
+// Canonical alphabet at shape s (reading R13): split(i, d) for i ascending and
+// d ascending over the divisors with 1 < d < s_i, then merge(p, q) for p < q
+// lexicographic, then swap(p, q) for p < q lexicographic.
+std::vector<COp> alphabet(const Space& sp) {
+  std::vector<COp> out;
+  for (int i = 0; i < sp.r; ++i)
+    for (i64 d : nontrivial_divisors(sp.s[i])) out.push_back({OP_SPLIT, i, -1, d});
+  for (int p = 0; p < sp.r; ++p)
+    for (int q = p + 1; q < sp.r; ++q) out.push_back({OP_MERGE, p, q, 0});
+  for (int p = 0; p < sp.r; ++p)
+    for (int q = p + 1; q < sp.r; ++q) out.push_back({OP_SWAP, p, q, 0});
+  return out;
+}
+
+bool apply_cop(std::vector<Prim>& prims, Space& sp, const COp& c) {
+  if (c.op == OP_SPLIT) return push_split(prims, sp, c.p, c.d);
+  if (c.op == OP_MERGE) return push_merge(prims, sp, c.p, c.q);
+  return push_swap(prims, sp, c.p, c.q);
+}
+
+void enum_chains_rec(Space sp, int remaining, std::vector<COp>& cur,
+                     std::vector<std::vector<COp>>& out) {
+  if (remaining == 0) { out.push_back(cur); return; }
+  auto A = alphabet(sp);
+  for (auto& c : A) {
+    Space nsp = sp;
+    std::vector<Prim> dummy;
+    apply_cop(dummy, nsp, c);
+    cur.push_back(c);
+    enum_chains_rec(nsp, remaining - 1, cur, out);
+    cur.pop_back();
+  }
+}
+
+// All chains of depth 0..max_depth over the canonical alphabet, ordered by
+// depth, then lexicographically by the sequence of alphabet positions.
+std::vector<std::vector<COp>> enum_chains(int n, int g, int max_depth) {
+  std::vector<std::vector<COp>> out;
+  Space sp;
+  sp.r = 2; sp.s[0] = n; sp.s[1] = g;
+  for (int depth = 0; depth <= max_depth; ++depth) {
+    std::vector<COp> cur;
+    enum_chains_rec(sp, depth, cur, out);
+  }
+  return out;
+}
+
+// ------------------------------------------------- matmul moved-bytes cost
+
+// Owner (node, proc) of every flat index b of the 1-D space obtained by
+// flattening chain(m0) with merge(0, 1) repeatedly.  This is the resolution
+// of each b through the flatten merges and the chain; it does not depend on
+// the factorisation, so it is tabulated once per chain.
+struct ChainTable {
+  std::vector<i64> node, proc;
+};
+
+ChainTable chain_table(int n, int g, const std::vector<COp>& chain) {
+  Plan pl;
+  pl.n = n; pl.g = g; pl.k = 1; pl.dist = D_LINEAR_CYCLIC; pl.b = 1;
+  Space sp;
+  sp.r = 2; sp.s[0] = n; sp.s[1] = g;
+  for (auto& c : chain) apply_cop(pl.prims, sp, c);
+  flatten(pl.prims, sp);
+  pl.rank = 1;
+  pl.s[0] = sp.s[0];
+  i64 P = (i64)n * g;
+  ChainTable tb;
+  tb.node.resize(P);
+  tb.proc.resize(P);
+  for (i64 b = 0; b < P; ++b) {
+    i64 a[1] = {b};
+    resolve(pl, a, tb.node[b], tb.proc[b]);
+  }
+  return tb;
+}
+
+// Flat index of the decompose split of the flattened space into f = (f0, f1,
+// f2): inverse of split(1, f1) then of split(0, f0) (dimension 0 fastest).
+inline i64 flat_of(const i64* f, i64 a0, i64 a1, i64 a2) { return a0 + f[0] * (a1 + f[1] * a2); }
+
+inline i64 blk(i64 x, i64 f, i64 L) { return (i64)((i128)x * f / L); }
+
+// Literal reading R12 on the full tile grid: for every tile of A(i,k),
+// B(k,j), C(i,j), count the distinct processors (and nodes) among the points
+// (i,j,k) that touch it; the tile costs (distinct - 1) tile transfers.
+// O(M N K) -- only for small grids (brute-force pin of the grouped form).
+void matmul_cost_literal(i64 M, i64 N, i64 K, const ChainTable& tb, const i64* f,
+                         i128& prim, i128& sec) {
+  prim = 0; sec = 0;
+  auto own = [&](i64 i, i64 j, i64 k) { return flat_of(f, blk(i, f[0], M), blk(j, f[1], N), blk(k, f[2], K)); };
+  auto count = [&](std::vector<i64>& bs) {
+    std::vector<i64> procs, nodes;
+    for (i64 b : bs) { procs.push_back(tb.node[b] * 1000003 + tb.proc[b]); nodes.push_back(tb.node[b]); }
+    std::sort(procs.begin(), procs.end());
+    std::sort(nodes.begin(), nodes.end());
+    i64 dp = std::unique(procs.begin(), procs.end()) - procs.begin();
+    i64 dn = std::unique(nodes.begin(), nodes.end()) - nodes.begin();
+    prim += dp - 1;
+    sec += dn - 1;
+  };
+  std::vector<i64> bs;
+  for (i64 i = 0; i < M; ++i)      // A(i,k): points (i, j, k) over j
+    for (i64 k = 0; k < K; ++k) {
+      bs.clear();
+      for (i64 j = 0; j < N; ++j) bs.push_back(own(i, j, k));
+      count(bs);
+    }
+  for (i64 k = 0; k < K; ++k)      // B(k,j): over i
+    for (i64 j = 0; j < N; ++j) {
+      bs.clear();
+      for (i64 i = 0; i < M; ++i) bs.push_back(own(i, j, k));
+      count(bs);
+    }
+  for (i64 i = 0; i < M; ++i)      // C(i,j): over k (reduction traffic)
+    for (i64 j = 0; j < N; ++j) {
+      bs.clear();
+      for (i64 k = 0; k < K; ++k) bs.push_back(own(i, j, k));
+      count(bs);
+    }
+}
+
+// The same cost grouped by block coordinates: every tile whose two fixed
+// coordinates fall in the same pair of blocks touches the same set of owners
+// (the owner depends on a coordinate only through its block), so one fibre
+// per block pair is evaluated and weighted by the number of tiles in it.
+void matmul_cost_grouped(i64 M, i64 N, i64 K, const ChainTable& tb, const i64* f,
+                         i64 n_nodes, i128& prim, i128& sec) {
+  const i64 ext[3] = {M, N, K};
+  std::vector<std::vector<i64>> reps(3), wts(3);
+  for (int t = 0; t < 3; ++t) {
+    // distinct block coordinates of dimension t and how many tiles fall in each
+    std::vector<i64> cnt(f[t], 0);
+    for (i64 x = 0; x < ext[t]; ++x) cnt[blk(x, f[t], ext[t])]++;
+    for (i64 a = 0; a < f[t]; ++a)
+      if (cnt[a] > 0) { reps[t].push_back(a); wts[t].push_back(cnt[a]); }
+  }
+  prim = 0; sec = 0;
+  std::vector<char> seen_node(n_nodes, 0);
+  std::vector<i64> touched;
+  // family v: the fibre varies block coordinate v; u, w are the fixed ones
+  for (int v = 0; v < 3; ++v) {
+    int u = (v + 1) % 3, w = (v + 2) % 3;
+    for (size_t iu = 0; iu < reps[u].size(); ++iu)
+      for (size_t iw = 0; iw < reps[w].size(); ++iw) {
+        i64 weight = wts[u][iu] * wts[w][iw];
+        i64 distinct_nodes = 0;
+        touched.clear();
+        for (size_t iv = 0; iv < reps[v].size(); ++iv) {
+          i64 a[3];
+          a[u] = reps[u][iu]; a[w] = reps[w][iw]; a[v] = reps[v][iv];
+          i64 b = flat_of(f, a[0], a[1], a[2]);
+          i64 nd = tb.node[b];
+          if (!seen_node[nd]) { seen_node[nd] = 1; touched.push_back(nd); ++distinct_nodes; }
+        }
+        for (i64 nd : touched) seen_node[nd] = 0;
+        // distinct processors: the chain is a bijection, so distinct block
+        // coordinates along the fibre are distinct processors
+        prim += (i128)weight * (i64)(reps[v].size() - 1);
+        sec += (i128)weight * (distinct_nodes - 1);
+      }
+  }
+}
+
+}  // namespace
+
+// ====================================================================== C API
+
+extern "C" {
+
+// Final processor-space shape after chain + rank fix-up.  Returns 0 or 1 (invalid).
+int or_final_shape(const int64_t* L, int k, int n, int g, const int64_t* xf, int nxf, int dist,
+                   int b, int64_t* shape_out, int* rank_out) {
+  Plan pl;
+  if (build_plan(pl, L, k, n, g, xf, nxf, dist, b)) return 1;
+  *rank_out = pl.rank;
+  for (int t = 0; t < pl.rank; ++t) shape_out[t] = pl.s[t];
+  return 0;
+}
+
+// Primitive list after expansion: 4 int64 per primitive [op, p, q, d]; returns count or -1.
+int or_expand(const int64_t* L, int k, int n, int g, const int64_t* xf, int nxf, int dist, int b,
+              int64_t* out, int cap) {
+  Plan pl;
+  if (build_plan(pl, L, k, n, g, xf, nxf, dist, b)) return -1;
+  int m = (int)pl.prims.size();
+  for (int o = 0; o < m && o < cap; ++o) {
+    out[4 * o + 0] = pl.prims[o].op;
+    out[4 * o + 1] = pl.prims[o].p;
+    out[4 * o + 2] = pl.prims[o].q;
+    out[4 * o + 3] = pl.prims[o].d;
+  }
+  return m;
+}
+
+// Resolve final-space indices (rank r rows of `a`) to (node, proc).
+int or_resolve(const int64_t* L, int k, int n, int g, const int64_t* xf, int nxf, int dist, int b,
+               const int64_t* a, int64_t m, int64_t* node_out, int64_t* proc_out) {
+  Plan pl;
+  if (build_plan(pl, L, k, n, g, xf, nxf, dist, b)) return 1;
+  for (int64_t e = 0; e < m; ++e) {
+    i64 nd, pr;
+    resolve(pl, a + e * pl.rank, nd, pr);
+    node_out[e] = nd;
+    proc_out[e] = pr;
+  }
+  return 0;
+}
+
+// ids[lin] for every point (C-order), hist[P]; either may be NULL.
+int or_map_points(const int64_t* L, int k, int n, int g, const int64_t* xf, int nxf, int dist,
+                  int b, int32_t* ids, uint64_t* hist, int threads) {
+  Plan pl;
+  if (build_plan(pl, L, k, n, g, xf, nxf, dist, b)) return 1;
+  int T = threads < 1 ? 1 : threads;
+  std::vector<std::vector<u64>> part(T, std::vector<u64>(hist ? pl.P : 0, 0));
+  parallel_for(pl.npoints, T, [&](i64 lo, i64 hi, int w) {
+    i64 x[4];
+    for (i64 lin = lo; lin < hi; ++lin) {
+      unravel(pl, lin, x);
+      i64 id = owner_of_point(pl, x);
+      if (ids) ids[lin] = (int32_t)id;
+      if (hist) part[w][id]++;
+    }
+  });
+  if (hist) {
+    for (i64 p = 0; p < pl.P; ++p) {
+      u64 s = 0;
+      for (int w = 0; w < T; ++w) s += part[w][p];
+      hist[p] = s;
+    }
+  }
+  return 0;
+}
+
+// Owner of each listed linear point index (C-order).
+int or_owner_of(const int64_t* L, int k, int n, int g, const int64_t* xf, int nxf, int dist, int b,
+                const int64_t* lins, int64_t m, int32_t* ids_out) {
+  Plan pl;
+  if (build_plan(pl, L, k, n, g, xf, nxf, dist, b)) return 1;
+  i64 x[4];
+  for (int64_t e = 0; e < m; ++e) {
+    unravel(pl, lins[e], x);
+    ids_out[e] = (int32_t)owner_of_point(pl, x);
+  }
+  return 0;
+}
+
+// Halo volume (reading R10): every directed pair (x, x + delta e_t), delta =
+// +-1, with both points inside the launch and different owners, adds
+// face_bytes[t]; the receiver is the owner of x.  The neighbour's owner is
+// evaluated independently for every pair.
+int or_comm_volume(const int64_t* L, int k, int n, int g, const int64_t* xf, int nxf, int dist,
+                   int b, const uint64_t* face_bytes, uint64_t* total, uint64_t* recv,
+                   int threads) {
+  Plan pl;
+  if (build_plan(pl, L, k, n, g, xf, nxf, dist, b)) return 1;
+  int T = threads < 1 ? 1 : threads;
+  std::vector<u64> tot(T, 0);
+  std::vector<std::vector<u64>> part(T, std::vector<u64>(recv ? pl.P : 0, 0));
+  parallel_for(pl.npoints, T, [&](i64 lo, i64 hi, int w) {
+    i64 x[4], y[4];
+    for (i64 lin = lo; lin < hi; ++lin) {
+      unravel(pl, lin, x);
+      i64 me = owner_of_point(pl, x);
+      for (int t = 0; t < pl.k; ++t)
+        for (int delta = -1; delta <= 1; delta += 2) {
+          for (int u = 0; u < pl.k; ++u) y[u] = x[u];
+          y[t] += delta;
+          if (y[t] < 0 || y[t] >= pl.L[t]) continue;
+          i64 other = owner_of_point(pl, y);
+          if (other != me) {
+            tot[w] += face_bytes[t];
+            if (recv) part[w][me] += face_bytes[t];
+          }
+        }
+    }
+  });
+  u64 s = 0;
+  for (int w = 0; w < T; ++w) s += tot[w];
+  *total = s;
+  if (recv)
+    for (i64 p = 0; p < pl.P; ++p) {
+      u64 r = 0;
+      for (int w = 0; w < T; ++w) r += part[w][p];
+      recv[p] = r;
+    }
+  return 0;
+}
+
+// Closed-form halo volume (derived from the surface formula of Sec. 4.2,
+// Fig. 10, for the separable distributions): along dimension t the number of
+// positions x_t in [0, L_t - 1) whose two sides differ in the distributed
+// coordinate(s) is B_t, and every such position is a crossing for all
+// prod_{u != t} L_u points, in both directions.
+int or_halo_closed_form(const int64_t* L, int k, int n, int g, const int64_t* xf, int nxf,
+                        int dist, int b, const uint64_t* face_bytes, uint64_t* total) {
+  Plan pl;
+  if (build_plan(pl, L, k, n, g, xf, nxf, dist, b)) return 1;
+  u64 s = 0;
+  for (int t = 0; t < k; ++t) {
+    i64 Bt = 0;
+    i64 Lt = pl.L[t];
+    switch (dist) {
+      case D_BLOCK: Bt = std::min(pl.s[t], Lt) - 1; break;
+      case D_CYCLIC: Bt = pl.s[t] >= 2 ? Lt - 1 : 0; break;
+      case D_BLOCK_CYCLIC: Bt = pl.s[t] >= 2 ? (Lt + b - 1) / b - 1 : 0; break;
+      case D_HIER: Bt = pl.s[k + t] >= 2 ? Lt - 1 : std::min(pl.s[t], Lt) - 1; break;
+      case D_LINEAR_CYCLIC: {
+        i128 stride = 1;
+        for (int u = t + 1; u < k; ++u) stride *= pl.L[u];
+        Bt = (stride % pl.P != 0) ? Lt - 1 : 0;
+        break;
+      }
+    }
+    u64 others = 1;
+    for (int u = 0; u < k; ++u)
+      if (u != t) others *= (u64)pl.L[u];
+    s += face_bytes[t] * 2 * (u64)Bt * others;
+  }
+  *total = s;
+  return 0;
+}
+
+// Workload-balancing greedy of Sec. 4.3's counterexample: the primes of d
+// (ascending, with multiplicity) are placed one at a time on the dimension
+// that leaves the smallest spread max(w) - min(w) of the workload vector
+// w_m = l_m / d_m (first dimension on ties).  Exact rational comparisons.
+int or_greedy_workload(int64_t d, int k, const int64_t* l, int64_t* out) {
+  if (d < 1 || k < 1 || k > 4) return 1;
+  std::vector<i64> primes;
+  for (auto& pe : prime_factorise(d))
+    for (int e = 0; e < pe.second; ++e) primes.push_back(pe.first);
+  std::vector<i64> fac(k, 1);
+  // spread of w for factors f, as a fraction num/den (den > 0)
+  auto spread = [&](const std::vector<i64>& f, i128& num, i128& den) {
+    int imax = 0, imin = 0;   // w_a > w_b  <=>  l_a d_b > l_b d_a
+    for (int m = 1; m < k; ++m) {
+      if ((i128)l[m] * f[imax] > (i128)l[imax] * f[m]) imax = m;
+      if ((i128)l[m] * f[imin] < (i128)l[imin] * f[m]) imin = m;
+    }
+    num = (i128)l[imax] * f[imin] - (i128)l[imin] * f[imax];
+    den = (i128)f[imax] * f[imin];
+  };
+  for (i64 p : primes) {
+    int bestj = -1;
+    i128 bn = 0, bd = 1;
+    for (int j = 0; j < k; ++j) {
+      std::vector<i64> f = fac;
+      f[j] *= p;
+      i128 nn, dd;
+      spread(f, nn, dd);
+      if (bestj < 0 || nn * bd < bn * dd) { bestj = j; bn = nn; bd = dd; }
+    }
+    fac[bestj] *= p;
+  }
+  for (int m = 0; m < k; ++m) out[m] = fac[m];
+  return 0;
+}
+
+// Ordered k-factorisations of d, lexicographic; writes up to cap tuples (k
+// int64 each) and returns the total count.
+int64_t or_factorisations(int64_t d, int k, int64_t* out, int64_t cap) {
+  auto all = factorisations(d, k);
+  for (int64_t e = 0; e < (int64_t)all.size() && e < cap; ++e)
+    for (int m = 0; m < k; ++m) out[e * k + m] = all[e][m];
+  return (int64_t)all.size();
+}
+
+int or_decompose(int64_t d, int k, const int64_t* l, int64_t* out) {
+  if (d < 1 || k < 1 || k > 4) return 1;
+  auto f = decompose_factors(d, k, l);
+  for (int m = 0; m < k; ++m) out[m] = f[m];
+  return 0;
+}
+
+// Algorithm A1: primes ascending; each goes to the currently smallest factor
+// (first index on ties, reading R15); the factors are sorted descending.
+int or_greedy(int64_t d, int k, int64_t* out) {
+  if (d < 1 || k < 1) return 1;
+  std::vector<i64> primes;
+  for (auto& pe : prime_factorise(d))
+    for (int e = 0; e < pe.second; ++e) primes.push_back(pe.first);
+  std::vector<i64> fac(k, 1);
+  for (i64 p : primes) {
+    int j = 0;
+    for (int m = 1; m < k; ++m)
+      if (fac[m] < fac[j]) j = m;
+    fac[j] *= p;
+  }
+  std::sort(fac.begin(), fac.end(), [](i64 a, i64 b) { return a > b; });
+  for (int m = 0; m < k; ++m) out[m] = fac[m];
+  return 0;
+}
+
+// Chains of depth <= max_depth on (n, g) in canonical order.  Each chain is
+// written as max_depth ops of 4 int64 [op, p, q, d] (unused ops op = -1).
+// Returns the total count; writes at most cap chains.
+int64_t or_chains(int n, int g, int max_depth, int64_t* out, int64_t cap) {
+  auto all = enum_chains(n, g, max_depth);
+  for (int64_t c = 0; c < (int64_t)all.size() && c < cap; ++c)
+    for (int o = 0; o < max_depth; ++o) {
+      int64_t* e = out + (c * max_depth + o) * 4;
+      if (o < (int)all[c].size()) {
+        e[0] = all[c][o].op; e[1] = all[c][o].p; e[2] = all[c][o].q; e[3] = all[c][o].d;
+      } else {
+        e[0] = -1; e[1] = e[2] = e[3] = 0;
+      }
+    }
+  return (int64_t)all.size();
+}
+
+// A chain drawn from random numbers: at each step the op is
+// alphabet[draws[step] mod |alphabet|]; an empty alphabet ends the chain.
+// Output: 9-int64 user ops.  Returns the number of ops.
+int or_chain_from_draws(int n, int g, int depth, const uint64_t* draws, int64_t* xf_out) {
+  Space sp;
+  sp.r = 2; sp.s[0] = n; sp.s[1] = g;
+  int m = 0;
+  for (int step = 0; step < depth; ++step) {
+    auto A = alphabet(sp);
+    if (A.empty()) break;
+    COp c = A[draws[step] % A.size()];
+    std::vector<Prim> dummy;
+    apply_cop(dummy, sp, c);
+    int64_t* e = xf_out + 9 * m;
+    for (int z = 0; z < 9; ++z) e[z] = 0;
+    e[0] = c.op;
+    e[1] = c.p;
+    e[2] = c.op == OP_SPLIT ? 0 : c.q;
+    e[4] = c.op == OP_SPLIT ? c.d : 0;
+    ++m;
+  }
+  return m;
+}
+
+// Matmul moved-tile cost of one candidate (chain = ops [op,p,q,d] x depth,
+// op = -1 padding).  mode 0 = literal O(MNK), 1 = grouped.  Costs in tiles.
+int or_matmul_cost(int64_t M, int64_t N, int64_t K, int n, int g, const int64_t* chain, int depth,
+                   const int64_t* f, int mode, int64_t* primary, int64_t* secondary) {
+  std::vector<COp> ch;
+  for (int o = 0; o < depth; ++o) {
+    const int64_t* e = chain + 4 * o;
+    if (e[0] < 0) break;
+    ch.push_back({(int)e[0], (int)e[1], (int)e[2], e[3]});
+  }
+  if (f[0] * f[1] * f[2] != (i64)n * g) return 1;
+  ChainTable tb = chain_table(n, g, ch);
+  i128 p, s;
+  if (mode == 0) matmul_cost_literal(M, N, K, tb, f, p, s);
+  else matmul_cost_grouped(M, N, K, tb, f, n, p, s);
+  *primary = (int64_t)p;
+  *secondary = (int64_t)s;
+  return 0;
+}
+
+// Exhaustive decompose search for one 3-D matmul query (reading R13):
+// candidates are (factorisation f of P into 3, chain c of depth <= max_depth
+// on (P/g, g)), index = f_rank * n_chains + c_rank; the winner minimises
+// (primary, secondary, index) lexicographically.  Costs are in tiles.
+// out: [index, f0, f1, f2, c_rank, primary, secondary, n_candidates]
+int or_search(int64_t M, int64_t N, int64_t K, int n, int g, int max_depth, int threads,
+              int64_t* out) {
+  auto fs = factorisations((i64)n * g, 3);
+  auto chains = enum_chains(n, g, max_depth);
+  i64 NC = (i64)chains.size();
+  int T = threads < 1 ? 1 : threads;
+  struct Best { i128 p, s; i64 idx; };
+  std::vector<Best> best(T, Best{-1, -1, -1});
+  parallel_for(NC, T, [&](i64 lo, i64 hi, int w) {
+    for (i64 c = lo; c < hi; ++c) {
+      ChainTable tb = chain_table(n, g, chains[c]);
+      for (i64 fr = 0; fr < (i64)fs.size(); ++fr) {
+        i128 p, s;
+        matmul_cost_grouped(M, N, K, tb, fs[fr].data(), n, p, s);
+        i64 idx = fr * NC + c;
+        Best& b = best[w];
+        if (b.idx < 0 || p < b.p || (p == b.p && (s < b.s || (s == b.s && idx < b.idx))))
+          b = Best{p, s, idx};
+      }
+    }
+  }
+  );
+  Best b = best[0];
+  for (int w = 1; w < T; ++w) {
+    const Best& o = best[w];
+    if (o.idx < 0) continue;
+    if (b.idx < 0 || o.p < b.p || (o.p == b.p && (o.s < b.s || (o.s == b.s && o.idx < b.idx)))) b = o;
+  }
+  i64 fr = b.idx / NC, c = b.idx % NC;
+  out[0] = b.idx;
+  out[1] = fs[fr][0]; out[2] = fs[fr][1]; out[3] = fs[fr][2];
+  out[4] = c;
+  out[5] = (int64_t)b.p;
+  out[6] = (int64_t)b.s;
+  out[7] = (int64_t)fs.size() * NC;
+  return 0;
+}
+
+// Cost of an explicit list of candidate indices (for sampled checks).
+int or_candidate_costs(int64_t M, int64_t N, int64_t K, int n, int g, int max_depth,
+                       const int64_t* idx, int64_t m, int64_t* primary, int64_t* secondary) {
+  auto fs = factorisations((i64)n * g, 3);
+  auto chains = enum_chains(n, g, max_depth);
+  i64 NC = (i64)chains.size();
+  for (int64_t e = 0; e < m; ++e) {
+    i64 fr = idx[e] / NC, c = idx[e] % NC;
+    if (idx[e] < 0 || fr >= (i64)fs.size()) return 1;
+    ChainTable tb = chain_table(n, g, chains[c]);
+    i128 p, s;
+    matmul_cost_grouped(M, N, K, tb, fs[fr].data(), n, p, s);
+    primary[e] = (int64_t)p;
+    secondary[e] = (int64_t)s;
+  }
+  return 0;
+}
+
+}  // extern "C"
