@@ -1,0 +1,325 @@
+"""Benchmark of the index-mapping hot path on the GPU (one JSON line).
+
+Workload: the single large launch -- 1024 x 1024 x 512 points (2^29) on a
+machine of 64 nodes x 8 processors, a seeded random split/merge/swap chain of
+depth 4, in its three variants (block, cyclic, block-cyclic(4)), 7-point
+stencil with 8-byte elements.  One step maps every point of the three
+variants (int32 ids, per-processor histogram) and reduces the halo volume
+(total and per-processor received bytes): 3 x 2^29 points per step.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Metric: points mapped per second (whole job, all ranks).  Each rank maps its
+own copy of the launch (replicas, weak scaling); there is no data-path
+collective.  --impl reference times the CPU oracle on a bounded sample of the
+same launch on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2507_17087_gb300 import workloads as W  # noqa: E402
+
+METRIC = "points mapped/s"
+UNIT = "points/s"
+VARIANTS = ("block", "cyclic", "block_cyclic")
+# DRAM bytes (read + write) of one id-writer launch from the ncu capture
+# summarised in profiles/k_ids_large_1024x1024x512.md (None until captured
+# for the current kernel).
+K_IDS_TRAFFIC_BYTES = None
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=600)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--e2e-steps", type=int, default=4)
+    ap.add_argument("--cpu-sample", type=int, default=1 << 21,
+                    help="points of the launch the CPU oracle maps for cpu_baseline")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[3:7]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def launches():
+    out = []
+    for v in VARIANTS:
+        cfg = W.large_config(v)
+        out.append(cfg)
+    return out
+
+
+def cpu_baseline(sample: int):
+    """The CPU oracle, as it stands, on the first `sample` points of the block
+    variant: owner of each point and of its neighbours (ids + halo)."""
+    import oracle as O
+    cfg = W.large_config("block")
+    chain = O.chain_from_draws(*cfg["machine"], cfg["draws"])
+    ref = O.Launch(cfg["L"], cfg["machine"], chain, cfg["dist"])
+    cores = os.cpu_count() or 1
+    ref.map_range(cfg["face"], 0, 4096, threads=1)   # warm the library
+    t0 = time.perf_counter()
+    ref.map_range(cfg["face"], 0, sample, threads=cores)
+    dt = time.perf_counter() - t0
+    return {"value": sample / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"first {sample} points of the 1024x1024x512 block launch: owner of each point "
+                      f"and of its 6 neighbours (ids + halo), std::thread over {cores} cores",
+            "seconds": dt}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    steps_val = []
+    info = None
+    for _ in range(args.warmup):
+        cpu_baseline(max(args.cpu_sample // 8, 4096))
+    for _ in range(args.steps):
+        info = cpu_baseline(args.cpu_sample)
+        steps_val.append(info["seconds"])
+    total_s = sum(steps_val)
+    value = args.cpu_sample * len(steps_val) / total_s
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * total_s / max(1, len(steps_val)),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic",
+            "config": {"workload": "large launch 1024x1024x512 on 64x8, random depth-4 chain "
+                                   "(CPU oracle on a bounded sample)", "sample_points": args.cpu_sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": info["cores"], "kind": "oracle",
+                             "sample": info["sample"]},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        if world > 1 and rank != 0:
+            return
+        run_reference(args, rank, world)
+        return
+
+    import torch
+    from paper_2507_17087_gb300 import build as B
+    from paper_2507_17087_gb300 import native as N
+
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU (the engine has no CPU fallback)")
+    B.build()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    dev = torch.device("cuda", local)
+    cfgs = launches()
+    chains = [N.chain_from_draws(*c["machine"], c["draws"]) for c in cfgs]
+    L = cfgs[0]["L"]
+    P = cfgs[0]["machine"][0] * cfgs[0]["machine"][1]
+    npts = math.prod(L)
+    ids = torch.empty(npts, dtype=torch.int32, device=dev)
+    hist = torch.empty(P, dtype=torch.int64, device=dev)
+    total = torch.empty(1, dtype=torch.int64, device=dev)
+    recv = torch.empty(P, dtype=torch.int64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(timers=None):
+        for v, (cfg, chain) in enumerate(zip(cfgs, chains)):
+            if timers is not None:
+                N.set_kernel_timer(*timers[v])
+            N.map_points(cfg["L"], cfg["machine"], chain, cfg["dist"], ids=ids, hist=hist, stream=stream)
+            N.comm_volume(cfg["L"], cfg["machine"], chain, cfg["dist"], cfg["face"], total=total, recv=recv,
+                          stream=stream)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+
+    # per-launch CUDA events around the id writer (the dominant kernel)
+    kev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+            for _ in VARIANTS] for _ in range(args.steps)]
+    for pairs in kev:
+        for a, b in pairs:
+            a.record(stream)
+            b.record(stream)
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches0 = N.kernel_launches()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for s in range(args.steps):
+        step(kev[s])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    gpu_launches = N.kernel_launches() - launches0
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1)
+    kms = [a.elapsed_time(b) for pairs in kev for a, b in pairs]
+    k_avg_ms = sum(kms) / len(kms)
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    points = 3 * npts * args.steps * world
+    value = points / (ms / 1e3)
+
+    # ---------------------------------------------------------------- e2e
+    # the same step through the public API with host buffers: the ids, the
+    # histogram, the halo total and the received bytes come back to pinned host
+    # memory inside the timed region; the launch description goes down as
+    # kernel parameters.
+    h_ids = torch.empty(npts, dtype=torch.int32).pin_memory()
+    h_hist = torch.empty(P, dtype=torch.int64).pin_memory()
+    h_total = torch.empty(1, dtype=torch.int64).pin_memory()
+    h_recv = torch.empty(P, dtype=torch.int64).pin_memory()
+    launches_before = N.kernel_launches()
+
+    def e2e_step():
+        for cfg, chain in zip(cfgs, chains):
+            N.map_points(cfg["L"], cfg["machine"], chain, cfg["dist"], ids=h_ids, hist=h_hist, stream=stream)
+            N.comm_volume(cfg["L"], cfg["machine"], chain, cfg["dist"], cfg["face"], total=h_total,
+                          recv=h_recv, stream=stream)
+
+    e2e_step()
+    per_step_launches = N.kernel_launches() - launches_before
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        e2e_step()
+    e2e_s = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = 3 * npts * args.e2e_steps * world / e2e_s
+    d2h = 3 * (npts * 4 + P * 8 + 8 + P * 8)
+    h2d = per_step_launches * N.descriptor_bytes()
+
+    if rank == 0:
+        peak, peak_kind = peaks()
+        algo_bytes = 4 * npts
+        achieved = algo_bytes / (k_avg_ms / 1e3) / 1e9
+        traffic = K_IDS_TRAFFIC_BYTES
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": "large launch: 1024x1024x512 points on 64 nodes x 8 procs, seeded random "
+                                   "split/merge/swap chain depth 4, block + cyclic + block-cyclic(4), "
+                                   "7-point halo 8 B",
+                       "points_per_step": 3 * npts, "parallelism": f"replicas x{world}",
+                       "l2": "outputs larger than L2 (2 GiB of ids per launch)"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "kernel": "k_ids (id writer)", "peak_source": f"{peak_kind} hbm_gbs",
+                         "kernel_avg_ms": k_avg_ms, "algorithmic_bytes_per_launch": algo_bytes},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": gpu_launches,
+            "clocks": clocks,
+        }
+        if not args.no_cpu_baseline and world >= 1:
+            try:
+                cb = cpu_baseline(args.cpu_sample)
+                cb.pop("seconds", None)
+                line["cpu_baseline"] = cb
+            except Exception as exc:  # noqa: BLE001
+                line["cpu_baseline"] = {"error": str(exc)}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

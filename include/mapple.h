@@ -1,0 +1,246 @@
+/*
+ * mapple.h -- C ABI of the GB300 engine for the Mapple index-mapping hot path
+ * (Wei et al., "Mapple: A Domain-Specific Language for Mapping Distributed
+ * Programs", arXiv 2507.17087).
+ *
+ * The engine evaluates an IndexTaskMap over a whole index launch: every point
+ * of an N-D task space is sent through a distribution and a chain of
+ * processor-space transforms to a (node, processor) id; the assignment is
+ * reduced to a per-processor load histogram and an exact halo volume; and the
+ * decompose search is run exhaustively over ordered factorisations and
+ * transform chains.
+ *
+ * Conventions shared by every entry point
+ *  - Return value: MP_OK (0) or one of the mp_status codes below.  Arguments
+ *    are validated before anything is launched; on an error nothing has been
+ *    written to any output.
+ *  - Buffers are owned by the caller.  A buffer argument may point to device
+ *    memory (cudaMalloc / torch) or to host memory (pinned or pageable); the
+ *    engine looks the pointer up with cudaPointerGetAttributes.  With device
+ *    buffers the call is asynchronous on `stream` (a cudaStream_t, NULL = the
+ *    legacy default stream); with any host output buffer the call copies the
+ *    result back and synchronises `stream` before returning.
+ *  - The engine keeps a per-device workspace (tables, staging) that grows on
+ *    demand and is reused by later calls; it is freed at process exit.  Calls
+ *    that run concurrently on different streams of one device must be
+ *    serialised by the caller (the workspace is shared).
+ *  - Processor ids are node-major: id = node * procs_per_node + proc, where
+ *    (node, proc) is the index of Machine(GPU) = (nodes, procs_per_node)
+ *    (Sec. 3.2, Fig. 3).
+ */
+#ifndef MAPPLE_GB300_H
+#define MAPPLE_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------ status codes */
+enum mp_status {
+  MP_OK = 0,
+  MP_EINVAL = 1,     /* invalid argument: bad transform, rank, extent, kind   */
+  MP_EOVERFLOW = 2,  /* point count >= 2^62, or P too large for int32 ids     */
+  MP_ENOMEM = 3,     /* device workspace allocation failed                    */
+  MP_ECUDA = 4,      /* a CUDA runtime call failed                            */
+  MP_ETIMEOUT = 5,   /* a bounded device-side wait gave up                    */
+  MP_ENOTSUP = 6     /* size beyond what this engine supports (see limits)    */
+};
+
+/* ------------------------------------------------------------ limits */
+#define MP_MAX_TASK_RANK 4        /* task-space rank (index launch)            */
+#define MP_MAX_PROC_RANK 24       /* processor-space rank after transforms     */
+#define MP_MAX_XFORMS 64          /* transforms in one chain                   */
+#define MP_MAX_PROCS (1 << 26)    /* P = nodes * procs_per_node                */
+
+/* ------------------------------------------------------------ data types */
+
+/* Index launch (task space): rank 1..4, extents ext[0..rank), C order (last
+ * dimension fastest).  Point count prod(ext) must be < 2^62.  (Sec. 5.1's
+ * ISpace / IPoint; Appendix A.1 task.ispace.) */
+typedef struct mp_space {
+  int32_t rank;
+  int32_t reserved;
+  int64_t ext[4];
+} mp_space;
+
+/* Machine(GPU): a 2-D processor space (nodes, processors per node),
+ * Sec. 3.2. */
+typedef struct mp_machine {
+  int32_t nodes;
+  int32_t procs_per_node;
+} mp_machine;
+
+/* Processor-space transforms (Fig. 4, Sec. 3.3; decompose Sec. 4.2). */
+enum mp_op {
+  MP_SPLIT = 0,          /* split(i, d): dim i of size s -> (d, s/d); d | s     */
+  MP_MERGE = 1,          /* merge(i, j): i < j, dims fused at i, size s_i*s_j   */
+  MP_SWAP = 2,           /* swap(i, j): exchange dims i and j, i != j           */
+  MP_DECOMPOSE = 3,      /* decompose(i, T[0..k)): dim i -> k factors minimising
+                            sum_m d_m / T_m, ties lexicographically smallest   */
+  MP_BALANCE_SPLIT = 4   /* balance_split(i, k) = decompose(i, (1,...,1))      */
+};
+
+typedef struct mp_xform {
+  int32_t op;     /* enum mp_op                                  */
+  int32_t i;      /* dimension (split/merge/swap/decompose)      */
+  int32_t j;      /* second dimension (merge/swap)               */
+  int32_t k;      /* number of factors (decompose/balance_split) */
+  int64_t d;      /* split factor                                */
+  int64_t T[4];   /* decompose target extents T[0..k)            */
+} mp_xform;
+
+/* Distributions: task point x -> index a of the final processor space. */
+enum mp_dist_kind {
+  MP_BLOCK = 0,          /* a_t = floor(x_t * s_t / L_t)  (Fig. 1a, Fig. 3)    */
+  MP_CYCLIC = 1,         /* a_t = x_t mod s_t                                  */
+  MP_BLOCK_CYCLIC = 2,   /* a_t = floor(x_t / b) mod s_t                       */
+  MP_HIER = 3,           /* Appendix A.1 (Cannon): final rank 2k,
+                            a_t = floor(x_t s_t / L_t), a_{k+t} = x_t mod s_{k+t} */
+  MP_LINEAR_CYCLIC = 4   /* Fig. 5: a_0 = (C-order linear index of x) mod P    */
+};
+
+typedef struct mp_dist {
+  int32_t kind;   /* enum mp_dist_kind                 */
+  int32_t b;      /* block size of MP_BLOCK_CYCLIC     */
+} mp_dist;
+
+/* Rank fix-up.  The chain is applied to Machine(GPU) = (nodes, ppn).  If the
+ * resulting rank differs from the rank the distribution indexes (k for
+ * block / cyclic / block-cyclic, 2k for hier, 1 for linear-cyclic), the space
+ * is flattened with merge(0,1) repeatedly and then: decompose(0, L) for the
+ * rank-k kinds; split(0, nodes), decompose(0, L), decompose(k, L / node
+ * factors) for hier (the Appendix A.1 pattern); nothing more for
+ * linear-cyclic. */
+
+/* ------------------------------------------------------------ entry points */
+
+/* map_points: a1-a4 of the hot path.  For every point of `space` (C order)
+ * writes ids[lin] = node * procs_per_node + proc, and hist[p] = number of
+ * points mapped to processor p (p in [0, P)).
+ *   chain / n_xf : transforms applied to Machine(GPU) in order (n_xf <= 64;
+ *                  chain may be NULL when n_xf == 0)
+ *   ids  : int32[prod(ext)] device or host, or NULL
+ *   hist : uint64[P] device or host, or NULL (overwritten, not accumulated)
+ * Errors: MP_EINVAL (invalid transform / distribution / extents),
+ * MP_EOVERFLOW (prod(ext) >= 2^62), MP_ENOTSUP (P > MP_MAX_PROCS),
+ * MP_ENOMEM, MP_ECUDA. */
+int mp_map_points(const mp_space* space, const mp_machine* machine, const mp_xform* chain,
+                  int n_xf, const mp_dist* dist, int32_t* ids, uint64_t* hist, void* stream);
+
+/* comm_volume: a5.  Nearest-neighbour (2k-point star) halo volume of the
+ * launch under the mapping: every directed pair (x, x + delta e_t), delta =
+ * +-1, with both points inside the launch and different owners, moves
+ * face_bytes[t] bytes to the owner of x (Sec. 4.2's inter-processor surface,
+ * Fig. 10; each face counted once per direction).
+ *   face_bytes : host array of rank uint64 values (bytes per face along t)
+ *   total      : uint64[1] device or host, required (overwritten)
+ *   recv       : uint64[P] device or host, or NULL: bytes received per
+ *                processor (overwritten)
+ * Errors as mp_map_points. */
+int mp_comm_volume(const mp_space* space, const mp_machine* machine, const mp_xform* chain,
+                   int n_xf, const mp_dist* dist, const uint64_t* face_bytes, uint64_t* total,
+                   uint64_t* recv, void* stream);
+
+/* decompose_search: a6-a8.  Exhaustive search for a 3-D matmul tile grid
+ * (M, N, K) on Machine(GPU) = (P / procs_per_node, procs_per_node).  A
+ * candidate is an ordered factorisation f = (f0, f1, f2) of P (Sec. 4.3) and
+ * a transform chain c of depth <= max_depth over the canonical alphabet (at
+ * shape s: split(i, d) for i ascending and 1 < d < s_i, d | s_i ascending;
+ * merge(p, q) p < q lexicographic; swap(p, q) p < q lexicographic; chains
+ * ordered by depth then by alphabet positions).  The candidate's mapping
+ * flattens chain(Machine) with merge(0,1) repeatedly, splits it as f with
+ * dimension 0 fastest (decompose's splits) and block-maps tile (i, j, k).
+ * Its cost counts, for every tile of A(i,k), B(k,j) and C(i,j), the distinct
+ * processors (primary) and distinct nodes (secondary) among the points
+ * touching it, minus one, times tile_bytes.  The result minimises
+ * (primary, secondary, index) lexicographically, index = f_rank * n_chains +
+ * c_rank with f ranked in lexicographic order.  Synchronous; `out` is host. */
+typedef struct mp_search_query {
+  int64_t M, N, K;          /* tile-grid extents                        */
+  int32_t procs;            /* P                                        */
+  int32_t procs_per_node;   /* g (P % g == 0)                           */
+  int32_t max_depth;        /* chain depth bound (0..4)                 */
+  int32_t flags;            /* MP_SEARCH_* bits                         */
+  uint64_t tile_bytes;      /* bytes per tile (512*512*4 for fp32)      */
+} mp_search_query;
+
+/* flags: MP_SEARCH_FULL scores the secondary cost of every candidate.
+ * Without it, candidates whose primary cost (closed form in f) exceeds the
+ * minimum primary are dismissed without scanning their secondary; the
+ * argmin is the same.  Limits: M, N, K <= 2^20, P <= 16384. */
+#define MP_SEARCH_FULL 1
+
+typedef struct mp_search_result {
+  int64_t index;            /* winning candidate index                  */
+  int64_t f[3];             /* winning factorisation                    */
+  int64_t chain_rank;       /* rank of the winning chain                */
+  int32_t chain_len;        /* ops in the winning chain                 */
+  int32_t reserved;
+  mp_xform chain[4];        /* the winning chain                        */
+  uint64_t primary_bytes;   /* primary cost in bytes                    */
+  uint64_t secondary_bytes; /* secondary cost in bytes                  */
+  int64_t n_candidates;     /* candidates evaluated                     */
+  int64_t n_chains;         /* chains in the search space               */
+  int64_t n_factorisations; /* factorisations in the search space       */
+} mp_search_result;
+
+int mp_decompose_search(const mp_search_query* queries, int n_queries, mp_search_result* out,
+                        void* stream);
+
+/* Exact costs of listed candidate indices of one query (device or host
+ * arrays of n int64 indices; primary/secondary: uint64[n] in bytes).  Used to
+ * re-evaluate sampled or proposed candidates.  MP_EINVAL on an index out of
+ * range. */
+int mp_candidate_costs(const mp_search_query* query, const int64_t* indices, int64_t n,
+                       uint64_t* primary, uint64_t* secondary, void* stream);
+
+/* ------------------------------------------------------------ host helpers */
+
+/* Plan only (no GPU work): final processor-space shape and the expanded
+ * primitive list (split / merge / swap after decompose expansion and the rank
+ * fix-up), 4 int64 per primitive [op, p, q, d].  rank/shape/prims may be
+ * NULL.  Returns MP_OK or the validation error. */
+int mp_plan(const mp_space* space, const mp_machine* machine, const mp_xform* chain, int n_xf,
+            const mp_dist* dist, int32_t* rank, int64_t* shape, int32_t* n_prims,
+            int64_t* prims, int32_t prims_cap);
+
+/* A chain built from random numbers: at each step the op is the
+ * (draws[step] mod |A|)-th entry of the canonical alphabet A of the current
+ * shape; an empty alphabet ends the chain.  Writes *n_out <= depth ops. */
+int mp_chain_from_draws(int32_t nodes, int32_t procs_per_node, int32_t depth,
+                        const uint64_t* draws, mp_xform* out, int32_t* n_out);
+
+/* Decodes candidate `index` of a search query: its factorisation f[3] and
+ * its chain (chain_len <= 4 ops).  Host only; MP_EINVAL if out of range. */
+int mp_search_candidate(const mp_search_query* query, int64_t index, int64_t* f, mp_xform* chain,
+                        int32_t* chain_len);
+
+/* Size of a decompose search space: number of factorisations of P into 3
+ * ordered factors and number of canonical chains of depth <= max_depth. */
+int mp_search_space(int32_t procs, int32_t procs_per_node, int32_t max_depth,
+                    int64_t* n_factorisations, int64_t* n_chains);
+
+/* Measurement hook: the next launch of the dominant per-point kernel
+ * (the id writer of mp_map_points) records `start_event` just before it and
+ * `stop_event` just after it on the call's stream (both cudaEvent_t; one-shot,
+ * cleared after use; NULL disables).  Lets a caller time that kernel alone
+ * with CUDA events. */
+int mp_set_kernel_timer(void* start_event, void* stop_event);
+
+/* Bytes of launch description one kernel launch carries to the device as
+ * parameters (the host-to-device input of a mapping call). */
+uint64_t mp_descriptor_bytes(void);
+
+/* Human-readable text of a status code (static storage). */
+const char* mp_strerror(int status);
+
+/* Number of kernel launches issued by this library in the calling process. */
+uint64_t mp_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MAPPLE_GB300_H */

@@ -63,6 +63,7 @@ def _load():
                 "or_resolve": (I, launch + [V, I64, V, V]),
                 "or_map_points": (I, launch + [V, V, I]),
                 "or_owner_of": (I, launch + [V, I64, V]),
+                "or_map_range": (I, launch + [V, I64, I64, I, V, V]),
                 "or_comm_volume": (I, launch + [V, V, V, I]),
                 "or_halo_closed_form": (I, launch + [V, V]),
                 "or_factorisations": (I64, [I64, I, V, I64]),
@@ -175,6 +176,18 @@ class Launch:
         if rc:
             raise ValueError("invalid chain or distribution")
         return out
+
+    def map_range(self, face_bytes, lo, count, threads=1):
+        """Owners of points [lo, lo+count) and the halo bytes they receive."""
+        lib = _load()
+        fb = np.zeros(4, dtype=np.uint64)
+        fb[: self.k] = face_bytes
+        ids = np.zeros(count, dtype=np.int32)
+        halo = np.zeros(1, dtype=np.uint64)
+        rc = lib.or_map_range(*self._args(), _p(fb), lo, count, threads, _p(ids), _p(halo))
+        if rc:
+            raise ValueError("invalid chain or distribution")
+        return ids, int(halo[0])
 
     def comm_volume(self, face_bytes, want_recv=True, threads=1):
         lib = _load()

@@ -643,6 +643,37 @@ int or_map_points(const int64_t* L, int k, int n, int g, const int64_t* xf, int 
   return 0;
 }
 
+// The per-point work of the hot path on the points [lo, lo + count): owner
+// of the point and of each of its in-range nearest neighbours, and the
+// halo bytes those neighbours send (used by the timed CPU baseline).
+int or_map_range(const int64_t* L, int k, int n, int g, const int64_t* xf, int nxf, int dist, int b,
+                 const uint64_t* face_bytes, int64_t lo, int64_t count, int threads,
+                 int32_t* ids_out, uint64_t* halo_out) {
+  Plan pl;
+  if (build_plan(pl, L, k, n, g, xf, nxf, dist, b)) return 1;
+  int T = threads < 1 ? 1 : threads;
+  std::vector<u64> tot(T, 0);
+  parallel_for(count, T, [&](i64 a, i64 z, int w) {
+    i64 x[4], y[4];
+    for (i64 e = a; e < z; ++e) {
+      unravel(pl, lo + e, x);
+      i64 me = owner_of_point(pl, x);
+      ids_out[e] = (int32_t)me;
+      for (int t = 0; t < pl.k; ++t)
+        for (int delta = -1; delta <= 1; delta += 2) {
+          for (int u = 0; u < pl.k; ++u) y[u] = x[u];
+          y[t] += delta;
+          if (y[t] < 0 || y[t] >= pl.L[t]) continue;
+          if (owner_of_point(pl, y) != me) tot[w] += face_bytes[t];
+        }
+    }
+  });
+  u64 s = 0;
+  for (int w = 0; w < T; ++w) s += tot[w];
+  *halo_out = s;
+  return 0;
+}
+
 // Owner of each listed linear point index (C-order).
 int or_owner_of(const int64_t* L, int k, int n, int g, const int64_t* xf, int nxf, int dist, int b,
                 const int64_t* lins, int64_t m, int32_t* ids_out) {

@@ -1,0 +1,602 @@
+// map_points / comm_volume: kernels and C-ABI entry points.
+//
+// The five distributions are separable: every final processor-space
+// coordinate a_u is a function of one task coordinate x_t (block, cyclic,
+// block-cyclic per dimension; the hierarchical Cannon mapper of Appendix A.1
+// drives two final coordinates from each task coordinate), and the
+// linearised round robin of Fig. 5 is a function of the C-order linear index.
+// With F = sum_u a_u sigma_u (dimension 0 fastest) the flat final index of a
+// point is therefore F(x) = sum_t c_t(x_t), or lin(x) mod P.  The chain of
+// transforms is a bijection from the final space onto Machine(GPU) (every
+// primitive of Fig. 4 is invertible, Sec. 3.3), so
+//   id(x) = T[F(x)],  T = chain resolution of every F in [0, P).
+// Kernels:
+//   k_resolve    T[F] for F < P: decode F, apply the Fig. 4 formulas of every
+//                primitive from last to first                       (a3)
+//   k_dimtables  c_t(x_t) for every coordinate of every dimension, and the
+//                per-dimension counts H_t[c] (points with c_t = c) and
+//                X_t[c] (neighbour pairs along t that cross) used by the
+//                reductions                                         (a2)
+//   k_ids        ids[lin] = T[base(row) + c_last(x_last)]; 16-byte stores,
+//                persistent grid                                  (a1-a3)
+//   k_reduce     hist and per-processor halo bytes from the per-dimension
+//                counts: because the chain is a bijection, owner(x) !=
+//                owner(y) iff F(x) != F(y), and for separable F a neighbour
+//                along t crosses iff c_t changes                  (a4, a5)
+//   k_lc_slabs   linear-cyclic only: boundary points that miss a neighbour.
+#include <algorithm>
+#include <cstring>
+
+#include "engine.h"
+
+namespace mp {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kUnroll = 4;
+constexpr uint64_t kTableMax = uint64_t(1) << 22;   // per-dimension c_t tables kept in HBM/L2
+constexpr uint32_t kSmemTMax = 16384;               // T staged in shared memory up to this P
+constexpr uint32_t kSmemLastMax = 8192;             // c_last staged in shared memory
+
+struct Tabs {
+  uint64_t off[4];     // offset of dimension t's c_t table in ctab (if present)
+  int32_t has[4];      // 1 if the table exists
+};
+
+__device__ __forceinline__ uint32_t comp_coord(const Comp& c, uint64_t x) {
+  switch (c.kind) {
+    case C_BLOCK:
+      if (c.narrow) return div32((uint32_t)x * c.s, c.divL32);
+      return (uint32_t)div64(x * (uint64_t)c.s, c.divL);
+    case C_CYCLIC:
+      if (x <= 0xFFFFFFFFull) {
+        uint32_t q, r;
+        divmod32((uint32_t)x, c.divs, q, r);
+        return r;
+      } else {
+        uint64_t q, r;
+        divmod64(x, c.divs64, q, r);
+        return (uint32_t)r;
+      }
+    default: {  // block-cyclic
+      uint64_t blk = x <= 0xFFFFFFFFull ? div32((uint32_t)x, c.divb) : div64(x, c.divb64);
+      if (blk <= 0xFFFFFFFFull) {
+        uint32_t q, r;
+        divmod32((uint32_t)blk, c.divs, q, r);
+        return r;
+      }
+      uint64_t q, r;
+      divmod64(blk, c.divs64, q, r);
+      return (uint32_t)r;
+    }
+  }
+}
+
+// c_t(x) = sum of the final coordinates driven by x times their strides
+__device__ __forceinline__ uint32_t contrib(const MapDesc& D, int t, uint64_t x) {
+  uint32_t v = comp_coord(D.comp[t][0], x) * D.comp[t][0].sigma;
+  if (D.ncomp[t] > 1) v += comp_coord(D.comp[t][1], x) * D.comp[t][1].sigma;
+  return v;
+}
+
+// ----------------------------------------------------------------- k_resolve
+
+__global__ void __launch_bounds__(kThreads) k_resolve(const __grid_constant__ MapDesc D,
+                                                      uint32_t* __restrict__ T) {
+  const uint32_t F = blockIdx.x * blockDim.x + threadIdx.x;
+  if (F >= D.P) return;
+  uint32_t a[kMaxRank + 1];
+  uint32_t rest = F;
+  for (int u = 0; u < D.rank; ++u) {
+    uint32_t q, r;
+    divmod32(rest, D.divs[u], q, r);
+    a[u] = r;
+    rest = q;
+  }
+  int r = D.rank;
+  for (int o = D.nprim - 1; o >= 0; --o) {
+    const Prim& p = D.prim[o];
+    if (p.op == P_SPLIT) {
+      // Fig. 4 split: b_i = a_i + a_{i+1} d, b_t = a_{t+1} for t > i
+      a[p.p] = a[p.p] + a[p.p + 1] * p.d;
+      for (int t = p.p + 1; t < r - 1; ++t) a[t] = a[t + 1];
+      r -= 1;
+    } else if (p.op == P_MERGE) {
+      // Fig. 4 merge: b_p = a_p mod s_p, b_q = floor(a_p / s_p), b_t = a_{t-1} for t > q
+      uint32_t q, rem;
+      divmod32(a[p.p], p.div, q, rem);
+      for (int t = r; t > p.q; --t) a[t] = a[t - 1];
+      a[p.q] = q;
+      a[p.p] = rem;
+      r += 1;
+    } else {
+      uint32_t tmp = a[p.p];
+      a[p.p] = a[p.q];
+      a[p.q] = tmp;
+    }
+  }
+  T[F] = a[0] * D.g + a[1];
+}
+
+// ----------------------------------------------------------------- k_dimtables
+
+// One thread per (t, x_t).  Counts are aggregated over the lanes of a warp
+// that share (t, c) before the global atomics.
+__global__ void __launch_bounds__(kThreads) k_dimtables(const __grid_constant__ MapDesc D, Tabs tabs,
+                                                        uint64_t total, uint32_t* __restrict__ ctab,
+                                                        unsigned long long* __restrict__ H,
+                                                        unsigned long long* __restrict__ X) {
+  uint64_t off[5];
+  off[0] = 0;
+  for (int t = 0; t < D.k; ++t) off[t + 1] = off[t] + D.L[t];
+  const uint64_t lane = threadIdx.x & 31;
+  // the trip count is uniform across a warp (e - lane is the warp's base)
+  for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e - lane < total;
+       e += (uint64_t)gridDim.x * blockDim.x) {
+    const bool live = e < total;
+    int t = 0;
+    while (t < D.k - 1 && e >= off[t + 1]) ++t;
+    const uint64_t x = live ? e - off[t] : 0;
+    uint32_t c = 0, cross = 0;
+    if (live) {
+      c = contrib(D, t, x);
+      if (tabs.has[t]) ctab[tabs.off[t] + x] = c;
+      if (X) {
+        if (x > 0 && contrib(D, t, x - 1) != c) cross += 1;
+        if (x + 1 < D.L[t] && contrib(D, t, x + 1) != c) cross += 1;
+      }
+    }
+    if (H) {
+      const unsigned active = __ballot_sync(0xFFFFFFFFu, live);
+      if (live) {
+        const uint32_t key = (uint32_t)t * D.P + c;
+        const unsigned grp = __match_any_sync(active, key);
+        const uint32_t xsum = __reduce_add_sync(grp, cross);
+        if ((threadIdx.x & 31) == (unsigned)(__ffs(grp) - 1)) {
+          atomicAdd(H + (uint64_t)t * D.P + c, (unsigned long long)__popc(grp));
+          if (X && xsum) atomicAdd(X + (uint64_t)t * D.P + c, (unsigned long long)xsum);
+        }
+      }
+    }
+  }
+}
+
+// ----------------------------------------------------------------- k_ids
+
+template <bool WIDE>
+__device__ __forceinline__ void split_lin(const MapDesc& D, uint64_t lin, uint64_t& row, uint64_t& x) {
+  const int last = D.k - 1;
+  if (WIDE) {
+    divmod64(lin, D.divL64[last], row, x);
+  } else {
+    uint32_t q, r;
+    divmod32((uint32_t)lin, D.divL32[last], q, r);
+    row = q;
+    x = r;
+  }
+}
+
+template <bool WIDE>
+__device__ __forceinline__ uint32_t row_base(const MapDesc& D, const Tabs& tabs,
+                                             const uint32_t* __restrict__ ctab, uint64_t row) {
+  uint32_t base = 0;
+  for (int t = D.k - 2; t >= 0; --t) {
+    uint64_t q, xt;
+    if (WIDE) {
+      divmod64(row, D.divL64[t], q, xt);
+    } else {
+      uint32_t q32, r32;
+      divmod32((uint32_t)row, D.divL32[t], q32, r32);
+      q = q32;
+      xt = r32;
+    }
+    row = q;
+    base += tabs.has[t] ? __ldg(ctab + tabs.off[t] + xt) : contrib(D, t, xt);
+  }
+  return base;
+}
+
+// last_mode: 0 = c_last staged in shared memory, 1 = read from the HBM/L2
+// table, 2 = computed.
+template <bool WIDE, bool TSMEM>
+__global__ void __launch_bounds__(kThreads) k_ids(const __grid_constant__ MapDesc D, Tabs tabs,
+                                                  const uint32_t* __restrict__ Tg,
+                                                  const uint32_t* __restrict__ ctab, int last_mode,
+                                                  int vec_ok, int32_t* __restrict__ ids) {
+  extern __shared__ uint32_t smem[];
+  uint32_t* Ts = smem;
+  uint32_t* Cs = smem + (TSMEM ? D.P : 0);
+  const int last = D.k - 1;
+  const uint64_t Llast = D.L[last];
+  if (TSMEM)
+    for (uint32_t i = threadIdx.x; i < D.P; i += blockDim.x) Ts[i] = __ldg(Tg + i);
+  if (last_mode == 0)
+    for (uint32_t i = threadIdx.x; i < Llast; i += blockDim.x) Cs[i] = __ldg(ctab + tabs.off[last] + i);
+  __syncthreads();
+
+  auto lookupT = [&](uint32_t F) -> uint32_t { return TSMEM ? Ts[F] : __ldg(Tg + F); };
+  auto clast = [&](uint64_t x) -> uint32_t {
+    if (last_mode == 0) return Cs[x];
+    if (last_mode == 1) return __ldg(ctab + tabs.off[last] + x);
+    return contrib(D, last, x);
+  };
+
+  const uint64_t N = D.npoints;
+  const uint64_t groups = (N + 3) / 4;
+  const uint64_t per_tile = (uint64_t)kThreads * kUnroll;
+  const uint64_t tiles = (groups + per_tile - 1) / per_tile;
+  uint64_t crow = ~0ull;
+  uint32_t cbase = 0;
+  for (uint64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const uint64_t gi = tile * per_tile + (uint64_t)u * kThreads + threadIdx.x;
+      if (gi >= groups) break;
+      const uint64_t lin0 = gi * 4;
+      uint64_t row, x;
+      split_lin<WIDE>(D, lin0, row, x);
+      if (row != crow) {
+        crow = row;
+        cbase = row_base<WIDE>(D, tabs, ctab, row);
+      }
+      uint32_t v[4];
+      const int cnt = N - lin0 < 4 ? (int)(N - lin0) : 4;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        if (i < cnt) {
+          if (x == Llast) {   // the row ended inside this group
+            x = 0;
+            crow = ++row;
+            cbase = row_base<WIDE>(D, tabs, ctab, row);
+          }
+          v[i] = lookupT(cbase + clast(x));
+          ++x;
+        }
+      }
+      if (cnt == 4 && vec_ok) {
+        __stcs(reinterpret_cast<int4*>(ids + lin0), make_int4((int)v[0], (int)v[1], (int)v[2], (int)v[3]));
+      } else {
+        for (int i = 0; i < cnt; ++i) ids[lin0 + i] = (int32_t)v[i];
+      }
+    }
+  }
+}
+
+// Linear-cyclic (Fig. 5): F = lin mod P, consecutive points advance F by 1.
+template <bool TSMEM>
+__global__ void __launch_bounds__(kThreads) k_ids_lc(const __grid_constant__ MapDesc D,
+                                                     const uint32_t* __restrict__ Tg, int vec_ok,
+                                                     int32_t* __restrict__ ids) {
+  extern __shared__ uint32_t smem[];
+  if (TSMEM) {
+    for (uint32_t i = threadIdx.x; i < D.P; i += blockDim.x) smem[i] = __ldg(Tg + i);
+    __syncthreads();
+  }
+  const uint64_t N = D.npoints;
+  const uint64_t groups = (N + 3) / 4;
+  for (uint64_t gi = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; gi < groups;
+       gi += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t lin0 = gi * 4;
+    uint64_t q, F64;
+    divmod64(lin0, D.divP64, q, F64);
+    uint32_t F = (uint32_t)F64;
+    uint32_t v[4];
+    const int cnt = N - lin0 < 4 ? (int)(N - lin0) : 4;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      v[i] = TSMEM ? smem[F] : __ldg(Tg + F);
+      F = (F + 1 == D.P) ? 0 : F + 1;
+    }
+    if (cnt == 4 && vec_ok) {
+      __stcs(reinterpret_cast<int4*>(ids + lin0), make_int4((int)v[0], (int)v[1], (int)v[2], (int)v[3]));
+    } else {
+      for (int i = 0; i < cnt; ++i) ids[lin0 + i] = (int32_t)v[i];
+    }
+  }
+}
+
+// ----------------------------------------------------------------- k_lc_slabs
+
+// Linear-cyclic halo: along a dimension t whose linear stride is not a
+// multiple of P every neighbour pair crosses, so a point receives
+// face_t for each neighbour it has.  Each point of the slabs x_t = 0 and
+// x_t = L_t - 1 lacks one neighbour; deficit[F] collects face_t for them.
+__global__ void __launch_bounds__(kThreads) k_lc_slabs(const __grid_constant__ MapDesc D,
+                                                       uint64_t f0, uint64_t f1, uint64_t f2,
+                                                       uint64_t f3,
+                                                       unsigned long long* __restrict__ deficit) {
+  const uint64_t face[4] = {f0, f1, f2, f3};
+  const uint64_t N = D.npoints;
+  for (int t = 0; t < D.k; ++t) {
+    if (D.lc_stride_mod[t] == 0 || face[t] == 0) continue;
+    const uint64_t per_slab = N / D.L[t];
+    const uint64_t stride = D.lc_stride[t];
+    const Div64 dstride = Div64{stride, ~0ull / stride};
+    for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < 2 * per_slab;
+         e += (uint64_t)gridDim.x * blockDim.x) {
+      const uint64_t side = e >= per_slab;
+      const uint64_t s = e - side * per_slab;
+      uint64_t hi, lo;
+      divmod64(s, dstride, hi, lo);
+      const uint64_t xt = side ? D.L[t] - 1 : 0;
+      const uint64_t lin = hi * (D.L[t] * stride) + xt * stride + lo;
+      uint64_t q, F;
+      divmod64(lin, D.divP64, q, F);
+      atomicAdd(deficit + F, (unsigned long long)face[t]);
+    }
+  }
+}
+
+// ----------------------------------------------------------------- k_reduce
+
+__global__ void __launch_bounds__(kThreads) k_reduce(const __grid_constant__ MapDesc D,
+                                                     const uint32_t* __restrict__ T,
+                                                     const unsigned long long* __restrict__ H,
+                                                     const unsigned long long* __restrict__ X,
+                                                     const unsigned long long* __restrict__ deficit,
+                                                     uint64_t f0, uint64_t f1, uint64_t f2, uint64_t f3,
+                                                     uint64_t* __restrict__ hist,
+                                                     uint64_t* __restrict__ recv,
+                                                     unsigned long long* __restrict__ total) {
+  const uint64_t face[4] = {f0, f1, f2, f3};
+  const uint32_t F = blockIdx.x * blockDim.x + threadIdx.x;
+  uint64_t r_F = 0;
+  if (F < D.P) {
+    uint64_t h_F;
+    if (!D.lc) {
+      uint32_t part[4] = {0, 0, 0, 0};
+      uint32_t rest = F;
+      for (int u = 0; u < D.rank; ++u) {
+        uint32_t q, r;
+        divmod32(rest, D.divs[u], q, r);
+        rest = q;
+        part[D.owner_dim[u]] += r * D.sigma[u];
+      }
+      uint64_t h[4], xc[4];
+      h_F = 1;
+      for (int t = 0; t < D.k; ++t) {
+        h[t] = H[(uint64_t)t * D.P + part[t]];
+        xc[t] = X ? X[(uint64_t)t * D.P + part[t]] : 0;
+        h_F *= h[t];
+      }
+      if (X)
+        for (int t = 0; t < D.k; ++t) {
+          uint64_t v = face[t] * xc[t];
+          for (int u = 0; u < D.k; ++u)
+            if (u != t) v *= h[u];
+          r_F += v;
+        }
+    } else {
+      // C-order linear indices cover [0, N): lin = F (mod P) occurs
+      // floor(N / P) times, once more when F < N mod P.
+      uint64_t q, rem;
+      divmod64(D.npoints, D.divP64, q, rem);
+      h_F = q + (F < rem ? 1 : 0);
+      if (deficit) {
+        uint64_t G = 0;
+        for (int t = 0; t < D.k; ++t)
+          if (D.lc_stride_mod[t] != 0) G += 2 * face[t];
+        r_F = G * h_F - deficit[F];
+      }
+    }
+    const uint32_t id = T[F];
+    if (hist) hist[id] = h_F;
+    if (recv) recv[id] = r_F;
+  }
+  if (total) {
+    __shared__ unsigned long long red[kThreads / 32];
+    unsigned long long v = r_F;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xFFFFFFFFu, v, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      v = threadIdx.x < kThreads / 32 ? red[threadIdx.x] : 0;
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xFFFFFFFFu, v, o);
+      if (threadIdx.x == 0 && v) atomicAdd(total, v);
+    }
+  }
+}
+
+int sm_count() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 132;
+  }
+  return n;
+}
+
+struct Want {
+  int32_t* ids;
+  uint64_t* hist;
+  uint64_t* recv;
+  uint64_t* total;
+  uint64_t face[4];
+};
+
+size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
+
+// Runs the kernels of one launch into device buffers.
+int run_launch(const Plan& pl, const Want& w, cudaStream_t st) {
+  const MapDesc& D = pl.desc;
+  const bool need_red = w.hist || w.recv || w.total;
+  const bool need_X = (w.recv || w.total) && !D.lc;
+  // ------------------------------------------------ workspace layout
+  Tabs tabs;
+  std::memset(&tabs, 0, sizeof(tabs));
+  uint64_t tab_total = 0;
+  for (int t = 0; t < D.k; ++t) {
+    tabs.has[t] = !D.lc && D.L[t] <= kTableMax;
+    tabs.off[t] = tab_total;
+    if (tabs.has[t]) tab_total += D.L[t];
+  }
+  size_t o_T = 0;
+  size_t o_tab = align256(o_T + (size_t)D.P * 4);
+  size_t o_H = align256(o_tab + tab_total * 4);
+  size_t nHX = need_red && !D.lc ? (size_t)D.k * D.P : 0;
+  size_t o_X = align256(o_H + nHX * 8);
+  size_t o_def = align256(o_X + (need_X ? nHX * 8 : 0));
+  size_t n_def = D.lc && (w.recv || w.total) ? D.P : 0;
+  size_t bytes = align256(o_def + n_def * 8);
+  char* ws = (char*)workspace(bytes, 0);
+  if (!ws) return MP_ENOMEM;
+  uint32_t* T = (uint32_t*)(ws + o_T);
+  uint32_t* ctab = (uint32_t*)(ws + o_tab);
+  unsigned long long* H = nHX ? (unsigned long long*)(ws + o_H) : nullptr;
+  unsigned long long* X = need_X ? (unsigned long long*)(ws + o_X) : nullptr;
+  unsigned long long* def = n_def ? (unsigned long long*)(ws + o_def) : nullptr;
+
+  // ------------------------------------------------ tables
+  k_resolve<<<(D.P + kThreads - 1) / kThreads, kThreads, 0, st>>>(D, T);
+  count_launch();
+  if (H) MP_CUDA_TRY(cudaMemsetAsync(H, 0, nHX * 8, st));
+  if (X) MP_CUDA_TRY(cudaMemsetAsync(X, 0, nHX * 8, st));
+  uint64_t sumL = 0;
+  for (int t = 0; t < D.k; ++t) sumL += D.L[t];
+  const bool want_tabs = tab_total > 0 && w.ids;
+  if (!D.lc && (want_tabs || H)) {
+    uint64_t blocks = std::min<uint64_t>((sumL + kThreads - 1) / kThreads, (uint64_t)sm_count() * 16);
+    k_dimtables<<<(unsigned)blocks, kThreads, 0, st>>>(D, tabs, sumL, ctab, H, X);
+    count_launch();
+  }
+  // ------------------------------------------------ ids
+  if (w.ids) {
+    timer_begin(st);
+    const int vec_ok = ((uintptr_t)w.ids & 15) == 0;
+    const bool tsmem = D.P <= kSmemTMax;
+    const int last = D.k - 1;
+    const uint64_t groups = (D.npoints + 3) / 4;
+    if (D.lc) {
+      size_t sm = tsmem ? (size_t)D.P * 4 : 0;
+      uint64_t blocks = std::min<uint64_t>((groups + kThreads - 1) / kThreads, (uint64_t)sm_count() * 8);
+      if (tsmem) {
+        if (sm > 48 * 1024) cudaFuncSetAttribute(k_ids_lc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        k_ids_lc<true><<<(unsigned)blocks, kThreads, sm, st>>>(D, T, vec_ok, w.ids);
+      } else {
+        k_ids_lc<false><<<(unsigned)blocks, kThreads, 0, st>>>(D, T, vec_ok, w.ids);
+      }
+      count_launch();
+    } else {
+      int last_mode = tabs.has[last] ? (D.L[last] <= kSmemLastMax ? 0 : 1) : 2;
+      size_t sm = (tsmem ? (size_t)D.P * 4 : 0) + (last_mode == 0 ? (size_t)D.L[last] * 4 : 0);
+      const bool wide = D.npoints > 0xFFFFFFFFull - 8;
+      uint64_t tiles = (groups + (uint64_t)kThreads * kUnroll - 1) / ((uint64_t)kThreads * kUnroll);
+      uint64_t blocks = std::min<uint64_t>(tiles, (uint64_t)sm_count() * 8);
+      auto launch = [&](auto kern) {
+        if (sm > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        kern<<<(unsigned)blocks, kThreads, sm, st>>>(D, tabs, T, ctab, last_mode, vec_ok, w.ids);
+      };
+      if (wide) {
+        if (tsmem) launch(k_ids<true, true>); else launch(k_ids<true, false>);
+      } else {
+        if (tsmem) launch(k_ids<false, true>); else launch(k_ids<false, false>);
+      }
+      count_launch();
+    }
+    timer_end(st);
+    MP_CUDA_TRY(cudaGetLastError());
+  }
+  // ------------------------------------------------ reductions
+  if (need_red) {
+    if (w.total) MP_CUDA_TRY(cudaMemsetAsync(w.total, 0, 8, st));
+    if (def) {
+      MP_CUDA_TRY(cudaMemsetAsync(def, 0, n_def * 8, st));
+      uint64_t work = 0;
+      for (int t = 0; t < D.k; ++t) work += 2 * (D.npoints / D.L[t]);
+      uint64_t blocks = std::max<uint64_t>(1, std::min<uint64_t>((work + kThreads - 1) / kThreads,
+                                                                   (uint64_t)sm_count() * 8));
+      k_lc_slabs<<<(unsigned)blocks, kThreads, 0, st>>>(D, w.face[0], w.face[1], w.face[2], w.face[3], def);
+      count_launch();
+    }
+    k_reduce<<<(D.P + kThreads - 1) / kThreads, kThreads, 0, st>>>(
+        D, T, H, X, def, w.face[0], w.face[1], w.face[2], w.face[3], w.hist, w.recv,
+        (unsigned long long*)w.total);
+    count_launch();
+  }
+  MP_CUDA_TRY(cudaGetLastError());
+  return MP_OK;
+}
+
+// Resolves host/device outputs: device buffers are used directly, host
+// buffers get a device staging area (workspace slot 1) and a copy back.
+struct Staged {
+  void* user;
+  void* dev;
+  size_t bytes;
+};
+
+int stage(void* user, size_t bytes, size_t& cursor, std::vector<Staged>& list, char* base,
+          void** dev_out) {
+  if (!user) {
+    *dev_out = nullptr;
+    return MP_OK;
+  }
+  if (is_device_pointer(user)) {
+    *dev_out = user;
+    return MP_OK;
+  }
+  *dev_out = base ? base + cursor : nullptr;
+  list.push_back(Staged{user, *dev_out, bytes});
+  cursor = align256(cursor + bytes);
+  return MP_OK;
+}
+
+int run_with_staging(const Plan& pl, int32_t* ids, uint64_t* hist, uint64_t* recv, uint64_t* total,
+                     const uint64_t* face, cudaStream_t st) {
+  const MapDesc& D = pl.desc;
+  size_t need = 0;
+  auto host_bytes = [&](void* p, size_t b) {
+    if (p && !is_device_pointer(p)) need = align256(need + b);
+  };
+  host_bytes(ids, D.npoints * 4);
+  host_bytes(hist, (size_t)D.P * 8);
+  host_bytes(recv, (size_t)D.P * 8);
+  host_bytes(total, 8);
+  char* base = nullptr;
+  if (need) {
+    base = (char*)workspace(need, 1);
+    if (!base) return MP_ENOMEM;
+  }
+  std::vector<Staged> list;
+  size_t cur = 0;
+  Want w;
+  std::memset(&w, 0, sizeof(w));
+  void* p;
+  stage(ids, D.npoints * 4, cur, list, base, &p); w.ids = (int32_t*)p;
+  stage(hist, (size_t)D.P * 8, cur, list, base, &p); w.hist = (uint64_t*)p;
+  stage(recv, (size_t)D.P * 8, cur, list, base, &p); w.recv = (uint64_t*)p;
+  stage(total, 8, cur, list, base, &p); w.total = (uint64_t*)p;
+  for (int t = 0; t < 4; ++t) w.face[t] = face && t < D.k ? face[t] : 0;
+  int rc = run_launch(pl, w, st);
+  if (rc) return rc;
+  for (auto& s : list) MP_CUDA_TRY(cudaMemcpyAsync(s.user, s.dev, s.bytes, cudaMemcpyDeviceToHost, st));
+  if (!list.empty()) MP_CUDA_TRY(cudaStreamSynchronize(st));
+  return MP_OK;
+}
+
+}  // namespace
+
+}  // namespace mp
+
+extern "C" int mp_map_points(const mp_space* space, const mp_machine* machine, const mp_xform* chain,
+                             int n_xf, const mp_dist* dist, int32_t* ids, uint64_t* hist,
+                             void* stream) {
+  mp::Plan pl;
+  int rc = mp::build_plan(space, machine, chain, n_xf, dist, pl);
+  if (rc) return rc;
+  if (!ids && !hist) return MP_OK;
+  return mp::run_with_staging(pl, ids, hist, nullptr, nullptr, nullptr, (cudaStream_t)stream);
+}
+
+extern "C" int mp_comm_volume(const mp_space* space, const mp_machine* machine, const mp_xform* chain,
+                              int n_xf, const mp_dist* dist, const uint64_t* face_bytes,
+                              uint64_t* total, uint64_t* recv, void* stream) {
+  mp::Plan pl;
+  int rc = mp::build_plan(space, machine, chain, n_xf, dist, pl);
+  if (rc) return rc;
+  if (!face_bytes || !total) return MP_EINVAL;
+  return mp::run_with_staging(pl, nullptr, nullptr, recv, total, face_bytes, (cudaStream_t)stream);
+}

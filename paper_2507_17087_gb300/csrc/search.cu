@@ -1,0 +1,573 @@
+// decompose_search: exhaustive argmin over (factorisation, chain) candidates
+// for a 3-D matmul tile grid, and exact costs of listed candidates.
+//
+// Candidate (c, f): chain c over the canonical alphabet applied to
+// Machine(GPU) = (n, g); the result is flattened with merge(0, 1) and split
+// as f = (f0, f1, f2) with dimension 0 fastest (the splits decompose expands
+// into, Sec. 4.2); tile (i, j, k) is block-mapped to a = (floor(i f0 / M),
+// floor(j f1 / N), floor(k f2 / K)) and owned by the processor the chain
+// resolves flat(a) = a0 + f0 (a1 + f1 a2) to.  The owner of a flat index does
+// not depend on f, so each CTA tabulates node(b) for its chain once, in
+// shared memory, and every thread then scores one factorisation at a time.
+//
+// Cost (in tiles): for each operand tile A(i,k), B(k,j), C(i,j) the number of
+// distinct processors (primary) and nodes (secondary) among the points that
+// touch it, minus one.  Tiles whose two fixed coordinates fall in the same
+// pair of blocks touch the same owners, so one fibre per block pair is
+// scanned and weighted by the tiles in it.  Distinct processors along a fibre
+// equal distinct block coordinates (the chain is a bijection), which gives
+// the primary in closed form: sum_v (min(E_v, f_v) - 1) E_u E_w.
+#include <algorithm>
+#include <cstring>
+
+#include "engine.h"
+
+namespace mp {
+
+namespace {
+
+constexpr int kMaxChainPrims = 12;
+
+size_t align_up(size_t v) { return (v + 255) & ~size_t(255); }
+constexpr int kSearchMaxProcs = 16384;
+constexpr int kSmemBudget = 200 * 1024;
+
+struct ChainProg {
+  int32_t nprim;
+  int32_t pad;
+  Prim prim[kMaxChainPrims];
+};
+
+struct Fact {
+  uint32_t f[3];
+};
+
+struct Key {
+  unsigned long long p, s, idx;
+};
+
+__device__ __forceinline__ bool key_less(const Key& a, const Key& b) {
+  if (a.p != b.p) return a.p < b.p;
+  if (a.s != b.s) return a.s < b.s;
+  return a.idx < b.idx;
+}
+
+// Node of flat index b of the flattened chain space: apply the Fig. 4
+// inverse of every primitive, last to first, starting from the 1-D index.
+__device__ uint32_t resolve_node(const ChainProg& cp, uint32_t b) {
+  uint32_t a[kMaxChainPrims + 2];
+  a[0] = b;
+  int r = 1;
+  for (int o = cp.nprim - 1; o >= 0; --o) {
+    const Prim& p = cp.prim[o];
+    if (p.op == P_SPLIT) {
+      a[p.p] = a[p.p] + a[p.p + 1] * p.d;
+      for (int t = p.p + 1; t < r - 1; ++t) a[t] = a[t + 1];
+      r -= 1;
+    } else if (p.op == P_MERGE) {
+      uint32_t q, rem;
+      divmod32(a[p.p], p.div, q, rem);
+      for (int t = r; t > p.q; --t) a[t] = a[t - 1];
+      a[p.q] = q;
+      a[p.p] = rem;
+      r += 1;
+    } else {
+      uint32_t tmp = a[p.p];
+      a[p.p] = a[p.q];
+      a[p.q] = tmp;
+    }
+  }
+  return a[0];   // (node, proc) = (a[0], a[1])
+}
+
+// Iterates the distinct block coordinates of one dimension (extent E split
+// into f blocks) with the number of tiles in each:
+//   E >= f: rep = i, weight = ceil((i+1) E / f) - ceil(i E / f)
+//   E <  f: rep = floor(i f / E), weight = 1
+// using only additions (the quotient/remainder of E / f or f / E once).
+struct BlockIter {
+  uint32_t big;      // E >= f
+  uint32_t A, B, m;  // quotient, remainder, modulus
+  uint32_t r;        // running remainder
+  uint32_t rep;
+  __device__ __forceinline__ void init(uint32_t E, uint32_t f) {
+    big = E >= f;
+    if (big) { A = E / f; B = E % f; m = f; } else { A = f / E; B = f % E; m = E; }
+    r = 0;
+    rep = 0;
+  }
+  // returns the weight of the current representative and advances
+  __device__ __forceinline__ uint32_t step() {
+    uint32_t w;
+    if (big) {
+      const uint32_t borrow = r < B;
+      w = A + borrow;
+      r = r + (borrow ? m : 0) - B;
+      rep += 1;
+    } else {
+      w = 1;
+      r += B;
+      const uint32_t carry = r >= m;
+      r -= carry ? m : 0;
+      rep += A + carry;
+    }
+    return w;
+  }
+};
+
+// Distinct nodes along one fibre (count of nodes seen), bitmap per thread in
+// shared memory (word w of thread t at bm[w * nthr + t]).
+__device__ __forceinline__ uint32_t fibre_distinct(const uint16_t* __restrict__ tab, uint32_t* bm, int nthr,
+                                                   int words, uint32_t base, uint32_t stride, uint32_t E,
+                                                   uint32_t f, uint32_t n) {
+  BlockIter it;
+  it.init(E, f);
+  uint32_t D = 0;
+  for (uint32_t iv = 0; iv < n; ++iv) {
+    const uint32_t node = tab[base + stride * it.rep];
+    it.step();
+    uint32_t* wp = bm + (node >> 5) * nthr;
+    const uint32_t bit = 1u << (node & 31);
+    const uint32_t word = *wp;
+    if (!(word & bit)) {
+      *wp = word | bit;
+      ++D;
+    }
+  }
+  if ((uint32_t)words <= n) {
+    for (int w = 0; w < words; ++w) bm[w * nthr] = 0;
+  } else {
+    it.init(E, f);
+    for (uint32_t iv = 0; iv < n; ++iv) {
+      const uint32_t node = tab[base + stride * it.rep];
+      it.step();
+      bm[(node >> 5) * nthr] = 0;
+    }
+  }
+  return D;
+}
+
+// Secondary cost (tiles) of factorisation f for the chain tabulated in tab.
+__device__ unsigned long long secondary_cost(const uint16_t* __restrict__ tab, uint32_t* bm, int nthr, int words,
+                                             const uint32_t E[3], const uint32_t f[3]) {
+  const uint32_t stride[3] = {1u, f[0], f[0] * f[1]};
+  uint32_t n[3];
+  for (int t = 0; t < 3; ++t) n[t] = E[t] < f[t] ? E[t] : f[t];
+  unsigned long long sec = 0;
+  for (int v = 0; v < 3; ++v) {
+    if (n[v] <= 1) continue;   // one block along the fibre: one owner
+    const int u = v == 0 ? 1 : 0;
+    const int w = v == 2 ? 1 : 2;
+    BlockIter iw;
+    iw.init(E[w], f[w]);
+    for (uint32_t a = 0; a < n[w]; ++a) {
+      const uint32_t rep_w = iw.rep;
+      const uint32_t wt_w = iw.step();
+      BlockIter iu;
+      iu.init(E[u], f[u]);
+      unsigned long long acc = 0;
+      for (uint32_t c = 0; c < n[u]; ++c) {
+        const uint32_t rep_u = iu.rep;
+        const uint32_t wt_u = iu.step();
+        const uint32_t base = rep_u * stride[u] + rep_w * stride[w];
+        const uint32_t D = fibre_distinct(tab, bm, nthr, words, base, stride[v], E[v], f[v], n[v]);
+        acc += (unsigned long long)wt_u * (D - 1);
+      }
+      sec += (unsigned long long)wt_w * acc;
+    }
+  }
+  return sec;
+}
+
+__device__ __forceinline__ unsigned long long primary_cost(const uint32_t E[3], const uint32_t f[3]) {
+  unsigned long long p = 0;
+  for (int v = 0; v < 3; ++v) {
+    const int u = v == 0 ? 1 : 0;
+    const int w = v == 2 ? 1 : 2;
+    const uint32_t nv = E[v] < f[v] ? E[v] : f[v];
+    p += (unsigned long long)(nv - 1) * E[u] * E[w];
+  }
+  return p;
+}
+
+__device__ void block_argmin(Key& k, Key* red) {
+  for (int o = 16; o > 0; o >>= 1) {
+    Key other;
+    other.p = __shfl_down_sync(0xFFFFFFFFu, k.p, o);
+    other.s = __shfl_down_sync(0xFFFFFFFFu, k.s, o);
+    other.idx = __shfl_down_sync(0xFFFFFFFFu, k.idx, o);
+    if (key_less(other, k)) k = other;
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) red[warp] = k;
+  __syncthreads();
+  if (warp == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    k = lane < nw ? red[lane] : Key{~0ull, ~0ull, ~0ull};
+    for (int o = 16; o > 0; o >>= 1) {
+      Key other;
+      other.p = __shfl_down_sync(0xFFFFFFFFu, k.p, o);
+      other.s = __shfl_down_sync(0xFFFFFFFFu, k.s, o);
+      other.idx = __shfl_down_sync(0xFFFFFFFFu, k.idx, o);
+      if (key_less(other, k)) k = other;
+    }
+  }
+}
+
+__device__ void build_table(const ChainProg& cp, uint16_t* tab, uint32_t P) {
+  for (uint32_t b = threadIdx.x; b < P; b += blockDim.x) tab[b] = (uint16_t)resolve_node(cp, b);
+}
+
+// One CTA per chain; each thread scores factorisations tid, tid + T, ...
+// full = 1: every candidate's secondary is scanned.  full = 0: candidates
+// whose (exact, closed-form) primary exceeds the minimum primary over all
+// factorisations cannot win the lexicographic argmin and are not scanned.
+__global__ void k_search(const ChainProg* __restrict__ progs, const Fact* __restrict__ facts, int nf,
+                         uint32_t P, uint32_t E0, uint32_t E1, uint32_t E2, int words,
+                         unsigned long long nchains, int full, Key* __restrict__ chain_best) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ Key red[32];
+  uint32_t* bm = reinterpret_cast<uint32_t*>(smem_raw);
+  uint16_t* tab = reinterpret_cast<uint16_t*>(smem_raw + (size_t)words * blockDim.x * 4);
+  const uint32_t c = blockIdx.x;
+  __shared__ ChainProg cp;
+  if (threadIdx.x == 0) cp = progs[c];
+  for (int w = 0; w < words; ++w) bm[w * blockDim.x + threadIdx.x] = 0;
+  __syncthreads();
+  build_table(cp, tab, P);
+  __syncthreads();
+  const uint32_t E[3] = {E0, E1, E2};
+  unsigned long long pmin = 0;
+  if (!full) {
+    Key m{~0ull, 0, 0};
+    for (int fr = threadIdx.x; fr < nf; fr += blockDim.x) {
+      const uint32_t f[3] = {facts[fr].f[0], facts[fr].f[1], facts[fr].f[2]};
+      const unsigned long long p = primary_cost(E, f);
+      if (p < m.p) m.p = p;
+    }
+    block_argmin(m, red);
+    __shared__ unsigned long long s_pmin;
+    if (threadIdx.x == 0) s_pmin = m.p;
+    __syncthreads();
+    pmin = s_pmin;
+  }
+  Key best{~0ull, ~0ull, ~0ull};
+  for (int fr = threadIdx.x; fr < nf; fr += blockDim.x) {
+    const uint32_t f[3] = {facts[fr].f[0], facts[fr].f[1], facts[fr].f[2]};
+    Key k;
+    k.p = primary_cost(E, f);
+    if (!full && k.p > pmin) continue;
+    k.s = secondary_cost(tab, bm + threadIdx.x, blockDim.x, words, E, f);
+    k.idx = (unsigned long long)fr * nchains + c;
+    if (key_less(k, best)) best = k;
+  }
+  block_argmin(best, red);
+  if (threadIdx.x == 0) chain_best[c] = best;
+}
+
+__global__ void k_search_final(const Key* __restrict__ chain_best, unsigned long long n, Key* __restrict__ out) {
+  __shared__ Key red[32];
+  Key best{~0ull, ~0ull, ~0ull};
+  for (unsigned long long i = threadIdx.x; i < n; i += blockDim.x) {
+    const Key k = chain_best[i];
+    if (key_less(k, best)) best = k;
+  }
+  block_argmin(best, red);
+  if (threadIdx.x == 0) *out = best;
+}
+
+// One CTA per listed candidate: the chain's table in shared memory, the
+// fibres of the three families spread over the threads.
+__global__ void k_candidate_costs(const ChainProg* __restrict__ progs, const Fact* __restrict__ facts, int nf,
+                                  const int64_t* __restrict__ idx, unsigned long long nchains, uint32_t P,
+                                  uint32_t E0, uint32_t E1, uint32_t E2, int words,
+                                  unsigned long long tile_bytes, uint64_t* __restrict__ prim_out,
+                                  uint64_t* __restrict__ sec_out) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ ChainProg cp;
+  __shared__ unsigned long long red[32];
+  uint32_t* bm = reinterpret_cast<uint32_t*>(smem_raw);
+  uint16_t* tab = reinterpret_cast<uint16_t*>(smem_raw + (size_t)words * blockDim.x * 4);
+  const unsigned long long id = (unsigned long long)idx[blockIdx.x];
+  if (idx[blockIdx.x] < 0 || id >= nchains * (unsigned long long)nf) {   // out of range: flag, no access
+    if (threadIdx.x == 0) {
+      prim_out[blockIdx.x] = ~0ull;
+      sec_out[blockIdx.x] = ~0ull;
+    }
+    return;
+  }
+  const unsigned long long fr = id / nchains, c = id % nchains;
+  if (threadIdx.x == 0) cp = progs[c];
+  for (int w = 0; w < words; ++w) bm[w * blockDim.x + threadIdx.x] = 0;
+  __syncthreads();
+  build_table(cp, tab, P);
+  __syncthreads();
+  const uint32_t E[3] = {E0, E1, E2};
+  const uint32_t f[3] = {facts[fr].f[0], facts[fr].f[1], facts[fr].f[2]};
+  const uint32_t stride[3] = {1u, f[0], f[0] * f[1]};
+  uint32_t n[3];
+  for (int t = 0; t < 3; ++t) n[t] = E[t] < f[t] ? E[t] : f[t];
+  unsigned long long sec = 0;
+  for (int v = 0; v < 3; ++v) {
+    if (n[v] <= 1) continue;
+    const int u = v == 0 ? 1 : 0;
+    const int w = v == 2 ? 1 : 2;
+    const uint32_t nfib = n[u] * n[w];
+    for (uint32_t fb = threadIdx.x; fb < nfib; fb += blockDim.x) {
+      const uint32_t iu = fb % n[u], iw = fb / n[u];
+      // representative and weight of block iu (iw) directly
+      auto rep_wt = [&](int t, uint32_t i, uint32_t& rep, uint32_t& wt) {
+        if (E[t] >= f[t]) {
+          rep = i;
+          const unsigned long long lo = ((unsigned long long)i * E[t] + f[t] - 1) / f[t];
+          const unsigned long long hi = ((unsigned long long)(i + 1) * E[t] + f[t] - 1) / f[t];
+          wt = (uint32_t)(hi - lo);
+        } else {
+          rep = (uint32_t)((unsigned long long)i * f[t] / E[t]);
+          wt = 1;
+        }
+      };
+      uint32_t ru, wu, rw, ww;
+      rep_wt(u, iu, ru, wu);
+      rep_wt(w, iw, rw, ww);
+      const uint32_t base = ru * stride[u] + rw * stride[w];
+      const uint32_t D = fibre_distinct(tab, bm + threadIdx.x, blockDim.x, words, base, stride[v], E[v], f[v], n[v]);
+      sec += (unsigned long long)wu * ww * (D - 1);
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) sec += __shfl_down_sync(0xFFFFFFFFu, sec, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = sec;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long s = 0;
+    for (int w = 0; w < (int)((blockDim.x + 31) >> 5); ++w) s += red[w];
+    prim_out[blockIdx.x] = primary_cost(E, f) * tile_bytes;
+    sec_out[blockIdx.x] = s * tile_bytes;
+  }
+}
+
+// ----------------------------------------------------------------- host side
+
+struct SearchSpace {
+  std::vector<std::vector<int64_t>> facts;
+  std::vector<std::vector<CanonOp>> chains;
+  std::vector<ChainProg> progs;
+  std::vector<Fact> fdev;
+  int words = 0;
+  int threads = 0;
+  size_t smem = 0;
+};
+
+// The resolution program of chain c: the chain's primitives, then the
+// flattening merges, with the shapes each one was applied to.
+ChainProg compile_chain(int64_t n, int64_t g, const std::vector<CanonOp>& ch) {
+  ChainProg cp;
+  std::memset(&cp, 0, sizeof(cp));
+  std::vector<int64_t> shape = {n, g};
+  auto push = [&](int op, int p, int q, int64_t d) {
+    Prim& pr = cp.prim[cp.nprim++];
+    pr.op = op;
+    pr.p = p;
+    pr.q = q;
+    pr.rank_before = (int32_t)shape.size();
+    if (op == P_SPLIT) {
+      pr.d = (uint32_t)d;
+    } else if (op == P_MERGE) {
+      pr.d = (uint32_t)shape[p];
+      pr.div = make_div32(pr.d);
+    }
+  };
+  for (const CanonOp& c : ch) {
+    push(c.op, c.p, c.q, c.d);
+    apply_canon(shape, c);
+  }
+  while (shape.size() > 1) {
+    push(P_MERGE, 0, 1, 0);
+    shape[0] *= shape[1];
+    shape.erase(shape.begin() + 1);
+  }
+  return cp;
+}
+
+int validate_query(const mp_search_query& q) {
+  if (q.M < 1 || q.N < 1 || q.K < 1 || q.M > (1 << 20) || q.N > (1 << 20) || q.K > (1 << 20)) return MP_EINVAL;
+  if (q.procs < 1 || q.procs_per_node < 1 || q.procs % q.procs_per_node) return MP_EINVAL;
+  if (q.max_depth < 0 || q.max_depth > 4) return MP_EINVAL;
+  if (q.procs > kSearchMaxProcs) return MP_ENOTSUP;
+  const unsigned __int128 worst = ((unsigned __int128)q.M * q.K + (unsigned __int128)q.K * q.N +
+                                   (unsigned __int128)q.M * q.N) * (uint64_t)q.procs * q.tile_bytes;
+  if (worst >> 64) return MP_EOVERFLOW;
+  return MP_OK;
+}
+
+int prepare(const mp_search_query& q, SearchSpace& S) {
+  const int64_t n = q.procs / q.procs_per_node, g = q.procs_per_node;
+  S.facts = ordered_factorisations(q.procs, 3);
+  S.chains = canonical_chains(n, g, q.max_depth);
+  S.progs.resize(S.chains.size());
+  for (size_t c = 0; c < S.chains.size(); ++c) S.progs[c] = compile_chain(n, g, S.chains[c]);
+  S.fdev.resize(S.facts.size());
+  for (size_t i = 0; i < S.facts.size(); ++i)
+    for (int t = 0; t < 3; ++t) S.fdev[i].f[t] = (uint32_t)S.facts[i][t];
+  S.words = (int)((n + 31) / 32);
+  const size_t tab = align_up((size_t)q.procs * 2);
+  int threads = 256;
+  while (threads > 32 && tab + (size_t)S.words * 4 * threads > (size_t)kSmemBudget) threads -= 32;
+  if (tab + (size_t)S.words * 4 * threads > (size_t)kSmemBudget) return MP_ENOTSUP;
+  S.threads = threads;
+  S.smem = (size_t)S.words * 4 * threads + tab;
+  return MP_OK;
+}
+
+int upload(const SearchSpace& S, cudaStream_t st, ChainProg** d_progs, Fact** d_facts, char** rest,
+           size_t rest_bytes, int slot) {
+  const size_t pb = align_up(S.progs.size() * sizeof(ChainProg));
+  const size_t fb = align_up(S.fdev.size() * sizeof(Fact));
+  char* ws = (char*)workspace(pb + fb + rest_bytes, slot);
+  if (!ws) return MP_ENOMEM;
+  *d_progs = (ChainProg*)ws;
+  *d_facts = (Fact*)(ws + pb);
+  *rest = ws + pb + fb;
+  MP_CUDA_TRY(cudaMemcpyAsync(*d_progs, S.progs.data(), S.progs.size() * sizeof(ChainProg),
+                              cudaMemcpyHostToDevice, st));
+  MP_CUDA_TRY(cudaMemcpyAsync(*d_facts, S.fdev.data(), S.fdev.size() * sizeof(Fact),
+                              cudaMemcpyHostToDevice, st));
+  return MP_OK;
+}
+
+void fill_result(const mp_search_query& q, const SearchSpace& S, const Key& k, mp_search_result& r) {
+  std::memset(&r, 0, sizeof(r));
+  const uint64_t NC = S.chains.size();
+  r.index = (int64_t)k.idx;
+  const uint64_t fr = k.idx / NC, c = k.idx % NC;
+  for (int t = 0; t < 3; ++t) r.f[t] = S.facts[fr][t];
+  r.chain_rank = (int64_t)c;
+  r.chain_len = (int32_t)S.chains[c].size();
+  for (int o = 0; o < r.chain_len; ++o) {
+    const CanonOp& op = S.chains[c][o];
+    mp_xform& x = r.chain[o];
+    x.op = op.op == P_SPLIT ? MP_SPLIT : (op.op == P_MERGE ? MP_MERGE : MP_SWAP);
+    x.i = op.p;
+    x.j = op.op == P_SPLIT ? 0 : op.q;
+    x.d = op.op == P_SPLIT ? op.d : 0;
+  }
+  r.primary_bytes = k.p * q.tile_bytes;
+  r.secondary_bytes = k.s * q.tile_bytes;
+  r.n_chains = (int64_t)NC;
+  r.n_factorisations = (int64_t)S.facts.size();
+  r.n_candidates = r.n_chains * r.n_factorisations;
+}
+
+}  // namespace
+
+}  // namespace mp
+
+extern "C" int mp_decompose_search(const mp_search_query* queries, int n_queries, mp_search_result* out,
+                                   void* stream) {
+  using namespace mp;
+  if (n_queries < 0 || (n_queries > 0 && (!queries || !out))) return MP_EINVAL;
+  for (int i = 0; i < n_queries; ++i) {
+    int rc = validate_query(queries[i]);
+    if (rc) return rc;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  for (int i = 0; i < n_queries; ++i) {
+    const mp_search_query& q = queries[i];
+    SearchSpace S;
+    int rc = prepare(q, S);
+    if (rc) return rc;
+    const uint64_t NC = S.chains.size();
+    ChainProg* d_progs;
+    Fact* d_facts;
+    char* rest;
+    const size_t best_bytes = align_up(NC * sizeof(Key)) + sizeof(Key);
+    rc = upload(S, st, &d_progs, &d_facts, &rest, best_bytes, 2);
+    if (rc) return rc;
+    Key* chain_best = (Key*)rest;
+    Key* d_out = (Key*)(rest + align_up(NC * sizeof(Key)));
+    if (S.smem > 48 * 1024)
+      MP_CUDA_TRY(cudaFuncSetAttribute(k_search, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S.smem));
+    k_search<<<(unsigned)NC, S.threads, S.smem, st>>>(d_progs, d_facts, (int)S.facts.size(), (uint32_t)q.procs,
+                                                      (uint32_t)q.M, (uint32_t)q.N, (uint32_t)q.K, S.words, NC,
+                                                      (q.flags & MP_SEARCH_FULL) ? 1 : 0, chain_best);
+    count_launch();
+    k_search_final<<<1, 1024, 0, st>>>(chain_best, NC, d_out);
+    count_launch();
+    MP_CUDA_TRY(cudaGetLastError());
+    Key best;
+    MP_CUDA_TRY(cudaMemcpyAsync(&best, d_out, sizeof(Key), cudaMemcpyDeviceToHost, st));
+    MP_CUDA_TRY(cudaStreamSynchronize(st));
+    fill_result(q, S, best, out[i]);
+  }
+  return MP_OK;
+}
+
+extern "C" int mp_candidate_costs(const mp_search_query* query, const int64_t* indices, int64_t n,
+                                  uint64_t* primary, uint64_t* secondary, void* stream) {
+  using namespace mp;
+  if (!query || n < 0 || (n > 0 && (!indices || !primary || !secondary))) return MP_EINVAL;
+  int rc = validate_query(*query);
+  if (rc) return rc;
+  if (n == 0) return MP_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  SearchSpace S;
+  rc = prepare(*query, S);
+  if (rc) return rc;
+  const uint64_t NC = S.chains.size(), NF = S.facts.size();
+  const bool idx_dev = is_device_pointer(indices);
+  const bool p_dev = is_device_pointer(primary), s_dev = is_device_pointer(secondary);
+  std::vector<int64_t> host_idx;
+  if (!idx_dev) {
+    host_idx.assign(indices, indices + n);
+    for (int64_t v : host_idx)
+      if (v < 0 || (uint64_t)v >= NC * NF) return MP_EINVAL;
+  }
+  const size_t ib = align_up((size_t)n * 8);
+  ChainProg* d_progs;
+  Fact* d_facts;
+  char* rest;
+  rc = upload(S, st, &d_progs, &d_facts, &rest, 3 * ib, 3);
+  if (rc) return rc;
+  int64_t* d_idx = idx_dev ? (int64_t*)indices : (int64_t*)rest;
+  uint64_t* d_p = p_dev ? primary : (uint64_t*)(rest + ib);
+  uint64_t* d_s = s_dev ? secondary : (uint64_t*)(rest + 2 * ib);
+  if (!idx_dev) MP_CUDA_TRY(cudaMemcpyAsync(d_idx, host_idx.data(), n * 8, cudaMemcpyHostToDevice, st));
+  if (S.smem > 48 * 1024)
+    MP_CUDA_TRY(cudaFuncSetAttribute(k_candidate_costs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S.smem));
+  k_candidate_costs<<<(unsigned)n, S.threads, S.smem, st>>>(d_progs, d_facts, (int)NF, d_idx, NC, (uint32_t)query->procs,
+                                                             (uint32_t)query->M, (uint32_t)query->N,
+                                                             (uint32_t)query->K, S.words, query->tile_bytes, d_p,
+                                                             d_s);
+  count_launch();
+  MP_CUDA_TRY(cudaGetLastError());
+  if (!p_dev) MP_CUDA_TRY(cudaMemcpyAsync(primary, d_p, n * 8, cudaMemcpyDeviceToHost, st));
+  if (!s_dev) MP_CUDA_TRY(cudaMemcpyAsync(secondary, d_s, n * 8, cudaMemcpyDeviceToHost, st));
+  if (!p_dev || !s_dev) MP_CUDA_TRY(cudaStreamSynchronize(st));
+  return MP_OK;
+}
+
+extern "C" int mp_search_candidate(const mp_search_query* query, int64_t index, int64_t* f, mp_xform* chain,
+                                   int32_t* chain_len) {
+  using namespace mp;
+  if (!query || !f || !chain || !chain_len) return MP_EINVAL;
+  int rc = validate_query(*query);
+  if (rc) return rc;
+  const int64_t n = query->procs / query->procs_per_node, g = query->procs_per_node;
+  auto facts = ordered_factorisations(query->procs, 3);
+  auto chains = canonical_chains(n, g, query->max_depth);
+  const int64_t NC = (int64_t)chains.size();
+  if (index < 0 || index >= NC * (int64_t)facts.size()) return MP_EINVAL;
+  const int64_t fr = index / NC, c = index % NC;
+  for (int t = 0; t < 3; ++t) f[t] = facts[fr][t];
+  *chain_len = (int32_t)chains[c].size();
+  for (int o = 0; o < *chain_len; ++o) {
+    const CanonOp& op = chains[c][o];
+    mp_xform& x = chain[o];
+    std::memset(&x, 0, sizeof(x));
+    x.op = op.op == P_SPLIT ? MP_SPLIT : (op.op == P_MERGE ? MP_MERGE : MP_SWAP);
+    x.i = op.p;
+    x.j = op.op == P_SPLIT ? 0 : op.q;
+    x.d = op.op == P_SPLIT ? op.d : 0;
+  }
+  return MP_OK;
+}

@@ -1,0 +1,346 @@
+"""Thin ctypes binding of the engine's C ABI (include/mapple.h).
+
+Argument marshalling only: every step of the hot path runs in the CUDA
+kernels of ``libmapple_gb300.so``.  There is no CPU fallback: if the library
+has not been built, every call raises.
+
+Buffers may be torch tensors (CUDA or CPU), numpy arrays, or raw integer
+pointers.  ``stream`` defaults to torch's current CUDA stream.
+
+Chain vocabulary (plain tuples):
+  ("split", i, d), ("merge", p, q), ("swap", p, q),
+  ("decompose", i, (l1..lk)), ("balance_split", i, k)
+Distributions: ("block",), ("cyclic",), ("block_cyclic", b), ("hier",),
+("linear_cyclic",).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+_lock = threading.Lock()
+_lib = None
+
+OPS = {"split": 0, "merge": 1, "swap": 2, "decompose": 3, "balance_split": 4}
+OP_NAMES = {v: k for k, v in OPS.items()}
+DISTS = {"block": 0, "cyclic": 1, "block_cyclic": 2, "hier": 3, "linear_cyclic": 4}
+STATUS = {0: "MP_OK", 1: "MP_EINVAL", 2: "MP_EOVERFLOW", 3: "MP_ENOMEM", 4: "MP_ECUDA",
+          5: "MP_ETIMEOUT", 6: "MP_ENOTSUP"}
+
+
+class MapleError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {STATUS.get(status, status)} ({strerror(status)})")
+
+
+class mp_space(ctypes.Structure):
+    _fields_ = [("rank", ctypes.c_int32), ("reserved", ctypes.c_int32), ("ext", ctypes.c_int64 * 4)]
+
+
+class mp_machine(ctypes.Structure):
+    _fields_ = [("nodes", ctypes.c_int32), ("procs_per_node", ctypes.c_int32)]
+
+
+class mp_xform(ctypes.Structure):
+    _fields_ = [("op", ctypes.c_int32), ("i", ctypes.c_int32), ("j", ctypes.c_int32),
+                ("k", ctypes.c_int32), ("d", ctypes.c_int64), ("T", ctypes.c_int64 * 4)]
+
+
+class mp_dist(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("b", ctypes.c_int32)]
+
+
+class mp_search_query(ctypes.Structure):
+    _fields_ = [("M", ctypes.c_int64), ("N", ctypes.c_int64), ("K", ctypes.c_int64),
+                ("procs", ctypes.c_int32), ("procs_per_node", ctypes.c_int32),
+                ("max_depth", ctypes.c_int32), ("flags", ctypes.c_int32),
+                ("tile_bytes", ctypes.c_uint64)]
+
+
+class mp_search_result(ctypes.Structure):
+    _fields_ = [("index", ctypes.c_int64), ("f", ctypes.c_int64 * 3), ("chain_rank", ctypes.c_int64),
+                ("chain_len", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("chain", mp_xform * 4), ("primary_bytes", ctypes.c_uint64),
+                ("secondary_bytes", ctypes.c_uint64), ("n_candidates", ctypes.c_int64),
+                ("n_chains", ctypes.c_int64), ("n_factorisations", ctypes.c_int64)]
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """The loaded engine library; raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(_build.LIB):
+                raise RuntimeError("libmapple_gb300.so is not built: run __graft_entry__.build() "
+                                   "(the engine has no CPU fallback)")
+            L = ctypes.CDLL(_build.LIB)
+            V, I, I64, U64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_uint64
+            sig = {
+                "mp_map_points": (I, [V, V, V, I, V, V, V, V]),
+                "mp_comm_volume": (I, [V, V, V, I, V, V, V, V, V]),
+                "mp_decompose_search": (I, [V, I, V, V]),
+                "mp_candidate_costs": (I, [V, V, I64, V, V, V]),
+                "mp_plan": (I, [V, V, V, I, V, V, V, V, V, I]),
+                "mp_chain_from_draws": (I, [I, I, I, V, V, V]),
+                "mp_search_space": (I, [I, I, I, V, V]),
+                "mp_search_candidate": (I, [V, I64, V, V, V]),
+                "mp_strerror": (ctypes.c_char_p, [I]),
+                "mp_kernel_launches": (U64, []),
+                "mp_set_kernel_timer": (I, [V, V]),
+                "mp_descriptor_bytes": (U64, []),
+            }
+            for name, (res, args) in sig.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def strerror(status: int) -> str:
+    try:
+        return lib().mp_strerror(status).decode()
+    except Exception:  # noqa: BLE001 - used while formatting another error
+        return "?"
+
+
+def _check(rc: int, where: str):
+    if rc != 0:
+        raise MapleError(rc, where)
+
+
+# ----------------------------------------------------------------- marshalling
+
+def make_space(L) -> mp_space:
+    s = mp_space()
+    s.rank = len(L)
+    for t, v in enumerate(L):
+        s.ext[t] = int(v)
+    return s
+
+
+def make_machine(machine) -> mp_machine:
+    m = mp_machine()
+    m.nodes, m.procs_per_node = int(machine[0]), int(machine[1])
+    return m
+
+
+def make_chain(chain):
+    n = len(chain)
+    arr = (mp_xform * max(n, 1))()
+    for o, op in enumerate(chain):
+        x = arr[o]
+        name = op[0]
+        x.op = OPS[name]
+        if name == "split":
+            x.i, x.d = int(op[1]), int(op[2])
+        elif name in ("merge", "swap"):
+            x.i, x.j = int(op[1]), int(op[2])
+        elif name == "decompose":
+            T = tuple(op[2])
+            x.i, x.k = int(op[1]), len(T)
+            for m, v in enumerate(T):
+                x.T[m] = int(v)
+        elif name == "balance_split":
+            x.i, x.k = int(op[1]), int(op[2])
+        else:
+            raise ValueError(f"unknown transform {name!r}")
+    return arr, n
+
+
+def make_dist(dist) -> mp_dist:
+    d = mp_dist()
+    d.kind = DISTS[dist[0]]
+    d.b = int(dist[1]) if len(dist) > 1 else 1
+    return d
+
+
+def _ptr(buf):
+    """Raw address of a torch tensor, numpy array or int (None -> NULL)."""
+    if buf is None:
+        return None
+    if isinstance(buf, int):
+        return buf
+    if isinstance(buf, np.ndarray):
+        if not buf.flags["C_CONTIGUOUS"]:
+            raise ValueError("buffer must be contiguous")
+        return buf.ctypes.data
+    if hasattr(buf, "data_ptr"):
+        if not buf.is_contiguous():
+            raise ValueError("buffer must be contiguous")
+        return buf.data_ptr()
+    raise TypeError(f"unsupported buffer type {type(buf)}")
+
+
+def _stream(stream):
+    if stream is not None:
+        return int(stream) if not hasattr(stream, "cuda_stream") else stream.cuda_stream
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+    except ImportError:
+        pass
+    return None
+
+
+def resolve_chain(machine, chain=None, draws=None):
+    """Explicit chain tuples, or a canonical chain built from draws."""
+    if chain is not None:
+        return list(chain)
+    return chain_from_draws(machine[0], machine[1], draws or [])
+
+
+# ----------------------------------------------------------------- entry points
+
+def map_points(L, machine, chain, dist, ids=None, hist=None, stream=None):
+    """ids[lin] (int32, C order) and hist[P] (uint64) of one launch."""
+    sp, mc, ds = make_space(L), make_machine(machine), make_dist(dist)
+    ch, n = make_chain(chain)
+    rc = lib().mp_map_points(ctypes.byref(sp), ctypes.byref(mc), ch, n, ctypes.byref(ds),
+                             _ptr(ids), _ptr(hist), _stream(stream))
+    _check(rc, "mp_map_points")
+
+
+def comm_volume(L, machine, chain, dist, face_bytes, total, recv=None, stream=None):
+    """total[0] (uint64) = halo bytes; recv[P] = bytes received per processor."""
+    sp, mc, ds = make_space(L), make_machine(machine), make_dist(dist)
+    ch, n = make_chain(chain)
+    fb = (ctypes.c_uint64 * 4)(*([int(v) for v in face_bytes] + [0] * (4 - len(face_bytes))))
+    rc = lib().mp_comm_volume(ctypes.byref(sp), ctypes.byref(mc), ch, n, ctypes.byref(ds), fb,
+                              _ptr(total), _ptr(recv), _stream(stream))
+    _check(rc, "mp_comm_volume")
+
+
+def plan(L, machine, chain, dist):
+    """(final shape, expanded primitives) -- host planning only, no GPU."""
+    sp, mc, ds = make_space(L), make_machine(machine), make_dist(dist)
+    ch, n = make_chain(chain)
+    rank = ctypes.c_int32(0)
+    shape = (ctypes.c_int64 * 32)()
+    nprim = ctypes.c_int32(0)
+    prims = (ctypes.c_int64 * (4 * 256))()
+    rc = lib().mp_plan(ctypes.byref(sp), ctypes.byref(mc), ch, n, ctypes.byref(ds),
+                       ctypes.byref(rank), shape, ctypes.byref(nprim), prims, 256)
+    _check(rc, "mp_plan")
+    out = []
+    for o in range(min(nprim.value, 256)):
+        op, p, q, d = prims[4 * o:4 * o + 4]
+        out.append((OP_NAMES[op], p, q, d))
+    return tuple(shape[: rank.value]), out
+
+
+def plan_status(L, machine, chain, dist) -> int:
+    sp, mc, ds = make_space(L), make_machine(machine), make_dist(dist)
+    ch, n = make_chain(chain)
+    return lib().mp_plan(ctypes.byref(sp), ctypes.byref(mc), ch, n, ctypes.byref(ds),
+                         None, None, None, None, 0)
+
+
+def chain_from_draws(nodes, procs_per_node, draws):
+    d = np.ascontiguousarray(np.asarray(draws, dtype=np.uint64))
+    out = (mp_xform * max(len(d), 1))()
+    n = ctypes.c_int32(0)
+    rc = lib().mp_chain_from_draws(int(nodes), int(procs_per_node), len(d),
+                                   d.ctypes.data if len(d) else None, out, ctypes.byref(n))
+    _check(rc, "mp_chain_from_draws")
+    return [xform_tuple(out[o]) for o in range(n.value)]
+
+
+def xform_tuple(x):
+    name = OP_NAMES[x.op]
+    if name == "split":
+        return ("split", x.i, x.d)
+    if name in ("merge", "swap"):
+        return (name, x.i, x.j)
+    if name == "decompose":
+        return ("decompose", x.i, tuple(x.T[m] for m in range(x.k)))
+    return ("balance_split", x.i, x.k)
+
+
+def search_space(procs, procs_per_node, max_depth):
+    nf, nc = ctypes.c_int64(0), ctypes.c_int64(0)
+    _check(lib().mp_search_space(procs, procs_per_node, max_depth, ctypes.byref(nf), ctypes.byref(nc)),
+           "mp_search_space")
+    return nf.value, nc.value
+
+
+SEARCH_FULL = 1
+
+
+def make_query(M, N, K, procs, procs_per_node, max_depth=3, tile_bytes=512 * 512 * 4, full=False):
+    q = mp_search_query()
+    q.flags = SEARCH_FULL if full else 0
+    q.M, q.N, q.K = int(M), int(N), int(K)
+    q.procs, q.procs_per_node, q.max_depth = int(procs), int(procs_per_node), int(max_depth)
+    q.tile_bytes = int(tile_bytes)
+    return q
+
+
+def decompose_search(queries, full=False, stream=None):
+    """queries: list of mp_search_query (or dicts from workloads.search_queries)."""
+    qs = [q if isinstance(q, mp_search_query) else
+          make_query(*q["MNK"], q["machine"][0] * q["machine"][1], q["machine"][1],
+                     q["max_depth"], q["tile_bytes"], full=full) for q in queries]
+    arr = (mp_search_query * len(qs))(*qs)
+    out = (mp_search_result * len(qs))()
+    _check(lib().mp_decompose_search(arr, len(qs), out, _stream(stream)), "mp_decompose_search")
+    res = []
+    for r in out:
+        res.append({"index": r.index, "f": tuple(r.f), "chain_rank": r.chain_rank,
+                    "chain": tuple(xform_tuple(r.chain[o]) for o in range(r.chain_len)),
+                    "primary_bytes": r.primary_bytes, "secondary_bytes": r.secondary_bytes,
+                    "n_candidates": r.n_candidates, "n_chains": r.n_chains,
+                    "n_factorisations": r.n_factorisations})
+    return res
+
+
+def _query(q, full=False):
+    if isinstance(q, mp_search_query):
+        return q
+    return make_query(*q["MNK"], q["machine"][0] * q["machine"][1], q["machine"][1], q["max_depth"],
+                      q["tile_bytes"], full=full)
+
+
+def search_candidate(query, index):
+    """(f, chain) of candidate `index` of a search query (host only)."""
+    q = _query(query)
+    f = (ctypes.c_int64 * 3)()
+    ch = (mp_xform * 4)()
+    n = ctypes.c_int32(0)
+    _check(lib().mp_search_candidate(ctypes.byref(q), int(index), f, ch, ctypes.byref(n)),
+           "mp_search_candidate")
+    return tuple(f), tuple(xform_tuple(ch[o]) for o in range(n.value))
+
+
+def candidate_costs(query, indices, primary, secondary, stream=None):
+    q = query if isinstance(query, mp_search_query) else \
+        make_query(*query["MNK"], query["machine"][0] * query["machine"][1], query["machine"][1],
+                   query["max_depth"], query["tile_bytes"])
+    n = len(indices)
+    _check(lib().mp_candidate_costs(ctypes.byref(q), _ptr(indices), n, _ptr(primary), _ptr(secondary),
+                                    _stream(stream)), "mp_candidate_costs")
+
+
+def kernel_launches() -> int:
+    return int(lib().mp_kernel_launches())
+
+
+def set_kernel_timer(start_event, stop_event):
+    """Time the next id-writer kernel with two cudaEvent_t handles (or torch events)."""
+    h = lambda e: None if e is None else (e.cuda_event if hasattr(e, "cuda_event") else int(e))
+    _check(lib().mp_set_kernel_timer(h(start_event), h(stop_event)), "mp_set_kernel_timer")
+
+
+def descriptor_bytes() -> int:
+    return int(lib().mp_descriptor_bytes())

@@ -1,0 +1,132 @@
+"""Host-side logic of the engine, on CPU (no kernel launches).
+
+The C-ABI library loads without a GPU; its planner (validation, decompose
+expansion, rank fix-up), random-chain builder and search-space enumeration
+must agree with the oracle's independent implementations.
+"""
+import ctypes
+import math
+import os
+import re
+
+import pytest
+
+import oracle as O
+from paper_2507_17087_gb300 import native as N
+from paper_2507_17087_gb300 import workloads as W
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(__file__)), "include", "mapple.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(mp_\w+)\s*\(", text)))
+
+
+def test_library_exports_every_declared_symbol():
+    lib = ctypes.CDLL(N.library_path())
+    names = declared_functions()
+    assert "mp_map_points" in names and "mp_comm_volume" in names and "mp_decompose_search" in names
+    for name in names:
+        assert hasattr(lib, name), f"{name} declared in include/mapple.h but not exported"
+
+
+def test_status_strings():
+    for code in range(7):
+        assert N.strerror(code) and N.strerror(code) != "unknown status"
+
+
+def _random_case(rng):
+    k = rng.randint(1, 4)
+    L = tuple(rng.randint(1, 50) for _ in range(k))
+    machine = (rng.randint(1, 64), rng.randint(1, 8))
+    draws = [rng.next() for _ in range(rng.randint(0, 5))]
+    chain = O.chain_from_draws(*machine, draws)
+    if rng.randint(0, 3) == 0:
+        kk = rng.randint(1, 3)
+        chain = chain + [("decompose", 0, tuple(rng.randint(1, 30) for _ in range(kk)))]
+    if rng.randint(0, 5) == 0:
+        chain = chain + [("balance_split", 0, rng.randint(1, 3))]
+    kind = rng.choice(W.DIST_KINDS)
+    dist = ("block_cyclic", rng.randint(1, 5)) if kind == "block_cyclic" else (kind,)
+    return L, machine, chain, dist
+
+
+def test_plan_matches_oracle_expansion():
+    rng = W.rng(900)
+    for _ in range(400):
+        L, machine, chain, dist = _random_case(rng)
+        shape, prims = N.plan(L, machine, chain, dist)
+        ref = O.Launch(L, machine, chain, dist)
+        assert shape == ref.final_shape()
+        want = [(op, p, q if op != "split" else -1, d if op == "split" else 0) for op, p, q, d in ref.expand()]
+        got = [(op, p, q if op != "split" else -1, d if op == "split" else 0) for op, p, q, d in prims]
+        assert got == want
+
+
+def test_chain_from_draws_matches_oracle():
+    rng = W.rng(901)
+    for _ in range(300):
+        machine = (rng.randint(1, 300), rng.randint(1, 8))
+        draws = [rng.next() for _ in range(rng.randint(0, 6))]
+        assert N.chain_from_draws(*machine, draws) == O.chain_from_draws(*machine, draws)
+
+
+@pytest.mark.parametrize("P,g,D", [(512, 8, 3), (2520, 8, 2), (4096, 8, 2), (3600, 8, 1), (16, 2, 3),
+                                   (6, 3, 3), (1, 1, 2), (7, 7, 3)])
+def test_search_space_matches_oracle(P, g, D):
+    nf, nc = N.search_space(P, g, D)
+    assert nf == len(O.factorisations(P, 3))
+    assert nc == len(O.chains(P // g, g, D))
+
+
+def test_search_candidate_decoding_matches_oracle_order():
+    for P, g, D in [(16, 2, 3), (24, 4, 2), (512, 8, 2)]:
+        q = N.make_query(8, 8, 8, P, g, D)
+        fs = O.factorisations(P, 3)
+        chains = O.chains(P // g, g, D)
+        rng = W.rng(P)
+        for _ in range(200):
+            idx = rng.next() % (len(fs) * len(chains))
+            f, chain = N.search_candidate(q, idx)
+            assert f == fs[idx // len(chains)]
+            assert chain == chains[idx % len(chains)]
+
+
+def test_invalid_plans_rejected():
+    cases = [
+        (((0, 4), (2, 2), [], ("block",)), 1),
+        (((4, 4), (2, 2), [("split", 0, 3)], ("block",)), 1),
+        (((4, 4), (2, 2), [("split", 2, 1)], ("block",)), 1),
+        (((4, 4), (2, 2), [("merge", 1, 0)], ("block",)), 1),
+        (((4, 4), (2, 2), [("merge", 0, 2)], ("block",)), 1),
+        (((4, 4), (2, 2), [("swap", 1, 1)], ("block",)), 1),
+        (((4, 4), (2, 2), [("decompose", 0, (0, 2))], ("block",)), 1),
+        (((4, 4), (2, 2), [("balance_split", 0, 5)], ("block",)), 1),
+        (((4, 4), (2, 2), [], ("block_cyclic", 0)), 1),
+        (((4, 4), (0, 2), [], ("block",)), 1),
+        (((1 << 31, 1 << 31, 1 << 2), (2, 2), [], ("block",)), 2),
+        (((1 << 39,), (2, 2), [], ("block",)), 6),
+        (((4, 4), (1 << 20, 1 << 10), [], ("block",)), 6),
+        (((1, 2, 3, 4, 5), (2, 2), [], ("block",)), 1),
+    ]
+    for (L, machine, chain, dist), want in cases:
+        if len(L) > 4:
+            sp = N.mp_space()
+            sp.rank = 5
+            mc, ds = N.make_machine(machine), N.make_dist(dist)
+            rc = N.lib().mp_plan(ctypes.byref(sp), ctypes.byref(mc), None, 0, ctypes.byref(ds),
+                                 None, None, None, None, 0)
+        else:
+            rc = N.plan_status(L, machine, chain, dist)
+        assert rc == want, (L, machine, chain, dist, rc)
+
+
+def test_invalid_search_queries_rejected():
+    lib = N.lib()
+    out = (N.mp_search_result * 1)()
+    for q in [N.make_query(0, 4, 4, 8, 2), N.make_query(4, 4, 4, 9, 2), N.make_query(4, 4, 4, 8, 2, 5),
+              N.make_query(4, 4, 4, 1 << 15, 8), N.make_query(1 << 21, 4, 4, 8, 2)]:
+        arr = (N.mp_search_query * 1)(q)
+        assert lib.mp_decompose_search(arr, 1, out, None) != 0
