@@ -34,7 +34,6 @@ namespace mp {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kUnroll = 4;
 constexpr uint64_t kTableMax = uint64_t(1) << 22;   // per-dimension c_t tables kept in HBM/L2
 constexpr uint32_t kSmemTMax = 16384;               // T staged in shared memory up to this P
 constexpr uint32_t kSmemLastMax = 8192;             // c_last staged in shared memory
@@ -163,126 +162,169 @@ __global__ void __launch_bounds__(kThreads) k_dimtables(const __grid_constant__ 
 }
 
 // ----------------------------------------------------------------- k_ids
+//
+// Each warp owns one contiguous range of 4-point groups; lane l takes groups
+// start + l, start + l + 32, ... so that every store instruction of the warp
+// writes 512 contiguous bytes.  Between two groups of a lane the linear index
+// advances by 128 points: x_last advances by 128 and the row (the slow
+// coordinates) only changes when x_last wraps, so the row's contribution
+// base(row) = sum_{t < k-1} c_t(x_t) is recomputed once per row.
 
-template <bool WIDE>
-__device__ __forceinline__ void split_lin(const MapDesc& D, uint64_t lin, uint64_t& row, uint64_t& x) {
+template <typename I>
+__device__ __forceinline__ void split_lin(const MapDesc& D, I lin, I& row, I& x) {
   const int last = D.k - 1;
-  if (WIDE) {
-    divmod64(lin, D.divL64[last], row, x);
+  if (sizeof(I) == 8) {
+    uint64_t q, r;
+    divmod64((uint64_t)lin, D.divL64[last], q, r);
+    row = (I)q;
+    x = (I)r;
   } else {
     uint32_t q, r;
     divmod32((uint32_t)lin, D.divL32[last], q, r);
-    row = q;
-    x = r;
+    row = (I)q;
+    x = (I)r;
   }
 }
 
-template <bool WIDE>
-__device__ __forceinline__ uint32_t row_base(const MapDesc& D, const Tabs& tabs,
-                                             const uint32_t* __restrict__ ctab, uint64_t row) {
+template <typename I>
+__device__ __noinline__ uint32_t row_base(const MapDesc& D, const Tabs& tabs,
+                                          const uint32_t* __restrict__ ctab, I row) {
   uint32_t base = 0;
   for (int t = D.k - 2; t >= 0; --t) {
-    uint64_t q, xt;
-    if (WIDE) {
-      divmod64(row, D.divL64[t], q, xt);
+    I q, xt;
+    if (t == 0) {
+      q = 0;
+      xt = row;
+    } else if (sizeof(I) == 8) {
+      uint64_t q64, r64;
+      divmod64((uint64_t)row, D.divL64[t], q64, r64);
+      q = (I)q64;
+      xt = (I)r64;
     } else {
       uint32_t q32, r32;
       divmod32((uint32_t)row, D.divL32[t], q32, r32);
-      q = q32;
-      xt = r32;
+      q = (I)q32;
+      xt = (I)r32;
     }
     row = q;
-    base += tabs.has[t] ? __ldg(ctab + tabs.off[t] + xt) : contrib(D, t, xt);
+    base += tabs.has[t] ? __ldg(ctab + tabs.off[t] + xt) : contrib(D, t, (uint64_t)xt);
   }
   return base;
 }
 
-// last_mode: 0 = c_last staged in shared memory, 1 = read from the HBM/L2
-// table, 2 = computed.
-template <bool WIDE, bool TSMEM>
-__global__ void __launch_bounds__(kThreads) k_ids(const __grid_constant__ MapDesc D, Tabs tabs,
+enum IdsMode : int { M_FAST_SMEM = 0, M_FAST_GLOBAL = 1, M_GENERAL = 2 };
+
+template <typename I, int MODE, bool TSMEM>
+__global__ void __launch_bounds__(kThreads) k_ids(const __grid_constant__ MapDesc D,
+                                                  const __grid_constant__ Tabs tabs,
                                                   const uint32_t* __restrict__ Tg,
-                                                  const uint32_t* __restrict__ ctab, int last_mode,
-                                                  int vec_ok, int32_t* __restrict__ ids) {
-  extern __shared__ uint32_t smem[];
+                                                  const uint32_t* __restrict__ ctab, int vec_ok,
+                                                  uint64_t groups_per_warp, int32_t* __restrict__ ids) {
+  extern __shared__ __align__(16) uint32_t smem[];
   uint32_t* Ts = smem;
-  uint32_t* Cs = smem + (TSMEM ? D.P : 0);
+  uint32_t* Cs = smem + (TSMEM ? ((D.P + 3) & ~3u) : 0);
   const int last = D.k - 1;
-  const uint64_t Llast = D.L[last];
+  const I Llast = (I)D.L[last];
+  const uint32_t* __restrict__ cg = ctab + tabs.off[last];
   if (TSMEM)
     for (uint32_t i = threadIdx.x; i < D.P; i += blockDim.x) Ts[i] = __ldg(Tg + i);
-  if (last_mode == 0)
-    for (uint32_t i = threadIdx.x; i < Llast; i += blockDim.x) Cs[i] = __ldg(ctab + tabs.off[last] + i);
+  if (MODE == M_FAST_SMEM)
+    for (uint32_t i = threadIdx.x; i < (uint32_t)Llast; i += blockDim.x) Cs[i] = __ldg(cg + i);
   __syncthreads();
 
-  auto lookupT = [&](uint32_t F) -> uint32_t { return TSMEM ? Ts[F] : __ldg(Tg + F); };
-  auto clast = [&](uint64_t x) -> uint32_t {
-    if (last_mode == 0) return Cs[x];
-    if (last_mode == 1) return __ldg(ctab + tabs.off[last] + x);
-    return contrib(D, last, x);
-  };
+  const I N = (I)D.npoints;
+  const I groups = (N + 3) / 4;
+  const I warp_id = (I)blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5);
+  const I gbeg = warp_id * (I)groups_per_warp;
+  const I gend = min(groups, gbeg + (I)groups_per_warp);
+  I g = gbeg + (threadIdx.x & 31);
+  if (g >= gend) return;
+  I lin0 = g * 4;
+  I row, x;
+  split_lin<I>(D, lin0, row, x);
+  uint32_t base = row_base<I>(D, tabs, ctab, row);
 
-  const uint64_t N = D.npoints;
-  const uint64_t groups = (N + 3) / 4;
-  const uint64_t per_tile = (uint64_t)kThreads * kUnroll;
-  const uint64_t tiles = (groups + per_tile - 1) / per_tile;
-  uint64_t crow = ~0ull;
-  uint32_t cbase = 0;
-  for (uint64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
-#pragma unroll
-    for (int u = 0; u < kUnroll; ++u) {
-      const uint64_t gi = tile * per_tile + (uint64_t)u * kThreads + threadIdx.x;
-      if (gi >= groups) break;
-      const uint64_t lin0 = gi * 4;
-      uint64_t row, x;
-      split_lin<WIDE>(D, lin0, row, x);
-      if (row != crow) {
-        crow = row;
-        cbase = row_base<WIDE>(D, tabs, ctab, row);
+  for (; g < gend; g += 32, lin0 += 128) {
+    uint32_t v0, v1, v2, v3;
+    int cnt = 4;
+    if (MODE != M_GENERAL) {
+      // Llast % 4 == 0: the group lies inside one row and x % 4 == 0
+      const uint4 c = MODE == M_FAST_SMEM ? *reinterpret_cast<const uint4*>(Cs + x)
+                                          : __ldg(reinterpret_cast<const uint4*>(cg + x));
+      if (TSMEM) {
+        v0 = Ts[base + c.x]; v1 = Ts[base + c.y]; v2 = Ts[base + c.z]; v3 = Ts[base + c.w];
+      } else {
+        v0 = __ldg(Tg + base + c.x); v1 = __ldg(Tg + base + c.y);
+        v2 = __ldg(Tg + base + c.z); v3 = __ldg(Tg + base + c.w);
       }
-      uint32_t v[4];
-      const int cnt = N - lin0 < 4 ? (int)(N - lin0) : 4;
+    } else {
+      // any shape: walk the four points, carrying into the next rows
+      cnt = N - lin0 < 4 ? (int)(N - lin0) : 4;
+      I xi = x, ri = row;
+      uint32_t bi = base;
+      uint32_t v[4] = {0, 0, 0, 0};
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
         if (i < cnt) {
-          if (x == Llast) {   // the row ended inside this group
-            x = 0;
-            crow = ++row;
-            cbase = row_base<WIDE>(D, tabs, ctab, row);
+          if (xi == Llast) {
+            xi = 0;
+            ri += 1;
+            bi = row_base<I>(D, tabs, ctab, ri);
           }
-          v[i] = lookupT(cbase + clast(x));
-          ++x;
+          const uint32_t c = tabs.has[last] ? __ldg(cg + xi) : contrib(D, last, (uint64_t)xi);
+          v[i] = TSMEM ? Ts[bi + c] : __ldg(Tg + bi + c);
+          ++xi;
         }
       }
-      if (cnt == 4 && vec_ok) {
-        __stcs(reinterpret_cast<int4*>(ids + lin0), make_int4((int)v[0], (int)v[1], (int)v[2], (int)v[3]));
+      v0 = v[0]; v1 = v[1]; v2 = v[2]; v3 = v[3];
+    }
+    if (cnt == 4 && vec_ok) {
+      __stcs(reinterpret_cast<int4*>(ids + lin0), make_int4((int)v0, (int)v1, (int)v2, (int)v3));
+    } else {
+      const uint32_t vv[4] = {v0, v1, v2, v3};
+      for (int i = 0; i < cnt; ++i) ids[lin0 + i] = (int32_t)vv[i];
+    }
+    // next group of this lane: 128 points further
+    x += 128;
+    if (x >= Llast) {
+      if (Llast >= 128) {
+        x -= Llast;
+        row += 1;
       } else {
-        for (int i = 0; i < cnt; ++i) ids[lin0 + i] = (int32_t)v[i];
+        split_lin<I>(D, lin0 + 128, row, x);
       }
+      base = row_base<I>(D, tabs, ctab, row);
     }
   }
 }
 
-// Linear-cyclic (Fig. 5): F = lin mod P, consecutive points advance F by 1.
-template <bool TSMEM>
+// Linear-cyclic (Fig. 5): F = lin mod P; consecutive points advance F by 1
+// and consecutive groups of a lane by 128 mod P.
+template <typename I, bool TSMEM>
 __global__ void __launch_bounds__(kThreads) k_ids_lc(const __grid_constant__ MapDesc D,
                                                      const uint32_t* __restrict__ Tg, int vec_ok,
-                                                     int32_t* __restrict__ ids) {
-  extern __shared__ uint32_t smem[];
+                                                     uint64_t groups_per_warp, int32_t* __restrict__ ids) {
+  extern __shared__ __align__(16) uint32_t smem[];
   if (TSMEM) {
     for (uint32_t i = threadIdx.x; i < D.P; i += blockDim.x) smem[i] = __ldg(Tg + i);
     __syncthreads();
   }
-  const uint64_t N = D.npoints;
-  const uint64_t groups = (N + 3) / 4;
-  for (uint64_t gi = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; gi < groups;
-       gi += (uint64_t)gridDim.x * blockDim.x) {
-    const uint64_t lin0 = gi * 4;
-    uint64_t q, F64;
-    divmod64(lin0, D.divP64, q, F64);
-    uint32_t F = (uint32_t)F64;
-    uint32_t v[4];
+  const I N = (I)D.npoints;
+  const I groups = (N + 3) / 4;
+  const I warp_id = (I)blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5);
+  const I gbeg = warp_id * (I)groups_per_warp;
+  const I gend = min(groups, gbeg + (I)groups_per_warp);
+  I g = gbeg + (threadIdx.x & 31);
+  if (g >= gend) return;
+  I lin0 = g * 4;
+  uint64_t q, F64;
+  divmod64((uint64_t)lin0, D.divP64, q, F64);
+  uint32_t F0 = (uint32_t)F64;
+  const uint32_t inc = 128 % D.P;
+  for (; g < gend; g += 32, lin0 += 128) {
     const int cnt = N - lin0 < 4 ? (int)(N - lin0) : 4;
+    uint32_t v[4];
+    uint32_t F = F0;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       v[i] = TSMEM ? smem[F] : __ldg(Tg + F);
@@ -293,6 +335,8 @@ __global__ void __launch_bounds__(kThreads) k_ids_lc(const __grid_constant__ Map
     } else {
       for (int i = 0; i < cnt; ++i) ids[lin0 + i] = (int32_t)v[i];
     }
+    F0 += inc;
+    if (F0 >= D.P) F0 -= D.P;
   }
 }
 
@@ -420,34 +464,49 @@ struct Want {
 size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
 
 // Runs the kernels of one launch into device buffers.
-int run_launch(const Plan& pl, const Want& w, cudaStream_t st) {
-  const MapDesc& D = pl.desc;
-  const bool need_red = w.hist || w.recv || w.total;
-  const bool need_X = (w.recv || w.total) && !D.lc;
-  // ------------------------------------------------ workspace layout
+// Device scratch of one launch: the chain table T, the per-dimension c_t
+// tables, the per-dimension counts H / X and the linear-cyclic deficits.
+struct Layout {
   Tabs tabs;
-  std::memset(&tabs, 0, sizeof(tabs));
-  uint64_t tab_total = 0;
+  uint64_t tab_total;
+  size_t o_T, o_tab, o_H, o_X, o_def, nHX, n_def, bytes;
+  bool need_red, need_X;
+};
+
+Layout make_layout(const MapDesc& D, const Want& w) {
+  Layout ly;
+  std::memset(&ly, 0, sizeof(ly));
+  ly.need_red = w.hist || w.recv || w.total;
+  ly.need_X = (w.recv || w.total) && !D.lc;
   for (int t = 0; t < D.k; ++t) {
-    tabs.has[t] = !D.lc && D.L[t] <= kTableMax;
-    tabs.off[t] = tab_total;
-    if (tabs.has[t]) tab_total += D.L[t];
+    ly.tabs.has[t] = !D.lc && D.L[t] <= kTableMax;
+    ly.tabs.off[t] = ly.tab_total;
+    if (ly.tabs.has[t]) ly.tab_total += (D.L[t] + 3) & ~uint64_t(3);
   }
-  size_t o_T = 0;
-  size_t o_tab = align256(o_T + (size_t)D.P * 4);
-  size_t o_H = align256(o_tab + tab_total * 4);
-  size_t nHX = need_red && !D.lc ? (size_t)D.k * D.P : 0;
-  size_t o_X = align256(o_H + nHX * 8);
-  size_t o_def = align256(o_X + (need_X ? nHX * 8 : 0));
-  size_t n_def = D.lc && (w.recv || w.total) ? D.P : 0;
-  size_t bytes = align256(o_def + n_def * 8);
-  char* ws = (char*)workspace(bytes, 0);
-  if (!ws) return MP_ENOMEM;
-  uint32_t* T = (uint32_t*)(ws + o_T);
-  uint32_t* ctab = (uint32_t*)(ws + o_tab);
-  unsigned long long* H = nHX ? (unsigned long long*)(ws + o_H) : nullptr;
-  unsigned long long* X = need_X ? (unsigned long long*)(ws + o_X) : nullptr;
-  unsigned long long* def = n_def ? (unsigned long long*)(ws + o_def) : nullptr;
+  ly.o_T = 0;
+  ly.o_tab = align256(ly.o_T + (size_t)D.P * 4);
+  ly.o_H = align256(ly.o_tab + ly.tab_total * 4);
+  ly.nHX = ly.need_red && !D.lc ? (size_t)D.k * D.P : 0;
+  ly.o_X = align256(ly.o_H + ly.nHX * 8);
+  ly.o_def = align256(ly.o_X + (ly.need_X ? ly.nHX * 8 : 0));
+  ly.n_def = D.lc && (w.recv || w.total) ? D.P : 0;
+  ly.bytes = align256(ly.o_def + ly.n_def * 8);
+  return ly;
+}
+
+// Runs the kernels of one launch into device buffers, with the scratch at ws
+// (at least ly.bytes).
+int run_launch_ws(const Plan& pl, const Want& w, const Layout& ly, char* ws, cudaStream_t st) {
+  const MapDesc& D = pl.desc;
+  const Tabs& tabs = ly.tabs;
+  const uint64_t tab_total = ly.tab_total;
+  const bool need_red = ly.need_red;
+  const size_t nHX = ly.nHX, n_def = ly.n_def;
+  uint32_t* T = (uint32_t*)(ws + ly.o_T);
+  uint32_t* ctab = (uint32_t*)(ws + ly.o_tab);
+  unsigned long long* H = nHX ? (unsigned long long*)(ws + ly.o_H) : nullptr;
+  unsigned long long* X = ly.need_X ? (unsigned long long*)(ws + ly.o_X) : nullptr;
+  unsigned long long* def = n_def ? (unsigned long long*)(ws + ly.o_def) : nullptr;
 
   // ------------------------------------------------ tables
   k_resolve<<<(D.P + kThreads - 1) / kThreads, kThreads, 0, st>>>(D, T);
@@ -469,32 +528,47 @@ int run_launch(const Plan& pl, const Want& w, cudaStream_t st) {
     const bool tsmem = D.P <= kSmemTMax;
     const int last = D.k - 1;
     const uint64_t groups = (D.npoints + 3) / 4;
+    const bool wide = D.npoints > 0xFFFFFFFFull - 1024;
+    const size_t tbytes = tsmem ? (size_t)((D.P + 3) & ~3u) * 4 : 0;
+    auto grid_for = [&](const void* kern, size_t sm, uint64_t& gpw) {
+      int per_sm = 0;
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, sm);
+      if (per_sm < 1) per_sm = 1;
+      uint64_t blocks = (uint64_t)sm_count() * per_sm;
+      const uint64_t warps_needed = (groups + 31) / 32;
+      blocks = std::max<uint64_t>(1, std::min<uint64_t>(blocks, (warps_needed + 7) / 8));
+      const uint64_t warps = blocks * (kThreads / 32);
+      gpw = ((groups + warps - 1) / warps + 31) / 32 * 32;
+      return (unsigned)blocks;
+    };
+    auto go = [&](const void* kern, size_t sm, auto launch) {
+      if (sm > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      uint64_t gpw = 0;
+      const unsigned blocks = grid_for(kern, sm, gpw);
+      launch(blocks, gpw);
+      count_launch();
+    };
     if (D.lc) {
-      size_t sm = tsmem ? (size_t)D.P * 4 : 0;
-      uint64_t blocks = std::min<uint64_t>((groups + kThreads - 1) / kThreads, (uint64_t)sm_count() * 8);
-      if (tsmem) {
-        if (sm > 48 * 1024) cudaFuncSetAttribute(k_ids_lc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        k_ids_lc<true><<<(unsigned)blocks, kThreads, sm, st>>>(D, T, vec_ok, w.ids);
-      } else {
-        k_ids_lc<false><<<(unsigned)blocks, kThreads, 0, st>>>(D, T, vec_ok, w.ids);
-      }
-      count_launch();
+      const size_t sm = tbytes;
+#define MP_LC(I, TS) go((const void*)k_ids_lc<I, TS>, sm, [&](unsigned b, uint64_t gpw) { \
+        k_ids_lc<I, TS><<<b, kThreads, sm, st>>>(D, T, vec_ok, gpw, w.ids); })
+      if (wide) { if (tsmem) MP_LC(uint64_t, true); else MP_LC(uint64_t, false); }
+      else { if (tsmem) MP_LC(uint32_t, true); else MP_LC(uint32_t, false); }
+#undef MP_LC
     } else {
-      int last_mode = tabs.has[last] ? (D.L[last] <= kSmemLastMax ? 0 : 1) : 2;
-      size_t sm = (tsmem ? (size_t)D.P * 4 : 0) + (last_mode == 0 ? (size_t)D.L[last] * 4 : 0);
-      const bool wide = D.npoints > 0xFFFFFFFFull - 8;
-      uint64_t tiles = (groups + (uint64_t)kThreads * kUnroll - 1) / ((uint64_t)kThreads * kUnroll);
-      uint64_t blocks = std::min<uint64_t>(tiles, (uint64_t)sm_count() * 8);
-      auto launch = [&](auto kern) {
-        if (sm > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        kern<<<(unsigned)blocks, kThreads, sm, st>>>(D, tabs, T, ctab, last_mode, vec_ok, w.ids);
-      };
-      if (wide) {
-        if (tsmem) launch(k_ids<true, true>); else launch(k_ids<true, false>);
-      } else {
-        if (tsmem) launch(k_ids<false, true>); else launch(k_ids<false, false>);
-      }
-      count_launch();
+      const bool aligned = D.L[last] % 4 == 0 && tabs.has[last];
+      const int mode = !aligned ? M_GENERAL : (D.L[last] <= kSmemLastMax ? M_FAST_SMEM : M_FAST_GLOBAL);
+      const size_t sm = tbytes + (mode == M_FAST_SMEM ? (size_t)D.L[last] * 4 : 0);
+#define MP_IDS(I, MODE, TS) go((const void*)k_ids<I, MODE, TS>, sm, [&](unsigned b, uint64_t gpw) { \
+        k_ids<I, MODE, TS><<<b, kThreads, sm, st>>>(D, tabs, T, ctab, vec_ok, gpw, w.ids); })
+#define MP_IDS_T(I, MODE) do { if (tsmem) MP_IDS(I, MODE, true); else MP_IDS(I, MODE, false); } while (0)
+#define MP_IDS_M(I) do { if (mode == M_FAST_SMEM) MP_IDS_T(I, M_FAST_SMEM); \
+                         else if (mode == M_FAST_GLOBAL) MP_IDS_T(I, M_FAST_GLOBAL); \
+                         else MP_IDS_T(I, M_GENERAL); } while (0)
+      if (wide) MP_IDS_M(uint64_t); else MP_IDS_M(uint32_t);
+#undef MP_IDS_M
+#undef MP_IDS_T
+#undef MP_IDS
     }
     timer_end(st);
     MP_CUDA_TRY(cudaGetLastError());
@@ -518,6 +592,14 @@ int run_launch(const Plan& pl, const Want& w, cudaStream_t st) {
   }
   MP_CUDA_TRY(cudaGetLastError());
   return MP_OK;
+}
+
+// Runs one launch with the scratch in the per-device workspace.
+int run_launch(const Plan& pl, const Want& w, cudaStream_t st) {
+  const Layout ly = make_layout(pl.desc, w);
+  char* ws = (char*)workspace(ly.bytes, 0);
+  if (!ws) return MP_ENOMEM;
+  return run_launch_ws(pl, w, ly, ws, st);
 }
 
 // Resolves host/device outputs: device buffers are used directly, host

@@ -1,0 +1,103 @@
+"""GPU parity of decompose_search and candidate_costs against the CPU oracle.
+
+The exhaustive argmin (index, primary, secondary) must equal the oracle's
+exhaustive search exactly, with and without the primary-bound dismissal.  On
+the 3-D matmul queries (P up to 4096) the oracle re-evaluates the winner, a
+random sample of candidates (none may beat the winner) and the engine's own
+per-candidate costs.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2507_17087_gb300 import native as N
+from paper_2507_17087_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TILE = 512 * 512 * 4
+
+
+def oracle_best(q, threads=16):
+    M, N_, K = q["MNK"]
+    return O.search(M, N_, K, q["machine"], q["max_depth"], threads=threads)
+
+
+@pytest.mark.parametrize("full", [False, True])
+def test_small_queries_exhaustive(full):
+    for q in W.search_query_small(count=24):
+        got = N.decompose_search([q], full=full)[0]
+        ref = oracle_best(q)
+        assert got["index"] == ref["index"], (q, got, ref)
+        assert got["primary_bytes"] == ref["primary"] * TILE
+        assert got["secondary_bytes"] == ref["secondary"] * TILE
+        assert got["n_candidates"] == ref["n_candidates"]
+        assert got["f"] == ref["f"]
+
+
+def test_worked_shapes():
+    # (4,8,4) on 16 processors.  Among factorisations with f <= (M,N,K) the
+    # least primary cost is decompose's (2,4,2) (Fig. 10); the moved-tile cost
+    # has no load-balance term, so (1,1,16) -- four idle processor rows along
+    # K -- moves fewer tiles (96 < 112) and wins the unrestricted search.
+    q = {"MNK": (4, 8, 4), "machine": (2, 8), "max_depth": 2, "tile_bytes": TILE}
+    got = N.decompose_search([q])[0]
+    ref = oracle_best(q)
+    assert (got["index"], got["f"]) == (ref["index"], ref["f"]) and got["f"] == (1, 1, 16)
+    assert got["primary_bytes"] == 96 * TILE
+    assert O.matmul_cost(4, 8, 4, (2, 8), (), (2, 4, 2))[0] == 112
+    fits = [f for f in O.factorisations(16, 3) if all(a <= b for a, b in zip(f, (4, 8, 4)))]
+    assert min(fits, key=lambda f: (O.matmul_cost(4, 8, 4, (2, 8), (), f)[0], f)) == (2, 4, 2)
+    # the plain 64x64 case as a degenerate 3-D grid (K = 1): 8 processors
+    q = {"MNK": (64, 64, 1), "machine": (2, 4), "max_depth": 1, "tile_bytes": TILE}
+    assert N.decompose_search([q])[0]["index"] == oracle_best(q)["index"]
+
+
+@pytest.mark.parametrize("qi", range(8))
+def test_matmul_queries_full_size(qi):
+    q = W.search_queries(8)[qi]
+    M, N_, K = q["MNK"]
+    n, g = q["machine"]
+    P = n * g
+    got = N.decompose_search([q])[0]
+    nf, nc = N.search_space(P, g, q["max_depth"])
+    assert got["n_candidates"] == nf * nc == len(O.factorisations(P, 3)) * len(O.chains(n, g, 3))
+    if P in (512, 4096):
+        ref = oracle_best(q)
+        assert (got["index"], got["primary_bytes"], got["secondary_bytes"]) == \
+            (ref["index"], ref["primary"] * TILE, ref["secondary"] * TILE)
+        return
+    # winner re-evaluated by the oracle; a random sample never beats it
+    p, s = O.candidate_costs(M, N_, K, q["machine"], 3, [got["index"]])
+    assert (int(p[0]) * TILE, int(s[0]) * TILE) == (got["primary_bytes"], got["secondary_bytes"])
+    rng = np.random.default_rng(qi)
+    sample = rng.integers(0, got["n_candidates"], 3000, dtype=np.int64)
+    sp, ss = O.candidate_costs(M, N_, K, q["machine"], 3, sample)
+    key = (got["primary_bytes"] // TILE, got["secondary_bytes"] // TILE, got["index"])
+    for a, b, i in zip(sp, ss, sample):
+        assert key <= (int(a), int(b), int(i))
+    # the engine's own costs of the sample match the oracle's
+    gp = np.zeros(len(sample), dtype=np.uint64)
+    gs = np.zeros(len(sample), dtype=np.uint64)
+    N.candidate_costs(q, sample, gp, gs)
+    assert np.array_equal(gp, sp.astype(np.uint64) * TILE)
+    assert np.array_equal(gs, ss.astype(np.uint64) * TILE)
+
+
+def test_candidate_costs_device_buffers_and_out_of_range():
+    q = W.search_query_small(count=1)[0]
+    nf, nc = N.search_space(q["machine"][0] * q["machine"][1], q["machine"][1], q["max_depth"])
+    idx = torch.tensor([0, nf * nc - 1, 5 % (nf * nc), nf * nc, -1], dtype=torch.int64, device="cuda")
+    p = torch.zeros(5, dtype=torch.int64, device="cuda")
+    s = torch.zeros(5, dtype=torch.int64, device="cuda")
+    N.candidate_costs(q, idx, p, s)
+    torch.cuda.synchronize()
+    M, N_, K = q["MNK"]
+    rp, rs = O.candidate_costs(M, N_, K, q["machine"], q["max_depth"], idx[:3].cpu().numpy())
+    assert p[:3].cpu().numpy().tolist() == (rp * TILE).tolist()
+    assert s[:3].cpu().numpy().tolist() == (rs * TILE).tolist()
+    # out-of-range indices are flagged, not evaluated
+    assert p[3:].cpu().numpy().astype(np.uint64).tolist() == [2 ** 64 - 1] * 2
+    with pytest.raises(N.MapleError):
+        N.candidate_costs(q, np.array([nf * nc], dtype=np.int64), np.zeros(1, np.uint64), np.zeros(1, np.uint64))
