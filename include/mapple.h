@@ -143,6 +143,32 @@ int mp_comm_volume(const mp_space* space, const mp_machine* machine, const mp_xf
                    int n_xf, const mp_dist* dist, const uint64_t* face_bytes, uint64_t* total,
                    uint64_t* recv, void* stream);
 
+/* map_points without any allocation.  The paper has no counterpart: this
+ * entry point exists for callers that cannot allocate device memory -- code
+ * running under a memory manager that owns the device's whole budget (a
+ * framework's caching allocator, or a pool sized once at start-up), and
+ * latency-critical loops in which cudaMalloc's implicit device-wide
+ * synchronisation would stall other streams.  It computes exactly what
+ * mp_map_points computes and calls no cudaMalloc, cudaFree or other
+ * allocating routine.
+ *   ids / hist : device memory only (a host buffer would need a staging
+ *                area): MP_EINVAL otherwise; either may be NULL.
+ *   scratch    : one 8 MiB array in this library's device memory, present on
+ *                every GPU that loads the library until the process exits.  A
+ *                launch whose scratch (4 P bytes of chain table, 4 bytes per
+ *                coordinate of each c_t table, 8 * rank * P bytes of counts
+ *                when hist is requested, plus alignment) exceeds 8 MiB returns
+ *                MP_ENOTSUP.  The scratch is rewritten (counts are cleared) by
+ *                every call.
+ *   set-up     : the first call on a device looks up the array's device
+ *                address (cudaGetSymbolAddress, with that device current); make
+ *                that first call before any stream capture.
+ *   concurrency: every call shares the one array, so calls that overlap on
+ *                the GPU (other streams, other host threads) race; serialise
+ *                them. */
+int mp_map_points_noalloc(const mp_space* space, const mp_machine* machine, const mp_xform* chain,
+                          int n_xf, const mp_dist* dist, int32_t* ids, uint64_t* hist, void* stream);
+
 /* decompose_search: a6-a8.  Exhaustive search for a 3-D matmul tile grid
  * (M, N, K) on Machine(GPU) = (P / procs_per_node, procs_per_node).  A
  * candidate is an ordered factorisation f = (f0, f1, f2) of P (Sec. 4.3) and

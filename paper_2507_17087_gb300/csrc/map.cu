@@ -26,6 +26,7 @@
 //   k_lc_slabs   linear-cyclic only: boundary points that miss a neighbour.
 #include <algorithm>
 #include <cstring>
+#include <mutex>
 
 #include "engine.h"
 
@@ -681,4 +682,61 @@ extern "C" int mp_comm_volume(const mp_space* space, const mp_machine* machine, 
   if (rc) return rc;
   if (!face_bytes || !total) return MP_EINVAL;
   return mp::run_with_staging(pl, nullptr, nullptr, recv, total, face_bytes, (cudaStream_t)stream);
+}
+
+// ------------------------------------------------------------ no-allocation variant
+//
+// mp_map_points_noalloc: the same launch as mp_map_points, with its scratch
+// (chain table, per-dimension tables and counts) in one fixed array of this
+// module's device memory instead of the grow-on-demand workspace.
+
+namespace mp {
+namespace {
+
+constexpr size_t kNoAllocBytes = size_t(8) << 20;   // 8 MiB on every device that loads the library
+
+__device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[64] = {};
+
+// The array's name is a host-side stand-in in host code; its device address
+// is looked up once per device, with that device current.
+int noalloc_scratch(char** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return MP_ECUDA;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess) {
+      cudaGetLastError();
+      return MP_ECUDA;
+    }
+    g_noalloc_addr[dev] = p;
+  }
+  *out = (char*)g_noalloc_addr[dev];
+  return MP_OK;
+}
+
+}  // namespace
+}  // namespace mp
+
+extern "C" int mp_map_points_noalloc(const mp_space* space, const mp_machine* machine,
+                                     const mp_xform* chain, int n_xf, const mp_dist* dist, int32_t* ids,
+                                     uint64_t* hist, void* stream) {
+  mp::Plan pl;
+  int rc = mp::build_plan(space, machine, chain, n_xf, dist, pl);
+  if (rc) return rc;
+  if (!ids && !hist) return MP_OK;
+  if ((ids && !mp::is_device_pointer(ids)) || (hist && !mp::is_device_pointer(hist))) return MP_EINVAL;
+  mp::Want w;
+  std::memset(&w, 0, sizeof(w));
+  w.ids = ids;
+  w.hist = hist;
+  const mp::Layout ly = mp::make_layout(pl.desc, w);
+  if (ly.bytes > mp::kNoAllocBytes) return MP_ENOTSUP;
+  char* ws = nullptr;
+  rc = mp::noalloc_scratch(&ws);
+  if (rc) return rc;
+  return mp::run_launch_ws(pl, w, ly, ws, (cudaStream_t)stream);
 }

@@ -87,6 +87,7 @@ def lib():
             V, I, I64, U64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_uint64
             sig = {
                 "mp_map_points": (I, [V, V, V, I, V, V, V, V]),
+                "mp_map_points_noalloc": (I, [V, V, V, I, V, V, V, V]),
                 "mp_comm_volume": (I, [V, V, V, I, V, V, V, V, V]),
                 "mp_decompose_search": (I, [V, I, V, V]),
                 "mp_candidate_costs": (I, [V, V, I64, V, V, V]),
@@ -210,6 +211,21 @@ def map_points(L, machine, chain, dist, ids=None, hist=None, stream=None):
     rc = lib().mp_map_points(ctypes.byref(sp), ctypes.byref(mc), ch, n, ctypes.byref(ds),
                              _ptr(ids), _ptr(hist), _stream(stream))
     _check(rc, "mp_map_points")
+
+
+def map_points_noalloc(L, machine, chain, dist, ids=None, hist=None, stream=None):
+    """map_points with its scratch in the library's fixed 8 MiB device array.
+
+    For callers that cannot allocate device memory (a framework that owns the
+    whole device budget, latency-critical loops that cannot absorb
+    cudaMalloc's device-wide synchronisation).  ids / hist must be device
+    memory.  Calls share the one array: do not overlap them on the GPU.
+    """
+    sp, mc, ds = make_space(L), make_machine(machine), make_dist(dist)
+    ch, n = make_chain(chain)
+    rc = lib().mp_map_points_noalloc(ctypes.byref(sp), ctypes.byref(mc), ch, n, ctypes.byref(ds),
+                                     _ptr(ids), _ptr(hist), _stream(stream))
+    _check(rc, "mp_map_points_noalloc")
 
 
 def comm_volume(L, machine, chain, dist, face_bytes, total, recv=None, stream=None):
