@@ -156,8 +156,9 @@ int mp_comm_volume(const mp_space* space, const mp_machine* machine, const mp_xf
  *   scratch    : one 8 MiB array in this library's device memory, present on
  *                every GPU that loads the library until the process exits.  A
  *                launch whose scratch (4 P bytes of chain table, 4 bytes per
- *                coordinate of each c_t table, 8 * rank * P bytes of counts
- *                when hist is requested, plus alignment) exceeds 8 MiB returns
+ *                coordinate of each tabled c_t, and, when hist is requested,
+ *                8 bytes per sub-index of each dimension's counts -- at most
+ *                8 * rank * P -- plus alignment) exceeds 8 MiB returns
  *                MP_ENOTSUP.  The scratch is rewritten (counts are cleared) by
  *                every call.
  *   set-up     : the first call on a device looks up the array's device
@@ -221,6 +222,52 @@ int mp_decompose_search(const mp_search_query* queries, int n_queries, mp_search
  * range. */
 int mp_candidate_costs(const mp_search_query* query, const int64_t* indices, int64_t n,
                        uint64_t* primary, uint64_t* secondary, void* stream);
+
+/* ------------------------------------------------------------ batched launches */
+
+/* One mapping query of a batch: a launch as mp_map_points / mp_comm_volume
+ * take it, with its stencil face bytes. */
+typedef struct mp_query {
+  mp_space space;
+  mp_machine machine;
+  const mp_xform* chain;    /* read during mp_batch_create only            */
+  int32_t n_xf;
+  int32_t reserved;
+  mp_dist dist;
+  uint64_t face_bytes[4];
+} mp_query;
+
+typedef struct mp_batch mp_batch;   /* opaque planned batch */
+
+/* Plans a batch once: validates and compiles every query (as mp_map_points),
+ * lays out the output regions and uploads the descriptors to the current
+ * device.  Limits per query: P <= 16384, fewer than 2^31 points.  Errors as
+ * mp_map_points for the first bad query; MP_ENOMEM if the device pools
+ * cannot be allocated.  The batch owns device memory until mp_batch_destroy. */
+int mp_batch_create(const mp_query* queries, int n_queries, mp_batch** out);
+
+/* Output layout: ids of query q start at ids_offsets[q] (a multiple of 4;
+ * total_ids entries in all), hist / recv of query q at proc_offsets[q]
+ * (total_procs entries in all; entry proc_offsets[q] + p is processor p of
+ * query q).  Arrays of n + 1 entries, or NULL.  tile_groups: 4-point groups
+ * per work tile of the persistent id writer (after autotuning). */
+int mp_batch_info(const mp_batch* batch, uint64_t* total_ids, uint64_t* total_procs, uint64_t* ids_offsets,
+                  uint64_t* proc_offsets, int32_t* tile_groups);
+
+/* Runs the batch on `stream`: ids (int32[total_ids]), hist and recv
+ * (uint64[total_procs]) and halo (uint64[n], total halo bytes per query) are
+ * device buffers or NULL; results as mp_map_points / mp_comm_volume for every
+ * query.  The kernels are captured into a CUDA graph on first use (and again
+ * when the output pointers change) and replayed.  flags: MP_BATCH_AUTOTUNE
+ * first times the persistent id writer at several tile sizes and keeps the
+ * fastest; MP_BATCH_NO_GRAPH launches the kernels directly.  Asynchronous.
+ * Runs of one batch must not overlap on the GPU (they share its pools). */
+#define MP_BATCH_AUTOTUNE 1
+#define MP_BATCH_NO_GRAPH 2
+int mp_batch_run(mp_batch* batch, int32_t* ids, uint64_t* hist, uint64_t* halo, uint64_t* recv, int flags,
+                 void* stream);
+
+int mp_batch_destroy(mp_batch* batch);
 
 /* ------------------------------------------------------------ host helpers */
 

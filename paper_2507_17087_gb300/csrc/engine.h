@@ -105,9 +105,12 @@ struct Comp {
   Div32 divL32, divs, divb;
 };
 
-// Everything a kernel needs to map one index launch.  The flat final index
-// is F = sum_u a_u * sigma_u with dimension 0 fastest (sigma_0 = 1).
-struct MapDesc {
+// Everything a kernel needs to map one index launch, except the primitive
+// list.  The flat final index is F = sum_u a_u * sigma_u with dimension 0
+// fastest (sigma_0 = 1).  Task dimension t drives the final coordinates of
+// its components; their sub-index j_t = a_{c0} + s_{c0} * a_{c1} ranges over
+// [0, J[t]) and indexes the per-dimension counts at Joff[t] + j_t.
+struct MapCore {
   int32_t k;          // task rank
   int32_t lc;         // 1: linear-cyclic (F = lin mod P)
   int32_t rank;       // final processor-space rank
@@ -119,14 +122,19 @@ struct MapDesc {
   Div32 divL32[4];
   int32_t ncomp[4];
   Comp comp[4][2];
+  uint32_t J[4], Joff[4], Jtotal;
   uint32_t s[kMaxRank];
   uint32_t sigma[kMaxRank];
   Div32 divs[kMaxRank];
   int32_t owner_dim[kMaxRank];
+  int32_t owner_slot[kMaxRank];
   uint32_t lc_stride_mod[4];   // (prod_{u > t} L_u) mod P
   uint64_t lc_stride[4];       // prod_{u > t} L_u
   Div32 divP;
   Div64 divP64;
+};
+
+struct MapDesc : MapCore {
   Prim prim[kMaxPrim];
 };
 

@@ -278,7 +278,7 @@ int build_plan(const mp_space* space, const mp_machine* machine, const mp_xform*
     D.divs[u] = make_div32((uint32_t)B.shape[u]);
     sigma *= (uint32_t)B.shape[u];
   }
-  auto comp = [&](int kind, int u, int t) {
+  auto comp = [&](int kind, int u, int t, int slot) {
     Comp c;
     std::memset(&c, 0, sizeof(c));
     c.kind = kind;
@@ -294,19 +294,25 @@ int build_plan(const mp_space* space, const mp_machine* machine, const mp_xform*
     c.divs = make_div32(c.s);
     c.divb = make_div32(c.b);
     D.owner_dim[u] = t;
+    D.owner_slot[u] = slot;
     return c;
   };
   for (int t = 0; t < k; ++t) {
     switch (dist->kind) {
-      case MP_BLOCK: D.ncomp[t] = 1; D.comp[t][0] = comp(C_BLOCK, t, t); break;
-      case MP_CYCLIC: D.ncomp[t] = 1; D.comp[t][0] = comp(C_CYCLIC, t, t); break;
-      case MP_BLOCK_CYCLIC: D.ncomp[t] = 1; D.comp[t][0] = comp(C_BCYC, t, t); break;
+      case MP_BLOCK: D.ncomp[t] = 1; D.comp[t][0] = comp(C_BLOCK, t, t, 0); break;
+      case MP_CYCLIC: D.ncomp[t] = 1; D.comp[t][0] = comp(C_CYCLIC, t, t, 0); break;
+      case MP_BLOCK_CYCLIC: D.ncomp[t] = 1; D.comp[t][0] = comp(C_BCYC, t, t, 0); break;
       case MP_HIER:
         D.ncomp[t] = 2;
-        D.comp[t][0] = comp(C_BLOCK, t, t);
-        D.comp[t][1] = comp(C_CYCLIC, k + t, t);
+        D.comp[t][0] = comp(C_BLOCK, t, t, 0);
+        D.comp[t][1] = comp(C_CYCLIC, k + t, t, 1);
         break;
       default: D.ncomp[t] = 0; break;
+    }
+    if (D.ncomp[t] > 0) {
+      D.J[t] = D.comp[t][0].s * (D.ncomp[t] > 1 ? D.comp[t][1].s : 1u);
+      D.Joff[t] = D.Jtotal;
+      D.Jtotal += D.J[t];
     }
   }
   if (D.lc) {

@@ -56,6 +56,12 @@ class mp_dist(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("b", ctypes.c_int32)]
 
 
+class mp_query(ctypes.Structure):
+    _fields_ = [("space", mp_space), ("machine", mp_machine), ("chain", ctypes.c_void_p),
+                ("n_xf", ctypes.c_int32), ("reserved", ctypes.c_int32), ("dist", mp_dist),
+                ("face_bytes", ctypes.c_uint64 * 4)]
+
+
 class mp_search_query(ctypes.Structure):
     _fields_ = [("M", ctypes.c_int64), ("N", ctypes.c_int64), ("K", ctypes.c_int64),
                 ("procs", ctypes.c_int32), ("procs_per_node", ctypes.c_int32),
@@ -98,6 +104,10 @@ def lib():
                 "mp_strerror": (ctypes.c_char_p, [I]),
                 "mp_kernel_launches": (U64, []),
                 "mp_set_kernel_timer": (I, [V, V]),
+                "mp_batch_create": (I, [V, I, V]),
+                "mp_batch_info": (I, [V, V, V, V, V, V]),
+                "mp_batch_run": (I, [V, V, V, V, V, I, V]),
+                "mp_batch_destroy": (I, [V]),
                 "mp_descriptor_bytes": (U64, []),
             }
             for name, (res, args) in sig.items():
@@ -360,3 +370,58 @@ def set_kernel_timer(start_event, stop_event):
 
 def descriptor_bytes() -> int:
     return int(lib().mp_descriptor_bytes())
+
+
+BATCH_AUTOTUNE = 1
+BATCH_NO_GRAPH = 2
+
+
+class Batch:
+    """A planned batch of mapping queries (mp_batch_create / mp_batch_run).
+
+    launches: iterable of (L, machine, chain, dist, face_bytes) tuples.
+    """
+
+    def __init__(self, launches):
+        launches = list(launches)
+        self.n = len(launches)
+        arr = (mp_query * self.n)()
+        keep = []
+        for q, (L, machine, chain, dist, face) in enumerate(launches):
+            ch, n = make_chain(chain)
+            keep.append(ch)
+            arr[q].space = make_space(L)
+            arr[q].machine = make_machine(machine)
+            arr[q].chain = ctypes.cast(ch, ctypes.c_void_p)
+            arr[q].n_xf = n
+            arr[q].dist = make_dist(dist)
+            for t, v in enumerate(face):
+                arr[q].face_bytes[t] = int(v)
+        self._h = ctypes.c_void_p()
+        _check(lib().mp_batch_create(arr, self.n, ctypes.byref(self._h)), "mp_batch_create")
+
+    def info(self):
+        ti, tp = ctypes.c_uint64(0), ctypes.c_uint64(0)
+        io = np.zeros(self.n + 1, dtype=np.uint64)
+        po = np.zeros(self.n + 1, dtype=np.uint64)
+        tg = ctypes.c_int32(0)
+        _check(lib().mp_batch_info(self._h, ctypes.byref(ti), ctypes.byref(tp), io.ctypes.data,
+                                   po.ctypes.data, ctypes.byref(tg)), "mp_batch_info")
+        return {"total_ids": ti.value, "total_procs": tp.value, "ids_offsets": io, "proc_offsets": po,
+                "tile_groups": tg.value}
+
+    def run(self, ids=None, hist=None, halo=None, recv=None, autotune=False, graph=True, stream=None):
+        flags = (BATCH_AUTOTUNE if autotune else 0) | (0 if graph else BATCH_NO_GRAPH)
+        _check(lib().mp_batch_run(self._h, _ptr(ids), _ptr(hist), _ptr(halo), _ptr(recv), flags,
+                                  _stream(stream)), "mp_batch_run")
+
+    def close(self):
+        if self._h:
+            lib().mp_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001 - interpreter shutdown
+            pass

@@ -55,6 +55,6 @@ def test_noalloc_rejects_host_buffers_and_oversized_scratch():
     L, machine, chain, dist = (16, 16), (2, 4), [], ("block",)
     host = torch.zeros(256, dtype=torch.int32)
     assert call_noalloc(L, machine, chain, dist, host, None) == 1            # MP_EINVAL
-    # P = 2^20 processors: 4 MiB of chain table + 16 MiB of counts > 8 MiB
-    assert call_noalloc((4096, 4096), (1 << 17, 8), [], ("cyclic",), None,
-                        torch.empty(1 << 20, dtype=torch.int64, device="cuda")) == 6   # MP_ENOTSUP
+    # P = 2^22 processors: the chain table alone (4 P bytes = 16 MiB) exceeds 8 MiB
+    assert call_noalloc((8, 8), (1 << 19, 8), [], ("cyclic",), None,
+                        torch.empty(1 << 22, dtype=torch.int64, device="cuda")) == 6   # MP_ENOTSUP
