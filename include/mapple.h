@@ -269,6 +269,17 @@ int mp_batch_run(mp_batch* batch, int32_t* ids, uint64_t* hist, uint64_t* halo, 
 
 int mp_batch_destroy(mp_batch* batch);
 
+/* ------------------------------------------------------------ learned cost model */
+/* The paper has no learned component; this is the project's surrogate that
+ * prunes the decompose search (see mp_learned_search).  Its tensor-core
+ * building block is exported for testing: */
+
+/* C[M x N] (float32, row-major) = A[M x K] * B[N x K]^T with A, B bfloat16
+ * row-major, FP32 accumulation on the tcgen05 tensor cores.  M % 128 == 0,
+ * N % 64 == 0, K % 64 == 0; device buffers only.  Synchronous.  MP_ETIMEOUT
+ * if a tensor-core completion wait gave up. */
+int mp_gemm_bf16(const void* A, const void* B, float* C, int M, int N, int K, void* stream);
+
 /* ------------------------------------------------------------ host helpers */
 
 /* Plan only (no GPU work): final processor-space shape and the expanded

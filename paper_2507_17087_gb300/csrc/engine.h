@@ -168,6 +168,9 @@ std::vector<CanonOp> canonical_alphabet(const std::vector<int64_t>& shape);
 void apply_canon(std::vector<int64_t>& shape, const CanonOp& c);
 std::vector<std::vector<CanonOp>> canonical_chains(int64_t nodes, int64_t ppn, int max_depth);
 
+// C = A * B^T, BF16 operands (row-major, K contiguous), FP32 result (mlp.cu).
+int gemm_tn(const void* A, const void* B, float* C, int M, int N, int K, int* status, cudaStream_t st);
+
 // ------------------------------------------------------------------ runtime
 
 // Grow-only per-device workspace; returns nullptr on allocation failure.

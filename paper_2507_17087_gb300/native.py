@@ -108,6 +108,7 @@ def lib():
                 "mp_batch_info": (I, [V, V, V, V, V, V]),
                 "mp_batch_run": (I, [V, V, V, V, V, I, V]),
                 "mp_batch_destroy": (I, [V]),
+                "mp_gemm_bf16": (I, [V, V, V, I, I, I, V]),
                 "mp_descriptor_bytes": (U64, []),
             }
             for name, (res, args) in sig.items():
@@ -425,3 +426,10 @@ class Batch:
             self.close()
         except Exception:  # noqa: BLE001 - interpreter shutdown
             pass
+
+
+def gemm_bf16(A, B, C, stream=None):
+    """C = A @ B.T on the tcgen05 tensor cores (A, B bfloat16, C float32)."""
+    M, K = A.shape
+    N = B.shape[0]
+    _check(lib().mp_gemm_bf16(_ptr(A), _ptr(B), _ptr(C), M, N, K, _stream(stream)), "mp_gemm_bf16")
