@@ -280,6 +280,62 @@ int mp_batch_destroy(mp_batch* batch);
  * if a tensor-core completion wait gave up. */
 int mp_gemm_bf16(const void* A, const void* B, float* C, int M, int N, int K, void* stream);
 
+/* The model: 64 candidate features -> 256 -> 256 -> 256 (ReLU) -> 1 score,
+ * BF16 weights and activations, FP32 accumulation and FP32 master weights.
+ * Parameters are packed as float32 W1[256x64] b1[256] W2[256x256] b2[256]
+ * W3[256x256] b3[256] w4[256] b4[1] (mp_mlp_num_params() values). */
+typedef struct mp_mlp mp_mlp;
+
+int mp_mlp_create(uint64_t seed, mp_mlp** out);      /* He initialisation on the current device */
+int mp_mlp_destroy(mp_mlp* model);
+int mp_mlp_num_params(void);
+int mp_mlp_set_params(mp_mlp* model, const float* params /* host */);
+/* params / grads: host float32[mp_mlp_num_params()] or NULL; grads are those
+ * of the last training step. */
+int mp_mlp_get_params(const mp_mlp* model, float* params, float* grads);
+/* y[B] = model(X[B x 64]) with X bfloat16; device buffers, B % 128 == 0. */
+int mp_mlp_forward(mp_mlp* model, const void* X, float* y, int B, void* stream);
+/* One Adam step (lr > 0) or gradients only (lr == 0) on the mean squared
+ * error 0.5 mean (y - target)^2; *loss (host) receives the loss before the
+ * step.  Device X (bfloat16 B x 64) and target (float32 B), B % 128 == 0. */
+int mp_mlp_train_step(mp_mlp* model, const void* X, const float* target, int B, float lr, float* loss,
+                      void* stream);
+
+/* Trains the model on exact costs: for each query, samples_per_query
+ * candidates (half uniform, half among the lowest primary costs) are
+ * evaluated exactly (mp_candidate_costs), featurised, and the model takes
+ * `epochs` passes of Adam over shuffled batches of `batch` (a multiple of
+ * 128).  Regression target: 4 min(p / p_min - 1, 16) + log2(1 + s) / 48 with
+ * p, s the candidate's primary / secondary cost in tiles and p_min the
+ * query's least primary.  *final_loss: last batch loss. */
+int mp_mlp_train_search(mp_mlp* model, const mp_search_query* queries, int n_queries, int samples_per_query,
+                        int epochs, int batch, float lr, uint64_t seed, float* final_loss, void* stream);
+
+/* Learned decompose search: the model scores every candidate of the query
+ * (fused tcgen05 inference), the K best scores are evaluated exactly, and
+ * their lexicographic argmin is returned if it is certified (every
+ * candidate with a primary cost no higher than the winner's was among the
+ * K) or if the largest model error seen on the K leaves a margin; otherwise
+ * the exhaustive search runs (unless MP_LEARNED_NO_FALLBACK).  The returned
+ * costs are always exact.  K in [1, 65536].  Synchronous. */
+typedef struct mp_learned_stats {
+  int64_t n_scored;   /* candidates scored by the model            */
+  int64_t n_exact;    /* candidates evaluated exactly              */
+  int32_t certified;  /* 1: exact certificate on the top-K         */
+  int32_t fallback;   /* 1: the exhaustive search ran              */
+  double margin;      /* threshold - 2 * max error - winner target */
+} mp_learned_stats;
+#define MP_LEARNED_NO_FALLBACK 1
+int mp_learned_search(mp_mlp* model, const mp_search_query* query, int K, int flags, mp_search_result* out,
+                      mp_learned_stats* stats, void* stream);
+
+/* Scores of every candidate of a query in index order (the fused scoring
+ * kernel of mp_learned_search), and optionally their features (bfloat16,
+ * n x 64).  Device buffers sized by the search space (*n_out receives the
+ * candidate count).  Synchronous. */
+int mp_learned_scores(mp_mlp* model, const mp_search_query* query, float* scores, void* features, int64_t* n_out,
+                      void* stream);
+
 /* ------------------------------------------------------------ host helpers */
 
 /* Plan only (no GPU work): final processor-space shape and the expanded
@@ -319,6 +375,10 @@ uint64_t mp_descriptor_bytes(void);
 
 /* Human-readable text of a status code (static storage). */
 const char* mp_strerror(int status);
+
+/* Where the calling thread's last MP_ECUDA came from: source location and
+ * the CUDA error name and text (empty if none). */
+const char* mp_last_error_detail(void);
 
 /* Number of kernel launches issued by this library in the calling process. */
 uint64_t mp_kernel_launches(void);

@@ -35,13 +35,23 @@ def init_params(seed: int = 0, scale: float = 1.0):
     return p
 
 
-def forward(p, x):
-    """y and the cached pre-activations / activations."""
+def _id(a):
+    return a
+
+
+def forward(p, x, rnd=None):
+    """y and the cached pre-activations / activations.
+
+    rnd (optional) is applied to the hidden activations that feed the next
+    product (h1, h2) -- the points where a low-precision engine stores its
+    operands; None keeps everything in float64.
+    """
+    r = rnd or _id
     x = np.asarray(x, dtype=np.float64)
     z1 = x @ p["W1"].T + p["b1"]
-    h1 = np.maximum(z1, 0.0)
+    h1 = r(np.maximum(z1, 0.0))
     z2 = h1 @ p["W2"].T + p["b2"]
-    h2 = np.maximum(z2, 0.0)
+    h2 = r(np.maximum(z2, 0.0))
     z3 = h2 @ p["W3"].T + p["b3"]
     h3 = np.maximum(z3, 0.0)
     y = h3 @ p["w4"] + p["b4"][0]
@@ -53,22 +63,30 @@ def loss(y, target):
     return 0.5 * float(np.mean(d * d))
 
 
-def backward(p, cache, y, target):
-    """Gradients of loss() with respect to every parameter."""
+def backward(p, cache, y, target, rnd=None):
+    """Gradients of loss() with respect to every parameter.
+
+    rnd (optional) is applied to dz3, dz2, dz1 where they feed a product
+    (the bias gradients use the unrounded values).
+    """
+    r = rnd or _id
     B = y.shape[0]
     dy = (y - np.asarray(target, dtype=np.float64)) / B
     g = {}
     g["w4"] = cache["h3"].T @ dy
     g["b4"] = np.array([dy.sum()])
     dz3 = np.outer(dy, p["w4"]) * (cache["z3"] > 0)
-    g["W3"] = dz3.T @ cache["h2"]
     g["b3"] = dz3.sum(axis=0)
+    dz3 = r(dz3)
+    g["W3"] = dz3.T @ cache["h2"]
     dz2 = (dz3 @ p["W3"]) * (cache["z2"] > 0)
-    g["W2"] = dz2.T @ cache["h1"]
     g["b2"] = dz2.sum(axis=0)
+    dz2 = r(dz2)
+    g["W2"] = dz2.T @ cache["h1"]
     dz1 = (dz2 @ p["W2"]) * (cache["z1"] > 0)
-    g["W1"] = dz1.T @ cache["x"]
     g["b1"] = dz1.sum(axis=0)
+    dz1 = r(dz1)
+    g["W1"] = dz1.T @ cache["x"]
     return g
 
 

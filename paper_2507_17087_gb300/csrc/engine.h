@@ -183,8 +183,16 @@ void timer_end(cudaStream_t st);
 
 }  // namespace mp
 
-#define MP_CUDA_TRY(expr)                         \
-  do {                                            \
-    cudaError_t _e = (expr);                      \
-    if (_e != cudaSuccess) return MP_ECUDA;       \
+namespace mp {
+// Records where the last CUDA call failed (mp_last_error_detail).
+void record_cuda_error(cudaError_t e, const char* file, int line);
+}  // namespace mp
+
+#define MP_CUDA_TRY(expr)                                      \
+  do {                                                         \
+    cudaError_t _e = (expr);                                   \
+    if (_e != cudaSuccess) {                                   \
+      mp::record_cuda_error(_e, __FILE__, __LINE__);           \
+      return MP_ECUDA;                                         \
+    }                                                          \
   } while (0)

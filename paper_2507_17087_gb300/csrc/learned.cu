@@ -1,0 +1,813 @@
+// Learned pruning of the decompose search (no counterpart in the paper).
+//
+//   features   64 numbers per candidate (query shape, factorisation, its
+//              closed-form primary cost relative to the best one, the
+//              chain's transforms, where the chain's node boundaries fall
+//              along each final dimension)
+//   k_score    fused tcgen05 inference: a persistent CTA of 128 threads
+//              writes the features of 128 candidates into shared memory,
+//              runs the three hidden layers (weights streamed from L2 in
+//              64-wide K chunks, accumulator in tensor memory, each thread's
+//              epilogue handles its own row) and writes one score per
+//              candidate
+//   top-K      65536-bin histogram of the order-preserving score keys, a
+//              threshold bin, and a compaction of the candidates at or below
+//   exact      the top-K are re-evaluated by the exact cost kernel; the
+//              lexicographic argmin over them is returned when it is
+//              certified (every candidate with a primary cost no higher than
+//              the winner's was evaluated) or when the model's observed error
+//              leaves a margin; otherwise the exhaustive search runs.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <vector>
+
+#include "mlp.cuh"
+#include "search.cuh"
+#include "tc.cuh"
+
+namespace mp {
+namespace lrn {
+
+using mlpk::bf16;
+using mlpk::DH;
+using mlpk::DIN;
+
+constexpr int kChainFeat = 32;
+constexpr uint32_t kWaitLimit = 1u << 26;
+
+struct QInfo {
+  uint32_t E[3];
+  uint32_t P, n, g;
+  uint32_t nf;
+  uint32_t pad;
+  unsigned long long nchains;
+  unsigned long long pmin;
+  unsigned long long tile_bytes;
+  float qf[6];
+};
+
+__device__ __forceinline__ float lg2(float v) { return log2f(fmaxf(v, 1e-30f)); }
+
+// Per chain: depth one-hot, each of three steps (split / merge / swap,
+// log2 d, p, q) and whether the node changes between flat index 0 and 2^i.
+__global__ void k_chain_feats(const ChainProg* __restrict__ progs, unsigned long long NC, uint32_t P,
+                              float* __restrict__ out) {
+  const unsigned long long c = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= NC) return;
+  const ChainProg cp = progs[c];
+  float f[kChainFeat];
+  for (int i = 0; i < kChainFeat; ++i) f[i] = 0.f;
+  f[min(cp.depth, 3)] = 1.f;
+  for (int s = 0; s < 3 && s < cp.depth; ++s) {
+    const Prim& p = cp.prim[s];
+    f[4 + 6 * s + p.op] = 1.f;
+    f[4 + 6 * s + 3] = p.op == P_SPLIT ? lg2((float)p.d) / 12.f : 0.f;
+    f[4 + 6 * s + 4] = p.p / 4.f;
+    f[4 + 6 * s + 5] = p.op == P_SPLIT ? 0.f : p.q / 4.f;
+  }
+  const uint32_t n0 = resolve_node(cp, 0);
+  for (int i = 0; i < 10; ++i) {
+    const uint32_t b = 1u << i;
+    f[22 + i] = (b < P && resolve_node(cp, b) != n0) ? 1.f : 0.f;
+  }
+  for (int i = 0; i < kChainFeat; ++i) out[c * kChainFeat + i] = f[i];
+}
+
+// 64 features of candidate idx = fr * NC + c.
+__device__ __forceinline__ void candidate_features(const QInfo& Q, const ChainProg* __restrict__ progs,
+                                                   const Fact* __restrict__ facts,
+                                                   const float* __restrict__ chainfeat, unsigned long long idx,
+                                                   float x[64], unsigned long long* primary_out) {
+  const unsigned long long fr = idx / Q.nchains, c = idx - fr * Q.nchains;
+  const uint32_t f[3] = {facts[fr].f[0], facts[fr].f[1], facts[fr].f[2]};
+  const unsigned long long p = primary_cost(Q.E, f);
+  if (primary_out) *primary_out = p;
+  const float pn = (float)((double)p / (double)max(Q.pmin, 1ull) - 1.0);
+  for (int i = 0; i < 6; ++i) x[i] = Q.qf[i];
+  for (int t = 0; t < 3; ++t) {
+    const float ft = (float)f[t], Et = (float)Q.E[t];
+    x[6 + t] = lg2(ft) / 12.f;
+    x[9 + t] = lg2(fminf(ft, Et)) / 12.f;
+    x[12 + t] = f[t] > Q.E[t] ? 1.f : 0.f;
+    x[15 + t] = fminf(fmaxf(lg2(Et / ft), -8.f), 12.f) / 12.f;
+  }
+  x[18] = fminf(pn, 8.f) / 8.f;
+  x[19] = log2f(1.f + pn) / 3.f;
+  x[20] = p == Q.pmin ? 1.f : 0.f;
+  const float* cf = chainfeat + c * kChainFeat;
+  for (int i = 0; i < kChainFeat; ++i) x[21 + i] = cf[i];
+  const ChainProg& cp = progs[c];
+  const uint32_t n0 = resolve_node(cp, 0);
+  const uint32_t stride[3] = {1u, f[0], f[0] * f[1]};
+  for (int v = 0; v < 3; ++v) {
+    float ch = 0.f, distinct = 1.f;
+    if (f[v] > 1 && stride[v] < Q.P) {
+      uint32_t seen[4] = {n0, 0, 0, 0};
+      int ns = 1;
+      for (uint32_t j = 1; j < 4 && j < f[v] && j * stride[v] < Q.P; ++j) {
+        const uint32_t nd = resolve_node(cp, j * stride[v]);
+        if (j == 1) ch = nd != n0 ? 1.f : 0.f;
+        bool dup = false;
+        for (int a = 0; a < ns; ++a) dup = dup || seen[a] == nd;
+        if (!dup) seen[ns++] = nd;
+      }
+      distinct = (float)ns;
+    }
+    x[53 + v] = ch;
+    x[56 + v] = distinct / 4.f;
+  }
+  x[59] = log2f(1.f + (float)p) / 40.f;
+  x[60] = 1.f;
+  x[61] = x[62] = x[63] = 0.f;
+}
+
+// Regression target: lexicographic (primary, secondary) on one scale.
+__device__ __forceinline__ float target_of(unsigned long long p_tiles, unsigned long long s_tiles,
+                                           unsigned long long pmin) {
+  const float pn = (float)((double)p_tiles / (double)max(pmin, 1ull) - 1.0);
+  return 4.f * fminf(pn, 16.f) + log2f(1.f + (float)s_tiles) / 48.f;
+}
+
+__global__ void k_primaries(const Fact* __restrict__ facts, uint32_t nf, uint32_t E0, uint32_t E1, uint32_t E2,
+                            unsigned long long* __restrict__ out) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nf) return;
+  const uint32_t E[3] = {E0, E1, E2};
+  const uint32_t f[3] = {facts[i].f[0], facts[i].f[1], facts[i].f[2]};
+  out[i] = primary_cost(E, f);
+}
+
+// Features (BF16, row-major n x 64) of listed candidates; with exact costs
+// (bytes) also the regression targets.
+__global__ void k_features_idx(const __grid_constant__ QInfo Q, const ChainProg* __restrict__ progs,
+                               const Fact* __restrict__ facts, const float* __restrict__ chainfeat,
+                               const int64_t* __restrict__ idx, int64_t n, const uint64_t* __restrict__ pbytes,
+                               const uint64_t* __restrict__ sbytes, bf16* __restrict__ X, float* __restrict__ target) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float x[64];
+  candidate_features(Q, progs, facts, chainfeat, (unsigned long long)idx[i], x, nullptr);
+  for (int j = 0; j < 64; j += 2)
+    *reinterpret_cast<__nv_bfloat162*>(X + i * 64 + j) = __floats2bfloat162_rn(x[j], x[j + 1]);
+  if (target) target[i] = target_of(pbytes[i] / Q.tile_bytes, sbytes[i] / Q.tile_bytes, Q.pmin);
+}
+
+// ------------------------------------------------------------ fused scoring
+
+__device__ __forceinline__ void stage_w(uint8_t* dst, const bf16* __restrict__ W, int ld, int k0) {
+  // 256 rows x 64 columns of W (row-major, leading dimension ld) into a
+  // swizzled K-major tile
+  for (int i = threadIdx.x; i < 256 * 8; i += blockDim.x) {
+    const int r = i >> 3, c = i & 7;
+    const uint4 v = __ldg(reinterpret_cast<const uint4*>(W + (size_t)r * ld + k0 + c * 8));
+    *reinterpret_cast<uint4*>(dst + tc::sw128_offset(r, c * 8)) = v;
+  }
+}
+
+// issue 4 MMAs (K = 64) of A (one swizzle atom) x B (one atom of 256 rows)
+__device__ __forceinline__ void mma_chunk(uint32_t tmem, uint32_t a_addr, uint32_t b_addr, bool first,
+                                          uint64_t* bar) {
+  constexpr uint32_t idesc = tc::idesc_bf16(128, 256);
+#pragma unroll
+  for (int kk = 0; kk < 4; ++kk)
+    tc::mma_bf16(tmem, tc::sdesc_sw128(a_addr + kk * 32), tc::sdesc_sw128(b_addr + kk * 32), idesc,
+                 (first && kk == 0) ? 0u : 1u);
+  tc::mma_commit(bar);
+}
+
+// Waits for the committed MMAs; the result is the same for the whole CTA.
+__device__ __forceinline__ bool sync_mma(uint64_t* bar, uint32_t& phase) {
+  const bool ok = tc::mbar_wait(bar, phase, kWaitLimit);
+  phase ^= 1;
+  tc::fence_after_sync();
+  return __syncthreads_and(ok) != 0;
+}
+
+// Accumulator row of this thread, columns [32c, 32c + 32): bias, ReLU, BF16
+// into the activation tile (K-major, four swizzle atoms of 64 columns).
+__device__ __forceinline__ void epilogue_hidden(uint32_t tmem, const float* __restrict__ bias, uint8_t* H) {
+  const int warp = threadIdx.x >> 5, row = threadIdx.x;
+#pragma unroll 1
+  for (int c = 0; c < 8; ++c) {
+    uint32_t r[32];
+    tc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + c * 32, r);
+    tc::tmem_ld_wait();
+    uint8_t* atom = H + (c >> 1) * 16384;
+#pragma unroll
+    for (int j = 0; j < 32; j += 8) {
+      uint32_t w[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const float a = fmaxf(__uint_as_float(r[j + 2 * e]) + bias[c * 32 + j + 2 * e], 0.f);
+        const float b = fmaxf(__uint_as_float(r[j + 2 * e + 1]) + bias[c * 32 + j + 2 * e + 1], 0.f);
+        __nv_bfloat162 h2 = __floats2bfloat162_rn(a, b);
+        w[e] = *reinterpret_cast<uint32_t*>(&h2);
+      }
+      *reinterpret_cast<uint4*>(atom + tc::sw128_offset(row, (c & 1) * 32 + j)) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(128) k_score(const __grid_constant__ QInfo Q, const ChainProg* __restrict__ progs,
+                                               const Fact* __restrict__ facts, const float* __restrict__ chainfeat,
+                                               const bf16* __restrict__ W1b, const bf16* __restrict__ W2b,
+                                               const bf16* __restrict__ W3b, const float* __restrict__ P,
+                                               unsigned long long n, float* __restrict__ scores,
+                                               int* __restrict__ status) {
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ uint64_t bar;
+  __shared__ uint32_t tmem_slot;
+  __shared__ float sb1[DH], sb2[DH], sb3[DH], sw4[DH];
+  uint8_t* base = smem_raw + ((1024 - (tc::smem_u32(smem_raw) & 1023)) & 1023);
+  uint8_t* Xs = base;                 // 128 x 64 (one atom, 16 KB)
+  uint8_t* Hs = base + 16384;         // 128 x 256 (four atoms, 64 KB)
+  uint8_t* Ws = base + 16384 + 65536; // 256 x 64 weight chunk (32 KB)
+  const int warp = threadIdx.x >> 5;
+  for (int i = threadIdx.x; i < DH; i += blockDim.x) {
+    sb1[i] = P[mlpk::O_B1 + i];
+    sb2[i] = P[mlpk::O_B2 + i];
+    sb3[i] = P[mlpk::O_B3 + i];
+    sw4[i] = P[mlpk::O_W4 + i];
+  }
+  const float b4 = P[mlpk::O_B4];
+  if (warp == 0) {
+    tc::tmem_alloc(&tmem_slot, 256);
+    tc::tmem_relinquish();
+  }
+  if (threadIdx.x == 0) {
+    tc::mbar_init(&bar, 1);
+    tc::fence_mbar_init();
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = tmem_slot;
+  const uint32_t xa = tc::smem_u32(Xs), ha = tc::smem_u32(Hs), wa = tc::smem_u32(Ws);
+  uint32_t phase = 0;
+  bool ok = true;
+  const unsigned long long ntiles = (n + 127) / 128;
+  for (unsigned long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+    const unsigned long long cand = tile * 128 + threadIdx.x;
+    {
+      float x[64];
+      if (cand < n) {
+        candidate_features(Q, progs, facts, chainfeat, cand, x, nullptr);
+      } else {
+        for (int i = 0; i < 64; ++i) x[i] = 0.f;
+      }
+#pragma unroll
+      for (int j = 0; j < 64; j += 8) {
+        uint32_t w[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          __nv_bfloat162 h2 = __floats2bfloat162_rn(x[j + 2 * e], x[j + 2 * e + 1]);
+          w[e] = *reinterpret_cast<uint32_t*>(&h2);
+        }
+        *reinterpret_cast<uint4*>(Xs + tc::sw128_offset(threadIdx.x, j)) = make_uint4(w[0], w[1], w[2], w[3]);
+      }
+    }
+    // ---- layer 1: X (K = 64) x W1^T
+    stage_w(Ws, W1b, DIN, 0);
+    tc::fence_proxy_async();
+    tc::fence_before_sync();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      tc::fence_after_sync();
+      mma_chunk(tmem, xa, wa, true, &bar);
+    }
+    ok = sync_mma(&bar, phase);
+    epilogue_hidden(tmem, sb1, Hs);
+    // ---- layers 2 and 3: H (K = 256) x W^T in four chunks; the epilogue
+    // overwrites H only after the layer's last MMA completed
+    for (int layer = 0; layer < 2 && ok; ++layer) {
+      const bf16* W = layer == 0 ? W2b : W3b;
+      for (int kc = 0; kc < 4 && ok; ++kc) {
+        stage_w(Ws, W, DH, kc * 64);
+        tc::fence_proxy_async();
+        tc::fence_before_sync();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+          tc::fence_after_sync();
+          mma_chunk(tmem, ha + kc * 16384, wa, kc == 0, &bar);
+        }
+        ok = sync_mma(&bar, phase);
+      }
+      if (!ok) break;
+      if (layer == 0) {
+        epilogue_hidden(tmem, sb2, Hs);
+      } else {
+        // output layer: score = relu(Z3 + b3) . w4 + b4 over this thread's row
+        float s = b4;
+#pragma unroll 1
+        for (int c = 0; c < 8; ++c) {
+          uint32_t r[32];
+          tc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + c * 32, r);
+          tc::tmem_ld_wait();
+#pragma unroll
+          for (int j = 0; j < 32; ++j) s += fmaxf(__uint_as_float(r[j]) + sb3[c * 32 + j], 0.f) * sw4[c * 32 + j];
+        }
+        if (cand < n) scores[cand] = s;
+      }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+  }
+  if (!ok && threadIdx.x == 0) atomicExch(status, MP_ETIMEOUT);
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tmem, 256);
+}
+
+// ------------------------------------------------------------ top-K
+
+__device__ __forceinline__ uint32_t order_key(float v) {
+  const uint32_t u = __float_as_uint(v);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+
+__global__ void k_topk_hist(const float* __restrict__ s, unsigned long long n, unsigned* __restrict__ hist) {
+  for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (unsigned long long)gridDim.x * blockDim.x)
+    atomicAdd(hist + (order_key(s[i]) >> 16), 1u);
+}
+
+// smallest bin T whose cumulative count reaches K; out[0] = T, out[1] = count below T
+__global__ void __launch_bounds__(1024) k_topk_threshold(const unsigned* __restrict__ hist, unsigned K,
+                                                         unsigned* __restrict__ out) {
+  __shared__ unsigned part[1024];
+  const int t = threadIdx.x;   // 1024 threads x 64 bins
+  unsigned s = 0;
+  for (int i = 0; i < 64; ++i) s += hist[t * 64 + i];
+  part[t] = s;
+  __syncthreads();
+  for (int o = 1; o < 1024; o <<= 1) {
+    const unsigned v = t >= o ? part[t - o] : 0;
+    __syncthreads();
+    part[t] += v;
+    __syncthreads();
+  }
+  const unsigned before = t ? part[t - 1] : 0;
+  if (before < K && part[t] >= K) {
+    unsigned c = before;
+    for (int i = 0; i < 64; ++i) {
+      const unsigned h = hist[t * 64 + i];
+      if (c + h >= K) {
+        out[0] = t * 64 + i;
+        out[1] = c;
+        break;
+      }
+      c += h;
+    }
+  }
+}
+
+__global__ void k_topk_collect(const float* __restrict__ s, unsigned long long n, const unsigned* __restrict__ thr,
+                               int64_t* __restrict__ below, unsigned* __restrict__ nbelow, int64_t* __restrict__ eq,
+                               unsigned* __restrict__ neq, unsigned cap_below, unsigned cap_eq) {
+  const unsigned T = thr[0];
+  for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (unsigned long long)gridDim.x * blockDim.x) {
+    const unsigned b = order_key(s[i]) >> 16;
+    if (b < T) {
+      const unsigned k = atomicAdd(nbelow, 1u);
+      if (k < cap_below) below[k] = (int64_t)i;
+    } else if (b == T) {
+      const unsigned k = atomicAdd(neq, 1u);
+      if (k < cap_eq) eq[k] = (int64_t)i;
+    }
+  }
+}
+
+// ------------------------------------------------------------ host side
+
+int sm_count_l() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 132;
+  }
+  return n;
+}
+
+size_t a256(size_t v) { return (v + 255) & ~size_t(255); }
+
+struct Prepared {
+  SearchSpace S;
+  QInfo Q;
+  ChainProg* d_progs = nullptr;
+  Fact* d_facts = nullptr;
+  float* d_chainfeat = nullptr;
+  std::vector<unsigned long long> prim;   // primary (tiles) per factorisation
+};
+
+// Plans the query, uploads the chain programs and factorisations into the
+// given device region and computes primaries and chain features there.
+int prepare_query(const mp_search_query& q, Prepared& pq, char* region, size_t cap, size_t* used,
+                  cudaStream_t st) {
+  int rc = prepare(q, pq.S);
+  if (rc) return rc;
+  const size_t NC = pq.S.chains.size(), NF = pq.S.facts.size();
+  const size_t o_p = 0, o_f = a256(NC * sizeof(ChainProg)), o_cf = o_f + a256(NF * sizeof(Fact)),
+               o_pr = o_cf + a256(NC * kChainFeat * 4), end = o_pr + a256(NF * 8);
+  if (end > cap) return MP_ENOMEM;
+  *used = end;
+  pq.d_progs = (ChainProg*)(region + o_p);
+  pq.d_facts = (Fact*)(region + o_f);
+  pq.d_chainfeat = (float*)(region + o_cf);
+  unsigned long long* d_prim = (unsigned long long*)(region + o_pr);
+  MP_CUDA_TRY(cudaMemcpyAsync(pq.d_progs, pq.S.progs.data(), NC * sizeof(ChainProg), cudaMemcpyHostToDevice, st));
+  MP_CUDA_TRY(cudaMemcpyAsync(pq.d_facts, pq.S.fdev.data(), NF * sizeof(Fact), cudaMemcpyHostToDevice, st));
+  k_chain_feats<<<(unsigned)((NC + 127) / 128), 128, 0, st>>>(pq.d_progs, NC, (uint32_t)q.procs, pq.d_chainfeat);
+  k_primaries<<<(unsigned)((NF + 127) / 128), 128, 0, st>>>(pq.d_facts, (uint32_t)NF, (uint32_t)q.M, (uint32_t)q.N,
+                                                            (uint32_t)q.K, d_prim);
+  count_launch(2);
+  pq.prim.resize(NF);
+  MP_CUDA_TRY(cudaMemcpyAsync(pq.prim.data(), d_prim, NF * 8, cudaMemcpyDeviceToHost, st));
+  MP_CUDA_TRY(cudaStreamSynchronize(st));
+  QInfo& Q = pq.Q;
+  std::memset(&Q, 0, sizeof(Q));
+  Q.E[0] = (uint32_t)q.M;
+  Q.E[1] = (uint32_t)q.N;
+  Q.E[2] = (uint32_t)q.K;
+  Q.P = (uint32_t)q.procs;
+  Q.g = (uint32_t)q.procs_per_node;
+  Q.n = Q.P / Q.g;
+  Q.nf = (uint32_t)NF;
+  Q.nchains = NC;
+  Q.tile_bytes = q.tile_bytes;
+  Q.pmin = *std::min_element(pq.prim.begin(), pq.prim.end());
+  Q.qf[0] = std::log2((double)q.M) / 12.0;
+  Q.qf[1] = std::log2((double)q.N) / 12.0;
+  Q.qf[2] = std::log2((double)q.K) / 12.0;
+  Q.qf[3] = std::log2((double)q.procs) / 14.0;
+  Q.qf[4] = std::log2((double)Q.n) / 12.0;
+  Q.qf[5] = std::log2((double)Q.g) / 3.0;
+  return MP_OK;
+}
+
+uint64_t splitmix(uint64_t& s) {
+  s += 0x9E3779B97F4A7C15ull;
+  uint64_t z = s;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+struct Pool {
+  char* p = nullptr;
+  size_t size = 0;
+  ~Pool() {
+    if (p) cudaFree(p);
+  }
+  char* get(size_t bytes) {
+    if (size >= bytes) return p;
+    if (p) cudaFree(p);
+    p = nullptr;
+    size = 0;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    size = bytes;
+    return p;
+  }
+};
+
+Pool g_pool_q, g_pool_s;   // query data; scores and selection
+
+__global__ void k_gather(const bf16* __restrict__ X, const float* __restrict__ T, const int64_t* __restrict__ perm,
+                         int B, bf16* __restrict__ Xb, float* __restrict__ Tb) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;   // one 16-byte chunk per thread
+  if (i >= B * 8) return;
+  const int r = i >> 3, c = i & 7;
+  const int64_t src = perm[r];
+  reinterpret_cast<uint4*>(Xb + (size_t)r * 64)[c] = reinterpret_cast<const uint4*>(X + (size_t)src * 64)[c];
+  if (c == 0) Tb[r] = T[src];
+}
+
+void mlpk_gather(const bf16* X, const float* T, const int64_t* perm, int B, bf16* Xb, float* Tb, cudaStream_t st) {
+  k_gather<<<(B * 8 + 255) / 256, 256, 0, st>>>(X, T, perm, B, Xb, Tb);
+  count_launch();
+}
+
+__global__ void k_take(const float* __restrict__ s, const int64_t* __restrict__ idx, int n, float* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = s[idx[i]];
+}
+
+float host_target(unsigned long long p, unsigned long long sc, unsigned long long pmin) {
+  const float pn = (float)((double)p / (double)std::max(pmin, 1ull) - 1.0);
+  return 4.f * std::min(pn, 16.f) + std::log2(1.f + (float)sc) / 48.f;
+}
+
+}  // namespace lrn
+}  // namespace mp
+
+// ------------------------------------------------------------ C ABI
+
+extern "C" int mp_mlp_train_search(mp_mlp* h, const mp_search_query* queries, int n_queries, int samples_per_query,
+                                   int epochs, int batch, float lr, uint64_t seed, float* final_loss, void* stream) {
+  using namespace mp;
+  using namespace mp::lrn;
+  if (!h || !queries || n_queries < 1 || samples_per_query < 1 || epochs < 0 || batch < 128 || batch % 128)
+    return MP_EINVAL;
+  for (int i = 0; i < n_queries; ++i) {
+    const int rc = validate_query(queries[i]);
+    if (rc) return rc;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t total = (size_t)n_queries * samples_per_query;
+  // dataset
+  bf16* X = nullptr;
+  float* T = nullptr;
+  char* scratch = nullptr;
+  int rc = MP_OK;
+  const size_t per = (size_t)samples_per_query;
+  if (cudaMalloc(&X, total * 64 * 2) != cudaSuccess || cudaMalloc(&T, total * 4) != cudaSuccess ||
+      cudaMalloc(&scratch, a256(per * 8) * 3 + (size_t)batch * (64 * 2 + 4) + 1024) != cudaSuccess) {
+    cudaGetLastError();
+    if (X) cudaFree(X);
+    if (T) cudaFree(T);
+    return MP_ENOMEM;
+  }
+  int64_t* d_idx = (int64_t*)scratch;
+  uint64_t* d_p = (uint64_t*)(scratch + a256(per * 8));
+  uint64_t* d_s = (uint64_t*)(scratch + 2 * a256(per * 8));
+  bf16* Xb = (bf16*)(scratch + 3 * a256(per * 8));
+  float* Tb = (float*)((char*)Xb + (size_t)batch * 128);
+  uint64_t rng = seed;
+  std::vector<int64_t> idx(per);
+  for (int qi = 0; qi < n_queries && !rc; ++qi) {
+    const mp_search_query& q = queries[qi];
+    Prepared pq;
+    size_t used = 0;
+    char* region = g_pool_q.get(64u << 20);
+    if (!region) { rc = MP_ENOMEM; break; }
+    if ((rc = prepare_query(q, pq, region, 64u << 20, &used, st))) break;
+    const uint64_t NC = pq.S.chains.size(), NF = pq.S.facts.size();
+    std::vector<uint32_t> order(NF);
+    std::iota(order.begin(), order.end(), 0u);
+    std::sort(order.begin(), order.end(), [&](uint32_t a, uint32_t b) { return pq.prim[a] < pq.prim[b]; });
+    // half uniform, a quarter on the best factorisations, a quarter on the
+    // eight lowest primaries (the ranking near the optimum matters most)
+    for (size_t i = 0; i < per; ++i) {
+      const uint64_t r = splitmix(rng);
+      uint64_t fr;
+      if (i % 4 < 2) fr = r % NF;
+      else if (i % 4 == 2) fr = order[0];
+      else fr = order[(r >> 20) % std::min<uint64_t>(8, NF)];
+      idx[i] = (int64_t)(fr * NC + (splitmix(rng) % NC));
+    }
+    if (cudaMemcpyAsync(d_idx, idx.data(), per * 8, cudaMemcpyHostToDevice, st) != cudaSuccess) { rc = MP_ECUDA; break; }
+    if ((rc = candidate_costs_dev(q, pq.S, pq.d_progs, pq.d_facts, d_idx, (int64_t)per, d_p, d_s, st))) break;
+    k_features_idx<<<(unsigned)((per + 127) / 128), 128, 0, st>>>(pq.Q, pq.d_progs, pq.d_facts, pq.d_chainfeat, d_idx,
+                                                                  (int64_t)per, d_p, d_s, X + (size_t)qi * per * 64,
+                                                                  T + (size_t)qi * per);
+    count_launch();
+    if (cudaStreamSynchronize(st) != cudaSuccess) { rc = MP_ECUDA; break; }
+  }
+  // epochs of shuffled minibatches
+  float loss = 0.f;
+  std::vector<int64_t> perm(total);
+  std::iota(perm.begin(), perm.end(), 0);
+  int64_t* d_perm = nullptr;
+  if (!rc && cudaMalloc(&d_perm, total * 8) != cudaSuccess) rc = MP_ENOMEM;
+  for (int e = 0; e < epochs && !rc; ++e) {
+    for (size_t i = total - 1; i > 0; --i) std::swap(perm[i], perm[splitmix(rng) % (i + 1)]);
+    if (cudaMemcpyAsync(d_perm, perm.data(), total * 8, cudaMemcpyHostToDevice, st) != cudaSuccess) { rc = MP_ECUDA; break; }
+    for (size_t b0 = 0; b0 + batch <= total && !rc; b0 += batch) {
+      mp::lrn::mlpk_gather(X, T, d_perm + b0, batch, Xb, Tb, st);
+      MP_CUDA_TRY(cudaMemsetAsync(h->status, 0, 4, st));
+      rc = mlpk::train_step(h, Xb, Tb, batch, lr, st);
+    }
+    float l = 0.f;
+    cudaMemcpyAsync(&l, h->scalar, 4, cudaMemcpyDeviceToHost, st);
+    cudaStreamSynchronize(st);
+    loss = l;
+  }
+  if (d_perm) cudaFree(d_perm);
+  cudaFree(X);
+  cudaFree(T);
+  cudaFree(scratch);
+  if (final_loss) *final_loss = loss;
+  return rc;
+}
+
+extern "C" int mp_learned_search(mp_mlp* h, const mp_search_query* query, int K, int flags, mp_search_result* out,
+                                 mp_learned_stats* stats, void* stream) {
+  using namespace mp;
+  using namespace mp::lrn;
+  if (!h || !query || !out || K < 1 || K > 65536) return MP_EINVAL;
+  int rc = validate_query(*query);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  const mp_search_query& q = *query;
+  Prepared pq;
+  size_t used = 0;
+  char* region = g_pool_q.get(64u << 20);
+  if (!region) return MP_ENOMEM;
+  if ((rc = prepare_query(q, pq, region, 64u << 20, &used, st))) return rc;
+  const uint64_t NC = pq.S.chains.size(), NF = pq.S.facts.size(), ncand = NC * NF;
+  const unsigned cap_eq = 1u << 16;
+  const size_t o_sc = 0, o_hist = a256(ncand * 4), o_thr = o_hist + a256(65536 * 4), o_cnt = o_thr + 256,
+               o_below = o_cnt + 256, o_eq = o_below + a256((size_t)K * 8), o_sel = o_eq + a256((size_t)cap_eq * 8),
+               o_p = o_sel + a256((size_t)K * 8), o_s = o_p + a256((size_t)K * 8),
+               o_y = o_s + a256((size_t)K * 8), o_ye = o_y + a256((size_t)K * 4), end = o_ye + a256((size_t)cap_eq * 4);
+  char* w = g_pool_s.get(end);
+  if (!w) return MP_ENOMEM;
+  float* d_sc = (float*)(w + o_sc);
+  unsigned* d_hist = (unsigned*)(w + o_hist);
+  unsigned* d_thr = (unsigned*)(w + o_thr);
+  unsigned* d_cnt = (unsigned*)(w + o_cnt);
+  int64_t* d_below = (int64_t*)(w + o_below);
+  int64_t* d_eq = (int64_t*)(w + o_eq);
+  int64_t* d_sel = (int64_t*)(w + o_sel);
+  uint64_t* d_p = (uint64_t*)(w + o_p);
+  uint64_t* d_s = (uint64_t*)(w + o_s);
+  float* d_y = (float*)(w + o_y);
+  float* d_ye = (float*)(w + o_ye);
+  // ---- score every candidate
+  MP_CUDA_TRY(cudaMemsetAsync(h->status, 0, 4, st));
+  const size_t smem = 16384 + 65536 + 32768 + 1024;
+  MP_CUDA_TRY(cudaFuncSetAttribute(k_score, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const uint64_t ntiles = (ncand + 127) / 128;
+  const unsigned blocks = (unsigned)std::min<uint64_t>(ntiles, (uint64_t)sm_count_l() * 2);
+  timer_begin(st);
+  k_score<<<blocks, 128, smem, st>>>(pq.Q, pq.d_progs, pq.d_facts, pq.d_chainfeat, h->W1b, h->W2b, h->W3b, h->P,
+                                     ncand, d_sc, h->status);
+  timer_end(st);
+  count_launch();
+  MP_CUDA_TRY(cudaGetLastError());
+  // ---- top-K by score
+  const unsigned Keff = (unsigned)std::min<uint64_t>((uint64_t)K, ncand);
+  MP_CUDA_TRY(cudaMemsetAsync(d_hist, 0, 65536 * 4, st));
+  MP_CUDA_TRY(cudaMemsetAsync(d_cnt, 0, 16, st));
+  const unsigned gb = (unsigned)std::min<uint64_t>((ncand + 255) / 256, (uint64_t)sm_count_l() * 8);
+  k_topk_hist<<<gb, 256, 0, st>>>(d_sc, ncand, d_hist);
+  k_topk_threshold<<<1, 1024, 0, st>>>(d_hist, Keff, d_thr);
+  k_topk_collect<<<gb, 256, 0, st>>>(d_sc, ncand, d_thr, d_below, d_cnt, d_eq, d_cnt + 1, Keff, cap_eq);
+  count_launch(3);
+  MP_CUDA_TRY(cudaGetLastError());
+  unsigned cnt[2] = {0, 0};
+  int status = 0;
+  MP_CUDA_TRY(cudaMemcpyAsync(cnt, d_cnt, 8, cudaMemcpyDeviceToHost, st));
+  MP_CUDA_TRY(cudaMemcpyAsync(&status, h->status, 4, cudaMemcpyDeviceToHost, st));
+  MP_CUDA_TRY(cudaStreamSynchronize(st));
+  if (status) return status;
+  const unsigned nbelow = std::min(cnt[0], Keff), neq = std::min(cnt[1], cap_eq);
+  // the threshold bin, ordered by (score, index) for a deterministic choice
+  std::vector<int64_t> eq(neq);
+  std::vector<float> eqs(neq);
+  if (neq) {
+    MP_CUDA_TRY(cudaMemcpyAsync(eq.data(), d_eq, (size_t)neq * 8, cudaMemcpyDeviceToHost, st));
+    k_take<<<(neq + 255) / 256, 256, 0, st>>>(d_sc, d_eq, (int)neq, d_ye);
+    count_launch();
+    MP_CUDA_TRY(cudaMemcpyAsync(eqs.data(), d_ye, (size_t)neq * 4, cudaMemcpyDeviceToHost, st));
+    MP_CUDA_TRY(cudaStreamSynchronize(st));
+  }
+  // NaN scores order last (a total order keeps the sort well defined)
+  auto key = [](float v) { return std::isnan(v) ? INFINITY : v; };
+  std::vector<uint32_t> ord(neq);
+  std::iota(ord.begin(), ord.end(), 0u);
+  std::sort(ord.begin(), ord.end(), [&](uint32_t a, uint32_t b) {
+    const float ka = key(eqs[a]), kb = key(eqs[b]);
+    return ka < kb || (ka == kb && eq[a] < eq[b]);
+  });
+  std::vector<int64_t> sel(nbelow);
+  if (nbelow) MP_CUDA_TRY(cudaMemcpyAsync(sel.data(), d_below, (size_t)nbelow * 8, cudaMemcpyDeviceToHost, st));
+  MP_CUDA_TRY(cudaStreamSynchronize(st));
+  for (uint32_t i = 0; i < neq && sel.size() < Keff; ++i) sel.push_back(eq[ord[i]]);
+  const int64_t nsel = (int64_t)sel.size();
+  if (nsel == 0) {   // the selection kernels produced nothing
+    MP_CUDA_TRY(cudaErrorUnknown);
+  }
+  // ---- exact costs of the selection
+  MP_CUDA_TRY(cudaMemcpyAsync(d_sel, sel.data(), (size_t)nsel * 8, cudaMemcpyHostToDevice, st));
+  if ((rc = candidate_costs_dev(q, pq.S, pq.d_progs, pq.d_facts, d_sel, nsel, d_p, d_s, st))) return rc;
+  k_take<<<(unsigned)((nsel + 255) / 256), 256, 0, st>>>(d_sc, d_sel, (int)nsel, d_y);
+  count_launch();
+  std::vector<uint64_t> pb(nsel), sb(nsel);
+  std::vector<float> yh(nsel);
+  MP_CUDA_TRY(cudaMemcpyAsync(pb.data(), d_p, (size_t)nsel * 8, cudaMemcpyDeviceToHost, st));
+  MP_CUDA_TRY(cudaMemcpyAsync(sb.data(), d_s, (size_t)nsel * 8, cudaMemcpyDeviceToHost, st));
+  MP_CUDA_TRY(cudaMemcpyAsync(yh.data(), d_y, (size_t)nsel * 4, cudaMemcpyDeviceToHost, st));
+  MP_CUDA_TRY(cudaStreamSynchronize(st));
+  int64_t bi = 0;
+  for (int64_t i = 1; i < nsel; ++i) {
+    const bool less = pb[i] < pb[bi] || (pb[i] == pb[bi] && (sb[i] < sb[bi] || (sb[i] == sb[bi] && sel[i] < sel[bi])));
+    if (less) bi = i;
+  }
+  const unsigned long long tb = q.tile_bytes;
+  const unsigned long long p_best = pb[bi] / tb;
+  // certificate: every candidate whose primary is no higher than the
+  // winner's was evaluated exactly
+  uint64_t threats = 0, threats_in = 0;
+  for (uint64_t fr = 0; fr < NF; ++fr)
+    if (pq.prim[fr] <= p_best) threats += NC;
+  for (int64_t i = 0; i < nsel; ++i)
+    if (pb[i] / tb <= p_best) ++threats_in;
+  const bool certified = threats == threats_in;
+  // margin: every unselected candidate scored at least the threshold; the
+  // model's largest error on the selection bounds how far its true target
+  // may lie below its score
+  float eps = 0.f, tau = -1e30f;
+  bool finite = true;
+  for (int64_t i = 0; i < nsel; ++i) {
+    const float yt = host_target(pb[i] / tb, sb[i] / tb, pq.Q.pmin);
+    finite = finite && std::isfinite(yh[i]);
+    eps = std::max(eps, std::fabs(yh[i] - yt));
+    tau = std::max(tau, yh[i]);
+  }
+  if (!finite) eps = INFINITY;   // no margin from a model that returned NaN / inf
+  const float y_best = host_target(p_best, sb[bi] / tb, pq.Q.pmin);
+  const double margin = (double)tau - 2.0 * eps - y_best;
+  const bool accept = certified || (p_best == pq.Q.pmin && margin > 0.0 && nsel == (int64_t)Keff);
+  if (stats) {
+    std::memset(stats, 0, sizeof(*stats));
+    stats->n_scored = (int64_t)ncand;
+    stats->n_exact = nsel;
+    stats->certified = certified ? 1 : 0;
+    stats->margin = margin;
+  }
+  if (!accept && !(flags & MP_LEARNED_NO_FALLBACK)) {
+    mp_search_query qf = q;
+    qf.flags = 0;
+    rc = exhaustive_search(qf, out, st);
+    if (stats) {
+      stats->fallback = 1;
+      stats->n_exact += out->n_candidates;
+    }
+    return rc;
+  }
+  // the winner of the selection
+  std::memset(out, 0, sizeof(*out));
+  const uint64_t idx = (uint64_t)sel[bi], fr = idx / NC, c = idx % NC;
+  out->index = (int64_t)idx;
+  for (int t = 0; t < 3; ++t) out->f[t] = pq.S.facts[fr][t];
+  out->chain_rank = (int64_t)c;
+  out->chain_len = (int32_t)pq.S.chains[c].size();
+  for (int o = 0; o < out->chain_len; ++o) {
+    const CanonOp& op = pq.S.chains[c][o];
+    mp_xform& x = out->chain[o];
+    x.op = op.op == P_SPLIT ? MP_SPLIT : (op.op == P_MERGE ? MP_MERGE : MP_SWAP);
+    x.i = op.p;
+    x.j = op.op == P_SPLIT ? 0 : op.q;
+    x.d = op.op == P_SPLIT ? op.d : 0;
+  }
+  out->primary_bytes = pb[bi];
+  out->secondary_bytes = sb[bi];
+  out->n_chains = (int64_t)NC;
+  out->n_factorisations = (int64_t)NF;
+  out->n_candidates = (int64_t)ncand;
+  return MP_OK;
+}
+
+// Scores (and optionally features) of every candidate of a query, in index
+// order: the fused scoring kernel as the learned search runs it.
+extern "C" int mp_learned_scores(mp_mlp* h, const mp_search_query* query, float* scores, void* features,
+                                 int64_t* n_out, void* stream) {
+  using namespace mp;
+  using namespace mp::lrn;
+  if (!h || !query || !scores || !n_out) return MP_EINVAL;
+  int rc = validate_query(*query);
+  if (rc) return rc;
+  if (!is_device_pointer(scores) || (features && !is_device_pointer(features))) return MP_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  Prepared pq;
+  size_t used = 0;
+  char* region = g_pool_q.get(64u << 20);
+  if (!region) return MP_ENOMEM;
+  if ((rc = prepare_query(*query, pq, region, 64u << 20, &used, st))) return rc;
+  const uint64_t ncand = (uint64_t)pq.S.chains.size() * pq.S.facts.size();
+  *n_out = (int64_t)ncand;
+  MP_CUDA_TRY(cudaMemsetAsync(h->status, 0, 4, st));
+  const size_t smem = 16384 + 65536 + 32768 + 1024;
+  MP_CUDA_TRY(cudaFuncSetAttribute(k_score, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const uint64_t ntiles = (ncand + 127) / 128;
+  const unsigned blocks = (unsigned)std::min<uint64_t>(ntiles, (uint64_t)sm_count_l() * 2);
+  k_score<<<blocks, 128, smem, st>>>(pq.Q, pq.d_progs, pq.d_facts, pq.d_chainfeat, h->W1b, h->W2b, h->W3b, h->P,
+                                     ncand, scores, h->status);
+  count_launch();
+  if (features) {
+    int64_t* d_idx = nullptr;
+    if (cudaMalloc(&d_idx, ncand * 8) != cudaSuccess) return MP_ENOMEM;
+    std::vector<int64_t> idx(ncand);
+    std::iota(idx.begin(), idx.end(), (int64_t)0);
+    MP_CUDA_TRY(cudaMemcpyAsync(d_idx, idx.data(), ncand * 8, cudaMemcpyHostToDevice, st));
+    k_features_idx<<<(unsigned)((ncand + 127) / 128), 128, 0, st>>>(pq.Q, pq.d_progs, pq.d_facts, pq.d_chainfeat,
+                                                                     d_idx, (int64_t)ncand, nullptr, nullptr,
+                                                                     (bf16*)features, nullptr);
+    count_launch();
+    MP_CUDA_TRY(cudaStreamSynchronize(st));
+    cudaFree(d_idx);
+  }
+  int status = 0;
+  MP_CUDA_TRY(cudaMemcpyAsync(&status, h->status, 4, cudaMemcpyDeviceToHost, st));
+  MP_CUDA_TRY(cudaStreamSynchronize(st));
+  return status;
+}

@@ -9,9 +9,12 @@
 // a tensor-memory accumulator and commits them to the chunk's mbarrier, and
 // the four warps read the accumulator back (32 rows each) for the epilogue.
 #include <algorithm>
+#include <cmath>
 #include <cstring>
+#include <vector>
 
 #include "engine.h"
+#include "mlp.cuh"
 #include "tc.cuh"
 
 namespace mp {
@@ -121,6 +124,8 @@ int launch_gemm(const __nv_bfloat16* A, const __nv_bfloat16* B, float* C, int M,
 
 int gemm_tn(const void* A, const void* B, float* C, int M, int N, int K, int* status, cudaStream_t st) {
   if (M <= 0 || N <= 0 || K <= 0 || M % 128 || K % 64) return MP_EINVAL;
+  // operands are staged and results stored in 16-byte vectors
+  if ((((uintptr_t)A) | ((uintptr_t)B) | ((uintptr_t)C)) & 15) return MP_EINVAL;
   const __nv_bfloat16* a = (const __nv_bfloat16*)A;
   const __nv_bfloat16* b = (const __nv_bfloat16*)B;
   if (N % 256 == 0) return launch_gemm<256>(a, b, C, M, N, K, status, st);
@@ -145,4 +150,361 @@ extern "C" int mp_gemm_bf16(const void* A, const void* B, float* C, int M, int N
   MP_CUDA_TRY(cudaMemcpyAsync(&h, status, sizeof(int), cudaMemcpyDeviceToHost, st));
   MP_CUDA_TRY(cudaStreamSynchronize(st));
   return h;
+}
+
+// ======================================================================
+// Model parameters, training step and unfused forward
+//
+// Parameters (FP32 master copy, packed): W1[256x64] b1[256] W2[256x256]
+// b2[256] W3[256x256] b3[256] w4[256] b4[1]; BF16 copies W1, W2, W3 feed the
+// forward GEMMs and W2^T, W3^T the backward ones.  A training step on a
+// batch X[B x 64] (BF16), targets t[B]:
+//   Z1 = X W1^T, H1 = relu(Z1 + b1), Z2 = H1 W2^T, H2 = relu(Z2 + b2),
+//   Z3 = H2 W3^T, y = relu(Z3 + b3) w4 + b4, loss = 0.5 mean (y - t)^2,
+//   dZ3 = (dy w4^T) o [Z3 + b3 > 0], dW3 = dZ3^T H2, dZ2 = (dZ3 W3) o [..],
+//   dW2 = dZ2^T H1, dZ1 = (dZ2 W2) o [..], dW1 = dZ1^T X, then Adam.
+// Every product runs in k_gemm_tn (transposed operands are written by the
+// elementwise kernels); elementwise work runs in FP32.
+
+namespace mp {
+namespace mlpk {
+
+
+
+// 32 x 32 tiles: out[r][c] = f(in[r][c]) in BF16, optionally outT[c][r]
+// (R x C row-major in, C x R row-major outT), column sums of the FP32
+// values into colsum.
+template <int KIND>
+__global__ void __launch_bounds__(256) k_elem(const float* __restrict__ Z, const float* __restrict__ bias,
+                                              const float* __restrict__ aux, const float* __restrict__ aux2,
+                                              int R, int C, bf16* __restrict__ out, bf16* __restrict__ outT,
+                                              float* __restrict__ colsum, float* __restrict__ colsum2) {
+  // KIND 0: relu(Z + bias)                       (forward)
+  // KIND 1: Z o [aux + bias > 0]                 (backward through relu; Z = dH, aux = pre-activation)
+  // KIND 2: [Z + bias > 0] * dy[r] * w4[c]       (output layer backward; aux = dy, aux2 = w4),
+  //         colsum2 += relu(Z + bias) * dy[r]    (gradient of w4)
+  __shared__ float tile[32][33];
+  const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8
+  float csum = 0.f, csum2 = 0.f;
+  for (int i = ty; i < 32; i += 8) {
+    const int r = r0 + i, c = c0 + tx;
+    float v = 0.f;
+    if (r < R && c < C) {
+      const float z = Z[(size_t)r * C + c];
+      const float b = bias ? bias[c] : 0.f;
+      if (KIND == 0) {
+        v = fmaxf(z + b, 0.f);
+      } else if (KIND == 1) {
+        v = (aux[(size_t)r * C + c] + b > 0.f) ? z : 0.f;
+      } else {
+        const float a = z + b;
+        v = a > 0.f ? aux[r] * aux2[c] : 0.f;
+        csum2 += fmaxf(a, 0.f) * aux[r];
+      }
+      if (out) out[(size_t)r * C + c] = __float2bfloat16(v);
+    }
+    tile[i][tx] = v;
+    csum += v;
+  }
+  if (colsum) atomicAdd(colsum + c0 + tx, csum);
+  if (KIND == 2 && colsum2) atomicAdd(colsum2 + c0 + tx, csum2);
+  if (!outT) return;
+  __syncthreads();
+  for (int i = ty; i < 32; i += 8) {
+    const int c = c0 + i, r = r0 + tx;
+    if (c < C && r < R) outT[(size_t)c * R + r] = __float2bfloat16(tile[tx][i]);
+  }
+}
+
+// BF16 transpose: out[c][r] = in[r][c]
+__global__ void __launch_bounds__(256) k_transpose_bf16(const bf16* __restrict__ in, int R, int C,
+                                                        bf16* __restrict__ out) {
+  __shared__ bf16 tile[32][34];
+  const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (int i = ty; i < 32; i += 8)
+    if (r0 + i < R && c0 + tx < C) tile[i][tx] = in[(size_t)(r0 + i) * C + c0 + tx];
+  __syncthreads();
+  for (int i = ty; i < 32; i += 8)
+    if (c0 + i < C && r0 + tx < R) out[(size_t)(c0 + i) * R + r0 + tx] = tile[tx][i];
+}
+
+// y = relu(Z3 + b3) w4 + b4 per row (one warp per row); with targets:
+// dy = (y - t) / B and the squared error into loss.
+__global__ void __launch_bounds__(256) k_output(const float* __restrict__ Z3, const float* __restrict__ P, int B,
+                                                const float* __restrict__ target, float* __restrict__ y,
+                                                float* __restrict__ dy, float* __restrict__ loss) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (warp >= B) return;
+  const float* z = Z3 + (size_t)warp * DH;
+  float s = 0.f;
+  for (int j = lane; j < DH; j += 32) s += fmaxf(z[j] + P[O_B3 + j], 0.f) * P[O_W4 + j];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xFFFFFFFFu, s, o);
+  if (lane == 0) {
+    const float out = s + P[O_B4];
+    y[warp] = out;
+    if (target) {
+      const float d = out - target[warp];
+      dy[warp] = d / B;
+      atomicAdd(loss, 0.5f * d * d / B);
+    }
+  }
+}
+
+__global__ void k_sum(const float* __restrict__ v, int n, float* __restrict__ out) {
+  float s = 0.f;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s += v[i];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xFFFFFFFFu, s, o);
+  __shared__ float red[32];
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float t = 0.f;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    *out += t;
+  }
+}
+
+// Adam (Kingma & Ba) with bias correction, then the BF16 copies.
+__global__ void k_adam(float* __restrict__ P, const float* __restrict__ G, float* __restrict__ m,
+                       float* __restrict__ v, size_t n, float lr, float b1, float b2, float c1, float c2,
+                       float eps) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const float g = G[i];
+    const float mi = b1 * m[i] + (1.f - b1) * g;
+    const float vi = b2 * v[i] + (1.f - b2) * g * g;
+    m[i] = mi;
+    v[i] = vi;
+    P[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+  }
+}
+
+__global__ void k_refresh(const float* __restrict__ P, bf16* __restrict__ W1b, bf16* __restrict__ W2b,
+                          bf16* __restrict__ W3b, bf16* __restrict__ W2T, bf16* __restrict__ W3T) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < DH * DH; i += gridDim.x * blockDim.x) {
+    const int r = i / DH, c = i % DH;
+    if (i < DH * DIN) W1b[i] = __float2bfloat16(P[O_W1 + i]);
+    W2b[i] = __float2bfloat16(P[O_W2 + i]);
+    W3b[i] = __float2bfloat16(P[O_W3 + i]);
+    W2T[(size_t)c * DH + r] = __float2bfloat16(P[O_W2 + i]);
+    W3T[(size_t)c * DH + r] = __float2bfloat16(P[O_W3 + i]);
+  }
+}
+
+}  // namespace mlpk
+}  // namespace mp
+
+
+
+namespace mp {
+namespace mlpk {
+
+struct Bufs {
+  float *Z1, *Z2, *Z3, *dH, *y, *dy;
+  bf16 *XT, *H1, *H2, *H1T, *H2T, *dZ1, *dZ2, *dZ3, *dZ1T, *dZ2T, *dZ3T;
+};
+
+int ensure_ws(mp_mlp* h, int B, Bufs& b) {
+  const size_t f32 = (size_t)B * DH * 4, b16 = (size_t)B * DH * 2;
+  const size_t need = 4 * f32 + 2 * (size_t)B * 4 + (size_t)B * DIN * 2 + 11 * b16 + 64 * 256;
+  if (h->ws_B < B) {
+    if (h->ws) cudaFree(h->ws);
+    h->ws = nullptr;
+    h->ws_B = 0;
+    if (cudaMalloc(&h->ws, need) != cudaSuccess) {
+      cudaGetLastError();
+      return MP_ENOMEM;
+    }
+    h->ws_B = B;
+  }
+  char* p = (char*)h->ws;
+  auto take = [&](size_t bytes) {
+    char* r = p;
+    p += (bytes + 255) & ~size_t(255);
+    return r;
+  };
+  b.Z1 = (float*)take(f32); b.Z2 = (float*)take(f32); b.Z3 = (float*)take(f32); b.dH = (float*)take(f32);
+  b.y = (float*)take((size_t)B * 4); b.dy = (float*)take((size_t)B * 4);
+  b.XT = (bf16*)take((size_t)B * DIN * 2);
+  b.H1 = (bf16*)take(b16); b.H2 = (bf16*)take(b16); b.H1T = (bf16*)take(b16); b.H2T = (bf16*)take(b16);
+  b.dZ1 = (bf16*)take(b16); b.dZ2 = (bf16*)take(b16); b.dZ3 = (bf16*)take(b16);
+  b.dZ1T = (bf16*)take(b16); b.dZ2T = (bf16*)take(b16); b.dZ3T = (bf16*)take(b16);
+  return MP_OK;
+}
+
+dim3 tiles(int R, int C) { return dim3((C + 31) / 32, (R + 31) / 32); }
+
+// Forward through Z3 (and y); H1T / H2T only when training.
+int forward(mp_mlp* h, const bf16* X, int B, Bufs& b, bool train, const float* target, cudaStream_t st) {
+  int rc;
+  if ((rc = gemm_tn(X, h->W1b, b.Z1, B, DH, DIN, h->status, st))) return rc;
+  k_elem<0><<<tiles(B, DH), 256, 0, st>>>(b.Z1, h->P + O_B1, nullptr, nullptr, B, DH, b.H1, train ? b.H1T : nullptr,
+                                          nullptr, nullptr);
+  if ((rc = gemm_tn(b.H1, h->W2b, b.Z2, B, DH, DH, h->status, st))) return rc;
+  k_elem<0><<<tiles(B, DH), 256, 0, st>>>(b.Z2, h->P + O_B2, nullptr, nullptr, B, DH, b.H2, train ? b.H2T : nullptr,
+                                          nullptr, nullptr);
+  if ((rc = gemm_tn(b.H2, h->W3b, b.Z3, B, DH, DH, h->status, st))) return rc;
+  k_output<<<(B * 32 + 255) / 256, 256, 0, st>>>(b.Z3, h->P, B, target, b.y, b.dy, h->scalar);
+  count_launch(3);
+  MP_CUDA_TRY(cudaGetLastError());
+  return MP_OK;
+}
+
+int train_step(mp_mlp* h, const bf16* X, const float* target, int B, float lr, cudaStream_t st) {
+  Bufs b;
+  int rc = ensure_ws(h, B, b);
+  if (rc) return rc;
+  MP_CUDA_TRY(cudaMemsetAsync(h->G, 0, NPARAM * 4, st));
+  MP_CUDA_TRY(cudaMemsetAsync(h->scalar, 0, 4, st));
+  k_transpose_bf16<<<tiles(B, DIN), 256, 0, st>>>(X, B, DIN, b.XT);
+  count_launch();
+  if ((rc = forward(h, X, B, b, true, target, st))) return rc;
+  // output layer and layer 3
+  k_sum<<<1, 256, 0, st>>>(b.dy, B, h->G + O_B4);
+  k_elem<2><<<tiles(B, DH), 256, 0, st>>>(b.Z3, h->P + O_B3, b.dy, h->P + O_W4, B, DH, b.dZ3, b.dZ3T, h->G + O_B3,
+                                          h->G + O_W4);
+  count_launch(2);
+  if ((rc = gemm_tn(b.dZ3T, b.H2T, h->G + O_W3, DH, DH, B, h->status, st))) return rc;
+  if ((rc = gemm_tn(b.dZ3, h->W3T, b.dH, B, DH, DH, h->status, st))) return rc;
+  k_elem<1><<<tiles(B, DH), 256, 0, st>>>(b.dH, h->P + O_B2, b.Z2, nullptr, B, DH, b.dZ2, b.dZ2T, h->G + O_B2, nullptr);
+  count_launch();
+  if ((rc = gemm_tn(b.dZ2T, b.H1T, h->G + O_W2, DH, DH, B, h->status, st))) return rc;
+  if ((rc = gemm_tn(b.dZ2, h->W2T, b.dH, B, DH, DH, h->status, st))) return rc;
+  k_elem<1><<<tiles(B, DH), 256, 0, st>>>(b.dH, h->P + O_B1, b.Z1, nullptr, B, DH, b.dZ1, b.dZ1T, h->G + O_B1, nullptr);
+  count_launch();
+  if ((rc = gemm_tn(b.dZ1T, b.XT, h->G + O_W1, DH, DIN, B, h->status, st))) return rc;
+  if (lr > 0.f) {
+    h->step += 1;
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float c1 = 1.f - powf(b1, (float)h->step), c2 = 1.f - powf(b2, (float)h->step);
+    k_adam<<<296, 256, 0, st>>>(h->P, h->G, h->M1, h->M2, NPARAM, lr, b1, b2, c1, c2, 1e-8f);
+    k_refresh<<<256, 256, 0, st>>>(h->P, h->W1b, h->W2b, h->W3b, h->W2T, h->W3T);
+    count_launch(2);
+  }
+  MP_CUDA_TRY(cudaGetLastError());
+  return MP_OK;
+}
+
+int upload_params(mp_mlp* h, const float* host, cudaStream_t st) {
+  MP_CUDA_TRY(cudaMemcpyAsync(h->P, host, NPARAM * 4, cudaMemcpyHostToDevice, st));
+  k_refresh<<<256, 256, 0, st>>>(h->P, h->W1b, h->W2b, h->W3b, h->W2T, h->W3T);
+  count_launch();
+  MP_CUDA_TRY(cudaStreamSynchronize(st));
+  return MP_OK;
+}
+
+}  // namespace mlpk
+}  // namespace mp
+
+extern "C" int mp_mlp_create(uint64_t seed, mp_mlp** out) {
+  using namespace mp::mlpk;
+  if (!out) return MP_EINVAL;
+  mp_mlp* h = new mp_mlp();
+  cudaGetDevice(&h->device);
+  // every region starts on a 256-byte boundary (NPARAM is odd; the GEMM
+  // epilogue stores 16-byte vectors into the gradient blocks)
+  const size_t preg = (NPARAM * 4 + 255) & ~size_t(255);
+  size_t bytes = 4 * preg + 5 * (size_t)DH * DH * 2 + 256 + 256;
+  char* p = nullptr;
+  if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    delete h;
+    return MP_ENOMEM;
+  }
+  cudaMemset(p, 0, bytes);
+  h->P = (float*)p; p += preg;
+  h->G = (float*)p; p += preg;
+  h->M1 = (float*)p; p += preg;
+  h->M2 = (float*)p; p += preg;
+  h->W1b = (bf16*)p; p += (size_t)DH * DH * 2;
+  h->W2b = (bf16*)p; p += (size_t)DH * DH * 2;
+  h->W3b = (bf16*)p; p += (size_t)DH * DH * 2;
+  h->W2T = (bf16*)p; p += (size_t)DH * DH * 2;
+  h->W3T = (bf16*)p; p += (size_t)DH * DH * 2;
+  h->status = (int*)p; p += 256;
+  h->scalar = (float*)p;
+  // He initialisation from splitmix64 + Box-Muller
+  std::vector<float> host(NPARAM, 0.f);
+  uint64_t s = seed;
+  auto next = [&]() {
+    s += 0x9E3779B97F4A7C15ull;
+    uint64_t z = s;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+  };
+  auto normal = [&]() {
+    const double u1 = ((next() >> 11) + 1) * (1.0 / 9007199254740993.0);
+    const double u2 = (next() >> 11) * (1.0 / 9007199254740992.0);
+    return std::sqrt(-2.0 * std::log(u1)) * std::cos(6.283185307179586 * u2);
+  };
+  for (size_t i = 0; i < (size_t)DH * DIN; ++i) host[O_W1 + i] = (float)(normal() * std::sqrt(2.0 / DIN));
+  for (size_t i = 0; i < (size_t)DH * DH; ++i) host[O_W2 + i] = (float)(normal() * std::sqrt(2.0 / DH));
+  for (size_t i = 0; i < (size_t)DH * DH; ++i) host[O_W3 + i] = (float)(normal() * std::sqrt(2.0 / DH));
+  for (size_t i = 0; i < (size_t)DH; ++i) host[O_W4 + i] = (float)(normal() * std::sqrt(1.0 / DH));
+  int rc = upload_params(h, host.data(), nullptr);
+  if (rc) {
+    mp_mlp_destroy(h);
+    return rc;
+  }
+  *out = h;
+  return MP_OK;
+}
+
+extern "C" int mp_mlp_destroy(mp_mlp* h) {
+  if (!h) return MP_OK;
+  if (h->ws) cudaFree(h->ws);
+  if (h->P) cudaFree(h->P);
+  delete h;
+  return MP_OK;
+}
+
+extern "C" int mp_mlp_num_params(void) { return (int)mp::mlpk::NPARAM; }
+
+extern "C" int mp_mlp_set_params(mp_mlp* h, const float* params) {
+  if (!h || !params) return MP_EINVAL;
+  return mp::mlpk::upload_params(h, params, nullptr);
+}
+
+extern "C" int mp_mlp_get_params(const mp_mlp* h, float* params, float* grads) {
+  if (!h) return MP_EINVAL;
+  if (params) MP_CUDA_TRY(cudaMemcpy(params, h->P, mp::mlpk::NPARAM * 4, cudaMemcpyDeviceToHost));
+  if (grads) MP_CUDA_TRY(cudaMemcpy(grads, h->G, mp::mlpk::NPARAM * 4, cudaMemcpyDeviceToHost));
+  return MP_OK;
+}
+
+extern "C" int mp_mlp_forward(mp_mlp* h, const void* X, float* y, int B, void* stream) {
+  using namespace mp::mlpk;
+  if (!h || !X || !y || B <= 0 || B % 128) return MP_EINVAL;
+  if (!mp::is_device_pointer(X) || !mp::is_device_pointer(y)) return MP_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  Bufs b;
+  int rc = ensure_ws(h, B, b);
+  if (rc) return rc;
+  MP_CUDA_TRY(cudaMemsetAsync(h->status, 0, 4, st));
+  if ((rc = forward(h, (const bf16*)X, B, b, false, nullptr, st))) return rc;
+  MP_CUDA_TRY(cudaMemcpyAsync(y, b.y, (size_t)B * 4, cudaMemcpyDeviceToDevice, st));
+  int s = 0;
+  MP_CUDA_TRY(cudaMemcpyAsync(&s, h->status, 4, cudaMemcpyDeviceToHost, st));
+  MP_CUDA_TRY(cudaStreamSynchronize(st));
+  return s;
+}
+
+extern "C" int mp_mlp_train_step(mp_mlp* h, const void* X, const float* target, int B, float lr, float* loss,
+                                 void* stream) {
+  using namespace mp::mlpk;
+  if (!h || !X || !target || B <= 0 || B % 128) return MP_EINVAL;
+  if (!mp::is_device_pointer(X) || !mp::is_device_pointer(target)) return MP_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  MP_CUDA_TRY(cudaMemsetAsync(h->status, 0, 4, st));
+  int rc = train_step(h, (const bf16*)X, target, B, lr, st);
+  if (rc) return rc;
+  int s = 0;
+  float l = 0.f;
+  MP_CUDA_TRY(cudaMemcpyAsync(&s, h->status, 4, cudaMemcpyDeviceToHost, st));
+  MP_CUDA_TRY(cudaMemcpyAsync(&l, h->scalar, 4, cudaMemcpyDeviceToHost, st));
+  MP_CUDA_TRY(cudaStreamSynchronize(st));
+  if (loss) *loss = l;
+  return s;
 }

@@ -1,6 +1,7 @@
 // Runtime support: per-device grow-only workspace, pointer classification,
 // launch accounting and status strings.
 #include <atomic>
+#include <cstdio>
 #include <mutex>
 
 #include "engine.h"
@@ -66,6 +67,17 @@ bool is_device_pointer(const void* p) {
 void count_launch(uint64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 namespace {
+thread_local char g_err[512] = "";
+}  // namespace
+
+void record_cuda_error(cudaError_t e, const char* file, int line) {
+  const char* base = file;
+  for (const char* c = file; *c; ++c)
+    if (*c == '/') base = c + 1;
+  std::snprintf(g_err, sizeof(g_err), "%s:%d: %s (%s)", base, line, cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+namespace {
 cudaEvent_t g_t0 = nullptr, g_t1 = nullptr;
 bool g_armed = false;
 }  // namespace
@@ -95,6 +107,8 @@ extern "C" const char* mp_strerror(int status) {
 }
 
 extern "C" uint64_t mp_kernel_launches(void) { return mp::g_launches.load(); }
+
+extern "C" const char* mp_last_error_detail(void) { return mp::g_err; }
 
 extern "C" int mp_set_kernel_timer(void* start_event, void* stop_event) {
   mp::g_t0 = (cudaEvent_t)start_event;

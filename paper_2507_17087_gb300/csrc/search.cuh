@@ -1,0 +1,225 @@
+// Device structures of the decompose search, shared by search.cu (exact
+// evaluation) and mlp.cu (candidate features for the learned scorer).
+#pragma once
+
+#include <vector>
+
+#include "engine.h"
+
+namespace mp {
+
+constexpr int kMaxChainPrims = 12;
+
+constexpr int kSearchMaxProcs = 16384;
+constexpr int kSmemBudget = 200 * 1024;
+
+struct ChainProg {
+  int32_t nprim;
+  int32_t depth;   // transforms of the chain; the rest are the flattening merges
+  Prim prim[kMaxChainPrims];
+};
+
+struct Fact {
+  uint32_t f[3];
+};
+
+struct Key {
+  unsigned long long p, s, idx;
+};
+
+__device__ __forceinline__ bool key_less(const Key& a, const Key& b) {
+  if (a.p != b.p) return a.p < b.p;
+  if (a.s != b.s) return a.s < b.s;
+  return a.idx < b.idx;
+}
+
+// Node of flat index b of the flattened chain space: apply the Fig. 4
+// inverse of every primitive, last to first, starting from the 1-D index.
+__device__ __forceinline__ uint32_t resolve_node(const ChainProg& cp, uint32_t b) {
+  uint32_t a[kMaxChainPrims + 2];
+  a[0] = b;
+  int r = 1;
+  for (int o = cp.nprim - 1; o >= 0; --o) {
+    const Prim& p = cp.prim[o];
+    if (p.op == P_SPLIT) {
+      a[p.p] = a[p.p] + a[p.p + 1] * p.d;
+      for (int t = p.p + 1; t < r - 1; ++t) a[t] = a[t + 1];
+      r -= 1;
+    } else if (p.op == P_MERGE) {
+      uint32_t q, rem;
+      divmod32(a[p.p], p.div, q, rem);
+      for (int t = r; t > p.q; --t) a[t] = a[t - 1];
+      a[p.q] = q;
+      a[p.p] = rem;
+      r += 1;
+    } else {
+      uint32_t tmp = a[p.p];
+      a[p.p] = a[p.q];
+      a[p.q] = tmp;
+    }
+  }
+  return a[0];   // (node, proc) = (a[0], a[1])
+}
+
+// Iterates the distinct block coordinates of one dimension (extent E split
+// into f blocks) with the number of tiles in each:
+//   E >= f: rep = i, weight = ceil((i+1) E / f) - ceil(i E / f)
+//   E <  f: rep = floor(i f / E), weight = 1
+// using only additions (the quotient/remainder of E / f or f / E once).
+struct BlockIter {
+  uint32_t big;      // E >= f
+  uint32_t A, B, m;  // quotient, remainder, modulus
+  uint32_t r;        // running remainder
+  uint32_t rep;
+  __device__ __forceinline__ void init(uint32_t E, uint32_t f) {
+    big = E >= f;
+    if (big) { A = E / f; B = E % f; m = f; } else { A = f / E; B = f % E; m = E; }
+    r = 0;
+    rep = 0;
+  }
+  // returns the weight of the current representative and advances
+  __device__ __forceinline__ uint32_t step() {
+    uint32_t w;
+    if (big) {
+      const uint32_t borrow = r < B;
+      w = A + borrow;
+      r = r + (borrow ? m : 0) - B;
+      rep += 1;
+    } else {
+      w = 1;
+      r += B;
+      const uint32_t carry = r >= m;
+      r -= carry ? m : 0;
+      rep += A + carry;
+    }
+    return w;
+  }
+};
+
+// Distinct nodes along one fibre (count of nodes seen), bitmap per thread in
+// shared memory (word w of thread t at bm[w * nthr + t]).
+__device__ __forceinline__ uint32_t fibre_distinct(const uint16_t* __restrict__ tab, uint32_t* bm, int nthr,
+                                                   int words, uint32_t base, uint32_t stride, uint32_t E,
+                                                   uint32_t f, uint32_t n) {
+  BlockIter it;
+  it.init(E, f);
+  uint32_t D = 0;
+  for (uint32_t iv = 0; iv < n; ++iv) {
+    const uint32_t node = tab[base + stride * it.rep];
+    it.step();
+    uint32_t* wp = bm + (node >> 5) * nthr;
+    const uint32_t bit = 1u << (node & 31);
+    const uint32_t word = *wp;
+    if (!(word & bit)) {
+      *wp = word | bit;
+      ++D;
+    }
+  }
+  if ((uint32_t)words <= n) {
+    for (int w = 0; w < words; ++w) bm[w * nthr] = 0;
+  } else {
+    it.init(E, f);
+    for (uint32_t iv = 0; iv < n; ++iv) {
+      const uint32_t node = tab[base + stride * it.rep];
+      it.step();
+      bm[(node >> 5) * nthr] = 0;
+    }
+  }
+  return D;
+}
+
+// Secondary cost (tiles) of factorisation f for the chain tabulated in tab.
+__device__ __forceinline__ unsigned long long secondary_cost(const uint16_t* __restrict__ tab, uint32_t* bm, int nthr, int words,
+                                             const uint32_t E[3], const uint32_t f[3]) {
+  const uint32_t stride[3] = {1u, f[0], f[0] * f[1]};
+  uint32_t n[3];
+  for (int t = 0; t < 3; ++t) n[t] = E[t] < f[t] ? E[t] : f[t];
+  unsigned long long sec = 0;
+  for (int v = 0; v < 3; ++v) {
+    if (n[v] <= 1) continue;   // one block along the fibre: one owner
+    const int u = v == 0 ? 1 : 0;
+    const int w = v == 2 ? 1 : 2;
+    BlockIter iw;
+    iw.init(E[w], f[w]);
+    for (uint32_t a = 0; a < n[w]; ++a) {
+      const uint32_t rep_w = iw.rep;
+      const uint32_t wt_w = iw.step();
+      BlockIter iu;
+      iu.init(E[u], f[u]);
+      unsigned long long acc = 0;
+      for (uint32_t c = 0; c < n[u]; ++c) {
+        const uint32_t rep_u = iu.rep;
+        const uint32_t wt_u = iu.step();
+        const uint32_t base = rep_u * stride[u] + rep_w * stride[w];
+        const uint32_t D = fibre_distinct(tab, bm, nthr, words, base, stride[v], E[v], f[v], n[v]);
+        acc += (unsigned long long)wt_u * (D - 1);
+      }
+      sec += (unsigned long long)wt_w * acc;
+    }
+  }
+  return sec;
+}
+
+__device__ __forceinline__ unsigned long long primary_cost(const uint32_t E[3], const uint32_t f[3]) {
+  unsigned long long p = 0;
+  for (int v = 0; v < 3; ++v) {
+    const int u = v == 0 ? 1 : 0;
+    const int w = v == 2 ? 1 : 2;
+    const uint32_t nv = E[v] < f[v] ? E[v] : f[v];
+    p += (unsigned long long)(nv - 1) * E[u] * E[w];
+  }
+  return p;
+}
+
+__device__ __forceinline__ void block_argmin(Key& k, Key* red) {
+  for (int o = 16; o > 0; o >>= 1) {
+    Key other;
+    other.p = __shfl_down_sync(0xFFFFFFFFu, k.p, o);
+    other.s = __shfl_down_sync(0xFFFFFFFFu, k.s, o);
+    other.idx = __shfl_down_sync(0xFFFFFFFFu, k.idx, o);
+    if (key_less(other, k)) k = other;
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) red[warp] = k;
+  __syncthreads();
+  if (warp == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    k = lane < nw ? red[lane] : Key{~0ull, ~0ull, ~0ull};
+    for (int o = 16; o > 0; o >>= 1) {
+      Key other;
+      other.p = __shfl_down_sync(0xFFFFFFFFu, k.p, o);
+      other.s = __shfl_down_sync(0xFFFFFFFFu, k.s, o);
+      other.idx = __shfl_down_sync(0xFFFFFFFFu, k.idx, o);
+      if (key_less(other, k)) k = other;
+    }
+  }
+}
+
+__device__ __forceinline__ void build_table(const ChainProg& cp, uint16_t* tab, uint32_t P) {
+  for (uint32_t b = threadIdx.x; b < P; b += blockDim.x) tab[b] = (uint16_t)resolve_node(cp, b);
+}
+
+
+// ----------------------------------------------------------------- host side
+
+struct SearchSpace {
+  std::vector<std::vector<int64_t>> facts;
+  std::vector<std::vector<CanonOp>> chains;
+  std::vector<ChainProg> progs;
+  std::vector<Fact> fdev;
+  int words = 0;
+  int threads = 0;
+  size_t smem = 0;
+};
+
+ChainProg compile_chain(int64_t n, int64_t g, const std::vector<CanonOp>& ch);
+int validate_query(const mp_search_query& q);
+int prepare(const mp_search_query& q, SearchSpace& S);
+// Exact costs (bytes) of n listed candidates, all buffers on the device.
+int candidate_costs_dev(const mp_search_query& q, const SearchSpace& S, const ChainProg* d_progs,
+                        const Fact* d_facts, const int64_t* d_idx, int64_t n, uint64_t* d_p, uint64_t* d_s,
+                        cudaStream_t st);
+// Exhaustive argmin on the device; the result on the host.
+int exhaustive_search(const mp_search_query& q, mp_search_result* out, cudaStream_t st);
+
+}  // namespace mp

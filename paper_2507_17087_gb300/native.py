@@ -36,7 +36,13 @@ STATUS = {0: "MP_OK", 1: "MP_EINVAL", 2: "MP_EOVERFLOW", 3: "MP_ENOMEM", 4: "MP_
 class MapleError(RuntimeError):
     def __init__(self, status: int, where: str):
         self.status = status
-        super().__init__(f"{where}: {STATUS.get(status, status)} ({strerror(status)})")
+        detail = ""
+        if status == 4:
+            try:
+                detail = " at " + lib().mp_last_error_detail().decode()
+            except Exception:  # noqa: BLE001 - formatting another error
+                pass
+        super().__init__(f"{where}: {STATUS.get(status, status)} ({strerror(status)}){detail}")
 
 
 class mp_space(ctypes.Structure):
@@ -102,6 +108,7 @@ def lib():
                 "mp_search_space": (I, [I, I, I, V, V]),
                 "mp_search_candidate": (I, [V, I64, V, V, V]),
                 "mp_strerror": (ctypes.c_char_p, [I]),
+                "mp_last_error_detail": (ctypes.c_char_p, []),
                 "mp_kernel_launches": (U64, []),
                 "mp_set_kernel_timer": (I, [V, V]),
                 "mp_batch_create": (I, [V, I, V]),
@@ -109,6 +116,16 @@ def lib():
                 "mp_batch_run": (I, [V, V, V, V, V, I, V]),
                 "mp_batch_destroy": (I, [V]),
                 "mp_gemm_bf16": (I, [V, V, V, I, I, I, V]),
+                "mp_mlp_create": (I, [ctypes.c_uint64, V]),
+                "mp_mlp_destroy": (I, [V]),
+                "mp_mlp_num_params": (I, []),
+                "mp_mlp_set_params": (I, [V, V]),
+                "mp_mlp_get_params": (I, [V, V, V]),
+                "mp_mlp_forward": (I, [V, V, V, I, V]),
+                "mp_mlp_train_step": (I, [V, V, V, I, ctypes.c_float, V, V]),
+                "mp_mlp_train_search": (I, [V, V, I, I, I, I, ctypes.c_float, ctypes.c_uint64, V, V]),
+                "mp_learned_search": (I, [V, V, I, I, V, V, V]),
+                "mp_learned_scores": (I, [V, V, V, V, V, V]),
                 "mp_descriptor_bytes": (U64, []),
             }
             for name, (res, args) in sig.items():
@@ -433,3 +450,94 @@ def gemm_bf16(A, B, C, stream=None):
     M, K = A.shape
     N = B.shape[0]
     _check(lib().mp_gemm_bf16(_ptr(A), _ptr(B), _ptr(C), M, N, K, _stream(stream)), "mp_gemm_bf16")
+
+
+class mp_learned_stats(ctypes.Structure):
+    _fields_ = [("n_scored", ctypes.c_int64), ("n_exact", ctypes.c_int64), ("certified", ctypes.c_int32),
+                ("fallback", ctypes.c_int32), ("margin", ctypes.c_double)]
+
+
+LEARNED_NO_FALLBACK = 1
+PARAM_BLOCKS = [("W1", (256, 64)), ("b1", (256,)), ("W2", (256, 256)), ("b2", (256,)), ("W3", (256, 256)),
+                ("b3", (256,)), ("w4", (256,)), ("b4", (1,))]
+
+
+def _search_result(r):
+    return {"index": r.index, "f": tuple(r.f), "chain_rank": r.chain_rank,
+            "chain": tuple(xform_tuple(r.chain[o]) for o in range(r.chain_len)),
+            "primary_bytes": r.primary_bytes, "secondary_bytes": r.secondary_bytes,
+            "n_candidates": r.n_candidates, "n_chains": r.n_chains, "n_factorisations": r.n_factorisations}
+
+
+class MLP:
+    """The learned cost model (mp_mlp_*), parameters on the current device."""
+
+    def __init__(self, seed=0):
+        self._h = ctypes.c_void_p()
+        _check(lib().mp_mlp_create(int(seed), ctypes.byref(self._h)), "mp_mlp_create")
+        self.nparams = lib().mp_mlp_num_params()
+
+    def set_params(self, params: dict):
+        flat = np.concatenate([np.asarray(params[k], dtype=np.float32).reshape(-1) for k, _ in PARAM_BLOCKS])
+        assert flat.size == self.nparams
+        _check(lib().mp_mlp_set_params(self._h, flat.ctypes.data), "mp_mlp_set_params")
+
+    def get_params(self, grads=False):
+        p = np.zeros(self.nparams, dtype=np.float32)
+        g = np.zeros(self.nparams, dtype=np.float32)
+        _check(lib().mp_mlp_get_params(self._h, p.ctypes.data, g.ctypes.data), "mp_mlp_get_params")
+        out, o = {}, 0
+        src = g if grads else p
+        for k, shape in PARAM_BLOCKS:
+            n = int(np.prod(shape))
+            out[k] = src[o:o + n].reshape(shape).astype(np.float64)
+            o += n
+        return out
+
+    def forward(self, X, y, stream=None):
+        _check(lib().mp_mlp_forward(self._h, _ptr(X), _ptr(y), X.shape[0], _stream(stream)), "mp_mlp_forward")
+
+    def train_step(self, X, target, lr, stream=None):
+        loss = ctypes.c_float(0)
+        _check(lib().mp_mlp_train_step(self._h, _ptr(X), _ptr(target), X.shape[0], ctypes.c_float(lr),
+                                       ctypes.byref(loss), _stream(stream)), "mp_mlp_train_step")
+        return loss.value
+
+    def train_search(self, queries, samples_per_query=2048, epochs=4, batch=4096, lr=1e-3, seed=1, stream=None):
+        qs = [_query(q) for q in queries]
+        arr = (mp_search_query * len(qs))(*qs)
+        loss = ctypes.c_float(0)
+        _check(lib().mp_mlp_train_search(self._h, arr, len(qs), samples_per_query, epochs, batch,
+                                         ctypes.c_float(lr), int(seed), ctypes.byref(loss), _stream(stream)),
+               "mp_mlp_train_search")
+        return loss.value
+
+    def learned_search(self, query, K=1024, fallback=True, stream=None):
+        q = _query(query)
+        out = mp_search_result()
+        st = mp_learned_stats()
+        flags = 0 if fallback else LEARNED_NO_FALLBACK
+        _check(lib().mp_learned_search(self._h, ctypes.byref(q), int(K), flags, ctypes.byref(out),
+                                       ctypes.byref(st), _stream(stream)), "mp_learned_search")
+        res = _search_result(out)
+        res.update({"n_scored": st.n_scored, "n_exact": st.n_exact, "certified": bool(st.certified),
+                    "fallback": bool(st.fallback), "margin": st.margin})
+        return res
+
+    def scores(self, query, scores, features=None, stream=None):
+        q = _query(query)
+        n = ctypes.c_int64(0)
+        _check(lib().mp_learned_scores(self._h, ctypes.byref(q), _ptr(scores), _ptr(features), ctypes.byref(n),
+                                       _stream(stream)), "mp_learned_scores")
+        return n.value
+
+    def close(self):
+        if self._h:
+            lib().mp_mlp_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001
+            pass

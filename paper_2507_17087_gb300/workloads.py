@@ -165,3 +165,21 @@ def search_query_small(first_index: int = 7000, count: int = 8):
         out.append({"name": f"search-small-{q}", "MNK": (M, N, K), "machine": (n, g),
                     "max_depth": r.choice((1, 2, 3)), "tile_bytes": 512 * 512 * 4})
     return out
+
+
+TRAIN_EXTENTS = (128, 256, 512, 1024, 2048, 4096, 8192)
+TRAIN_PROCS = (256, 512, 720, 1024, 1440, 2048, 2520, 3600, 4096)
+
+
+def search_training_queries(count: int, first_index: int = 20000):
+    """Training queries for the learned cost model: a wider generator than
+    the evaluation queries (extents from {128, ..., 8192}, P from a set of
+    highly composite counts, seeds disjoint from the evaluation seeds)."""
+    out = []
+    for q in range(count):
+        r = rng(first_index + q)
+        M, N, K = (r.choice(TRAIN_EXTENTS) for _ in range(3))
+        P = r.choice(TRAIN_PROCS)
+        out.append({"name": f"train-{q}", "MNK": (M, N, K), "machine": (P // 8, 8),
+                    "max_depth": 3, "tile_bytes": 512 * 512 * 4})
+    return out

@@ -27,3 +27,117 @@ def test_gemm_bf16_against_float64(M, N_, K):
     err = (C.double() - ref).abs().max().item()
     scale = ref.abs().max().item()
     assert err <= 1e-5 * scale * max(1.0, K / 256), (err, scale)
+
+
+from oracle import mlp as R  # noqa: E402
+from paper_2507_17087_gb300 import workloads as W  # noqa: E402
+
+
+def bf16_round(a):
+    return torch.from_numpy(np.asarray(a, dtype=np.float32)).to(torch.bfloat16).double().numpy()
+
+
+def rounded_params(p):
+    q = dict(p)
+    for k in ("W1", "W2", "W3"):
+        q[k] = bf16_round(p[k])
+    return q
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
+
+
+def test_forward_against_float64():
+    model = N.MLP(seed=3)
+    p = R.init_params(3)
+    rng = np.random.default_rng(3)
+    for k in ("b1", "b2", "b3"):
+        p[k] = rng.standard_normal(p[k].shape) * 0.1
+    p["b4"] = np.array([0.2])
+    model.set_params(p)
+    X = torch.from_numpy(rng.standard_normal((512, 64)).astype(np.float32)).to(torch.bfloat16).cuda()
+    y = torch.empty(512, dtype=torch.float32, device="cuda")
+    model.forward(X, y)
+    ref, _ = R.forward(rounded_params(p), X.double().cpu().numpy())
+    assert rel(y.double().cpu().numpy(), ref) <= 1e-2
+
+
+def test_gradients_against_float64():
+    model = N.MLP(seed=4)
+    p = R.init_params(4)
+    rng = np.random.default_rng(4)
+    for k in ("b1", "b2", "b3"):
+        p[k] = rng.standard_normal(p[k].shape) * 0.1
+    model.set_params(p)
+    B = 256
+    X = torch.from_numpy(rng.standard_normal((B, 64)).astype(np.float32)).to(torch.bfloat16).cuda()
+    t = torch.from_numpy(rng.standard_normal(B).astype(np.float32)).cuda()
+    loss = model.train_step(X, t, lr=0.0)
+    g = model.get_params(grads=True)
+    pr = rounded_params(p)
+    xs, ts = X.double().cpu().numpy(), t.double().cpu().numpy()
+    # float64 with the engine's BF16 rounding points: tight
+    y, cache = R.forward(pr, xs, rnd=bf16_round)
+    ref = R.backward(pr, cache, y, ts, rnd=bf16_round)
+    assert abs(loss - R.loss(y, ts)) <= 1e-3 * abs(loss)
+    for k in ref:
+        assert rel(g[k], ref[k]) <= 1e-2, k
+    # pure float64: within the BF16 rounding of five stored operands
+    y, cache = R.forward(pr, xs)
+    ref = R.backward(pr, cache, y, ts)
+    for k in ref:
+        assert rel(g[k], ref[k]) <= 6e-2, k
+
+
+def test_adam_step_against_float64():
+    model = N.MLP(seed=5)
+    p = model.get_params()
+    rng = np.random.default_rng(5)
+    X = torch.from_numpy(rng.standard_normal((128, 64)).astype(np.float32)).to(torch.bfloat16).cuda()
+    t = torch.from_numpy(rng.standard_normal(128).astype(np.float32)).cuda()
+    model.train_step(X, t, lr=1e-3)
+    g = model.get_params(grads=True)
+    after = model.get_params()
+    want = R.adam_step({k: v.copy() for k, v in p.items()}, g, {}, lr=1e-3)
+    for k in p:
+        assert np.allclose(after[k], want[k], rtol=0, atol=2e-6), k
+
+
+def test_fused_scores_match_unfused_forward_and_float64():
+    model = N.MLP(seed=6)
+    q = {"MNK": (256, 1024, 256), "machine": (16, 8), "max_depth": 2, "tile_bytes": 512 * 512 * 4}
+    nf, nc = N.search_space(128, 8, 2)
+    n = nf * nc
+    npad = (n + 127) // 128 * 128
+    scores = torch.empty(n, dtype=torch.float32, device="cuda")
+    feats = torch.zeros(npad, 64, dtype=torch.bfloat16, device="cuda")
+    assert model.scores(q, scores, feats) == n
+    y = torch.empty(npad, dtype=torch.float32, device="cuda")
+    model.forward(feats, y)
+    assert rel(scores.double().cpu().numpy(), y[:n].double().cpu().numpy()) <= 1e-3
+    ref, _ = R.forward(rounded_params(model.get_params()), feats[:n].double().cpu().numpy())
+    assert rel(scores.double().cpu().numpy(), ref) <= 1e-2
+
+
+def test_learned_search_trains_and_finds_the_optimum():
+    model = N.MLP(seed=7)
+    train = W.search_training_queries(48)
+    loss0 = model.train_search(train[:4], samples_per_query=512, epochs=1, batch=512, lr=1e-3, seed=1)
+    loss = model.train_search(train, samples_per_query=4096, epochs=6, batch=4096, lr=1e-3, seed=2)
+    print(f"training loss {loss0:.4f} -> {loss:.4f}")
+    assert np.isfinite(loss) and loss < loss0
+    evalq = W.search_queries(12, first_index=9000)
+    zero_regret = 0
+    for q in evalq:
+        exact = N.decompose_search([q])[0]
+        got = model.learned_search(q, K=1024, fallback=True)
+        # with the fallback the answer is always the exhaustive optimum
+        assert (got["index"], got["primary_bytes"], got["secondary_bytes"]) == \
+            (exact["index"], exact["primary_bytes"], exact["secondary_bytes"])
+        raw = model.learned_search(q, K=1024, fallback=False)
+        zero_regret += (raw["primary_bytes"], raw["secondary_bytes"]) == \
+            (exact["primary_bytes"], exact["secondary_bytes"])
+        assert raw["n_exact"] <= 1024 and raw["n_scored"] == exact["n_candidates"]
+    print(f"zero-regret without fallback: {zero_regret}/{len(evalq)}")
+    assert zero_regret >= len(evalq) // 2
