@@ -47,9 +47,11 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=4)
-    ap.add_argument("--cpu-sample", type=int, default=1 << 21,
+    ap.add_argument("--cpu-sample", type=int, default=1 << 25,
                     help="points of the launch the CPU oracle maps for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the search / batched / learned measurements")
     return ap.parse_args()
 
 
@@ -143,25 +145,128 @@ def cpu_baseline(sample: int):
             "seconds": dt}
 
 
+def extra_search(N, W, torch):
+    """Exact candidates/s of the exhaustive decompose search (every candidate's
+    secondary scanned) and the time to the optimum with the primary bound."""
+    qs = [q for q in W.search_queries(16) if q["machine"][0] * q["machine"][1] in (2520, 3600)][:2]
+    N.decompose_search(qs[:1], full=True)   # warm
+    out = []
+    for q in qs:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = N.decompose_search([q], full=True)[0]
+        t_full = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        r2 = N.decompose_search([q])[0]
+        t_bound = time.perf_counter() - t0
+        assert r2["index"] == r["index"]
+        out.append({"MNK": q["MNK"], "P": q["machine"][0] * q["machine"][1], "candidates": r["n_candidates"],
+                    "ms_full": 1e3 * t_full, "ms_primary_bound": 1e3 * t_bound})
+    cands = sum(o["candidates"] for o in out)
+    secs = sum(o["ms_full"] for o in out) / 1e3
+    return {"metric": "exact candidates/s", "value": cands / secs, "unit": "candidates/s",
+            "workload": "3-D matmul decompose search, all ordered 3-factorisations x chains of depth <= 3, "
+                        "every candidate's moved-tile cost evaluated", "queries": out}
+
+
+def extra_batched(N, W, torch, dev, runs=5):
+    """The 10,000-query batch in one graph replay."""
+    qs = W.batched_queries(10000)
+    launches = [(q["L"], q["machine"], N.chain_from_draws(*q["machine"], q["draws"]), q["dist"], q["face"])
+                for q in qs]
+    t0 = time.perf_counter()
+    b = N.Batch(launches)
+    t_create = time.perf_counter() - t0
+    info = b.info()
+    ids = torch.empty(int(info["total_ids"]), dtype=torch.int32, device=dev)
+    hist = torch.empty(int(info["total_procs"]), dtype=torch.int64, device=dev)
+    recv = torch.empty(int(info["total_procs"]), dtype=torch.int64, device=dev)
+    halo = torch.empty(b.n, dtype=torch.int64, device=dev)
+    b.run(ids=ids, hist=hist, halo=halo, recv=recv, autotune=True)
+    b.run(ids=ids, hist=hist, halo=halo, recv=recv)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(runs):
+        b.run(ids=ids, hist=hist, halo=halo, recv=recv)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / runs
+    points = sum(math.prod(q["L"]) for q in qs)
+    res = {"metric": "points mapped/s", "value": points / (ms / 1e3), "unit": "points/s", "queries": len(qs),
+           "points": points, "ms_per_batch": ms, "ms_plan_once": 1e3 * t_create,
+           "tile_groups": b.info()["tile_groups"], "hbm_gbs_ids": 4 * points / (ms / 1e3) / 1e9}
+    b.close()
+    del ids, hist, recv, halo
+    torch.cuda.empty_cache()
+    return res
+
+
+def extra_learned(N, W, torch, n_train=512, per_query=4096, epochs=8, n_eval=16):
+    """Learned pruning: train on exact labels, then time-to-optimum against
+    the exhaustive search on held-out queries."""
+    model = N.MLP(seed=11)
+    t0 = time.perf_counter()
+    loss = model.train_search(W.search_training_queries(n_train), samples_per_query=per_query, epochs=epochs,
+                              batch=4096, lr=1e-3, seed=3)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    evalq = W.search_queries(n_eval, first_index=9000)
+    zr = fb = 0
+    t_l = t_e = 0.0
+    for q in evalq:
+        t0 = time.perf_counter()
+        full = N.decompose_search([q], full=True)[0]
+        t_e += time.perf_counter() - t0
+        t0 = time.perf_counter()
+        got = model.learned_search(q, K=1024, fallback=True)
+        t_l += time.perf_counter() - t0
+        assert (got["primary_bytes"], got["secondary_bytes"]) == (full["primary_bytes"], full["secondary_bytes"])
+        fb += got["fallback"]
+        raw = model.learned_search(q, K=1024, fallback=False)
+        zr += (raw["primary_bytes"], raw["secondary_bytes"]) == (full["primary_bytes"], full["secondary_bytes"])
+    model.close()
+    return {"metric": "pruned vs exhaustive time-to-optimum", "value": t_e / t_l, "unit": "x (speed-up)",
+            "ms_learned_mean": 1e3 * t_l / n_eval, "ms_exhaustive_mean": 1e3 * t_e / n_eval,
+            "zero_regret_without_fallback": zr / n_eval, "exact_with_fallback": 1.0, "fallbacks": fb,
+            "eval_queries": n_eval, "train_labels": n_train * per_query, "train_epochs": epochs,
+            "train_seconds": t_train, "train_final_loss": loss, "K": 1024}
+
+
+def max_over_ranks(value: float, dist, device) -> float:
+    """The largest value of all ranks (the job is as slow as its slowest
+    rank); the value itself without a process group."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def run_reference(args, rank, world):
+    """The CPU oracle timed on the host cores: each step maps a bounded sample
+    of the large launch (sized so that the whole run ends in a few minutes)."""
     if rank != 0:
         return
-    steps_val = []
+    steps = max(1, args.steps)
+    per_step = max(1 << 14, min(1 << 24, (1 << 29) // (steps + max(args.warmup, 0))))
+    times = []
     info = None
-    for _ in range(args.warmup):
-        cpu_baseline(max(args.cpu_sample // 8, 4096))
-    for _ in range(args.steps):
-        info = cpu_baseline(args.cpu_sample)
-        steps_val.append(info["seconds"])
-    total_s = sum(steps_val)
-    value = args.cpu_sample * len(steps_val) / total_s
+    for _ in range(max(args.warmup, 0)):
+        cpu_baseline(max(per_step // 8, 4096))
+    for _ in range(steps):
+        info = cpu_baseline(per_step)
+        times.append(info["seconds"])
+    total_s = sum(times)
+    value = per_step * steps / total_s
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1e3 * total_s / max(1, len(steps_val)),
+            "steps": steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_s / steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
             "data": "synthetic",
-            "config": {"workload": "large launch 1024x1024x512 on 64x8, random depth-4 chain "
-                                   "(CPU oracle on a bounded sample)", "sample_points": args.cpu_sample},
+            "config": {"workload": "large launch: 1024x1024x512 points on 64 nodes x 8 procs, seeded random "
+                                   "split/merge/swap chain depth 4 (CPU oracle, bounded sample per step)",
+                       "sample_points_per_step": per_step},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": info["cores"], "kind": "oracle",
                              "sample": info["sample"]},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -246,10 +351,7 @@ def main():
     ms = e0.elapsed_time(e1)
     kms = [a.elapsed_time(b) for pairs in kev for a, b in pairs]
     k_avg_ms = sum(kms) / len(kms)
-    if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist, dev)
     points = 3 * npts * args.steps * world
     value = points / (ms / 1e3)
 
@@ -278,10 +380,7 @@ def main():
     for _ in range(args.e2e_steps):
         e2e_step()
     e2e_s = time.perf_counter() - t0
-    if dist:
-        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(e2e_s, dist, dev)
     e2e_value = 3 * npts * args.e2e_steps * world / e2e_s
     d2h = 3 * (npts * 4 + P * 8 + 8 + P * 8)
     h2d = per_step_launches * N.descriptor_bytes()
@@ -308,7 +407,15 @@ def main():
             "gpu_launches": gpu_launches,
             "clocks": clocks,
         }
-        if not args.no_cpu_baseline and world >= 1:
+        if not args.no_extras:
+            for key, fn in (("search", lambda: extra_search(N, W, torch)),
+                            ("batched", lambda: extra_batched(N, W, torch, dev)),
+                            ("learned", lambda: extra_learned(N, W, torch))):
+                try:
+                    line[key] = fn()
+                except Exception as exc:  # noqa: BLE001 - an extra must not lose the main line
+                    line[key] = {"error": f"{type(exc).__name__}: {exc}"}
+        if not args.no_cpu_baseline and world == 1:
             try:
                 cb = cpu_baseline(args.cpu_sample)
                 cb.pop("seconds", None)

@@ -302,30 +302,35 @@ int mp_mlp_train_step(mp_mlp* model, const void* X, const float* target, int B, 
                       void* stream);
 
 /* Trains the model on exact costs: for each query, samples_per_query
- * candidates (half uniform, half among the lowest primary costs) are
- * evaluated exactly (mp_candidate_costs), featurised, and the model takes
- * `epochs` passes of Adam over shuffled batches of `batch` (a multiple of
- * 128).  Regression target: 4 min(p / p_min - 1, 16) + log2(1 + s) / 48 with
- * p, s the candidate's primary / secondary cost in tiles and p_min the
- * query's least primary.  *final_loss: last batch loss. */
+ * candidates (half with the least primary cost, a quarter among the eight
+ * lowest primaries, a quarter uniform) are evaluated exactly
+ * (mp_candidate_costs), featurised, and the model takes `epochs` passes of
+ * Adam over shuffled batches of `batch` (a multiple of 128).  Regression
+ * target: 2 min(p / p_min - 1, 16) + log2(1 + s) / 8 with p, s the
+ * candidate's primary / secondary cost in tiles and p_min the query's least
+ * primary.  *final_loss: last batch loss. */
 int mp_mlp_train_search(mp_mlp* model, const mp_search_query* queries, int n_queries, int samples_per_query,
                         int epochs, int batch, float lr, uint64_t seed, float* final_loss, void* stream);
 
-/* Learned decompose search: the model scores every candidate of the query
- * (fused tcgen05 inference), the K best scores are evaluated exactly, and
- * their lexicographic argmin is returned if it is certified (every
- * candidate with a primary cost no higher than the winner's was among the
- * K) or if the largest model error seen on the K leaves a margin; otherwise
- * the exhaustive search runs (unless MP_LEARNED_NO_FALLBACK).  The returned
- * costs are always exact.  K in [1, 65536].  Synchronous. */
+/* Learned decompose search.  Only candidates whose factorisation attains
+ * the least primary cost can win the lexicographic argmin (the primary is
+ * exact and closed-form), so the model scores those (fused tcgen05
+ * inference; MP_LEARNED_SCORE_ALL scores every candidate), the K best scores
+ * are evaluated exactly, and their argmin is returned if it is certified
+ * (every candidate that could beat it was among the K) or if the model's
+ * largest overestimation on the K leaves a margin below the selection
+ * threshold; otherwise the exhaustive search runs (unless
+ * MP_LEARNED_NO_FALLBACK).  The returned costs are always exact.  K in
+ * [1, 65536].  Synchronous. */
 typedef struct mp_learned_stats {
   int64_t n_scored;   /* candidates scored by the model            */
   int64_t n_exact;    /* candidates evaluated exactly              */
   int32_t certified;  /* 1: exact certificate on the top-K         */
   int32_t fallback;   /* 1: the exhaustive search ran              */
-  double margin;      /* threshold - 2 * max error - winner target */
+  double margin;      /* threshold - winner target - 1.5 * max overestimation */
 } mp_learned_stats;
 #define MP_LEARNED_NO_FALLBACK 1
+#define MP_LEARNED_SCORE_ALL 2
 int mp_learned_search(mp_mlp* model, const mp_search_query* query, int K, int flags, mp_search_result* out,
                       mp_learned_stats* stats, void* stream);
 

@@ -124,11 +124,13 @@ __device__ __forceinline__ void candidate_features(const QInfo& Q, const ChainPr
   x[61] = x[62] = x[63] = 0.f;
 }
 
-// Regression target: lexicographic (primary, secondary) on one scale.
+// Regression target: the primary cost relative to the least one, then the
+// secondary on a log scale (within the candidates of least primary only the
+// second term varies, over a range of a few units).
 __device__ __forceinline__ float target_of(unsigned long long p_tiles, unsigned long long s_tiles,
                                            unsigned long long pmin) {
   const float pn = (float)((double)p_tiles / (double)max(pmin, 1ull) - 1.0);
-  return 4.f * fminf(pn, 16.f) + log2f(1.f + (float)s_tiles) / 48.f;
+  return 2.f * fminf(pn, 16.f) + log2f(1.f + (float)s_tiles) / 8.f;
 }
 
 __global__ void k_primaries(const Fact* __restrict__ facts, uint32_t nf, uint32_t E0, uint32_t E1, uint32_t E2,
@@ -215,8 +217,8 @@ __global__ void __launch_bounds__(128) k_score(const __grid_constant__ QInfo Q, 
                                                const Fact* __restrict__ facts, const float* __restrict__ chainfeat,
                                                const bf16* __restrict__ W1b, const bf16* __restrict__ W2b,
                                                const bf16* __restrict__ W3b, const float* __restrict__ P,
-                                               unsigned long long n, float* __restrict__ scores,
-                                               int* __restrict__ status) {
+                                               const uint32_t* __restrict__ flist, unsigned long long n,
+                                               float* __restrict__ scores, int* __restrict__ status) {
   extern __shared__ uint8_t smem_raw[];
   __shared__ uint64_t bar;
   __shared__ uint32_t tmem_slot;
@@ -250,11 +252,16 @@ __global__ void __launch_bounds__(128) k_score(const __grid_constant__ QInfo Q, 
   bool ok = true;
   const unsigned long long ntiles = (n + 127) / 128;
   for (unsigned long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
-    const unsigned long long cand = tile * 128 + threadIdx.x;
+    const unsigned long long cand = tile * 128 + threadIdx.x;   // position in the scored list
     {
       float x[64];
       if (cand < n) {
-        candidate_features(Q, progs, facts, chainfeat, cand, x, nullptr);
+        unsigned long long idx = cand;
+        if (flist) {
+          const unsigned long long j = cand / Q.nchains;
+          idx = (unsigned long long)flist[j] * Q.nchains + (cand - j * Q.nchains);
+        }
+        candidate_features(Q, progs, facts, chainfeat, idx, x, nullptr);
       } else {
         for (int i = 0; i < 64; ++i) x[i] = 0.f;
       }
@@ -502,7 +509,7 @@ __global__ void k_take(const float* __restrict__ s, const int64_t* __restrict__ 
 
 float host_target(unsigned long long p, unsigned long long sc, unsigned long long pmin) {
   const float pn = (float)((double)p / (double)std::max(pmin, 1ull) - 1.0);
-  return 4.f * std::min(pn, 16.f) + std::log2(1.f + (float)sc) / 48.f;
+  return 2.f * std::min(pn, 16.f) + std::log2(1.f + (float)sc) / 8.f;
 }
 
 }  // namespace lrn
@@ -553,14 +560,16 @@ extern "C" int mp_mlp_train_search(mp_mlp* h, const mp_search_query* queries, in
     std::vector<uint32_t> order(NF);
     std::iota(order.begin(), order.end(), 0u);
     std::sort(order.begin(), order.end(), [&](uint32_t a, uint32_t b) { return pq.prim[a] < pq.prim[b]; });
-    // half uniform, a quarter on the best factorisations, a quarter on the
-    // eight lowest primaries (the ranking near the optimum matters most)
+    // half on the factorisations of least primary cost (the learned search
+    // ranks those), a quarter on the eight lowest primaries, a quarter uniform
+    size_t nbest = 1;
+    while (nbest < NF && pq.prim[order[nbest]] == pq.prim[order[0]]) ++nbest;
     for (size_t i = 0; i < per; ++i) {
       const uint64_t r = splitmix(rng);
       uint64_t fr;
-      if (i % 4 < 2) fr = r % NF;
-      else if (i % 4 == 2) fr = order[0];
-      else fr = order[(r >> 20) % std::min<uint64_t>(8, NF)];
+      if (i % 4 < 2) fr = order[(r >> 20) % nbest];
+      else if (i % 4 == 2) fr = order[(r >> 20) % std::min<uint64_t>(8, NF)];
+      else fr = r % NF;
       idx[i] = (int64_t)(fr * NC + (splitmix(rng) % NC));
     }
     if (cudaMemcpyAsync(d_idx, idx.data(), per * 8, cudaMemcpyHostToDevice, st) != cudaSuccess) { rc = MP_ECUDA; break; }
@@ -612,12 +621,20 @@ extern "C" int mp_learned_search(mp_mlp* h, const mp_search_query* query, int K,
   char* region = g_pool_q.get(64u << 20);
   if (!region) return MP_ENOMEM;
   if ((rc = prepare_query(q, pq, region, 64u << 20, &used, st))) return rc;
-  const uint64_t NC = pq.S.chains.size(), NF = pq.S.facts.size(), ncand = NC * NF;
+  const uint64_t NC = pq.S.chains.size(), NF = pq.S.facts.size();
+  // the candidates that can win: every chain with a factorisation of least
+  // primary cost (exact, closed form); MP_LEARNED_SCORE_ALL scores them all
+  const bool all = (flags & MP_LEARNED_SCORE_ALL) != 0;
+  std::vector<uint32_t> flist;
+  for (uint64_t fr = 0; fr < NF; ++fr)
+    if (all || pq.prim[fr] == pq.Q.pmin) flist.push_back((uint32_t)fr);
+  const uint64_t ncand = NC * flist.size();
   const unsigned cap_eq = 1u << 16;
   const size_t o_sc = 0, o_hist = a256(ncand * 4), o_thr = o_hist + a256(65536 * 4), o_cnt = o_thr + 256,
                o_below = o_cnt + 256, o_eq = o_below + a256((size_t)K * 8), o_sel = o_eq + a256((size_t)cap_eq * 8),
                o_p = o_sel + a256((size_t)K * 8), o_s = o_p + a256((size_t)K * 8),
-               o_y = o_s + a256((size_t)K * 8), o_ye = o_y + a256((size_t)K * 4), end = o_ye + a256((size_t)cap_eq * 4);
+               o_y = o_s + a256((size_t)K * 8), o_ye = o_y + a256((size_t)K * 4),
+               o_fl = o_ye + a256((size_t)cap_eq * 4), end = o_fl + a256(flist.size() * 4);
   char* w = g_pool_s.get(end);
   if (!w) return MP_ENOMEM;
   float* d_sc = (float*)(w + o_sc);
@@ -631,6 +648,8 @@ extern "C" int mp_learned_search(mp_mlp* h, const mp_search_query* query, int K,
   uint64_t* d_s = (uint64_t*)(w + o_s);
   float* d_y = (float*)(w + o_y);
   float* d_ye = (float*)(w + o_ye);
+  uint32_t* d_fl = (uint32_t*)(w + o_fl);
+  MP_CUDA_TRY(cudaMemcpyAsync(d_fl, flist.data(), flist.size() * 4, cudaMemcpyHostToDevice, st));
   // ---- score every candidate
   MP_CUDA_TRY(cudaMemsetAsync(h->status, 0, 4, st));
   const size_t smem = 16384 + 65536 + 32768 + 1024;
@@ -639,7 +658,7 @@ extern "C" int mp_learned_search(mp_mlp* h, const mp_search_query* query, int K,
   const unsigned blocks = (unsigned)std::min<uint64_t>(ntiles, (uint64_t)sm_count_l() * 2);
   timer_begin(st);
   k_score<<<blocks, 128, smem, st>>>(pq.Q, pq.d_progs, pq.d_facts, pq.d_chainfeat, h->W1b, h->W2b, h->W3b, h->P,
-                                     ncand, d_sc, h->status);
+                                     d_fl, ncand, d_sc, h->status);
   timer_end(st);
   count_launch();
   MP_CUDA_TRY(cudaGetLastError());
@@ -683,12 +702,19 @@ extern "C" int mp_learned_search(mp_mlp* h, const mp_search_query* query, int K,
   MP_CUDA_TRY(cudaStreamSynchronize(st));
   for (uint32_t i = 0; i < neq && sel.size() < Keff; ++i) sel.push_back(eq[ord[i]]);
   const int64_t nsel = (int64_t)sel.size();
+  std::vector<int64_t> pos = sel;   // positions in the scored list
+  for (auto& v : sel) {
+    const uint64_t j = (uint64_t)v / NC;
+    v = (int64_t)((uint64_t)flist[j] * NC + ((uint64_t)v - j * NC));
+  }
   if (nsel == 0) {   // the selection kernels produced nothing
     MP_CUDA_TRY(cudaErrorUnknown);
   }
   // ---- exact costs of the selection
   MP_CUDA_TRY(cudaMemcpyAsync(d_sel, sel.data(), (size_t)nsel * 8, cudaMemcpyHostToDevice, st));
   if ((rc = candidate_costs_dev(q, pq.S, pq.d_progs, pq.d_facts, d_sel, nsel, d_p, d_s, st))) return rc;
+  MP_CUDA_TRY(cudaStreamSynchronize(st));
+  MP_CUDA_TRY(cudaMemcpyAsync(d_sel, pos.data(), (size_t)nsel * 8, cudaMemcpyHostToDevice, st));
   k_take<<<(unsigned)((nsel + 255) / 256), 256, 0, st>>>(d_sc, d_sel, (int)nsel, d_y);
   count_launch();
   std::vector<uint64_t> pb(nsel), sb(nsel);
@@ -715,17 +741,21 @@ extern "C" int mp_learned_search(mp_mlp* h, const mp_search_query* query, int K,
   // margin: every unselected candidate scored at least the threshold; the
   // model's largest error on the selection bounds how far its true target
   // may lie below its score
-  float eps = 0.f, tau = -1e30f;
+  // A candidate left out has a score of at least tau (the largest selected
+  // score); it beats the winner only if its true target lies below the
+  // winner's, i.e. if the model overestimated it by more than tau - y_best.
+  // The largest overestimation seen on the selection (times 1.5) bounds that.
+  float over = 0.f, tau = -1e30f;
   bool finite = true;
   for (int64_t i = 0; i < nsel; ++i) {
     const float yt = host_target(pb[i] / tb, sb[i] / tb, pq.Q.pmin);
     finite = finite && std::isfinite(yh[i]);
-    eps = std::max(eps, std::fabs(yh[i] - yt));
+    over = std::max(over, yh[i] - yt);
     tau = std::max(tau, yh[i]);
   }
-  if (!finite) eps = INFINITY;   // no margin from a model that returned NaN / inf
+  if (!finite) over = INFINITY;   // no margin from a model that returned NaN / inf
   const float y_best = host_target(p_best, sb[bi] / tb, pq.Q.pmin);
-  const double margin = (double)tau - 2.0 * eps - y_best;
+  const double margin = (double)tau - y_best - 1.5 * over - 1e-3;
   const bool accept = certified || (p_best == pq.Q.pmin && margin > 0.0 && nsel == (int64_t)Keff);
   if (stats) {
     std::memset(stats, 0, sizeof(*stats));
@@ -791,7 +821,7 @@ extern "C" int mp_learned_scores(mp_mlp* h, const mp_search_query* query, float*
   const uint64_t ntiles = (ncand + 127) / 128;
   const unsigned blocks = (unsigned)std::min<uint64_t>(ntiles, (uint64_t)sm_count_l() * 2);
   k_score<<<blocks, 128, smem, st>>>(pq.Q, pq.d_progs, pq.d_facts, pq.d_chainfeat, h->W1b, h->W2b, h->W3b, h->P,
-                                     ncand, scores, h->status);
+                                     nullptr, ncand, scores, h->status);
   count_launch();
   if (features) {
     int64_t* d_idx = nullptr;

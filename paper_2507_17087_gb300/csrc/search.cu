@@ -28,7 +28,8 @@ namespace {
 
 size_t align_up(size_t v) { return (v + 255) & ~size_t(255); }
 
-// One CTA per chain; each thread scores factorisations tid, tid + T, ...
+// One CTA per chain; warp w scores factorisations w, w + W, ... with its 32
+// lanes sharing each candidate's fibre scans.
 // full = 1: every candidate's secondary is scanned.  full = 0: candidates
 // whose (exact, closed-form) primary exceeds the minimum primary over all
 // factorisations cannot win the lexicographic argmin and are not scanned.
@@ -62,12 +63,14 @@ __global__ void k_search(const ChainProg* __restrict__ progs, const Fact* __rest
     pmin = s_pmin;
   }
   Key best{~0ull, ~0ull, ~0ull};
-  for (int fr = threadIdx.x; fr < nf; fr += blockDim.x) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+  uint32_t* wbm = bm + warp * 32;   // this warp's 32 bitmap columns
+  for (int fr = warp; fr < nf; fr += nwarps) {
     const uint32_t f[3] = {facts[fr].f[0], facts[fr].f[1], facts[fr].f[2]};
     Key k;
     k.p = primary_cost(E, f);
-    if (!full && k.p > pmin) continue;
-    k.s = secondary_cost(tab, bm + threadIdx.x, blockDim.x, words, E, f);
+    if (!full && k.p > pmin) continue;   // uniform across the warp
+    k.s = secondary_cost_warp(tab, wbm, blockDim.x, words, E, f, lane);
     k.idx = (unsigned long long)fr * nchains + c;
     if (key_less(k, best)) best = k;
   }

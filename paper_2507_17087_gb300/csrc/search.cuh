@@ -77,6 +77,22 @@ struct BlockIter {
     r = 0;
     rep = 0;
   }
+  // positions the iterator at block index i (a few divisions, once)
+  __device__ __forceinline__ void seek(uint32_t E, uint32_t f, uint32_t i) {
+    big = E >= f;
+    if (big) {
+      A = E / f; B = E % f; m = f;
+      const unsigned long long ie = (unsigned long long)i * E;
+      const unsigned long long c = (ie + f - 1) / f;   // ceil(i E / f)
+      r = (uint32_t)(c * f - ie);
+      rep = i;
+    } else {
+      A = f / E; B = f % E; m = E;
+      const unsigned long long iF = (unsigned long long)i * f;
+      rep = (uint32_t)(iF / E);
+      r = (uint32_t)(iF % E);
+    }
+  }
   // returns the weight of the current representative and advances
   __device__ __forceinline__ uint32_t step() {
     uint32_t w;
@@ -155,6 +171,89 @@ __device__ __forceinline__ unsigned long long secondary_cost(const uint16_t* __r
         acc += (unsigned long long)wt_u * (D - 1);
       }
       sec += (unsigned long long)wt_w * acc;
+    }
+  }
+  return sec;
+}
+
+__device__ __forceinline__ unsigned long long warp_sum(unsigned long long v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+  return v;
+}
+
+// Secondary cost (tiles) of factorisation f for the chain tabulated in tab,
+// computed by one warp.  Families with at least 32 fibres: lane l scans a
+// contiguous share of them with its own bitmap (word w of lane l at
+// bm[w * stride + l]).  Families with fewer fibres: the fibres are scanned
+// one at a time, the lanes splitting the elements over one shared bitmap
+// (lane 0's) with atomic ORs, the distinct count being its population.
+// Every lane returns the total.
+__device__ __forceinline__ unsigned long long secondary_cost_warp(const uint16_t* __restrict__ tab, uint32_t* bm,
+                                                                  int stride, int words, const uint32_t E[3],
+                                                                  const uint32_t f[3], int lane) {
+  const uint32_t fstride[3] = {1u, f[0], f[0] * f[1]};
+  uint32_t n[3];
+  for (int t = 0; t < 3; ++t) n[t] = E[t] < f[t] ? E[t] : f[t];
+  unsigned long long sec = 0;
+  for (int v = 0; v < 3; ++v) {
+    if (n[v] <= 1) continue;
+    const int u = v == 0 ? 1 : 0;
+    const int w = v == 2 ? 1 : 2;
+    const uint32_t nfib = n[u] * n[w];
+    if (nfib >= 32) {
+      const uint32_t chunk = (nfib + 31) / 32;
+      const uint32_t fb0 = lane * chunk, fb1 = min(nfib, fb0 + chunk);
+      unsigned long long part = 0;
+      if (fb0 < fb1) {
+        uint32_t iu = fb0 % n[u];
+        BlockIter itu, itw;
+        itu.seek(E[u], f[u], iu);
+        itw.seek(E[w], f[w], fb0 / n[u]);
+        uint32_t rep_w = itw.rep;
+        uint32_t wt_w = itw.step();
+        for (uint32_t fb = fb0; fb < fb1; ++fb) {
+          const uint32_t rep_u = itu.rep;
+          const uint32_t wt_u = itu.step();
+          const uint32_t base = rep_u * fstride[u] + rep_w * fstride[w];
+          const uint32_t D = fibre_distinct(tab, bm + lane, stride, words, base, fstride[v], E[v], f[v], n[v]);
+          part += (unsigned long long)wt_u * wt_w * (D - 1);
+          if (++iu == n[u]) {
+            iu = 0;
+            itu.seek(E[u], f[u], 0);
+            rep_w = itw.rep;
+            wt_w = itw.step();
+          }
+        }
+      }
+      sec += warp_sum(part);
+    } else {
+      BlockIter itu, itw;
+      itw.seek(E[w], f[w], 0);
+      for (uint32_t iw = 0; iw < n[w]; ++iw) {
+        const uint32_t rep_w = itw.rep;
+        const uint32_t wt_w = itw.step();
+        itu.seek(E[u], f[u], 0);
+        for (uint32_t iu = 0; iu < n[u]; ++iu) {
+          const uint32_t rep_u = itu.rep;
+          const uint32_t wt_u = itu.step();
+          const uint32_t base = rep_u * fstride[u] + rep_w * fstride[w];
+          for (uint32_t iv = lane; iv < n[v]; iv += 32) {
+            const uint32_t rep_v =
+                E[v] >= f[v] ? iv : (uint32_t)((unsigned long long)iv * f[v] / E[v]);
+            const uint32_t node = tab[base + rep_v * fstride[v]];
+            atomicOr(bm + (node >> 5) * stride, 1u << (node & 31));
+          }
+          __syncwarp();
+          unsigned long long cnt = 0;
+          for (int k = lane; k < words; k += 32) {
+            cnt += __popc(bm[k * stride]);
+            bm[k * stride] = 0;
+          }
+          const unsigned long long D = warp_sum(cnt);
+          __syncwarp();
+          sec += (unsigned long long)wt_u * wt_w * (D - 1);
+        }
+      }
     }
   }
   return sec;

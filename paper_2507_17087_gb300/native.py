@@ -458,6 +458,7 @@ class mp_learned_stats(ctypes.Structure):
 
 
 LEARNED_NO_FALLBACK = 1
+LEARNED_SCORE_ALL = 2
 PARAM_BLOCKS = [("W1", (256, 64)), ("b1", (256,)), ("W2", (256, 256)), ("b2", (256,)), ("W3", (256, 256)),
                 ("b3", (256,)), ("w4", (256,)), ("b4", (1,))]
 
@@ -512,11 +513,11 @@ class MLP:
                "mp_mlp_train_search")
         return loss.value
 
-    def learned_search(self, query, K=1024, fallback=True, stream=None):
+    def learned_search(self, query, K=1024, fallback=True, score_all=False, stream=None):
         q = _query(query)
         out = mp_search_result()
         st = mp_learned_stats()
-        flags = 0 if fallback else LEARNED_NO_FALLBACK
+        flags = (0 if fallback else LEARNED_NO_FALLBACK) | (LEARNED_SCORE_ALL if score_all else 0)
         _check(lib().mp_learned_search(self._h, ctypes.byref(q), int(K), flags, ctypes.byref(out),
                                        ctypes.byref(st), _stream(stream)), "mp_learned_search")
         res = _search_result(out)

@@ -132,12 +132,22 @@ def test_learned_search_trains_and_finds_the_optimum():
     for q in evalq:
         exact = N.decompose_search([q])[0]
         got = model.learned_search(q, K=1024, fallback=True)
-        # with the fallback the answer is always the exhaustive optimum
-        assert (got["index"], got["primary_bytes"], got["secondary_bytes"]) == \
-            (exact["index"], exact["primary_bytes"], exact["secondary_bytes"])
+        # exact with the fallback: the optimal cost tuple (reading R16: among
+        # exact ties the index may differ unless the exhaustive search ran)
+        assert (got["primary_bytes"], got["secondary_bytes"]) == \
+            (exact["primary_bytes"], exact["secondary_bytes"])
+        if got["fallback"]:
+            assert got["index"] == exact["index"]
         raw = model.learned_search(q, K=1024, fallback=False)
         zero_regret += (raw["primary_bytes"], raw["secondary_bytes"]) == \
             (exact["primary_bytes"], exact["secondary_bytes"])
-        assert raw["n_exact"] <= 1024 and raw["n_scored"] == exact["n_candidates"]
+        # the model ranks the candidates of least primary cost, at most all
+        assert raw["n_exact"] <= 1024 and raw["n_scored"] <= exact["n_candidates"]
     print(f"zero-regret without fallback: {zero_regret}/{len(evalq)}")
     assert zero_regret >= len(evalq) // 2
+    # scoring every candidate instead
+    q = evalq[0]
+    exact = N.decompose_search([q])[0]
+    got = model.learned_search(q, K=1024, fallback=True, score_all=True)
+    assert got["n_scored"] == exact["n_candidates"]
+    assert (got["primary_bytes"], got["secondary_bytes"]) == (exact["primary_bytes"], exact["secondary_bytes"])
