@@ -34,10 +34,10 @@ from paper_2507_17087_gb300 import workloads as W  # noqa: E402
 METRIC = "points mapped/s"
 UNIT = "points/s"
 VARIANTS = ("block", "cyclic", "block_cyclic")
-# DRAM bytes (read + write) of one id-writer launch from the ncu capture
-# summarised in profiles/k_ids_large_1024x1024x512.md (None until captured
-# for the current kernel).
-K_IDS_TRAFFIC_BYTES = None
+# DRAM bytes (read + write) of one full-size id-writer launch from the ncu
+# capture summarised in profiles/k_ids_large_1024x1024x512.md (set to None
+# when the kernel changes, until it is captured again).
+K_IDS_TRAFFIC_BYTES = 2.09e9 + 4.224e4
 
 
 def parse():
@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the search / batched / learned measurements")
+    ap.add_argument("--profile-case", choices=sorted(PROFILE_CASES),
+                    help="run one small case for a profiler capture and exit (no JSON line)")
     return ap.parse_args()
 
 
@@ -273,6 +275,59 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def profile_case_ids(N, torch):
+    """256 x 1024 x 512 points (512 MiB of ids, larger than L2), the block
+    variant's chain, mapped four times."""
+    cfg = W.large_config("block")
+    L = (256, 1024, 512)
+    chain = N.chain_from_draws(*cfg["machine"], cfg["draws"])
+    ids = torch.empty(math.prod(L), dtype=torch.int32, device="cuda")
+    for _ in range(4):
+        N.map_points(L, cfg["machine"], chain, cfg["dist"], ids=ids)
+
+
+def _search_query_3600():
+    return [q for q in W.search_queries(16) if q["machine"][0] * q["machine"][1] == 3600][0]
+
+
+def profile_case_search(N, torch):
+    """The exhaustive search (every candidate's secondary scanned) of the first
+    P = 3600 query of the search workload, twice."""
+    q = _search_query_3600()
+    for _ in range(2):
+        N.decompose_search([q], full=True)
+
+
+def profile_case_score(N, torch):
+    """Fused scoring of every candidate of the same query (3.8 M candidates)
+    by a briefly trained model, twice."""
+    m = N.MLP(seed=11)
+    m.train_search(W.search_training_queries(16), samples_per_query=1024, epochs=1, batch=1024, lr=1e-3, seed=3)
+    q = _search_query_3600()
+    for _ in range(2):
+        m.learned_search(q, K=1024, fallback=False, score_all=True)
+    m.close()
+
+
+def profile_case_batched(N, torch):
+    """The first 1000 queries of the batched workload in one graph replay,
+    three times."""
+    qs = W.batched_queries(1000)
+    b = N.Batch([(q["L"], q["machine"], N.chain_from_draws(*q["machine"], q["draws"]), q["dist"], q["face"])
+                 for q in qs])
+    info = b.info()
+    ids = torch.empty(int(info["total_ids"]), dtype=torch.int32, device="cuda")
+    hist = torch.empty(int(info["total_procs"]), dtype=torch.int64, device="cuda")
+    for _ in range(3):
+        b.run(ids=ids, hist=hist)
+    torch.cuda.synchronize()
+    b.close()
+
+
+PROFILE_CASES = {"ids-small": profile_case_ids, "search": profile_case_search, "score": profile_case_score,
+                 "batched": profile_case_batched}
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -292,6 +347,11 @@ def main():
         raise SystemExit("bench.py needs a CUDA GPU (the engine has no CPU fallback)")
     B.build()
     torch.cuda.set_device(local)
+    if args.profile_case:
+        PROFILE_CASES[args.profile_case](N, torch)
+        torch.cuda.synchronize()
+        print("ok", args.profile_case, flush=True)
+        return
     dist = None
     if world > 1:
         import torch.distributed as dist

@@ -19,7 +19,9 @@
  *    engine looks the pointer up with cudaPointerGetAttributes.  With device
  *    buffers the call is asynchronous on `stream` (a cudaStream_t, NULL = the
  *    legacy default stream); with any host output buffer the call copies the
- *    result back and synchronises `stream` before returning.
+ *    result back (a page-locked id array is written by the id kernel directly
+ *    through its device alias; MAPPLE_PINNED_DIRECT=0 stages it instead) and
+ *    synchronises `stream` before returning.
  *  - The engine keeps a per-device workspace (tables, staging) that grows on
  *    demand and is reused by later calls; it is freed at process exit.  Calls
  *    that run concurrently on different streams of one device must be

@@ -40,6 +40,7 @@ struct QDesc : MapCore {
   int32_t mode;         // IdsMode
   uint64_t face[4];
 };
+static_assert(sizeof(QDesc) % 16 == 0, "QDesc is copied in 16-byte words");
 
 struct Tile {
   uint32_t q;
@@ -129,6 +130,10 @@ __global__ void __launch_bounds__(kThreads) k_b_ids(const QDesc* __restrict__ qd
   uint32_t* Ts = smem;
   uint32_t* Cs = smem + smem_T;
   __shared__ uint32_t s_tile;
+  // the current query's descriptor, staged in shared memory: the hot loop
+  // reads its fields from there instead of re-loading global memory after
+  // every store
+  __shared__ __align__(16) QDesc sQ;
   uint32_t cur_q = 0xFFFFFFFFu;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   while (true) {
@@ -137,8 +142,12 @@ __global__ void __launch_bounds__(kThreads) k_b_ids(const QDesc* __restrict__ qd
     const uint32_t tile = s_tile;
     if (tile >= ntiles) break;
     const Tile tl = tiles[tile];
-    const QDesc& Q = qd[tl.q];
+    const QDesc& Q = sQ;
     if (tl.q != cur_q) {
+      const uint4* src = reinterpret_cast<const uint4*>(qd + tl.q);
+      uint4* dst = reinterpret_cast<uint4*>(&sQ);
+      for (uint32_t i = threadIdx.x; i < sizeof(QDesc) / 16; i += blockDim.x) dst[i] = __ldg(src + i);
+      __syncthreads();
       for (uint32_t i = threadIdx.x; i < Q.P; i += blockDim.x) Ts[i] = __ldg(Tpool + Q.p_off + i);
       if (Q.mode == M_FAST_SMEM) {
         const int last = Q.k - 1;

@@ -176,6 +176,9 @@ int gemm_tn(const void* A, const void* B, float* C, int M, int N, int K, int* st
 // Grow-only per-device workspace; returns nullptr on allocation failure.
 void* workspace(size_t bytes, int slot);
 bool is_device_pointer(const void* p);
+// Device address of a page-locked host allocation (written by kernels over
+// the host link directly), or nullptr (also when MAPPLE_PINNED_DIRECT=0).
+void* pinned_alias(const void* p);
 void count_launch(uint64_t n = 1);
 // One-shot events around the dominant kernel (mp_set_kernel_timer).
 void timer_begin(cudaStream_t st);

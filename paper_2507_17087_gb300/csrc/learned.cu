@@ -4,7 +4,7 @@
 //              closed-form primary cost relative to the best one, the
 //              chain's transforms, where the chain's node boundaries fall
 //              along each final dimension)
-//   k_score    fused tcgen05 inference: a persistent CTA of 128 threads
+//   k_score    fused tcgen05 inference: a persistent CTA of 256 threads
 //              writes the features of 128 candidates into shared memory,
 //              runs the three hidden layers (weights streamed from L2 in
 //              64-wide K chunks, accumulator in tensor memory, each thread's
@@ -188,14 +188,18 @@ __device__ __forceinline__ bool sync_mma(uint64_t* bar, uint32_t& phase) {
   return __syncthreads_and(ok) != 0;
 }
 
-// Accumulator row of this thread, columns [32c, 32c + 32): bias, ReLU, BF16
-// into the activation tile (K-major, four swizzle atoms of 64 columns).
+// Epilogue of a hidden layer.  Warp w reads accumulator rows 32 (w % 4) ..
+// + 31 (its TMEM lane quadrant) and columns 128 (w / 4) .. + 127: bias,
+// ReLU, BF16, into the activation tile (K-major, four swizzle atoms of 64
+// columns) as the next layer's A operand.
 __device__ __forceinline__ void epilogue_hidden(uint32_t tmem, const float* __restrict__ bias, uint8_t* H) {
-  const int warp = threadIdx.x >> 5, row = threadIdx.x;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int row = (warp & 3) * 32 + lane, half = warp >> 2;
 #pragma unroll 1
-  for (int c = 0; c < 8; ++c) {
+  for (int cc = 0; cc < 4; ++cc) {
+    const int c = half * 4 + cc;   // 32-column block
     uint32_t r[32];
-    tc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + c * 32, r);
+    tc::tmem_ld32(tmem + ((uint32_t)((warp & 3) * 32) << 16) + c * 32, r);
     tc::tmem_ld_wait();
     uint8_t* atom = H + (c >> 1) * 16384;
 #pragma unroll
@@ -203,8 +207,8 @@ __device__ __forceinline__ void epilogue_hidden(uint32_t tmem, const float* __re
       uint32_t w[4];
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
-        const float a = fmaxf(__uint_as_float(r[j + 2 * e]) + bias[c * 32 + j + 2 * e], 0.f);
-        const float b = fmaxf(__uint_as_float(r[j + 2 * e + 1]) + bias[c * 32 + j + 2 * e + 1], 0.f);
+        const float a = fmaxf(__uint_as_float(r[j + 2 * e]) + __ldg(bias + c * 32 + j + 2 * e), 0.f);
+        const float b = fmaxf(__uint_as_float(r[j + 2 * e + 1]) + __ldg(bias + c * 32 + j + 2 * e + 1), 0.f);
         __nv_bfloat162 h2 = __floats2bfloat162_rn(a, b);
         w[e] = *reinterpret_cast<uint32_t*>(&h2);
       }
@@ -213,7 +217,11 @@ __device__ __forceinline__ void epilogue_hidden(uint32_t tmem, const float* __re
   }
 }
 
-__global__ void __launch_bounds__(128) k_score(const __grid_constant__ QInfo Q, const ChainProg* __restrict__ progs,
+// 256 threads: threads 0..127 build the features of the tile's 128 rows;
+// all eight warps stage weights and share the epilogues (column halves).
+// Shared memory: H (four 16 KB atoms; atom 0 doubles as the layer-1 input X)
+// and one 32 KB weight chunk -- two CTAs per SM.
+__global__ void __launch_bounds__(256) k_score(const __grid_constant__ QInfo Q, const ChainProg* __restrict__ progs,
                                                const Fact* __restrict__ facts, const float* __restrict__ chainfeat,
                                                const bf16* __restrict__ W1b, const bf16* __restrict__ W2b,
                                                const bf16* __restrict__ W3b, const float* __restrict__ P,
@@ -222,19 +230,16 @@ __global__ void __launch_bounds__(128) k_score(const __grid_constant__ QInfo Q, 
   extern __shared__ uint8_t smem_raw[];
   __shared__ uint64_t bar;
   __shared__ uint32_t tmem_slot;
-  __shared__ float sb1[DH], sb2[DH], sb3[DH], sw4[DH];
+  __shared__ float s_part[128];
   uint8_t* base = smem_raw + ((1024 - (tc::smem_u32(smem_raw) & 1023)) & 1023);
-  uint8_t* Xs = base;                 // 128 x 64 (one atom, 16 KB)
-  uint8_t* Hs = base + 16384;         // 128 x 256 (four atoms, 64 KB)
-  uint8_t* Ws = base + 16384 + 65536; // 256 x 64 weight chunk (32 KB)
-  const int warp = threadIdx.x >> 5;
-  for (int i = threadIdx.x; i < DH; i += blockDim.x) {
-    sb1[i] = P[mlpk::O_B1 + i];
-    sb2[i] = P[mlpk::O_B2 + i];
-    sb3[i] = P[mlpk::O_B3 + i];
-    sw4[i] = P[mlpk::O_W4 + i];
-  }
-  const float b4 = P[mlpk::O_B4];
+  uint8_t* Hs = base;                 // 128 x 256 (four atoms, 64 KB); atom 0 = X during layer 1
+  uint8_t* Ws = base + 65536;         // 256 x 64 weight chunk (32 KB)
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const float* b1 = P + mlpk::O_B1;
+  const float* b2 = P + mlpk::O_B2;
+  const float* b3 = P + mlpk::O_B3;
+  const float* w4 = P + mlpk::O_W4;
+  const float b4 = __ldg(P + mlpk::O_B4);
   if (warp == 0) {
     tc::tmem_alloc(&tmem_slot, 256);
     tc::tmem_relinquish();
@@ -247,13 +252,13 @@ __global__ void __launch_bounds__(128) k_score(const __grid_constant__ QInfo Q, 
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = tmem_slot;
-  const uint32_t xa = tc::smem_u32(Xs), ha = tc::smem_u32(Hs), wa = tc::smem_u32(Ws);
+  const uint32_t ha = tc::smem_u32(Hs), wa = tc::smem_u32(Ws);
   uint32_t phase = 0;
   bool ok = true;
   const unsigned long long ntiles = (n + 127) / 128;
   for (unsigned long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
     const unsigned long long cand = tile * 128 + threadIdx.x;   // position in the scored list
-    {
+    if (threadIdx.x < 128) {
       float x[64];
       if (cand < n) {
         unsigned long long idx = cand;
@@ -273,7 +278,7 @@ __global__ void __launch_bounds__(128) k_score(const __grid_constant__ QInfo Q, 
           __nv_bfloat162 h2 = __floats2bfloat162_rn(x[j + 2 * e], x[j + 2 * e + 1]);
           w[e] = *reinterpret_cast<uint32_t*>(&h2);
         }
-        *reinterpret_cast<uint4*>(Xs + tc::sw128_offset(threadIdx.x, j)) = make_uint4(w[0], w[1], w[2], w[3]);
+        *reinterpret_cast<uint4*>(Hs + tc::sw128_offset(threadIdx.x, j)) = make_uint4(w[0], w[1], w[2], w[3]);
       }
     }
     // ---- layer 1: X (K = 64) x W1^T
@@ -283,10 +288,11 @@ __global__ void __launch_bounds__(128) k_score(const __grid_constant__ QInfo Q, 
     __syncthreads();
     if (threadIdx.x == 0) {
       tc::fence_after_sync();
-      mma_chunk(tmem, xa, wa, true, &bar);
+      mma_chunk(tmem, ha, wa, true, &bar);
     }
     ok = sync_mma(&bar, phase);
-    epilogue_hidden(tmem, sb1, Hs);
+    if (!ok) break;
+    epilogue_hidden(tmem, b1, Hs);
     // ---- layers 2 and 3: H (K = 256) x W^T in four chunks; the epilogue
     // overwrites H only after the layer's last MMA completed
     for (int layer = 0; layer < 2 && ok; ++layer) {
@@ -304,19 +310,25 @@ __global__ void __launch_bounds__(128) k_score(const __grid_constant__ QInfo Q, 
       }
       if (!ok) break;
       if (layer == 0) {
-        epilogue_hidden(tmem, sb2, Hs);
+        epilogue_hidden(tmem, b2, Hs);
       } else {
-        // output layer: score = relu(Z3 + b3) . w4 + b4 over this thread's row
-        float s = b4;
+        // output layer: relu(Z3 + b3) . w4 over this thread's row and column half
+        const int row = (warp & 3) * 32 + lane, half = warp >> 2;
+        float s = 0.f;
 #pragma unroll 1
-        for (int c = 0; c < 8; ++c) {
+        for (int cc = 0; cc < 4; ++cc) {
+          const int c = half * 4 + cc;
           uint32_t r[32];
-          tc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + c * 32, r);
+          tc::tmem_ld32(tmem + ((uint32_t)((warp & 3) * 32) << 16) + c * 32, r);
           tc::tmem_ld_wait();
 #pragma unroll
-          for (int j = 0; j < 32; ++j) s += fmaxf(__uint_as_float(r[j]) + sb3[c * 32 + j], 0.f) * sw4[c * 32 + j];
+          for (int j = 0; j < 32; ++j)
+            s += fmaxf(__uint_as_float(r[j]) + __ldg(b3 + c * 32 + j), 0.f) * __ldg(w4 + c * 32 + j);
         }
-        if (cand < n) scores[cand] = s;
+        if (half) s_part[row] = s;
+        __syncthreads();
+        const unsigned long long out = tile * 128 + row;
+        if (!half && out < n) scores[out] = s + s_part[row] + b4;
       }
     }
     tc::fence_before_sync();
@@ -652,12 +664,12 @@ extern "C" int mp_learned_search(mp_mlp* h, const mp_search_query* query, int K,
   MP_CUDA_TRY(cudaMemcpyAsync(d_fl, flist.data(), flist.size() * 4, cudaMemcpyHostToDevice, st));
   // ---- score every candidate
   MP_CUDA_TRY(cudaMemsetAsync(h->status, 0, 4, st));
-  const size_t smem = 16384 + 65536 + 32768 + 1024;
+  const size_t smem = 65536 + 32768 + 1024;
   MP_CUDA_TRY(cudaFuncSetAttribute(k_score, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const uint64_t ntiles = (ncand + 127) / 128;
   const unsigned blocks = (unsigned)std::min<uint64_t>(ntiles, (uint64_t)sm_count_l() * 2);
   timer_begin(st);
-  k_score<<<blocks, 128, smem, st>>>(pq.Q, pq.d_progs, pq.d_facts, pq.d_chainfeat, h->W1b, h->W2b, h->W3b, h->P,
+  k_score<<<blocks, 256, smem, st>>>(pq.Q, pq.d_progs, pq.d_facts, pq.d_chainfeat, h->W1b, h->W2b, h->W3b, h->P,
                                      d_fl, ncand, d_sc, h->status);
   timer_end(st);
   count_launch();
@@ -816,11 +828,11 @@ extern "C" int mp_learned_scores(mp_mlp* h, const mp_search_query* query, float*
   const uint64_t ncand = (uint64_t)pq.S.chains.size() * pq.S.facts.size();
   *n_out = (int64_t)ncand;
   MP_CUDA_TRY(cudaMemsetAsync(h->status, 0, 4, st));
-  const size_t smem = 16384 + 65536 + 32768 + 1024;
+  const size_t smem = 65536 + 32768 + 1024;
   MP_CUDA_TRY(cudaFuncSetAttribute(k_score, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const uint64_t ntiles = (ncand + 127) / 128;
   const unsigned blocks = (unsigned)std::min<uint64_t>(ntiles, (uint64_t)sm_count_l() * 2);
-  k_score<<<blocks, 128, smem, st>>>(pq.Q, pq.d_progs, pq.d_facts, pq.d_chainfeat, h->W1b, h->W2b, h->W3b, h->P,
+  k_score<<<blocks, 256, smem, st>>>(pq.Q, pq.d_progs, pq.d_facts, pq.d_chainfeat, h->W1b, h->W2b, h->W3b, h->P,
                                      nullptr, ncand, scores, h->status);
   count_launch();
   if (features) {

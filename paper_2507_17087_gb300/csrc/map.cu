@@ -312,13 +312,19 @@ struct Staged {
 };
 
 int stage(void* user, size_t bytes, size_t& cursor, std::vector<Staged>& list, char* base,
-          void** dev_out) {
+          void** dev_out, bool direct_ok) {
   if (!user) {
     *dev_out = nullptr;
     return MP_OK;
   }
   if (is_device_pointer(user)) {
     *dev_out = user;
+    return MP_OK;
+  }
+  void* alias = direct_ok ? pinned_alias(user) : nullptr;
+  if (alias) {   // page-locked id array: the id writer stores into it directly
+    *dev_out = alias;
+    list.push_back(Staged{user, nullptr, 0});
     return MP_OK;
   }
   *dev_out = base ? base + cursor : nullptr;
@@ -331,13 +337,13 @@ int run_with_staging(const Plan& pl, int32_t* ids, uint64_t* hist, uint64_t* rec
                      const uint64_t* face, cudaStream_t st) {
   const MapDesc& D = pl.desc;
   size_t need = 0;
-  auto host_bytes = [&](void* p, size_t b) {
-    if (p && !is_device_pointer(p)) need = align256(need + b);
+  auto host_bytes = [&](void* p, size_t b, bool direct_ok) {
+    if (p && !is_device_pointer(p) && !(direct_ok && pinned_alias(p))) need = align256(need + b);
   };
-  host_bytes(ids, D.npoints * 4);
-  host_bytes(hist, (size_t)D.P * 8);
-  host_bytes(recv, (size_t)D.P * 8);
-  host_bytes(total, 8);
+  host_bytes(ids, D.npoints * 4, true);
+  host_bytes(hist, (size_t)D.P * 8, false);
+  host_bytes(recv, (size_t)D.P * 8, false);
+  host_bytes(total, 8, false);
   char* base = nullptr;
   if (need) {
     base = (char*)workspace(need, 1);
@@ -348,14 +354,15 @@ int run_with_staging(const Plan& pl, int32_t* ids, uint64_t* hist, uint64_t* rec
   Want w;
   std::memset(&w, 0, sizeof(w));
   void* p;
-  stage(ids, D.npoints * 4, cur, list, base, &p); w.ids = (int32_t*)p;
-  stage(hist, (size_t)D.P * 8, cur, list, base, &p); w.hist = (uint64_t*)p;
-  stage(recv, (size_t)D.P * 8, cur, list, base, &p); w.recv = (uint64_t*)p;
-  stage(total, 8, cur, list, base, &p); w.total = (uint64_t*)p;
+  stage(ids, D.npoints * 4, cur, list, base, &p, true); w.ids = (int32_t*)p;
+  stage(hist, (size_t)D.P * 8, cur, list, base, &p, false); w.hist = (uint64_t*)p;
+  stage(recv, (size_t)D.P * 8, cur, list, base, &p, false); w.recv = (uint64_t*)p;
+  stage(total, 8, cur, list, base, &p, false); w.total = (uint64_t*)p;
   for (int t = 0; t < 4; ++t) w.face[t] = face && t < D.k ? face[t] : 0;
   int rc = run_launch(pl, w, st);
   if (rc) return rc;
-  for (auto& s : list) MP_CUDA_TRY(cudaMemcpyAsync(s.user, s.dev, s.bytes, cudaMemcpyDeviceToHost, st));
+  for (auto& s : list)
+    if (s.bytes) MP_CUDA_TRY(cudaMemcpyAsync(s.user, s.dev, s.bytes, cudaMemcpyDeviceToHost, st));
   if (!list.empty()) MP_CUDA_TRY(cudaStreamSynchronize(st));
   return MP_OK;
 }

@@ -2,6 +2,7 @@
 // launch accounting and status strings.
 #include <atomic>
 #include <cstdio>
+#include <cstdlib>
 #include <mutex>
 
 #include "engine.h"
@@ -62,6 +63,21 @@ bool is_device_pointer(const void* p) {
     return false;
   }
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+void* pinned_alias(const void* p) {
+  if (!p) return nullptr;
+  static const bool enabled = [] {
+    const char* e = std::getenv("MAPPLE_PINNED_DIRECT");
+    return !(e && e[0] == '0');
+  }();
+  if (!enabled) return nullptr;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
 }
 
 void count_launch(uint64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
