@@ -14,6 +14,10 @@ Chain vocabulary (plain tuples, shared with the tests):
   ("merge", p, q)            Fig. 4 merge(p, q), p < q
   ("swap", p, q)             Fig. 4 swap(p, q)
   ("decompose", i, (l1..lk)) Sec. 4.2 decompose(i, T)
+  ("decompose", i, (l1..lk), (h1..hk), (n, ...))
+                             the appendix's generalised objective: halo
+                             widths h and all-to-all transposes along the
+                             listed target dimensions
   ("balance_split", i, k)    reading R7: decompose(i, (1,)*k)
 Distributions: ("block",), ("cyclic",), ("block_cyclic", b), ("hier",),
 ("linear_cyclic",).
@@ -65,6 +69,9 @@ def _load():
                 "or_owner_of": (I, launch + [V, I64, V]),
                 "or_map_range": (I, launch + [V, I64, I64, I, V, V]),
                 "or_comm_volume": (I, launch + [V, V, V, I]),
+                "or_halo_elements": (I, launch + [V, V, V, V, I]),
+                "or_decompose_weighted": (I, [I64, I, V, V, I, V]),
+                "or_weighted_objective": (I, [I64, I, V, V, V, I, V]),
                 "or_halo_closed_form": (I, launch + [V, V]),
                 "or_factorisations": (I64, [I64, I, V, I64]),
                 "or_decompose": (I, [I64, I, V, V]),
@@ -88,9 +95,13 @@ def _p(a):
     return a.ctypes.data_as(ctypes.c_void_p)
 
 
+XF_W = 14
+
+
 def encode_chain(chain) -> np.ndarray:
-    """Chain tuples -> the oracle's 9-int64-per-op array [op,i,j,k,d,T0..T3]."""
-    out = np.zeros((max(len(chain), 1), 9), dtype=np.int64)
+    """Chain tuples -> the oracle's 14-int64-per-op array
+    [op, i, j, k, d, T0..T3, h0..h3, transpose_mask]."""
+    out = np.zeros((max(len(chain), 1), XF_W), dtype=np.int64)
     for o, op in enumerate(chain):
         name = op[0]
         out[o, 0] = OPS[name]
@@ -102,6 +113,10 @@ def encode_chain(chain) -> np.ndarray:
             T = tuple(op[2])
             out[o, 1], out[o, 3] = op[1], len(T)
             out[o, 5:5 + len(T)] = T
+            if len(op) > 3 and op[3] is not None:
+                out[o, 9:9 + len(T)] = tuple(op[3])
+            if len(op) > 4:
+                out[o, 13] = sum(1 << int(n) for n in op[4])
         elif name == "balance_split":
             out[o, 1], out[o, 3] = op[1], op[2]
         else:
@@ -201,6 +216,22 @@ class Launch:
             raise ValueError("invalid chain or distribution")
         return int(tot[0]), recv
 
+    def halo_elements(self, width, elem_bytes, want_recv=True, threads=1):
+        """Anisotropic halo volume in elements (reading R17): per element and
+        dimension, one copy to each other owner within the halo width."""
+        lib = _load()
+        wd = np.zeros(4, dtype=np.int64)
+        wd[: self.k] = width
+        eb = np.zeros(4, dtype=np.uint64)
+        eb[: self.k] = elem_bytes
+        tot = np.zeros(1, dtype=np.uint64)
+        recv = np.zeros(self.P, dtype=np.uint64) if want_recv else None
+        rc = lib.or_halo_elements(*self._args(), _p(wd), _p(eb), _p(tot),
+                                  _p(recv) if recv is not None else None, threads)
+        if rc:
+            raise ValueError("invalid chain, distribution or width")
+        return int(tot[0]), recv
+
     def halo_closed_form(self, face_bytes):
         lib = _load()
         fb = np.zeros(4, dtype=np.uint64)
@@ -220,13 +251,35 @@ def factorisations(d: int, k: int):
     return [tuple(int(v) for v in row) for row in out[:cnt]]
 
 
-def decompose(d: int, l):
+def decompose(d: int, l, h=None, transposes=()):
+    """Sec. 4.2 decompose argmin; with halo widths h and/or transposes, the
+    appendix's generalised objective."""
     lib = _load()
     l = np.asarray(l, dtype=np.int64)
     out = np.zeros(len(l), dtype=np.int64)
-    if lib.or_decompose(d, len(l), _p(l), _p(out)):
-        raise ValueError("bad decompose")
+    if h is None and not transposes:
+        if lib.or_decompose(d, len(l), _p(l), _p(out)):
+            raise ValueError("bad decompose")
+    else:
+        hw = np.asarray(h if h is not None else [1] * len(l), dtype=np.int64)
+        mask = sum(1 << int(n) for n in transposes)
+        rc = lib.or_decompose_weighted(d, len(l), _p(l), _p(hw), mask, _p(out))
+        if rc:
+            raise (OverflowError if rc == 2 else ValueError)("bad decompose")
     return tuple(int(v) for v in out)
+
+
+def weighted_objective(d: int, f, l, h, transposes=()):
+    """d * (V + sum_T V*_n) of one factorisation f (exact integer)."""
+    lib = _load()
+    f = np.asarray(f, dtype=np.int64)
+    l = np.asarray(l, dtype=np.int64)
+    hw = np.asarray(h, dtype=np.int64)
+    out = np.zeros(2, dtype=np.int64)
+    mask = sum(1 << int(n) for n in transposes)
+    if lib.or_weighted_objective(d, len(l), _p(f), _p(l), _p(hw), mask, _p(out)):
+        raise OverflowError("objective overflow")
+    return (int(out[0]) << 64) + (int(out[1]) & ((1 << 64) - 1))
 
 
 def greedy(d: int, k: int):
@@ -259,7 +312,7 @@ def chains(n: int, g: int, max_depth: int):
 def chain_from_draws(n: int, g: int, draws):
     lib = _load()
     draws = np.ascontiguousarray(draws, dtype=np.uint64)
-    out = np.zeros((max(len(draws), 1), 9), dtype=np.int64)
+    out = np.zeros((max(len(draws), 1), XF_W), dtype=np.int64)
     m = lib.or_chain_from_draws(n, g, len(draws), _p(draws), _p(out))
     res = []
     for o in range(m):

@@ -22,6 +22,11 @@
 //     Fig. 5 (reading R8);
 //   * halo volume: every directed nearest-neighbour face whose two endpoints
 //     have different owners (Sec. 4.2, Fig. 10 surface formula; reading R10);
+//     and the anisotropic element count with per-dimension halo widths (the
+//     appendix's generalised decompose; readings R10 and R17): every element
+//     once per other owner that needs it along each dimension;
+//   * decompose with halo widths and all-to-all transposes: the appendix's
+//     generalised objective V + sum_T V*_n, compared exactly;
 //   * the greedy grid heuristic of Algorithm A1;
 //   * the matmul moved-bytes cost of a candidate (reading R12) and the
 //     exhaustive lexicographic argmin over (factorisation, chain) candidates
@@ -48,13 +53,10 @@ enum { D_BLOCK = 0, D_CYCLIC = 1, D_BLOCK_CYCLIC = 2, D_HIER = 3, D_LINEAR_CYCLI
 
 const int MAXR = 32;   // processor-space rank bound inside the oracle
 
-// A user transform as the oracle receives it: 9 int64 per op
-//   [op, i, j, k, d, T0, T1, T2, T3]
-struct UserOp {
-  int op, i, j, k;
-  i64 d;
-  i64 T[4];
-};
+// A user transform as the oracle receives it: XF_W int64 per op
+//   [op, i, j, k, d, T0, T1, T2, T3, h0, h1, h2, h3, transpose_mask]
+// (h and the mask only matter to decompose; all-zero h means isotropic).
+const int XF_W = 14;
 
 // After decompose / balance_split are expanded only these remain.
 struct Prim {
@@ -154,15 +156,63 @@ i128 decompose_objective(const std::vector<i64>& f, const i64* l, int k) {
   return tot;
 }
 
+// Generalised objective of the appendix ("Generalization of the Decompose
+// Primitive"): with halo width h_n along target dimension n the volume is
+//   V = sum_n d_n h_n prod_{m != n} l_m,
+// and an all-to-all transpose along dimension n adds
+//   V*_n = (1 - 1/d_n) (prod_m w_m) d,   w_m = l_m / d_m,  d = prod_m d_m,
+// i.e. (1 - 1/d_n) prod_m l_m.  The total V + sum_{n in T} V*_n is compared
+// exactly after multiplying by the constant d:
+//   d V + prod_m l_m * sum_{n in T} (d_n - 1) (d / d_n).
+// Returns false when the value does not fit in 127 bits.
+bool weighted_objective(const std::vector<i64>& f, const i64* l, const i64* h, int tmask, int k, i64 d,
+                        i128& out) {
+  const i128 lim = ((i128)1) << 125;
+  i128 V = 0;
+  for (int n = 0; n < k; ++n) {
+    i128 term = (i128)f[n] * h[n];
+    for (int m = 0; m < k; ++m) {
+      if (m == n) continue;
+      if (term > lim / l[m]) return false;
+      term *= l[m];
+    }
+    V += term;
+    if (V > lim) return false;
+  }
+  if (V > lim / d) return false;
+  i128 tot = V * d;
+  i128 Lambda = 1;
+  for (int m = 0; m < k; ++m) {
+    if (Lambda > lim / l[m]) return false;
+    Lambda *= l[m];
+  }
+  for (int n = 0; n < k; ++n) {
+    if (!((tmask >> n) & 1)) continue;
+    const i128 c = (i128)(f[n] - 1) * (d / f[n]);
+    if (c != 0 && Lambda > lim / c) return false;
+    tot += Lambda * c;
+    if (tot > lim) return false;
+  }
+  out = tot;
+  return true;
+}
+
 // argmin over all factorisations; ties go to the lexicographically smallest
 // tuple (reading R5) -- the enumeration is lexicographic and only a strictly
-// smaller objective replaces the incumbent.
-std::vector<i64> decompose_factors(i64 d, int k, const i64* l) {
+// smaller objective replaces the incumbent.  h == nullptr and tmask == 0 is
+// the isotropic objective of Sec. 4.2.  Empty result: objective overflow.
+std::vector<i64> decompose_factors(i64 d, int k, const i64* l, const i64* h = nullptr, int tmask = 0) {
   auto all = factorisations(d, k);
   std::vector<i64> best;
   i128 bestv = 0;
   for (auto& f : all) {
-    i128 v = decompose_objective(f, l, k);
+    i128 v;
+    if (h == nullptr && tmask == 0) {
+      v = decompose_objective(f, l, k);
+    } else {
+      i64 ones[4] = {1, 1, 1, 1};
+      if (!weighted_objective(f, l, h ? h : ones, tmask, k, d, v)) return {};
+    }
     if (best.empty() || v < bestv) { best = f; bestv = v; }
   }
   return best;
@@ -222,11 +272,24 @@ bool push_swap(std::vector<Prim>& prims, Space& sp, int p, int q) {
 }
 
 // decompose(i, T) = k-1 splits split(i + n - 1, d_n), n = 1..k-1 (Sec. 4.2)
-bool push_decompose(std::vector<Prim>& prims, Space& sp, int i, int k, const i64* T) {
+bool push_decompose(std::vector<Prim>& prims, Space& sp, int i, int k, const i64* T,
+                    const i64* h = nullptr, int tmask = 0) {
   if (i < 0 || i >= sp.r || k < 1 || k > 4) return false;
   for (int m = 0; m < k; ++m)
     if (T[m] < 1) return false;
-  std::vector<i64> f = decompose_factors(sp.s[i], k, T);
+  // all-zero widths and no transposes: the isotropic objective
+  bool weighted = tmask != 0;
+  if (h)
+    for (int m = 0; m < k; ++m) {
+      if (h[m] < 0) return false;
+      if (h[m] != 0) weighted = true;
+    }
+  if (tmask < 0 || tmask >= (1 << k)) return false;
+  i64 hw[4] = {1, 1, 1, 1};
+  if (h && weighted)
+    for (int m = 0; m < k; ++m) hw[m] = h[m];
+  std::vector<i64> f = weighted ? decompose_factors(sp.s[i], k, T, hw, tmask) : decompose_factors(sp.s[i], k, T);
+  if ((int)f.size() != k) return false;
   for (int n = 1; n < k; ++n)
     if (!push_split(prims, sp, i + n - 1, f[n - 1])) return false;
   return true;
@@ -262,14 +325,14 @@ int build_plan(Plan& pl, const i64* L, int k, int n, int g, const i64* xf, int n
   sp.s[1] = g;
   pl.prims.clear();
   for (int o = 0; o < nxf; ++o) {
-    const i64* e = xf + 9 * o;
+    const i64* e = xf + XF_W * o;
     int op = (int)e[0], i = (int)e[1], j = (int)e[2], kk = (int)e[3];
     i64 d = e[4];
     bool ok = false;
     if (op == OP_SPLIT) ok = push_split(pl.prims, sp, i, d);
     else if (op == OP_MERGE) ok = push_merge(pl.prims, sp, i, j);
     else if (op == OP_SWAP) ok = push_swap(pl.prims, sp, i, j);
-    else if (op == OP_DECOMPOSE) ok = push_decompose(pl.prims, sp, i, kk, e + 5);
+    else if (op == OP_DECOMPOSE) ok = push_decompose(pl.prims, sp, i, kk, e + 5, e + 9, (int)e[13]);
     else if (op == OP_BALANCE_SPLIT) {
       // reading R7: balance_split(i, k) = decompose(i, (1, ..., 1))
       i64 ones[4] = {1, 1, 1, 1};
@@ -729,6 +792,60 @@ int or_comm_volume(const int64_t* L, int k, int n, int g, const int64_t* xf, int
   return 0;
 }
 
+// Halo volume in elements with per-dimension widths (the anisotropic halo
+// of the appendix's "Generalization of the Decompose Primitive"; readings
+// R10 and R17).  A processor p that owns a point x needs every point
+// y = x + delta e_t with 1 <= |delta| <= width[t] inside the launch; each
+// element y it does not own is received once per dimension t along which it
+// is needed, whichever of p's points need it:
+//   total = sum_y sum_t bytes[t] * |{ owner(y + delta e_t) : 1 <= |delta| <= w_t,
+//                                     in bounds } \ { owner(y) }|,
+// and recv[p] gets bytes[t] for each such (p, y, t).
+int or_halo_elements(const int64_t* L, int k, int n, int g, const int64_t* xf, int nxf, int dist,
+                     int b, const int64_t* width, const uint64_t* bytes, uint64_t* total, uint64_t* recv,
+                     int threads) {
+  Plan pl;
+  if (build_plan(pl, L, k, n, g, xf, nxf, dist, b)) return 1;
+  for (int t = 0; t < k; ++t)
+    if (width[t] < 0) return 1;
+  int T = threads < 1 ? 1 : threads;
+  std::vector<u64> tot(T, 0);
+  std::vector<std::vector<u64>> part(T, std::vector<u64>(recv ? pl.P : 0, 0));
+  parallel_for(pl.npoints, T, [&](i64 lo, i64 hi, int w) {
+    i64 y[4], z[4];
+    std::vector<i64> seen;
+    for (i64 lin = lo; lin < hi; ++lin) {
+      unravel(pl, lin, y);
+      const i64 me = owner_of_point(pl, y);
+      for (int t = 0; t < pl.k; ++t) {
+        seen.clear();
+        for (i64 delta = -width[t]; delta <= width[t]; ++delta) {
+          if (delta == 0) continue;
+          for (int u = 0; u < pl.k; ++u) z[u] = y[u];
+          z[t] += delta;
+          if (z[t] < 0 || z[t] >= pl.L[t]) continue;
+          const i64 p = owner_of_point(pl, z);
+          if (p == me) continue;
+          if (std::find(seen.begin(), seen.end(), p) == seen.end()) seen.push_back(p);
+        }
+        tot[w] += bytes[t] * (u64)seen.size();
+        if (recv)
+          for (i64 p : seen) part[w][p] += bytes[t];
+      }
+    }
+  });
+  u64 s = 0;
+  for (int w = 0; w < T; ++w) s += tot[w];
+  *total = s;
+  if (recv)
+    for (i64 p = 0; p < pl.P; ++p) {
+      u64 r = 0;
+      for (int w = 0; w < T; ++w) r += part[w][p];
+      recv[p] = r;
+    }
+  return 0;
+}
+
 // Closed-form halo volume (derived from the surface formula of Sec. 4.2,
 // Fig. 10, for the separable distributions): along dimension t the number of
 // positions x_t in [0, L_t - 1) whose two sides differ in the distributed
@@ -815,6 +932,30 @@ int or_decompose(int64_t d, int k, const int64_t* l, int64_t* out) {
   return 0;
 }
 
+// decompose with halo widths h (k values >= 1) and a transpose mask: the
+// generalised objective of the appendix.  Returns 2 on objective overflow.
+int or_decompose_weighted(int64_t d, int k, const int64_t* l, const int64_t* h, int tmask, int64_t* out) {
+  if (d < 1 || k < 1 || k > 4 || tmask < 0 || tmask >= (1 << k)) return 1;
+  for (int m = 0; m < k; ++m)
+    if (l[m] < 1 || h[m] < 0) return 1;
+  auto f = decompose_factors(d, k, l, h, tmask);
+  if ((int)f.size() != k) return 2;
+  for (int m = 0; m < k; ++m) out[m] = f[m];
+  return 0;
+}
+
+// The generalised objective of one factorisation as the pair (d V, Lambda *
+// sum_T (d_n - 1) d / d_n) in two int64 halves each (hi, lo) -- for tests.
+int or_weighted_objective(int64_t d, int k, const int64_t* f, const int64_t* l, const int64_t* h, int tmask,
+                          int64_t* out_hi_lo) {
+  std::vector<i64> fv(f, f + k);
+  i128 v;
+  if (!weighted_objective(fv, l, h, tmask, k, d, v)) return 2;
+  out_hi_lo[0] = (int64_t)(v >> 64);
+  out_hi_lo[1] = (int64_t)(uint64_t)v;
+  return 0;
+}
+
 // Algorithm A1: primes ascending; each goes to the currently smallest factor
 // (first index on ties, reading R15); the factors are sorted descending.
 int or_greedy(int64_t d, int k, int64_t* out) {
@@ -853,7 +994,7 @@ int64_t or_chains(int n, int g, int max_depth, int64_t* out, int64_t cap) {
 
 // A chain drawn from random numbers: at each step the op is
 // alphabet[draws[step] mod |alphabet|]; an empty alphabet ends the chain.
-// Output: 9-int64 user ops.  Returns the number of ops.
+// Output: XF_W-int64 user ops.  Returns the number of ops.
 int or_chain_from_draws(int n, int g, int depth, const uint64_t* draws, int64_t* xf_out) {
   Space sp;
   sp.r = 2; sp.s[0] = n; sp.s[1] = g;
@@ -864,8 +1005,8 @@ int or_chain_from_draws(int n, int g, int depth, const uint64_t* draws, int64_t*
     COp c = A[draws[step] % A.size()];
     std::vector<Prim> dummy;
     apply_cop(dummy, sp, c);
-    int64_t* e = xf_out + 9 * m;
-    for (int z = 0; z < 9; ++z) e[z] = 0;
+    int64_t* e = xf_out + XF_W * m;
+    for (int z = 0; z < XF_W; ++z) e[z] = 0;
     e[0] = c.op;
     e[1] = c.p;
     e[2] = c.op == OP_SPLIT ? 0 : c.q;

@@ -487,3 +487,161 @@ def test_secondary_depends_on_chain():
     f = (4, 4, 4)
     vals = {O.matmul_cost(M, N, K, (n, g), ch, f)[1] for ch in O.chains(n, g, 1)}
     assert len(vals) > 1
+
+
+# ------------------------------------------- anisotropic halo and transposes
+# The appendix's "Generalization of the Decompose Primitive": halo width h_n
+# along dimension n gives V = sum_n d_n h_n prod_{m != n} l_m, and an
+# all-to-all transpose along n adds V*_n = (1 - 1/d_n) (prod_m w_m) d.
+
+def _grid_chain(f):
+    """A chain whose final space is the grid f on Machine(1, P)."""
+    ch = [("merge", 0, 1)]
+    for t in range(len(f) - 1):
+        ch.append(("split", t, f[t]))
+    return ch
+
+
+@pytest.mark.parametrize("L,f,h", [((12, 18), (2, 3), (2, 3)), ((16, 16), (4, 2), (1, 4)),
+                                   ((8, 12, 6), (2, 3, 2), (2, 1, 3)), ((30,), (5,), (3,))])
+def test_halo_elements_match_the_appendix_volume(L, f, h):
+    # BLOCK, extents divisible by the grid, width <= block width: every
+    # interior cut moves h_n layers each way.  The appendix's V counts d_n
+    # cuts per dimension (the outer surface included, reading R11): the exact
+    # count is 2 V - 2 sum_n h_n prod_{m != n} l_m.
+    P = math.prod(f)
+    ln = O.Launch(L, (1, P), _grid_chain(f), ("block",))
+    assert ln.final_shape() == tuple(f)
+    tot, recv = ln.halo_elements(h, [1] * len(L))
+    V = sum(f[n] * h[n] * math.prod(L[m] for m in range(len(L)) if m != n) for n in range(len(L)))
+    outer = sum(h[n] * math.prod(L[m] for m in range(len(L)) if m != n) for n in range(len(L)))
+    assert tot == 2 * V - 2 * outer
+    assert int(recv.sum()) == tot
+
+
+@pytest.mark.parametrize("dist", [("block",), ("block_cyclic", 3)])
+def test_halo_elements_width_one_equals_faces_for_blocks(dist):
+    # reading R10: with width 1 the de-duplicated count and the directed-face
+    # count differ only where both neighbours of an element belong to one
+    # other owner; with runs of at least two points per owner along every
+    # dimension (block, block-cyclic with b >= 2) that cannot happen
+    for q in range(4):
+        cfg = W.scaled_launch((9, 14, 5), (2, 3), dist[0], 300 + q)
+        ch = O.chain_from_draws(*cfg["machine"], cfg["draws"])
+        ln = O.Launch(cfg["L"], cfg["machine"], ch, dist)
+        assert ln.halo_elements((1, 1, 1), (8, 8, 8))[0] == ln.comm_volume((8, 8, 8))[0]
+
+
+def test_halo_elements_width_one_cyclic_pairs():
+    # CYCLIC over 2 residues: an interior element's two neighbours share one
+    # owner, so it is sent once (the face count sends it twice)
+    ln = O.Launch((10,), (1, 2), [], ("cyclic",))
+    assert ln.halo_elements((1,), (1,))[0] == 10
+    assert ln.comm_volume((1,))[0] == 18
+
+
+def test_halo_elements_cyclic_closed_form():
+    # CYCLIC with s_t > 2 w_t: all 2 w_t neighbours of an element along t
+    # have distinct residues, none equal to its own, so the element goes to
+    # min(y, w) + min(L - 1 - y, w) receivers; summed over y: 2 L w - w^2 - w
+    for L, w in (((40, 33), (3, 2)), ((25, 50), (1, 5))):
+        ln = O.Launch(L, (16, 16), [], ("cyclic",))
+        s = ln.final_shape()
+        assert all(s[t] > 2 * w[t] for t in range(2)), s
+        tot, _ = ln.halo_elements(w, (1, 1), want_recv=False)
+        want = sum((2 * L[t] * w[t] - w[t] * w[t] - w[t]) * L[1 - t] for t in range(2))
+        assert tot == want
+
+
+def _brute_elements(ids, L, width, eb, P):
+    """Brute force from an id array: per element and dimension, the set of
+    other owners within the halo width."""
+    a = ids.reshape(L)
+    tot = 0
+    recv = np.zeros(P, dtype=np.int64)
+    for y in itertools.product(*(range(e) for e in L)):
+        me = a[y]
+        for t in range(len(L)):
+            owners = set()
+            for dlt in range(-width[t], width[t] + 1):
+                z = list(y)
+                z[t] += dlt
+                if dlt == 0 or not 0 <= z[t] < L[t]:
+                    continue
+                o = int(a[tuple(z)])
+                if o != me:
+                    owners.add(o)
+            tot += eb[t] * len(owners)
+            for o in owners:
+                recv[o] += eb[t]
+    return tot, recv
+
+
+@pytest.mark.parametrize("kind", ["block", "cyclic", "block_cyclic", "hier", "linear_cyclic"])
+def test_halo_elements_brute_force(kind):
+    for q in range(3):
+        L = ((7, 9), (5, 4, 6), (23,))[q]
+        width = ((2, 3), (1, 2, 3), (4,))[q]
+        eb = ((3, 5), (1, 2, 4), (7,))[q]
+        cfg = W.scaled_launch(L, (2, 3), kind, 400 + q)
+        ch = O.chain_from_draws(*cfg["machine"], cfg["draws"])
+        ln = O.Launch(L, cfg["machine"], ch, cfg["dist"])
+        ids, _ = ln.map_points()
+        tot, recv = ln.halo_elements(width, eb)
+        bt, br = _brute_elements(ids, L, width, eb, ln.P)
+        assert tot == bt
+        assert np.array_equal(recv.astype(np.int64), br)
+
+
+def test_weighted_decompose_reduces_to_sec42():
+    # unit widths and no transposes: the Sec. 4.2 objective (pinned above);
+    # any uniform width scales it and keeps the argmin
+    for d, l in ((16, (64, 64)), (512, (1024, 1024, 512)), (3600, (256, 1024, 4096)), (6, (12, 18))):
+        base = O.decompose(d, l)
+        assert O.decompose(d, l, h=(1,) * len(l)) == base
+        assert O.decompose(d, l, h=(7,) * len(l)) == base
+
+
+def test_weighted_decompose_worked_values():
+    # d = 16, l = (64, 64), f = (4, 4), h = (1, 1), transpose along dim 0:
+    # V = 4*1*64 + 4*1*64 = 512; V*_0 = (1 - 1/4) * (16 * 16) * 16 = 3072;
+    # the oracle compares d * (V + V*_0) = 16 * 3584 = 57344
+    assert O.weighted_objective(16, (4, 4), (64, 64), (1, 1), (0,)) == 57344
+    # (1, 16): V = 64 + 1024 = 1088, V*_0 = 0 -> 17408, the argmin
+    assert O.weighted_objective(16, (1, 16), (64, 64), (1, 1), (0,)) == 17408
+    assert O.decompose(16, (64, 64), transposes=(0,)) == (1, 16)
+    # a wide halo along dim 0 keeps it uncut; (2, 8) wins for h = (4, 1):
+    # V(2,8) = 4*2*64 + 8*64 = 1024 < V(4,4) = V(1,16) = 1280
+    assert O.decompose(16, (64, 64), h=(1000, 1)) == (1, 16)
+    assert O.decompose(16, (64, 64), h=(4, 1)) == (2, 8)
+
+
+def test_weighted_decompose_transposes_only():
+    # no halo and a transpose along every dimension: minimise
+    # sum_n (1 - 1/d_n), i.e. put all of d on one dimension; the
+    # lexicographically smallest such tuple is (1, ..., 1, d)
+    for d, k in ((12, 2), (64, 3), (360, 4)):
+        assert O.decompose(d, (5,) * k, h=(0,) * k, transposes=tuple(range(k))) == (1,) * (k - 1) + (d,)
+
+
+def test_weighted_decompose_minimises_the_exact_halo_count():
+    # for BLOCK grids that divide the extents the exact element count is an
+    # affine function of V with a d-independent offset, so the weighted
+    # argmin is the grid of least exact volume (first in lexicographic order)
+    for L, P, h in (((24, 36), 12, (3, 1)), ((16, 48), 16, (1, 2)), ((12, 12, 24), 8, (2, 1, 1))):
+        best = None
+        for f in O.factorisations(P, len(L)):
+            if any(L[t] % f[t] or L[t] // f[t] < h[t] for t in range(len(L))):
+                continue
+            v, _ = O.Launch(L, (1, P), _grid_chain(f), ("block",)).halo_elements(h, [1] * len(L), want_recv=False)
+            if best is None or v < best[0]:
+                best = (v, f)
+        assert O.decompose(P, L, h=h) == best[1]
+
+
+def test_weighted_decompose_in_a_chain():
+    # the chain form applies the generalised objective to the machine
+    ln = O.Launch((64, 64), (4, 4), [("merge", 0, 1), ("decompose", 0, (64, 64), (4, 1))], ("block",))
+    assert ln.final_shape() == (2, 8)
+    ln = O.Launch((64, 64), (4, 4), [("merge", 0, 1), ("decompose", 0, (64, 64), None, (0,))], ("block",))
+    assert ln.final_shape() == (1, 16)
