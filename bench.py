@@ -154,6 +154,7 @@ def extra_search(N, W, torch):
     N.decompose_search(qs[:1], full=True)   # warm
     out = []
     for q in qs:
+        N.decompose_search([q])   # untimed: builds the candidate space once
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         r = N.decompose_search([q], full=True)[0]
@@ -206,7 +207,9 @@ def extra_batched(N, W, torch, dev, runs=5):
 
 def extra_learned(N, W, torch, n_train=512, per_query=4096, epochs=8, n_eval=16):
     """Learned pruning: train on exact labels, then time-to-optimum against
-    the exhaustive search on held-out queries."""
+    the exhaustive search (every candidate) and against the exact search with
+    the primary bound, on held-out queries.  Every search runs once untimed
+    first (the candidate space of a machine is built once and cached)."""
     model = N.MLP(seed=11)
     t0 = time.perf_counter()
     loss = model.train_search(W.search_training_queries(n_train), samples_per_query=per_query, epochs=epochs,
@@ -215,24 +218,73 @@ def extra_learned(N, W, torch, n_train=512, per_query=4096, epochs=8, n_eval=16)
     t_train = time.perf_counter() - t0
     evalq = W.search_queries(n_eval, first_index=9000)
     zr = fb = 0
-    t_l = t_e = 0.0
+    t_l = t_e = t_b = t_r = 0.0
+    phases = {"prepare": 0.0, "model": 0.0, "exact": 0.0, "fallback": 0.0}
+    rounds = []
+
+    def timed(fn):
+        t = time.perf_counter()
+        r = fn()
+        return r, time.perf_counter() - t
+
     for q in evalq:
-        t0 = time.perf_counter()
-        full = N.decompose_search([q], full=True)[0]
-        t_e += time.perf_counter() - t0
-        t0 = time.perf_counter()
-        got = model.learned_search(q, K=1024, fallback=True)
-        t_l += time.perf_counter() - t0
+        N.decompose_search([q])   # untimed: builds the candidate space once
+        full, dt = timed(lambda: N.decompose_search([q], full=True)[0])
+        t_e += dt
+        bound, dt = timed(lambda: N.decompose_search([q])[0])
+        t_b += dt
+        assert bound["index"] == full["index"]
+        got, dt = timed(lambda: model.learned_search(q, K=1024, fallback=True))
+        t_l += dt
         assert (got["primary_bytes"], got["secondary_bytes"]) == (full["primary_bytes"], full["secondary_bytes"])
         fb += got["fallback"]
-        raw = model.learned_search(q, K=1024, fallback=False)
+        rounds.append(got["rounds"])
+        for k in phases:
+            phases[k] += got["ms"][k] / n_eval
+        raw, dt = timed(lambda: model.learned_search(q, K=1024, fallback=False))
+        t_r += dt
         zr += (raw["primary_bytes"], raw["secondary_bytes"]) == (full["primary_bytes"], full["secondary_bytes"])
     model.close()
     return {"metric": "pruned vs exhaustive time-to-optimum", "value": t_e / t_l, "unit": "x (speed-up)",
             "ms_learned_mean": 1e3 * t_l / n_eval, "ms_exhaustive_mean": 1e3 * t_e / n_eval,
-            "zero_regret_without_fallback": zr / n_eval, "exact_with_fallback": 1.0, "fallbacks": fb,
-            "eval_queries": n_eval, "train_labels": n_train * per_query, "train_epochs": epochs,
+            "ms_primary_bound_mean": 1e3 * t_b / n_eval, "vs_primary_bound": t_b / t_l,
+            "ms_learned_top_k_only_mean": 1e3 * t_r / n_eval, "learned_phase_ms_mean": phases,
+            "rounds": rounds, "zero_regret_without_fallback": zr / n_eval, "exact_with_fallback": 1.0,
+            "fallbacks": fb, "eval_queries": n_eval, "train_labels": n_train * per_query, "train_epochs": epochs,
             "train_seconds": t_train, "train_final_loss": loss, "K": 1024}
+
+
+def extra_volume_study(N, W, torch, dev):
+    """Decompose vs the greedy grid of Algorithm A1 on the paper's 180-config
+    stencil grid: exact halo volume (width 1, 8-byte elements) of the block
+    mapping on each grid, computed by the engine."""
+    cfgs = W.stencil_study_configs()
+    total = torch.empty(1, dtype=torch.int64, device=dev)
+    rows = []
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for c in cfgs:
+        G = c["gpus"]
+        g = N.greedy_grid(G, 2)
+        vols = []
+        for chain in ([("merge", 0, 1), ("split", 0, g[0])], [("merge", 0, 1), ("decompose", 0, c["L"])]):
+            N.halo_volume(c["L"], c["machine"], chain, ("block",), (1, 1), (8, 8), total=total)
+            vols.append(int(total.item()))
+        rows.append((c, vols[0], vols[1]))
+    secs = time.perf_counter() - t0
+
+    def gmean_improvement(sel):
+        ratios = [vg / vd for c, vg, vd in rows if sel(c) and vd > 0]
+        gm = math.exp(sum(math.log(v) for v in ratios) / len(ratios))
+        return 1.0 - 1.0 / gm
+
+    by = lambda key, vals: {str(v): round(100 * gmean_improvement(lambda c, v=v: c[key] == v), 2) for v in vals}
+    return {"metric": "halo volume reduction of decompose over the greedy grid",
+            "unit": "% (geometric mean over configurations)",
+            "value": round(100 * gmean_improvement(lambda c: True), 2),
+            "configs": len(rows), "max_pct": round(100 * max(1 - vd / vg for _, vg, vd in rows), 2),
+            "by_aspect_ratio": by("ratio", W.STUDY_RATIOS), "by_points_per_node": by("area", W.STUDY_AREAS),
+            "by_gpus": by("gpus", W.STUDY_GPUS), "seconds": secs}
 
 
 def max_over_ranks(value: float, dist, device) -> float:
@@ -309,10 +361,24 @@ def profile_case_score(N, torch):
     m.close()
 
 
+def profile_case_score_features(N, torch):
+    """The same scoring, then the feature generator alone over every
+    candidate (k_features_idx writes the 64 BF16 features of each), to split
+    the scorer's time between features and the layers."""
+    m = N.MLP(seed=11)
+    q = _search_query_3600()
+    n = 3787020
+    scores = torch.empty(n, dtype=torch.float32, device="cuda")
+    feats = torch.empty((n + 127) // 128 * 128, 64, dtype=torch.bfloat16, device="cuda")
+    for _ in range(2):
+        assert m.scores(q, scores, feats) == n
+    m.close()
+
+
 def profile_case_batched(N, torch):
-    """The first 1000 queries of the batched workload in one graph replay,
-    three times."""
-    qs = W.batched_queries(1000)
+    """200 queries of the batched workload's recipe with at most 2^22 points
+    each (about 7e7 points, 270 MB of ids) in one graph replay, three times."""
+    qs = W.batched_queries(200, max_points=1 << 22)
     b = N.Batch([(q["L"], q["machine"], N.chain_from_draws(*q["machine"], q["draws"]), q["dist"], q["face"])
                  for q in qs])
     info = b.info()
@@ -325,7 +391,7 @@ def profile_case_batched(N, torch):
 
 
 PROFILE_CASES = {"ids-small": profile_case_ids, "search": profile_case_search, "score": profile_case_score,
-                 "batched": profile_case_batched}
+                 "score-features": profile_case_score_features, "batched": profile_case_batched}
 
 
 def main():
@@ -470,7 +536,8 @@ def main():
         if not args.no_extras:
             for key, fn in (("search", lambda: extra_search(N, W, torch)),
                             ("batched", lambda: extra_batched(N, W, torch, dev)),
-                            ("learned", lambda: extra_learned(N, W, torch))):
+                            ("learned", lambda: extra_learned(N, W, torch)),
+                            ("volume_study", lambda: extra_volume_study(N, W, torch, dev))):
                 try:
                     line[key] = fn()
                 except Exception as exc:  # noqa: BLE001 - an extra must not lose the main line

@@ -55,6 +55,7 @@ enum mp_status {
 #define MP_MAX_PROC_RANK 24       /* processor-space rank after transforms     */
 #define MP_MAX_XFORMS 64          /* transforms in one chain                   */
 #define MP_MAX_PROCS (1 << 26)    /* P = nodes * procs_per_node                */
+#define MP_MAX_HALO_WIDTH 16      /* halo width per dimension (mp_halo_volume)  */
 
 /* ------------------------------------------------------------ data types */
 
@@ -85,13 +86,24 @@ enum mp_op {
 };
 
 typedef struct mp_xform {
-  int32_t op;     /* enum mp_op                                  */
-  int32_t i;      /* dimension (split/merge/swap/decompose)      */
-  int32_t j;      /* second dimension (merge/swap)               */
-  int32_t k;      /* number of factors (decompose/balance_split) */
-  int64_t d;      /* split factor                                */
-  int64_t T[4];   /* decompose target extents T[0..k)            */
+  int32_t op;         /* enum mp_op                                  */
+  int32_t i;          /* dimension (split/merge/swap/decompose)      */
+  int32_t j;          /* second dimension (merge/swap)               */
+  int32_t k;          /* number of factors (decompose/balance_split) */
+  int64_t d;          /* split factor                                */
+  int64_t T[4];       /* decompose target extents T[0..k)            */
+  int32_t h[4];       /* decompose: halo width along target dimension m
+                         (0 everywhere = isotropic, width 1)         */
+  int32_t transpose;  /* decompose: bit m set = all-to-all transpose
+                         along target dimension m                    */
+  int32_t reserved;
 } mp_xform;
+/* With halo widths h or transposes, decompose minimises the appendix's
+ * generalised volume ("Generalization of the Decompose Primitive"):
+ *   V = sum_m d_m h_m prod_{n != m} T_n  plus, for each transposed m,
+ *   V*_m = (1 - 1/d_m) prod_n T_n,
+ * compared exactly (MP_EOVERFLOW if s_i * V does not fit in 127 bits);
+ * ties go to the lexicographically smallest factor tuple. */
 
 /* Distributions: task point x -> index a of the final processor space. */
 enum mp_dist_kind {
@@ -144,6 +156,34 @@ int mp_map_points(const mp_space* space, const mp_machine* machine, const mp_xfo
 int mp_comm_volume(const mp_space* space, const mp_machine* machine, const mp_xform* chain,
                    int n_xf, const mp_dist* dist, const uint64_t* face_bytes, uint64_t* total,
                    uint64_t* recv, void* stream);
+
+/* halo_volume: a5 with per-dimension halo widths.  Two counts:
+ *  MP_HALO_FACES     the count of mp_comm_volume (width 1; width ignored):
+ *                    bytes[t] per directed face (x, x +- e_t) across owners,
+ *                    received by the owner of x;
+ *  MP_HALO_ELEMENTS  de-duplicated elements (the appendix's anisotropic
+ *                    halo, "Generalization of the Decompose Primitive"): a
+ *                    processor p that owns a point x needs every
+ *                    y = x + delta e_t, 1 <= |delta| <= width[t], inside the
+ *                    launch; each such y that p does not own moves bytes[t]
+ *                    to p once per dimension t, however many of p's points
+ *                    need it.  For block layouts that divide the extents this
+ *                    is sum_t 2 (d_t - 1) width[t] prod_{u != t} L_u.
+ *   width : halo width per task dimension, 0..MP_MAX_HALO_WIDTH
+ *   bytes : bytes per face / element along each task dimension
+ *   total : uint64[1] device or host, required (overwritten)
+ *   recv  : uint64[P] device or host, or NULL (bytes received per processor)
+ * Errors as mp_map_points; MP_EINVAL for a width outside [0, 16] or an
+ * unknown mode. */
+enum mp_halo_mode { MP_HALO_FACES = 0, MP_HALO_ELEMENTS = 1 };
+typedef struct mp_halo {
+  int32_t mode;       /* enum mp_halo_mode            */
+  int32_t width[4];   /* per task dimension           */
+  int32_t reserved;
+  uint64_t bytes[4];  /* per task dimension           */
+} mp_halo;
+int mp_halo_volume(const mp_space* space, const mp_machine* machine, const mp_xform* chain, int n_xf,
+                   const mp_dist* dist, const mp_halo* halo, uint64_t* total, uint64_t* recv, void* stream);
 
 /* map_points without any allocation.  The paper has no counterpart: this
  * entry point exists for callers that cannot allocate device memory -- code
@@ -317,19 +357,31 @@ int mp_mlp_train_search(mp_mlp* model, const mp_search_query* queries, int n_que
 /* Learned decompose search.  Only candidates whose factorisation attains
  * the least primary cost can win the lexicographic argmin (the primary is
  * exact and closed-form), so the model scores those (fused tcgen05
- * inference; MP_LEARNED_SCORE_ALL scores every candidate), the K best scores
- * are evaluated exactly, and their argmin is returned if it is certified
- * (every candidate that could beat it was among the K) or if the model's
- * largest overestimation on the K leaves a margin below the selection
- * threshold; otherwise the exhaustive search runs (unless
- * MP_LEARNED_NO_FALLBACK).  The returned costs are always exact.  K in
- * [1, 65536].  Synchronous. */
+ * inference; MP_LEARNED_SCORE_ALL scores every candidate) and the K best
+ * scores are evaluated exactly.  Their argmin is returned if it is certified
+ * (every candidate that could beat it was among those evaluated) or if the
+ * model's largest overestimation on them leaves a margin below the
+ * selection threshold.  Otherwise the selection grows 8-fold in score order
+ * (while it stays within 65536 candidates and a quarter of those scored) and
+ * the rule is applied again; if it still fails, the exhaustive search runs.  MP_LEARNED_NO_FALLBACK
+ * returns the argmin of the first K without growing or falling back.  The
+ * returned costs are always exact.  K in [1, 65536].  Synchronous.
+ * Phase times are host wall-clock milliseconds, each ending at a stream
+ * synchronisation. */
 typedef struct mp_learned_stats {
-  int64_t n_scored;   /* candidates scored by the model            */
-  int64_t n_exact;    /* candidates evaluated exactly              */
-  int32_t certified;  /* 1: exact certificate on the top-K         */
-  int32_t fallback;   /* 1: the exhaustive search ran              */
-  double margin;      /* threshold - winner target - 1.5 * max overestimation */
+  int64_t n_scored;         /* candidates scored by the model                     */
+  int64_t n_exact;          /* candidate evaluations, summed over the rounds      */
+  int64_t n_selected;       /* size of the last selection                         */
+  int32_t certified;        /* 1: exact certificate on the last selection         */
+  int32_t fallback;         /* 1: the exhaustive search ran                       */
+  int32_t rounds;           /* selections evaluated (1 + growth steps)            */
+  int32_t reserved;
+  double margin;            /* threshold - winner target - 1.5 * max overestimation */
+  double max_overestimate;  /* largest score - target on the last selection        */
+  double ms_prepare;        /* candidate space, chain features, primaries          */
+  double ms_model;          /* fused scoring and the score histogram               */
+  double ms_exact;          /* selections and their exact costs                    */
+  double ms_fallback;       /* the exhaustive search, when it ran                  */
 } mp_learned_stats;
 #define MP_LEARNED_NO_FALLBACK 1
 #define MP_LEARNED_SCORE_ALL 2
@@ -368,6 +420,13 @@ int mp_search_candidate(const mp_search_query* query, int64_t index, int64_t* f,
  * ordered factors and number of canonical chains of depth <= max_depth. */
 int mp_search_space(int32_t procs, int32_t procs_per_node, int32_t max_depth,
                     int64_t* n_factorisations, int64_t* n_chains);
+
+/* The processor grid of Algorithm A1 (the greedy baseline the paper compares
+ * decompose with, Sec. 4.3 and the appendix's "Baseline Greedy Algorithm"):
+ * the prime factors of d in ascending order, each multiplied into the
+ * currently smallest of k factors (first one on ties), then sorted in
+ * descending order.  Host only; MP_EINVAL for d < 1 or k outside [1, 4]. */
+int mp_greedy_grid(int64_t d, int32_t k, int64_t* out);
 
 /* Measurement hook: the next launch of the dominant per-point kernel
  * (the id writer of mp_map_points) records `start_event` just before it and

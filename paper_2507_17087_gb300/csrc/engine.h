@@ -138,6 +138,19 @@ struct MapDesc : MapCore {
   Prim prim[kMaxPrim];
 };
 
+// Halo of the element-count mode for linear-cyclic launches (F = lin mod P):
+// along dimension t the neighbours y + delta e_t, 1 <= |delta| <= w_t, of an
+// element have flat indices F + delta * stride_t (mod P).  off[t][i] are the
+// distinct non-zero offsets (delta stride_t mod P); pos / neg the smallest
+// delta > 0 with +delta (resp. -delta) giving that offset, 0 if none.
+constexpr int kMaxHaloWidth = MP_MAX_HALO_WIDTH;
+struct LcHalo {
+  uint32_t n[4];
+  uint32_t off[4][2 * kMaxHaloWidth];
+  uint8_t pos[4][2 * kMaxHaloWidth];
+  uint8_t neg[4][2 * kMaxHaloWidth];
+};
+
 // Host-side plan: the descriptor plus the expanded primitive list.
 struct HostPrim {
   int32_t op, p, q;
@@ -158,6 +171,10 @@ int build_plan(const mp_space* space, const mp_machine* machine, const mp_xform*
 // Ordered k-factorisations of d (lexicographic) and the decompose argmin.
 std::vector<std::vector<int64_t>> ordered_factorisations(int64_t d, int k);
 std::vector<int64_t> decompose_argmin(int64_t d, int k, const int64_t* l);
+// With halo widths h (k values) and a transpose mask: the generalised
+// objective; returns MP_EOVERFLOW when it does not fit in 127 bits.
+int decompose_argmin_weighted(int64_t d, int k, const int64_t* l, const int64_t* h, int tmask,
+                              std::vector<int64_t>& out);
 
 // Canonical transform alphabet (split / merge / swap) of a shape.
 struct CanonOp {

@@ -152,12 +152,77 @@ __device__ __forceinline__ void dim_counts(const MapCore& D, int t, uint32_t j, 
   }
 }
 
+// Element-count halo along one dimension (readings R10, R17): the sub-index
+// j occupies runs of positions (first run starts at a, last run ends at e,
+// nq runs of `size` positions in all, consecutive runs `gap` apart); the
+// positions outside them within distance w of one are
+// |dilate(runs, w) \ runs|, clipped to [0, L).  Runs further apart than 2w
+// dilate separately; otherwise the dilation is one interval.
+__device__ __forceinline__ uint64_t run_dilation(uint64_t a, uint64_t e, uint64_t nq, uint64_t size,
+                                                 uint64_t gap, uint64_t L, uint64_t w) {
+  if (nq == 0 || w == 0) return 0;
+  if (nq == 1 || 2 * w >= gap) {
+    const uint64_t lo = a > w ? a - w : 0;
+    const uint64_t hi = L - e > w ? e + w : L;
+    return hi - lo - size;
+  }
+  const uint64_t cut_lo = w - (a < w ? a : w), cut_hi = w - (L - e < w ? L - e : w);
+  return 2 * w * nq - cut_lo - cut_hi;
+}
+
+// Positions y of task dimension t outside sub-index j's positions and within
+// distance w of one of them: the elements a processor with sub-index j along
+// t receives per point of the other dimensions.
+__device__ __forceinline__ uint64_t dim_elems(const MapCore& D, int t, uint32_t j, uint64_t w) {
+  const Comp& c0 = D.comp[t][0];
+  const uint64_t L = D.L[t];
+  const uint32_t alpha = j % c0.s;
+  if (D.ncomp[t] == 1) {
+    if (c0.kind == C_BLOCK) {
+      const uint64_t lo = ceil_div((uint64_t)alpha * L, c0.s);
+      const uint64_t hi = ceil_div((uint64_t)(alpha + 1) * L, c0.s);
+      return run_dilation(lo, hi, hi > lo ? 1 : 0, hi - lo, 0, L, w);
+    }
+    if (c0.kind == C_CYCLIC) {
+      const uint64_t nq = count_residue(L, alpha, c0.s);
+      if (!nq) return 0;
+      return run_dilation(alpha, alpha + (nq - 1) * c0.s + 1, nq, nq, c0.s - 1, L, w);
+    }
+    const uint64_t b = c0.b;
+    const uint64_t Q = ceil_div(L, b);
+    const uint64_t nq = count_residue(Q, alpha, c0.s);
+    if (!nq) return 0;
+    const uint64_t qlast = alpha + (nq - 1) * c0.s;
+    const uint64_t e = qlast * b + b < L ? qlast * b + b : L;
+    const uint64_t size = nq * b - (qlast * b + b - e);
+    return run_dilation((uint64_t)alpha * b, e, nq, size, (uint64_t)(c0.s - 1) * b, L, w);
+  }
+  // hierarchical: upper block alpha, lower residue beta (mod s_l) inside it
+  const Comp& c1 = D.comp[t][1];
+  const uint32_t beta = j / c0.s;
+  const uint64_t sl = c1.s;
+  const uint64_t lo = ceil_div((uint64_t)alpha * L, c0.s);
+  const uint64_t hi = ceil_div((uint64_t)(alpha + 1) * L, c0.s);
+  const uint64_t size = count_residue(hi, beta, sl) - count_residue(lo, beta, sl);
+  if (!size) return 0;
+  const uint64_t a = lo + (beta + sl - lo % sl) % sl;
+  return run_dilation(a, a + (size - 1) * sl + 1, size, size, sl - 1, L, w);
+}
+
+// Points lin in [0, N) with lin = c (mod P).
+__device__ __forceinline__ uint64_t lc_count(const MapCore& D, uint32_t c) {
+  uint64_t q, rem;
+  divmod64(D.npoints, D.divP64, q, rem);
+  return q + (c < rem ? 1 : 0);
+}
+
 // hist and received bytes of flat final index F from the per-dimension
 // counts (or, for linear-cyclic, from the closed form and the slab deficit).
+// lh != nullptr selects the element-count halo for linear-cyclic launches.
 __device__ __forceinline__ void reduce_F(const MapCore& D, const uint64_t* __restrict__ H,
                                          const uint64_t* __restrict__ X, const uint64_t* __restrict__ deficit,
                                          const uint64_t face[4], bool want_recv, uint32_t F, uint64_t& h_F,
-                                         uint64_t& r_F) {
+                                         uint64_t& r_F, const LcHalo* lh = nullptr) {
   r_F = 0;
   if (!D.lc) {
     uint32_t j[4] = {0, 0, 0, 0};
@@ -189,7 +254,17 @@ __device__ __forceinline__ void reduce_F(const MapCore& D, const uint64_t* __res
     uint64_t q, rem;
     divmod64(D.npoints, D.divP64, q, rem);
     h_F = q + (F < rem ? 1 : 0);
-    if (want_recv) {
+    if (want_recv && lh) {
+      // every element within the halo width of one of F's points, once per
+      // distinct offset; the boundary slabs' missing neighbours come off
+      uint64_t r = 0;
+      for (int t = 0; t < D.k; ++t)
+        for (uint32_t i = 0; i < lh->n[t]; ++i) {
+          const uint32_t off = lh->off[t][i];
+          r += face[t] * lc_count(D, F >= off ? F - off : F + D.P - off);
+        }
+      r_F = r - deficit[F];
+    } else if (want_recv) {
       uint64_t G = 0;
       for (int t = 0; t < D.k; ++t)
         if (D.lc_stride_mod[t] != 0) G += 2 * face[t];
@@ -243,7 +318,87 @@ __device__ __noinline__ uint32_t row_base(const MapCore& D, const Tabs& tabs, co
   return base;
 }
 
-enum IdsMode : int { M_FAST_SMEM = 0, M_FAST_GLOBAL = 1, M_GENERAL = 2 };
+enum IdsMode : int { M_FAST_SMEM = 0, M_FAST_GLOBAL = 1, M_GENERAL = 2, M_FUSED = 3 };
+
+// base of a row when the dimensions m..k-1 are fused into one fast
+// dimension: sum_{t < m} c_t(x_t) of the row's slow coordinates.
+template <typename I>
+__device__ __noinline__ uint32_t row_base_m(const MapCore& D, const Tabs& tabs, const uint32_t* __restrict__ ctab,
+                                            I row, int m) {
+  uint32_t base = 0;
+  for (int t = m - 1; t >= 0; --t) {
+    I xt = row;
+    if (t > 0) {
+      uint32_t q32, r32;
+      divmod32((uint32_t)row, D.divL32[t], q32, r32);
+      row = (I)q32;
+      xt = (I)r32;
+    }
+    base += tabs.has[t] ? __ldg(ctab + tabs.off[t] + xt) : contrib(D, t, (uint64_t)xt);
+  }
+  return base;
+}
+
+// ids for the 4-point groups [gbeg, gend) of one warp when the trailing
+// dimensions m..k-1 (Lf points per row) are fused: Cf[x] (shared memory) is
+// the contribution of the fused coordinates of row offset x.  Groups inside
+// a row read four table entries (one 16-byte load when ALIGNED, i.e.
+// Lf % 4 == 0, where no group crosses a row end); a group that crosses a row
+// end walks its points.  32-bit indices (the batched launches stay below 2^31
+// points).
+template <bool ALIGNED>
+__device__ __forceinline__ void ids_range_fused(const MapCore& D, const Tabs& tabs, const uint32_t* __restrict__ T,
+                                                const uint32_t* __restrict__ Cf, const uint32_t* __restrict__ ctab,
+                                                int m, uint32_t Lf, Div32 divLf, uint32_t gbeg, uint32_t gend,
+                                                int lane, int vec_ok, int32_t* __restrict__ ids) {
+  const uint32_t N = (uint32_t)D.npoints;
+  uint32_t g = gbeg + (uint32_t)lane;
+  if (g >= gend) return;
+  uint32_t lin0 = g * 4;
+  uint32_t row, x;
+  divmod32(lin0, divLf, row, x);
+  uint32_t base = row_base_m<uint32_t>(D, tabs, ctab, row, m);
+  for (; g < gend; g += 32, lin0 += 128) {
+    const int cnt = N - lin0 < 4 ? (int)(N - lin0) : 4;
+    uint32_t v[4] = {0, 0, 0, 0};
+    if (ALIGNED) {
+      const uint4 c = *reinterpret_cast<const uint4*>(Cf + x);
+      v[0] = T[base + c.x]; v[1] = T[base + c.y]; v[2] = T[base + c.z]; v[3] = T[base + c.w];
+    } else if (x + 4 <= Lf) {
+#pragma unroll
+      for (int i = 0; i < 4; ++i) v[i] = T[base + Cf[x + i]];
+    } else {
+      uint32_t xi = x, ri = row, bi = base;
+      for (int i = 0; i < cnt; ++i) {
+        while (xi >= Lf) {
+          xi -= Lf;
+          ri += 1;
+          bi = row_base_m<uint32_t>(D, tabs, ctab, ri, m);
+        }
+        v[i] = T[bi + Cf[xi]];
+        ++xi;
+      }
+    }
+    if (cnt == 4 && vec_ok) {
+      __stcs(reinterpret_cast<int4*>(ids + lin0), make_int4((int)v[0], (int)v[1], (int)v[2], (int)v[3]));
+    } else {
+      for (int i = 0; i < cnt; ++i) ids[lin0 + i] = (int32_t)v[i];
+    }
+    x += 128;
+    if (x >= Lf) {
+      if (Lf >= 128) {
+        x -= Lf;
+        row += 1;
+      } else {
+        uint32_t q, r;
+        divmod32(x, divLf, q, r);
+        row += q;
+        x = r;
+      }
+      base = row_base_m<uint32_t>(D, tabs, ctab, row, m);
+    }
+  }
+}
 
 // ids for the 4-point groups [gbeg, gend) of one warp: lane l takes groups
 // gbeg + l, gbeg + l + 32, ... so each store instruction of the warp writes
@@ -360,6 +515,24 @@ __device__ __forceinline__ uint32_t lc_slab_F(const MapCore& D, int t, uint64_t 
   const uint64_t stride = D.lc_stride[t];
   const uint64_t hi = s / stride, lo = s - hi * stride;
   const uint64_t xt = side ? D.L[t] - 1 : 0;
+  const uint64_t lin = hi * (D.L[t] * stride) + xt * stride + lo;
+  uint64_t q, F;
+  divmod64(lin, D.divP64, q, F);
+  return (uint32_t)F;
+}
+
+// Element-count halo of a linear-cyclic launch, slab entry e of dimension t:
+// the slabs are the positions x_t in [0, lo_n) and then L_t - 1, L_t - 2, ...
+// (the positions whose halo window the boundary cuts).  Returns F of the
+// point and its x_t.
+__device__ __forceinline__ uint32_t lc_wslab_point(const MapCore& D, int t, uint64_t e, uint64_t lo_n,
+                                                   uint64_t& xt) {
+  const uint64_t per_slab = D.npoints / D.L[t];
+  const uint64_t sidx = e / per_slab;
+  const uint64_t s = e - sidx * per_slab;
+  const uint64_t stride = D.lc_stride[t];
+  const uint64_t hi = s / stride, lo = s - hi * stride;
+  xt = sidx < lo_n ? sidx : D.L[t] - 1 - (sidx - lo_n);
   const uint64_t lin = hi * (D.L[t] * stride) + xt * stride + lo;
   uint64_t q, F;
   divmod64(lin, D.divP64, q, F);

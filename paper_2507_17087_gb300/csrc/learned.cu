@@ -430,7 +430,7 @@ int prepare_query(const mp_search_query& q, Prepared& pq, char* region, size_t c
                   cudaStream_t st) {
   int rc = prepare(q, pq.S);
   if (rc) return rc;
-  const size_t NC = pq.S.chains.size(), NF = pq.S.facts.size();
+  const size_t NC = pq.S.c->chains.size(), NF = pq.S.c->facts.size();
   const size_t o_p = 0, o_f = a256(NC * sizeof(ChainProg)), o_cf = o_f + a256(NF * sizeof(Fact)),
                o_pr = o_cf + a256(NC * kChainFeat * 4), end = o_pr + a256(NF * 8);
   if (end > cap) return MP_ENOMEM;
@@ -439,8 +439,8 @@ int prepare_query(const mp_search_query& q, Prepared& pq, char* region, size_t c
   pq.d_facts = (Fact*)(region + o_f);
   pq.d_chainfeat = (float*)(region + o_cf);
   unsigned long long* d_prim = (unsigned long long*)(region + o_pr);
-  MP_CUDA_TRY(cudaMemcpyAsync(pq.d_progs, pq.S.progs.data(), NC * sizeof(ChainProg), cudaMemcpyHostToDevice, st));
-  MP_CUDA_TRY(cudaMemcpyAsync(pq.d_facts, pq.S.fdev.data(), NF * sizeof(Fact), cudaMemcpyHostToDevice, st));
+  MP_CUDA_TRY(cudaMemcpyAsync(pq.d_progs, pq.S.c->progs.data(), NC * sizeof(ChainProg), cudaMemcpyHostToDevice, st));
+  MP_CUDA_TRY(cudaMemcpyAsync(pq.d_facts, pq.S.c->fdev.data(), NF * sizeof(Fact), cudaMemcpyHostToDevice, st));
   k_chain_feats<<<(unsigned)((NC + 127) / 128), 128, 0, st>>>(pq.d_progs, NC, (uint32_t)q.procs, pq.d_chainfeat);
   k_primaries<<<(unsigned)((NF + 127) / 128), 128, 0, st>>>(pq.d_facts, (uint32_t)NF, (uint32_t)q.M, (uint32_t)q.N,
                                                             (uint32_t)q.K, d_prim);
@@ -568,7 +568,7 @@ extern "C" int mp_mlp_train_search(mp_mlp* h, const mp_search_query* queries, in
     char* region = g_pool_q.get(64u << 20);
     if (!region) { rc = MP_ENOMEM; break; }
     if ((rc = prepare_query(q, pq, region, 64u << 20, &used, st))) break;
-    const uint64_t NC = pq.S.chains.size(), NF = pq.S.facts.size();
+    const uint64_t NC = pq.S.c->chains.size(), NF = pq.S.c->facts.size();
     std::vector<uint32_t> order(NF);
     std::iota(order.begin(), order.end(), 0u);
     std::sort(order.begin(), order.end(), [&](uint32_t a, uint32_t b) { return pq.prim[a] < pq.prim[b]; });
@@ -623,17 +623,21 @@ extern "C" int mp_learned_search(mp_mlp* h, const mp_search_query* query, int K,
                                  mp_learned_stats* stats, void* stream) {
   using namespace mp;
   using namespace mp::lrn;
+  using clk = std::chrono::steady_clock;
+  auto ms_since = [](clk::time_point a) { return std::chrono::duration<double, std::milli>(clk::now() - a).count(); };
   if (!h || !query || !out || K < 1 || K > 65536) return MP_EINVAL;
   int rc = validate_query(*query);
   if (rc) return rc;
+  if (stats) std::memset(stats, 0, sizeof(*stats));
   cudaStream_t st = (cudaStream_t)stream;
   const mp_search_query& q = *query;
+  auto t_phase = clk::now();
   Prepared pq;
   size_t used = 0;
   char* region = g_pool_q.get(64u << 20);
   if (!region) return MP_ENOMEM;
   if ((rc = prepare_query(q, pq, region, 64u << 20, &used, st))) return rc;
-  const uint64_t NC = pq.S.chains.size(), NF = pq.S.facts.size();
+  const uint64_t NC = pq.S.c->chains.size(), NF = pq.S.c->facts.size();
   // the candidates that can win: every chain with a factorisation of least
   // primary cost (exact, closed form); MP_LEARNED_SCORE_ALL scores them all
   const bool all = (flags & MP_LEARNED_SCORE_ALL) != 0;
@@ -641,12 +645,16 @@ extern "C" int mp_learned_search(mp_mlp* h, const mp_search_query* query, int K,
   for (uint64_t fr = 0; fr < NF; ++fr)
     if (all || pq.prim[fr] == pq.Q.pmin) flist.push_back((uint32_t)fr);
   const uint64_t ncand = NC * flist.size();
+  // the selection grows by 8x (up to kMaxSel) while the acceptance rule fails
+  const unsigned kMaxSel = 1u << 16;
+  const unsigned Kmax = (unsigned)std::min<uint64_t>(std::max<unsigned>((unsigned)K, kMaxSel), ncand);
   const unsigned cap_eq = 1u << 16;
   const size_t o_sc = 0, o_hist = a256(ncand * 4), o_thr = o_hist + a256(65536 * 4), o_cnt = o_thr + 256,
-               o_below = o_cnt + 256, o_eq = o_below + a256((size_t)K * 8), o_sel = o_eq + a256((size_t)cap_eq * 8),
-               o_p = o_sel + a256((size_t)K * 8), o_s = o_p + a256((size_t)K * 8),
-               o_y = o_s + a256((size_t)K * 8), o_ye = o_y + a256((size_t)K * 4),
-               o_fl = o_ye + a256((size_t)cap_eq * 4), end = o_fl + a256(flist.size() * 4);
+               o_below = o_cnt + 256, o_eq = o_below + a256((size_t)Kmax * 8),
+               o_sel = o_eq + a256((size_t)cap_eq * 8), o_p = o_sel + a256((size_t)Kmax * 8),
+               o_s = o_p + a256((size_t)Kmax * 8), o_y = o_s + a256((size_t)Kmax * 8),
+               o_ye = o_y + a256((size_t)Kmax * 4), o_fl = o_ye + a256((size_t)cap_eq * 4),
+               end = o_fl + a256(flist.size() * 4);
   char* w = g_pool_s.get(end);
   if (!w) return MP_ENOMEM;
   float* d_sc = (float*)(w + o_sc);
@@ -662,6 +670,8 @@ extern "C" int mp_learned_search(mp_mlp* h, const mp_search_query* query, int K,
   float* d_ye = (float*)(w + o_ye);
   uint32_t* d_fl = (uint32_t*)(w + o_fl);
   MP_CUDA_TRY(cudaMemcpyAsync(d_fl, flist.data(), flist.size() * 4, cudaMemcpyHostToDevice, st));
+  if (stats) stats->ms_prepare = ms_since(t_phase);
+  t_phase = clk::now();
   // ---- score every candidate
   MP_CUDA_TRY(cudaMemsetAsync(h->status, 0, 4, st));
   const size_t smem = 65536 + 32768 + 1024;
@@ -674,115 +684,140 @@ extern "C" int mp_learned_search(mp_mlp* h, const mp_search_query* query, int K,
   timer_end(st);
   count_launch();
   MP_CUDA_TRY(cudaGetLastError());
-  // ---- top-K by score
-  const unsigned Keff = (unsigned)std::min<uint64_t>((uint64_t)K, ncand);
   MP_CUDA_TRY(cudaMemsetAsync(d_hist, 0, 65536 * 4, st));
-  MP_CUDA_TRY(cudaMemsetAsync(d_cnt, 0, 16, st));
   const unsigned gb = (unsigned)std::min<uint64_t>((ncand + 255) / 256, (uint64_t)sm_count_l() * 8);
   k_topk_hist<<<gb, 256, 0, st>>>(d_sc, ncand, d_hist);
-  k_topk_threshold<<<1, 1024, 0, st>>>(d_hist, Keff, d_thr);
-  k_topk_collect<<<gb, 256, 0, st>>>(d_sc, ncand, d_thr, d_below, d_cnt, d_eq, d_cnt + 1, Keff, cap_eq);
-  count_launch(3);
+  count_launch();
   MP_CUDA_TRY(cudaGetLastError());
-  unsigned cnt[2] = {0, 0};
   int status = 0;
-  MP_CUDA_TRY(cudaMemcpyAsync(cnt, d_cnt, 8, cudaMemcpyDeviceToHost, st));
   MP_CUDA_TRY(cudaMemcpyAsync(&status, h->status, 4, cudaMemcpyDeviceToHost, st));
   MP_CUDA_TRY(cudaStreamSynchronize(st));
   if (status) return status;
-  const unsigned nbelow = std::min(cnt[0], Keff), neq = std::min(cnt[1], cap_eq);
-  // the threshold bin, ordered by (score, index) for a deterministic choice
-  std::vector<int64_t> eq(neq);
-  std::vector<float> eqs(neq);
-  if (neq) {
-    MP_CUDA_TRY(cudaMemcpyAsync(eq.data(), d_eq, (size_t)neq * 8, cudaMemcpyDeviceToHost, st));
-    k_take<<<(neq + 255) / 256, 256, 0, st>>>(d_sc, d_eq, (int)neq, d_ye);
-    count_launch();
-    MP_CUDA_TRY(cudaMemcpyAsync(eqs.data(), d_ye, (size_t)neq * 4, cudaMemcpyDeviceToHost, st));
-    MP_CUDA_TRY(cudaStreamSynchronize(st));
-  }
-  // NaN scores order last (a total order keeps the sort well defined)
-  auto key = [](float v) { return std::isnan(v) ? INFINITY : v; };
-  std::vector<uint32_t> ord(neq);
-  std::iota(ord.begin(), ord.end(), 0u);
-  std::sort(ord.begin(), ord.end(), [&](uint32_t a, uint32_t b) {
-    const float ka = key(eqs[a]), kb = key(eqs[b]);
-    return ka < kb || (ka == kb && eq[a] < eq[b]);
-  });
-  std::vector<int64_t> sel(nbelow);
-  if (nbelow) MP_CUDA_TRY(cudaMemcpyAsync(sel.data(), d_below, (size_t)nbelow * 8, cudaMemcpyDeviceToHost, st));
-  MP_CUDA_TRY(cudaStreamSynchronize(st));
-  for (uint32_t i = 0; i < neq && sel.size() < Keff; ++i) sel.push_back(eq[ord[i]]);
-  const int64_t nsel = (int64_t)sel.size();
-  std::vector<int64_t> pos = sel;   // positions in the scored list
-  for (auto& v : sel) {
-    const uint64_t j = (uint64_t)v / NC;
-    v = (int64_t)((uint64_t)flist[j] * NC + ((uint64_t)v - j * NC));
-  }
-  if (nsel == 0) {   // the selection kernels produced nothing
-    MP_CUDA_TRY(cudaErrorUnknown);
-  }
-  // ---- exact costs of the selection
-  MP_CUDA_TRY(cudaMemcpyAsync(d_sel, sel.data(), (size_t)nsel * 8, cudaMemcpyHostToDevice, st));
-  if ((rc = candidate_costs_dev(q, pq.S, pq.d_progs, pq.d_facts, d_sel, nsel, d_p, d_s, st))) return rc;
-  MP_CUDA_TRY(cudaStreamSynchronize(st));
-  MP_CUDA_TRY(cudaMemcpyAsync(d_sel, pos.data(), (size_t)nsel * 8, cudaMemcpyHostToDevice, st));
-  k_take<<<(unsigned)((nsel + 255) / 256), 256, 0, st>>>(d_sc, d_sel, (int)nsel, d_y);
-  count_launch();
-  std::vector<uint64_t> pb(nsel), sb(nsel);
-  std::vector<float> yh(nsel);
-  MP_CUDA_TRY(cudaMemcpyAsync(pb.data(), d_p, (size_t)nsel * 8, cudaMemcpyDeviceToHost, st));
-  MP_CUDA_TRY(cudaMemcpyAsync(sb.data(), d_s, (size_t)nsel * 8, cudaMemcpyDeviceToHost, st));
-  MP_CUDA_TRY(cudaMemcpyAsync(yh.data(), d_y, (size_t)nsel * 4, cudaMemcpyDeviceToHost, st));
-  MP_CUDA_TRY(cudaStreamSynchronize(st));
-  int64_t bi = 0;
-  for (int64_t i = 1; i < nsel; ++i) {
-    const bool less = pb[i] < pb[bi] || (pb[i] == pb[bi] && (sb[i] < sb[bi] || (sb[i] == sb[bi] && sel[i] < sel[bi])));
-    if (less) bi = i;
-  }
-  const unsigned long long tb = q.tile_bytes;
-  const unsigned long long p_best = pb[bi] / tb;
-  // certificate: every candidate whose primary is no higher than the
-  // winner's was evaluated exactly
-  uint64_t threats = 0, threats_in = 0;
-  for (uint64_t fr = 0; fr < NF; ++fr)
-    if (pq.prim[fr] <= p_best) threats += NC;
-  for (int64_t i = 0; i < nsel; ++i)
-    if (pb[i] / tb <= p_best) ++threats_in;
-  const bool certified = threats == threats_in;
-  // margin: every unselected candidate scored at least the threshold; the
-  // model's largest error on the selection bounds how far its true target
-  // may lie below its score
-  // A candidate left out has a score of at least tau (the largest selected
-  // score); it beats the winner only if its true target lies below the
-  // winner's, i.e. if the model overestimated it by more than tau - y_best.
-  // The largest overestimation seen on the selection (times 1.5) bounds that.
-  float over = 0.f, tau = -1e30f;
-  bool finite = true;
-  for (int64_t i = 0; i < nsel; ++i) {
-    const float yt = host_target(pb[i] / tb, sb[i] / tb, pq.Q.pmin);
-    finite = finite && std::isfinite(yh[i]);
-    over = std::max(over, yh[i] - yt);
-    tau = std::max(tau, yh[i]);
-  }
-  if (!finite) over = INFINITY;   // no margin from a model that returned NaN / inf
-  const float y_best = host_target(p_best, sb[bi] / tb, pq.Q.pmin);
-  const double margin = (double)tau - y_best - 1.5 * over - 1e-3;
-  const bool accept = certified || (p_best == pq.Q.pmin && margin > 0.0 && nsel == (int64_t)Keff);
   if (stats) {
-    std::memset(stats, 0, sizeof(*stats));
+    stats->ms_model = ms_since(t_phase);
     stats->n_scored = (int64_t)ncand;
-    stats->n_exact = nsel;
+  }
+  t_phase = clk::now();
+
+  // ---- the Kc best scores, evaluated exactly; Kc grows until accepted
+  auto key = [](float v) { return std::isnan(v) ? INFINITY : v; };   // NaN orders last
+  const unsigned long long tb = q.tile_bytes;
+  unsigned Kc = (unsigned)std::min<uint64_t>((uint64_t)K, ncand);
+  std::vector<int64_t> sel, pos;
+  std::vector<uint64_t> pb, sb;
+  std::vector<float> yh;
+  int64_t bi = 0;
+  bool accept = false, certified = false;
+  double margin = 0.0;
+  float over = 0.f;
+  int rounds = 0;
+  for (;;) {
+    ++rounds;
+    MP_CUDA_TRY(cudaMemsetAsync(d_cnt, 0, 16, st));
+    k_topk_threshold<<<1, 1024, 0, st>>>(d_hist, Kc, d_thr);
+    k_topk_collect<<<gb, 256, 0, st>>>(d_sc, ncand, d_thr, d_below, d_cnt, d_eq, d_cnt + 1, Kc, cap_eq);
+    count_launch(2);
+    MP_CUDA_TRY(cudaGetLastError());
+    unsigned cnt[2] = {0, 0};
+    MP_CUDA_TRY(cudaMemcpyAsync(cnt, d_cnt, 8, cudaMemcpyDeviceToHost, st));
+    MP_CUDA_TRY(cudaStreamSynchronize(st));
+    const unsigned nbelow = std::min(cnt[0], Kc), neq = std::min(cnt[1], cap_eq);
+    // the threshold bin, ordered by (score, index) for a deterministic choice
+    std::vector<int64_t> eq(neq);
+    std::vector<float> eqs(neq);
+    if (neq) {
+      MP_CUDA_TRY(cudaMemcpyAsync(eq.data(), d_eq, (size_t)neq * 8, cudaMemcpyDeviceToHost, st));
+      k_take<<<(neq + 255) / 256, 256, 0, st>>>(d_sc, d_eq, (int)neq, d_ye);
+      count_launch();
+      MP_CUDA_TRY(cudaMemcpyAsync(eqs.data(), d_ye, (size_t)neq * 4, cudaMemcpyDeviceToHost, st));
+    }
+    pos.assign(nbelow, 0);
+    if (nbelow) MP_CUDA_TRY(cudaMemcpyAsync(pos.data(), d_below, (size_t)nbelow * 8, cudaMemcpyDeviceToHost, st));
+    MP_CUDA_TRY(cudaStreamSynchronize(st));
+    std::vector<uint32_t> ord(neq);
+    std::iota(ord.begin(), ord.end(), 0u);
+    std::sort(ord.begin(), ord.end(), [&](uint32_t a, uint32_t b) {
+      const float ka = key(eqs[a]), kb = key(eqs[b]);
+      return ka < kb || (ka == kb && eq[a] < eq[b]);
+    });
+    for (uint32_t i = 0; i < neq && pos.size() < Kc; ++i) pos.push_back(eq[ord[i]]);
+    const int64_t nsel = (int64_t)pos.size();
+    if (nsel == 0) MP_CUDA_TRY(cudaErrorUnknown);   // the selection kernels produced nothing
+    sel = pos;   // positions in the scored list -> candidate indices
+    for (auto& v : sel) {
+      const uint64_t j = (uint64_t)v / NC;
+      v = (int64_t)((uint64_t)flist[j] * NC + ((uint64_t)v - j * NC));
+    }
+    MP_CUDA_TRY(cudaMemcpyAsync(d_sel, sel.data(), (size_t)nsel * 8, cudaMemcpyHostToDevice, st));
+    if ((rc = candidate_costs_dev(q, pq.S, pq.d_progs, pq.d_facts, d_sel, nsel, d_p, d_s, st))) return rc;
+    MP_CUDA_TRY(cudaMemcpyAsync(d_sel, pos.data(), (size_t)nsel * 8, cudaMemcpyHostToDevice, st));
+    k_take<<<(unsigned)((nsel + 255) / 256), 256, 0, st>>>(d_sc, d_sel, (int)nsel, d_y);
+    count_launch();
+    pb.resize(nsel);
+    sb.resize(nsel);
+    yh.resize(nsel);
+    MP_CUDA_TRY(cudaMemcpyAsync(pb.data(), d_p, (size_t)nsel * 8, cudaMemcpyDeviceToHost, st));
+    MP_CUDA_TRY(cudaMemcpyAsync(sb.data(), d_s, (size_t)nsel * 8, cudaMemcpyDeviceToHost, st));
+    MP_CUDA_TRY(cudaMemcpyAsync(yh.data(), d_y, (size_t)nsel * 4, cudaMemcpyDeviceToHost, st));
+    MP_CUDA_TRY(cudaStreamSynchronize(st));
+    bi = 0;
+    for (int64_t i = 1; i < nsel; ++i) {
+      const bool less = pb[i] < pb[bi] || (pb[i] == pb[bi] && (sb[i] < sb[bi] || (sb[i] == sb[bi] && sel[i] < sel[bi])));
+      if (less) bi = i;
+    }
+    const unsigned long long p_best = pb[bi] / tb;
+    // certificate: every candidate whose primary is no higher than the
+    // winner's was evaluated exactly
+    uint64_t threats = 0, threats_in = 0;
+    for (uint64_t fr = 0; fr < NF; ++fr)
+      if (pq.prim[fr] <= p_best) threats += NC;
+    for (int64_t i = 0; i < nsel; ++i)
+      if (pb[i] / tb <= p_best) ++threats_in;
+    certified = threats == threats_in;
+    // margin: a candidate left out scored at least tau (the largest selected
+    // score); it beats the winner only if its true target lies below the
+    // winner's, i.e. if the model overestimated it by more than
+    // tau - y_best.  The largest overestimation seen on the selection
+    // (times 1.5) bounds that.
+    float tau = -1e30f;
+    bool finite = true;
+    over = 0.f;
+    for (int64_t i = 0; i < nsel; ++i) {
+      const float yt = host_target(pb[i] / tb, sb[i] / tb, pq.Q.pmin);
+      finite = finite && std::isfinite(yh[i]);
+      over = std::max(over, yh[i] - yt);
+      tau = std::max(tau, yh[i]);
+    }
+    if (!finite) over = INFINITY;   // no margin from a model that returned NaN / inf
+    const float y_best = host_target(p_best, sb[bi] / tb, pq.Q.pmin);
+    margin = (double)tau - y_best - 1.5 * over - 1e-3;
+    accept = certified || (p_best == pq.Q.pmin && margin > 0.0 && nsel == (int64_t)Kc);
+    if (stats) stats->n_exact += nsel;
+    if (accept || (flags & MP_LEARNED_NO_FALLBACK)) break;
+    // grow while the next selection stays a small part of the scored set;
+    // beyond that the exhaustive search (which shares each chain's table
+    // over its factorisations) is the cheaper way to an exact answer
+    const uint64_t next = (uint64_t)Kc * 8;
+    if (next > kMaxSel || next * 4 > ncand) break;
+    Kc = (unsigned)next;
+  }
+  if (stats) {
+    stats->ms_exact = ms_since(t_phase);
     stats->certified = certified ? 1 : 0;
     stats->margin = margin;
+    stats->max_overestimate = over;
+    stats->rounds = rounds;
+    stats->n_selected = (int64_t)sel.size();
   }
   if (!accept && !(flags & MP_LEARNED_NO_FALLBACK)) {
+    t_phase = clk::now();
     mp_search_query qf = q;
     qf.flags = 0;
     rc = exhaustive_search(qf, out, st);
     if (stats) {
       stats->fallback = 1;
       stats->n_exact += out->n_candidates;
+      stats->ms_fallback = ms_since(t_phase);
     }
     return rc;
   }
@@ -790,11 +825,11 @@ extern "C" int mp_learned_search(mp_mlp* h, const mp_search_query* query, int K,
   std::memset(out, 0, sizeof(*out));
   const uint64_t idx = (uint64_t)sel[bi], fr = idx / NC, c = idx % NC;
   out->index = (int64_t)idx;
-  for (int t = 0; t < 3; ++t) out->f[t] = pq.S.facts[fr][t];
+  for (int t = 0; t < 3; ++t) out->f[t] = pq.S.c->facts[fr][t];
   out->chain_rank = (int64_t)c;
-  out->chain_len = (int32_t)pq.S.chains[c].size();
+  out->chain_len = (int32_t)pq.S.c->chains[c].size();
   for (int o = 0; o < out->chain_len; ++o) {
-    const CanonOp& op = pq.S.chains[c][o];
+    const CanonOp& op = pq.S.c->chains[c][o];
     mp_xform& x = out->chain[o];
     x.op = op.op == P_SPLIT ? MP_SPLIT : (op.op == P_MERGE ? MP_MERGE : MP_SWAP);
     x.i = op.p;
@@ -805,7 +840,7 @@ extern "C" int mp_learned_search(mp_mlp* h, const mp_search_query* query, int K,
   out->secondary_bytes = sb[bi];
   out->n_chains = (int64_t)NC;
   out->n_factorisations = (int64_t)NF;
-  out->n_candidates = (int64_t)ncand;
+  out->n_candidates = (int64_t)(NC * NF);
   return MP_OK;
 }
 
@@ -825,7 +860,7 @@ extern "C" int mp_learned_scores(mp_mlp* h, const mp_search_query* query, float*
   char* region = g_pool_q.get(64u << 20);
   if (!region) return MP_ENOMEM;
   if ((rc = prepare_query(*query, pq, region, 64u << 20, &used, st))) return rc;
-  const uint64_t ncand = (uint64_t)pq.S.chains.size() * pq.S.facts.size();
+  const uint64_t ncand = (uint64_t)pq.S.c->chains.size() * pq.S.c->facts.size();
   *n_out = (int64_t)ncand;
   MP_CUDA_TRY(cudaMemsetAsync(h->status, 0, 4, st));
   const size_t smem = 65536 + 32768 + 1024;

@@ -51,8 +51,10 @@ __global__ void __launch_bounds__(kThreads) k_tables(const __grid_constant__ Map
   }
 }
 
+// elem_mode = 1: X holds the element counts (dim_elems) for halo widths w.
 __global__ void __launch_bounds__(kThreads) k_counts(const __grid_constant__ MapDesc D, uint64_t* __restrict__ H,
-                                                     uint64_t* __restrict__ X) {
+                                                     uint64_t* __restrict__ X, int elem_mode, uint32_t w0,
+                                                     uint32_t w1, uint32_t w2, uint32_t w3) {
   const uint32_t e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= D.Jtotal) return;
   int t = 0;
@@ -60,7 +62,10 @@ __global__ void __launch_bounds__(kThreads) k_counts(const __grid_constant__ Map
   uint64_t h, xc;
   dim_counts(D, t, e - D.Joff[t], h, xc);
   H[e] = h;
-  if (X) X[e] = xc;
+  if (X) {
+    const uint32_t w[4] = {w0, w1, w2, w3};
+    X[e] = elem_mode ? dim_elems(D, t, e - D.Joff[t], w[t]) : xc;
+  }
 }
 
 template <typename I, int MODE, bool TSMEM>
@@ -116,18 +121,52 @@ __global__ void __launch_bounds__(kThreads) k_lc_slabs(const __grid_constant__ M
   }
 }
 
+// Element-count halo of a linear-cyclic launch: the points of the boundary
+// slabs lack the offsets their cut window does not reach; each such offset
+// comes off the receiving flat index F + offset.
+__global__ void __launch_bounds__(kThreads) k_lc_wslabs(const __grid_constant__ MapDesc D,
+                                                        const __grid_constant__ LcHalo lh, uint64_t f0,
+                                                        uint64_t f1, uint64_t f2, uint64_t f3, uint32_t w0,
+                                                        uint32_t w1, uint32_t w2, uint32_t w3,
+                                                        unsigned long long* __restrict__ deficit) {
+  const uint64_t face[4] = {f0, f1, f2, f3};
+  const uint64_t wd[4] = {w0, w1, w2, w3};
+  for (int t = 0; t < D.k; ++t) {
+    if (lh.n[t] == 0 || face[t] == 0) continue;
+    const uint64_t Lt = D.L[t];
+    const uint64_t lo_n = wd[t] < Lt ? wd[t] : Lt;
+    const uint64_t hi_n = wd[t] < Lt - lo_n ? wd[t] : Lt - lo_n;
+    const uint64_t n = (lo_n + hi_n) * (D.npoints / Lt);
+    for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+         e += (uint64_t)gridDim.x * blockDim.x) {
+      uint64_t xt;
+      const uint32_t F = lc_wslab_point(D, t, e, lo_n, xt);
+      const uint64_t a = xt < wd[t] ? xt : wd[t];                     // reach towards 0
+      const uint64_t b = Lt - 1 - xt < wd[t] ? Lt - 1 - xt : wd[t];   // reach towards L_t - 1
+      for (uint32_t i = 0; i < lh.n[t]; ++i) {
+        const bool reached = (lh.pos[t][i] && lh.pos[t][i] <= b) || (lh.neg[t][i] && lh.neg[t][i] <= a);
+        if (reached) continue;
+        uint32_t G = F + lh.off[t][i];
+        if (G >= D.P) G -= D.P;
+        atomicAdd(deficit + G, (unsigned long long)face[t]);
+      }
+    }
+  }
+}
+
 __global__ void __launch_bounds__(kThreads) k_reduce(const __grid_constant__ MapDesc D, const uint32_t* __restrict__ T,
                                                      const uint64_t* __restrict__ H, const uint64_t* __restrict__ X,
                                                      const uint64_t* __restrict__ deficit, uint64_t f0, uint64_t f1,
                                                      uint64_t f2, uint64_t f3, uint64_t* __restrict__ hist,
                                                      uint64_t* __restrict__ recv,
-                                                     unsigned long long* __restrict__ total) {
+                                                     unsigned long long* __restrict__ total,
+                                                     const __grid_constant__ LcHalo lh, int use_lh) {
   const uint64_t face[4] = {f0, f1, f2, f3};
   const uint32_t F = blockIdx.x * blockDim.x + threadIdx.x;
   uint64_t r_F = 0;
   if (F < D.P) {
     uint64_t h_F;
-    reduce_F(D, H, X, deficit, face, recv || total, F, h_F, r_F);
+    reduce_F(D, H, X, deficit, face, recv || total, F, h_F, r_F, use_lh ? &lh : nullptr);
     const uint32_t id = T[F];
     if (hist) hist[id] = h_F;
     if (recv) recv[id] = r_F;
@@ -162,8 +201,33 @@ struct Want {
   uint64_t* hist;
   uint64_t* recv;
   uint64_t* total;
-  uint64_t face[4];
+  uint64_t face[4];     // bytes per face (faces mode) or per element
+  int elem_mode;        // 1: element-count halo with widths
+  uint32_t width[4];
 };
+
+// Offsets of the element-count halo of a linear-cyclic launch (see LcHalo).
+LcHalo make_lc_halo(const MapDesc& D, const Want& w) {
+  LcHalo lh;
+  std::memset(&lh, 0, sizeof(lh));
+  for (int t = 0; t < D.k; ++t) {
+    const uint64_t S = D.lc_stride_mod[t];
+    for (uint32_t delta = 1; delta <= w.width[t] && delta < D.L[t]; ++delta) {
+      const uint32_t plus = (uint32_t)(((unsigned __int128)delta * S) % D.P);
+      const uint32_t minus = plus ? D.P - plus : 0;
+      for (int side = 0; side < 2; ++side) {
+        const uint32_t off = side ? minus : plus;
+        if (off == 0) continue;
+        uint32_t i = 0;
+        while (i < lh.n[t] && lh.off[t][i] != off) ++i;
+        if (i == lh.n[t]) lh.off[t][lh.n[t]++] = off;
+        uint8_t& slot = side ? lh.neg[t][i] : lh.pos[t][i];
+        if (!slot) slot = (uint8_t)delta;
+      }
+    }
+  }
+  return lh;
+}
 
 size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
 
@@ -219,7 +283,8 @@ int run_launch_ws(const Plan& pl, const Want& w, const Layout& ly, char* ws, cud
     count_launch();
   }
   if (H) {
-    k_counts<<<(D.Jtotal + kThreads - 1) / kThreads, kThreads, 0, st>>>(D, H, X);
+    k_counts<<<(D.Jtotal + kThreads - 1) / kThreads, kThreads, 0, st>>>(D, H, X, w.elem_mode, w.width[0],
+                                                                         w.width[1], w.width[2], w.width[3]);
     count_launch();
   }
   // ------------------------------------------------ ids
@@ -277,18 +342,30 @@ int run_launch_ws(const Plan& pl, const Want& w, const Layout& ly, char* ws, cud
   // ------------------------------------------------ reductions
   if (ly.need_red) {
     if (w.total) MP_CUDA_TRY(cudaMemsetAsync(w.total, 0, 8, st));
+    const bool lc_elem = D.lc && w.elem_mode;
+    LcHalo lh;
+    std::memset(&lh, 0, sizeof(lh));
+    if (lc_elem) lh = make_lc_halo(D, w);
     if (def) {
       MP_CUDA_TRY(cudaMemsetAsync(def, 0, ly.n_def * 8, st));
       uint64_t work = 0;
-      for (int t = 0; t < D.k; ++t) work += 2 * (D.npoints / D.L[t]);
+      for (int t = 0; t < D.k; ++t) {
+        const uint64_t lo_n = std::min<uint64_t>(lc_elem ? w.width[t] : 1, D.L[t]);
+        const uint64_t hi_n = std::min<uint64_t>(lc_elem ? w.width[t] : 1, D.L[t] - lo_n);
+        work += (lc_elem ? lo_n + hi_n : 2) * (D.npoints / D.L[t]);
+      }
       const uint64_t blocks = std::max<uint64_t>(1, std::min<uint64_t>((work + kThreads - 1) / kThreads,
                                                                          (uint64_t)sm_count() * 8));
-      k_lc_slabs<<<(unsigned)blocks, kThreads, 0, st>>>(D, w.face[0], w.face[1], w.face[2], w.face[3], def);
+      if (lc_elem)
+        k_lc_wslabs<<<(unsigned)blocks, kThreads, 0, st>>>(D, lh, w.face[0], w.face[1], w.face[2], w.face[3],
+                                                           w.width[0], w.width[1], w.width[2], w.width[3], def);
+      else
+        k_lc_slabs<<<(unsigned)blocks, kThreads, 0, st>>>(D, w.face[0], w.face[1], w.face[2], w.face[3], def);
       count_launch();
     }
     k_reduce<<<(D.P + kThreads - 1) / kThreads, kThreads, 0, st>>>(
         D, T, H, X, (const uint64_t*)def, w.face[0], w.face[1], w.face[2], w.face[3], w.hist, w.recv,
-        (unsigned long long*)w.total);
+        (unsigned long long*)w.total, lh, lc_elem ? 1 : 0);
     count_launch();
   }
   MP_CUDA_TRY(cudaGetLastError());
@@ -334,7 +411,7 @@ int stage(void* user, size_t bytes, size_t& cursor, std::vector<Staged>& list, c
 }
 
 int run_with_staging(const Plan& pl, int32_t* ids, uint64_t* hist, uint64_t* recv, uint64_t* total,
-                     const uint64_t* face, cudaStream_t st) {
+                     const uint64_t* face, cudaStream_t st, int elem_mode = 0, const int32_t* width = nullptr) {
   const MapDesc& D = pl.desc;
   size_t need = 0;
   auto host_bytes = [&](void* p, size_t b, bool direct_ok) {
@@ -359,6 +436,8 @@ int run_with_staging(const Plan& pl, int32_t* ids, uint64_t* hist, uint64_t* rec
   stage(recv, (size_t)D.P * 8, cur, list, base, &p, false); w.recv = (uint64_t*)p;
   stage(total, 8, cur, list, base, &p, false); w.total = (uint64_t*)p;
   for (int t = 0; t < 4; ++t) w.face[t] = face && t < D.k ? face[t] : 0;
+  w.elem_mode = elem_mode;
+  for (int t = 0; t < 4; ++t) w.width[t] = width && t < D.k ? (uint32_t)width[t] : 0;
   int rc = run_launch(pl, w, st);
   if (rc) return rc;
   for (auto& s : list)
@@ -389,6 +468,21 @@ extern "C" int mp_comm_volume(const mp_space* space, const mp_machine* machine, 
   if (rc) return rc;
   if (!face_bytes || !total) return MP_EINVAL;
   return mp::run_with_staging(pl, nullptr, nullptr, recv, total, face_bytes, (cudaStream_t)stream);
+}
+
+extern "C" int mp_halo_volume(const mp_space* space, const mp_machine* machine, const mp_xform* chain,
+                              int n_xf, const mp_dist* dist, const mp_halo* halo, uint64_t* total,
+                              uint64_t* recv, void* stream) {
+  mp::Plan pl;
+  int rc = mp::build_plan(space, machine, chain, n_xf, dist, pl);
+  if (rc) return rc;
+  if (!halo || !total) return MP_EINVAL;
+  if (halo->mode != MP_HALO_FACES && halo->mode != MP_HALO_ELEMENTS) return MP_EINVAL;
+  if (halo->mode == MP_HALO_ELEMENTS)
+    for (int t = 0; t < space->rank; ++t)
+      if (halo->width[t] < 0 || halo->width[t] > MP_MAX_HALO_WIDTH) return MP_EINVAL;
+  return mp::run_with_staging(pl, nullptr, nullptr, recv, total, halo->bytes, (cudaStream_t)stream,
+                              halo->mode == MP_HALO_ELEMENTS ? 1 : 0, halo->width);
 }
 
 // ------------------------------------------------------------ no-allocation variant

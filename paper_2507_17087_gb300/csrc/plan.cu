@@ -79,7 +79,8 @@ struct Builder {
   }
   // decompose(i, T): argmin factorisation of s_i, then k - 1 splits
   // split(i + n - 1, d_n), n = 1 .. k - 1 (Sec. 4.2).
-  int decompose(int i, int k, const int64_t* T) {
+  // h (may be null) and tmask select the generalised objective.
+  int decompose(int i, int k, const int64_t* T, const int32_t* h = nullptr, int tmask = 0) {
     int r = (int)shape.size();
     if (i < 0 || i >= r || k < 1 || k > 4) return MP_EINVAL;
     unsigned __int128 prod = 1;
@@ -88,7 +89,26 @@ struct Builder {
       prod *= (uint64_t)T[m];
       if (prod >= (unsigned __int128)kMaxPoints) return MP_EINVAL;
     }
-    std::vector<int64_t> f = decompose_argmin(shape[i], k, T);
+    if (tmask < 0 || tmask >= (1 << k)) return MP_EINVAL;
+    bool weighted = tmask != 0;
+    int64_t hw[4] = {1, 1, 1, 1};
+    if (h) {
+      bool any = false;
+      for (int m = 0; m < k; ++m) {
+        if (h[m] < 0) return MP_EINVAL;
+        any = any || h[m] != 0;
+      }
+      if (any)
+        for (int m = 0; m < k; ++m) hw[m] = h[m];
+      weighted = weighted || any;
+    }
+    std::vector<int64_t> f;
+    if (weighted) {
+      int rc = decompose_argmin_weighted(shape[i], k, T, hw, tmask, f);
+      if (rc) return rc;
+    } else {
+      f = decompose_argmin(shape[i], k, T);
+    }
     for (int n = 1; n < k; ++n) {
       int rc = split(i + n - 1, f[n - 1]);
       if (rc) return rc;
@@ -140,6 +160,50 @@ std::vector<int64_t> decompose_argmin(int64_t d, int k, const int64_t* l) {
     }
   }
   return best;
+}
+
+// The appendix's generalised objective ("Generalization of the Decompose
+// Primitive"): halo volume V = sum_m d_m h_m prod_{n != m} l_m plus
+// (1 - 1/d_m) prod_n l_m for every transposed m.  Scaled by d (a constant of
+// the argmin) every term is an integer: d V + prod l * sum_T (d_m - 1) d / d_m.
+int decompose_argmin_weighted(int64_t d, int k, const int64_t* l, const int64_t* h, int tmask,
+                              std::vector<int64_t>& out) {
+  typedef unsigned __int128 u128;
+  const u128 cap = ((u128)1) << 126;
+  auto mul = [&](u128 a, u128 b, u128& r) {
+    if (a != 0 && b > cap / a) return false;
+    r = a * b;
+    return true;
+  };
+  u128 Lambda = 1;
+  for (int m = 0; m < k; ++m)
+    if (!mul(Lambda, (uint64_t)l[m], Lambda)) return MP_EOVERFLOW;
+  out.clear();
+  u128 best_v = 0;
+  for (auto& f : ordered_factorisations(d, k)) {
+    u128 V = 0;
+    for (int m = 0; m < k; ++m) {
+      u128 term = (u128)(uint64_t)f[m] * (uint64_t)h[m];
+      for (int n = 0; n < k; ++n)
+        if (n != m && !mul(term, (uint64_t)l[n], term)) return MP_EOVERFLOW;
+      V += term;
+      if (V > cap) return MP_EOVERFLOW;
+    }
+    u128 v;
+    if (!mul(V, (uint64_t)d, v)) return MP_EOVERFLOW;
+    for (int m = 0; m < k; ++m) {
+      if (!((tmask >> m) & 1)) continue;
+      u128 add;
+      if (!mul(Lambda, (u128)(uint64_t)(f[m] - 1) * (uint64_t)(d / f[m]), add)) return MP_EOVERFLOW;
+      v += add;
+      if (v > cap) return MP_EOVERFLOW;
+    }
+    if (out.empty() || v < best_v) {
+      out = f;
+      best_v = v;
+    }
+  }
+  return MP_OK;
 }
 
 std::vector<CanonOp> canonical_alphabet(const std::vector<int64_t>& shape) {
@@ -223,7 +287,7 @@ int build_plan(const mp_space* space, const mp_machine* machine, const mp_xform*
       case MP_SPLIT: rc = B.split(x.i, x.d); break;
       case MP_MERGE: rc = B.merge(x.i, x.j); break;
       case MP_SWAP: rc = B.swap(x.i, x.j); break;
-      case MP_DECOMPOSE: rc = B.decompose(x.i, x.k, x.T); break;
+      case MP_DECOMPOSE: rc = B.decompose(x.i, x.k, x.T, x.h, x.transpose); break;
       case MP_BALANCE_SPLIT: {
         // balance_split(i, k) = decompose(i, (1, ..., 1))
         const int64_t ones[4] = {1, 1, 1, 1};
@@ -400,5 +464,28 @@ extern "C" int mp_search_space(int32_t procs, int32_t procs_per_node, int32_t ma
   if (n_factorisations) *n_factorisations = (int64_t)mp::ordered_factorisations(procs, 3).size();
   if (n_chains)
     *n_chains = (int64_t)mp::canonical_chains(procs / procs_per_node, procs_per_node, max_depth).size();
+  return MP_OK;
+}
+
+// Algorithm A1: primes ascending, each into the smallest factor so far (the
+// first on ties), factors sorted descending at the end.
+extern "C" int mp_greedy_grid(int64_t d, int32_t k, int64_t* out) {
+  if (d < 1 || k < 1 || k > 4 || !out) return MP_EINVAL;
+  std::vector<int64_t> grid((size_t)k, 1);
+  int64_t rest = d;
+  auto place = [&](int64_t p) {
+    size_t j = 0;
+    for (size_t m = 1; m < grid.size(); ++m)
+      if (grid[m] < grid[j]) j = m;
+    grid[j] *= p;
+  };
+  for (int64_t p = 2; p <= rest / p; ++p)
+    while (rest % p == 0) {
+      place(p);
+      rest /= p;
+    }
+  if (rest > 1) place(rest);
+  std::sort(grid.begin(), grid.end(), [](int64_t a, int64_t b) { return a > b; });
+  for (int m = 0; m < k; ++m) out[m] = grid[(size_t)m];
   return MP_OK;
 }

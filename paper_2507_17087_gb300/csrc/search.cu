@@ -18,7 +18,9 @@
 // equal distinct block coordinates (the chain is a bijection), which gives
 // the primary in closed form: sum_v (min(E_v, f_v) - 1) E_u E_w.
 #include <algorithm>
+#include <array>
 #include <cstring>
+#include <mutex>
 
 #include "search.cuh"
 
@@ -204,15 +206,47 @@ int validate_query(const mp_search_query& q) {
   return MP_OK;
 }
 
+namespace {
+
+// Recently used candidate spaces, most recent first.  Building one enumerates
+// every chain of the depth bound and compiles it (milliseconds for thousands
+// of chains); a deployment queries the same machine over and over.
+constexpr size_t kSpaceCache = 8;
+std::mutex g_space_mu;
+std::vector<std::pair<std::array<int64_t, 3>, std::shared_ptr<const SpaceCore>>> g_spaces;
+
+std::shared_ptr<const SpaceCore> space_core(int64_t procs, int64_t g, int depth) {
+  const std::array<int64_t, 3> key{procs, g, depth};
+  {
+    std::lock_guard<std::mutex> lk(g_space_mu);
+    for (size_t i = 0; i < g_spaces.size(); ++i)
+      if (g_spaces[i].first == key) {
+        auto hit = g_spaces[i];
+        g_spaces.erase(g_spaces.begin() + (long)i);
+        g_spaces.insert(g_spaces.begin(), hit);
+        return hit.second;
+      }
+  }
+  auto core = std::make_shared<SpaceCore>();
+  const int64_t n = procs / g;
+  core->facts = ordered_factorisations(procs, 3);
+  core->chains = canonical_chains(n, g, depth);
+  core->progs.resize(core->chains.size());
+  for (size_t c = 0; c < core->chains.size(); ++c) core->progs[c] = compile_chain(n, g, core->chains[c]);
+  core->fdev.resize(core->facts.size());
+  for (size_t i = 0; i < core->facts.size(); ++i)
+    for (int t = 0; t < 3; ++t) core->fdev[i].f[t] = (uint32_t)core->facts[i][t];
+  std::lock_guard<std::mutex> lk(g_space_mu);
+  g_spaces.insert(g_spaces.begin(), {key, core});
+  if (g_spaces.size() > kSpaceCache) g_spaces.pop_back();
+  return core;
+}
+
+}  // namespace
+
 int prepare(const mp_search_query& q, SearchSpace& S) {
-  const int64_t n = q.procs / q.procs_per_node, g = q.procs_per_node;
-  S.facts = ordered_factorisations(q.procs, 3);
-  S.chains = canonical_chains(n, g, q.max_depth);
-  S.progs.resize(S.chains.size());
-  for (size_t c = 0; c < S.chains.size(); ++c) S.progs[c] = compile_chain(n, g, S.chains[c]);
-  S.fdev.resize(S.facts.size());
-  for (size_t i = 0; i < S.facts.size(); ++i)
-    for (int t = 0; t < 3; ++t) S.fdev[i].f[t] = (uint32_t)S.facts[i][t];
+  const int64_t n = q.procs / q.procs_per_node;
+  S.c = space_core(q.procs, q.procs_per_node, q.max_depth);
   S.words = (int)((n + 31) / 32);
   const size_t tab = align_up((size_t)q.procs * 2);
   int threads = 256;
@@ -227,30 +261,30 @@ namespace {
 
 int upload(const SearchSpace& S, cudaStream_t st, ChainProg** d_progs, Fact** d_facts, char** rest,
            size_t rest_bytes, int slot) {
-  const size_t pb = align_up(S.progs.size() * sizeof(ChainProg));
-  const size_t fb = align_up(S.fdev.size() * sizeof(Fact));
+  const size_t pb = align_up(S.c->progs.size() * sizeof(ChainProg));
+  const size_t fb = align_up(S.c->fdev.size() * sizeof(Fact));
   char* ws = (char*)workspace(pb + fb + rest_bytes, slot);
   if (!ws) return MP_ENOMEM;
   *d_progs = (ChainProg*)ws;
   *d_facts = (Fact*)(ws + pb);
   *rest = ws + pb + fb;
-  MP_CUDA_TRY(cudaMemcpyAsync(*d_progs, S.progs.data(), S.progs.size() * sizeof(ChainProg),
+  MP_CUDA_TRY(cudaMemcpyAsync(*d_progs, S.c->progs.data(), S.c->progs.size() * sizeof(ChainProg),
                               cudaMemcpyHostToDevice, st));
-  MP_CUDA_TRY(cudaMemcpyAsync(*d_facts, S.fdev.data(), S.fdev.size() * sizeof(Fact),
+  MP_CUDA_TRY(cudaMemcpyAsync(*d_facts, S.c->fdev.data(), S.c->fdev.size() * sizeof(Fact),
                               cudaMemcpyHostToDevice, st));
   return MP_OK;
 }
 
 void fill_result(const mp_search_query& q, const SearchSpace& S, const Key& k, mp_search_result& r) {
   std::memset(&r, 0, sizeof(r));
-  const uint64_t NC = S.chains.size();
+  const uint64_t NC = S.c->chains.size();
   r.index = (int64_t)k.idx;
   const uint64_t fr = k.idx / NC, c = k.idx % NC;
-  for (int t = 0; t < 3; ++t) r.f[t] = S.facts[fr][t];
+  for (int t = 0; t < 3; ++t) r.f[t] = S.c->facts[fr][t];
   r.chain_rank = (int64_t)c;
-  r.chain_len = (int32_t)S.chains[c].size();
+  r.chain_len = (int32_t)S.c->chains[c].size();
   for (int o = 0; o < r.chain_len; ++o) {
-    const CanonOp& op = S.chains[c][o];
+    const CanonOp& op = S.c->chains[c][o];
     mp_xform& x = r.chain[o];
     x.op = op.op == P_SPLIT ? MP_SPLIT : (op.op == P_MERGE ? MP_MERGE : MP_SWAP);
     x.i = op.p;
@@ -260,7 +294,7 @@ void fill_result(const mp_search_query& q, const SearchSpace& S, const Key& k, m
   r.primary_bytes = k.p * q.tile_bytes;
   r.secondary_bytes = k.s * q.tile_bytes;
   r.n_chains = (int64_t)NC;
-  r.n_factorisations = (int64_t)S.facts.size();
+  r.n_factorisations = (int64_t)S.c->facts.size();
   r.n_candidates = r.n_chains * r.n_factorisations;
 }
 
@@ -270,7 +304,7 @@ int exhaustive_search(const mp_search_query& q, mp_search_result* out, cudaStrea
   SearchSpace S;
   int rc = prepare(q, S);
   if (rc) return rc;
-  const uint64_t NC = S.chains.size();
+  const uint64_t NC = S.c->chains.size();
   ChainProg* d_progs;
   Fact* d_facts;
   char* rest;
@@ -281,7 +315,7 @@ int exhaustive_search(const mp_search_query& q, mp_search_result* out, cudaStrea
   Key* d_out = (Key*)(rest + align_up(NC * sizeof(Key)));
   if (S.smem > 48 * 1024)
     MP_CUDA_TRY(cudaFuncSetAttribute(k_search, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S.smem));
-  k_search<<<(unsigned)NC, S.threads, S.smem, st>>>(d_progs, d_facts, (int)S.facts.size(), (uint32_t)q.procs,
+  k_search<<<(unsigned)NC, S.threads, S.smem, st>>>(d_progs, d_facts, (int)S.c->facts.size(), (uint32_t)q.procs,
                                                     (uint32_t)q.M, (uint32_t)q.N, (uint32_t)q.K, S.words, NC,
                                                     (q.flags & MP_SEARCH_FULL) ? 1 : 0, chain_best);
   count_launch();
@@ -301,8 +335,8 @@ int candidate_costs_dev(const mp_search_query& q, const SearchSpace& S, const Ch
   if (n <= 0) return MP_OK;
   if (S.smem > 48 * 1024)
     MP_CUDA_TRY(cudaFuncSetAttribute(k_candidate_costs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S.smem));
-  k_candidate_costs<<<(unsigned)n, S.threads, S.smem, st>>>(d_progs, d_facts, (int)S.facts.size(), d_idx,
-                                                             (unsigned long long)S.chains.size(), (uint32_t)q.procs,
+  k_candidate_costs<<<(unsigned)n, S.threads, S.smem, st>>>(d_progs, d_facts, (int)S.c->facts.size(), d_idx,
+                                                             (unsigned long long)S.c->chains.size(), (uint32_t)q.procs,
                                                              (uint32_t)q.M, (uint32_t)q.N, (uint32_t)q.K, S.words,
                                                              q.tile_bytes, d_p, d_s);
   count_launch();
@@ -338,7 +372,7 @@ extern "C" int mp_candidate_costs(const mp_search_query* query, const int64_t* i
   SearchSpace S;
   rc = prepare(*query, S);
   if (rc) return rc;
-  const uint64_t NC = S.chains.size(), NF = S.facts.size();
+  const uint64_t NC = S.c->chains.size(), NF = S.c->facts.size();
   const bool idx_dev = is_device_pointer(indices);
   const bool p_dev = is_device_pointer(primary), s_dev = is_device_pointer(secondary);
   std::vector<int64_t> host_idx;

@@ -2,6 +2,7 @@
 // evaluation) and mlp.cu (candidate features for the learned scorer).
 #pragma once
 
+#include <memory>
 #include <vector>
 
 #include "engine.h"
@@ -301,11 +302,18 @@ __device__ __forceinline__ void build_table(const ChainProg& cp, uint16_t* tab, 
 
 // ----------------------------------------------------------------- host side
 
-struct SearchSpace {
+// The candidate space of one machine shape and depth bound: factorisations,
+// chains and their compiled programs.  Immutable once built and shared by
+// every query on the same (processors, processors per node, depth).
+struct SpaceCore {
   std::vector<std::vector<int64_t>> facts;
   std::vector<std::vector<CanonOp>> chains;
   std::vector<ChainProg> progs;
   std::vector<Fact> fdev;
+};
+
+struct SearchSpace {
+  std::shared_ptr<const SpaceCore> c;
   int words = 0;
   int threads = 0;
   size_t smem = 0;

@@ -55,7 +55,18 @@ class mp_machine(ctypes.Structure):
 
 class mp_xform(ctypes.Structure):
     _fields_ = [("op", ctypes.c_int32), ("i", ctypes.c_int32), ("j", ctypes.c_int32),
-                ("k", ctypes.c_int32), ("d", ctypes.c_int64), ("T", ctypes.c_int64 * 4)]
+                ("k", ctypes.c_int32), ("d", ctypes.c_int64), ("T", ctypes.c_int64 * 4),
+                ("h", ctypes.c_int32 * 4), ("transpose", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class mp_halo(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int32), ("width", ctypes.c_int32 * 4), ("reserved", ctypes.c_int32),
+                ("bytes", ctypes.c_uint64 * 4)]
+
+
+HALO_FACES = 0
+HALO_ELEMENTS = 1
+MAX_HALO_WIDTH = 16
 
 
 class mp_dist(ctypes.Structure):
@@ -101,6 +112,8 @@ def lib():
                 "mp_map_points": (I, [V, V, V, I, V, V, V, V]),
                 "mp_map_points_noalloc": (I, [V, V, V, I, V, V, V, V]),
                 "mp_comm_volume": (I, [V, V, V, I, V, V, V, V, V]),
+                "mp_halo_volume": (I, [V, V, V, I, V, V, V, V, V]),
+                "mp_greedy_grid": (I, [I64, I, V]),
                 "mp_decompose_search": (I, [V, I, V, V]),
                 "mp_candidate_costs": (I, [V, V, I64, V, V, V]),
                 "mp_plan": (I, [V, V, V, I, V, V, V, V, V, I]),
@@ -180,6 +193,11 @@ def make_chain(chain):
             x.i, x.k = int(op[1]), len(T)
             for m, v in enumerate(T):
                 x.T[m] = int(v)
+            if len(op) > 3 and op[3] is not None:
+                for m, v in enumerate(op[3]):
+                    x.h[m] = int(v)
+            if len(op) > 4:
+                x.transpose = sum(1 << int(m) for m in op[4])
         elif name == "balance_split":
             x.i, x.k = int(op[1]), int(op[2])
         else:
@@ -266,6 +284,29 @@ def comm_volume(L, machine, chain, dist, face_bytes, total, recv=None, stream=No
     _check(rc, "mp_comm_volume")
 
 
+def halo_volume(L, machine, chain, dist, width, elem_bytes, total, recv=None, elements=True, stream=None):
+    """mp_halo_volume: the element count with per-dimension halo widths
+    (elements=True) or the directed face count."""
+    sp, mc, ds = make_space(L), make_machine(machine), make_dist(dist)
+    ch, n = make_chain(chain)
+    h = mp_halo()
+    h.mode = HALO_ELEMENTS if elements else HALO_FACES
+    for t, v in enumerate(width):
+        h.width[t] = int(v)
+    for t, v in enumerate(elem_bytes):
+        h.bytes[t] = int(v)
+    rc = lib().mp_halo_volume(ctypes.byref(sp), ctypes.byref(mc), ch, n, ctypes.byref(ds), ctypes.byref(h),
+                              _ptr(total), _ptr(recv), _stream(stream))
+    _check(rc, "mp_halo_volume")
+
+
+def greedy_grid(d, k):
+    """Algorithm A1's processor grid (host only)."""
+    out = (ctypes.c_int64 * 4)()
+    _check(lib().mp_greedy_grid(int(d), int(k), out), "mp_greedy_grid")
+    return tuple(out[m] for m in range(k))
+
+
 def plan(L, machine, chain, dist):
     """(final shape, expanded primitives) -- host planning only, no GPU."""
     sp, mc, ds = make_space(L), make_machine(machine), make_dist(dist)
@@ -308,7 +349,12 @@ def xform_tuple(x):
     if name in ("merge", "swap"):
         return (name, x.i, x.j)
     if name == "decompose":
-        return ("decompose", x.i, tuple(x.T[m] for m in range(x.k)))
+        T = tuple(x.T[m] for m in range(x.k))
+        h = tuple(x.h[m] for m in range(x.k))
+        tr = tuple(m for m in range(x.k) if (x.transpose >> m) & 1)
+        if any(h) or tr:
+            return ("decompose", x.i, T, h if any(h) else None, tr)
+        return ("decompose", x.i, T)
     return ("balance_split", x.i, x.k)
 
 
@@ -453,8 +499,11 @@ def gemm_bf16(A, B, C, stream=None):
 
 
 class mp_learned_stats(ctypes.Structure):
-    _fields_ = [("n_scored", ctypes.c_int64), ("n_exact", ctypes.c_int64), ("certified", ctypes.c_int32),
-                ("fallback", ctypes.c_int32), ("margin", ctypes.c_double)]
+    _fields_ = [("n_scored", ctypes.c_int64), ("n_exact", ctypes.c_int64), ("n_selected", ctypes.c_int64),
+                ("certified", ctypes.c_int32), ("fallback", ctypes.c_int32), ("rounds", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("margin", ctypes.c_double), ("max_overestimate", ctypes.c_double),
+                ("ms_prepare", ctypes.c_double), ("ms_model", ctypes.c_double), ("ms_exact", ctypes.c_double),
+                ("ms_fallback", ctypes.c_double)]
 
 
 LEARNED_NO_FALLBACK = 1
@@ -521,8 +570,11 @@ class MLP:
         _check(lib().mp_learned_search(self._h, ctypes.byref(q), int(K), flags, ctypes.byref(out),
                                        ctypes.byref(st), _stream(stream)), "mp_learned_search")
         res = _search_result(out)
-        res.update({"n_scored": st.n_scored, "n_exact": st.n_exact, "certified": bool(st.certified),
-                    "fallback": bool(st.fallback), "margin": st.margin})
+        res.update({"n_scored": st.n_scored, "n_exact": st.n_exact, "n_selected": st.n_selected,
+                    "certified": bool(st.certified), "fallback": bool(st.fallback), "rounds": st.rounds,
+                    "margin": st.margin, "max_overestimate": st.max_overestimate,
+                    "ms": {"prepare": st.ms_prepare, "model": st.ms_model, "exact": st.ms_exact,
+                           "fallback": st.ms_fallback}})
         return res
 
     def scores(self, query, scores, features=None, stream=None):

@@ -183,3 +183,29 @@ def search_training_queries(count: int, first_index: int = 20000):
         out.append({"name": f"train-{q}", "MNK": (M, N, K), "machine": (P // 8, 8),
                     "max_depth": 3, "tile_bytes": 512 * 512 * 4})
     return out
+
+
+# ------------------------------------------------------ decompose vs greedy
+#
+# The stencil grid of the paper's decompose study (Sec. 6, "Performance Study
+# of the Decompose Primitive"): six aspect ratios 1:1 .. 1:32, five task-space
+# sizes per node (1e6 .. 4e8 points), 4 .. 128 GPUs in powers of two at four
+# GPUs per node -- 180 configurations of a 2-D task space.
+
+STUDY_RATIOS = (1, 2, 4, 8, 16, 32)
+STUDY_AREAS = (10 ** 6, 10 ** 7, 10 ** 8, 2 * 10 ** 8, 4 * 10 ** 8)
+STUDY_GPUS = (4, 8, 16, 32, 64, 128)
+STUDY_GPUS_PER_NODE = 4
+
+
+def stencil_study_configs():
+    """(X, r X) task spaces with about area x nodes points on (G / 4, 4)."""
+    out = []
+    for r in STUDY_RATIOS:
+        for area in STUDY_AREAS:
+            for G in STUDY_GPUS:
+                nodes = G // STUDY_GPUS_PER_NODE
+                X = max(1, int(round(math.sqrt(area * nodes / r))))
+                out.append({"name": f"stencil-1:{r}-{area}-{G}", "L": (X, r * X),
+                            "machine": (nodes, STUDY_GPUS_PER_NODE), "ratio": r, "area": area, "gpus": G})
+    return out

@@ -45,7 +45,14 @@ def _random_case(rng):
     chain = O.chain_from_draws(*machine, draws)
     if rng.randint(0, 3) == 0:
         kk = rng.randint(1, 3)
-        chain = chain + [("decompose", 0, tuple(rng.randint(1, 30) for _ in range(kk)))]
+        T = tuple(rng.randint(1, 30) for _ in range(kk))
+        r = rng.randint(0, 3)
+        if r == 0:     # the appendix's generalised objective: widths and transposes
+            h = tuple(rng.randint(0, 6) for _ in range(kk))
+            tr = tuple(m for m in range(kk) if rng.randint(0, 2) == 0)
+            chain = chain + [("decompose", 0, T, h, tr)]
+        else:
+            chain = chain + [("decompose", 0, T)]
     if rng.randint(0, 5) == 0:
         chain = chain + [("balance_split", 0, rng.randint(1, 3))]
     kind = rng.choice(W.DIST_KINDS)
@@ -103,6 +110,8 @@ def test_invalid_plans_rejected():
         (((4, 4), (2, 2), [("merge", 0, 2)], ("block",)), 1),
         (((4, 4), (2, 2), [("swap", 1, 1)], ("block",)), 1),
         (((4, 4), (2, 2), [("decompose", 0, (0, 2))], ("block",)), 1),
+        (((4, 4), (2, 2), [("decompose", 0, (4, 2), (1, -1))], ("block",)), 1),
+        (((4, 4), (2, 2), [("decompose", 0, (4, 2), None, (2,))], ("block",)), 1),
         (((4, 4), (2, 2), [("balance_split", 0, 5)], ("block",)), 1),
         (((4, 4), (2, 2), [], ("block_cyclic", 0)), 1),
         (((4, 4), (0, 2), [], ("block",)), 1),
@@ -130,3 +139,26 @@ def test_invalid_search_queries_rejected():
               N.make_query(4, 4, 4, 1 << 15, 8), N.make_query(1 << 21, 4, 4, 8, 2)]:
         arr = (N.mp_search_query * 1)(q)
         assert lib.mp_decompose_search(arr, 1, out, None) != 0
+
+
+def test_weighted_decompose_matches_oracle():
+    # the appendix's generalised objective, engine planner vs oracle
+    rng = W.rng(905)
+    for _ in range(300):
+        k = rng.randint(1, 4)
+        d = rng.choice((6, 12, 16, 24, 36, 48, 64, 96, 128, 360, 512, 720, 1024))
+        T = tuple(rng.randint(1, 4096) for _ in range(k))
+        h = tuple(rng.randint(0, 16) for _ in range(k))
+        tr = tuple(m for m in range(k) if rng.randint(0, 2) == 0)
+        chain = [("merge", 0, 1), ("decompose", 0, T, h, tr)]
+        shape, _ = N.plan((8,) * k, (d, 1), chain, ("block",))
+        hw = h if any(h) else (1,) * k
+        assert shape == O.decompose(d, T, h=hw, transposes=tr), (d, T, h, tr)
+
+
+def test_greedy_grid_matches_oracle():
+    # Algorithm A1, engine vs oracle (the oracle's version is pinned to the
+    # paper's Sec. 4.1 example and the Sec. 4.3 counterexample)
+    for d in list(range(1, 300)) + [512, 720, 2520, 3600, 4096, 65536, 9699690]:
+        for k in (1, 2, 3, 4):
+            assert N.greedy_grid(d, k) == O.greedy(d, k), (d, k)
