@@ -29,7 +29,8 @@ namespace {
 
 constexpr uint32_t kBatchMaxP = 16384;
 constexpr uint64_t kBatchTableMax = 65536;   // tabled coordinates per dimension
-constexpr uint64_t kFuseTarget = 4096;        // fused fast dimension: rows of at least this many points
+constexpr uint64_t kFuseTarget = 2048;        // fused rows: at least this many points when the extents allow
+constexpr uint64_t kFuseMax = 4096;           // fused rows staged in shared memory: at most this many points
 
 struct QDesc : MapCore {
   Tabs tabs;            // offsets relative to tab_base
@@ -40,13 +41,15 @@ struct QDesc : MapCore {
   uint32_t prim_off;    // primitives in the primitive pool
   int32_t mode;         // IdsMode
   uint64_t face[4];
-  // M_FUSED: dimensions fuse_m..k-1 form one fast dimension of Lf points
-  // whose contributions sit at fuse_off (relative to tab_base)
+  // M_FUSED: dimensions fuse_m..k-1 form rows of Lf points; rsrc (RowSrc)
+  // says where a row offset's contribution comes from (a table at fuse_off,
+  // relative to tab_base, or the last dimension's components)
   int32_t fuse_m;
   uint32_t Lf;
   Div32 divLf;
   uint64_t fuse_off;
-  uint64_t pad_;
+  int32_t rsrc;
+  int32_t pad_;
 };
 static_assert(sizeof(QDesc) % 16 == 0, "QDesc is copied in 16-byte words");
 
@@ -84,7 +87,7 @@ __global__ void __launch_bounds__(kThreads) k_b_tables(const QDesc* __restrict__
     const uint32_t q = find_query(tab_pref, n, e);
     const QDesc& Q = qd[q];
     const uint64_t r = e - Q.tab_base;
-    if (Q.mode == M_FUSED && r >= Q.fuse_off) {
+    if (Q.mode == M_FUSED && Q.rsrc <= R_TAB4 && r >= Q.fuse_off) {
       // fused row offset x -> coordinates of dimensions fuse_m..k-1 (C order)
       uint64_t x = r - Q.fuse_off;
       if (x >= Q.Lf) continue;
@@ -174,7 +177,7 @@ __global__ void __launch_bounds__(kThreads) k_b_ids(const QDesc* __restrict__ qd
         const int last = Q.k - 1;
         const uint32_t* cg = tabpool + Q.tab_base + Q.tabs.off[last];
         for (uint32_t i = threadIdx.x; i < (uint32_t)Q.L[last]; i += blockDim.x) Cs[i] = __ldg(cg + i);
-      } else if (Q.mode == M_FUSED) {
+      } else if (Q.mode == M_FUSED && Q.rsrc <= R_TAB4) {
         const uint32_t* cg = tabpool + Q.tab_base + Q.fuse_off;
         for (uint32_t i = threadIdx.x; i < Q.Lf; i += blockDim.x) Cs[i] = __ldg(cg + i);
       }
@@ -191,10 +194,16 @@ __global__ void __launch_bounds__(kThreads) k_b_ids(const QDesc* __restrict__ qd
     if (Q.lc) {
       ids_range_lc<uint32_t, true>(Q, Ts, wb, we, lane, vec_ok, qids);
     } else if (Q.mode == M_FUSED) {
-      if (Q.Lf % 4 == 0)
-        ids_range_fused<true>(Q, Q.tabs, Ts, Cs, ctab, Q.fuse_m, Q.Lf, Q.divLf, wb, we, lane, vec_ok, qids);
-      else
-        ids_range_fused<false>(Q, Q.tabs, Ts, Cs, ctab, Q.fuse_m, Q.Lf, Q.divLf, wb, we, lane, vec_ok, qids);
+#define MP_ROWS(SRC) ids_range_rows<SRC>(Q, Q.tabs, Ts, Cs, ctab, Q.fuse_m, Q.Lf, Q.divLf, wb, we, lane, vec_ok, qids)
+      switch (Q.rsrc) {
+        case R_TAB4: MP_ROWS(R_TAB4); break;
+        case R_TAB: MP_ROWS(R_TAB); break;
+        case R_BLOCK: MP_ROWS(R_BLOCK); break;
+        case R_CYCLIC: MP_ROWS(R_CYCLIC); break;
+        case R_BCYC: MP_ROWS(R_BCYC); break;
+        default: MP_ROWS(R_HIER); break;
+      }
+#undef MP_ROWS
     } else if (Q.mode == M_FAST_SMEM) {
       ids_range<uint32_t, M_FAST_SMEM, true>(Q, Q.tabs, Ts, Cs, ctab, wb, we, lane, vec_ok, qids);
     } else if (Q.mode == M_FAST_GLOBAL) {
@@ -449,26 +458,34 @@ extern "C" int mp_batch_create(const mp_query* queries, int n, mp_batch** out) {
     }
     const int last = Q.k - 1;
     const bool aligned = !Q.lc && Q.L[last] % 4 == 0 && Q.tabs.has[last];
-    Q.mode = !aligned ? M_GENERAL : (Q.L[last] <= kSmemLastMax ? M_FAST_SMEM : M_FAST_GLOBAL);
-    if (!Q.lc && (Q.mode == M_GENERAL || (Q.mode == M_FAST_SMEM && Q.L[last] < kFuseTarget))) {
-      // short or unaligned rows: fuse trailing dimensions into one fast
-      // dimension of at most kSmemLastMax points (at least kFuseTarget when
-      // the extents allow, so that a lane meets a row end rarely), with its
-      // contributions in one table
+    Q.mode = M_GENERAL;
+    if (aligned && Q.L[last] > kFuseMax) {
+      Q.mode = M_FAST_GLOBAL;   // long aligned rows: 16-byte loads of the last table from L2
+    } else if (!Q.lc) {
+      // rows of the trailing dimensions fused into one table of at most
+      // kFuseMax points (at least kFuseTarget when the extents allow), staged
+      // in shared memory; rows longer than that (the last extent alone) take
+      // their contribution from the last dimension's components in place
       int m = last;
       uint64_t Lf = Q.L[last];
-      while (m > 0 && Lf < kFuseTarget && Lf * Q.L[m - 1] <= kSmemLastMax) Lf *= Q.L[--m];
-      if (Lf <= kSmemLastMax) {
-        Q.mode = M_FUSED;
-        Q.fuse_m = m;
-        Q.Lf = (uint32_t)Lf;
-        Q.divLf = make_div32((uint32_t)Lf);
+      while (m > 0 && Lf < kFuseTarget && Lf * Q.L[m - 1] <= kFuseMax) Lf *= Q.L[--m];
+      Q.mode = M_FUSED;
+      Q.fuse_m = m;
+      Q.Lf = (uint32_t)Lf;
+      Q.divLf = make_div32((uint32_t)Lf);
+      if (Lf <= kFuseMax) {
+        Q.rsrc = Lf % 4 == 0 ? R_TAB4 : R_TAB;
         Q.fuse_off = tabq;
         tabq += (Lf + 3) & ~uint64_t(3);
+      } else if (Q.ncomp[last] == 2) {
+        Q.rsrc = R_HIER;
+      } else {
+        const int kind = Q.comp[last][0].kind;
+        Q.rsrc = kind == C_BLOCK ? R_BLOCK : (kind == C_CYCLIC ? R_CYCLIC : R_BCYC);
       }
     }
     if (Q.mode == M_FAST_SMEM) b->maxC = std::max<uint32_t>(b->maxC, (uint32_t)Q.L[last]);
-    if (Q.mode == M_FUSED) b->maxC = std::max<uint32_t>(b->maxC, Q.Lf);
+    if (Q.mode == M_FUSED && Q.rsrc <= R_TAB4) b->maxC = std::max<uint32_t>(b->maxC, Q.Lf);
     b->maxP = std::max(b->maxP, Q.P);
     Q.p_off = (uint32_t)P_acc;
     Q.cnt_off = (uint32_t)J_acc;

@@ -339,18 +339,49 @@ __device__ __noinline__ uint32_t row_base_m(const MapCore& D, const Tabs& tabs, 
   return base;
 }
 
-// ids for the 4-point groups [gbeg, gend) of one warp when the trailing
-// dimensions m..k-1 (Lf points per row) are fused: Cf[x] (shared memory) is
-// the contribution of the fused coordinates of row offset x.  Groups inside
-// a row read four table entries (one 16-byte load when ALIGNED, i.e.
-// Lf % 4 == 0, where no group crosses a row end); a group that crosses a row
-// end walks its points.  32-bit indices (the batched launches stay below 2^31
+// Where ids_range_rows finds the contribution of a row offset x:
+//   R_TAB / R_TAB4  fused table Cf in shared memory (R_TAB4: Lf % 4 == 0, one
+//                   16-byte load per group)
+//   R_BLOCK, R_CYCLIC, R_BCYC, R_HIER  computed from the last dimension's
+//                   components (rows = the last dimension, no table)
+enum RowSrc : int { R_TAB = 0, R_TAB4 = 1, R_BLOCK = 2, R_CYCLIC = 3, R_BCYC = 4, R_HIER = 5 };
+
+template <int SRC>
+__device__ __forceinline__ uint32_t row_contrib(const MapCore& D, const uint32_t* __restrict__ Cf, uint32_t x) {
+  if (SRC == R_TAB || SRC == R_TAB4) return Cf[x];
+  const Comp& c0 = D.comp[D.k - 1][0];
+  uint32_t a;
+  if (SRC == R_BLOCK || SRC == R_HIER) {
+    a = c0.narrow ? div32(x * c0.s, c0.divL32) : (uint32_t)div64((uint64_t)x * c0.s, c0.divL);
+  } else if (SRC == R_CYCLIC) {
+    uint32_t q;
+    divmod32(x, c0.divs, q, a);
+  } else {
+    uint32_t q;
+    divmod32(div32(x, c0.divb), c0.divs, q, a);
+  }
+  uint32_t v = a * c0.sigma;
+  if (SRC == R_HIER) {
+    const Comp& c1 = D.comp[D.k - 1][1];
+    uint32_t q, r;
+    divmod32(x, c1.divs, q, r);
+    v += r * c1.sigma;
+  }
+  return v;
+}
+
+// ids for the 4-point groups [gbeg, gend) of one warp, row by row: the
+// dimensions m..k-1 form rows of Lf points (fused into one table, or the last
+// dimension alone with its contribution computed in place), the dimensions
+// before m give the row base.  Groups inside a row take four contributions;
+// a group that crosses a row end walks its points, and the next row's base
+// it computes is kept for the wrap.  32-bit indices (launches below 2^31
 // points).
-template <bool ALIGNED>
-__device__ __forceinline__ void ids_range_fused(const MapCore& D, const Tabs& tabs, const uint32_t* __restrict__ T,
-                                                const uint32_t* __restrict__ Cf, const uint32_t* __restrict__ ctab,
-                                                int m, uint32_t Lf, Div32 divLf, uint32_t gbeg, uint32_t gend,
-                                                int lane, int vec_ok, int32_t* __restrict__ ids) {
+template <int SRC>
+__device__ __forceinline__ void ids_range_rows(const MapCore& D, const Tabs& tabs, const uint32_t* __restrict__ T,
+                                               const uint32_t* __restrict__ Cf, const uint32_t* __restrict__ ctab,
+                                               int m, uint32_t Lf, Div32 divLf, uint32_t gbeg, uint32_t gend,
+                                               int lane, int vec_ok, int32_t* __restrict__ ids) {
   const uint32_t N = (uint32_t)D.npoints;
   uint32_t g = gbeg + (uint32_t)lane;
   if (g >= gend) return;
@@ -358,15 +389,16 @@ __device__ __forceinline__ void ids_range_fused(const MapCore& D, const Tabs& ta
   uint32_t row, x;
   divmod32(lin0, divLf, row, x);
   uint32_t base = row_base_m<uint32_t>(D, tabs, ctab, row, m);
+  uint32_t next_row = 0xFFFFFFFFu, next_base = 0;   // a row base computed ahead of the wrap
   for (; g < gend; g += 32, lin0 += 128) {
     const int cnt = N - lin0 < 4 ? (int)(N - lin0) : 4;
     uint32_t v[4] = {0, 0, 0, 0};
-    if (ALIGNED) {
+    if (SRC == R_TAB4) {
       const uint4 c = *reinterpret_cast<const uint4*>(Cf + x);
       v[0] = T[base + c.x]; v[1] = T[base + c.y]; v[2] = T[base + c.z]; v[3] = T[base + c.w];
     } else if (x + 4 <= Lf) {
 #pragma unroll
-      for (int i = 0; i < 4; ++i) v[i] = T[base + Cf[x + i]];
+      for (int i = 0; i < 4; ++i) v[i] = T[base + row_contrib<SRC>(D, Cf, x + i)];
     } else {
       uint32_t xi = x, ri = row, bi = base;
       for (int i = 0; i < cnt; ++i) {
@@ -374,8 +406,10 @@ __device__ __forceinline__ void ids_range_fused(const MapCore& D, const Tabs& ta
           xi -= Lf;
           ri += 1;
           bi = row_base_m<uint32_t>(D, tabs, ctab, ri, m);
+          next_row = ri;
+          next_base = bi;
         }
-        v[i] = T[bi + Cf[xi]];
+        v[i] = T[bi + row_contrib<SRC>(D, Cf, xi)];
         ++xi;
       }
     }
@@ -395,7 +429,7 @@ __device__ __forceinline__ void ids_range_fused(const MapCore& D, const Tabs& ta
         row += q;
         x = r;
       }
-      base = row_base_m<uint32_t>(D, tabs, ctab, row, m);
+      base = row == next_row ? next_base : row_base_m<uint32_t>(D, tabs, ctab, row, m);
     }
   }
 }

@@ -4,12 +4,14 @@
 //              closed-form primary cost relative to the best one, the
 //              chain's transforms, where the chain's node boundaries fall
 //              along each final dimension)
-//   k_score    fused tcgen05 inference: a persistent CTA of 256 threads
-//              writes the features of 128 candidates into shared memory,
-//              runs the three hidden layers (weights streamed from L2 in
-//              64-wide K chunks, accumulator in tensor memory, each thread's
-//              epilogue handles its own row) and writes one score per
-//              candidate
+//   scoring    k_feat_img writes the candidates' features as swizzled BF16
+//              operand tiles (full occupancy hides the feature arithmetic's
+//              latency); k_mlp_img, one persistent CTA of 256 threads per
+//              SM, bulk-copies two tiles and the nine weight chunk images
+//              (double-buffered) into shared memory and runs the three
+//              hidden layers as tcgen05 MMAs with FP32 accumulators in 512
+//              TMEM columns; warps 0-3 and 4-7 run the epilogues of the two
+//              tiles and the output dot product
 //   top-K      65536-bin histogram of the order-preserving score keys, a
 //              threshold bin, and a compaction of the candidates at or below
 //   exact      the top-K are re-evaluated by the exact cost kernel; the
@@ -157,49 +159,63 @@ __global__ void k_features_idx(const __grid_constant__ QInfo Q, const ChainProg*
   if (target) target[i] = target_of(pbytes[i] / Q.tile_bytes, sbytes[i] / Q.tile_bytes, Q.pmin);
 }
 
-// ------------------------------------------------------------ fused scoring
+// ------------------------------------------------------------ scoring in two kernels
+//
+// k_feat_img writes the features of a run of scored candidates as BF16
+// operand images (one 16 KB K-major, 128-byte swizzled tile of 128 rows per
+// 128 candidates; rows past the end are zero) at full occupancy, where the
+// latency of the feature arithmetic (chain walks, table loads) hides behind
+// many resident warps.  k_mlp_img then runs the three layers on those tiles:
+// a persistent CTA per SM takes two tiles (256 candidates) per pass, bulk-
+// copies them and the nine 32 KB weight chunk images into shared memory
+// (weights double-buffered, the next chunk in flight while the current
+// chunk's MMAs run), accumulates both tiles in 512 TMEM columns, and runs the
+// epilogues with warps 0-3 on the first tile and warps 4-7 on the second.
 
-__device__ __forceinline__ void stage_w(uint8_t* dst, const bf16* __restrict__ W, int ld, int k0) {
-  // 256 rows x 64 columns of W (row-major, leading dimension ld) into a
-  // swizzled K-major tile
-  for (int i = threadIdx.x; i < 256 * 8; i += blockDim.x) {
-    const int r = i >> 3, c = i & 7;
-    const uint4 v = __ldg(reinterpret_cast<const uint4*>(W + (size_t)r * ld + k0 + c * 8));
-    *reinterpret_cast<uint4*>(dst + tc::sw128_offset(r, c * 8)) = v;
+constexpr uint32_t kTileBytes = 128 * 128;   // 128 rows x 64 BF16
+
+__global__ void __launch_bounds__(128) k_feat_img(const __grid_constant__ QInfo Q, const ChainProg* __restrict__ progs,
+                                                  const Fact* __restrict__ facts, const float* __restrict__ chainfeat,
+                                                  const uint32_t* __restrict__ flist, unsigned long long c0,
+                                                  unsigned long long n, uint8_t* __restrict__ img) {
+  const unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;   // < padded n
+  float x[64];
+  if (i < n) {
+    const unsigned long long cand = c0 + i;
+    unsigned long long idx = cand;
+    if (flist) {
+      const unsigned long long j = cand / Q.nchains;
+      idx = (unsigned long long)flist[j] * Q.nchains + (cand - j * Q.nchains);
+    }
+    candidate_features(Q, progs, facts, chainfeat, idx, x, nullptr);
+  } else {
+    for (int j = 0; j < 64; ++j) x[j] = 0.f;
+  }
+  uint8_t* tile = img + (i / 128) * kTileBytes;
+  const uint32_t row = (uint32_t)(i % 128);
+#pragma unroll
+  for (int j = 0; j < 64; j += 8) {
+    uint32_t w[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      __nv_bfloat162 h2 = __floats2bfloat162_rn(x[j + 2 * e], x[j + 2 * e + 1]);
+      w[e] = *reinterpret_cast<uint32_t*>(&h2);
+    }
+    *reinterpret_cast<uint4*>(tile + tc::sw128_offset(row, j)) = make_uint4(w[0], w[1], w[2], w[3]);
   }
 }
 
-// issue 4 MMAs (K = 64) of A (one swizzle atom) x B (one atom of 256 rows)
-__device__ __forceinline__ void mma_chunk(uint32_t tmem, uint32_t a_addr, uint32_t b_addr, bool first,
-                                          uint64_t* bar) {
-  constexpr uint32_t idesc = tc::idesc_bf16(128, 256);
-#pragma unroll
-  for (int kk = 0; kk < 4; ++kk)
-    tc::mma_bf16(tmem, tc::sdesc_sw128(a_addr + kk * 32), tc::sdesc_sw128(b_addr + kk * 32), idesc,
-                 (first && kk == 0) ? 0u : 1u);
-  tc::mma_commit(bar);
-}
-
-// Waits for the committed MMAs; the result is the same for the whole CTA.
-__device__ __forceinline__ bool sync_mma(uint64_t* bar, uint32_t& phase) {
-  const bool ok = tc::mbar_wait(bar, phase, kWaitLimit);
-  phase ^= 1;
-  tc::fence_after_sync();
-  return __syncthreads_and(ok) != 0;
-}
-
-// Epilogue of a hidden layer.  Warp w reads accumulator rows 32 (w % 4) ..
-// + 31 (its TMEM lane quadrant) and columns 128 (w / 4) .. + 127: bias,
-// ReLU, BF16, into the activation tile (K-major, four swizzle atoms of 64
-// columns) as the next layer's A operand.
-__device__ __forceinline__ void epilogue_hidden(uint32_t tmem, const float* __restrict__ bias, uint8_t* H) {
+// Epilogue of one tile's hidden layer: rows 32 (w % 4) + lane of the tile,
+// all 256 columns of its accumulator (TMEM columns col0 ..), bias and ReLU,
+// BF16 into the tile's activation atoms.
+__device__ __forceinline__ void epilogue_rows(uint32_t tmem, uint32_t col0, const float* __restrict__ bias,
+                                              uint8_t* H) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int row = (warp & 3) * 32 + lane, half = warp >> 2;
+  const int row = (warp & 3) * 32 + lane;
 #pragma unroll 1
-  for (int cc = 0; cc < 4; ++cc) {
-    const int c = half * 4 + cc;   // 32-column block
+  for (int c = 0; c < 8; ++c) {
     uint32_t r[32];
-    tc::tmem_ld32(tmem + ((uint32_t)((warp & 3) * 32) << 16) + c * 32, r);
+    tc::tmem_ld32(tmem + ((uint32_t)((warp & 3) * 32) << 16) + col0 + c * 32, r);
     tc::tmem_ld_wait();
     uint8_t* atom = H + (c >> 1) * 16384;
 #pragma unroll
@@ -207,8 +223,8 @@ __device__ __forceinline__ void epilogue_hidden(uint32_t tmem, const float* __re
       uint32_t w[4];
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
-        const float a = fmaxf(__uint_as_float(r[j + 2 * e]) + __ldg(bias + c * 32 + j + 2 * e), 0.f);
-        const float b = fmaxf(__uint_as_float(r[j + 2 * e + 1]) + __ldg(bias + c * 32 + j + 2 * e + 1), 0.f);
+        const float a = fmaxf(__uint_as_float(r[j + 2 * e]) + bias[c * 32 + j + 2 * e], 0.f);
+        const float b = fmaxf(__uint_as_float(r[j + 2 * e + 1]) + bias[c * 32 + j + 2 * e + 1], 0.f);
         __nv_bfloat162 h2 = __floats2bfloat162_rn(a, b);
         w[e] = *reinterpret_cast<uint32_t*>(&h2);
       }
@@ -217,127 +233,149 @@ __device__ __forceinline__ void epilogue_hidden(uint32_t tmem, const float* __re
   }
 }
 
-// 256 threads: threads 0..127 build the features of the tile's 128 rows;
-// all eight warps stage weights and share the epilogues (column halves).
-// Shared memory: H (four 16 KB atoms; atom 0 doubles as the layer-1 input X)
-// and one 32 KB weight chunk -- two CTAs per SM.
-__global__ void __launch_bounds__(256) k_score(const __grid_constant__ QInfo Q, const ChainProg* __restrict__ progs,
-                                               const Fact* __restrict__ facts, const float* __restrict__ chainfeat,
-                                               const bf16* __restrict__ W1b, const bf16* __restrict__ W2b,
-                                               const bf16* __restrict__ W3b, const float* __restrict__ P,
-                                               const uint32_t* __restrict__ flist, unsigned long long n,
-                                               float* __restrict__ scores, int* __restrict__ status) {
+constexpr size_t kMlpSmem = 2 * 65536 + 2 * mlpk::kWChunkBytes + 1024;
+
+__global__ void __launch_bounds__(256, 1) k_mlp_img(const uint8_t* __restrict__ img, uint32_t ntiles,
+                                                    const uint8_t* __restrict__ Wimg, const float* __restrict__ P,
+                                                    unsigned long long n, float* __restrict__ scores,
+                                                    int* __restrict__ status) {
   extern __shared__ uint8_t smem_raw[];
-  __shared__ uint64_t bar;
+  __shared__ uint64_t wbar[2], xbar, mbar;
   __shared__ uint32_t tmem_slot;
-  __shared__ float s_part[128];
+  __shared__ float sb[4][256];   // b1, b2, b3, w4
   uint8_t* base = smem_raw + ((1024 - (tc::smem_u32(smem_raw) & 1023)) & 1023);
-  uint8_t* Hs = base;                 // 128 x 256 (four atoms, 64 KB); atom 0 = X during layer 1
-  uint8_t* Ws = base + 65536;         // 256 x 64 weight chunk (32 KB)
+  uint8_t* H[2] = {base, base + 65536};                                 // two tiles x four atoms
+  uint8_t* Wb[2] = {base + 131072, base + 131072 + mlpk::kWChunkBytes};  // weight chunk buffers
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const float* b1 = P + mlpk::O_B1;
-  const float* b2 = P + mlpk::O_B2;
-  const float* b3 = P + mlpk::O_B3;
-  const float* w4 = P + mlpk::O_W4;
+  const uint32_t npass = ntiles > 2 * blockIdx.x ? (ntiles - 2 * blockIdx.x + 2 * gridDim.x - 1) / (2 * gridDim.x) : 0;
+  const uint32_t total_chunks = npass * mlpk::kWChunks;
+  for (int i = threadIdx.x; i < 256; i += blockDim.x) {
+    sb[0][i] = __ldg(P + mlpk::O_B1 + i);
+    sb[1][i] = __ldg(P + mlpk::O_B2 + i);
+    sb[2][i] = __ldg(P + mlpk::O_B3 + i);
+    sb[3][i] = __ldg(P + mlpk::O_W4 + i);
+  }
   const float b4 = __ldg(P + mlpk::O_B4);
   if (warp == 0) {
-    tc::tmem_alloc(&tmem_slot, 256);
+    tc::tmem_alloc(&tmem_slot, 512);
     tc::tmem_relinquish();
   }
   if (threadIdx.x == 0) {
-    tc::mbar_init(&bar, 1);
+    tc::mbar_init(&wbar[0], 1);
+    tc::mbar_init(&wbar[1], 1);
+    tc::mbar_init(&xbar, 1);
+    tc::mbar_init(&mbar, 1);
     tc::fence_mbar_init();
+    // the first two weight chunks
+    for (uint32_t c = 0; c < 2 && c < total_chunks; ++c) {
+      tc::mbar_expect_tx(&wbar[c], (uint32_t)mlpk::kWChunkBytes);
+      tc::bulk_g2s(Wb[c], Wimg + (size_t)c * mlpk::kWChunkBytes, (uint32_t)mlpk::kWChunkBytes, &wbar[c]);
+    }
   }
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = tmem_slot;
-  const uint32_t ha = tc::smem_u32(Hs), wa = tc::smem_u32(Ws);
-  uint32_t phase = 0;
+  constexpr uint32_t idesc = tc::idesc_bf16(128, 256);
+  __shared__ int s_ok;
+  uint32_t wphase[2] = {0, 0}, xphase = 0, mphase = 0;
+  uint32_t G = 0;        // weight chunks consumed so far
+  uint32_t waited = 0;   // weight chunks seen landed (thread 0)
+  uint32_t issued = total_chunks < 2 ? total_chunks : 2;   // weight chunk copies issued (thread 0)
+  bool x_pending = false;                                    // a tile copy not yet seen landed
   bool ok = true;
-  const unsigned long long ntiles = (n + 127) / 128;
-  for (unsigned long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
-    const unsigned long long cand = tile * 128 + threadIdx.x;   // position in the scored list
-    if (threadIdx.x < 128) {
-      float x[64];
-      if (cand < n) {
-        unsigned long long idx = cand;
-        if (flist) {
-          const unsigned long long j = cand / Q.nchains;
-          idx = (unsigned long long)flist[j] * Q.nchains + (cand - j * Q.nchains);
-        }
-        candidate_features(Q, progs, facts, chainfeat, idx, x, nullptr);
-      } else {
-        for (int i = 0; i < 64; ++i) x[i] = 0.f;
-      }
-#pragma unroll
-      for (int j = 0; j < 64; j += 8) {
-        uint32_t w[4];
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          __nv_bfloat162 h2 = __floats2bfloat162_rn(x[j + 2 * e], x[j + 2 * e + 1]);
-          w[e] = *reinterpret_cast<uint32_t*>(&h2);
-        }
-        *reinterpret_cast<uint4*>(Hs + tc::sw128_offset(threadIdx.x, j)) = make_uint4(w[0], w[1], w[2], w[3]);
-      }
-    }
-    // ---- layer 1: X (K = 64) x W1^T
-    stage_w(Ws, W1b, DIN, 0);
-    tc::fence_proxy_async();
-    tc::fence_before_sync();
-    __syncthreads();
+  for (uint32_t pass = 0; pass < npass && ok; ++pass) {
+    const uint32_t tA = 2 * (blockIdx.x + pass * gridDim.x);
+    const uint32_t nt = tA + 1 < ntiles ? 2 : 1;
     if (threadIdx.x == 0) {
-      tc::fence_after_sync();
-      mma_chunk(tmem, ha, wa, true, &bar);
+      tc::mbar_expect_tx(&xbar, nt * kTileBytes);
+      for (uint32_t t = 0; t < nt; ++t) tc::bulk_g2s(H[t], img + (size_t)(tA + t) * kTileBytes, kTileBytes, &xbar);
     }
-    ok = sync_mma(&bar, phase);
+    x_pending = true;
+    // every wait's outcome is agreed on by the whole CTA before it goes on
+    ok = __syncthreads_and(tc::mbar_wait(&xbar, xphase, kWaitLimit)) != 0;
     if (!ok) break;
-    epilogue_hidden(tmem, b1, Hs);
-    // ---- layers 2 and 3: H (K = 256) x W^T in four chunks; the epilogue
-    // overwrites H only after the layer's last MMA completed
-    for (int layer = 0; layer < 2 && ok; ++layer) {
-      const bf16* W = layer == 0 ? W2b : W3b;
-      for (int kc = 0; kc < 4 && ok; ++kc) {
-        stage_w(Ws, W, DH, kc * 64);
+    x_pending = false;
+    xphase ^= 1;
+    for (int j = 0; j < mlpk::kWChunks; ++j) {
+      const uint32_t b = G & 1;
+      // A operand: atom kc of each tile (X for layer 1)
+      const uint32_t kc = j == 0 ? 0 : (uint32_t)((j - 1) & 3);
+      const bool first = j == 0 || kc == 0;
+      if (threadIdx.x == 0) {
+        const bool landed = tc::mbar_wait(&wbar[b], wphase[b], kWaitLimit);
+        if (landed) {
+          ++waited;
+          tc::fence_after_sync();
+          for (uint32_t t = 0; t < nt; ++t) {
+            const uint32_t a_addr = tc::smem_u32(H[t] + kc * 16384), b_addr = tc::smem_u32(Wb[b]);
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk)
+              tc::mma_bf16(tmem + t * 256, tc::sdesc_sw128(a_addr + kk * 32), tc::sdesc_sw128(b_addr + kk * 32),
+                           idesc, (first && kk == 0) ? 0u : 1u);
+          }
+          tc::mma_commit(&mbar);
+        }
+        s_ok = landed ? 1 : 0;
+      }
+      __syncthreads();
+      if (!s_ok) {
+        ok = false;
+        break;
+      }
+      wphase[b] ^= 1;
+      ok = __syncthreads_and(tc::mbar_wait(&mbar, mphase, kWaitLimit)) != 0;
+      if (!ok) break;
+      mphase ^= 1;
+      tc::fence_after_sync();
+      ++G;
+      // this chunk's buffer is free again: the chunk two ahead goes into it
+      if (threadIdx.x == 0 && G + 1 < total_chunks) {
+        ++issued;
+        tc::mbar_expect_tx(&wbar[b], (uint32_t)mlpk::kWChunkBytes);
+        tc::bulk_g2s(Wb[b], Wimg + (size_t)((G + 1) % mlpk::kWChunks) * mlpk::kWChunkBytes,
+                     (uint32_t)mlpk::kWChunkBytes, &wbar[b]);
+      }
+      const uint32_t t = (uint32_t)warp >> 2;   // the tile this warp's epilogue serves
+      if (j == 0 || j == 4) {
+        // hidden layer 1 or 2 done: its activations become the next A operand
+        if (t < nt) epilogue_rows(tmem, t * 256, sb[j == 0 ? 0 : 1], H[t]);
         tc::fence_proxy_async();
         tc::fence_before_sync();
         __syncthreads();
-        if (threadIdx.x == 0) {
-          tc::fence_after_sync();
-          mma_chunk(tmem, ha + kc * 16384, wa, kc == 0, &bar);
-        }
-        ok = sync_mma(&bar, phase);
-      }
-      if (!ok) break;
-      if (layer == 0) {
-        epilogue_hidden(tmem, b2, Hs);
-      } else {
-        // output layer: relu(Z3 + b3) . w4 over this thread's row and column half
-        const int row = (warp & 3) * 32 + lane, half = warp >> 2;
-        float s = 0.f;
+      } else if (j == 8) {
+        // layer 3 and the output dot product
+        if (t < nt) {
+          const int row = (warp & 3) * 32 + lane;
+          float acc = 0.f;
 #pragma unroll 1
-        for (int cc = 0; cc < 4; ++cc) {
-          const int c = half * 4 + cc;
-          uint32_t r[32];
-          tc::tmem_ld32(tmem + ((uint32_t)((warp & 3) * 32) << 16) + c * 32, r);
-          tc::tmem_ld_wait();
+          for (int c = 0; c < 8; ++c) {
+            uint32_t r[32];
+            tc::tmem_ld32(tmem + ((uint32_t)((warp & 3) * 32) << 16) + t * 256 + c * 32, r);
+            tc::tmem_ld_wait();
 #pragma unroll
-          for (int j = 0; j < 32; ++j)
-            s += fmaxf(__uint_as_float(r[j]) + __ldg(b3 + c * 32 + j), 0.f) * __ldg(w4 + c * 32 + j);
+            for (int q = 0; q < 32; ++q) acc += fmaxf(__uint_as_float(r[q]) + sb[2][c * 32 + q], 0.f) * sb[3][c * 32 + q];
+          }
+          const unsigned long long out = (unsigned long long)(tA + t) * 128 + row;
+          if (out < n) scores[out] = acc + b4;
         }
-        if (half) s_part[row] = s;
+        tc::fence_before_sync();
         __syncthreads();
-        const unsigned long long out = tile * 128 + row;
-        if (!half && out < n) scores[out] = s + s_part[row] + b4;
       }
     }
-    tc::fence_before_sync();
-    __syncthreads();
   }
-  if (!ok && threadIdx.x == 0) atomicExch(status, MP_ETIMEOUT);
+  if (!ok && threadIdx.x == 0) {
+    atomicExch(status, MP_ETIMEOUT);
+    // let the weight copies still in flight land before the CTA exits: the
+    // chunks issued but not yet seen landed (each buffer's phase still
+    // matches the oldest of them)
+    for (uint32_t c = waited; c < issued; ++c)
+      if (tc::mbar_wait(&wbar[c & 1], wphase[c & 1], kWaitLimit)) wphase[c & 1] ^= 1;
+    if (x_pending) tc::mbar_wait(&xbar, xphase, kWaitLimit);
+  }
   tc::fence_before_sync();
   __syncthreads();
-  if (warp == 0) tc::tmem_dealloc(tmem, 256);
+  if (warp == 0) tc::tmem_dealloc(tmem, 512);
 }
 
 // ------------------------------------------------------------ top-K
@@ -498,6 +536,31 @@ struct Pool {
 };
 
 Pool g_pool_q, g_pool_s;   // query data; scores and selection
+
+Pool g_pool_img;   // feature tile images of the scoring kernels
+
+// Scores of the candidates at positions [0, ncand) of the scored list (flist
+// maps positions to factorisation ranks; null = every candidate), in runs
+// of 2^19 (64 MB of feature tiles, resident in L2 between the two kernels).
+int score_candidates(mp_mlp* h, const Prepared& pq, const uint32_t* d_fl, uint64_t ncand, float* d_sc,
+                     cudaStream_t st) {
+  constexpr uint64_t kRun = uint64_t(1) << 19;
+  const uint64_t run = std::min<uint64_t>(kRun, (ncand + 255) / 256 * 256);
+  uint8_t* img = (uint8_t*)g_pool_img.get(run / 128 * kTileBytes);
+  if (!img) return MP_ENOMEM;
+  MP_CUDA_TRY(cudaFuncSetAttribute(k_mlp_img, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMlpSmem));
+  for (uint64_t c0 = 0; c0 < ncand; c0 += kRun) {
+    const uint64_t n = std::min<uint64_t>(kRun, ncand - c0);
+    const uint32_t ntiles = (uint32_t)((n + 127) / 128);
+    k_feat_img<<<ntiles, 128, 0, st>>>(pq.Q, pq.d_progs, pq.d_facts, pq.d_chainfeat, d_fl, c0, n, img);
+    const unsigned grid = (unsigned)std::min<uint64_t>((ntiles + 1) / 2, (uint64_t)sm_count_l());
+    k_mlp_img<<<grid, 256, kMlpSmem, st>>>(img, ntiles, h->Wimg, h->P, n, d_sc + c0, h->status);
+    count_launch(2);
+    MP_CUDA_TRY(cudaGetLastError());
+  }
+  return MP_OK;
+}
+
 
 __global__ void k_gather(const bf16* __restrict__ X, const float* __restrict__ T, const int64_t* __restrict__ perm,
                          int B, bf16* __restrict__ Xb, float* __restrict__ Tb) {
@@ -674,16 +737,7 @@ extern "C" int mp_learned_search(mp_mlp* h, const mp_search_query* query, int K,
   t_phase = clk::now();
   // ---- score every candidate
   MP_CUDA_TRY(cudaMemsetAsync(h->status, 0, 4, st));
-  const size_t smem = 65536 + 32768 + 1024;
-  MP_CUDA_TRY(cudaFuncSetAttribute(k_score, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  const uint64_t ntiles = (ncand + 127) / 128;
-  const unsigned blocks = (unsigned)std::min<uint64_t>(ntiles, (uint64_t)sm_count_l() * 2);
-  timer_begin(st);
-  k_score<<<blocks, 256, smem, st>>>(pq.Q, pq.d_progs, pq.d_facts, pq.d_chainfeat, h->W1b, h->W2b, h->W3b, h->P,
-                                     d_fl, ncand, d_sc, h->status);
-  timer_end(st);
-  count_launch();
-  MP_CUDA_TRY(cudaGetLastError());
+  if ((rc = score_candidates(h, pq, d_fl, ncand, d_sc, st))) return rc;
   MP_CUDA_TRY(cudaMemsetAsync(d_hist, 0, 65536 * 4, st));
   const unsigned gb = (unsigned)std::min<uint64_t>((ncand + 255) / 256, (uint64_t)sm_count_l() * 8);
   k_topk_hist<<<gb, 256, 0, st>>>(d_sc, ncand, d_hist);
@@ -863,13 +917,7 @@ extern "C" int mp_learned_scores(mp_mlp* h, const mp_search_query* query, float*
   const uint64_t ncand = (uint64_t)pq.S.c->chains.size() * pq.S.c->facts.size();
   *n_out = (int64_t)ncand;
   MP_CUDA_TRY(cudaMemsetAsync(h->status, 0, 4, st));
-  const size_t smem = 65536 + 32768 + 1024;
-  MP_CUDA_TRY(cudaFuncSetAttribute(k_score, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  const uint64_t ntiles = (ncand + 127) / 128;
-  const unsigned blocks = (unsigned)std::min<uint64_t>(ntiles, (uint64_t)sm_count_l() * 2);
-  k_score<<<blocks, 256, smem, st>>>(pq.Q, pq.d_progs, pq.d_facts, pq.d_chainfeat, h->W1b, h->W2b, h->W3b, h->P,
-                                     nullptr, ncand, scores, h->status);
-  count_launch();
+  if ((rc = score_candidates(h, pq, nullptr, ncand, scores, st))) return rc;
   if (features) {
     int64_t* d_idx = nullptr;
     if (cudaMalloc(&d_idx, ncand * 8) != cudaSuccess) return MP_ENOMEM;

@@ -281,14 +281,20 @@ __global__ void k_adam(float* __restrict__ P, const float* __restrict__ G, float
 }
 
 __global__ void k_refresh(const float* __restrict__ P, bf16* __restrict__ W1b, bf16* __restrict__ W2b,
-                          bf16* __restrict__ W3b, bf16* __restrict__ W2T, bf16* __restrict__ W3T) {
+                          bf16* __restrict__ W3b, bf16* __restrict__ W2T, bf16* __restrict__ W3T,
+                          unsigned char* __restrict__ Wimg) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < DH * DH; i += gridDim.x * blockDim.x) {
     const int r = i / DH, c = i % DH;
-    if (i < DH * DIN) W1b[i] = __float2bfloat16(P[O_W1 + i]);
+    if (i < DH * DIN) {
+      W1b[i] = __float2bfloat16(P[O_W1 + i]);
+      *reinterpret_cast<bf16*>(Wimg + wimg_offset(1, i / DIN, i % DIN)) = W1b[i];
+    }
     W2b[i] = __float2bfloat16(P[O_W2 + i]);
     W3b[i] = __float2bfloat16(P[O_W3 + i]);
     W2T[(size_t)c * DH + r] = __float2bfloat16(P[O_W2 + i]);
     W3T[(size_t)c * DH + r] = __float2bfloat16(P[O_W3 + i]);
+    *reinterpret_cast<bf16*>(Wimg + wimg_offset(2, r, c)) = W2b[i];
+    *reinterpret_cast<bf16*>(Wimg + wimg_offset(3, r, c)) = W3b[i];
   }
 }
 
@@ -379,7 +385,7 @@ int train_step(mp_mlp* h, const bf16* X, const float* target, int B, float lr, c
     const float b1 = 0.9f, b2 = 0.999f;
     const float c1 = 1.f - powf(b1, (float)h->step), c2 = 1.f - powf(b2, (float)h->step);
     k_adam<<<296, 256, 0, st>>>(h->P, h->G, h->M1, h->M2, NPARAM, lr, b1, b2, c1, c2, 1e-8f);
-    k_refresh<<<256, 256, 0, st>>>(h->P, h->W1b, h->W2b, h->W3b, h->W2T, h->W3T);
+    k_refresh<<<256, 256, 0, st>>>(h->P, h->W1b, h->W2b, h->W3b, h->W2T, h->W3T, h->Wimg);
     count_launch(2);
   }
   MP_CUDA_TRY(cudaGetLastError());
@@ -388,7 +394,7 @@ int train_step(mp_mlp* h, const bf16* X, const float* target, int B, float lr, c
 
 int upload_params(mp_mlp* h, const float* host, cudaStream_t st) {
   MP_CUDA_TRY(cudaMemcpyAsync(h->P, host, NPARAM * 4, cudaMemcpyHostToDevice, st));
-  k_refresh<<<256, 256, 0, st>>>(h->P, h->W1b, h->W2b, h->W3b, h->W2T, h->W3T);
+  k_refresh<<<256, 256, 0, st>>>(h->P, h->W1b, h->W2b, h->W3b, h->W2T, h->W3T, h->Wimg);
   count_launch();
   MP_CUDA_TRY(cudaStreamSynchronize(st));
   return MP_OK;
@@ -405,7 +411,7 @@ extern "C" int mp_mlp_create(uint64_t seed, mp_mlp** out) {
   // every region starts on a 256-byte boundary (NPARAM is odd; the GEMM
   // epilogue stores 16-byte vectors into the gradient blocks)
   const size_t preg = (NPARAM * 4 + 255) & ~size_t(255);
-  size_t bytes = 4 * preg + 5 * (size_t)DH * DH * 2 + 256 + 256;
+  size_t bytes = 4 * preg + 5 * (size_t)DH * DH * 2 + kWChunks * kWChunkBytes + 256 + 256;
   char* p = nullptr;
   if (cudaMalloc(&p, bytes) != cudaSuccess) {
     cudaGetLastError();
@@ -422,6 +428,7 @@ extern "C" int mp_mlp_create(uint64_t seed, mp_mlp** out) {
   h->W3b = (bf16*)p; p += (size_t)DH * DH * 2;
   h->W2T = (bf16*)p; p += (size_t)DH * DH * 2;
   h->W3T = (bf16*)p; p += (size_t)DH * DH * 2;
+  h->Wimg = (unsigned char*)p; p += kWChunks * kWChunkBytes;
   h->status = (int*)p; p += 256;
   h->scalar = (float*)p;
   // He initialisation from splitmix64 + Box-Muller
