@@ -82,6 +82,8 @@ def _load():
                 "or_matmul_cost": (I, [I64, I64, I64, I, I, V, I, V, I, V, V]),
                 "or_search": (I, [I64, I64, I64, I, I, I, I, V]),
                 "or_candidate_costs": (I, [I64, I64, I64, I, I, I, V, I64, V, V]),
+                "or_hier_costs": (I, [V, I, I, I, V, V, I, V, V, I, V, V]),
+                "or_hier_search": (I, [V, I, I, I, I, V, V, I, V]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(lib, name)
@@ -380,3 +382,44 @@ def greedy_workload(d: int, l):
     if lib.or_greedy_workload(d, len(l), _p(l), _p(out)):
         raise ValueError("bad greedy")
     return tuple(int(v) for v in out)
+
+
+HIER_VARIANTS = {"block": 0, "cyclic": 1}
+
+
+def _hier_args(L, width, elem_bytes):
+    k = len(L)
+    Lv = np.asarray(L, dtype=np.int64)
+    wd = np.zeros(4, dtype=np.int64)
+    wd[:k] = width
+    eb = np.zeros(4, dtype=np.uint64)
+    eb[:k] = elem_bytes
+    return k, Lv, wd, eb
+
+
+def hier_costs(L, machine, a, b, variant, width, elem_bytes, threads=1):
+    """(inter-node, inter-processor) element halo bytes of the two-level
+    mapping with node grid a and GPU grid b (reading R20)."""
+    lib = _load()
+    k, Lv, wd, eb = _hier_args(L, width, elem_bytes)
+    av = np.asarray(a, dtype=np.int64)
+    bv = np.asarray(b, dtype=np.int64)
+    p = np.zeros(1, dtype=np.uint64)
+    s = np.zeros(1, dtype=np.uint64)
+    if lib.or_hier_costs(_p(Lv), k, machine[0], machine[1], _p(av), _p(bv), HIER_VARIANTS[variant], _p(wd), _p(eb),
+                         threads, _p(p), _p(s)):
+        raise ValueError("bad hierarchical candidate")
+    return int(p[0]), int(s[0])
+
+
+def hier_search(L, machine, variant, width, elem_bytes, threads=1):
+    """Exhaustive lexicographic argmin over (node grid, GPU grid)."""
+    lib = _load()
+    k, Lv, wd, eb = _hier_args(L, width, elem_bytes)
+    out = np.zeros(12, dtype=np.int64)
+    if lib.or_hier_search(_p(Lv), k, machine[0], machine[1], HIER_VARIANTS[variant], _p(wd), _p(eb), threads,
+                          _p(out)):
+        raise ValueError("bad hierarchical query")
+    return {"index": int(out[0]), "a": tuple(int(v) for v in out[1:1 + k]),
+            "b": tuple(int(v) for v in out[5:5 + k]), "primary": int(out[9]), "secondary": int(out[10]),
+            "n_candidates": int(out[11])}

@@ -30,7 +30,10 @@
 //   * the greedy grid heuristic of Algorithm A1;
 //   * the matmul moved-bytes cost of a candidate (reading R12) and the
 //     exhaustive lexicographic argmin over (factorisation, chain) candidates
-//     (reading R13).
+//     (reading R13);
+//   * the two-level search over node grid x GPU grid (the Solomonik mapper
+//     of Fig. 5b and the Cannon mapper of Appendix A.1 as search spaces;
+//     reading R20): inter-node then inter-processor element halo volume.
 //
 // Parity status: the Fig. 5 linearised cyclic distribution (R8) and
 // balance_split (R7) are "parity unpinned" beyond the special cases the tests
@@ -1076,6 +1079,147 @@ int or_search(int64_t M, int64_t N, int64_t K, int n, int g, int max_depth, int 
   out[5] = (int64_t)b.p;
   out[6] = (int64_t)b.s;
   out[7] = (int64_t)fs.size() * NC;
+  return 0;
+}
+
+// ------------------------------------------------------------ hierarchical search
+//
+// Two-level mappings of a k-D launch on Machine(GPU) = (n, g) (reading R20):
+// the node dimension split into a node grid a (prod a = n), the GPU dimension
+// into a GPU grid b (prod b = g).  Node coordinate u_t = floor(x_t a_t / L_t)
+// in both variants; GPU coordinate
+//   variant 0 (block within the node, the Solomonik mapper of Fig. 5b):
+//             v_t = floor(x_t a_t b_t / L_t) mod b_t
+//   variant 1 (cyclic within the node, the Cannon mapper of Appendix A.1):
+//             v_t = x_t mod b_t.
+// Node index u_0 + a_0 (u_1 + a_1 (...)), GPU index v_0 + b_0 (v_1 + ...)
+// (the split formula of Fig. 4, first factor fastest); id = node * g + gpu.
+// Candidates: a over the ordered k-factorisations of n, b over those of g,
+// both lexicographic; index = rank(a) * |F(g)| + rank(b).  Costs: primary =
+// the element halo volume (reading R17) between nodes, secondary = the same
+// between processors; the winner minimises (primary, secondary, index).
+
+namespace {
+
+struct Hier {
+  int k;
+  i64 L[4], a[4], b[4];
+  int variant;
+  int g;
+};
+
+void hier_owner(const Hier& h, const i64* x, i64& node, i64& proc) {
+  i64 nd = 0, gp = 0, sa = 1, sb = 1;
+  for (int t = 0; t < h.k; ++t) {
+    const i64 u = (i64)((i128)x[t] * h.a[t] / h.L[t]);
+    const i64 v = h.variant == 0 ? (i64)(((i128)x[t] * h.a[t] * h.b[t] / h.L[t]) % h.b[t]) : x[t] % h.b[t];
+    nd += u * sa;
+    gp += v * sb;
+    sa *= h.a[t];
+    sb *= h.b[t];
+  }
+  node = nd;
+  proc = nd * h.g + gp;
+}
+
+// element halo volumes (node level, processor level) by brute force
+void hier_costs(const Hier& h, const i64* width, const u64* bytes, int threads, u64& prim, u64& sec) {
+  i64 N = 1;
+  for (int t = 0; t < h.k; ++t) N *= h.L[t];
+  int T = threads < 1 ? 1 : threads;
+  std::vector<u64> pp(T, 0), ss(T, 0);
+  parallel_for(N, T, [&](i64 lo, i64 hi, int w) {
+    i64 y[4], z[4];
+    std::vector<i64> sn, sp;
+    for (i64 lin = lo; lin < hi; ++lin) {
+      i64 rest = lin;
+      for (int t = h.k - 1; t >= 0; --t) {
+        y[t] = rest % h.L[t];
+        rest /= h.L[t];
+      }
+      i64 n0, p0;
+      hier_owner(h, y, n0, p0);
+      for (int t = 0; t < h.k; ++t) {
+        sn.clear();
+        sp.clear();
+        for (i64 d = -width[t]; d <= width[t]; ++d) {
+          if (d == 0) continue;
+          for (int u = 0; u < h.k; ++u) z[u] = y[u];
+          z[t] += d;
+          if (z[t] < 0 || z[t] >= h.L[t]) continue;
+          i64 n1, p1;
+          hier_owner(h, z, n1, p1);
+          if (n1 != n0 && std::find(sn.begin(), sn.end(), n1) == sn.end()) sn.push_back(n1);
+          if (p1 != p0 && std::find(sp.begin(), sp.end(), p1) == sp.end()) sp.push_back(p1);
+        }
+        pp[w] += bytes[t] * (u64)sn.size();
+        ss[w] += bytes[t] * (u64)sp.size();
+      }
+    }
+  });
+  prim = sec = 0;
+  for (int w = 0; w < T; ++w) {
+    prim += pp[w];
+    sec += ss[w];
+  }
+}
+
+}  // namespace
+
+// Costs of one hierarchical candidate (a, b).
+int or_hier_costs(const int64_t* L, int k, int n, int g, const int64_t* a, const int64_t* b, int variant,
+                  const int64_t* width, const uint64_t* bytes, int threads, uint64_t* primary, uint64_t* secondary) {
+  if (k < 1 || k > 4 || n < 1 || g < 1 || variant < 0 || variant > 1) return 1;
+  Hier h;
+  h.k = k;
+  h.variant = variant;
+  h.g = g;
+  i64 pa = 1, pb = 1;
+  for (int t = 0; t < k; ++t) {
+    if (L[t] < 1 || a[t] < 1 || b[t] < 1 || width[t] < 0) return 1;
+    h.L[t] = L[t];
+    h.a[t] = a[t];
+    h.b[t] = b[t];
+    pa *= a[t];
+    pb *= b[t];
+  }
+  if (pa != n || pb != g) return 1;
+  u64 p, s;
+  hier_costs(h, width, bytes, threads, p, s);
+  *primary = p;
+  *secondary = s;
+  return 0;
+}
+
+// Exhaustive hierarchical search.  out: [index, a0..a3, b0..b3, primary,
+// secondary, n_candidates]
+int or_hier_search(const int64_t* L, int k, int n, int g, int variant, const int64_t* width,
+                   const uint64_t* bytes, int threads, int64_t* out) {
+  if (k < 1 || k > 4 || n < 1 || g < 1 || variant < 0 || variant > 1) return 1;
+  auto fa = factorisations(n, k);
+  auto fb = factorisations(g, k);
+  i64 best = -1;
+  u64 bp = 0, bs = 0;
+  for (size_t i = 0; i < fa.size(); ++i)
+    for (size_t j = 0; j < fb.size(); ++j) {
+      u64 p, s;
+      if (or_hier_costs(L, k, n, g, fa[i].data(), fb[j].data(), variant, width, bytes, threads, &p, &s)) return 1;
+      const i64 idx = (i64)(i * fb.size() + j);
+      if (best < 0 || p < bp || (p == bp && s < bs)) {   // ties keep the lower index
+        best = idx;
+        bp = p;
+        bs = s;
+      }
+    }
+  const i64 i = best / (i64)fb.size(), j = best % (i64)fb.size();
+  out[0] = best;
+  for (int t = 0; t < 4; ++t) {
+    out[1 + t] = t < k ? fa[i][t] : 0;
+    out[5 + t] = t < k ? fb[j][t] : 0;
+  }
+  out[9] = (int64_t)bp;
+  out[10] = (int64_t)bs;
+  out[11] = (int64_t)(fa.size() * fb.size());
   return 0;
 }
 

@@ -645,3 +645,82 @@ def test_weighted_decompose_in_a_chain():
     assert ln.final_shape() == (2, 8)
     ln = O.Launch((64, 64), (4, 4), [("merge", 0, 1), ("decompose", 0, (64, 64), None, (0,))], ("block",))
     assert ln.final_shape() == (1, 16)
+
+
+# ------------------------------------------------------ hierarchical search
+# Two-level (node grid a x GPU grid b) mappings, reading R20.
+
+def hier_chain(k, a, b, variant):
+    """Split/swap/merge chain on Machine(n, g) whose final space realises the
+    two-level mapping: node dimension split by a, GPU dimension by b; for
+    the block variant each pair (b_t, a_t) is merged (GPU digit fastest) so
+    that a block distribution over the product grid gives node w_t div b_t,
+    GPU w_t mod b_t; for the cyclic variant the 2k-D space is the
+    hierarchical distribution's (Appendix A.1)."""
+    ch = [("split", i, a[i]) for i in range(k - 1)]
+    ch += [("split", k + j, b[j]) for j in range(k - 1)]
+    if variant == "cyclic":
+        return ch, ("hier",)
+    labels = [("u", t) for t in range(k)] + [("v", t) for t in range(k)]
+    want = [lab for t in range(k) for lab in (("v", t), ("u", t))]
+    for pos in range(2 * k):
+        j = labels.index(want[pos])
+        if j != pos:
+            ch.append(("swap", pos, j))
+            labels[pos], labels[j] = labels[j], labels[pos]
+    ch += [("merge", t, t + 1) for t in range(k)]
+    return ch, ("block",)
+
+
+def node_chain(k, a):
+    ch = [("split", i, a[i]) for i in range(k - 1)]
+    return ch + [("merge", k - 1, k)]
+
+
+@pytest.mark.parametrize("N", [4, 6, 8])
+def test_hier_search_recovers_the_fig5b_mapper(N):
+    # Fig. 5b: on 2 nodes x 4 GPUs a 3-D launch longer along x maps with node
+    # space (2,1,1) and GPU space (1,2,2); the search's optimum is that pair
+    r = O.hier_search((2 * N, N, N), (2, 4), "block", (1, 1, 1), (1, 1, 1), threads=8)
+    assert r["a"] == ints(G["fig5b_solomonik_node_space"])
+    assert r["b"] == ints(G["fig5b_solomonik_gpu_space"])
+    assert r["primary"] == 2 * N * N   # one node cut of N x N, both directions
+
+
+@pytest.mark.parametrize("variant", ["block", "cyclic"])
+def test_hier_costs_match_chain_mappings(variant):
+    # the direct formulas of reading R20 against the same mappings written as
+    # split / swap / merge chains with the block or hierarchical distribution
+    rng = W.rng(810)
+    for _ in range(12):
+        k = rng.randint(1, 3)
+        n, g = rng.choice((1, 2, 3, 4, 6)), rng.choice((1, 2, 4, 8))
+        L = tuple(rng.randint(1, 13) for _ in range(k))
+        fa, fb = O.factorisations(n, k), O.factorisations(g, k)
+        a, b = fa[rng.randint(0, len(fa) - 1)], fb[rng.randint(0, len(fb) - 1)]
+        width = tuple(rng.randint(0, 3) for _ in range(k))
+        eb = tuple(rng.randint(1, 9) for _ in range(k))
+        p, s = O.hier_costs(L, (n, g), a, b, variant, width, eb)
+        ch, dist = hier_chain(k, a, b, variant)
+        ln = O.Launch(L, (n, g), ch, dist)
+        assert s == ln.halo_elements(width, eb, want_recv=False)[0], (L, n, g, a, b)
+        lnode = O.Launch(L, (n, 1), node_chain(k, a), ("block",))
+        assert p == lnode.halo_elements(width, eb, want_recv=False)[0], (L, n, g, a, b)
+
+
+def test_hier_primary_closed_form():
+    # extents divisible by the node grid: interior node cuts only
+    for L, a, w in (((12, 8, 6), (3, 2, 1), (1, 2, 1)), ((16, 16), (4, 2), (3, 1))):
+        n = math.prod(a)
+        p, _ = O.hier_costs(L, (n, 2), a, (2,) + (1,) * (len(L) - 1), "block", w, (1,) * len(L))
+        assert p == sum(2 * (a[t] - 1) * w[t] * math.prod(L[u] for u in range(len(L)) if u != t)
+                        for t in range(len(L)))
+
+
+def test_hier_cyclic_lower_is_worst_for_stencils():
+    # within a node the cyclic lower level puts every neighbour on another
+    # GPU once b_t >= 2: its processor volume is never below the block one
+    for L in ((16, 8, 8), (12, 12, 6)):
+        rb = O.hier_search(L, (2, 4), "block", (1, 1, 1), (1, 1, 1), threads=8)
+        rc = O.hier_search(L, (2, 4), "cyclic", (1, 1, 1), (1, 1, 1), threads=8)
+        assert rb["primary"] == rc["primary"] and rb["secondary"] <= rc["secondary"]
