@@ -287,6 +287,26 @@ def extra_volume_study(N, W, torch, dev):
             "by_gpus": by("gpus", W.STUDY_GPUS), "seconds": secs}
 
 
+def extra_hier_search(N, W, torch):
+    """Two-level (node grid x GPU grid) search on the large launch's task
+    space and machine, both variants: exact inter-node and inter-processor
+    element halo volumes of every candidate on the GPU."""
+    L, machine = W.large_config("block")["L"], W.large_config("block")["machine"]
+    out = {}
+    for variant in ("block", "cyclic"):
+        N.hier_search(L, machine, variant, (1, 1, 1), (8, 8, 8))   # warm
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = N.hier_search(L, machine, variant, (1, 1, 1), (8, 8, 8))
+        dt = time.perf_counter() - t0
+        out[variant] = {"ms": 1e3 * dt, "candidates": r["n_candidates"], "a": r["a"], "b": r["b"],
+                        "inter_node_bytes": r["primary"], "inter_proc_bytes": r["secondary"]}
+    cands = sum(v["candidates"] for v in out.values())
+    secs = sum(v["ms"] for v in out.values()) / 1e3
+    return {"metric": "two-level candidates/s", "value": cands / secs, "unit": "candidates/s",
+            "workload": "1024x1024x512 on 64 x 8, node grid x GPU grid, width-1 element halo", **out}
+
+
 def max_over_ranks(value: float, dist, device) -> float:
     """The largest value of all ranks (the job is as slow as its slowest
     rank); the value itself without a process group."""
@@ -537,7 +557,8 @@ def main():
             for key, fn in (("search", lambda: extra_search(N, W, torch)),
                             ("batched", lambda: extra_batched(N, W, torch, dev)),
                             ("learned", lambda: extra_learned(N, W, torch)),
-                            ("volume_study", lambda: extra_volume_study(N, W, torch, dev))):
+                            ("volume_study", lambda: extra_volume_study(N, W, torch, dev)),
+                            ("hier_search", lambda: extra_hier_search(N, W, torch))):
                 try:
                     line[key] = fn()
                 except Exception as exc:  # noqa: BLE001 - an extra must not lose the main line

@@ -185,6 +185,48 @@ typedef struct mp_halo {
 int mp_halo_volume(const mp_space* space, const mp_machine* machine, const mp_xform* chain, int n_xf,
                    const mp_dist* dist, const mp_halo* halo, uint64_t* total, uint64_t* recv, void* stream);
 
+/* Two-level search (the Solomonik mapper of Fig. 5b and the Cannon mapper of
+ * Appendix A.1 as search spaces).  A candidate splits the node dimension of
+ * Machine(GPU) into a node grid a (prod a = nodes) and the processor
+ * dimension into a GPU grid b (prod b = procs_per_node), k = rank factors
+ * each.  Node coordinate u_t = floor(x_t a_t / L_t); GPU coordinate
+ *   MP_HIER_BLOCK   floor(x_t a_t b_t / L_t) mod b_t  (block within the node)
+ *   MP_HIER_CYCLIC  x_t mod b_t                        (cyclic within the node)
+ * node index u_0 + a_0 (u_1 + a_1 (...)), GPU index likewise, id = node *
+ * procs_per_node + GPU.  Candidates: a over the ordered factorisations of
+ * nodes, b over those of procs_per_node, both in lexicographic order; index =
+ * rank(a) * |F(procs_per_node)| + rank(b).  Primary cost: the element halo
+ * volume (mp_halo_volume, MP_HALO_ELEMENTS) between nodes; secondary: the
+ * same between processors; the winner minimises (primary, secondary, index).
+ * Every candidate's volumes are computed on the GPU.  Synchronous.
+ * Errors: MP_EINVAL (rank, machine, widths, variant), MP_ENOTSUP (more than
+ * 65536 candidates), as mp_halo_volume otherwise. */
+enum mp_hier_variant { MP_HIER_BLOCK = 0, MP_HIER_CYCLIC = 1 };
+typedef struct mp_hier_query {
+  mp_space space;
+  mp_machine machine;
+  int32_t variant;    /* enum mp_hier_variant               */
+  int32_t width[4];   /* halo width per task dimension      */
+  uint64_t bytes[4];  /* bytes per element, per dimension   */
+} mp_hier_query;
+typedef struct mp_hier_result {
+  int64_t index;
+  int64_t a[4];               /* node grid (rank entries)            */
+  int64_t b[4];               /* GPU grid                            */
+  uint64_t primary_bytes;     /* inter-node halo bytes               */
+  uint64_t secondary_bytes;   /* inter-processor halo bytes          */
+  int64_t n_candidates;
+} mp_hier_result;
+int mp_hier_search(const mp_hier_query* query, mp_hier_result* out, void* stream);
+
+/* The chain of a two-level candidate (for mp_map_points / mp_halo_volume):
+ * splits of the node and GPU dimensions by a and b, then for MP_HIER_BLOCK
+ * swaps and merges that pair each GPU factor (fastest) with its node factor,
+ * to be used with the block distribution; for MP_HIER_CYCLIC the 2k-D space
+ * of the hierarchical distribution.  Host only; writes at most 16 ops. */
+int mp_hier_chain(int32_t rank, const int64_t* a, const int64_t* b, int32_t variant, mp_xform* chain,
+                  int32_t* n_xf, mp_dist* dist);
+
 /* map_points without any allocation.  The paper has no counterpart: this
  * entry point exists for callers that cannot allocate device memory -- code
  * running under a memory manager that owns the device's whole budget (a

@@ -485,6 +485,160 @@ extern "C" int mp_halo_volume(const mp_space* space, const mp_machine* machine, 
                               halo->mode == MP_HALO_ELEMENTS ? 1 : 0, halo->width);
 }
 
+// ------------------------------------------------------------ two-level search
+
+namespace mp {
+namespace {
+
+// Chain realising a two-level candidate on Machine(n, g): the node dimension
+// split by a, the processor dimension by b; for the block variant each
+// (b_t, a_t) pair is brought together by swaps and merged with the GPU
+// digit fastest, so that a block distribution over the product grid gives
+// node floor(w_t / b_t) and GPU w_t mod b_t.
+int hier_chain(int k, const int64_t* a, const int64_t* b, int variant, std::vector<mp_xform>& ch, mp_dist& dist) {
+  ch.clear();
+  auto op = [&](int o, int i, int j, int64_t d) {
+    mp_xform x;
+    std::memset(&x, 0, sizeof(x));
+    x.op = o;
+    x.i = i;
+    x.j = j;
+    x.d = d;
+    ch.push_back(x);
+  };
+  for (int i = 0; i + 1 < k; ++i) op(MP_SPLIT, i, 0, a[i]);
+  for (int j = 0; j + 1 < k; ++j) op(MP_SPLIT, k + j, 0, b[j]);
+  dist.b = 1;
+  if (variant == MP_HIER_CYCLIC) {
+    dist.kind = MP_HIER;
+    return MP_OK;
+  }
+  dist.kind = MP_BLOCK;
+  // labels: node factor t = t, GPU factor t = k + t; wanted order
+  // (gpu 0, node 0, gpu 1, node 1, ...)
+  int lab[8];
+  for (int t = 0; t < 2 * k; ++t) lab[t] = t;
+  for (int pos = 0; pos < 2 * k; ++pos) {
+    const int want = (pos & 1) ? pos / 2 : k + pos / 2;
+    int j = pos;
+    while (lab[j] != want) ++j;
+    if (j != pos) {
+      op(MP_SWAP, pos, j, 0);
+      std::swap(lab[pos], lab[j]);
+    }
+  }
+  for (int t = 0; t < k; ++t) op(MP_MERGE, t, t + 1, 0);
+  return MP_OK;
+}
+
+}  // namespace
+}  // namespace mp
+
+extern "C" int mp_hier_chain(int32_t rank, const int64_t* a, const int64_t* b, int32_t variant, mp_xform* chain,
+                             int32_t* n_xf, mp_dist* dist) {
+  if (rank < 1 || rank > 4 || !a || !b || !chain || !n_xf || !dist) return MP_EINVAL;
+  if (variant != MP_HIER_BLOCK && variant != MP_HIER_CYCLIC) return MP_EINVAL;
+  std::vector<mp_xform> ch;
+  int rc = mp::hier_chain(rank, a, b, variant, ch, *dist);
+  if (rc) return rc;
+  for (size_t o = 0; o < ch.size(); ++o) chain[o] = ch[o];
+  *n_xf = (int32_t)ch.size();
+  return MP_OK;
+}
+
+extern "C" int mp_hier_search(const mp_hier_query* query, mp_hier_result* out, void* stream) {
+  using namespace mp;
+  if (!query || !out) return MP_EINVAL;
+  const mp_hier_query& q = *query;
+  const int k = q.space.rank;
+  if (k < 1 || k > MP_MAX_TASK_RANK) return MP_EINVAL;
+  if (q.variant != MP_HIER_BLOCK && q.variant != MP_HIER_CYCLIC) return MP_EINVAL;
+  if (q.machine.nodes < 1 || q.machine.procs_per_node < 1) return MP_EINVAL;
+  for (int t = 0; t < k; ++t)
+    if (q.width[t] < 0 || q.width[t] > MP_MAX_HALO_WIDTH) return MP_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  const auto fa = ordered_factorisations(q.machine.nodes, k);
+  const auto fb = ordered_factorisations(q.machine.procs_per_node, k);
+  const size_t NA = fa.size(), NB = fb.size(), ncand = NA * NB;
+  if (ncand > 65536) return MP_ENOTSUP;
+  const mp_machine node_machine{q.machine.nodes, 1};
+  // candidate plans: the node-level launch of node grid a (Machine(n, 1),
+  // the node splits, the trailing size-1 dimension merged), and the
+  // processor-level launch of (a, b)
+  auto plan_node = [&](size_t i, Plan& pl) {
+    std::vector<mp_xform> ch;
+    mp_dist d;
+    const int64_t ones[4] = {1, 1, 1, 1};
+    hier_chain(k, fa[i].data(), ones, MP_HIER_BLOCK, ch, d);
+    std::vector<mp_xform> nch(ch.begin(), ch.begin() + (k - 1));
+    mp_xform m;
+    std::memset(&m, 0, sizeof(m));
+    m.op = MP_MERGE;
+    m.i = k - 1;
+    m.j = k;
+    nch.push_back(m);
+    const mp_dist blk{MP_BLOCK, 1};
+    return build_plan(&q.space, &node_machine, nch.data(), (int)nch.size(), &blk, pl);
+  };
+  auto plan_proc = [&](size_t c, Plan& pl) {
+    std::vector<mp_xform> ch;
+    mp_dist d;
+    hier_chain(k, fa[c / NB].data(), fb[c % NB].data(), q.variant, ch, d);
+    return build_plan(&q.space, &q.machine, ch.data(), (int)ch.size(), &d, pl);
+  };
+  Plan pl;
+  // every plan is validated before anything is launched
+  for (size_t i = 0; i < NA; ++i) {
+    int rc = plan_node(i, pl);
+    if (rc) return rc;
+  }
+  for (size_t c = 0; c < ncand; ++c) {
+    int rc = plan_proc(c, pl);
+    if (rc) return rc;
+  }
+  uint64_t* totals = (uint64_t*)workspace((NA + ncand) * 8, 5);
+  if (!totals) return MP_ENOMEM;
+  auto run = [&](const Plan& p, uint64_t* total) {
+    Want w;
+    std::memset(&w, 0, sizeof(w));
+    w.total = total;
+    w.elem_mode = 1;
+    for (int t = 0; t < 4; ++t) {
+      w.face[t] = t < k ? q.bytes[t] : 0;
+      w.width[t] = t < k ? (uint32_t)q.width[t] : 0;
+    }
+    return run_launch(p, w, st);
+  };
+  for (size_t i = 0; i < NA; ++i) {
+    int rc = plan_node(i, pl);
+    if (!rc) rc = run(pl, totals + i);
+    if (rc) return rc;
+  }
+  for (size_t c = 0; c < ncand; ++c) {
+    int rc = plan_proc(c, pl);
+    if (!rc) rc = run(pl, totals + NA + c);
+    if (rc) return rc;
+  }
+  std::vector<uint64_t> h(NA + ncand);
+  MP_CUDA_TRY(cudaMemcpyAsync(h.data(), totals, h.size() * 8, cudaMemcpyDeviceToHost, st));
+  MP_CUDA_TRY(cudaStreamSynchronize(st));
+  size_t best = 0;
+  for (size_t c = 1; c < ncand; ++c) {
+    const uint64_t p = h[c / NB], s = h[NA + c], bp = h[best / NB], bs = h[NA + best];
+    if (p < bp || (p == bp && s < bs)) best = c;
+  }
+  std::memset(out, 0, sizeof(*out));
+  out->index = (int64_t)best;
+  for (int t = 0; t < k; ++t) {
+    out->a[t] = fa[best / NB][t];
+    out->b[t] = fb[best % NB][t];
+  }
+  out->primary_bytes = h[best / NB];
+  out->secondary_bytes = h[NA + best];
+  out->n_candidates = (int64_t)ncand;
+  return MP_OK;
+}
+
 // ------------------------------------------------------------ no-allocation variant
 //
 // mp_map_points_noalloc: the same launch as mp_map_points, with its scratch

@@ -67,10 +67,22 @@ class mp_halo(ctypes.Structure):
 HALO_FACES = 0
 HALO_ELEMENTS = 1
 MAX_HALO_WIDTH = 16
+HIER_VARIANTS = {"block": 0, "cyclic": 1}
 
 
 class mp_dist(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("b", ctypes.c_int32)]
+
+
+class mp_hier_query(ctypes.Structure):
+    _fields_ = [("space", mp_space), ("machine", mp_machine), ("variant", ctypes.c_int32),
+                ("width", ctypes.c_int32 * 4), ("bytes", ctypes.c_uint64 * 4)]
+
+
+class mp_hier_result(ctypes.Structure):
+    _fields_ = [("index", ctypes.c_int64), ("a", ctypes.c_int64 * 4), ("b", ctypes.c_int64 * 4),
+                ("primary_bytes", ctypes.c_uint64), ("secondary_bytes", ctypes.c_uint64),
+                ("n_candidates", ctypes.c_int64)]
 
 
 class mp_query(ctypes.Structure):
@@ -114,6 +126,8 @@ def lib():
                 "mp_comm_volume": (I, [V, V, V, I, V, V, V, V, V]),
                 "mp_halo_volume": (I, [V, V, V, I, V, V, V, V, V]),
                 "mp_greedy_grid": (I, [I64, I, V]),
+                "mp_hier_search": (I, [V, V, V]),
+                "mp_hier_chain": (I, [I, V, V, I, V, V, V]),
                 "mp_decompose_search": (I, [V, I, V, V]),
                 "mp_candidate_costs": (I, [V, V, I64, V, V, V]),
                 "mp_plan": (I, [V, V, V, I, V, V, V, V, V, I]),
@@ -298,6 +312,37 @@ def halo_volume(L, machine, chain, dist, width, elem_bytes, total, recv=None, el
     rc = lib().mp_halo_volume(ctypes.byref(sp), ctypes.byref(mc), ch, n, ctypes.byref(ds), ctypes.byref(h),
                               _ptr(total), _ptr(recv), _stream(stream))
     _check(rc, "mp_halo_volume")
+
+
+def hier_chain(a, b, variant):
+    """(chain, distribution) realising the two-level candidate (a, b)."""
+    k = len(a)
+    av = (ctypes.c_int64 * 4)(*[int(v) for v in a], *([0] * (4 - k)))
+    bv = (ctypes.c_int64 * 4)(*[int(v) for v in b], *([0] * (4 - k)))
+    ch = (mp_xform * 16)()
+    n = ctypes.c_int32(0)
+    d = mp_dist()
+    _check(lib().mp_hier_chain(k, av, bv, HIER_VARIANTS[variant], ch, ctypes.byref(n), ctypes.byref(d)),
+           "mp_hier_chain")
+    kind = {v: k_ for k_, v in DISTS.items()}[d.kind]
+    return [xform_tuple(ch[o]) for o in range(n.value)], (kind,)
+
+
+def hier_search(L, machine, variant, width, elem_bytes, stream=None):
+    """mp_hier_search: the two-level (node grid, GPU grid) argmin."""
+    q = mp_hier_query()
+    q.space = make_space(L)
+    q.machine = make_machine(machine)
+    q.variant = HIER_VARIANTS[variant]
+    for t, v in enumerate(width):
+        q.width[t] = int(v)
+    for t, v in enumerate(elem_bytes):
+        q.bytes[t] = int(v)
+    r = mp_hier_result()
+    _check(lib().mp_hier_search(ctypes.byref(q), ctypes.byref(r), _stream(stream)), "mp_hier_search")
+    k = len(L)
+    return {"index": r.index, "a": tuple(r.a[:k]), "b": tuple(r.b[:k]), "primary": r.primary_bytes,
+            "secondary": r.secondary_bytes, "n_candidates": r.n_candidates}
 
 
 def greedy_grid(d, k):

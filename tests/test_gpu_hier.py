@@ -1,0 +1,53 @@
+"""GPU parity of mp_hier_search (two-level node grid x GPU grid search)
+against the CPU oracle's direct evaluation of the Fig. 5b and Appendix A.1
+mappings."""
+import math
+
+import pytest
+
+import oracle as O
+from paper_2507_17087_gb300 import native as N
+from paper_2507_17087_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("variant", ["block", "cyclic"])
+def test_random_queries_match_oracle(variant):
+    rng = W.rng(820 + (variant == "cyclic"))
+    for _ in range(10):
+        k = rng.randint(1, 3)
+        L = tuple(rng.randint(2, 24) for _ in range(k))
+        machine = (rng.choice((1, 2, 3, 4, 6, 8)), rng.choice((1, 2, 4)))
+        width = tuple(rng.randint(0, 3) for _ in range(k))
+        eb = tuple(rng.randint(1, 16) for _ in range(k))
+        got = N.hier_search(L, machine, variant, width, eb)
+        want = O.hier_search(L, machine, variant, width, eb, threads=8)
+        assert got == want, (L, machine, variant, width)
+
+
+def test_fig5b_case():
+    got = N.hier_search((32, 16, 16), (2, 4), "block", (1, 1, 1), (8, 8, 8))
+    assert got["a"] == (2, 1, 1) and got["b"] == (1, 2, 2)
+    assert got == O.hier_search((32, 16, 16), (2, 4), "block", (1, 1, 1), (8, 8, 8), threads=8)
+
+
+def test_large_launch_against_closed_forms():
+    # 1024 x 1024 x 512 on 64 x 8, width 1: every candidate's volumes from
+    # the oracle's closed form (block layouts: element count = face count)
+    L, machine, eb = (1024, 1024, 512), (64, 8), (8, 8, 8)
+    got = N.hier_search(L, machine, "block", (1, 1, 1), eb)
+    fa, fb = O.factorisations(64, 3), O.factorisations(8, 3)
+    best = None
+    for i, a in enumerate(fa):
+        ch, dist = N.hier_chain(a, (1, 1, 1), "block")
+        node_ch = ch[:2] + [("merge", 2, 3)]
+        p = O.Launch(L, (64, 1), node_ch, ("block",)).halo_closed_form(eb)
+        for j, b in enumerate(fb):
+            ch, dist = N.hier_chain(a, b, "block")
+            s = O.Launch(L, machine, ch, dist).halo_closed_form(eb)
+            key = (p, s, i * len(fb) + j)
+            best = key if best is None or key < best else best
+    assert (got["primary"], got["secondary"], got["index"]) == best
+    assert got["n_candidates"] == len(fa) * len(fb)

@@ -162,3 +162,22 @@ def test_greedy_grid_matches_oracle():
     for d in list(range(1, 300)) + [512, 720, 2520, 3600, 4096, 65536, 9699690]:
         for k in (1, 2, 3, 4):
             assert N.greedy_grid(d, k) == O.greedy(d, k), (d, k)
+
+
+def test_hier_chain_matches_the_pinned_construction():
+    # the engine's two-level chains equal the oracle-pinned construction of
+    # tests/test_oracle_pins.py, and plan to the expected final spaces
+    import test_oracle_pins as T
+    rng = W.rng(906)
+    for _ in range(60):
+        k = rng.randint(1, 4)
+        n, g = rng.choice((1, 2, 4, 6, 12, 64)), rng.choice((1, 2, 4, 8))
+        fa, fb = O.factorisations(n, k), O.factorisations(g, k)
+        a, b = fa[rng.randint(0, len(fa) - 1)], fb[rng.randint(0, len(fb) - 1)]
+        for variant in ("block", "cyclic"):
+            ch, dist = N.hier_chain(a, b, variant)
+            want_ch, want_dist = T.hier_chain(k, a, b, variant)
+            assert (ch, dist) == (want_ch, want_dist)
+            shape, _ = N.plan((8,) * k, (n, g), ch, dist)
+            want = tuple(a[t] * b[t] for t in range(k)) if variant == "block" else tuple(a) + tuple(b)
+            assert shape == want
