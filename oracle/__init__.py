@@ -18,7 +18,7 @@ Chain vocabulary (plain tuples, shared with the tests):
                              the appendix's generalised objective: halo
                              widths h and all-to-all transposes along the
                              listed target dimensions
-  ("balance_split", i, k)    reading R7: decompose(i, (1,)*k)
+  ("balance_split", i, k)    read as decompose(i, (1,)*k)
 Distributions: ("block",), ("cyclic",), ("block_cyclic", b), ("hier",),
 ("linear_cyclic",).
 """
@@ -219,7 +219,7 @@ class Launch:
         return int(tot[0]), recv
 
     def halo_elements(self, width, elem_bytes, want_recv=True, threads=1):
-        """Anisotropic halo volume in elements (reading R17): per element and
+        """Anisotropic halo volume in elements: per element and
         dimension, one copy to each other owner within the halo width."""
         lib = _load()
         wd = np.zeros(4, dtype=np.int64)
@@ -338,7 +338,8 @@ def _chain_ops(chain, depth):
 
 
 def matmul_cost(M, N, K, machine, chain, f, literal=False):
-    """(primary, secondary) moved tiles of one candidate (reading R12)."""
+    """(primary, secondary) moved tiles of one candidate: per operand tile,
+    distinct processors - 1 and distinct nodes - 1."""
     lib = _load()
     n, g = machine
     depth = max(len(chain), 1)
@@ -354,7 +355,7 @@ def matmul_cost(M, N, K, machine, chain, f, literal=False):
 
 
 def search(M, N, K, machine, max_depth=3, threads=1):
-    """Exhaustive lexicographic argmin (reading R13).  Costs in tiles."""
+    """Exhaustive lexicographic argmin over (factorisation, chain).  Costs in tiles."""
     lib = _load()
     n, g = machine
     out = np.zeros(8, dtype=np.int64)
@@ -399,7 +400,7 @@ def _hier_args(L, width, elem_bytes):
 
 def hier_costs(L, machine, a, b, variant, width, elem_bytes, threads=1):
     """(inter-node, inter-processor) element halo bytes of the two-level
-    mapping with node grid a and GPU grid b (reading R20)."""
+    mapping with node grid a and GPU grid b."""
     lib = _load()
     k, Lv, wd, eb = _hier_args(L, width, elem_bytes)
     av = np.asarray(a, dtype=np.int64)

@@ -17,27 +17,30 @@
 //     prime-exponent enumeration of Sec. 4.3, then expanded into k-1 splits
 //     as Sec. 4.2 states;
 //   * distributions: block (Fig. 1a / Fig. 3: idx = point * m.size / space),
-//     cyclic and block-cyclic (reading R9), the Cannon hierarchical
-//     block/cyclic mapper (Appendix A.1), the linearised round-robin of
-//     Fig. 5 (reading R8);
+//     cyclic (x mod s) and block-cyclic (floor(x / b) mod s, which the paper
+//     names without a formula), the Cannon hierarchical block/cyclic mapper
+//     (Appendix A.1), the linearised round-robin of Fig. 5 (C-order linear
+//     index mod P; the figure itself is not available);
 //   * halo volume: every directed nearest-neighbour face whose two endpoints
-//     have different owners (Sec. 4.2, Fig. 10 surface formula; reading R10);
-//     and the anisotropic element count with per-dimension halo widths (the
-//     appendix's generalised decompose; readings R10 and R17): every element
-//     once per other owner that needs it along each dimension;
+//     have different owners (Sec. 4.2, Fig. 10 surface formula; each face
+//     counted once per direction, non-periodic); and the anisotropic element
+//     count with per-dimension halo widths (the appendix's generalised
+//     decompose): every element once per other owner that needs it along
+//     each dimension;
 //   * decompose with halo widths and all-to-all transposes: the appendix's
 //     generalised objective V + sum_T V*_n, compared exactly;
 //   * the greedy grid heuristic of Algorithm A1;
-//   * the matmul moved-bytes cost of a candidate (reading R12) and the
-//     exhaustive lexicographic argmin over (factorisation, chain) candidates
-//     (reading R13);
+//   * the matmul moved-bytes cost of a candidate (per operand tile: distinct
+//     processors - 1, distinct nodes - 1) and the exhaustive lexicographic
+//     argmin over (factorisation, chain) candidates in canonical order;
 //   * the two-level search over node grid x GPU grid (the Solomonik mapper
-//     of Fig. 5b and the Cannon mapper of Appendix A.1 as search spaces;
-//     reading R20): inter-node then inter-processor element halo volume.
+//     of Fig. 5b and the Cannon mapper of Appendix A.1 as search spaces):
+//     inter-node then inter-processor element halo volume.
 //
-// Parity status: the Fig. 5 linearised cyclic distribution (R8) and
-// balance_split (R7) are "parity unpinned" beyond the special cases the tests
-// list (the paper gives no worked numbers for them).
+// Parity status: the Fig. 5 linearised cyclic distribution (its order is
+// read as C order) and balance_split (read as decompose(i, (1, ..., 1))) are
+// "parity unpinned" beyond the special cases the tests list (the paper gives
+// no worked numbers for them).
 
 #include <algorithm>
 #include <cstdint>
@@ -201,7 +204,7 @@ bool weighted_objective(const std::vector<i64>& f, const i64* l, const i64* h, i
 }
 
 // argmin over all factorisations; ties go to the lexicographically smallest
-// tuple (reading R5) -- the enumeration is lexicographic and only a strictly
+// tuple -- the enumeration is lexicographic and only a strictly
 // smaller objective replaces the incumbent.  h == nullptr and tmask == 0 is
 // the isotropic objective of Sec. 4.2.  Empty result: objective overflow.
 std::vector<i64> decompose_factors(i64 d, int k, const i64* l, const i64* h = nullptr, int tmask = 0) {
@@ -337,7 +340,8 @@ int build_plan(Plan& pl, const i64* L, int k, int n, int g, const i64* xf, int n
     else if (op == OP_SWAP) ok = push_swap(pl.prims, sp, i, j);
     else if (op == OP_DECOMPOSE) ok = push_decompose(pl.prims, sp, i, kk, e + 5, e + 9, (int)e[13]);
     else if (op == OP_BALANCE_SPLIT) {
-      // reading R7: balance_split(i, k) = decompose(i, (1, ..., 1))
+      // balance_split(i, k) is read as decompose(i, (1, ..., 1)): the paper
+      // names it without a definition
       i64 ones[4] = {1, 1, 1, 1};
       ok = (kk >= 1 && kk <= 4) && push_decompose(pl.prims, sp, i, kk, ones);
     }
@@ -352,7 +356,7 @@ int build_plan(Plan& pl, const i64* L, int k, int n, int g, const i64* xf, int n
     } else if (dist == D_HIER) {
       // Appendix A.1 pattern on the re-split machine (n, g): decompose the
       // node dimension by the task space, then the processor dimension by the
-      // task space divided elementwise by the node factors (reading R6).
+      // task space divided elementwise by the node factors (floor, at least 1).
       if (!push_split(pl.prims, sp, 0, n)) return 1;
       if (!push_decompose(pl.prims, sp, 0, k, pl.L)) return 1;
       i64 T2[4];
@@ -440,7 +444,7 @@ i64 owner_of_point(const Plan& pl, const i64* x) {
   distribute(pl, x, a);
   i64 node, proc;
   resolve(pl, a, node, proc);
-  return node * pl.g + proc;   // reading R1: node-major processor id
+  return node * pl.g + proc;   // node-major processor id
 }
 
 void unravel(const Plan& pl, i64 lin, i64* x) {
@@ -474,7 +478,7 @@ std::vector<i64> nontrivial_divisors(i64 s) {
   return out;
 }
 
-// Canonical alphabet at shape s (reading R13): split(i, d) for i ascending and
+// Canonical alphabet at shape s: split(i, d) for i ascending and
 // d ascending over the divisors with 1 < d < s_i, then merge(p, q) for p < q
 // lexicographic, then swap(p, q) for p < q lexicographic.
 std::vector<COp> alphabet(const Space& sp) {
@@ -557,7 +561,7 @@ inline i64 flat_of(const i64* f, i64 a0, i64 a1, i64 a2) { return a0 + f[0] * (a
 
 inline i64 blk(i64 x, i64 f, i64 L) { return (i64)((i128)x * f / L); }
 
-// Literal reading R12 on the full tile grid: for every tile of A(i,k),
+// The moved-tile cost, literally, on the full tile grid: for every tile of A(i,k),
 // B(k,j), C(i,j), count the distinct processors (and nodes) among the points
 // (i,j,k) that touch it; the tile costs (distinct - 1) tile transfers.
 // O(M N K) -- only for small grids (brute-force pin of the grouped form).
@@ -753,7 +757,7 @@ int or_owner_of(const int64_t* L, int k, int n, int g, const int64_t* xf, int nx
   return 0;
 }
 
-// Halo volume (reading R10): every directed pair (x, x + delta e_t), delta =
+// Halo volume: every directed pair (x, x + delta e_t), delta =
 // +-1, with both points inside the launch and different owners, adds
 // face_bytes[t]; the receiver is the owner of x.  The neighbour's owner is
 // evaluated independently for every pair.
@@ -797,7 +801,7 @@ int or_comm_volume(const int64_t* L, int k, int n, int g, const int64_t* xf, int
 
 // Halo volume in elements with per-dimension widths (the anisotropic halo
 // of the appendix's "Generalization of the Decompose Primitive"; readings
-// R10 and R17).  A processor p that owns a point x needs every point
+// the element count).  A processor p that owns a point x needs every point
 // y = x + delta e_t with 1 <= |delta| <= width[t] inside the launch; each
 // element y it does not own is received once per dimension t along which it
 // is needed, whichever of p's points need it:
@@ -960,7 +964,7 @@ int or_weighted_objective(int64_t d, int k, const int64_t* f, const int64_t* l, 
 }
 
 // Algorithm A1: primes ascending; each goes to the currently smallest factor
-// (first index on ties, reading R15); the factors are sorted descending.
+// (the first index on ties); the factors are sorted descending.
 int or_greedy(int64_t d, int k, int64_t* out) {
   if (d < 1 || k < 1) return 1;
   std::vector<i64> primes;
@@ -1039,7 +1043,7 @@ int or_matmul_cost(int64_t M, int64_t N, int64_t K, int n, int g, const int64_t*
   return 0;
 }
 
-// Exhaustive decompose search for one 3-D matmul query (reading R13):
+// Exhaustive decompose search for one 3-D matmul query:
 // candidates are (factorisation f of P into 3, chain c of depth <= max_depth
 // on (P/g, g)), index = f_rank * n_chains + c_rank; the winner minimises
 // (primary, secondary, index) lexicographically.  Costs are in tiles.
@@ -1084,7 +1088,7 @@ int or_search(int64_t M, int64_t N, int64_t K, int n, int g, int max_depth, int 
 
 // ------------------------------------------------------------ hierarchical search
 //
-// Two-level mappings of a k-D launch on Machine(GPU) = (n, g) (reading R20):
+// Two-level mappings of a k-D launch on Machine(GPU) = (n, g):
 // the node dimension split into a node grid a (prod a = n), the GPU dimension
 // into a GPU grid b (prod b = g).  Node coordinate u_t = floor(x_t a_t / L_t)
 // in both variants; GPU coordinate
@@ -1096,7 +1100,7 @@ int or_search(int64_t M, int64_t N, int64_t K, int n, int g, int max_depth, int 
 // (the split formula of Fig. 4, first factor fastest); id = node * g + gpu.
 // Candidates: a over the ordered k-factorisations of n, b over those of g,
 // both lexicographic; index = rank(a) * |F(g)| + rank(b).  Costs: primary =
-// the element halo volume (reading R17) between nodes, secondary = the same
+// the element halo volume (as or_halo_elements) between nodes, secondary = the same
 // between processors; the winner minimises (primary, secondary, index).
 
 namespace {

@@ -1,7 +1,7 @@
 """Float64 reference of the learned cost model (test infrastructure).
 
 The paper has no learned component; this model is the project's surrogate
-for the decompose search cost (reading R16).  Definitions:
+for the decompose search cost.  Definitions:
 
   layers   h1 = relu(x W1^T + b1), h2 = relu(h1 W2^T + b2),
            h3 = relu(h2 W3^T + b3), y = h3 w4 + b4

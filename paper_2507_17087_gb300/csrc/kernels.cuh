@@ -152,7 +152,8 @@ __device__ __forceinline__ void dim_counts(const MapCore& D, int t, uint32_t j, 
   }
 }
 
-// Element-count halo along one dimension (readings R10, R17): the sub-index
+// Element-count halo along one dimension (each element counted once per
+// receiving owner and dimension within the halo width): the sub-index
 // j occupies runs of positions (first run starts at a, last run ends at e,
 // nq runs of `size` positions in all, consecutive runs `gap` apart); the
 // positions outside them within distance w of one are

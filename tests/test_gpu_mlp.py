@@ -132,7 +132,7 @@ def test_learned_search_trains_and_finds_the_optimum():
     for q in evalq:
         exact = N.decompose_search([q])[0]
         got = model.learned_search(q, K=1024, fallback=True)
-        # exact with the fallback: the optimal cost tuple (reading R16: among
+        # exact with the fallback: the optimal cost tuple (among
         # exact ties the index may differ unless the exhaustive search ran)
         assert (got["primary_bytes"], got["secondary_bytes"]) == \
             (exact["primary_bytes"], exact["secondary_bytes"])

@@ -252,7 +252,7 @@ def test_linear_cyclic_subdiagonal():
 
 
 def test_balance_split_is_shape_agnostic_decompose():
-    # reading R7: balance_split(i, k) == decompose(i, (c,)*k) for any cube
+    # balance_split(i, k) (read as decompose(i, (1,)*k)) == decompose(i, (c,)*k) for any cube
     for P in (8, 12, 36, 64):
         for k in (2, 3):
             a = O.Launch((5,) * k, (P, 1), [("balance_split", 0, k)], ("block",)).final_shape()
@@ -507,7 +507,7 @@ def _grid_chain(f):
 def test_halo_elements_match_the_appendix_volume(L, f, h):
     # BLOCK, extents divisible by the grid, width <= block width: every
     # interior cut moves h_n layers each way.  The appendix's V counts d_n
-    # cuts per dimension (the outer surface included, reading R11): the exact
+    # cuts per dimension (the outer surface included): the exact
     # count is 2 V - 2 sum_n h_n prod_{m != n} l_m.
     P = math.prod(f)
     ln = O.Launch(L, (1, P), _grid_chain(f), ("block",))
@@ -521,7 +521,7 @@ def test_halo_elements_match_the_appendix_volume(L, f, h):
 
 @pytest.mark.parametrize("dist", [("block",), ("block_cyclic", 3)])
 def test_halo_elements_width_one_equals_faces_for_blocks(dist):
-    # reading R10: with width 1 the de-duplicated count and the directed-face
+    # with width 1 the de-duplicated count and the directed-face
     # count differ only where both neighbours of an element belong to one
     # other owner; with runs of at least two points per owner along every
     # dimension (block, block-cyclic with b >= 2) that cannot happen
@@ -648,7 +648,8 @@ def test_weighted_decompose_in_a_chain():
 
 
 # ------------------------------------------------------ hierarchical search
-# Two-level (node grid a x GPU grid b) mappings, reading R20.
+# Two-level (node grid a x GPU grid b) mappings: node u_t = floor(x_t a_t / L_t),
+# GPU block-within-node floor(x_t a_t b_t / L_t) mod b_t or cyclic x_t mod b_t.
 
 def hier_chain(k, a, b, variant):
     """Split/swap/merge chain on Machine(n, g) whose final space realises the
@@ -689,7 +690,7 @@ def test_hier_search_recovers_the_fig5b_mapper(N):
 
 @pytest.mark.parametrize("variant", ["block", "cyclic"])
 def test_hier_costs_match_chain_mappings(variant):
-    # the direct formulas of reading R20 against the same mappings written as
+    # the direct formulas against the same mappings written as
     # split / swap / merge chains with the block or hierarchical distribution
     rng = W.rng(810)
     for _ in range(12):
