@@ -221,6 +221,7 @@ def extra_learned(N, W, torch, n_train=512, per_query=4096, epochs=8, n_eval=16)
     t_l = t_e = t_b = t_r = 0.0
     phases = {"prepare": 0.0, "model": 0.0, "exact": 0.0, "fallback": 0.0}
     rounds = []
+    cert = {}
 
     def timed(fn):
         t = time.perf_counter()
@@ -238,6 +239,7 @@ def extra_learned(N, W, torch, n_train=512, per_query=4096, epochs=8, n_eval=16)
         t_l += dt
         assert (got["primary_bytes"], got["secondary_bytes"]) == (full["primary_bytes"], full["secondary_bytes"])
         fb += got["fallback"]
+        cert[got["certified"]] = cert.get(got["certified"], 0) + 1
         rounds.append(got["rounds"])
         for k in phases:
             phases[k] += got["ms"][k] / n_eval
@@ -249,7 +251,9 @@ def extra_learned(N, W, torch, n_train=512, per_query=4096, epochs=8, n_eval=16)
             "ms_learned_mean": 1e3 * t_l / n_eval, "ms_exhaustive_mean": 1e3 * t_e / n_eval,
             "ms_primary_bound_mean": 1e3 * t_b / n_eval, "vs_primary_bound": t_b / t_l,
             "ms_learned_top_k_only_mean": 1e3 * t_r / n_eval, "learned_phase_ms_mean": phases,
-            "rounds": rounds, "zero_regret_without_fallback": zr / n_eval, "exact_with_fallback": 1.0,
+            "rounds": rounds, "certified": {{0: "none", 1: "all threats evaluated", 2: "secondary lower bound"}[k]: v
+                                            for k, v in sorted(cert.items())},
+            "zero_regret_without_fallback": zr / n_eval, "exact_with_fallback": 1.0,
             "fallbacks": fb, "eval_queries": n_eval, "train_labels": n_train * per_query, "train_epochs": epochs,
             "train_seconds": t_train, "train_final_loss": loss, "K": 1024}
 

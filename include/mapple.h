@@ -401,7 +401,9 @@ int mp_mlp_train_search(mp_mlp* model, const mp_search_query* queries, int n_que
  * exact and closed-form), so the model scores those (fused tcgen05
  * inference; MP_LEARNED_SCORE_ALL scores every candidate) and the K best
  * scores are evaluated exactly.  Their argmin is returned if it is certified
- * (every candidate that could beat it was among those evaluated) or if the
+ * (every candidate that could beat it was among those evaluated, or its
+ * secondary cost reaches mp_secondary_lower_bound of every factorisation of
+ * least primary cost) or if the
  * model's largest overestimation on them leaves a margin below the
  * selection threshold.  Otherwise the selection grows 8-fold in score order
  * (while it stays within 65536 candidates and a quarter of those scored) and
@@ -414,7 +416,9 @@ typedef struct mp_learned_stats {
   int64_t n_scored;         /* candidates scored by the model                     */
   int64_t n_exact;          /* candidate evaluations, summed over the rounds      */
   int64_t n_selected;       /* size of the last selection                         */
-  int32_t certified;        /* 1: exact certificate on the last selection         */
+  int32_t certified;        /* 1: every candidate that could win was evaluated;
+                               2: the winner reaches mp_secondary_lower_bound
+                               of every least-primary factorisation            */
   int32_t fallback;         /* 1: the exhaustive search ran                       */
   int32_t rounds;           /* selections evaluated (1 + growth steps)            */
   int32_t reserved;
@@ -457,6 +461,17 @@ int mp_chain_from_draws(int32_t nodes, int32_t procs_per_node, int32_t depth,
  * its chain (chain_len <= 4 ops).  Host only; MP_EINVAL if out of range. */
 int mp_search_candidate(const mp_search_query* query, int64_t index, int64_t* f, mp_xform* chain,
                         int32_t* chain_len);
+
+/* A lower bound on the secondary cost (bytes) of factorisation f[3] of a
+ * search query over every chain: each node owns procs_per_node cells of the
+ * f0 x f1 x f2 block grid; the lines of a fibre family a node meets are its
+ * projection, minimised over down-sets of that many cells (pushing a cell set
+ * towards the origin along an axis never enlarges a projection), each line
+ * weighted by the smallest tile count of its fibres.  0 when no bound
+ * applies (an extent below its factor, or more than 32 processors per node).
+ * Exact when the extents are divisible by f and an optimal chain gives every
+ * node an optimal down-set.  Host only. */
+int mp_secondary_lower_bound(const mp_search_query* query, const int64_t* f, uint64_t* lb_bytes);
 
 /* Size of a decompose search space: number of factorisations of P into 3
  * ordered factors and number of canonical chains of depth <= max_depth. */

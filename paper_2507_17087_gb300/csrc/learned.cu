@@ -753,6 +753,16 @@ extern "C" int mp_learned_search(mp_mlp* h, const mp_search_query* query, int K,
   }
   t_phase = clk::now();
 
+  // a lower bound on the secondary of every candidate that can win (the
+  // least-primary factorisations); reaching it certifies the winner
+  uint64_t min_lb = ~0ull;
+  for (uint64_t fr = 0; fr < NF; ++fr)
+    if (pq.prim[fr] == pq.Q.pmin) {
+      const uint32_t f[3] = {(uint32_t)pq.S.c->facts[fr][0], (uint32_t)pq.S.c->facts[fr][1],
+                             (uint32_t)pq.S.c->facts[fr][2]};
+      const uint64_t lb = secondary_lower_bound(pq.Q.E, f, pq.Q.n, pq.Q.g);
+      if (lb < min_lb) min_lb = lb;
+    }
   // ---- the Kc best scores, evaluated exactly; Kc grows until accepted
   auto key = [](float v) { return std::isnan(v) ? INFINITY : v; };   // NaN orders last
   const unsigned long long tb = q.tile_bytes;
@@ -762,6 +772,7 @@ extern "C" int mp_learned_search(mp_mlp* h, const mp_search_query* query, int K,
   std::vector<float> yh;
   int64_t bi = 0;
   bool accept = false, certified = false;
+  int cert_kind_last = 0;
   double margin = 0.0;
   float over = 0.f;
   int rounds = 0;
@@ -828,6 +839,11 @@ extern "C" int mp_learned_search(mp_mlp* h, const mp_search_query* query, int K,
     for (int64_t i = 0; i < nsel; ++i)
       if (pb[i] / tb <= p_best) ++threats_in;
     certified = threats == threats_in;
+    int cert_kind = certified ? 1 : 0;
+    if (!certified && p_best == pq.Q.pmin && sb[bi] / tb <= min_lb) {
+      certified = true;   // no chain of any least-primary factorisation does better
+      cert_kind = 2;
+    }
     // margin: a candidate left out scored at least tau (the largest selected
     // score); it beats the winner only if its true target lies below the
     // winner's, i.e. if the model overestimated it by more than
@@ -845,6 +861,7 @@ extern "C" int mp_learned_search(mp_mlp* h, const mp_search_query* query, int K,
     if (!finite) over = INFINITY;   // no margin from a model that returned NaN / inf
     const float y_best = host_target(p_best, sb[bi] / tb, pq.Q.pmin);
     margin = (double)tau - y_best - 1.5 * over - 1e-3;
+    cert_kind_last = cert_kind;
     accept = certified || (p_best == pq.Q.pmin && margin > 0.0 && nsel == (int64_t)Kc);
     if (stats) stats->n_exact += nsel;
     if (accept || (flags & MP_LEARNED_NO_FALLBACK)) break;
@@ -857,7 +874,7 @@ extern "C" int mp_learned_search(mp_mlp* h, const mp_search_query* query, int K,
   }
   if (stats) {
     stats->ms_exact = ms_since(t_phase);
-    stats->certified = certified ? 1 : 0;
+    stats->certified = cert_kind_last;
     stats->margin = margin;
     stats->max_overestimate = over;
     stats->rounds = rounds;

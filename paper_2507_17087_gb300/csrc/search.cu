@@ -430,3 +430,104 @@ extern "C" int mp_search_candidate(const mp_search_query* query, int64_t index, 
   }
   return MP_OK;
 }
+
+// ------------------------------------------------------------ secondary lower bound
+//
+// Every node owns g cells of the f0 x f1 x f2 block grid (the chain is a
+// bijection).  For fibre family v (lines along v), sum over fibres of
+// (distinct nodes - 1) x tiles per fibre >= w_v (sum over nodes of the number
+// of v-lines the node's cells meet - number of v-lines), with w_v the
+// smallest tile count of a v-fibre (floor(E_u / f_u) floor(E_w / f_w)).  The
+// lines a cell set meets along v are its projection along v, and pushing
+// the set towards the origin along any axis keeps that axis' projection and
+// shrinks the other two (a line's count becomes the longest run over the
+// merged lines), so the least weighted projection sum of g cells is reached
+// by a down-set: heights h[i][j] non-increasing in i and j, summing to g.
+// Its projections are sum_j h[0][j] (along dim 0), sum_i h[i][0] (dim 1) and
+// the number of non-zero heights (dim 2).  Applies when E_t >= f_t (every
+// block holds tiles) and g <= 32; 0 otherwise.
+
+namespace mp {
+namespace {
+
+struct DownSet {
+  uint32_t f0, f1, f2, g;
+  uint64_t w[3];
+  uint64_t best;
+  uint32_t h[32][32];
+  void rec(uint32_t i, uint32_t j, uint32_t rem) {
+    if (rem == 0) {
+      uint64_t p0 = 0, p1 = 0, p2 = 0;
+      const uint32_t na = f0 < g ? f0 : g, nb = f1 < g ? f1 : g;
+      for (uint32_t a = 0; a < na; ++a)
+        for (uint32_t b = 0; b < nb; ++b) {
+          if (!h[a][b]) continue;
+          if (a == 0) p0 += h[a][b];
+          if (b == 0) p1 += h[a][b];
+          ++p2;
+        }
+      const uint64_t c = w[0] * p0 + w[1] * p1 + w[2] * p2;
+      if (c < best) best = c;
+      return;
+    }
+    if (i >= f0 || i >= g) return;
+    if (j >= f1 || j >= g) {   // next row
+      rec(i + 1, 0, rem);
+      return;
+    }
+    const uint32_t up = i ? h[i - 1][j] : f2, left = j ? h[i][j - 1] : f2;
+    uint32_t cap = up < left ? up : left;
+    if (cap > rem) cap = rem;
+    if (cap == 0) {   // the rest of this row is zero; a zero first cell ends the set
+      if (j == 0) return;
+      rec(i + 1, 0, rem);
+      return;
+    }
+    for (uint32_t v = cap; v >= 1; --v) {
+      h[i][j] = v;
+      rec(i, j + 1, rem - v);
+    }
+    h[i][j] = 0;
+    if (j > 0) rec(i + 1, 0, rem);   // row ends here
+  }
+};
+
+}  // namespace
+
+uint64_t secondary_lower_bound(const uint32_t E[3], const uint32_t f[3], uint32_t nodes, uint32_t g) {
+  if (g == 0 || g > 32) return 0;
+  for (int t = 0; t < 3; ++t)
+    if (f[t] == 0 || E[t] < f[t]) return 0;
+  DownSet ds;
+  std::memset(&ds, 0, sizeof(ds));
+  ds.f0 = f[0];
+  ds.f1 = f[1];
+  ds.f2 = f[2];
+  ds.g = g;
+  for (int v = 0; v < 3; ++v) {
+    const int u = v == 0 ? 1 : 0, w = v == 2 ? 1 : 2;
+    ds.w[v] = (uint64_t)(E[u] / f[u]) * (E[w] / f[w]);
+  }
+  ds.best = ~0ull;
+  ds.rec(0, 0, g);
+  if (ds.best == ~0ull) return 0;
+  const uint64_t lines = ds.w[0] * f[1] * f[2] + ds.w[1] * f[0] * f[2] + ds.w[2] * f[0] * f[1];
+  const unsigned __int128 tot = (unsigned __int128)ds.best * nodes;
+  return tot > lines ? (uint64_t)(tot - lines) : 0;
+}
+
+}  // namespace mp
+
+extern "C" int mp_secondary_lower_bound(const mp_search_query* query, const int64_t* f, uint64_t* lb_bytes) {
+  using namespace mp;
+  if (!query || !f || !lb_bytes) return MP_EINVAL;
+  int rc = validate_query(*query);
+  if (rc) return rc;
+  if (f[0] < 1 || f[1] < 1 || f[2] < 1 || f[0] * f[1] * f[2] != query->procs) return MP_EINVAL;
+  const uint32_t E[3] = {(uint32_t)query->M, (uint32_t)query->N, (uint32_t)query->K};
+  const uint32_t ff[3] = {(uint32_t)f[0], (uint32_t)f[1], (uint32_t)f[2]};
+  *lb_bytes = secondary_lower_bound(E, ff, (uint32_t)(query->procs / query->procs_per_node),
+                                    (uint32_t)query->procs_per_node) * query->tile_bytes;
+  return MP_OK;
+}
+

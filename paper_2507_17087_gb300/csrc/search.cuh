@@ -328,5 +328,8 @@ int candidate_costs_dev(const mp_search_query& q, const SearchSpace& S, const Ch
                         cudaStream_t st);
 // Exhaustive argmin on the device; the result on the host.
 int exhaustive_search(const mp_search_query& q, mp_search_result* out, cudaStream_t st);
+// Lower bound (tiles) on the secondary cost of factorisation f over every
+// chain; 0 when no bound applies (see search.cu).
+uint64_t secondary_lower_bound(const uint32_t E[3], const uint32_t f[3], uint32_t nodes, uint32_t g);
 
 }  // namespace mp

@@ -126,6 +126,7 @@ def lib():
                 "mp_comm_volume": (I, [V, V, V, I, V, V, V, V, V]),
                 "mp_halo_volume": (I, [V, V, V, I, V, V, V, V, V]),
                 "mp_greedy_grid": (I, [I64, I, V]),
+                "mp_secondary_lower_bound": (I, [V, V, V]),
                 "mp_hier_search": (I, [V, V, V]),
                 "mp_hier_chain": (I, [I, V, V, I, V, V, V]),
                 "mp_decompose_search": (I, [V, I, V, V]),
@@ -447,6 +448,16 @@ def _query(q, full=False):
                       q["tile_bytes"], full=full)
 
 
+def secondary_lower_bound(query, f):
+    """Lower bound (bytes) on the secondary cost of factorisation f over
+    every chain (host only)."""
+    q = _query(query)
+    fv = (ctypes.c_int64 * 3)(*[int(v) for v in f])
+    lb = ctypes.c_uint64(0)
+    _check(lib().mp_secondary_lower_bound(ctypes.byref(q), fv, ctypes.byref(lb)), "mp_secondary_lower_bound")
+    return lb.value
+
+
 def search_candidate(query, index):
     """(f, chain) of candidate `index` of a search query (host only)."""
     q = _query(query)
@@ -616,7 +627,7 @@ class MLP:
                                        ctypes.byref(st), _stream(stream)), "mp_learned_search")
         res = _search_result(out)
         res.update({"n_scored": st.n_scored, "n_exact": st.n_exact, "n_selected": st.n_selected,
-                    "certified": bool(st.certified), "fallback": bool(st.fallback), "rounds": st.rounds,
+                    "certified": int(st.certified), "fallback": bool(st.fallback), "rounds": st.rounds,
                     "margin": st.margin, "max_overestimate": st.max_overestimate,
                     "ms": {"prepare": st.ms_prepare, "model": st.ms_model, "exact": st.ms_exact,
                            "fallback": st.ms_fallback}})

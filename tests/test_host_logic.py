@@ -181,3 +181,54 @@ def test_hier_chain_matches_the_pinned_construction():
             shape, _ = N.plan((8,) * k, (n, g), ch, dist)
             want = tuple(a[t] * b[t] for t in range(k)) if variant == "block" else tuple(a) + tuple(b)
             assert shape == want
+
+
+def _pool_min_secondaries(q):
+    """Least secondary (tiles) over every chain, per factorisation, from the
+    oracle's exact costs."""
+    import numpy as np
+    M, Nn, K = q["MNK"]
+    n, g = q["machine"]
+    fs = O.factorisations(n * g, 3)
+    nch = len(O.chains(n, g, q["max_depth"]))
+    out = {}
+    for i, f in enumerate(fs):
+        idx = np.arange(i * nch, (i + 1) * nch, dtype=np.int64)
+        _, s = O.candidate_costs(M, Nn, K, (n, g), q["max_depth"], idx)
+        out[f] = int(s.min())
+    return out
+
+
+def test_secondary_lower_bound_is_a_lower_bound():
+    # never above the least secondary any chain reaches (oracle, every chain)
+    checked = 0
+    for q in W.search_query_small(count=8):
+        mins = _pool_min_secondaries(q)
+        for f, smin in mins.items():
+            lb = N.secondary_lower_bound(q, f) // q["tile_bytes"]
+            assert lb <= smin, (q, f, lb, smin)
+            checked += lb > 0
+    assert checked > 0
+
+
+def test_secondary_lower_bound_is_reached_on_divisible_grids():
+    # extents divisible by the factors on 64 x 8: an optimal chain gives every
+    # node an optimal down-set, so the bound equals the least secondary for
+    # the factorisations of least primary cost
+    import math
+    for MNK in ((1024, 4096, 1024), (4096, 4096, 1024)):
+        q = {"MNK": MNK, "machine": (64, 8), "max_depth": 3, "tile_bytes": 512 * 512 * 4}
+        fs = O.factorisations(512, 3)
+
+        def primary(f):
+            return sum((min(MNK[v], f[v]) - 1) * math.prod(MNK[t] for t in range(3) if t != v) for v in range(3))
+
+        pmin = min(primary(f) for f in fs)
+        pool = [f for f in fs if primary(f) == pmin]
+        import numpy as np
+        nch = len(O.chains(64, 8, 3))
+        for f in pool:
+            i = fs.index(f)
+            idx = np.arange(i * nch, (i + 1) * nch, dtype=np.int64)
+            _, s = O.candidate_costs(*MNK, (64, 8), 3, idx)
+            assert N.secondary_lower_bound(q, f) // q["tile_bytes"] == int(s.min()), (MNK, f)
