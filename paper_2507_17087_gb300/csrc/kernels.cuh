@@ -324,6 +324,23 @@ enum IdsMode : int { M_FAST_SMEM = 0, M_FAST_GLOBAL = 1, M_GENERAL = 2, M_FUSED 
 // base of a row when the dimensions m..k-1 are fused into one fast
 // dimension: sum_{t < m} c_t(x_t) of the row's slow coordinates.
 template <typename I>
+__device__ __forceinline__ uint32_t row_base_inl(const MapCore& D, const Tabs& tabs,
+                                                 const uint32_t* __restrict__ ctab, I row, int m) {
+  uint32_t base = 0;
+  for (int t = m - 1; t >= 0; --t) {
+    I xt = row;
+    if (t > 0) {
+      uint32_t q32, r32;
+      divmod32((uint32_t)row, D.divL32[t], q32, r32);
+      row = (I)q32;
+      xt = (I)r32;
+    }
+    base += tabs.has[t] ? __ldg(ctab + tabs.off[t] + xt) : contrib(D, t, (uint64_t)xt);
+  }
+  return base;
+}
+
+template <typename I>
 __device__ __noinline__ uint32_t row_base_m(const MapCore& D, const Tabs& tabs, const uint32_t* __restrict__ ctab,
                                             I row, int m) {
   uint32_t base = 0;
@@ -389,8 +406,11 @@ __device__ __forceinline__ void ids_range_rows(const MapCore& D, const Tabs& tab
   uint32_t lin0 = g * 4;
   uint32_t row, x;
   divmod32(lin0, divLf, row, x);
+  const uint32_t rows = N / Lf;
   uint32_t base = row_base_m<uint32_t>(D, tabs, ctab, row, m);
-  uint32_t next_row = 0xFFFFFFFFu, next_base = 0;   // a row base computed ahead of the wrap
+  // the next row's base, loaded a wrap ahead so that its latency overlaps
+  // the groups in between
+  uint32_t nbase = row + 1 < rows ? row_base_inl<uint32_t>(D, tabs, ctab, row + 1, m) : 0;
   for (; g < gend; g += 32, lin0 += 128) {
     const int cnt = N - lin0 < 4 ? (int)(N - lin0) : 4;
     uint32_t v[4] = {0, 0, 0, 0};
@@ -406,9 +426,7 @@ __device__ __forceinline__ void ids_range_rows(const MapCore& D, const Tabs& tab
         while (xi >= Lf) {
           xi -= Lf;
           ri += 1;
-          bi = row_base_m<uint32_t>(D, tabs, ctab, ri, m);
-          next_row = ri;
-          next_base = bi;
+          bi = ri == row + 1 ? nbase : row_base_m<uint32_t>(D, tabs, ctab, ri, m);
         }
         v[i] = T[bi + row_contrib<SRC>(D, Cf, xi)];
         ++xi;
@@ -424,13 +442,15 @@ __device__ __forceinline__ void ids_range_rows(const MapCore& D, const Tabs& tab
       if (Lf >= 128) {
         x -= Lf;
         row += 1;
+        base = nbase;
       } else {
         uint32_t q, r;
         divmod32(x, divLf, q, r);
         row += q;
         x = r;
+        base = row_base_m<uint32_t>(D, tabs, ctab, row, m);
       }
-      base = row == next_row ? next_base : row_base_m<uint32_t>(D, tabs, ctab, row, m);
+      nbase = row + 1 < rows ? row_base_inl<uint32_t>(D, tabs, ctab, row + 1, m) : 0;
     }
   }
 }
