@@ -75,7 +75,9 @@ __global__ void k_chain_feats(const ChainProg* __restrict__ progs, unsigned long
     const uint32_t b = 1u << i;
     f[22 + i] = (b < P && resolve_node(cp, b) != n0) ? 1.f : 0.f;
   }
-  for (int i = 0; i < kChainFeat; ++i) out[c * kChainFeat + i] = f[i];
+  // feature-major (feature i of every chain contiguous): the candidates a
+  // warp scores have consecutive chains, so each feature load is coalesced
+  for (int i = 0; i < kChainFeat; ++i) out[(unsigned long long)i * NC + c] = f[i];
 }
 
 // 64 features of candidate idx = fr * NC + c.
@@ -99,8 +101,7 @@ __device__ __forceinline__ void candidate_features(const QInfo& Q, const ChainPr
   x[18] = fminf(pn, 8.f) / 8.f;
   x[19] = log2f(1.f + pn) / 3.f;
   x[20] = p == Q.pmin ? 1.f : 0.f;
-  const float* cf = chainfeat + c * kChainFeat;
-  for (int i = 0; i < kChainFeat; ++i) x[21 + i] = cf[i];
+  for (int i = 0; i < kChainFeat; ++i) x[21 + i] = __ldg(chainfeat + (unsigned long long)i * Q.nchains + c);
   const ChainProg& cp = progs[c];
   const uint32_t n0 = resolve_node(cp, 0);
   const uint32_t stride[3] = {1u, f[0], f[0] * f[1]};
@@ -773,6 +774,7 @@ extern "C" int mp_learned_search(mp_mlp* h, const mp_search_query* query, int K,
   int64_t bi = 0;
   bool accept = false, certified = false;
   int cert_kind_last = 0;
+  unsigned long long p_best_last = ~0ull, s_best_last = ~0ull;   // tiles
   double margin = 0.0;
   float over = 0.f;
   int rounds = 0;
@@ -862,6 +864,8 @@ extern "C" int mp_learned_search(mp_mlp* h, const mp_search_query* query, int K,
     const float y_best = host_target(p_best, sb[bi] / tb, pq.Q.pmin);
     margin = (double)tau - y_best - 1.5 * over - 1e-3;
     cert_kind_last = cert_kind;
+    p_best_last = p_best;
+    s_best_last = sb[bi] / tb;
     accept = certified || (p_best == pq.Q.pmin && margin > 0.0 && nsel == (int64_t)Kc);
     if (stats) stats->n_exact += nsel;
     if (accept || (flags & MP_LEARNED_NO_FALLBACK)) break;
@@ -884,7 +888,8 @@ extern "C" int mp_learned_search(mp_mlp* h, const mp_search_query* query, int K,
     t_phase = clk::now();
     mp_search_query qf = q;
     qf.flags = 0;
-    rc = exhaustive_search(qf, out, st);
+    // the selection's winner bounds the secondary the search must look for
+    rc = exhaustive_search(qf, out, st, p_best_last == pq.Q.pmin ? s_best_last : ~0ull);
     if (stats) {
       stats->fallback = 1;
       stats->n_exact += out->n_candidates;

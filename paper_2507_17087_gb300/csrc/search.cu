@@ -35,9 +35,10 @@ size_t align_up(size_t v) { return (v + 255) & ~size_t(255); }
 // full = 1: every candidate's secondary is scanned.  full = 0: candidates
 // whose (exact, closed-form) primary exceeds the minimum primary over all
 // factorisations cannot win the lexicographic argmin and are not scanned.
-__global__ void k_search(const ChainProg* __restrict__ progs, const Fact* __restrict__ facts, int nf,
+__global__ void __launch_bounds__(256, 4) k_search(const ChainProg* __restrict__ progs, const Fact* __restrict__ facts, int nf,
                          uint32_t P, uint32_t E0, uint32_t E1, uint32_t E2, int words,
-                         unsigned long long nchains, int full, Key* __restrict__ chain_best) {
+                         unsigned long long nchains, int full, unsigned long long ub,
+                         Key* __restrict__ chain_best) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ Key red[32];
   uint32_t* bm = reinterpret_cast<uint32_t*>(smem_raw);
@@ -72,7 +73,7 @@ __global__ void k_search(const ChainProg* __restrict__ progs, const Fact* __rest
     Key k;
     k.p = primary_cost(E, f);
     if (!full && k.p > pmin) continue;   // uniform across the warp
-    k.s = secondary_cost_warp(tab, wbm, blockDim.x, words, E, f, lane);
+    k.s = secondary_cost_warp(tab, wbm, blockDim.x, words, E, f, lane, ub);
     k.idx = (unsigned long long)fr * nchains + c;
     if (key_less(k, best)) best = k;
   }
@@ -300,7 +301,8 @@ void fill_result(const mp_search_query& q, const SearchSpace& S, const Key& k, m
 
 }  // namespace
 
-int exhaustive_search(const mp_search_query& q, mp_search_result* out, cudaStream_t st) {
+int exhaustive_search(const mp_search_query& q, mp_search_result* out, cudaStream_t st,
+                      unsigned long long ub_secondary) {
   SearchSpace S;
   int rc = prepare(q, S);
   if (rc) return rc;
@@ -317,7 +319,8 @@ int exhaustive_search(const mp_search_query& q, mp_search_result* out, cudaStrea
     MP_CUDA_TRY(cudaFuncSetAttribute(k_search, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S.smem));
   k_search<<<(unsigned)NC, S.threads, S.smem, st>>>(d_progs, d_facts, (int)S.c->facts.size(), (uint32_t)q.procs,
                                                     (uint32_t)q.M, (uint32_t)q.N, (uint32_t)q.K, S.words, NC,
-                                                    (q.flags & MP_SEARCH_FULL) ? 1 : 0, chain_best);
+                                                    (q.flags & MP_SEARCH_FULL) ? 1 : 0,
+                                                    (q.flags & MP_SEARCH_FULL) ? ~0ull : ub_secondary, chain_best);
   count_launch();
   k_search_final<<<1, 1024, 0, st>>>(chain_best, NC, d_out);
   count_launch();

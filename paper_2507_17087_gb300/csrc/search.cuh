@@ -118,6 +118,28 @@ struct BlockIter {
 __device__ __forceinline__ uint32_t fibre_distinct(const uint16_t* __restrict__ tab, uint32_t* bm, int nthr,
                                                    int words, uint32_t base, uint32_t stride, uint32_t E,
                                                    uint32_t f, uint32_t n) {
+  if (E >= f) {
+    // every block holds tiles: the fibre's blocks are 0 .. n - 1 in order
+    const uint16_t* p = tab + base;
+    uint32_t D = 0;
+    for (uint32_t iv = 0; iv < n; ++iv, p += stride) {
+      const uint32_t node = *p;
+      uint32_t* wp = bm + (node >> 5) * nthr;
+      const uint32_t bit = 1u << (node & 31);
+      const uint32_t word = *wp;
+      if (!(word & bit)) {
+        *wp = word | bit;
+        ++D;
+      }
+    }
+    if ((uint32_t)words <= n) {
+      for (int w = 0; w < words; ++w) bm[w * nthr] = 0;
+    } else {
+      p = tab + base;
+      for (uint32_t iv = 0; iv < n; ++iv, p += stride) bm[(*p >> 5) * nthr] = 0;
+    }
+    return D;
+  }
   BlockIter it;
   it.init(E, f);
   uint32_t D = 0;
@@ -189,9 +211,12 @@ __device__ __forceinline__ unsigned long long warp_sum(unsigned long long v) {
 // one at a time, the lanes splitting the elements over one shared bitmap
 // (lane 0's) with atomic ORs, the distinct count being its population.
 // Every lane returns the total.
+// ub: once the running total exceeds it the remaining families are skipped
+// and ~0 is returned (the caller only needs costs up to ub).
 __device__ __forceinline__ unsigned long long secondary_cost_warp(const uint16_t* __restrict__ tab, uint32_t* bm,
                                                                   int stride, int words, const uint32_t E[3],
-                                                                  const uint32_t f[3], int lane) {
+                                                                  const uint32_t f[3], int lane,
+                                                                  unsigned long long ub = ~0ull) {
   const uint32_t fstride[3] = {1u, f[0], f[0] * f[1]};
   uint32_t n[3];
   for (int t = 0; t < 3; ++t) n[t] = E[t] < f[t] ? E[t] : f[t];
@@ -256,6 +281,7 @@ __device__ __forceinline__ unsigned long long secondary_cost_warp(const uint16_t
         }
       }
     }
+    if (sec > ub) return ~0ull;   // uniform across the warp
   }
   return sec;
 }
@@ -327,7 +353,11 @@ int candidate_costs_dev(const mp_search_query& q, const SearchSpace& S, const Ch
                         const Fact* d_facts, const int64_t* d_idx, int64_t n, uint64_t* d_p, uint64_t* d_s,
                         cudaStream_t st);
 // Exhaustive argmin on the device; the result on the host.
-int exhaustive_search(const mp_search_query& q, mp_search_result* out, cudaStream_t st);
+// ub_secondary (tiles): a secondary cost some candidate of least primary is
+// known to reach; candidates are scanned only as far as needed to show they
+// exceed it (the result is the same as without it).
+int exhaustive_search(const mp_search_query& q, mp_search_result* out, cudaStream_t st,
+                      unsigned long long ub_secondary = ~0ull);
 // Lower bound (tiles) on the secondary cost of factorisation f over every
 // chain; 0 when no bound applies (see search.cu).
 uint64_t secondary_lower_bound(const uint32_t E[3], const uint32_t f[3], uint32_t nodes, uint32_t g);
