@@ -138,3 +138,41 @@ def test_batch_rejects_invalid_queries():
         N.Batch([((4, 4), (2, 2), [("split", 0, 3)], ("block",), (1, 1))])
     with pytest.raises(N.MapleError):
         N.Batch([((4, 4), (1 << 15, 1), [], ("block",), (1, 1))])   # P > 16384
+
+
+def test_full_10000_query_batch_sampled():
+    # the whole 10,000-query batch as bench.py runs it (1.2e10 points, 49 GB
+    # of ids, autotuned, graph replay): per-query properties on every query,
+    # the oracle's owner of sampled points and its closed-form halo on
+    # sampled queries
+    qs = W.batched_queries(10000)
+    launches = launches_from(qs)
+    b = N.Batch(launches)
+    info, ids, hist, halo, recv = batch_outputs(b)
+    b.run(ids=ids, hist=hist, halo=halo, recv=recv, autotune=True)
+    b.run(ids=ids, hist=hist, halo=halo, recv=recv)
+    torch.cuda.synchronize()
+    io = torch.as_tensor(np.asarray(info["ids_offsets"], dtype=np.int64))
+    po = np.asarray(info["proc_offsets"], dtype=np.int64)
+    npts = np.array([math.prod(q["L"]) for q in qs], dtype=np.int64)
+    Ps = np.array([q["machine"][0] * q["machine"][1] for q in qs], dtype=np.int64)
+    # every histogram sums to its point count; every halo total is the sum of
+    # its received bytes
+    hsum = torch.zeros(len(qs), dtype=torch.int64, device=DEV)
+    rsum = torch.zeros(len(qs), dtype=torch.int64, device=DEV)
+    owner = torch.from_numpy(np.repeat(np.arange(len(qs)), Ps)).to(DEV)
+    hsum.index_add_(0, owner, hist[: int(Ps.sum())])
+    rsum.index_add_(0, owner, recv[: int(Ps.sum())])
+    assert torch.equal(hsum.cpu(), torch.from_numpy(npts))
+    assert torch.equal(rsum, halo)
+    rng = np.random.default_rng(11)
+    for q in rng.choice(len(qs), 60, replace=False):
+        L, machine, chain, dist, face = launches[q]
+        ref = O.Launch(L, machine, chain, dist)
+        lins = rng.integers(0, npts[q], 300).astype(np.int64)
+        got = ids[torch.from_numpy(lins + int(io[q])).to(DEV)].cpu().numpy()
+        assert np.array_equal(got, ref.owner_of(lins)), (q, L, machine, chain, dist)
+        assert int(halo[q].item()) == ref.halo_closed_form(face), (q, L, machine, chain, dist)
+    b.close()
+    del ids, hist, halo, recv
+    torch.cuda.empty_cache()
