@@ -37,7 +37,7 @@ VARIANTS = ("block", "cyclic", "block_cyclic")
 # DRAM bytes (read + write) of one full-size id-writer launch from the ncu
 # capture summarised in profiles/k_ids_large_1024x1024x512.md (set to None
 # when the kernel changes, until it is captured again).
-K_IDS_TRAFFIC_BYTES = 2.09e9 + 4.224e4
+K_IDS_TRAFFIC_BYTES = 2085650688 + 45824
 
 
 def parse():
@@ -205,7 +205,7 @@ def extra_batched(N, W, torch, dev, runs=5):
     return res
 
 
-def extra_learned(N, W, torch, n_train=512, per_query=4096, epochs=8, n_eval=16):
+def extra_learned(N, W, torch, n_train=512, per_query=4096, epochs=8, n_eval=200):
     """Learned pruning: train on exact labels, then time-to-optimum against
     the exhaustive search (every candidate) and against the exact search with
     the primary bound, on held-out queries.  Every search runs once untimed

@@ -475,6 +475,11 @@ __device__ __forceinline__ void ids_range(const MapCore& D, const Tabs& tabs, co
   I row, x;
   split_lin<I>(D, lin0, row, x);
   uint32_t base = row_base<I>(D, tabs, ctab, row);
+  // fast rows of at least 128 points, 32-bit indices: the next row's base is
+  // loaded a wrap ahead, so its latency overlaps the groups in between
+  const bool ahead = MODE != M_GENERAL && sizeof(I) == 4 && Llast >= 128;
+  const I rows = N / Llast;
+  uint32_t nbase = ahead && row + 1 < rows ? row_base_inl<uint32_t>(D, tabs, ctab, (uint32_t)(row + 1), last) : 0;
   for (; g < gend; g += 32, lin0 += 128) {
     uint32_t v0, v1, v2, v3;
     int cnt = 4;
@@ -523,7 +528,12 @@ __device__ __forceinline__ void ids_range(const MapCore& D, const Tabs& tabs, co
       } else {
         split_lin<I>(D, lin0 + 128, row, x);
       }
-      base = row_base<I>(D, tabs, ctab, row);
+      if (ahead) {
+        base = nbase;
+        nbase = row + 1 < rows ? row_base_inl<uint32_t>(D, tabs, ctab, (uint32_t)(row + 1), last) : 0;
+      } else {
+        base = row_base<I>(D, tabs, ctab, row);
+      }
     }
   }
 }
