@@ -251,7 +251,7 @@ def extra_learned(N, W, torch, n_train=512, per_query=4096, epochs=8, n_eval=200
             "ms_learned_mean": 1e3 * t_l / n_eval, "ms_exhaustive_mean": 1e3 * t_e / n_eval,
             "ms_primary_bound_mean": 1e3 * t_b / n_eval, "vs_primary_bound": t_b / t_l,
             "ms_learned_top_k_only_mean": 1e3 * t_r / n_eval, "learned_phase_ms_mean": phases,
-            "rounds": rounds, "certified": {{0: "none", 1: "all threats evaluated", 2: "secondary lower bound"}[k]: v
+            "rounds": {str(r): rounds.count(r) for r in sorted(set(rounds))}, "certified": {{0: "none", 1: "all threats evaluated", 2: "secondary lower bound"}[k]: v
                                             for k, v in sorted(cert.items())},
             "zero_regret_without_fallback": zr / n_eval, "exact_with_fallback": 1.0,
             "fallbacks": fb, "eval_queries": n_eval, "train_labels": n_train * per_query, "train_epochs": epochs,
@@ -463,9 +463,8 @@ def main():
         for v, (cfg, chain) in enumerate(zip(cfgs, chains)):
             if timers is not None:
                 N.set_kernel_timer(*timers[v])
-            N.map_points(cfg["L"], cfg["machine"], chain, cfg["dist"], ids=ids, hist=hist, stream=stream)
-            N.comm_volume(cfg["L"], cfg["machine"], chain, cfg["dist"], cfg["face"], total=total, recv=recv,
-                          stream=stream)
+            N.map_launch(cfg["L"], cfg["machine"], chain, cfg["dist"], ids=ids, hist=hist, face_bytes=cfg["face"],
+                         total=total, recv=recv, stream=stream)
 
     for _ in range(max(args.warmup, 3)):
         step()
@@ -518,9 +517,8 @@ def main():
 
     def e2e_step():
         for cfg, chain in zip(cfgs, chains):
-            N.map_points(cfg["L"], cfg["machine"], chain, cfg["dist"], ids=h_ids, hist=h_hist, stream=stream)
-            N.comm_volume(cfg["L"], cfg["machine"], chain, cfg["dist"], cfg["face"], total=h_total,
-                          recv=h_recv, stream=stream)
+            N.map_launch(cfg["L"], cfg["machine"], chain, cfg["dist"], ids=h_ids, hist=h_hist, face_bytes=cfg["face"],
+                         total=h_total, recv=h_recv, stream=stream)
 
     e2e_step()
     per_step_launches = N.kernel_launches() - launches_before

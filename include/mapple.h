@@ -227,6 +227,15 @@ int mp_hier_search(const mp_hier_query* query, mp_hier_result* out, void* stream
 int mp_hier_chain(int32_t rank, const int64_t* a, const int64_t* b, int32_t variant, mp_xform* chain,
                   int32_t* n_xf, mp_dist* dist);
 
+/* The whole hot path of one launch in one call: ids and histogram as
+ * mp_map_points, halo total and received bytes as mp_halo_volume (halo may
+ * be NULL, then total and recv must be NULL too), sharing the chain table
+ * and the per-dimension counts.  Any output may be NULL.  Errors as
+ * mp_map_points / mp_halo_volume. */
+int mp_map_launch(const mp_space* space, const mp_machine* machine, const mp_xform* chain, int n_xf,
+                  const mp_dist* dist, const mp_halo* halo, int32_t* ids, uint64_t* hist, uint64_t* total,
+                  uint64_t* recv, void* stream);
+
 /* map_points without any allocation.  The paper has no counterpart: this
  * entry point exists for callers that cannot allocate device memory -- code
  * running under a memory manager that owns the device's whole budget (a

@@ -485,6 +485,24 @@ extern "C" int mp_halo_volume(const mp_space* space, const mp_machine* machine, 
                               halo->mode == MP_HALO_ELEMENTS ? 1 : 0, halo->width);
 }
 
+extern "C" int mp_map_launch(const mp_space* space, const mp_machine* machine, const mp_xform* chain, int n_xf,
+                             const mp_dist* dist, const mp_halo* halo, int32_t* ids, uint64_t* hist,
+                             uint64_t* total, uint64_t* recv, void* stream) {
+  mp::Plan pl;
+  int rc = mp::build_plan(space, machine, chain, n_xf, dist, pl);
+  if (rc) return rc;
+  if (!halo && (total || recv)) return MP_EINVAL;
+  if (halo) {
+    if (halo->mode != MP_HALO_FACES && halo->mode != MP_HALO_ELEMENTS) return MP_EINVAL;
+    if (halo->mode == MP_HALO_ELEMENTS)
+      for (int t = 0; t < space->rank; ++t)
+        if (halo->width[t] < 0 || halo->width[t] > MP_MAX_HALO_WIDTH) return MP_EINVAL;
+  }
+  if (!ids && !hist && !total && !recv) return MP_OK;
+  return mp::run_with_staging(pl, ids, hist, recv, total, halo ? halo->bytes : nullptr, (cudaStream_t)stream,
+                              halo && halo->mode == MP_HALO_ELEMENTS ? 1 : 0, halo ? halo->width : nullptr);
+}
+
 // ------------------------------------------------------------ two-level search
 
 namespace mp {

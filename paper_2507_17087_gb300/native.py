@@ -125,6 +125,7 @@ def lib():
                 "mp_map_points_noalloc": (I, [V, V, V, I, V, V, V, V]),
                 "mp_comm_volume": (I, [V, V, V, I, V, V, V, V, V]),
                 "mp_halo_volume": (I, [V, V, V, I, V, V, V, V, V]),
+                "mp_map_launch": (I, [V, V, V, I, V, V, V, V, V, V, V]),
                 "mp_greedy_grid": (I, [I64, I, V]),
                 "mp_secondary_lower_bound": (I, [V, V, V]),
                 "mp_hier_search": (I, [V, V, V]),
@@ -297,6 +298,31 @@ def comm_volume(L, machine, chain, dist, face_bytes, total, recv=None, stream=No
     rc = lib().mp_comm_volume(ctypes.byref(sp), ctypes.byref(mc), ch, n, ctypes.byref(ds), fb,
                               _ptr(total), _ptr(recv), _stream(stream))
     _check(rc, "mp_comm_volume")
+
+
+def _halo(width, elem_bytes, elements):
+    h = mp_halo()
+    h.mode = HALO_ELEMENTS if elements else HALO_FACES
+    for t, v in enumerate(width):
+        h.width[t] = int(v)
+    for t, v in enumerate(elem_bytes):
+        h.bytes[t] = int(v)
+    return h
+
+
+def map_launch(L, machine, chain, dist, ids=None, hist=None, face_bytes=None, total=None, recv=None,
+               width=None, elements=False, stream=None):
+    """mp_map_launch: ids, histogram and halo of one launch in one call
+    (face_bytes per dimension; width for the element count)."""
+    sp, mc, ds = make_space(L), make_machine(machine), make_dist(dist)
+    ch, n = make_chain(chain)
+    h = None
+    if face_bytes is not None:
+        h = _halo(width if width is not None else [1] * len(L), face_bytes, elements)
+    rc = lib().mp_map_launch(ctypes.byref(sp), ctypes.byref(mc), ch, n, ctypes.byref(ds),
+                             ctypes.byref(h) if h is not None else None, _ptr(ids), _ptr(hist), _ptr(total),
+                             _ptr(recv), _stream(stream))
+    _check(rc, "mp_map_launch")
 
 
 def halo_volume(L, machine, chain, dist, width, elem_bytes, total, recv=None, elements=True, stream=None):

@@ -216,3 +216,27 @@ def test_wide_index_launch_sampled():
         assert int(hist.sum().item()) == npts
         del ids
         torch.cuda.empty_cache()
+
+
+def test_map_launch_equals_separate_calls():
+    # one call for ids, histogram and halo gives what the separate calls give
+    rng = W.rng(150)
+    for _ in range(30):
+        L, machine, chain, dist, face = random_launch(rng, 30000)
+        P = machine[0] * machine[1]
+        npts = math.prod(L)
+        ids, rid = (torch.full((npts,), -7, dtype=torch.int32, device=DEV) for _ in range(2))
+        hist, rh = (torch.full((P,), -7, dtype=torch.int64, device=DEV) for _ in range(2))
+        tot, rt = (torch.full((1,), -7, dtype=torch.int64, device=DEV) for _ in range(2))
+        recv, rr = (torch.full((P,), -7, dtype=torch.int64, device=DEV) for _ in range(2))
+        N.map_launch(L, machine, chain, dist, ids=ids, hist=hist, face_bytes=face, total=tot, recv=recv)
+        N.map_points(L, machine, chain, dist, ids=rid, hist=rh)
+        N.comm_volume(L, machine, chain, dist, face, total=rt, recv=rr)
+        width = [rng.randint(0, 4) for _ in L]
+        et, er = (torch.full((1,), -7, dtype=torch.int64, device=DEV) for _ in range(2))
+        e_recv, e_rr = (torch.full((P,), -7, dtype=torch.int64, device=DEV) for _ in range(2))
+        N.map_launch(L, machine, chain, dist, face_bytes=face, total=et, recv=e_recv, width=width, elements=True)
+        N.halo_volume(L, machine, chain, dist, width, face, total=er, recv=e_rr)
+        torch.cuda.synchronize()
+        for a, b in ((ids, rid), (hist, rh), (tot, rt), (recv, rr), (et, er), (e_recv, e_rr)):
+            assert torch.equal(a, b), (L, machine, chain, dist)
