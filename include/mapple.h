@@ -360,6 +360,11 @@ int mp_batch_info(const mp_batch* batch, uint64_t* total_ids, uint64_t* total_pr
 int mp_batch_run(mp_batch* batch, int32_t* ids, uint64_t* hist, uint64_t* halo, uint64_t* recv, int flags,
                  void* stream);
 
+/* Sets the persistent id writer's tile size (4-point groups per tile, > 0),
+ * e.g. one an earlier autotuning chose for the same batch: the persisted
+ * autotune result.  The next run recaptures its graph.  Host side. */
+int mp_batch_set_tile(mp_batch* batch, int32_t tile_groups);
+
 int mp_batch_destroy(mp_batch* batch);
 
 /* ------------------------------------------------------------ learned cost model */
@@ -504,6 +509,29 @@ int mp_set_kernel_timer(void* start_event, void* stop_event);
 /* Bytes of launch description one kernel launch carries to the device as
  * parameters (the host-to-device input of a mapping call). */
 uint64_t mp_descriptor_bytes(void);
+
+/* ------------------------------------------------------------ checkpoint, self-tests */
+
+/* Model checkpoint (training can resume from it): a binary file with a
+ * versioned header -- 8 bytes "MAPLEMLP", uint32 format version (1), uint32
+ * parameter count, int64 Adam step -- followed by the float32 parameters and
+ * the two float32 Adam moment arrays.  mp_mlp_load rejects another magic,
+ * version or parameter count (MP_EINVAL) and a short file (MP_EINVAL);
+ * MP_ECUDA / file errors otherwise.  Synchronous. */
+int mp_mlp_save(const mp_mlp* model, const char* path);
+int mp_mlp_load(mp_mlp* model, const char* path);
+
+/* Device-side failure reporting without a fault: one CTA waits on an
+ * mbarrier that nothing arrives on, with the same bounded polling the
+ * tensor-core kernels use, `limit` polls (1 .. 2^26), and records
+ * MP_ETIMEOUT in a status word; returns that status (MP_ETIMEOUT expected).
+ * The context stays usable.  Synchronous. */
+int mp_selftest_wait_timeout(uint32_t limit, void* stream);
+
+/* Host-side fault injection: the next n requests for device workspace fail
+ * as if the allocation had failed (the calls return MP_ENOMEM before
+ * launching anything).  n = 0 clears it. */
+int mp_debug_fail_allocations(int32_t n);
 
 /* Human-readable text of a status code (static storage). */
 const char* mp_strerror(int status);

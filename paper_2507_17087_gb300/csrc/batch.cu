@@ -639,6 +639,19 @@ extern "C" int mp_batch_run(mp_batch* b, int32_t* ids, uint64_t* hist, uint64_t*
   return MP_OK;
 }
 
+extern "C" int mp_batch_set_tile(mp_batch* b, int32_t tile_groups) {
+  using namespace mp;
+  if (!b || tile_groups < 1) return MP_EINVAL;
+  std::lock_guard<std::mutex> lock(b->mu);
+  int rc = upload_tiles(*b, (uint32_t)tile_groups);
+  if (rc) return rc;
+  if (b->exec) {
+    cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
+  }
+  return MP_OK;
+}
+
 extern "C" int mp_batch_destroy(mp_batch* b) {
   if (!b) return MP_OK;
   if (b->exec) cudaGraphExecDestroy(b->exec);

@@ -10,6 +10,7 @@
 // the four warps read the accumulator back (32 rows each) for the epilogue.
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <vector>
 
@@ -514,4 +515,90 @@ extern "C" int mp_mlp_train_step(mp_mlp* h, const void* X, const float* target, 
   MP_CUDA_TRY(cudaStreamSynchronize(st));
   if (loss) *loss = l;
   return s;
+}
+
+// ------------------------------------------------------------ checkpoint
+
+namespace mp {
+namespace mlpk {
+namespace {
+
+constexpr char kMagic[8] = {'M', 'A', 'P', 'L', 'E', 'M', 'L', 'P'};
+constexpr uint32_t kFormat = 1;
+
+struct CkptHeader {
+  char magic[8];
+  uint32_t version;
+  uint32_t nparam;
+  int64_t step;
+};
+
+// Waits on an mbarrier that nothing arrives on, as the tensor-core kernels
+// wait on theirs: bounded polling, then MP_ETIMEOUT in the status word.
+__global__ void k_wait_nobody(uint32_t limit, int* status) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    tc::mbar_init(&bar, 1);
+    tc::fence_mbar_init();
+  }
+  __syncthreads();
+  const bool done = tc::mbar_wait(&bar, 0, limit);
+  if (!done && threadIdx.x == 0) atomicExch(status, MP_ETIMEOUT);
+}
+
+}  // namespace
+}  // namespace mlpk
+}  // namespace mp
+
+extern "C" int mp_mlp_save(const mp_mlp* h, const char* path) {
+  using namespace mp::mlpk;
+  if (!h || !path) return MP_EINVAL;
+  std::vector<float> buf(3 * NPARAM);
+  MP_CUDA_TRY(cudaMemcpy(buf.data(), h->P, NPARAM * 4, cudaMemcpyDeviceToHost));
+  MP_CUDA_TRY(cudaMemcpy(buf.data() + NPARAM, h->M1, NPARAM * 4, cudaMemcpyDeviceToHost));
+  MP_CUDA_TRY(cudaMemcpy(buf.data() + 2 * NPARAM, h->M2, NPARAM * 4, cudaMemcpyDeviceToHost));
+  CkptHeader hd;
+  std::memcpy(hd.magic, kMagic, 8);
+  hd.version = kFormat;
+  hd.nparam = (uint32_t)NPARAM;
+  hd.step = h->step;
+  FILE* f = std::fopen(path, "wb");
+  if (!f) return MP_EINVAL;
+  const bool ok = std::fwrite(&hd, sizeof(hd), 1, f) == 1 && std::fwrite(buf.data(), 4, buf.size(), f) == buf.size();
+  const bool closed = std::fclose(f) == 0;
+  return ok && closed ? MP_OK : MP_EINVAL;
+}
+
+extern "C" int mp_mlp_load(mp_mlp* h, const char* path) {
+  using namespace mp::mlpk;
+  if (!h || !path) return MP_EINVAL;
+  FILE* f = std::fopen(path, "rb");
+  if (!f) return MP_EINVAL;
+  CkptHeader hd;
+  std::vector<float> buf(3 * NPARAM);
+  const bool ok = std::fread(&hd, sizeof(hd), 1, f) == 1 && std::memcmp(hd.magic, kMagic, 8) == 0 &&
+                  hd.version == kFormat && hd.nparam == (uint32_t)NPARAM &&
+                  std::fread(buf.data(), 4, buf.size(), f) == buf.size();
+  std::fclose(f);
+  if (!ok) return MP_EINVAL;
+  MP_CUDA_TRY(cudaMemcpy(h->M1, buf.data() + NPARAM, NPARAM * 4, cudaMemcpyHostToDevice));
+  MP_CUDA_TRY(cudaMemcpy(h->M2, buf.data() + 2 * NPARAM, NPARAM * 4, cudaMemcpyHostToDevice));
+  h->step = (int)hd.step;
+  return upload_params(h, buf.data(), nullptr);
+}
+
+extern "C" int mp_selftest_wait_timeout(uint32_t limit, void* stream) {
+  using namespace mp;
+  if (limit < 1 || limit > (1u << 26)) return MP_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  int* status = (int*)workspace(sizeof(int), 6);
+  if (!status) return MP_ENOMEM;
+  MP_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(int), st));
+  mlpk::k_wait_nobody<<<1, 32, 0, st>>>(limit, status);
+  count_launch();
+  MP_CUDA_TRY(cudaGetLastError());
+  int h = 0;
+  MP_CUDA_TRY(cudaMemcpyAsync(&h, status, sizeof(int), cudaMemcpyDeviceToHost, st));
+  MP_CUDA_TRY(cudaStreamSynchronize(st));
+  return h;
 }

@@ -22,6 +22,7 @@ struct Ws {
 Ws g_ws[kMaxDevices];
 std::mutex g_ws_mu;
 std::atomic<uint64_t> g_launches{0};
+std::atomic<int> g_fail_allocs{0};   // injected workspace failures still to deliver
 
 }  // namespace
 
@@ -29,6 +30,8 @@ void* workspace(size_t bytes, int slot) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return nullptr;
   if (slot < 0 || slot >= kSlots) return nullptr;
+  for (int left = g_fail_allocs.load(); left > 0;)
+    if (g_fail_allocs.compare_exchange_weak(left, left - 1)) return nullptr;
   std::lock_guard<std::mutex> lock(g_ws_mu);
   Ws& w = g_ws[dev];
   if (bytes == 0) bytes = 256;
@@ -134,3 +137,9 @@ extern "C" int mp_set_kernel_timer(void* start_event, void* stop_event) {
 }
 
 extern "C" uint64_t mp_descriptor_bytes(void) { return sizeof(mp::MapDesc); }
+
+extern "C" int mp_debug_fail_allocations(int32_t n) {
+  if (n < 0) return MP_EINVAL;
+  mp::g_fail_allocs.store(n);
+  return MP_OK;
+}

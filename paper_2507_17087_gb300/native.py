@@ -16,6 +16,8 @@ Distributions: ("block",), ("cyclic",), ("block_cyclic", b), ("hier",),
 from __future__ import annotations
 
 import ctypes
+import hashlib
+import json
 import os
 import threading
 
@@ -127,6 +129,11 @@ def lib():
                 "mp_halo_volume": (I, [V, V, V, I, V, V, V, V, V]),
                 "mp_map_launch": (I, [V, V, V, I, V, V, V, V, V, V, V]),
                 "mp_greedy_grid": (I, [I64, I, V]),
+                "mp_batch_set_tile": (I, [V, I]),
+                "mp_mlp_save": (I, [V, ctypes.c_char_p]),
+                "mp_mlp_load": (I, [V, ctypes.c_char_p]),
+                "mp_selftest_wait_timeout": (I, [ctypes.c_uint32, V]),
+                "mp_debug_fail_allocations": (I, [I]),
                 "mp_secondary_lower_bound": (I, [V, V, V]),
                 "mp_hier_search": (I, [V, V, V]),
                 "mp_hier_chain": (I, [I, V, V, I, V, V, V]),
@@ -372,6 +379,16 @@ def hier_search(L, machine, variant, width, elem_bytes, stream=None):
             "secondary": r.secondary_bytes, "n_candidates": r.n_candidates}
 
 
+def selftest_wait_timeout(limit=1000, stream=None):
+    """Status of a bounded wait that nothing completes (MP_ETIMEOUT)."""
+    return lib().mp_selftest_wait_timeout(int(limit), _stream(stream))
+
+
+def debug_fail_allocations(n):
+    """Make the next n device workspace requests fail (host-side injection)."""
+    _check(lib().mp_debug_fail_allocations(int(n)), "mp_debug_fail_allocations")
+
+
 def greedy_grid(d, k):
     """Algorithm A1's processor grid (host only)."""
     out = (ctypes.c_int64 * 4)()
@@ -531,6 +548,9 @@ class Batch:
     def __init__(self, launches):
         launches = list(launches)
         self.n = len(launches)
+        # identifies the batch's queries (for the persisted autotune choice)
+        self.signature = hashlib.sha256(repr([(tuple(L), tuple(m), [tuple(o) for o in ch], tuple(d), tuple(f))
+                                              for L, m, ch, d, f in launches]).encode()).hexdigest()
         arr = (mp_query * self.n)()
         keep = []
         for q, (L, machine, chain, dist, face) in enumerate(launches):
@@ -555,6 +575,30 @@ class Batch:
                                    po.ctypes.data, ctypes.byref(tg)), "mp_batch_info")
         return {"total_ids": ti.value, "total_procs": tp.value, "ids_offsets": io, "proc_offsets": po,
                 "tile_groups": tg.value}
+
+    def set_tile(self, tile_groups):
+        _check(lib().mp_batch_set_tile(self._h, int(tile_groups)), "mp_batch_set_tile")
+
+    def autotune_cached(self, cache_path, ids, stream=None):
+        """The id writer's tile size from a JSON cache (version 1, keyed by
+        the batch signature), or autotuned now and recorded there."""
+        cache = {"version": 1, "tiles": {}}
+        if os.path.exists(cache_path):
+            with open(cache_path) as f:
+                loaded = json.load(f)
+            if loaded.get("version") == 1 and isinstance(loaded.get("tiles"), dict):
+                cache = loaded
+        tile = cache["tiles"].get(self.signature)
+        if tile is not None:
+            self.set_tile(tile)
+            return int(tile)
+        self.run(ids=ids, autotune=True, stream=stream)
+        cache["tiles"][self.signature] = int(self.info()["tile_groups"])
+        tmp = cache_path + f".tmp{os.getpid()}"
+        with open(tmp, "w") as f:
+            json.dump(cache, f)
+        os.replace(tmp, cache_path)
+        return cache["tiles"][self.signature]
 
     def run(self, ids=None, hist=None, halo=None, recv=None, autotune=False, graph=True, stream=None):
         flags = (BATCH_AUTOTUNE if autotune else 0) | (0 if graph else BATCH_NO_GRAPH)
@@ -658,6 +702,13 @@ class MLP:
                     "ms": {"prepare": st.ms_prepare, "model": st.ms_model, "exact": st.ms_exact,
                            "fallback": st.ms_fallback}})
         return res
+
+    def save(self, path):
+        """Checkpoint: parameters, Adam moments and step (versioned header)."""
+        _check(lib().mp_mlp_save(self._h, os.fsencode(path)), "mp_mlp_save")
+
+    def load(self, path):
+        _check(lib().mp_mlp_load(self._h, os.fsencode(path)), "mp_mlp_load")
 
     def scores(self, query, scores, features=None, stream=None):
         q = _query(query)

@@ -209,3 +209,38 @@ def stencil_study_configs():
                 out.append({"name": f"stencil-1:{r}-{area}-{G}", "L": (X, r * X),
                             "machine": (nodes, STUDY_GPUS_PER_NODE), "ratio": r, "area": area, "gpus": G})
     return out
+
+
+# ------------------------------------------------------ application shapes
+#
+# Launch shapes of the paper's applications (Sec. 6: Circuit, PENNANT,
+# Stencil, Cannon, SUMMA, PUMMA, Johnson, COSMA), at 2^28-2^29 points on
+# 64 nodes x 8 processors; the applications' own sizes are not given, so the
+# piece counts are powers of two chosen to fill 1-2 GB of ids.
+
+def application_shapes():
+    n, g = 64, 8
+    P = n * g
+    return [
+        # Circuit: a 1-D launch of pieces, c per processor, block over P
+        {"name": "circuit-1d-block", "L": (P * (1 << 20),), "machine": (n, g), "chain": [],
+         "dist": ("block",), "face": (8,)},
+        # PENNANT-like: 1-D zone chunks dealt block-cyclically
+        {"name": "pennant-1d-block-cyclic", "L": (P * (1 << 20),), "machine": (n, g), "chain": [],
+         "dist": ("block_cyclic", 1024), "face": (8,)},
+        # 2-D stencil: block mapping through decompose (Sec. 4)
+        {"name": "stencil-2d-decompose", "L": (16384, 32768), "machine": (n, g),
+         "chain": [("merge", 0, 1), ("decompose", 0, (16384, 32768))], "dist": ("block",), "face": (8, 8)},
+        # Cannon: the hierarchical block / cyclic mapper of Appendix A.1
+        {"name": "cannon-2d-hier", "L": (16384, 16384), "machine": (n, g), "chain": [],
+         "dist": ("hier",), "face": (8, 8)},
+        # SUMMA: block over an explicit 16 x 32 processor grid
+        {"name": "summa-2d-block", "L": (16384, 16384), "machine": (n, g),
+         "chain": [("merge", 0, 1), ("split", 0, 16)], "dist": ("block",), "face": (8, 8)},
+        # PUMMA: block-cyclic over the same grid
+        {"name": "pumma-2d-block-cyclic", "L": (16384, 16384), "machine": (n, g),
+         "chain": [("merge", 0, 1), ("split", 0, 16)], "dist": ("block_cyclic", 256), "face": (8, 8)},
+        # Johnson / COSMA: a cubic 8 x 8 x 8 grid over a 3-D launch
+        {"name": "johnson-3d-cubic", "L": (512, 1024, 512), "machine": (n, g),
+         "chain": [("merge", 0, 1), ("split", 0, 8), ("split", 1, 8)], "dist": ("block",), "face": (8, 8, 8)},
+    ]
