@@ -311,6 +311,43 @@ def extra_hier_search(N, W, torch):
             "workload": "1024x1024x512 on 64 x 8, node grid x GPU grid, width-1 element halo", **out}
 
 
+def extra_applications(N, W, torch, dev, reps=5):
+    """ids + histogram + halo of launches shaped like the paper's
+    applications (Circuit, PENNANT, stencil, Cannon, SUMMA, PUMMA,
+    Johnson/COSMA) on 64 x 8: points/s and the id stream's GB/s."""
+    out = []
+    for w in W.application_shapes():
+        npts = math.prod(w["L"])
+        P = w["machine"][0] * w["machine"][1]
+        ids = torch.empty(npts, dtype=torch.int32, device=dev)
+        hist = torch.empty(P, dtype=torch.int64, device=dev)
+        total = torch.empty(1, dtype=torch.int64, device=dev)
+        recv = torch.empty(P, dtype=torch.int64, device=dev)
+
+        def once():
+            N.map_launch(w["L"], w["machine"], w["chain"], w["dist"], ids=ids, hist=hist, face_bytes=w["face"],
+                         total=total, recv=recv)
+
+        for _ in range(2):
+            once()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            once()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        out.append({"workload": w["name"], "L": list(w["L"]), "points": npts, "ms": ms,
+                    "points_per_s": npts / (ms / 1e3), "ids_gbs": 4 * npts / (ms / 1e3) / 1e9})
+        del ids, hist, total, recv
+    torch.cuda.empty_cache()
+    pts = sum(o["points"] for o in out)
+    secs = sum(o["ms"] for o in out) / 1e3
+    return {"metric": "points mapped/s", "value": pts / secs, "unit": "points/s",
+            "note": "ids + histogram + halo per launch, one call each", "launches": out}
+
+
 def max_over_ranks(value: float, dist, device) -> float:
     """The largest value of all ranks (the job is as slow as its slowest
     rank); the value itself without a process group."""
@@ -560,7 +597,8 @@ def main():
                             ("batched", lambda: extra_batched(N, W, torch, dev)),
                             ("learned", lambda: extra_learned(N, W, torch)),
                             ("volume_study", lambda: extra_volume_study(N, W, torch, dev)),
-                            ("hier_search", lambda: extra_hier_search(N, W, torch))):
+                            ("hier_search", lambda: extra_hier_search(N, W, torch)),
+                            ("applications", lambda: extra_applications(N, W, torch, dev))):
                 try:
                     line[key] = fn()
                 except Exception as exc:  # noqa: BLE001 - an extra must not lose the main line

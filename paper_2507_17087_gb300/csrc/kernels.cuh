@@ -411,10 +411,32 @@ __device__ __forceinline__ void ids_range_rows(const MapCore& D, const Tabs& tab
   // the next row's base, loaded a wrap ahead so that its latency overlaps
   // the groups in between
   uint32_t nbase = row + 1 < rows ? row_base_inl<uint32_t>(D, tabs, ctab, row + 1, m) : 0;
+  // R_BLOCK / R_BCYC: the run [run_lo, run_hi) of the last dimension with
+  // one final coordinate (block, or block of b points) that holds x, with
+  // contribution rc; a group inside it has one id, looked up once
+  constexpr bool RUNS = SRC == R_BLOCK || SRC == R_BCYC;
+  const Comp& cl = D.comp[D.k - 1][0];
+  uint32_t rc = 0, run_lo = 1, run_hi = 0;
   for (; g < gend; g += 32, lin0 += 128) {
     const int cnt = N - lin0 < 4 ? (int)(N - lin0) : 4;
     uint32_t v[4] = {0, 0, 0, 0};
-    if (SRC == R_TAB4) {
+    if (RUNS && (x < run_lo || x >= run_hi)) {
+      rc = row_contrib<SRC>(D, Cf, x);
+      uint64_t lo, hi;
+      if (SRC == R_BLOCK) {
+        const uint64_t a = rc / cl.sigma;
+        lo = (a * cl.L + cl.s - 1) / cl.s;
+        hi = ((a + 1) * cl.L + cl.s - 1) / cl.s;
+      } else {
+        lo = (uint64_t)(x / cl.b) * cl.b;
+        hi = lo + cl.b;
+      }
+      run_lo = (uint32_t)lo;
+      run_hi = (uint32_t)(hi < Lf ? hi : Lf);
+    }
+    if (RUNS && x + 4 <= run_hi) {
+      v[0] = v[1] = v[2] = v[3] = T[base + rc];
+    } else if (SRC == R_TAB4) {
       const uint4 c = *reinterpret_cast<const uint4*>(Cf + x);
       v[0] = T[base + c.x]; v[1] = T[base + c.y]; v[2] = T[base + c.z]; v[3] = T[base + c.w];
     } else if (x + 4 <= Lf) {

@@ -90,6 +90,45 @@ __global__ void __launch_bounds__(kThreads) k_ids(const __grid_constant__ MapDes
   ids_range<I, MODE, TSMEM>(D, tabs, TSMEM ? Ts : Tg, Cs, ctab, gbeg, gend, threadIdx.x & 31, vec_ok, ids);
 }
 
+// Rows of Lf points (the dimensions m..k-1; their contributions computed
+// into shared memory by each CTA when SRC is a table source, or taken from
+// the last dimension's components in place) for launches whose last extent
+// is unaligned or untabled; 32-bit indices.
+template <int SRC, bool TSMEM>
+__global__ void __launch_bounds__(kThreads) k_ids_rows(const __grid_constant__ MapDesc D,
+                                                       const __grid_constant__ Tabs tabs,
+                                                       const uint32_t* __restrict__ Tg,
+                                                       const uint32_t* __restrict__ ctab, int m, uint32_t Lf,
+                                                       Div32 divLf, int vec_ok, uint64_t groups_per_warp,
+                                                       int32_t* __restrict__ ids) {
+  extern __shared__ __align__(16) uint32_t smem[];
+  uint32_t* Ts = smem;
+  uint32_t* Cf = smem + (TSMEM ? ((D.P + 3) & ~3u) : 0);
+  if (TSMEM)
+    for (uint32_t i = threadIdx.x; i < D.P; i += blockDim.x) Ts[i] = __ldg(Tg + i);
+  if (SRC == R_TAB || SRC == R_TAB4)
+    for (uint32_t x = threadIdx.x; x < Lf; x += blockDim.x) {
+      // row offset x -> coordinates of dimensions m..k-1 (C order)
+      uint32_t rest = x, c = 0;
+      for (int t = D.k - 1; t >= m; --t) {
+        uint32_t q, r;
+        divmod32(rest, D.divL32[t], q, r);
+        c += contrib(D, t, r);
+        rest = q;
+      }
+      Cf[x] = c;
+    }
+  __syncthreads();
+  const uint32_t groups = (uint32_t)((D.npoints + 3) / 4);
+  const uint32_t warp_id = blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5);
+  const uint64_t gb = (uint64_t)warp_id * groups_per_warp;
+  if (gb >= groups) return;
+  const uint32_t gbeg = (uint32_t)gb;
+  const uint64_t ge = gb + groups_per_warp;
+  const uint32_t gend = (uint32_t)(ge < groups ? ge : groups);
+  ids_range_rows<SRC>(D, tabs, TSMEM ? Ts : Tg, Cf, ctab, m, Lf, divLf, gbeg, gend, threadIdx.x & 31, vec_ok, ids);
+}
+
 template <typename I, bool TSMEM>
 __global__ void __launch_bounds__(kThreads) k_ids_lc(const __grid_constant__ MapDesc D,
                                                      const uint32_t* __restrict__ Tg, int vec_ok,
@@ -324,6 +363,36 @@ int run_launch_ws(const Plan& pl, const Want& w, const Layout& ly, char* ws, cud
     } else {
       const bool aligned = D.L[last] % 4 == 0 && tabs.has[last];
       const int mode = !aligned ? M_GENERAL : (D.L[last] <= kSmemLastMax ? M_FAST_SMEM : M_FAST_GLOBAL);
+      if (mode == M_GENERAL && !wide) {
+        // unaligned or untabled rows: fuse trailing dimensions into rows of
+        // up to 4096 points with a table in shared memory, or compute the
+        // last dimension's contribution in place
+        int m = last;
+        uint64_t Lf = D.L[last];
+        while (m > 0 && Lf < 2048 && Lf * D.L[m - 1] <= 4096) Lf *= D.L[--m];
+        int src;
+        if (Lf <= 4096) src = Lf % 4 == 0 ? R_TAB4 : R_TAB;
+        else if (D.ncomp[last] == 2) src = R_HIER;
+        else src = D.comp[last][0].kind == C_BLOCK ? R_BLOCK : (D.comp[last][0].kind == C_CYCLIC ? R_CYCLIC : R_BCYC);
+        const Div32 divLf = make_div32((uint32_t)Lf);
+        const size_t sm = tbytes + (src <= R_TAB4 ? (size_t)((Lf + 3) & ~3ull) * 4 : 0);
+#define MP_ROWS(SRC, TS) go((const void*)k_ids_rows<SRC, TS>, sm, [&](unsigned b, uint64_t gpw) { \
+        k_ids_rows<SRC, TS><<<b, kThreads, sm, st>>>(D, tabs, T, ctab, m, (uint32_t)Lf, divLf, vec_ok, gpw, w.ids); })
+#define MP_ROWS_T(SRC) do { if (tsmem) MP_ROWS(SRC, true); else MP_ROWS(SRC, false); } while (0)
+        switch (src) {
+          case R_TAB4: MP_ROWS_T(R_TAB4); break;
+          case R_TAB: MP_ROWS_T(R_TAB); break;
+          case R_BLOCK: MP_ROWS_T(R_BLOCK); break;
+          case R_CYCLIC: MP_ROWS_T(R_CYCLIC); break;
+          case R_BCYC: MP_ROWS_T(R_BCYC); break;
+          default: MP_ROWS_T(R_HIER); break;
+        }
+#undef MP_ROWS_T
+#undef MP_ROWS
+        timer_end(st);
+        MP_CUDA_TRY(cudaGetLastError());
+        goto ids_done;
+      }
       const size_t sm = tbytes + (mode == M_FAST_SMEM ? (size_t)D.L[last] * 4 : 0);
 #define MP_IDS(I, MODE, TS) go((const void*)k_ids<I, MODE, TS>, sm, [&](unsigned b, uint64_t gpw) { \
         k_ids<I, MODE, TS><<<b, kThreads, sm, st>>>(D, tabs, T, ctab, vec_ok, gpw, w.ids); })
@@ -339,6 +408,7 @@ int run_launch_ws(const Plan& pl, const Want& w, const Layout& ly, char* ws, cud
     timer_end(st);
     MP_CUDA_TRY(cudaGetLastError());
   }
+ids_done:
   // ------------------------------------------------ reductions
   if (ly.need_red) {
     if (w.total) MP_CUDA_TRY(cudaMemsetAsync(w.total, 0, 8, st));
