@@ -4,15 +4,16 @@
 // mp_batch_create plans every query once (validation, decompose expansion,
 // rank fix-up), lays out one pool per kind of scratch (chain tables, c_t
 // tables, per-dimension counts, linear-cyclic deficits) and uploads the
-// per-query descriptors.  mp_batch_run replays a graph of six kernels:
+// per-query descriptors.  mp_batch_run replays a graph of these kernels:
 //   k_b_resolve  chain table of every query          (sum P threads)
 //   k_b_tables   c_t tables of every query           (sum of tabled L_t)
 //   k_b_counts   closed-form per-dimension counts     (sum J)
-//   k_b_slabs    linear-cyclic boundary deficits
+//   k_b_slabs    linear-cyclic boundary deficits as residue ranges
+//   k_b_defscan  their prefix sums
 //   k_b_ids      persistent id writer: CTAs pull fixed-size tiles of 4-point
 //                groups from an atomic work counter, stage the tile's chain
-//                table (and c_last) in shared memory when the query changes,
-//                and write the tile with the same warp-range loop as k_ids
+//                table (and its row contributions) in shared memory when the
+//                query changes, and write the tile with k_ids's warp loops
 //   k_b_reduce   histogram, received bytes, halo total per query
 // The tile size is picked on the first run by timing the persistent kernel
 // at a few sizes (autotune) and kept with the batch.
@@ -133,15 +134,115 @@ struct Slab {
   uint64_t begin;   // first work index of this slab pair
 };
 
+// Linear-cyclic face deficits as residue ranges.  The points of slab x_t of
+// dimension t are lin = hi * (L_t S_t) + x_t S_t + lo, lo < S_t (S_t the
+// stride of t), hi < N / (L_t S_t): for each (slab, hi) their residues
+// lin mod P form one cyclic run of S_t residues from r0.  Whole turns add to
+// every residue (defall), the rest of the run goes into a difference array
+// (deficit, prefix-summed by k_b_defscan).  Work: 2 N / (L_t S_t) entries
+// per dimension instead of one per slab point.
 __global__ void __launch_bounds__(kThreads) k_b_slabs(const QDesc* __restrict__ qd, const Slab* __restrict__ slabs,
                                                       const uint64_t* __restrict__ slab_pref, uint32_t nslabs,
-                                                      uint64_t total, unsigned long long* __restrict__ deficit) {
+                                                      uint64_t total, unsigned long long* __restrict__ deficit,
+                                                      unsigned long long* __restrict__ defall) {
   for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
        e += (uint64_t)gridDim.x * blockDim.x) {
     const uint32_t i = find_query(slab_pref, nslabs, e);
     const Slab sl = slabs[i];
     const QDesc& Q = qd[sl.q];
-    atomicAdd(deficit + Q.p_off + lc_slab_F(Q, sl.t, e - sl.begin), (unsigned long long)Q.face[sl.t]);
+    const uint32_t t = (uint32_t)sl.t;
+    const uint64_t S = Q.lc_stride[t], Lt = Q.L[t];
+    const uint64_t H = Q.npoints / (Lt * S);
+    const uint64_t local = e - sl.begin;
+    const uint64_t side = local / H, hi = local - side * H;
+    const uint64_t xt = side ? Lt - 1 : 0;
+    const unsigned long long f = Q.face[t];
+    uint64_t q0, r0;
+    divmod64(hi * (Lt * S) + xt * S, Q.divP64, q0, r0);
+    uint64_t full, rem;
+    divmod64(S, Q.divP64, full, rem);
+    if (full) atomicAdd(defall + sl.q, full * f);
+    if (rem) {
+      unsigned long long* D = deficit + Q.p_off;
+      const uint64_t end = r0 + rem;
+      atomicAdd(D + r0, f);
+      if (end < Q.P) {
+        atomicAdd(D + end, (unsigned long long)(-(long long)f));
+      } else if (end > Q.P) {
+        atomicAdd(D, f);
+        atomicAdd(D + (end - Q.P), (unsigned long long)(-(long long)f));
+      }
+    }
+  }
+}
+
+// Extended Euclid: g = gcd(a, m) and the inverse of a / g modulo m / g.
+__device__ __forceinline__ void gcd_inverse(int64_t a, int64_t m, int64_t& g, int64_t& inv) {
+  int64_t r0 = a, r1 = m, s0 = 1, s1 = 0;
+  while (r1 != 0) {
+    const int64_t q = r0 / r1;
+    int64_t tmp = r0 - q * r1; r0 = r1; r1 = tmp;
+    tmp = s0 - q * s1; s0 = s1; s1 = tmp;
+  }
+  g = r0;
+  const int64_t mg = m / g;
+  inv = mg == 1 ? 0 : ((s0 % mg) + mg) % mg;
+}
+
+// Prefix sum of each linear-cyclic query's difference array, plus its whole
+// turns: the deficit of every residue.  The last dimension's slabs (stride 1:
+// points hi * L + x, hi < N / L) are counted per residue F instead, in closed
+// form: hi * L = F - x (mod P) has solutions iff g = gcd(L mod P, P) divides
+// F - x, and then hi = h0 (mod P / g).  One CTA per query.
+__global__ void __launch_bounds__(kThreads) k_b_defscan(const QDesc* __restrict__ qd,
+                                                        unsigned long long* __restrict__ deficit,
+                                                        const unsigned long long* __restrict__ defall) {
+  const QDesc& Q = qd[blockIdx.x];
+  if (!Q.lc) return;
+  __shared__ unsigned long long part[kThreads];
+  __shared__ int64_t s_g, s_inv;
+  const int last = Q.k - 1;
+  const bool last_slabs = Q.lc_stride_mod[last] != 0 && Q.face[last] != 0;
+  if (threadIdx.x == 0 && last_slabs) {
+    int64_t g, inv;
+    gcd_inverse((int64_t)(Q.L[last] % Q.P), (int64_t)Q.P, g, inv);
+    s_g = g;
+    s_inv = inv;
+  }
+  unsigned long long* D = deficit + Q.p_off;
+  const uint32_t P = Q.P;
+  const uint32_t per = (P + kThreads - 1) / kThreads;
+  const uint32_t lo = min(P, threadIdx.x * per), hi = min(P, lo + per);
+  unsigned long long sum = 0;
+  for (uint32_t i = lo; i < hi; ++i) sum += D[i];
+  part[threadIdx.x] = sum;
+  __syncthreads();
+  for (int o = 1; o < kThreads; o <<= 1) {
+    const unsigned long long v = threadIdx.x >= (unsigned)o ? part[threadIdx.x - o] : 0;
+    __syncthreads();
+    part[threadIdx.x] += v;
+    __syncthreads();
+  }
+  unsigned long long run = (threadIdx.x ? part[threadIdx.x - 1] : 0) + defall[blockIdx.x];
+  for (uint32_t i = lo; i < hi; ++i) {
+    run += D[i];
+    D[i] = run;
+  }
+  if (last_slabs) {
+    const int64_t g = s_g, inv = s_inv, M = (int64_t)P / g;
+    const uint64_t Lt = Q.L[last], H = Q.npoints / Lt;
+    const unsigned long long f = Q.face[last];
+    for (uint32_t i = lo; i < hi; ++i) {
+      unsigned long long add = 0;
+      for (int side = 0; side < 2; ++side) {
+        const int64_t x = side ? (int64_t)((Lt - 1) % P) : 0;
+        const int64_t c = ((int64_t)i - x + (int64_t)P) % (int64_t)P;
+        if (c % g) continue;
+        const int64_t h0 = M == 1 ? 0 : (int64_t)(((unsigned __int128)(c / g) * (uint64_t)inv) % (uint64_t)M);
+        add += count_residue(H, (uint64_t)h0, (uint64_t)M);
+      }
+      D[i] += add * f;
+    }
   }
 }
 
@@ -287,7 +388,8 @@ struct mp_batch {
   mp::QDesc* d_qd = nullptr;
   mp::Prim* d_prims = nullptr;
   uint32_t *d_p_pref = nullptr, *d_cnt_pref = nullptr, *d_T = nullptr, *d_tab = nullptr;
-  uint64_t *d_tab_pref = nullptr, *d_slab_pref = nullptr, *d_H = nullptr, *d_X = nullptr, *d_def = nullptr;
+  uint64_t *d_tab_pref = nullptr, *d_slab_pref = nullptr, *d_H = nullptr, *d_X = nullptr, *d_def = nullptr,
+           *d_defall = nullptr;
   mp::Slab* d_slabs = nullptr;
   unsigned* d_counter = nullptr;
   // tiles and the persistent id writer's launch shape
@@ -367,12 +469,17 @@ int enqueue(mp_batch& b, int32_t* ids, uint64_t* hist, uint64_t* halo, uint64_t*
   }
   if (want_recv && b.any_lc) {
     MP_CUDA_TRY(cudaMemsetAsync(b.d_def, 0, (size_t)b.totalP * 8, st));
+    MP_CUDA_TRY(cudaMemsetAsync(b.d_defall, 0, (size_t)b.n * 8, st));
     if (b.total_slab) {
       k_b_slabs<<<blocks_for(b.total_slab), kThreads, 0, st>>>(b.d_qd, b.d_slabs, b.d_slab_pref,
                                                                (uint32_t)b.slabs.size(), b.total_slab,
-                                                               (unsigned long long*)b.d_def);
+                                                               (unsigned long long*)b.d_def,
+                                                               (unsigned long long*)b.d_defall);
       count_launch();
     }
+    k_b_defscan<<<(unsigned)b.n, kThreads, 0, st>>>(b.d_qd, (unsigned long long*)b.d_def,
+                                                   (const unsigned long long*)b.d_defall);
+    count_launch();
   }
   if (ids) {
     int rc = launch_ids(b, ids, st);
@@ -501,11 +608,11 @@ extern "C" int mp_batch_create(const mp_query* queries, int n, mp_batch** out) {
     ids_acc += (Q.npoints + 3) & ~uint64_t(3);
     if (Q.lc) {
       b->any_lc = true;
-      for (int t = 0; t < Q.k; ++t)
+      for (int t = 0; t + 1 < Q.k; ++t)   // the last dimension is counted in closed form
         if (Q.lc_stride_mod[t] != 0 && Q.face[t] != 0) {
           b->slabs.push_back(Slab{(uint32_t)q, t, slab_acc});
           b->slab_pref.push_back(slab_acc);
-          slab_acc += 2 * (Q.npoints / Q.L[t]);
+          slab_acc += 2 * (Q.npoints / (Q.L[t] * Q.lc_stride[t]));
         }
     }
     if (P_acc >= (uint64_t(1) << 31) || J_acc >= (uint64_t(1) << 31)) {
@@ -536,7 +643,8 @@ extern "C" int mp_batch_create(const mp_query* queries, int n, mp_batch** out) {
   const size_t o_H = a256(o_tab + std::max<uint64_t>(1, tab_acc) * 4);
   const size_t o_X = a256(o_H + std::max<uint64_t>(1, J_acc) * 8);
   const size_t o_def = a256(o_X + std::max<uint64_t>(1, J_acc) * 8);
-  const size_t o_cnt = a256(o_def + (b->any_lc ? P_acc : 1) * 8);
+  const size_t o_defall = a256(o_def + (b->any_lc ? P_acc : 1) * 8);
+  const size_t o_cnt = a256(o_defall + (size_t)n * 8);
   const size_t bytes = a256(o_cnt + 256);
   if (cudaMalloc(&b->dmem, bytes) != cudaSuccess) {
     cudaGetLastError();
@@ -557,6 +665,7 @@ extern "C" int mp_batch_create(const mp_query* queries, int n, mp_batch** out) {
   b->d_H = (uint64_t*)(base + o_H);
   b->d_X = (uint64_t*)(base + o_X);
   b->d_def = (uint64_t*)(base + o_def);
+  b->d_defall = (uint64_t*)(base + o_defall);
   b->d_counter = (unsigned*)(base + o_cnt);
   bool ok = cudaMemcpy(b->d_qd, b->qd.data(), b->qd.size() * sizeof(QDesc), cudaMemcpyHostToDevice) == cudaSuccess;
   if (!b->prims.empty())
