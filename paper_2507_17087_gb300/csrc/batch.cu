@@ -176,19 +176,6 @@ __global__ void __launch_bounds__(kThreads) k_b_slabs(const QDesc* __restrict__ 
   }
 }
 
-// Extended Euclid: g = gcd(a, m) and the inverse of a / g modulo m / g.
-__device__ __forceinline__ void gcd_inverse(int64_t a, int64_t m, int64_t& g, int64_t& inv) {
-  int64_t r0 = a, r1 = m, s0 = 1, s1 = 0;
-  while (r1 != 0) {
-    const int64_t q = r0 / r1;
-    int64_t tmp = r0 - q * r1; r0 = r1; r1 = tmp;
-    tmp = s0 - q * s1; s0 = s1; s1 = tmp;
-  }
-  g = r0;
-  const int64_t mg = m / g;
-  inv = mg == 1 ? 0 : ((s0 % mg) + mg) % mg;
-}
-
 // Prefix sum of each linear-cyclic query's difference array, plus its whole
 // turns: the deficit of every residue.  The last dimension's slabs (stride 1:
 // points hi * L + x, hi < N / L) are counted per residue F instead, in closed

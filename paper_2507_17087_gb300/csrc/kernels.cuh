@@ -608,6 +608,19 @@ __device__ __forceinline__ uint32_t lc_slab_F(const MapCore& D, int t, uint64_t 
   return (uint32_t)F;
 }
 
+// Extended Euclid: g = gcd(a, m) and the inverse of a / g modulo m / g.
+__device__ __forceinline__ void gcd_inverse(int64_t a, int64_t m, int64_t& g, int64_t& inv) {
+  int64_t r0 = a, r1 = m, s0 = 1, s1 = 0;
+  while (r1 != 0) {
+    const int64_t q = r0 / r1;
+    int64_t tmp = r0 - q * r1; r0 = r1; r1 = tmp;
+    tmp = s0 - q * s1; s0 = s1; s1 = tmp;
+  }
+  g = r0;
+  const int64_t mg = m / g;
+  inv = mg == 1 ? 0 : ((s0 % mg) + mg) % mg;
+}
+
 // Element-count halo of a linear-cyclic launch, slab entry e of dimension t:
 // the slabs are the positions x_t in [0, lo_n) and then L_t - 1, L_t - 2, ...
 // (the positions whose halo window the boundary cuts).  Returns F of the

@@ -193,6 +193,95 @@ __global__ void __launch_bounds__(kThreads) k_lc_wslabs(const __grid_constant__ 
   }
 }
 
+// Linear-cyclic face deficits without one atomic per boundary point (the
+// batched path does the same): the slab rows of every dimension but the last
+// are cyclic runs of residues -- whole turns into defall, the rest into the
+// difference array D (2 N / (L_t S_t) entries for dimension t); k_lc_scan
+// prefix-sums D and counts the last dimension's slabs per residue in closed
+// form.  Used when P <= kLcScanMax.
+constexpr uint32_t kLcScanMax = 1u << 20;
+
+struct LcRuns {
+  uint64_t begin[5];   // work entries of dimensions 0 .. k-2, prefix
+};
+
+__global__ void __launch_bounds__(kThreads) k_lc_runs(const __grid_constant__ MapDesc D, const __grid_constant__ LcRuns R,
+                                                      uint64_t f0, uint64_t f1, uint64_t f2, uint64_t f3,
+                                                      unsigned long long* __restrict__ Dd,
+                                                      unsigned long long* __restrict__ defall) {
+  const uint64_t face[4] = {f0, f1, f2, f3};
+  const uint64_t total = R.begin[D.k - 1];
+  for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (uint64_t)gridDim.x * blockDim.x) {
+    int t = 0;
+    while (e >= R.begin[t + 1]) ++t;
+    const uint64_t S = D.lc_stride[t], Lt = D.L[t];
+    const uint64_t H = D.npoints / (Lt * S);
+    const uint64_t local = e - R.begin[t];
+    const uint64_t side = local / H, hi = local - side * H;
+    const uint64_t xt = side ? Lt - 1 : 0;
+    const unsigned long long f = face[t];
+    uint64_t q0, r0, full, rem;
+    divmod64(hi * (Lt * S) + xt * S, D.divP64, q0, r0);
+    divmod64(S, D.divP64, full, rem);
+    if (full) atomicAdd(defall, full * f);
+    if (rem) {
+      const uint64_t end = r0 + rem;
+      atomicAdd(Dd + r0, f);
+      if (end < D.P) {
+        atomicAdd(Dd + end, (unsigned long long)(-(long long)f));
+      } else if (end > D.P) {
+        atomicAdd(Dd, f);
+        atomicAdd(Dd + (end - D.P), (unsigned long long)(-(long long)f));
+      }
+    }
+  }
+}
+
+__global__ void __launch_bounds__(1024) k_lc_scan(const __grid_constant__ MapDesc D, uint64_t f_last,
+                                                  unsigned long long* __restrict__ Dd,
+                                                  const unsigned long long* __restrict__ defall) {
+  __shared__ unsigned long long part[1024];
+  __shared__ int64_t s_g, s_inv;
+  const int last = D.k - 1;
+  const bool last_slabs = D.lc_stride_mod[last] != 0 && f_last != 0;
+  if (threadIdx.x == 0 && last_slabs) {
+    int64_t g, inv;
+    gcd_inverse((int64_t)(D.L[last] % D.P), (int64_t)D.P, g, inv);
+    s_g = g;
+    s_inv = inv;
+  }
+  const uint32_t P = D.P;
+  const uint32_t per = (P + 1023) / 1024;
+  const uint32_t lo = min(P, threadIdx.x * per), hi = min(P, lo + per);
+  unsigned long long sum = 0;
+  for (uint32_t i = lo; i < hi; ++i) sum += Dd[i];
+  part[threadIdx.x] = sum;
+  __syncthreads();
+  for (int o = 1; o < 1024; o <<= 1) {
+    const unsigned long long v = threadIdx.x >= (unsigned)o ? part[threadIdx.x - o] : 0;
+    __syncthreads();
+    part[threadIdx.x] += v;
+    __syncthreads();
+  }
+  unsigned long long run = (threadIdx.x ? part[threadIdx.x - 1] : 0) + *defall;
+  const int64_t g = last_slabs ? s_g : 1, inv = last_slabs ? s_inv : 0, M = (int64_t)P / g;
+  const uint64_t Lt = D.L[last], H = D.npoints / Lt;
+  for (uint32_t i = lo; i < hi; ++i) {
+    run += Dd[i];
+    unsigned long long add = 0;
+    if (last_slabs)
+      for (int side = 0; side < 2; ++side) {
+        const int64_t x = side ? (int64_t)((Lt - 1) % P) : 0;
+        const int64_t c = ((int64_t)i - x + (int64_t)P) % (int64_t)P;
+        if (c % g) continue;
+        const int64_t h0 = M == 1 ? 0 : (int64_t)(((unsigned __int128)(c / g) * (uint64_t)inv) % (uint64_t)M);
+        add += count_residue(H, (uint64_t)h0, (uint64_t)M);
+      }
+    Dd[i] = run + add * f_last;
+  }
+}
+
 __global__ void __launch_bounds__(kThreads) k_reduce(const __grid_constant__ MapDesc D, const uint32_t* __restrict__ T,
                                                      const uint64_t* __restrict__ H, const uint64_t* __restrict__ X,
                                                      const uint64_t* __restrict__ deficit, uint64_t f0, uint64_t f1,
@@ -297,7 +386,7 @@ Layout make_layout(const MapDesc& D, const Want& w) {
   ly.nHX = ly.need_red && !D.lc ? (size_t)D.Jtotal : 0;
   ly.o_X = align256(ly.o_H + ly.nHX * 8);
   ly.o_def = align256(ly.o_X + (ly.need_X ? ly.nHX * 8 : 0));
-  ly.n_def = D.lc && (w.recv || w.total) ? D.P : 0;
+  ly.n_def = D.lc && (w.recv || w.total) ? D.P + 1 : 0;   // + the whole-turn word of the runs
   ly.bytes = align256(ly.o_def + ly.n_def * 8);
   return ly;
 }
@@ -426,12 +515,32 @@ ids_done:
       }
       const uint64_t blocks = std::max<uint64_t>(1, std::min<uint64_t>((work + kThreads - 1) / kThreads,
                                                                          (uint64_t)sm_count() * 8));
-      if (lc_elem)
+      if (lc_elem) {
         k_lc_wslabs<<<(unsigned)blocks, kThreads, 0, st>>>(D, lh, w.face[0], w.face[1], w.face[2], w.face[3],
                                                            w.width[0], w.width[1], w.width[2], w.width[3], def);
-      else
+        count_launch();
+      } else if (D.P <= kLcScanMax) {
+        LcRuns R;
+        std::memset(&R, 0, sizeof(R));
+        for (int t = 0; t + 1 < D.k; ++t) {
+          const bool crosses = D.lc_stride_mod[t] != 0 && w.face[t] != 0;
+          R.begin[t + 1] = R.begin[t] + (crosses ? 2 * (D.npoints / (D.L[t] * D.lc_stride[t])) : 0);
+        }
+        unsigned long long* defall = def + D.P;   // one extra word after the deficits
+        MP_CUDA_TRY(cudaMemsetAsync(defall, 0, 8, st));
+        const uint64_t runs = R.begin[D.k - 1];
+        if (runs) {
+          const uint64_t rb = std::max<uint64_t>(1, std::min<uint64_t>((runs + kThreads - 1) / kThreads,
+                                                                       (uint64_t)sm_count() * 8));
+          k_lc_runs<<<(unsigned)rb, kThreads, 0, st>>>(D, R, w.face[0], w.face[1], w.face[2], w.face[3], def, defall);
+          count_launch();
+        }
+        k_lc_scan<<<1, 1024, 0, st>>>(D, w.face[D.k - 1], def, defall);
+        count_launch();
+      } else {
         k_lc_slabs<<<(unsigned)blocks, kThreads, 0, st>>>(D, w.face[0], w.face[1], w.face[2], w.face[3], def);
-      count_launch();
+        count_launch();
+      }
     }
     k_reduce<<<(D.P + kThreads - 1) / kThreads, kThreads, 0, st>>>(
         D, T, H, X, (const uint64_t*)def, w.face[0], w.face[1], w.face[2], w.face[3], w.hist, w.recv,

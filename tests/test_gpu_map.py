@@ -240,3 +240,15 @@ def test_map_launch_equals_separate_calls():
         torch.cuda.synchronize()
         for a, b in ((ids, rid), (hist, rh), (tot, rt), (recv, rr), (et, er), (e_recv, e_rr)):
             assert torch.equal(a, b), (L, machine, chain, dist)
+
+
+@pytest.mark.parametrize("L,machine", [((300, 200, 2), (64, 8)), ((2, 9082, 7), (7, 8)), ((97, 2, 3, 171), (16, 4)),
+                                       ((4096, 3), (1, 6)), ((5, 1, 4096), (3, 5)), ((65537,), (13, 1))])
+def test_linear_cyclic_deficits_in_closed_form(L, machine):
+    # the linear-cyclic face deficits are counted per residue run and, for the
+    # last dimension, from a linear congruence: degenerate extents against the
+    # oracle's per-neighbour count
+    rng = W.rng(sum(L))
+    chain = N.chain_from_draws(*machine, [rng.next() for _ in range(3)])
+    face = [3 + t for t in range(len(L))]
+    check_against_oracle(L, machine, chain, ("linear_cyclic",), face)
