@@ -208,30 +208,67 @@ __global__ void __launch_bounds__(128) k_feat_img(const __grid_constant__ QInfo 
 
 // Epilogue of one tile's hidden layer: rows 32 (w % 4) + lane of the tile,
 // all 256 columns of its accumulator (TMEM columns col0 ..), bias and ReLU,
-// BF16 into the tile's activation atoms.
+// BF16 into the tile's activation atoms.  The next 32 columns are loaded from
+// tensor memory while the current ones are converted.
+__device__ __forceinline__ void epilogue_block(const uint32_t (&r)[32], int c, int row,
+                                               const float* __restrict__ bias, uint8_t* H) {
+  uint8_t* atom = H + (c >> 1) * 16384;
+#pragma unroll
+  for (int j = 0; j < 32; j += 8) {
+    uint32_t w[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const float a = fmaxf(__uint_as_float(r[j + 2 * e]) + bias[c * 32 + j + 2 * e], 0.f);
+      const float b = fmaxf(__uint_as_float(r[j + 2 * e + 1]) + bias[c * 32 + j + 2 * e + 1], 0.f);
+      __nv_bfloat162 h2 = __floats2bfloat162_rn(a, b);
+      w[e] = *reinterpret_cast<uint32_t*>(&h2);
+    }
+    *reinterpret_cast<uint4*>(atom + tc::sw128_offset(row, (c & 1) * 32 + j)) = make_uint4(w[0], w[1], w[2], w[3]);
+  }
+}
+
 __device__ __forceinline__ void epilogue_rows(uint32_t tmem, uint32_t col0, const float* __restrict__ bias,
                                               uint8_t* H) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int row = (warp & 3) * 32 + lane;
+  const uint32_t t0 = tmem + ((uint32_t)((warp & 3) * 32) << 16) + col0;
+  uint32_t ra[32], rb[32];
+  tc::tmem_ld32(t0, ra);
+  tc::tmem_ld_wait();
 #pragma unroll 1
-  for (int c = 0; c < 8; ++c) {
-    uint32_t r[32];
-    tc::tmem_ld32(tmem + ((uint32_t)((warp & 3) * 32) << 16) + col0 + c * 32, r);
+  for (int c = 0; c < 8; c += 2) {
+    tc::tmem_ld32(t0 + (c + 1) * 32, rb);
+    epilogue_block(ra, c, row, bias, H);
     tc::tmem_ld_wait();
-    uint8_t* atom = H + (c >> 1) * 16384;
-#pragma unroll
-    for (int j = 0; j < 32; j += 8) {
-      uint32_t w[4];
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const float a = fmaxf(__uint_as_float(r[j + 2 * e]) + bias[c * 32 + j + 2 * e], 0.f);
-        const float b = fmaxf(__uint_as_float(r[j + 2 * e + 1]) + bias[c * 32 + j + 2 * e + 1], 0.f);
-        __nv_bfloat162 h2 = __floats2bfloat162_rn(a, b);
-        w[e] = *reinterpret_cast<uint32_t*>(&h2);
-      }
-      *reinterpret_cast<uint4*>(atom + tc::sw128_offset(row, (c & 1) * 32 + j)) = make_uint4(w[0], w[1], w[2], w[3]);
-    }
+    if (c + 2 < 8) tc::tmem_ld32(t0 + (c + 2) * 32, ra);
+    epilogue_block(rb, c + 1, row, bias, H);
+    tc::tmem_ld_wait();
   }
+}
+
+// Output layer of one tile's row: relu(Z3 + b3) . w4 over 256 columns, the
+// loads pipelined as in epilogue_rows.
+__device__ __forceinline__ float output_row(uint32_t tmem, uint32_t col0, const float* __restrict__ b3,
+                                           const float* __restrict__ w4) {
+  const int warp = threadIdx.x >> 5;
+  const uint32_t t0 = tmem + ((uint32_t)((warp & 3) * 32) << 16) + col0;
+  uint32_t ra[32], rb[32];
+  float acc = 0.f;
+  tc::tmem_ld32(t0, ra);
+  tc::tmem_ld_wait();
+#pragma unroll 1
+  for (int c = 0; c < 8; c += 2) {
+    tc::tmem_ld32(t0 + (c + 1) * 32, rb);
+#pragma unroll
+    for (int q = 0; q < 32; ++q) acc += fmaxf(__uint_as_float(ra[q]) + b3[c * 32 + q], 0.f) * w4[c * 32 + q];
+    tc::tmem_ld_wait();
+    if (c + 2 < 8) tc::tmem_ld32(t0 + (c + 2) * 32, ra);
+#pragma unroll
+    for (int q = 0; q < 32; ++q)
+      acc += fmaxf(__uint_as_float(rb[q]) + b3[(c + 1) * 32 + q], 0.f) * w4[(c + 1) * 32 + q];
+    tc::tmem_ld_wait();
+  }
+  return acc;
 }
 
 constexpr size_t kMlpSmem = 2 * 65536 + 2 * mlpk::kWChunkBytes + 1024;
@@ -241,8 +278,12 @@ __global__ void __launch_bounds__(256, 1) k_mlp_img(const uint8_t* __restrict__ 
                                                     unsigned long long n, float* __restrict__ scores,
                                                     int* __restrict__ status) {
   extern __shared__ uint8_t smem_raw[];
-  __shared__ uint64_t wbar[2], xbar, mbar;
+  // wbar[b]: weight chunk landed in buffer b; cbar[b]: the MMAs that read
+  // buffer b completed.  Chunk G uses buffer G & 1, and is the (G >> 1)-th
+  // use of it, so every wait's phase parity follows from G.
+  __shared__ uint64_t wbar[2], cbar[2], xbar;
   __shared__ uint32_t tmem_slot;
+  __shared__ int s_fail;
   __shared__ float sb[4][256];   // b1, b2, b3, w4
   uint8_t* base = smem_raw + ((1024 - (tc::smem_u32(smem_raw) & 1023)) & 1023);
   uint8_t* H[2] = {base, base + 65536};                                 // two tiles x four atoms
@@ -262,10 +303,12 @@ __global__ void __launch_bounds__(256, 1) k_mlp_img(const uint8_t* __restrict__ 
     tc::tmem_relinquish();
   }
   if (threadIdx.x == 0) {
-    tc::mbar_init(&wbar[0], 1);
-    tc::mbar_init(&wbar[1], 1);
+    s_fail = 0;
+    for (int b = 0; b < 2; ++b) {
+      tc::mbar_init(&wbar[b], 1);
+      tc::mbar_init(&cbar[b], 1);
+    }
     tc::mbar_init(&xbar, 1);
-    tc::mbar_init(&mbar, 1);
     tc::fence_mbar_init();
     // the first two weight chunks
     for (uint32_t c = 0; c < 2 && c < total_chunks; ++c) {
@@ -278,17 +321,19 @@ __global__ void __launch_bounds__(256, 1) k_mlp_img(const uint8_t* __restrict__ 
   tc::fence_after_sync();
   const uint32_t tmem = tmem_slot;
   constexpr uint32_t idesc = tc::idesc_bf16(128, 256);
-  __shared__ int s_ok;
-  uint32_t wphase[2] = {0, 0}, xphase = 0, mphase = 0;
-  uint32_t G = 0;        // weight chunks consumed so far
-  uint32_t waited = 0;   // weight chunks seen landed (thread 0)
-  uint32_t issued = total_chunks < 2 ? total_chunks : 2;   // weight chunk copies issued (thread 0)
-  bool x_pending = false;                                    // a tile copy not yet seen landed
+  uint32_t xphase = 0;
+  uint32_t G = 0;          // weight chunks consumed so far (the same in every thread)
+  uint32_t landed = 0;     // thread 0: chunks seen landed
+  uint32_t issued = total_chunks < 2 ? total_chunks : 2;   // thread 0: chunk copies issued
+  uint32_t committed = 0;  // thread 0: chunks whose MMAs were issued
+  uint32_t done = 0;       // thread 0: chunks whose MMAs were seen complete
+  bool x_pending = false;  // a tile copy not yet seen landed
   bool ok = true;
   for (uint32_t pass = 0; pass < npass && ok; ++pass) {
     const uint32_t tA = 2 * (blockIdx.x + pass * gridDim.x);
     const uint32_t nt = tA + 1 < ntiles ? 2 : 1;
-    if (threadIdx.x == 0) {
+    if (threadIdx.x == 0 && pass == 0) {
+      // later passes' tiles were copied during the previous pass
       tc::mbar_expect_tx(&xbar, nt * kTileBytes);
       for (uint32_t t = 0; t < nt; ++t) tc::bulk_g2s(H[t], img + (size_t)(tA + t) * kTileBytes, kTileBytes, &xbar);
     }
@@ -298,15 +343,18 @@ __global__ void __launch_bounds__(256, 1) k_mlp_img(const uint8_t* __restrict__ 
     if (!ok) break;
     x_pending = false;
     xphase ^= 1;
-    for (int j = 0; j < mlpk::kWChunks; ++j) {
+    for (int j = 0; j < mlpk::kWChunks; ++j, ++G) {
       const uint32_t b = G & 1;
       // A operand: atom kc of each tile (X for layer 1)
       const uint32_t kc = j == 0 ? 0 : (uint32_t)((j - 1) & 3);
       const bool first = j == 0 || kc == 0;
-      if (threadIdx.x == 0) {
-        const bool landed = tc::mbar_wait(&wbar[b], wphase[b], kWaitLimit);
-        if (landed) {
-          ++waited;
+      if (threadIdx.x == 0 && !s_fail) {
+        // issue this chunk's MMAs as soon as its weights are in; they queue
+        // behind the previous chunk's on the tensor pipe
+        if (!tc::mbar_wait(&wbar[b], (G >> 1) & 1, kWaitLimit)) {
+          s_fail = 1;
+        } else {
+          ++landed;
           tc::fence_after_sync();
           for (uint32_t t = 0; t < nt; ++t) {
             const uint32_t a_addr = tc::smem_u32(H[t] + kc * 16384), b_addr = tc::smem_u32(Wb[b]);
@@ -315,63 +363,65 @@ __global__ void __launch_bounds__(256, 1) k_mlp_img(const uint8_t* __restrict__ 
               tc::mma_bf16(tmem + t * 256, tc::sdesc_sw128(a_addr + kk * 32), tc::sdesc_sw128(b_addr + kk * 32),
                            idesc, (first && kk == 0) ? 0u : 1u);
           }
-          tc::mma_commit(&mbar);
+          tc::mma_commit(&cbar[b]);
+          ++committed;
+          // the previous chunk's buffer is free once its MMAs completed: the
+          // next chunk goes into it
+          if (G >= 1) {
+            if (!tc::mbar_wait(&cbar[b ^ 1], ((G - 1) >> 1) & 1, kWaitLimit)) {
+              s_fail = 1;
+            } else {
+              done = G;
+              if (j == 6 && pass + 1 < npass) {
+                // chunk 5 (layer 3's first, the last reader of atom 0) is
+                // done: the next pass's tiles go into atom 0 now
+                const uint32_t tN = 2 * (blockIdx.x + (pass + 1) * gridDim.x);
+                const uint32_t ntN = tN + 1 < ntiles ? 2 : 1;
+                tc::mbar_expect_tx(&xbar, ntN * kTileBytes);
+                for (uint32_t u = 0; u < ntN; ++u)
+                  tc::bulk_g2s(H[u], img + (size_t)(tN + u) * kTileBytes, kTileBytes, &xbar);
+                x_pending = true;
+              }
+              if (G + 1 < total_chunks) {
+                ++issued;
+                tc::mbar_expect_tx(&wbar[b ^ 1], (uint32_t)mlpk::kWChunkBytes);
+                tc::bulk_g2s(Wb[b ^ 1], Wimg + (size_t)((G + 1) % mlpk::kWChunks) * mlpk::kWChunkBytes,
+                             (uint32_t)mlpk::kWChunkBytes, &wbar[b ^ 1]);
+              }
+            }
+          }
         }
-        s_ok = landed ? 1 : 0;
       }
-      __syncthreads();
-      if (!s_ok) {
-        ok = false;
-        break;
-      }
-      wphase[b] ^= 1;
-      ok = __syncthreads_and(tc::mbar_wait(&mbar, mphase, kWaitLimit)) != 0;
+      if (j != 0 && j != 4 && j != 8) continue;
+      // a layer is complete: everyone waits for this chunk's MMAs
+      const bool mma_done = tc::mbar_wait(&cbar[b], (G >> 1) & 1, kWaitLimit);
+      __syncthreads();   // s_fail as thread 0 left it
+      ok = __syncthreads_and(mma_done && !s_fail) != 0;
       if (!ok) break;
-      mphase ^= 1;
       tc::fence_after_sync();
-      ++G;
-      // this chunk's buffer is free again: the chunk two ahead goes into it
-      if (threadIdx.x == 0 && G + 1 < total_chunks) {
-        ++issued;
-        tc::mbar_expect_tx(&wbar[b], (uint32_t)mlpk::kWChunkBytes);
-        tc::bulk_g2s(Wb[b], Wimg + (size_t)((G + 1) % mlpk::kWChunks) * mlpk::kWChunkBytes,
-                     (uint32_t)mlpk::kWChunkBytes, &wbar[b]);
-      }
+      if (threadIdx.x == 0) done = G + 1;
       const uint32_t t = (uint32_t)warp >> 2;   // the tile this warp's epilogue serves
-      if (j == 0 || j == 4) {
+      if (j != 8) {
         // hidden layer 1 or 2 done: its activations become the next A operand
         if (t < nt) epilogue_rows(tmem, t * 256, sb[j == 0 ? 0 : 1], H[t]);
         tc::fence_proxy_async();
-        tc::fence_before_sync();
-        __syncthreads();
-      } else if (j == 8) {
+      } else if (t < nt) {
         // layer 3 and the output dot product
-        if (t < nt) {
-          const int row = (warp & 3) * 32 + lane;
-          float acc = 0.f;
-#pragma unroll 1
-          for (int c = 0; c < 8; ++c) {
-            uint32_t r[32];
-            tc::tmem_ld32(tmem + ((uint32_t)((warp & 3) * 32) << 16) + t * 256 + c * 32, r);
-            tc::tmem_ld_wait();
-#pragma unroll
-            for (int q = 0; q < 32; ++q) acc += fmaxf(__uint_as_float(r[q]) + sb[2][c * 32 + q], 0.f) * sb[3][c * 32 + q];
-          }
-          const unsigned long long out = (unsigned long long)(tA + t) * 128 + row;
-          if (out < n) scores[out] = acc + b4;
-        }
-        tc::fence_before_sync();
-        __syncthreads();
+        const int row = (warp & 3) * 32 + lane;
+        const float acc = output_row(tmem, t * 256, sb[2], sb[3]);
+        const unsigned long long out = (unsigned long long)(tA + t) * 128 + row;
+        if (out < n) scores[out] = acc + b4;
       }
+      tc::fence_before_sync();
+      __syncthreads();
     }
   }
   if (!ok && threadIdx.x == 0) {
     atomicExch(status, MP_ETIMEOUT);
-    // let the weight copies still in flight land before the CTA exits: the
-    // chunks issued but not yet seen landed (each buffer's phase still
-    // matches the oldest of them)
-    for (uint32_t c = waited; c < issued; ++c)
-      if (tc::mbar_wait(&wbar[c & 1], wphase[c & 1], kWaitLimit)) wphase[c & 1] ^= 1;
+    // before the CTA exits: the chunk copies issued but not seen landed, the
+    // MMAs issued but not seen complete, and a tile copy in flight
+    for (uint32_t c = landed; c < issued; ++c) tc::mbar_wait(&wbar[c & 1], (c >> 1) & 1, kWaitLimit);
+    for (uint32_t c = done; c < committed; ++c) tc::mbar_wait(&cbar[c & 1], (c >> 1) & 1, kWaitLimit);
     if (x_pending) tc::mbar_wait(&xbar, xphase, kWaitLimit);
   }
   tc::fence_before_sync();
