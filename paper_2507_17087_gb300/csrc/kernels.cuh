@@ -442,6 +442,16 @@ __device__ __forceinline__ void ids_range_rows(const MapCore& D, const Tabs& tab
     } else if (x + 4 <= Lf) {
 #pragma unroll
       for (int i = 0; i < 4; ++i) v[i] = T[base + row_contrib<SRC>(D, Cf, x + i)];
+    } else if (Lf >= 4) {
+      // the group crosses into the next row (at most once): select, do not
+      // branch, so the lane does not hold its warp up (points past the end
+      // of the launch are not stored)
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const uint32_t xi = x + i;
+        const bool w = xi >= Lf;
+        v[i] = T[(w ? nbase : base) + row_contrib<SRC>(D, Cf, w ? xi - Lf : xi)];
+      }
     } else {
       uint32_t xi = x, ri = row, bi = base;
       for (int i = 0; i < cnt; ++i) {
