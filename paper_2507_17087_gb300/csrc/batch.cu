@@ -18,8 +18,10 @@
 // The tile size is picked on the first run by timing the persistent kernel
 // at a few sizes (autotune) and kept with the batch.
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 #include <mutex>
+#include <thread>
 #include <vector>
 
 #include "kernels.cuh"
@@ -32,6 +34,7 @@ constexpr uint32_t kBatchMaxP = 16384;
 constexpr uint64_t kBatchTableMax = 65536;   // tabled coordinates per dimension
 constexpr uint64_t kFuseTarget = 2048;        // fused rows: at least this many points when the extents allow
 constexpr uint64_t kFuseMax = 4096;           // fused rows staged in shared memory: at most this many points
+constexpr uint64_t kShortRow = 512;          // fused rows shorter than this take the next dimension too
 
 struct QDesc : MapCore {
   Tabs tabs;            // offsets relative to tab_base
@@ -44,14 +47,24 @@ struct QDesc : MapCore {
   uint64_t face[4];
   // M_FUSED: dimensions fuse_m..k-1 form rows of Lf points; rsrc (RowSrc)
   // says where a row offset's contribution comes from (a table at fuse_off,
-  // relative to tab_base, or the last dimension's components)
+  // relative to tab_base, or the last dimension's components).  R_TAB2: the
+  // table at fuse_off fuses dimensions fuse_m+1..k-1 into Lin points
   int32_t fuse_m;
   uint32_t Lf;
   Div32 divLf;
   uint64_t fuse_off;
   int32_t rsrc;
-  int32_t pad_;
+  uint32_t Lin;
+  Div32 divLin;
+  uint64_t pad_;
 };
+
+// the fused table's first dimension and length (0 when rows have no table)
+__host__ __device__ inline int fused_first(const QDesc& Q) { return Q.rsrc == R_TAB2 ? Q.fuse_m + 1 : Q.fuse_m; }
+__host__ __device__ inline uint32_t fused_len(const QDesc& Q) {
+  if (Q.mode != M_FUSED) return 0;
+  return Q.rsrc == R_TAB2 ? Q.Lin : (Q.rsrc <= R_TAB4 ? Q.Lf : 0);
+}
 static_assert(sizeof(QDesc) % 16 == 0, "QDesc is copied in 16-byte words");
 
 struct Tile {
@@ -88,12 +101,12 @@ __global__ void __launch_bounds__(kThreads) k_b_tables(const QDesc* __restrict__
     const uint32_t q = find_query(tab_pref, n, e);
     const QDesc& Q = qd[q];
     const uint64_t r = e - Q.tab_base;
-    if (Q.mode == M_FUSED && Q.rsrc <= R_TAB4 && r >= Q.fuse_off) {
-      // fused row offset x -> coordinates of dimensions fuse_m..k-1 (C order)
+    if (fused_len(Q) && r >= Q.fuse_off) {
+      // fused offset x -> coordinates of the fused dimensions (C order)
       uint64_t x = r - Q.fuse_off;
-      if (x >= Q.Lf) continue;
+      if (x >= fused_len(Q)) continue;
       uint32_t c = 0;
-      for (int t = Q.k - 1; t >= Q.fuse_m; --t) {
+      for (int t = Q.k - 1; t >= fused_first(Q); --t) {
         const uint64_t xt = x % Q.L[t];
         x /= Q.L[t];
         c += contrib(Q, t, xt);
@@ -265,9 +278,9 @@ __global__ void __launch_bounds__(kThreads) k_b_ids(const QDesc* __restrict__ qd
         const int last = Q.k - 1;
         const uint32_t* cg = tabpool + Q.tab_base + Q.tabs.off[last];
         for (uint32_t i = threadIdx.x; i < (uint32_t)Q.L[last]; i += blockDim.x) Cs[i] = __ldg(cg + i);
-      } else if (Q.mode == M_FUSED && Q.rsrc <= R_TAB4) {
+      } else if (fused_len(Q)) {
         const uint32_t* cg = tabpool + Q.tab_base + Q.fuse_off;
-        for (uint32_t i = threadIdx.x; i < Q.Lf; i += blockDim.x) Cs[i] = __ldg(cg + i);
+        for (uint32_t i = threadIdx.x; i < fused_len(Q); i += blockDim.x) Cs[i] = __ldg(cg + i);
       }
       cur_q = tl.q;
       __syncthreads();
@@ -282,8 +295,11 @@ __global__ void __launch_bounds__(kThreads) k_b_ids(const QDesc* __restrict__ qd
     if (Q.lc) {
       ids_range_lc<uint32_t, true>(Q, Ts, wb, we, lane, vec_ok, qids);
     } else if (Q.mode == M_FUSED) {
-#define MP_ROWS(SRC) ids_range_rows<SRC>(Q, Q.tabs, Ts, Cs, ctab, Q.fuse_m, Q.Lf, Q.divLf, wb, we, lane, vec_ok, qids)
+      const RowAux aux{ctab + Q.tabs.off[Q.fuse_m], Q.Lin, Q.divLin};
+#define MP_ROWS(SRC) \
+  ids_range_rows<SRC>(Q, Q.tabs, Ts, Cs, ctab, aux, Q.fuse_m, Q.Lf, Q.divLf, wb, we, lane, vec_ok, qids)
       switch (Q.rsrc) {
+        case R_TAB2: MP_ROWS(R_TAB2); break;
         case R_TAB4: MP_ROWS(R_TAB4); break;
         case R_TAB: MP_ROWS(R_TAB); break;
         case R_BLOCK: MP_ROWS(R_BLOCK); break;
@@ -528,21 +544,22 @@ extern "C" int mp_batch_create(const mp_query* queries, int n, mp_batch** out) {
   b->cnt_pref.resize(n + 1);
   b->tab_pref.resize(n + 1);
   b->ids_pref.resize(n + 1);
-  uint64_t P_acc = 0, J_acc = 0, tab_acc = 0, ids_acc = 0, slab_acc = 0;
-  for (int q = 0; q < n; ++q) {
+  // planning and the per-query choices are independent: host threads over
+  // the queries; the offsets are assigned in order afterwards
+  std::vector<std::vector<Prim>> qprims(n);
+  std::vector<uint64_t> qtab(n, 0);
+  std::vector<int> qrc(n, 0);
+  auto plan_query = [&](int q) {
     const mp_query& Qh = queries[q];
     Plan pl;
     int rc = build_plan(&Qh.space, &Qh.machine, Qh.chain, Qh.n_xf, &Qh.dist, pl);
     if (!rc && (pl.desc.P > kBatchMaxP || pl.desc.npoints >= (uint64_t(1) << 31))) rc = MP_ENOTSUP;
-    if (rc) {
-      delete b;
-      return rc;
-    }
+    qrc[q] = rc;
+    if (rc) return;
     QDesc& Q = b->qd[q];
     std::memset(&Q, 0, sizeof(Q));
     static_cast<MapCore&>(Q) = static_cast<const MapCore&>(pl.desc);
-    Q.prim_off = (uint32_t)b->prims.size();
-    for (int o = 0; o < pl.desc.nprim; ++o) b->prims.push_back(pl.desc.prim[o]);
+    qprims[q].assign(pl.desc.prim, pl.desc.prim + pl.desc.nprim);
     for (int t = 0; t < 4; ++t) Q.face[t] = t < Q.k ? Qh.face_bytes[t] : 0;
     uint64_t tabq = 0;
     for (int t = 0; t < Q.k; ++t) {
@@ -567,7 +584,18 @@ extern "C" int mp_batch_create(const mp_query* queries, int n, mp_batch** out) {
       Q.fuse_m = m;
       Q.Lf = (uint32_t)Lf;
       Q.divLf = make_div32((uint32_t)Lf);
-      if (Lf <= kFuseMax) {
+      if (Lf < kShortRow && m > 0 && Q.tabs.has[m - 1]) {
+        // rows this short would change their base every few groups: the
+        // next dimension joins the row through its own table
+        Q.rsrc = R_TAB2;
+        Q.Lin = (uint32_t)Lf;
+        Q.divLin = make_div32((uint32_t)Lf);
+        Q.fuse_m = m - 1;
+        Q.Lf = (uint32_t)(Lf * Q.L[m - 1]);
+        Q.divLf = make_div32(Q.Lf);
+        Q.fuse_off = tabq;
+        tabq += (Lf + 3) & ~uint64_t(3);
+      } else if (Lf <= kFuseMax) {
         Q.rsrc = Lf % 4 == 0 ? R_TAB4 : R_TAB;
         Q.fuse_off = tabq;
         tabq += (Lf + 3) & ~uint64_t(3);
@@ -578,8 +606,35 @@ extern "C" int mp_batch_create(const mp_query* queries, int n, mp_batch** out) {
         Q.rsrc = kind == C_BLOCK ? R_BLOCK : (kind == C_CYCLIC ? R_CYCLIC : R_BCYC);
       }
     }
+    qtab[q] = tabq;
+  };
+  {
+    const int nthr = (int)std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+    std::atomic<int> next{0};
+    auto worker = [&]() {
+      for (int q = next.fetch_add(64); q < n; q = next.fetch_add(64))
+        for (int e = q; e < std::min(n, q + 64); ++e) plan_query(e);
+    };
+    std::vector<std::thread> pool;
+    for (int i = 1; i < nthr && i * 64 < n; ++i) pool.emplace_back(worker);
+    worker();
+    for (auto& th : pool) th.join();
+  }
+  for (int q = 0; q < n; ++q)
+    if (qrc[q]) {
+      const int rc = qrc[q];
+      delete b;
+      return rc;
+    }
+  uint64_t P_acc = 0, J_acc = 0, tab_acc = 0, ids_acc = 0, slab_acc = 0;
+  for (int q = 0; q < n; ++q) {
+    QDesc& Q = b->qd[q];
+    const int last = Q.k - 1;
+    const uint64_t tabq = qtab[q];
+    Q.prim_off = (uint32_t)b->prims.size();
+    b->prims.insert(b->prims.end(), qprims[q].begin(), qprims[q].end());
     if (Q.mode == M_FAST_SMEM) b->maxC = std::max<uint32_t>(b->maxC, (uint32_t)Q.L[last]);
-    if (Q.mode == M_FUSED && Q.rsrc <= R_TAB4) b->maxC = std::max<uint32_t>(b->maxC, Q.Lf);
+    b->maxC = std::max<uint32_t>(b->maxC, fused_len(Q));
     b->maxP = std::max(b->maxP, Q.P);
     Q.p_off = (uint32_t)P_acc;
     Q.cnt_off = (uint32_t)J_acc;

@@ -362,11 +362,28 @@ __device__ __noinline__ uint32_t row_base_m(const MapCore& D, const Tabs& tabs, 
 //                   16-byte load per group)
 //   R_BLOCK, R_CYCLIC, R_BCYC, R_HIER  computed from the last dimension's
 //                   components (rows = the last dimension, no table)
-enum RowSrc : int { R_TAB = 0, R_TAB4 = 1, R_BLOCK = 2, R_CYCLIC = 3, R_BCYC = 4, R_HIER = 5 };
+//   R_TAB2          two levels: rows are dimension m followed by the fused
+//                   table's Lin points (dimensions m+1..k-1, too few for a
+//                   row of their own); x -> C2[x / Lin] + Cf[x % Lin], with
+//                   C2 dimension m's table in global memory
+enum RowSrc : int { R_TAB = 0, R_TAB4 = 1, R_BLOCK = 2, R_CYCLIC = 3, R_BCYC = 4, R_HIER = 5, R_TAB2 = 6 };
+
+// R_TAB2's second level (unused by the other row sources)
+struct RowAux {
+  const uint32_t* C2;
+  uint32_t Lin;
+  Div32 divLin;
+};
 
 template <int SRC>
-__device__ __forceinline__ uint32_t row_contrib(const MapCore& D, const uint32_t* __restrict__ Cf, uint32_t x) {
+__device__ __forceinline__ uint32_t row_contrib(const MapCore& D, const uint32_t* __restrict__ Cf, const RowAux& A,
+                                                uint32_t x) {
   if (SRC == R_TAB || SRC == R_TAB4) return Cf[x];
+  if (SRC == R_TAB2) {
+    uint32_t q, r;
+    divmod32(x, A.divLin, q, r);
+    return __ldg(A.C2 + q) + Cf[r];
+  }
   const Comp& c0 = D.comp[D.k - 1][0];
   uint32_t a;
   if (SRC == R_BLOCK || SRC == R_HIER) {
@@ -398,8 +415,8 @@ __device__ __forceinline__ uint32_t row_contrib(const MapCore& D, const uint32_t
 template <int SRC>
 __device__ __forceinline__ void ids_range_rows(const MapCore& D, const Tabs& tabs, const uint32_t* __restrict__ T,
                                                const uint32_t* __restrict__ Cf, const uint32_t* __restrict__ ctab,
-                                               int m, uint32_t Lf, Div32 divLf, uint32_t gbeg, uint32_t gend,
-                                               int lane, int vec_ok, int32_t* __restrict__ ids) {
+                                               const RowAux& A, int m, uint32_t Lf, Div32 divLf, uint32_t gbeg,
+                                               uint32_t gend, int lane, int vec_ok, int32_t* __restrict__ ids) {
   const uint32_t N = (uint32_t)D.npoints;
   uint32_t g = gbeg + (uint32_t)lane;
   if (g >= gend) return;
@@ -421,7 +438,7 @@ __device__ __forceinline__ void ids_range_rows(const MapCore& D, const Tabs& tab
     const int cnt = N - lin0 < 4 ? (int)(N - lin0) : 4;
     uint32_t v[4] = {0, 0, 0, 0};
     if (RUNS && (x < run_lo || x >= run_hi)) {
-      rc = row_contrib<SRC>(D, Cf, x);
+      rc = row_contrib<SRC>(D, Cf, A, x);
       uint64_t lo, hi;
       if (SRC == R_BLOCK) {
         const uint64_t a = rc / cl.sigma;
@@ -439,9 +456,22 @@ __device__ __forceinline__ void ids_range_rows(const MapCore& D, const Tabs& tab
     } else if (SRC == R_TAB4) {
       const uint4 c = *reinterpret_cast<const uint4*>(Cf + x);
       v[0] = T[base + c.x]; v[1] = T[base + c.y]; v[2] = T[base + c.z]; v[3] = T[base + c.w];
+    } else if (SRC == R_TAB2 && x + 4 <= Lf && A.Lin >= 4) {
+      // the group meets at most two entries of C2 (q0 and, when it crosses
+      // a boundary of the inner table, q0 + 1 < L[m], the row going on)
+      uint32_t q0, r0;
+      divmod32(x, A.divLin, q0, r0);
+      const uint32_t lo = base + __ldg(A.C2 + q0);
+      const uint32_t hi = r0 + 3 >= A.Lin ? base + __ldg(A.C2 + q0 + 1) : lo;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const uint32_t r = r0 + i;
+        const bool w = r >= A.Lin;
+        v[i] = T[(w ? hi : lo) + Cf[w ? r - A.Lin : r]];
+      }
     } else if (x + 4 <= Lf) {
 #pragma unroll
-      for (int i = 0; i < 4; ++i) v[i] = T[base + row_contrib<SRC>(D, Cf, x + i)];
+      for (int i = 0; i < 4; ++i) v[i] = T[base + row_contrib<SRC>(D, Cf, A, x + i)];
     } else if (Lf >= 4) {
       // the group crosses into the next row (at most once): select, do not
       // branch, so the lane does not hold its warp up (points past the end
@@ -450,7 +480,7 @@ __device__ __forceinline__ void ids_range_rows(const MapCore& D, const Tabs& tab
       for (int i = 0; i < 4; ++i) {
         const uint32_t xi = x + i;
         const bool w = xi >= Lf;
-        v[i] = T[(w ? nbase : base) + row_contrib<SRC>(D, Cf, w ? xi - Lf : xi)];
+        v[i] = T[(w ? nbase : base) + row_contrib<SRC>(D, Cf, A, w ? xi - Lf : xi)];
       }
     } else {
       uint32_t xi = x, ri = row, bi = base;
@@ -460,7 +490,7 @@ __device__ __forceinline__ void ids_range_rows(const MapCore& D, const Tabs& tab
           ri += 1;
           bi = ri == row + 1 ? nbase : row_base_m<uint32_t>(D, tabs, ctab, ri, m);
         }
-        v[i] = T[bi + row_contrib<SRC>(D, Cf, xi)];
+        v[i] = T[bi + row_contrib<SRC>(D, Cf, A, xi)];
         ++xi;
       }
     }

@@ -126,7 +126,8 @@ __global__ void __launch_bounds__(kThreads) k_ids_rows(const __grid_constant__ M
   const uint32_t gbeg = (uint32_t)gb;
   const uint64_t ge = gb + groups_per_warp;
   const uint32_t gend = (uint32_t)(ge < groups ? ge : groups);
-  ids_range_rows<SRC>(D, tabs, TSMEM ? Ts : Tg, Cf, ctab, m, Lf, divLf, gbeg, gend, threadIdx.x & 31, vec_ok, ids);
+  ids_range_rows<SRC>(D, tabs, TSMEM ? Ts : Tg, Cf, ctab, RowAux{}, m, Lf, divLf, gbeg, gend, threadIdx.x & 31,
+                      vec_ok, ids);
 }
 
 template <typename I, bool TSMEM>

@@ -228,6 +228,53 @@ def make_chain(chain):
     return arr, n
 
 
+_XFORM_DTYPE = np.dtype(mp_xform)
+_QUERY_DTYPE = np.dtype(mp_query)
+
+
+def _xform_row(op):
+    """One transform as a record of mp_xform's layout (see make_chain)."""
+    name = op[0]
+    i = j = k = d = tr = 0
+    T, h = (0, 0, 0, 0), (0, 0, 0, 0)
+    if name == "split":
+        i, d = int(op[1]), int(op[2])
+    elif name in ("merge", "swap"):
+        i, j = int(op[1]), int(op[2])
+    elif name == "decompose":
+        Tl = tuple(int(v) for v in op[2])
+        i, k = int(op[1]), len(Tl)
+        T = Tl + (0,) * (4 - k)
+        if len(op) > 3 and op[3] is not None:
+            hl = tuple(int(v) for v in op[3])
+            h = hl + (0,) * (4 - len(hl))
+        if len(op) > 4:
+            tr = sum(1 << int(m) for m in op[4])
+    elif name == "balance_split":
+        i, k = int(op[1]), int(op[2])
+    else:
+        raise ValueError(f"unknown transform {name!r}")
+    return (OPS[name], i, j, k, d, T, h, tr, 0)
+
+
+def query_records(launches):
+    """(L, machine, chain, dist, face_bytes) tuples as numpy records with the
+    layouts of mp_xform (every chain, one after the other) and mp_query (the
+    chain field pointing into the first array, which must outlive the use)."""
+    xrows, qrows = [], []
+    for L, machine, chain, dist, face in launches:
+        first = len(xrows)
+        xrows.extend(_xform_row(op) for op in chain)
+        ext = tuple(int(v) for v in L) + (0,) * (4 - len(L))
+        fb = tuple(int(v) for v in face) + (0,) * (4 - len(face))
+        qrows.append(((len(L), 0, ext), (int(machine[0]), int(machine[1])), first, len(chain), 0,
+                      (DISTS[dist[0]], int(dist[1]) if len(dist) > 1 else 1), fb))
+    xf = np.array(xrows or [_xform_row(("split", 0, 1))], dtype=_XFORM_DTYPE)
+    qs = np.array(qrows, dtype=_QUERY_DTYPE)
+    qs["chain"] = xf.ctypes.data + qs["chain"] * _XFORM_DTYPE.itemsize
+    return xf, qs
+
+
 def make_dist(dist) -> mp_dist:
     d = mp_dist()
     d.kind = DISTS[dist[0]]
@@ -548,23 +595,19 @@ class Batch:
     def __init__(self, launches):
         launches = list(launches)
         self.n = len(launches)
-        # identifies the batch's queries (for the persisted autotune choice)
-        self.signature = hashlib.sha256(repr([(tuple(L), tuple(m), [tuple(o) for o in ch], tuple(d), tuple(f))
-                                              for L, m, ch, d, f in launches]).encode()).hexdigest()
-        arr = (mp_query * self.n)()
-        keep = []
-        for q, (L, machine, chain, dist, face) in enumerate(launches):
-            ch, n = make_chain(chain)
-            keep.append(ch)
-            arr[q].space = make_space(L)
-            arr[q].machine = make_machine(machine)
-            arr[q].chain = ctypes.cast(ch, ctypes.c_void_p)
-            arr[q].n_xf = n
-            arr[q].dist = make_dist(dist)
-            for t, v in enumerate(face):
-                arr[q].face_bytes[t] = int(v)
+        self._launches = launches
+        self._signature = None
+        self._xf, self._qs = query_records(launches)
         self._h = ctypes.c_void_p()
-        _check(lib().mp_batch_create(arr, self.n, ctypes.byref(self._h)), "mp_batch_create")
+        _check(lib().mp_batch_create(self._qs.ctypes.data, self.n, ctypes.byref(self._h)), "mp_batch_create")
+
+    @property
+    def signature(self):
+        """Identifies the batch's queries (for the persisted autotune choice)."""
+        if self._signature is None:
+            self._signature = hashlib.sha256(repr([(tuple(L), tuple(m), [tuple(o) for o in ch], tuple(d), tuple(f))
+                                                   for L, m, ch, d, f in self._launches]).encode()).hexdigest()
+        return self._signature
 
     def info(self):
         ti, tp = ctypes.c_uint64(0), ctypes.c_uint64(0)

@@ -133,6 +133,41 @@ def test_batched_recipe_against_single_launch_path():
     b.close()
 
 
+# launch shapes that select each way a batched row finds its contributions:
+# rows fused into a table (multiple of 4 points or not, short or long),
+# two-level rows (a fused table under 128 points joined by the next
+# dimension's table; inner tables of 1 to 3 points cross several boundaries
+# within one 4-point group), rows computed in place (last extent above the
+# fused limit, aligned or not, above the table limit), 16-byte table rows
+ROW_SHAPES = [
+    (3, 5000, 7), (2, 4097, 1), (5, 2500, 2), (7, 3000, 3), (4, 1100, 4), (9, 33, 127), (6, 40, 4500, 2),
+    (3, 700, 100), (2, 3, 1500, 5), (11, 4097, 6), (40, 50, 60), (7, 2049), (13, 4093), (3, 66000),
+    (5, 40000), (2, 70001), (9, 8192), (4, 12, 5000), (2, 2, 2, 9001),
+]
+
+
+def test_row_shapes_against_oracle():
+    rng = W.rng(4300)
+    launches = []
+    for L in ROW_SHAPES:
+        for kind in W.DIST_KINDS:
+            machine = (rng.randint(1, 24), rng.randint(1, 8))
+            draws = [rng.next() for _ in range(rng.randint(0, 5))]
+            dist = ("block_cyclic", rng.randint(1, 7)) if kind == "block_cyclic" else (kind,)
+            launches.append((L, machine, N.chain_from_draws(*machine, draws), dist, [8] * len(L)))
+    b = N.Batch(launches)
+    info, ids, hist, halo, recv = batch_outputs(b)
+    b.run(ids=ids, hist=hist, halo=halo, recv=recv, autotune=True)
+    torch.cuda.synchronize()
+    ids, hist, halo, recv = (t.cpu().numpy() for t in (ids, hist, halo, recv))
+    for q, launch in enumerate(launches):
+        ref = O.Launch(*launch[:4])
+        rids, rhist = ref.map_points(threads=8)
+        rtot, rrecv = ref.comm_volume(launch[4], threads=8)
+        check_query(info, ids, hist, halo, recv, q, launch, rids, rhist, rtot, rrecv)
+    b.close()
+
+
 def test_batch_rejects_invalid_queries():
     with pytest.raises(N.MapleError):
         N.Batch([((4, 4), (2, 2), [("split", 0, 3)], ("block",), (1, 1))])

@@ -232,3 +232,27 @@ def test_secondary_lower_bound_is_reached_on_divisible_grids():
             idx = np.arange(i * nch, (i + 1) * nch, dtype=np.int64)
             _, s = O.candidate_costs(*MNK, (64, 8), 3, idx)
             assert N.secondary_lower_bound(q, f) // q["tile_bytes"] == int(s.min()), (MNK, f)
+
+
+def test_batch_query_records_match_the_c_structs():
+    # the numpy records handed to mp_batch_create hold, byte for byte, what
+    # the field-by-field ctypes structures hold (chain pointers aside, which
+    # must point at the same transforms)
+    from paper_2507_17087_gb300 import workloads as W
+    qs = W.batched_queries(400)
+    launches = [(q["L"], q["machine"], N.chain_from_draws(*q["machine"], q["draws"]), q["dist"], q["face"])
+                for q in qs]
+    launches.append(((5, 6), (2, 3), [("decompose", 0, (5, 6), (2, 1), (1,))], ("block_cyclic", 3), (4, 8)))
+    xf, rec = N.query_records(launches)
+    for q, (L, machine, chain, dist, face) in enumerate(launches):
+        ch, n = N.make_chain(chain)
+        a = N.mp_query()
+        a.space, a.machine, a.n_xf, a.dist = N.make_space(L), N.make_machine(machine), n, N.make_dist(dist)
+        for t, v in enumerate(face):
+            a.face_bytes[t] = int(v)
+        got, want = bytearray(rec[q].tobytes()), bytearray(bytes(a))
+        off = N.mp_query.chain.offset
+        got[off:off + 8] = want[off:off + 8] = bytes(8)
+        assert got == want, q
+        first = (int(rec[q]["chain"]) - xf.ctypes.data) // ctypes.sizeof(N.mp_xform)
+        assert xf[first:first + n].tobytes() == bytes(ch)[:ctypes.sizeof(N.mp_xform) * n], q
