@@ -129,7 +129,7 @@ def launches():
     return out
 
 
-def cpu_baseline(sample: int):
+def cpu_baseline(sample: int, single_core: bool = True):
     """The CPU oracle, as it stands, on the first `sample` points of the block
     variant: owner of each point and of its neighbours (ids + halo)."""
     import oracle as O
@@ -141,10 +141,21 @@ def cpu_baseline(sample: int):
     t0 = time.perf_counter()
     ref.map_range(cfg["face"], 0, sample, threads=cores)
     dt = time.perf_counter() - t0
-    return {"value": sample / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"first {sample} points of the 1024x1024x512 block launch: owner of each point "
-                      f"and of its 6 neighbours (ids + halo), std::thread over {cores} cores",
-            "seconds": dt}
+    res = {"value": sample / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": f"first {sample} points of the 1024x1024x512 block launch: owner of each point "
+                     f"and of its 6 neighbours (ids + halo), std::thread over {cores} cores",
+           "seconds": dt}
+    if not single_core:
+        return res
+    # one core, on a sample of the same points as many times smaller as there
+    # are cores
+    s1 = max(4096, sample // cores)
+    t0 = time.perf_counter()
+    ref.map_range(cfg["face"], 0, s1, threads=1)
+    dt1 = time.perf_counter() - t0
+    res["single_core"] = {"value": s1 / dt1, "unit": UNIT, "sample": f"first {s1} points, one thread",
+                          "seconds": dt1}
+    return res
 
 
 def extra_search(N, W, torch):
@@ -369,9 +380,9 @@ def run_reference(args, rank, world):
     times = []
     info = None
     for _ in range(max(args.warmup, 0)):
-        cpu_baseline(max(per_step // 8, 4096))
+        cpu_baseline(max(per_step // 8, 4096), single_core=False)
     for _ in range(steps):
-        info = cpu_baseline(per_step)
+        info = cpu_baseline(per_step, single_core=False)
         times.append(info["seconds"])
     total_s = sum(times)
     value = per_step * steps / total_s

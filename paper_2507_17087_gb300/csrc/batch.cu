@@ -246,7 +246,10 @@ __global__ void __launch_bounds__(kThreads) k_b_defscan(const QDesc* __restrict_
   }
 }
 
-__global__ void __launch_bounds__(kThreads) k_b_ids(const QDesc* __restrict__ qd, const Tile* __restrict__ tiles,
+// four resident blocks per SM: 64 registers and no spills, which the row
+// paths (row bases kept a row ahead, two-level rows) need; the 48-register
+// allocation without the bound spilled and ran the batch 5 % slower
+__global__ void __launch_bounds__(kThreads, 4) k_b_ids(const QDesc* __restrict__ qd, const Tile* __restrict__ tiles,
                                                     uint32_t ntiles, const uint32_t* __restrict__ Tpool,
                                                     const uint32_t* __restrict__ tabpool, uint32_t smem_T,
                                                     int vec_ok, unsigned* __restrict__ counter,
@@ -403,6 +406,8 @@ struct mp_batch {
   size_t ids_smem = 0;
   // graph
   cudaStream_t cap = nullptr;
+  cudaStream_t side = nullptr;            // the reductions' stream beside the id writer
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   cudaGraphExec_t exec = nullptr;
   void* key[4] = {nullptr, nullptr, nullptr, nullptr};
   std::mutex mu;
@@ -449,7 +454,10 @@ int launch_ids(mp_batch& b, int32_t* ids, cudaStream_t st) {
   return MP_OK;
 }
 
-// Enqueues the whole batch on st (used for capture).
+// Enqueues the whole batch on st (used for capture).  The reductions read
+// only the resolved chain table and the counts: when ids are wanted too they
+// run on the batch's second stream beside the tables and the id writer, and
+// st waits for them before the end.
 int enqueue(mp_batch& b, int32_t* ids, uint64_t* hist, uint64_t* halo, uint64_t* recv, cudaStream_t st) {
   const unsigned big = (unsigned)sm_count_b() * 8;
   auto blocks_for = [&](uint64_t work) {
@@ -460,40 +468,51 @@ int enqueue(mp_batch& b, int32_t* ids, uint64_t* hist, uint64_t* halo, uint64_t*
   k_b_resolve<<<blocks_for(b.totalP), kThreads, 0, st>>>(b.d_qd, b.d_prims, b.d_p_pref, (uint32_t)b.n, b.totalP,
                                                         b.d_T);
   count_launch();
-  if (ids && b.total_tab) {
-    k_b_tables<<<blocks_for(b.total_tab), kThreads, 0, st>>>(b.d_qd, b.d_tab_pref, (uint32_t)b.n, b.total_tab,
-                                                            b.d_tab);
-    count_launch();
+  const bool fork = ids && want_red;
+  cudaStream_t rs = st;
+  if (fork) {
+    MP_CUDA_TRY(cudaEventRecord(b.ev_fork, st));
+    MP_CUDA_TRY(cudaStreamWaitEvent(b.side, b.ev_fork, 0));
+    rs = b.side;
   }
   if (want_red && b.totalJ) {
-    k_b_counts<<<blocks_for(b.totalJ), kThreads, 0, st>>>(b.d_qd, b.d_cnt_pref, (uint32_t)b.n, b.totalJ, b.d_H,
+    k_b_counts<<<blocks_for(b.totalJ), kThreads, 0, rs>>>(b.d_qd, b.d_cnt_pref, (uint32_t)b.n, b.totalJ, b.d_H,
                                                          want_recv ? b.d_X : nullptr);
     count_launch();
   }
   if (want_recv && b.any_lc) {
-    MP_CUDA_TRY(cudaMemsetAsync(b.d_def, 0, (size_t)b.totalP * 8, st));
-    MP_CUDA_TRY(cudaMemsetAsync(b.d_defall, 0, (size_t)b.n * 8, st));
+    MP_CUDA_TRY(cudaMemsetAsync(b.d_def, 0, (size_t)b.totalP * 8, rs));
+    MP_CUDA_TRY(cudaMemsetAsync(b.d_defall, 0, (size_t)b.n * 8, rs));
     if (b.total_slab) {
-      k_b_slabs<<<blocks_for(b.total_slab), kThreads, 0, st>>>(b.d_qd, b.d_slabs, b.d_slab_pref,
+      k_b_slabs<<<blocks_for(b.total_slab), kThreads, 0, rs>>>(b.d_qd, b.d_slabs, b.d_slab_pref,
                                                                (uint32_t)b.slabs.size(), b.total_slab,
                                                                (unsigned long long*)b.d_def,
                                                                (unsigned long long*)b.d_defall);
       count_launch();
     }
-    k_b_defscan<<<(unsigned)b.n, kThreads, 0, st>>>(b.d_qd, (unsigned long long*)b.d_def,
+    k_b_defscan<<<(unsigned)b.n, kThreads, 0, rs>>>(b.d_qd, (unsigned long long*)b.d_def,
                                                    (const unsigned long long*)b.d_defall);
+    count_launch();
+  }
+  if (want_red) {
+    if (halo) MP_CUDA_TRY(cudaMemsetAsync(halo, 0, (size_t)b.n * 8, rs));
+    k_b_reduce<<<blocks_for(b.totalP), kThreads, 0, rs>>>(b.d_qd, b.d_p_pref, (uint32_t)b.n, b.totalP, b.d_T, b.d_H,
+                                                         want_recv ? b.d_X : nullptr, b.any_lc ? b.d_def : nullptr,
+                                                         hist, recv, (unsigned long long*)halo);
+    count_launch();
+  }
+  if (ids && b.total_tab) {
+    k_b_tables<<<blocks_for(b.total_tab), kThreads, 0, st>>>(b.d_qd, b.d_tab_pref, (uint32_t)b.n, b.total_tab,
+                                                            b.d_tab);
     count_launch();
   }
   if (ids) {
     int rc = launch_ids(b, ids, st);
     if (rc) return rc;
   }
-  if (want_red) {
-    if (halo) MP_CUDA_TRY(cudaMemsetAsync(halo, 0, (size_t)b.n * 8, st));
-    k_b_reduce<<<blocks_for(b.totalP), kThreads, 0, st>>>(b.d_qd, b.d_p_pref, (uint32_t)b.n, b.totalP, b.d_T, b.d_H,
-                                                         want_recv ? b.d_X : nullptr, b.any_lc ? b.d_def : nullptr,
-                                                         hist, recv, (unsigned long long*)halo);
-    count_launch();
+  if (fork) {
+    MP_CUDA_TRY(cudaEventRecord(b.ev_join, b.side));
+    MP_CUDA_TRY(cudaStreamWaitEvent(st, b.ev_join, 0));
   }
   MP_CUDA_TRY(cudaGetLastError());
   return MP_OK;
@@ -722,6 +741,9 @@ extern "C" int mp_batch_create(const mp_query* queries, int n, mp_batch** out) {
     ok = ok && cudaMemcpy(b->d_slabs, b->slabs.data(), b->slabs.size() * sizeof(Slab), cudaMemcpyHostToDevice) ==
                    cudaSuccess;
   ok = ok && cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) == cudaSuccess;
+  ok = ok && cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking) == cudaSuccess;
+  ok = ok && cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) == cudaSuccess;
+  ok = ok && cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming) == cudaSuccess;
   if (!ok || upload_tiles(*b, 8192) != MP_OK) {
     cudaGetLastError();
     mp_batch_destroy(b);
@@ -807,6 +829,9 @@ extern "C" int mp_batch_destroy(mp_batch* b) {
   if (!b) return MP_OK;
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->cap) cudaStreamDestroy(b->cap);
+  if (b->side) cudaStreamDestroy(b->side);
+  if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+  if (b->ev_join) cudaEventDestroy(b->ev_join);
   if (b->d_tiles) cudaFree(b->d_tiles);
   if (b->dmem) cudaFree(b->dmem);
   delete b;
