@@ -44,7 +44,7 @@ struct QInfo {
   uint32_t E[3];
   uint32_t P, n, g;
   uint32_t nf;
-  uint32_t pad;
+  uint32_t nd;   // divisors of P (entries of the fibre-node table, per step j)
   unsigned long long nchains;
   unsigned long long pmin;
   unsigned long long tile_bytes;
@@ -80,9 +80,29 @@ __global__ void k_chain_feats(const ChainProg* __restrict__ progs, unsigned long
   for (int i = 0; i < kChainFeat; ++i) out[(unsigned long long)i * NC + c] = f[i];
 }
 
-// 64 features of candidate idx = fr * NC + c.
-__device__ __forceinline__ void candidate_features(const QInfo& Q, const ChainProg* __restrict__ progs,
-                                                   const Fact* __restrict__ facts,
+// Fibre-node table: the node of flat index b of each chain, for b = 0 and
+// b = j * D[k] (j = 1, 2, 3; D the ascending divisors of P), which are the
+// first points of every fibre the features look at (fibre strides are
+// products of leading factors, so divisors of P).  Entry-major, entry
+// e = 0 or 1 + (j - 1) nd + k of chain c at e * NC + c; 0xFFFF where b >= P.
+// One warp per chain, so that its lanes walk the same chain program.
+__global__ void k_fibre_nodes(const ChainProg* __restrict__ progs, unsigned long long NC, uint32_t P,
+                              const uint32_t* __restrict__ D, uint32_t nd, uint16_t* __restrict__ out) {
+  const unsigned long long c = (unsigned long long)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+  if (c >= NC) return;
+  const ChainProg& cp = progs[c];
+  const uint32_t W = 1 + 3 * nd;
+  for (uint32_t e = threadIdx.x & 31; e < W; e += 32) {
+    uint32_t b = 0;
+    if (e > 0) b = (1 + (e - 1) / nd) * D[(e - 1) % nd];
+    out[(unsigned long long)e * NC + c] = b < P ? (uint16_t)resolve_node(cp, b) : (uint16_t)0xFFFF;
+  }
+}
+
+// 64 features of candidate idx = fr * NC + c.  fnode: the fibre-node table;
+// fdiv[fr]: the divisor indices of f0 (low half) and f0 f1 (high half).
+__device__ __forceinline__ void candidate_features(const QInfo& Q, const uint16_t* __restrict__ fnode,
+                                                   const uint32_t* __restrict__ fdiv, const Fact* __restrict__ facts,
                                                    const float* __restrict__ chainfeat, unsigned long long idx,
                                                    float x[64], unsigned long long* primary_out) {
   const unsigned long long fr = idx / Q.nchains, c = idx - fr * Q.nchains;
@@ -102,16 +122,17 @@ __device__ __forceinline__ void candidate_features(const QInfo& Q, const ChainPr
   x[19] = log2f(1.f + pn) / 3.f;
   x[20] = p == Q.pmin ? 1.f : 0.f;
   for (int i = 0; i < kChainFeat; ++i) x[21 + i] = __ldg(chainfeat + (unsigned long long)i * Q.nchains + c);
-  const ChainProg& cp = progs[c];
-  const uint32_t n0 = resolve_node(cp, 0);
+  const uint32_t n0 = __ldg(fnode + c);
   const uint32_t stride[3] = {1u, f[0], f[0] * f[1]};
+  const uint32_t dv = __ldg(fdiv + fr);
+  const uint32_t di[3] = {0u, dv & 0xFFFFu, dv >> 16};
   for (int v = 0; v < 3; ++v) {
     float ch = 0.f, distinct = 1.f;
     if (f[v] > 1 && stride[v] < Q.P) {
       uint32_t seen[4] = {n0, 0, 0, 0};
       int ns = 1;
       for (uint32_t j = 1; j < 4 && j < f[v] && j * stride[v] < Q.P; ++j) {
-        const uint32_t nd = resolve_node(cp, j * stride[v]);
+        const uint32_t nd = __ldg(fnode + (unsigned long long)(1 + (j - 1) * Q.nd + di[v]) * Q.nchains + c);
         if (j == 1) ch = nd != n0 ? 1.f : 0.f;
         bool dup = false;
         for (int a = 0; a < ns; ++a) dup = dup || seen[a] == nd;
@@ -147,14 +168,15 @@ __global__ void k_primaries(const Fact* __restrict__ facts, uint32_t nf, uint32_
 
 // Features (BF16, row-major n x 64) of listed candidates; with exact costs
 // (bytes) also the regression targets.
-__global__ void k_features_idx(const __grid_constant__ QInfo Q, const ChainProg* __restrict__ progs,
-                               const Fact* __restrict__ facts, const float* __restrict__ chainfeat,
+__global__ void k_features_idx(const __grid_constant__ QInfo Q, const uint16_t* __restrict__ fnode,
+                               const uint32_t* __restrict__ fdiv, const Fact* __restrict__ facts,
+                               const float* __restrict__ chainfeat,
                                const int64_t* __restrict__ idx, int64_t n, const uint64_t* __restrict__ pbytes,
                                const uint64_t* __restrict__ sbytes, bf16* __restrict__ X, float* __restrict__ target) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   float x[64];
-  candidate_features(Q, progs, facts, chainfeat, (unsigned long long)idx[i], x, nullptr);
+  candidate_features(Q, fnode, fdiv, facts, chainfeat, (unsigned long long)idx[i], x, nullptr);
   for (int j = 0; j < 64; j += 2)
     *reinterpret_cast<__nv_bfloat162*>(X + i * 64 + j) = __floats2bfloat162_rn(x[j], x[j + 1]);
   if (target) target[i] = target_of(pbytes[i] / Q.tile_bytes, sbytes[i] / Q.tile_bytes, Q.pmin);
@@ -175,8 +197,9 @@ __global__ void k_features_idx(const __grid_constant__ QInfo Q, const ChainProg*
 
 constexpr uint32_t kTileBytes = 128 * 128;   // 128 rows x 64 BF16
 
-__global__ void __launch_bounds__(128) k_feat_img(const __grid_constant__ QInfo Q, const ChainProg* __restrict__ progs,
-                                                  const Fact* __restrict__ facts, const float* __restrict__ chainfeat,
+__global__ void __launch_bounds__(128) k_feat_img(const __grid_constant__ QInfo Q, const uint16_t* __restrict__ fnode,
+                                                  const uint32_t* __restrict__ fdiv, const Fact* __restrict__ facts,
+                                                  const float* __restrict__ chainfeat,
                                                   const uint32_t* __restrict__ flist, unsigned long long c0,
                                                   unsigned long long n, uint8_t* __restrict__ img) {
   const unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;   // < padded n
@@ -188,7 +211,7 @@ __global__ void __launch_bounds__(128) k_feat_img(const __grid_constant__ QInfo 
       const unsigned long long j = cand / Q.nchains;
       idx = (unsigned long long)flist[j] * Q.nchains + (cand - j * Q.nchains);
     }
-    candidate_features(Q, progs, facts, chainfeat, idx, x, nullptr);
+    candidate_features(Q, fnode, fdiv, facts, chainfeat, idx, x, nullptr);
   } else {
     for (int j = 0; j < 64; ++j) x[j] = 0.f;
   }
@@ -504,68 +527,6 @@ int sm_count_l() {
 
 size_t a256(size_t v) { return (v + 255) & ~size_t(255); }
 
-struct Prepared {
-  SearchSpace S;
-  QInfo Q;
-  ChainProg* d_progs = nullptr;
-  Fact* d_facts = nullptr;
-  float* d_chainfeat = nullptr;
-  std::vector<unsigned long long> prim;   // primary (tiles) per factorisation
-};
-
-// Plans the query, uploads the chain programs and factorisations into the
-// given device region and computes primaries and chain features there.
-int prepare_query(const mp_search_query& q, Prepared& pq, char* region, size_t cap, size_t* used,
-                  cudaStream_t st) {
-  int rc = prepare(q, pq.S);
-  if (rc) return rc;
-  const size_t NC = pq.S.c->chains.size(), NF = pq.S.c->facts.size();
-  const size_t o_p = 0, o_f = a256(NC * sizeof(ChainProg)), o_cf = o_f + a256(NF * sizeof(Fact)),
-               o_pr = o_cf + a256(NC * kChainFeat * 4), end = o_pr + a256(NF * 8);
-  if (end > cap) return MP_ENOMEM;
-  *used = end;
-  pq.d_progs = (ChainProg*)(region + o_p);
-  pq.d_facts = (Fact*)(region + o_f);
-  pq.d_chainfeat = (float*)(region + o_cf);
-  unsigned long long* d_prim = (unsigned long long*)(region + o_pr);
-  MP_CUDA_TRY(cudaMemcpyAsync(pq.d_progs, pq.S.c->progs.data(), NC * sizeof(ChainProg), cudaMemcpyHostToDevice, st));
-  MP_CUDA_TRY(cudaMemcpyAsync(pq.d_facts, pq.S.c->fdev.data(), NF * sizeof(Fact), cudaMemcpyHostToDevice, st));
-  k_chain_feats<<<(unsigned)((NC + 127) / 128), 128, 0, st>>>(pq.d_progs, NC, (uint32_t)q.procs, pq.d_chainfeat);
-  k_primaries<<<(unsigned)((NF + 127) / 128), 128, 0, st>>>(pq.d_facts, (uint32_t)NF, (uint32_t)q.M, (uint32_t)q.N,
-                                                            (uint32_t)q.K, d_prim);
-  count_launch(2);
-  pq.prim.resize(NF);
-  MP_CUDA_TRY(cudaMemcpyAsync(pq.prim.data(), d_prim, NF * 8, cudaMemcpyDeviceToHost, st));
-  MP_CUDA_TRY(cudaStreamSynchronize(st));
-  QInfo& Q = pq.Q;
-  std::memset(&Q, 0, sizeof(Q));
-  Q.E[0] = (uint32_t)q.M;
-  Q.E[1] = (uint32_t)q.N;
-  Q.E[2] = (uint32_t)q.K;
-  Q.P = (uint32_t)q.procs;
-  Q.g = (uint32_t)q.procs_per_node;
-  Q.n = Q.P / Q.g;
-  Q.nf = (uint32_t)NF;
-  Q.nchains = NC;
-  Q.tile_bytes = q.tile_bytes;
-  Q.pmin = *std::min_element(pq.prim.begin(), pq.prim.end());
-  Q.qf[0] = std::log2((double)q.M) / 12.0;
-  Q.qf[1] = std::log2((double)q.N) / 12.0;
-  Q.qf[2] = std::log2((double)q.K) / 12.0;
-  Q.qf[3] = std::log2((double)q.procs) / 14.0;
-  Q.qf[4] = std::log2((double)Q.n) / 12.0;
-  Q.qf[5] = std::log2((double)Q.g) / 3.0;
-  return MP_OK;
-}
-
-uint64_t splitmix(uint64_t& s) {
-  s += 0x9E3779B97F4A7C15ull;
-  uint64_t z = s;
-  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-  return z ^ (z >> 31);
-}
-
 struct Pool {
   char* p = nullptr;
   size_t size = 0;
@@ -590,6 +551,92 @@ Pool g_pool_q, g_pool_s;   // query data; scores and selection
 
 Pool g_pool_img;   // feature tile images of the scoring kernels
 
+struct Prepared {
+  SearchSpace S;
+  QInfo Q;
+  ChainProg* d_progs = nullptr;
+  Fact* d_facts = nullptr;
+  float* d_chainfeat = nullptr;
+  uint16_t* d_fnode = nullptr;   // fibre-node table (k_fibre_nodes)
+  uint32_t* d_fdiv = nullptr;    // per factorisation: divisor indices of f0 and f0 f1
+  std::vector<unsigned long long> prim;   // primary (tiles) per factorisation
+};
+
+// Plans the query, uploads the chain programs and factorisations into the
+// query region (g_pool_q) and computes primaries, chain features and the
+// fibre-node table there.
+int prepare_query(const mp_search_query& q, Prepared& pq, cudaStream_t st) {
+  int rc = prepare(q, pq.S);
+  if (rc) return rc;
+  const size_t NC = pq.S.c->chains.size(), NF = pq.S.c->facts.size();
+  const uint32_t P = (uint32_t)q.procs;
+  std::vector<uint32_t> D;
+  for (uint32_t d = 1; d <= P; ++d)
+    if (P % d == 0) D.push_back(d);
+  const uint32_t nd = (uint32_t)D.size();
+  std::vector<uint32_t> fdiv(NF);
+  for (size_t i = 0; i < NF; ++i) {
+    const uint32_t f0 = (uint32_t)pq.S.c->facts[i][0], f01 = f0 * (uint32_t)pq.S.c->facts[i][1];
+    const uint32_t a = (uint32_t)(std::lower_bound(D.begin(), D.end(), f0) - D.begin());
+    const uint32_t b = (uint32_t)(std::lower_bound(D.begin(), D.end(), f01) - D.begin());
+    fdiv[i] = a | (b << 16);
+  }
+  const size_t W = 1 + 3 * (size_t)nd;
+  const size_t o_p = 0, o_f = a256(NC * sizeof(ChainProg)), o_cf = o_f + a256(NF * sizeof(Fact)),
+               o_pr = o_cf + a256(NC * kChainFeat * 4), o_fn = o_pr + a256(NF * 8), o_fd = o_fn + a256(NC * W * 2),
+               o_D = o_fd + a256(NF * 4), end = o_D + a256(nd * 4);
+  char* region = g_pool_q.get(std::max<size_t>(end, 64u << 20));
+  if (!region) return MP_ENOMEM;
+  pq.d_progs = (ChainProg*)(region + o_p);
+  pq.d_facts = (Fact*)(region + o_f);
+  pq.d_chainfeat = (float*)(region + o_cf);
+  pq.d_fnode = (uint16_t*)(region + o_fn);
+  pq.d_fdiv = (uint32_t*)(region + o_fd);
+  uint32_t* d_D = (uint32_t*)(region + o_D);
+  unsigned long long* d_prim = (unsigned long long*)(region + o_pr);
+  MP_CUDA_TRY(cudaMemcpyAsync(pq.d_progs, pq.S.c->progs.data(), NC * sizeof(ChainProg), cudaMemcpyHostToDevice, st));
+  MP_CUDA_TRY(cudaMemcpyAsync(pq.d_facts, pq.S.c->fdev.data(), NF * sizeof(Fact), cudaMemcpyHostToDevice, st));
+  MP_CUDA_TRY(cudaMemcpyAsync(pq.d_fdiv, fdiv.data(), NF * 4, cudaMemcpyHostToDevice, st));
+  MP_CUDA_TRY(cudaMemcpyAsync(d_D, D.data(), nd * 4, cudaMemcpyHostToDevice, st));
+  k_chain_feats<<<(unsigned)((NC + 127) / 128), 128, 0, st>>>(pq.d_progs, NC, P, pq.d_chainfeat);
+  k_primaries<<<(unsigned)((NF + 127) / 128), 128, 0, st>>>(pq.d_facts, (uint32_t)NF, (uint32_t)q.M, (uint32_t)q.N,
+                                                            (uint32_t)q.K, d_prim);
+  k_fibre_nodes<<<(unsigned)((NC + 3) / 4), 128, 0, st>>>(pq.d_progs, NC, P, d_D, nd, pq.d_fnode);
+  count_launch(3);
+  pq.prim.resize(NF);
+  MP_CUDA_TRY(cudaMemcpyAsync(pq.prim.data(), d_prim, NF * 8, cudaMemcpyDeviceToHost, st));
+  MP_CUDA_TRY(cudaStreamSynchronize(st));
+  QInfo& Q = pq.Q;
+  std::memset(&Q, 0, sizeof(Q));
+  Q.E[0] = (uint32_t)q.M;
+  Q.E[1] = (uint32_t)q.N;
+  Q.E[2] = (uint32_t)q.K;
+  Q.P = (uint32_t)q.procs;
+  Q.g = (uint32_t)q.procs_per_node;
+  Q.n = Q.P / Q.g;
+  Q.nf = (uint32_t)NF;
+  Q.nd = nd;
+  Q.nchains = NC;
+  Q.tile_bytes = q.tile_bytes;
+  Q.pmin = *std::min_element(pq.prim.begin(), pq.prim.end());
+  Q.qf[0] = std::log2((double)q.M) / 12.0;
+  Q.qf[1] = std::log2((double)q.N) / 12.0;
+  Q.qf[2] = std::log2((double)q.K) / 12.0;
+  Q.qf[3] = std::log2((double)q.procs) / 14.0;
+  Q.qf[4] = std::log2((double)Q.n) / 12.0;
+  Q.qf[5] = std::log2((double)Q.g) / 3.0;
+  return MP_OK;
+}
+
+uint64_t splitmix(uint64_t& s) {
+  s += 0x9E3779B97F4A7C15ull;
+  uint64_t z = s;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+
 // Scores of the candidates at positions [0, ncand) of the scored list (flist
 // maps positions to factorisation ranks; null = every candidate), in runs
 // of 2^19 (64 MB of feature tiles, resident in L2 between the two kernels).
@@ -603,7 +650,8 @@ int score_candidates(mp_mlp* h, const Prepared& pq, const uint32_t* d_fl, uint64
   for (uint64_t c0 = 0; c0 < ncand; c0 += kRun) {
     const uint64_t n = std::min<uint64_t>(kRun, ncand - c0);
     const uint32_t ntiles = (uint32_t)((n + 127) / 128);
-    k_feat_img<<<ntiles, 128, 0, st>>>(pq.Q, pq.d_progs, pq.d_facts, pq.d_chainfeat, d_fl, c0, n, img);
+    k_feat_img<<<ntiles, 128, 0, st>>>(pq.Q, pq.d_fnode, pq.d_fdiv, pq.d_facts, pq.d_chainfeat, d_fl, c0, n,
+                                       img);
     const unsigned grid = (unsigned)std::min<uint64_t>((ntiles + 1) / 2, (uint64_t)sm_count_l());
     k_mlp_img<<<grid, 256, kMlpSmem, st>>>(img, ntiles, h->Wimg, h->P, n, d_sc + c0, h->status);
     count_launch(2);
@@ -678,10 +726,7 @@ extern "C" int mp_mlp_train_search(mp_mlp* h, const mp_search_query* queries, in
   for (int qi = 0; qi < n_queries && !rc; ++qi) {
     const mp_search_query& q = queries[qi];
     Prepared pq;
-    size_t used = 0;
-    char* region = g_pool_q.get(64u << 20);
-    if (!region) { rc = MP_ENOMEM; break; }
-    if ((rc = prepare_query(q, pq, region, 64u << 20, &used, st))) break;
+    if ((rc = prepare_query(q, pq, st))) break;
     const uint64_t NC = pq.S.c->chains.size(), NF = pq.S.c->facts.size();
     std::vector<uint32_t> order(NF);
     std::iota(order.begin(), order.end(), 0u);
@@ -700,7 +745,8 @@ extern "C" int mp_mlp_train_search(mp_mlp* h, const mp_search_query* queries, in
     }
     if (cudaMemcpyAsync(d_idx, idx.data(), per * 8, cudaMemcpyHostToDevice, st) != cudaSuccess) { rc = MP_ECUDA; break; }
     if ((rc = candidate_costs_dev(q, pq.S, pq.d_progs, pq.d_facts, d_idx, (int64_t)per, d_p, d_s, st))) break;
-    k_features_idx<<<(unsigned)((per + 127) / 128), 128, 0, st>>>(pq.Q, pq.d_progs, pq.d_facts, pq.d_chainfeat, d_idx,
+    k_features_idx<<<(unsigned)((per + 127) / 128), 128, 0, st>>>(pq.Q, pq.d_fnode, pq.d_fdiv, pq.d_facts,
+                                                                  pq.d_chainfeat, d_idx,
                                                                   (int64_t)per, d_p, d_s, X + (size_t)qi * per * 64,
                                                                   T + (size_t)qi * per);
     count_launch();
@@ -747,10 +793,7 @@ extern "C" int mp_learned_search(mp_mlp* h, const mp_search_query* query, int K,
   const mp_search_query& q = *query;
   auto t_phase = clk::now();
   Prepared pq;
-  size_t used = 0;
-  char* region = g_pool_q.get(64u << 20);
-  if (!region) return MP_ENOMEM;
-  if ((rc = prepare_query(q, pq, region, 64u << 20, &used, st))) return rc;
+  if ((rc = prepare_query(q, pq, st))) return rc;
   const uint64_t NC = pq.S.c->chains.size(), NF = pq.S.c->facts.size();
   // the candidates that can win: every chain with a factorisation of least
   // primary cost (exact, closed form); MP_LEARNED_SCORE_ALL scores them all
@@ -982,10 +1025,7 @@ extern "C" int mp_learned_scores(mp_mlp* h, const mp_search_query* query, float*
   if (!is_device_pointer(scores) || (features && !is_device_pointer(features))) return MP_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
   Prepared pq;
-  size_t used = 0;
-  char* region = g_pool_q.get(64u << 20);
-  if (!region) return MP_ENOMEM;
-  if ((rc = prepare_query(*query, pq, region, 64u << 20, &used, st))) return rc;
+  if ((rc = prepare_query(*query, pq, st))) return rc;
   const uint64_t ncand = (uint64_t)pq.S.c->chains.size() * pq.S.c->facts.size();
   *n_out = (int64_t)ncand;
   MP_CUDA_TRY(cudaMemsetAsync(h->status, 0, 4, st));
@@ -996,7 +1036,8 @@ extern "C" int mp_learned_scores(mp_mlp* h, const mp_search_query* query, float*
     std::vector<int64_t> idx(ncand);
     std::iota(idx.begin(), idx.end(), (int64_t)0);
     MP_CUDA_TRY(cudaMemcpyAsync(d_idx, idx.data(), ncand * 8, cudaMemcpyHostToDevice, st));
-    k_features_idx<<<(unsigned)((ncand + 127) / 128), 128, 0, st>>>(pq.Q, pq.d_progs, pq.d_facts, pq.d_chainfeat,
+    k_features_idx<<<(unsigned)((ncand + 127) / 128), 128, 0, st>>>(pq.Q, pq.d_fnode, pq.d_fdiv, pq.d_facts,
+                                                                     pq.d_chainfeat,
                                                                      d_idx, (int64_t)ncand, nullptr, nullptr,
                                                                      (bf16*)features, nullptr);
     count_launch();

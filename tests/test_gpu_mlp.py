@@ -29,6 +29,7 @@ def test_gemm_bf16_against_float64(M, N_, K):
     assert err <= 1e-5 * scale * max(1.0, K / 256), (err, scale)
 
 
+import oracle as O  # noqa: E402
 from oracle import mlp as R  # noqa: E402
 from paper_2507_17087_gb300 import workloads as W  # noqa: E402
 
@@ -151,3 +152,49 @@ def test_learned_search_trains_and_finds_the_optimum():
     got = model.learned_search(q, K=1024, fallback=True, score_all=True)
     assert got["n_scored"] == exact["n_candidates"]
     assert (got["primary_bytes"], got["secondary_bytes"]) == (exact["primary_bytes"], exact["secondary_bytes"])
+
+
+def test_fibre_features_against_oracle_nodes():
+    # features 53..58 of a candidate (factorisation f, chain c): whether the
+    # node changes one step along each fibre, and how many distinct nodes its
+    # first four points reach; recomputed from the oracle's owner of each flat
+    # index of the chain space (values 0, 1/4 .. 1 are exact in BF16)
+    model = N.MLP(seed=8)
+    n, g = 30, 8
+    P = n * g
+    q = {"MNK": (256, 1024, 256), "machine": (n, g), "max_depth": 2, "tile_bytes": 512 * 512 * 4}
+    nf, nc = N.search_space(P, g, 2)
+    facts = O.factorisations(P, 3)
+    chains = O.chains(n, g, 2)
+    assert (len(facts), len(chains)) == (nf, nc)
+    npad = (nf * nc + 127) // 128 * 128
+    scores = torch.empty(nf * nc, dtype=torch.float32, device="cuda")
+    feats = torch.zeros(npad, 64, dtype=torch.bfloat16, device="cuda")
+    assert model.scores(q, scores, feats) == nf * nc
+    got = feats[:, 53:59].float().cpu().numpy()
+    rng = np.random.default_rng(8)
+    node_cache = {}
+    for c in rng.choice(nc, 40, replace=False):
+        if c not in node_cache:
+            own = O.Launch((P,), (n, g), list(chains[c]), ("block",)).owner_of(np.arange(P, dtype=np.int64))
+            node_cache[c] = own // g
+        node = node_cache[c]
+        for fr in rng.choice(nf, 25, replace=False):
+            f = facts[fr]
+            want = []
+            stride = (1, f[0], f[0] * f[1])
+            ch, dist = [0.0] * 3, [0.25] * 3
+            for v in range(3):
+                if f[v] > 1 and stride[v] < P:
+                    seen = [node[0]]
+                    j = 1
+                    while j < 4 and j < f[v] and j * stride[v] < P:
+                        nd = node[j * stride[v]]
+                        if j == 1:
+                            ch[v] = float(nd != node[0])
+                        if nd not in seen:
+                            seen.append(nd)
+                        j += 1
+                    dist[v] = len(seen) / 4.0
+            want = ch + dist
+            assert np.array_equal(got[fr * nc + c], np.array(want, dtype=np.float32)), (fr, c, f, chains[c])
