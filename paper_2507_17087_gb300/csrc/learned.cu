@@ -850,11 +850,13 @@ extern "C" int mp_learned_search(mp_mlp* h, const mp_search_query* query, int K,
   // a lower bound on the secondary of every candidate that can win (the
   // least-primary factorisations); reaching it certifies the winner
   uint64_t min_lb = ~0ull;
+  std::vector<uint64_t> lb_of(NF, 0);
   for (uint64_t fr = 0; fr < NF; ++fr)
     if (pq.prim[fr] == pq.Q.pmin) {
       const uint32_t f[3] = {(uint32_t)pq.S.c->facts[fr][0], (uint32_t)pq.S.c->facts[fr][1],
                              (uint32_t)pq.S.c->facts[fr][2]};
       const uint64_t lb = secondary_lower_bound(pq.Q.E, f, pq.Q.n, pq.Q.g);
+      lb_of[fr] = lb;
       if (lb < min_lb) min_lb = lb;
     }
   // ---- the Kc best scores, evaluated exactly; Kc grows until accepted
@@ -981,8 +983,13 @@ extern "C" int mp_learned_search(mp_mlp* h, const mp_search_query* query, int K,
     t_phase = clk::now();
     mp_search_query qf = q;
     qf.flags = 0;
-    // the selection's winner bounds the secondary the search must look for
-    rc = exhaustive_search(qf, out, st, p_best_last == pq.Q.pmin ? s_best_last : ~0ull);
+    // the selection's winner bounds the secondary the search must look for,
+    // and factorisations whose lower bound lies above it need no scan
+    const bool bounded = p_best_last == pq.Q.pmin;
+    std::vector<uint8_t> skip(NF, 0);
+    if (bounded)
+      for (uint64_t fr = 0; fr < NF; ++fr) skip[fr] = pq.prim[fr] == pq.Q.pmin && lb_of[fr] > s_best_last;
+    rc = exhaustive_search(qf, out, st, bounded ? s_best_last : ~0ull, bounded ? &skip : nullptr);
     if (stats) {
       stats->fallback = 1;
       stats->n_exact += out->n_candidates;

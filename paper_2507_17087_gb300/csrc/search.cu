@@ -38,7 +38,7 @@ size_t align_up(size_t v) { return (v + 255) & ~size_t(255); }
 __global__ void __launch_bounds__(256, 4) k_search(const ChainProg* __restrict__ progs, const Fact* __restrict__ facts, int nf,
                          uint32_t P, uint32_t E0, uint32_t E1, uint32_t E2, int words,
                          unsigned long long nchains, int full, unsigned long long ub,
-                         Key* __restrict__ chain_best) {
+                         const uint8_t* __restrict__ skip, Key* __restrict__ chain_best) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ Key red[32];
   uint32_t* bm = reinterpret_cast<uint32_t*>(smem_raw);
@@ -73,6 +73,7 @@ __global__ void __launch_bounds__(256, 4) k_search(const ChainProg* __restrict__
     Key k;
     k.p = primary_cost(E, f);
     if (!full && k.p > pmin) continue;   // uniform across the warp
+    if (skip && skip[fr]) continue;
     k.s = secondary_cost_warp(tab, wbm, blockDim.x, words, E, f, lane, ub);
     k.idx = (unsigned long long)fr * nchains + c;
     if (key_less(k, best)) best = k;
@@ -302,25 +303,32 @@ void fill_result(const mp_search_query& q, const SearchSpace& S, const Key& k, m
 }  // namespace
 
 int exhaustive_search(const mp_search_query& q, mp_search_result* out, cudaStream_t st,
-                      unsigned long long ub_secondary) {
+                      unsigned long long ub_secondary, const std::vector<uint8_t>* skip) {
   SearchSpace S;
   int rc = prepare(q, S);
   if (rc) return rc;
-  const uint64_t NC = S.c->chains.size();
+  const uint64_t NC = S.c->chains.size(), NF = S.c->facts.size();
+  if (skip && skip->size() != NF) return MP_EINVAL;
   ChainProg* d_progs;
   Fact* d_facts;
   char* rest;
-  const size_t best_bytes = align_up(NC * sizeof(Key)) + sizeof(Key);
+  const size_t best_bytes = align_up(NC * sizeof(Key)) + align_up(sizeof(Key)) + align_up(NF);
   rc = upload(S, st, &d_progs, &d_facts, &rest, best_bytes, 2);
   if (rc) return rc;
   Key* chain_best = (Key*)rest;
   Key* d_out = (Key*)(rest + align_up(NC * sizeof(Key)));
+  uint8_t* d_skip = nullptr;
+  if (skip) {
+    d_skip = (uint8_t*)(rest + align_up(NC * sizeof(Key)) + align_up(sizeof(Key)));
+    MP_CUDA_TRY(cudaMemcpyAsync(d_skip, skip->data(), NF, cudaMemcpyHostToDevice, st));
+  }
   if (S.smem > 48 * 1024)
     MP_CUDA_TRY(cudaFuncSetAttribute(k_search, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S.smem));
   k_search<<<(unsigned)NC, S.threads, S.smem, st>>>(d_progs, d_facts, (int)S.c->facts.size(), (uint32_t)q.procs,
                                                     (uint32_t)q.M, (uint32_t)q.N, (uint32_t)q.K, S.words, NC,
                                                     (q.flags & MP_SEARCH_FULL) ? 1 : 0,
-                                                    (q.flags & MP_SEARCH_FULL) ? ~0ull : ub_secondary, chain_best);
+                                                    (q.flags & MP_SEARCH_FULL) ? ~0ull : ub_secondary,
+                                                    (q.flags & MP_SEARCH_FULL) ? nullptr : d_skip, chain_best);
   count_launch();
   k_search_final<<<1, 1024, 0, st>>>(chain_best, NC, d_out);
   count_launch();

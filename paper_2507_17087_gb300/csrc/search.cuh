@@ -356,8 +356,10 @@ int candidate_costs_dev(const mp_search_query& q, const SearchSpace& S, const Ch
 // ub_secondary (tiles): a secondary cost some candidate of least primary is
 // known to reach; candidates are scanned only as far as needed to show they
 // exceed it (the result is the same as without it).
+// skip (optional, one byte per factorisation): factorisations known not to
+// hold the answer (a lower bound on their secondary above ub_secondary).
 int exhaustive_search(const mp_search_query& q, mp_search_result* out, cudaStream_t st,
-                      unsigned long long ub_secondary = ~0ull);
+                      unsigned long long ub_secondary = ~0ull, const std::vector<uint8_t>* skip = nullptr);
 // Lower bound (tiles) on the secondary cost of factorisation f over every
 // chain; 0 when no bound applies (see search.cu).
 uint64_t secondary_lower_bound(const uint32_t E[3], const uint32_t f[3], uint32_t nodes, uint32_t g);
