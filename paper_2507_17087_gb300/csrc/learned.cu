@@ -86,8 +86,11 @@ __global__ void k_chain_feats(const ChainProg* __restrict__ progs, unsigned long
 // products of leading factors, so divisors of P).  Entry-major, entry
 // e = 0 or 1 + (j - 1) nd + k of chain c at e * NC + c; 0xFFFF where b >= P.
 // One warp per chain, so that its lanes walk the same chain program.
+// gtab (may be null): every chain's node table (rows of Pp entries), read
+// instead of walking the chain program.
 __global__ void k_fibre_nodes(const ChainProg* __restrict__ progs, unsigned long long NC, uint32_t P,
-                              const uint32_t* __restrict__ D, uint32_t nd, uint16_t* __restrict__ out) {
+                              const uint32_t* __restrict__ D, uint32_t nd, const uint16_t* __restrict__ gtab,
+                              uint32_t Pp, uint16_t* __restrict__ out) {
   const unsigned long long c = (unsigned long long)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
   if (c >= NC) return;
   const ChainProg& cp = progs[c];
@@ -95,7 +98,9 @@ __global__ void k_fibre_nodes(const ChainProg* __restrict__ progs, unsigned long
   for (uint32_t e = threadIdx.x & 31; e < W; e += 32) {
     uint32_t b = 0;
     if (e > 0) b = (1 + (e - 1) / nd) * D[(e - 1) % nd];
-    out[(unsigned long long)e * NC + c] = b < P ? (uint16_t)resolve_node(cp, b) : (uint16_t)0xFFFF;
+    uint16_t v = 0xFFFF;
+    if (b < P) v = gtab ? __ldg(gtab + c * Pp + b) : (uint16_t)resolve_node(cp, b);
+    out[(unsigned long long)e * NC + c] = v;
   }
 }
 
@@ -554,8 +559,9 @@ Pool g_pool_img;   // feature tile images of the scoring kernels
 struct Prepared {
   SearchSpace S;
   QInfo Q;
-  ChainProg* d_progs = nullptr;
-  Fact* d_facts = nullptr;
+  const DeviceSpace* D = nullptr;   // the space's device copy (chain programs, factorisations, node tables)
+  const ChainProg* d_progs = nullptr;
+  const Fact* d_facts = nullptr;
   float* d_chainfeat = nullptr;
   uint16_t* d_fnode = nullptr;   // fibre-node table (k_fibre_nodes)
   uint32_t* d_fdiv = nullptr;    // per factorisation: divisor indices of f0 and f0 f1
@@ -582,26 +588,25 @@ int prepare_query(const mp_search_query& q, Prepared& pq, cudaStream_t st) {
     fdiv[i] = a | (b << 16);
   }
   const size_t W = 1 + 3 * (size_t)nd;
-  const size_t o_p = 0, o_f = a256(NC * sizeof(ChainProg)), o_cf = o_f + a256(NF * sizeof(Fact)),
-               o_pr = o_cf + a256(NC * kChainFeat * 4), o_fn = o_pr + a256(NF * 8), o_fd = o_fn + a256(NC * W * 2),
-               o_D = o_fd + a256(NF * 4), end = o_D + a256(nd * 4);
+  if ((rc = device_space(*pq.S.c, st, &pq.D))) return rc;
+  pq.d_progs = pq.D->progs;
+  pq.d_facts = pq.D->facts;
+  const size_t o_cf = 0, o_pr = o_cf + a256(NC * kChainFeat * 4), o_fn = o_pr + a256(NF * 8),
+               o_fd = o_fn + a256(NC * W * 2), o_D = o_fd + a256(NF * 4), end = o_D + a256(nd * 4);
   char* region = g_pool_q.get(std::max<size_t>(end, 64u << 20));
   if (!region) return MP_ENOMEM;
-  pq.d_progs = (ChainProg*)(region + o_p);
-  pq.d_facts = (Fact*)(region + o_f);
   pq.d_chainfeat = (float*)(region + o_cf);
   pq.d_fnode = (uint16_t*)(region + o_fn);
   pq.d_fdiv = (uint32_t*)(region + o_fd);
   uint32_t* d_D = (uint32_t*)(region + o_D);
   unsigned long long* d_prim = (unsigned long long*)(region + o_pr);
-  MP_CUDA_TRY(cudaMemcpyAsync(pq.d_progs, pq.S.c->progs.data(), NC * sizeof(ChainProg), cudaMemcpyHostToDevice, st));
-  MP_CUDA_TRY(cudaMemcpyAsync(pq.d_facts, pq.S.c->fdev.data(), NF * sizeof(Fact), cudaMemcpyHostToDevice, st));
   MP_CUDA_TRY(cudaMemcpyAsync(pq.d_fdiv, fdiv.data(), NF * 4, cudaMemcpyHostToDevice, st));
   MP_CUDA_TRY(cudaMemcpyAsync(d_D, D.data(), nd * 4, cudaMemcpyHostToDevice, st));
   k_chain_feats<<<(unsigned)((NC + 127) / 128), 128, 0, st>>>(pq.d_progs, NC, P, pq.d_chainfeat);
   k_primaries<<<(unsigned)((NF + 127) / 128), 128, 0, st>>>(pq.d_facts, (uint32_t)NF, (uint32_t)q.M, (uint32_t)q.N,
                                                             (uint32_t)q.K, d_prim);
-  k_fibre_nodes<<<(unsigned)((NC + 3) / 4), 128, 0, st>>>(pq.d_progs, NC, P, d_D, nd, pq.d_fnode);
+  k_fibre_nodes<<<(unsigned)((NC + 3) / 4), 128, 0, st>>>(pq.d_progs, NC, P, d_D, nd, pq.D->tab, pq.D->Pp,
+                                                           pq.d_fnode);
   count_launch(3);
   pq.prim.resize(NF);
   MP_CUDA_TRY(cudaMemcpyAsync(pq.prim.data(), d_prim, NF * 8, cudaMemcpyDeviceToHost, st));
@@ -744,7 +749,7 @@ extern "C" int mp_mlp_train_search(mp_mlp* h, const mp_search_query* queries, in
       idx[i] = (int64_t)(fr * NC + (splitmix(rng) % NC));
     }
     if (cudaMemcpyAsync(d_idx, idx.data(), per * 8, cudaMemcpyHostToDevice, st) != cudaSuccess) { rc = MP_ECUDA; break; }
-    if ((rc = candidate_costs_dev(q, pq.S, pq.d_progs, pq.d_facts, d_idx, (int64_t)per, d_p, d_s, st))) break;
+    if ((rc = candidate_costs_dev(q, pq.S, *pq.D, d_idx, (int64_t)per, d_p, d_s, st))) break;
     k_features_idx<<<(unsigned)((per + 127) / 128), 128, 0, st>>>(pq.Q, pq.d_fnode, pq.d_fdiv, pq.d_facts,
                                                                   pq.d_chainfeat, d_idx,
                                                                   (int64_t)per, d_p, d_s, X + (size_t)qi * per * 64,
@@ -911,7 +916,7 @@ extern "C" int mp_learned_search(mp_mlp* h, const mp_search_query* query, int K,
       v = (int64_t)((uint64_t)flist[j] * NC + ((uint64_t)v - j * NC));
     }
     MP_CUDA_TRY(cudaMemcpyAsync(d_sel, sel.data(), (size_t)nsel * 8, cudaMemcpyHostToDevice, st));
-    if ((rc = candidate_costs_dev(q, pq.S, pq.d_progs, pq.d_facts, d_sel, nsel, d_p, d_s, st))) return rc;
+    if ((rc = candidate_costs_dev(q, pq.S, *pq.D, d_sel, nsel, d_p, d_s, st))) return rc;
     MP_CUDA_TRY(cudaMemcpyAsync(d_sel, pos.data(), (size_t)nsel * 8, cudaMemcpyHostToDevice, st));
     k_take<<<(unsigned)((nsel + 255) / 256), 256, 0, st>>>(d_sc, d_sel, (int)nsel, d_y);
     count_launch();

@@ -38,7 +38,8 @@ size_t align_up(size_t v) { return (v + 255) & ~size_t(255); }
 __global__ void __launch_bounds__(256, 4) k_search(const ChainProg* __restrict__ progs, const Fact* __restrict__ facts, int nf,
                          uint32_t P, uint32_t E0, uint32_t E1, uint32_t E2, int words,
                          unsigned long long nchains, int full, unsigned long long ub,
-                         const uint8_t* __restrict__ skip, Key* __restrict__ chain_best) {
+                         const uint8_t* __restrict__ skip, const uint16_t* __restrict__ gtab, uint32_t Pp,
+                         Key* __restrict__ chain_best) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ Key red[32];
   uint32_t* bm = reinterpret_cast<uint32_t*>(smem_raw);
@@ -48,7 +49,8 @@ __global__ void __launch_bounds__(256, 4) k_search(const ChainProg* __restrict__
   if (threadIdx.x == 0) cp = progs[c];
   for (int w = 0; w < words; ++w) bm[w * blockDim.x + threadIdx.x] = 0;
   __syncthreads();
-  build_table(cp, tab, P);
+  if (gtab) load_table(gtab + (size_t)c * Pp, tab, Pp);
+  else build_table(cp, tab, P);
   __syncthreads();
   const uint32_t E[3] = {E0, E1, E2};
   unsigned long long pmin = 0;
@@ -82,6 +84,15 @@ __global__ void __launch_bounds__(256, 4) k_search(const ChainProg* __restrict__
   if (threadIdx.x == 0) chain_best[c] = best;
 }
 
+// Every chain's node table (one CTA per chain), for the space's device copy.
+__global__ void k_node_tables(const ChainProg* __restrict__ progs, uint32_t P, uint32_t Pp, uint16_t* __restrict__ tab) {
+  __shared__ ChainProg cp;
+  if (threadIdx.x == 0) cp = progs[blockIdx.x];
+  __syncthreads();
+  uint16_t* row = tab + (size_t)blockIdx.x * Pp;
+  for (uint32_t b = threadIdx.x; b < Pp; b += blockDim.x) row[b] = b < P ? (uint16_t)resolve_node(cp, b) : (uint16_t)0;
+}
+
 __global__ void k_search_final(const Key* __restrict__ chain_best, unsigned long long n, Key* __restrict__ out) {
   __shared__ Key red[32];
   Key best{~0ull, ~0ull, ~0ull};
@@ -98,8 +109,8 @@ __global__ void k_search_final(const Key* __restrict__ chain_best, unsigned long
 __global__ void k_candidate_costs(const ChainProg* __restrict__ progs, const Fact* __restrict__ facts, int nf,
                                   const int64_t* __restrict__ idx, unsigned long long nchains, uint32_t P,
                                   uint32_t E0, uint32_t E1, uint32_t E2, int words,
-                                  unsigned long long tile_bytes, uint64_t* __restrict__ prim_out,
-                                  uint64_t* __restrict__ sec_out) {
+                                  unsigned long long tile_bytes, const uint16_t* __restrict__ gtab, uint32_t Pp,
+                                  uint64_t* __restrict__ prim_out, uint64_t* __restrict__ sec_out) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ ChainProg cp;
   __shared__ unsigned long long red[32];
@@ -117,7 +128,8 @@ __global__ void k_candidate_costs(const ChainProg* __restrict__ progs, const Fac
   if (threadIdx.x == 0) cp = progs[c];
   for (int w = 0; w < words; ++w) bm[w * blockDim.x + threadIdx.x] = 0;
   __syncthreads();
-  build_table(cp, tab, P);
+  if (gtab) load_table(gtab + (size_t)c * Pp, tab, Pp);
+  else build_table(cp, tab, P);
   __syncthreads();
   const uint32_t E[3] = {E0, E1, E2};
   const uint32_t f[3] = {facts[fr].f[0], facts[fr].f[1], facts[fr].f[2]};
@@ -230,6 +242,7 @@ std::shared_ptr<const SpaceCore> space_core(int64_t procs, int64_t g, int depth)
       }
   }
   auto core = std::make_shared<SpaceCore>();
+  core->P = procs;
   const int64_t n = procs / g;
   core->facts = ordered_factorisations(procs, 3);
   core->chains = canonical_chains(n, g, depth);
@@ -259,23 +272,59 @@ int prepare(const mp_search_query& q, SearchSpace& S) {
   return MP_OK;
 }
 
-namespace {
+SpaceCore::~SpaceCore() {
+  // cudaFree waits for the device, so no kernel still reads these
+  if (dev.progs) cudaFree(dev.progs);
+  if (dev.tab) cudaFree(dev.tab);
+}
 
-int upload(const SearchSpace& S, cudaStream_t st, ChainProg** d_progs, Fact** d_facts, char** rest,
-           size_t rest_bytes, int slot) {
-  const size_t pb = align_up(S.c->progs.size() * sizeof(ChainProg));
-  const size_t fb = align_up(S.c->fdev.size() * sizeof(Fact));
-  char* ws = (char*)workspace(pb + fb + rest_bytes, slot);
-  if (!ws) return MP_ENOMEM;
-  *d_progs = (ChainProg*)ws;
-  *d_facts = (Fact*)(ws + pb);
-  *rest = ws + pb + fb;
-  MP_CUDA_TRY(cudaMemcpyAsync(*d_progs, S.c->progs.data(), S.c->progs.size() * sizeof(ChainProg),
-                              cudaMemcpyHostToDevice, st));
-  MP_CUDA_TRY(cudaMemcpyAsync(*d_facts, S.c->fdev.data(), S.c->fdev.size() * sizeof(Fact),
-                              cudaMemcpyHostToDevice, st));
+int device_space(const SpaceCore& c, cudaStream_t st, const DeviceSpace** out) {
+  int device = 0;
+  MP_CUDA_TRY(cudaGetDevice(&device));
+  std::lock_guard<std::mutex> lk(c.dev_mu);
+  DeviceSpace& D = c.dev;
+  if (D.progs) {
+    if (D.device != device) return MP_ENOTSUP;
+    *out = &D;
+    return MP_OK;
+  }
+  const size_t NC = c.progs.size(), NF = c.fdev.size();
+  const size_t pb = align_up(NC * sizeof(ChainProg)), fb = align_up(NF * sizeof(Fact));
+  char* mem = nullptr;
+  if (cudaMalloc(&mem, pb + fb) != cudaSuccess) {
+    cudaGetLastError();
+    return MP_ENOMEM;
+  }
+  const uint32_t Pp = (uint32_t)((c.P + 7) & ~int64_t(7));
+  uint16_t* tab = nullptr;
+  if (NC * Pp * 2 <= kNodeTableCacheBytes && cudaMalloc(&tab, NC * Pp * 2) != cudaSuccess) {
+    cudaGetLastError();
+    tab = nullptr;   // the kernels build each chain's table themselves
+  }
+  bool ok = cudaMemcpyAsync(mem, c.progs.data(), NC * sizeof(ChainProg), cudaMemcpyHostToDevice, st) == cudaSuccess &&
+            cudaMemcpyAsync(mem + pb, c.fdev.data(), NF * sizeof(Fact), cudaMemcpyHostToDevice, st) == cudaSuccess;
+  if (ok && tab && NC) {
+    k_node_tables<<<(unsigned)NC, 256, 0, st>>>((const ChainProg*)mem, (uint32_t)c.P, Pp, tab);
+    count_launch();
+    ok = cudaGetLastError() == cudaSuccess;
+  }
+  ok = ok && cudaStreamSynchronize(st) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    cudaFree(mem);
+    if (tab) cudaFree(tab);
+    return MP_ECUDA;
+  }
+  D.progs = (ChainProg*)mem;
+  D.facts = (Fact*)(mem + pb);
+  D.tab = tab;
+  D.Pp = Pp;
+  D.device = device;
+  *out = &D;
   return MP_OK;
 }
+
+namespace {
 
 void fill_result(const mp_search_query& q, const SearchSpace& S, const Key& k, mp_search_result& r) {
   std::memset(&r, 0, sizeof(r));
@@ -309,12 +358,11 @@ int exhaustive_search(const mp_search_query& q, mp_search_result* out, cudaStrea
   if (rc) return rc;
   const uint64_t NC = S.c->chains.size(), NF = S.c->facts.size();
   if (skip && skip->size() != NF) return MP_EINVAL;
-  ChainProg* d_progs;
-  Fact* d_facts;
-  char* rest;
+  const DeviceSpace* D = nullptr;
+  if ((rc = device_space(*S.c, st, &D))) return rc;
   const size_t best_bytes = align_up(NC * sizeof(Key)) + align_up(sizeof(Key)) + align_up(NF);
-  rc = upload(S, st, &d_progs, &d_facts, &rest, best_bytes, 2);
-  if (rc) return rc;
+  char* rest = (char*)workspace(best_bytes, 2);
+  if (!rest) return MP_ENOMEM;
   Key* chain_best = (Key*)rest;
   Key* d_out = (Key*)(rest + align_up(NC * sizeof(Key)));
   uint8_t* d_skip = nullptr;
@@ -324,11 +372,12 @@ int exhaustive_search(const mp_search_query& q, mp_search_result* out, cudaStrea
   }
   if (S.smem > 48 * 1024)
     MP_CUDA_TRY(cudaFuncSetAttribute(k_search, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S.smem));
-  k_search<<<(unsigned)NC, S.threads, S.smem, st>>>(d_progs, d_facts, (int)S.c->facts.size(), (uint32_t)q.procs,
+  k_search<<<(unsigned)NC, S.threads, S.smem, st>>>(D->progs, D->facts, (int)S.c->facts.size(), (uint32_t)q.procs,
                                                     (uint32_t)q.M, (uint32_t)q.N, (uint32_t)q.K, S.words, NC,
                                                     (q.flags & MP_SEARCH_FULL) ? 1 : 0,
                                                     (q.flags & MP_SEARCH_FULL) ? ~0ull : ub_secondary,
-                                                    (q.flags & MP_SEARCH_FULL) ? nullptr : d_skip, chain_best);
+                                                    (q.flags & MP_SEARCH_FULL) ? nullptr : d_skip, D->tab, D->Pp,
+                                                    chain_best);
   count_launch();
   k_search_final<<<1, 1024, 0, st>>>(chain_best, NC, d_out);
   count_launch();
@@ -340,16 +389,15 @@ int exhaustive_search(const mp_search_query& q, mp_search_result* out, cudaStrea
   return MP_OK;
 }
 
-int candidate_costs_dev(const mp_search_query& q, const SearchSpace& S, const ChainProg* d_progs,
-                        const Fact* d_facts, const int64_t* d_idx, int64_t n, uint64_t* d_p, uint64_t* d_s,
-                        cudaStream_t st) {
+int candidate_costs_dev(const mp_search_query& q, const SearchSpace& S, const DeviceSpace& D, const int64_t* d_idx,
+                        int64_t n, uint64_t* d_p, uint64_t* d_s, cudaStream_t st) {
   if (n <= 0) return MP_OK;
   if (S.smem > 48 * 1024)
     MP_CUDA_TRY(cudaFuncSetAttribute(k_candidate_costs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S.smem));
-  k_candidate_costs<<<(unsigned)n, S.threads, S.smem, st>>>(d_progs, d_facts, (int)S.c->facts.size(), d_idx,
+  k_candidate_costs<<<(unsigned)n, S.threads, S.smem, st>>>(D.progs, D.facts, (int)S.c->facts.size(), d_idx,
                                                              (unsigned long long)S.c->chains.size(), (uint32_t)q.procs,
                                                              (uint32_t)q.M, (uint32_t)q.N, (uint32_t)q.K, S.words,
-                                                             q.tile_bytes, d_p, d_s);
+                                                             q.tile_bytes, D.tab, D.Pp, d_p, d_s);
   count_launch();
   MP_CUDA_TRY(cudaGetLastError());
   return MP_OK;
@@ -393,21 +441,20 @@ extern "C" int mp_candidate_costs(const mp_search_query* query, const int64_t* i
       if (v < 0 || (uint64_t)v >= NC * NF) return MP_EINVAL;
   }
   const size_t ib = align_up((size_t)n * 8);
-  ChainProg* d_progs;
-  Fact* d_facts;
-  char* rest;
-  rc = upload(S, st, &d_progs, &d_facts, &rest, 3 * ib, 3);
-  if (rc) return rc;
+  const DeviceSpace* D = nullptr;
+  if ((rc = device_space(*S.c, st, &D))) return rc;
+  char* rest = (char*)workspace(3 * ib, 3);
+  if (!rest) return MP_ENOMEM;
   int64_t* d_idx = idx_dev ? (int64_t*)indices : (int64_t*)rest;
   uint64_t* d_p = p_dev ? primary : (uint64_t*)(rest + ib);
   uint64_t* d_s = s_dev ? secondary : (uint64_t*)(rest + 2 * ib);
   if (!idx_dev) MP_CUDA_TRY(cudaMemcpyAsync(d_idx, host_idx.data(), n * 8, cudaMemcpyHostToDevice, st));
   if (S.smem > 48 * 1024)
     MP_CUDA_TRY(cudaFuncSetAttribute(k_candidate_costs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S.smem));
-  k_candidate_costs<<<(unsigned)n, S.threads, S.smem, st>>>(d_progs, d_facts, (int)NF, d_idx, NC, (uint32_t)query->procs,
-                                                             (uint32_t)query->M, (uint32_t)query->N,
-                                                             (uint32_t)query->K, S.words, query->tile_bytes, d_p,
-                                                             d_s);
+  k_candidate_costs<<<(unsigned)n, S.threads, S.smem, st>>>(D->progs, D->facts, (int)NF, d_idx, NC,
+                                                             (uint32_t)query->procs, (uint32_t)query->M,
+                                                             (uint32_t)query->N, (uint32_t)query->K, S.words,
+                                                             query->tile_bytes, D->tab, D->Pp, d_p, d_s);
   count_launch();
   MP_CUDA_TRY(cudaGetLastError());
   if (!p_dev) MP_CUDA_TRY(cudaMemcpyAsync(primary, d_p, n * 8, cudaMemcpyDeviceToHost, st));

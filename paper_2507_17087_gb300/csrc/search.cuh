@@ -3,6 +3,7 @@
 #pragma once
 
 #include <memory>
+#include <mutex>
 #include <vector>
 
 #include "engine.h"
@@ -325,18 +326,49 @@ __device__ __forceinline__ void build_table(const ChainProg& cp, uint16_t* tab, 
   for (uint32_t b = threadIdx.x; b < P; b += blockDim.x) tab[b] = (uint16_t)resolve_node(cp, b);
 }
 
+// The chain's node table from its cached copy (16-byte rows of Pp entries).
+__device__ __forceinline__ void load_table(const uint16_t* __restrict__ row, uint16_t* tab, uint32_t Pp) {
+  const uint4* src = reinterpret_cast<const uint4*>(row);
+  uint4* dst = reinterpret_cast<uint4*>(tab);
+  for (uint32_t i = threadIdx.x; i < Pp / 8; i += blockDim.x) dst[i] = __ldg(src + i);
+}
+
 
 // ----------------------------------------------------------------- host side
 
 // The candidate space of one machine shape and depth bound: factorisations,
 // chains and their compiled programs.  Immutable once built and shared by
 // every query on the same (processors, processors per node, depth).
+// Its device copy (built on first use, kept with the space): the chain
+// programs, the factorisations and, when it takes at most
+// kNodeTableCacheBytes, every chain's node table (chain c's node of flat index
+// b at tab[c * Pp + b], Pp = P rounded up to 8 so that each chain's row is
+// 16-byte aligned), which the search kernels copy instead of rebuilding.
+struct DeviceSpace {
+  ChainProg* progs = nullptr;
+  Fact* facts = nullptr;
+  uint16_t* tab = nullptr;
+  uint32_t Pp = 0;
+  int device = -1;
+};
+
 struct SpaceCore {
   std::vector<std::vector<int64_t>> facts;
   std::vector<std::vector<CanonOp>> chains;
   std::vector<ChainProg> progs;
   std::vector<Fact> fdev;
+  int64_t P = 0;
+  mutable std::mutex dev_mu;
+  mutable DeviceSpace dev;
+  ~SpaceCore();
 };
+
+constexpr size_t kNodeTableCacheBytes = size_t(1) << 30;
+
+// The space's device copy on the current device, built on st on first use
+// (and synchronised then); MP_ENOTSUP when the space was first used on
+// another device.
+int device_space(const SpaceCore& c, cudaStream_t st, const DeviceSpace** out);
 
 struct SearchSpace {
   std::shared_ptr<const SpaceCore> c;
@@ -348,10 +380,10 @@ struct SearchSpace {
 ChainProg compile_chain(int64_t n, int64_t g, const std::vector<CanonOp>& ch);
 int validate_query(const mp_search_query& q);
 int prepare(const mp_search_query& q, SearchSpace& S);
-// Exact costs (bytes) of n listed candidates, all buffers on the device.
-int candidate_costs_dev(const mp_search_query& q, const SearchSpace& S, const ChainProg* d_progs,
-                        const Fact* d_facts, const int64_t* d_idx, int64_t n, uint64_t* d_p, uint64_t* d_s,
-                        cudaStream_t st);
+// Exact costs (bytes) of n listed candidates, all buffers on the device
+// (the space's device copy from device_space).
+int candidate_costs_dev(const mp_search_query& q, const SearchSpace& S, const DeviceSpace& D, const int64_t* d_idx,
+                        int64_t n, uint64_t* d_p, uint64_t* d_s, cudaStream_t st);
 // Exhaustive argmin on the device; the result on the host.
 // ub_secondary (tiles): a secondary cost some candidate of least primary is
 // known to reach; candidates are scanned only as far as needed to show they
