@@ -101,3 +101,27 @@ def test_candidate_costs_device_buffers_and_out_of_range():
     assert p[3:].cpu().numpy().astype(np.uint64).tolist() == [2 ** 64 - 1] * 2
     with pytest.raises(N.MapleError):
         N.candidate_costs(q, np.array([nf * nc], dtype=np.int64), np.zeros(1, np.uint64), np.zeros(1, np.uint64))
+
+
+def test_space_cache_eviction_and_reuse():
+    # more distinct candidate spaces (P, g, depth) than the device cache
+    # keeps, each searched twice in a row and again after it was evicted,
+    # with and without the primary bound: every answer equals the oracle's
+    shapes = [((n, g), d) for (n, g) in ((2, 2), (3, 2), (4, 2), (6, 1), (5, 2), (3, 4), (7, 1), (2, 8), (9, 2), (4, 4))
+              for d in (2,)]
+    queries = [{"MNK": (16, 8, 64), "machine": m, "max_depth": d, "tile_bytes": TILE} for m, d in shapes]
+    refs = [oracle_best(q) for q in queries]
+    for rnd in range(2):
+        for q, ref in zip(queries, refs):
+            for full in (False, True):
+                got = N.decompose_search([q], full=full)[0]
+                assert (got["index"], got["secondary_bytes"]) == (ref["index"], ref["secondary"] * TILE), (rnd, q)
+    # listed candidates through the cached tables, against the oracle's costs
+    q = queries[0]
+    nf, nc = N.search_space(q["machine"][0] * q["machine"][1], q["machine"][1], q["max_depth"])
+    idx = np.arange(nf * nc, dtype=np.int64)
+    p = np.zeros(nf * nc, dtype=np.uint64)
+    s = np.zeros(nf * nc, dtype=np.uint64)
+    N.candidate_costs(q, idx, p, s)
+    rp, rs = O.candidate_costs(*q["MNK"], q["machine"], q["max_depth"], idx)
+    assert np.array_equal(p, rp.astype(np.uint64) * TILE) and np.array_equal(s, rs.astype(np.uint64) * TILE)
