@@ -744,6 +744,79 @@ extern "C" int mp_hier_chain(int32_t rank, const int64_t* a, const int64_t* b, i
   return MP_OK;
 }
 
+namespace mp {
+namespace {
+
+// Element-halo totals of many launch plans at once (the two-level search):
+// the per-dimension counts of every plan, then one thread per flat final
+// index F of every plan.  A plan's total needs neither its chain table nor
+// its ids, only the counts (the owner changes exactly where a dimension's
+// final coordinate does).
+struct PlanHalo {
+  MapCore c;
+  uint64_t face[4];
+  uint32_t width[4];
+  uint32_t cnt_off, p_off;
+};
+
+// index q with pref[q] <= e < pref[q + 1]
+__device__ __forceinline__ uint32_t find_plan(const uint32_t* __restrict__ pref, uint32_t n, uint32_t e) {
+  uint32_t lo = 0, hi = n;
+  while (hi - lo > 1) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (pref[mid] <= e) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+__global__ void __launch_bounds__(kThreads) k_plans_counts(const PlanHalo* __restrict__ plans,
+                                                           const uint32_t* __restrict__ cnt_pref, uint32_t n,
+                                                           uint32_t total, uint64_t* __restrict__ H,
+                                                           uint64_t* __restrict__ X) {
+  for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+    const PlanHalo& Q = plans[find_plan(cnt_pref, n, e)];
+    const uint32_t r = e - Q.cnt_off;
+    int t = 0;
+    while (t < Q.c.k - 1 && r >= Q.c.Joff[t + 1]) ++t;
+    uint64_t h, xc;
+    dim_counts(Q.c, t, r - Q.c.Joff[t], h, xc);
+    H[e] = h;
+    X[e] = dim_elems(Q.c, t, r - Q.c.Joff[t], Q.width[t]);
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_plans_reduce(const PlanHalo* __restrict__ plans,
+                                                           const uint32_t* __restrict__ p_pref, uint32_t n,
+                                                           uint32_t total, const uint64_t* __restrict__ H,
+                                                           const uint64_t* __restrict__ X,
+                                                           unsigned long long* __restrict__ totals) {
+  for (uint32_t e0 = blockIdx.x * blockDim.x; e0 < total; e0 += gridDim.x * blockDim.x) {
+    const uint32_t e = e0 + threadIdx.x;
+    uint32_t q = 0xFFFFFFFFu;
+    unsigned long long r = 0;
+    if (e < total) {
+      q = find_plan(p_pref, n, e);
+      const PlanHalo& Q = plans[q];
+      uint64_t h_F, r_F;
+      reduce_F(Q.c, H + Q.cnt_off, X + Q.cnt_off, nullptr, Q.face, true, e - Q.p_off, h_F, r_F);
+      r = r_F;
+    }
+    // one atomic per group of lanes of the same plan
+    const unsigned same = __match_any_sync(0xFFFFFFFFu, q);
+    const int lane = threadIdx.x & 31;
+    if (q != 0xFFFFFFFFu) {
+      // the lowest lane of each group adds the group's sum
+      unsigned long long s = 0;
+      for (unsigned m = same; m; m &= m - 1) s += __shfl_sync(same, r, __ffs(m) - 1);
+      if (lane == __ffs(same) - 1 && s) atomicAdd(totals + q, s);
+    }
+  }
+}
+
+}  // namespace
+}  // namespace mp
+
 extern "C" int mp_hier_search(const mp_hier_query* query, mp_hier_result* out, void* stream) {
   using namespace mp;
   if (!query || !out) return MP_EINVAL;
@@ -785,6 +858,63 @@ extern "C" int mp_hier_search(const mp_hier_query* query, mp_hier_result* out, v
     return build_plan(&q.space, &q.machine, ch.data(), (int)ch.size(), &d, pl);
   };
   Plan pl;
+  uint64_t* totals = (uint64_t*)workspace((NA + ncand) * 8, 5);
+  if (!totals) return MP_ENOMEM;
+  // every plan's total in two launches when no plan is linearised cyclic
+  // (every plan built, so validated, before the launches)
+  {
+    std::vector<PlanHalo> ph(NA + ncand);
+    std::vector<uint32_t> cnt_pref(NA + ncand + 1, 0), p_pref(NA + ncand + 1, 0);
+    bool all_plain = true;
+    for (size_t i = 0; i < NA + ncand && all_plain; ++i) {
+      int rc = i < NA ? plan_node(i, pl) : plan_proc(i - NA, pl);
+      if (rc) return rc;
+      all_plain = !pl.desc.lc && (uint64_t)cnt_pref[i] + pl.desc.Jtotal < (1ull << 31) &&
+                  (uint64_t)p_pref[i] + pl.desc.P < (1ull << 31);
+      PlanHalo& h = ph[i];
+      std::memset(&h, 0, sizeof(h));
+      h.c = static_cast<const MapCore&>(pl.desc);
+      for (int t = 0; t < 4; ++t) {
+        h.face[t] = t < k ? q.bytes[t] : 0;
+        h.width[t] = t < k ? (uint32_t)q.width[t] : 0;
+      }
+      h.cnt_off = cnt_pref[i];
+      h.p_off = p_pref[i];
+      cnt_pref[i + 1] = cnt_pref[i] + pl.desc.Jtotal;
+      p_pref[i + 1] = p_pref[i] + pl.desc.P;
+    }
+    if (all_plain) {
+      const size_t NP = NA + ncand, J = cnt_pref[NP], PT = p_pref[NP];
+      auto align_up = [](size_t v) { return (v + 255) & ~size_t(255); };
+      const size_t o_ph = 0, o_cp = align_up(NP * sizeof(PlanHalo)), o_pp = o_cp + align_up((NP + 1) * 4),
+                   o_H = o_pp + align_up((NP + 1) * 4), o_X = o_H + align_up(J * 8), end = o_X + align_up(J * 8);
+      char* ws = (char*)workspace(end, 7);
+      if (!ws) return MP_ENOMEM;
+      PlanHalo* d_ph = (PlanHalo*)(ws + o_ph);
+      uint32_t* d_cp = (uint32_t*)(ws + o_cp);
+      uint32_t* d_pp = (uint32_t*)(ws + o_pp);
+      uint64_t* d_H = (uint64_t*)(ws + o_H);
+      uint64_t* d_X = (uint64_t*)(ws + o_X);
+      MP_CUDA_TRY(cudaMemcpyAsync(d_ph, ph.data(), NP * sizeof(PlanHalo), cudaMemcpyHostToDevice, st));
+      MP_CUDA_TRY(cudaMemcpyAsync(d_cp, cnt_pref.data(), (NP + 1) * 4, cudaMemcpyHostToDevice, st));
+      MP_CUDA_TRY(cudaMemcpyAsync(d_pp, p_pref.data(), (NP + 1) * 4, cudaMemcpyHostToDevice, st));
+      MP_CUDA_TRY(cudaMemsetAsync(totals, 0, NP * 8, st));
+      const unsigned big = (unsigned)sm_count() * 8;
+      auto blocks_for = [&](uint64_t work) {
+        return (unsigned)std::max<uint64_t>(1, std::min<uint64_t>((work + kThreads - 1) / kThreads, big));
+      };
+      if (J) {
+        k_plans_counts<<<blocks_for(J), kThreads, 0, st>>>(d_ph, d_cp, (uint32_t)NP, (uint32_t)J, d_H, d_X);
+        count_launch();
+      }
+      k_plans_reduce<<<blocks_for(PT), kThreads, 0, st>>>(d_ph, d_pp, (uint32_t)NP, (uint32_t)PT, d_H, d_X,
+                                                          (unsigned long long*)totals);
+      count_launch();
+      MP_CUDA_TRY(cudaGetLastError());
+    }
+    if (all_plain) goto totals_ready;
+  }
+  {
   // every plan is validated before anything is launched
   for (size_t i = 0; i < NA; ++i) {
     int rc = plan_node(i, pl);
@@ -794,8 +924,6 @@ extern "C" int mp_hier_search(const mp_hier_query* query, mp_hier_result* out, v
     int rc = plan_proc(c, pl);
     if (rc) return rc;
   }
-  uint64_t* totals = (uint64_t*)workspace((NA + ncand) * 8, 5);
-  if (!totals) return MP_ENOMEM;
   auto run = [&](const Plan& p, uint64_t* total) {
     Want w;
     std::memset(&w, 0, sizeof(w));
@@ -817,6 +945,8 @@ extern "C" int mp_hier_search(const mp_hier_query* query, mp_hier_result* out, v
     if (!rc) rc = run(pl, totals + NA + c);
     if (rc) return rc;
   }
+  }
+totals_ready:
   std::vector<uint64_t> h(NA + ncand);
   MP_CUDA_TRY(cudaMemcpyAsync(h.data(), totals, h.size() * 8, cudaMemcpyDeviceToHost, st));
   MP_CUDA_TRY(cudaStreamSynchronize(st));
