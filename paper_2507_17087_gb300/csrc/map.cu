@@ -360,6 +360,38 @@ LcHalo make_lc_halo(const MapDesc& D, const Want& w) {
 
 size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
 
+// A second stream (and its fork / join events) per host thread and device,
+// for the reductions that run beside an id writer.  Null if it cannot be
+// created (the reductions then run on the caller's stream).
+struct ForkStreams {
+  cudaStream_t side = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
+  bool ok = false;
+  ~ForkStreams() {
+    if (side) cudaStreamDestroy(side);
+    if (fork) cudaEventDestroy(fork);
+    if (join) cudaEventDestroy(join);
+  }
+};
+
+const ForkStreams* fork_streams() {
+  constexpr int kMaxDevices = 64;
+  thread_local ForkStreams per_device[kMaxDevices];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  ForkStreams& f = per_device[dev];
+  if (!f.ok && !f.side) {
+    f.ok = cudaStreamCreateWithFlags(&f.side, cudaStreamNonBlocking) == cudaSuccess &&
+           cudaEventCreateWithFlags(&f.fork, cudaEventDisableTiming) == cudaSuccess &&
+           cudaEventCreateWithFlags(&f.join, cudaEventDisableTiming) == cudaSuccess;
+    if (!f.ok) cudaGetLastError();
+  }
+  return f.ok ? &f : nullptr;
+}
+
 // Runs the kernels of one launch into device buffers.
 // Device scratch of one launch: the chain table T, the per-dimension c_t
 // tables, the per-dimension counts H / X and the linear-cyclic deficits.
@@ -406,14 +438,80 @@ int run_launch_ws(const Plan& pl, const Want& w, const Layout& ly, char* ws, cud
   // ------------------------------------------------ tables
   k_resolve<<<(D.P + kThreads - 1) / kThreads, kThreads, 0, st>>>(D, T);
   count_launch();
+  // ------------------------------------------------ reductions (on rs)
+  auto reductions = [&](cudaStream_t rs) -> int {
+    if (ly.need_red) {
+      if (w.total) MP_CUDA_TRY(cudaMemsetAsync(w.total, 0, 8, rs));
+      const bool lc_elem = D.lc && w.elem_mode;
+      LcHalo lh;
+      std::memset(&lh, 0, sizeof(lh));
+      if (lc_elem) lh = make_lc_halo(D, w);
+      if (def) {
+        MP_CUDA_TRY(cudaMemsetAsync(def, 0, ly.n_def * 8, rs));
+        uint64_t work = 0;
+        for (int t = 0; t < D.k; ++t) {
+          const uint64_t lo_n = std::min<uint64_t>(lc_elem ? w.width[t] : 1, D.L[t]);
+          const uint64_t hi_n = std::min<uint64_t>(lc_elem ? w.width[t] : 1, D.L[t] - lo_n);
+          work += (lc_elem ? lo_n + hi_n : 2) * (D.npoints / D.L[t]);
+        }
+        const uint64_t blocks = std::max<uint64_t>(1, std::min<uint64_t>((work + kThreads - 1) / kThreads,
+                                                                           (uint64_t)sm_count() * 8));
+        if (lc_elem) {
+          k_lc_wslabs<<<(unsigned)blocks, kThreads, 0, rs>>>(D, lh, w.face[0], w.face[1], w.face[2], w.face[3],
+                                                             w.width[0], w.width[1], w.width[2], w.width[3], def);
+          count_launch();
+        } else if (D.P <= kLcScanMax) {
+          LcRuns R;
+          std::memset(&R, 0, sizeof(R));
+          for (int t = 0; t + 1 < D.k; ++t) {
+            const bool crosses = D.lc_stride_mod[t] != 0 && w.face[t] != 0;
+            R.begin[t + 1] = R.begin[t] + (crosses ? 2 * (D.npoints / (D.L[t] * D.lc_stride[t])) : 0);
+          }
+          unsigned long long* defall = def + D.P;   // one extra word after the deficits
+          MP_CUDA_TRY(cudaMemsetAsync(defall, 0, 8, rs));
+          const uint64_t runs = R.begin[D.k - 1];
+          if (runs) {
+            const uint64_t rb = std::max<uint64_t>(1, std::min<uint64_t>((runs + kThreads - 1) / kThreads,
+                                                                         (uint64_t)sm_count() * 8));
+            k_lc_runs<<<(unsigned)rb, kThreads, 0, rs>>>(D, R, w.face[0], w.face[1], w.face[2], w.face[3], def, defall);
+            count_launch();
+          }
+          k_lc_scan<<<1, 1024, 0, rs>>>(D, w.face[D.k - 1], def, defall);
+          count_launch();
+        } else {
+          k_lc_slabs<<<(unsigned)blocks, kThreads, 0, rs>>>(D, w.face[0], w.face[1], w.face[2], w.face[3], def);
+          count_launch();
+        }
+      }
+      k_reduce<<<(D.P + kThreads - 1) / kThreads, kThreads, 0, rs>>>(
+          D, T, H, X, (const uint64_t*)def, w.face[0], w.face[1], w.face[2], w.face[3], w.hist, w.recv,
+          (unsigned long long*)w.total, lh, lc_elem ? 1 : 0);
+      count_launch();
+    }
+    return MP_OK;
+  };
+  // with ids wanted too, the counts and reductions (which read only the chain
+  // table) run on a second stream beside the tables and the id writer
+  const ForkStreams* fk = w.ids && ly.need_red ? fork_streams() : nullptr;
+  cudaStream_t rs = st;
+  if (fk) {
+    MP_CUDA_TRY(cudaEventRecord(fk->fork, st));
+    MP_CUDA_TRY(cudaStreamWaitEvent(fk->side, fk->fork, 0));
+    rs = fk->side;
+  }
+  if (H) {
+    k_counts<<<(D.Jtotal + kThreads - 1) / kThreads, kThreads, 0, rs>>>(D, H, X, w.elem_mode, w.width[0],
+                                                                         w.width[1], w.width[2], w.width[3]);
+    count_launch();
+  }
+  if (fk) {
+    int rc = reductions(rs);
+    if (rc) return rc;
+    MP_CUDA_TRY(cudaEventRecord(fk->join, rs));
+  }
   if (ly.tab_total) {
     const uint64_t blocks = std::min<uint64_t>((ly.tab_total + kThreads - 1) / kThreads, (uint64_t)sm_count() * 16);
     k_tables<<<(unsigned)blocks, kThreads, 0, st>>>(D, tabs, ly.tab_total, ctab);
-    count_launch();
-  }
-  if (H) {
-    k_counts<<<(D.Jtotal + kThreads - 1) / kThreads, kThreads, 0, st>>>(D, H, X, w.elem_mode, w.width[0],
-                                                                         w.width[1], w.width[2], w.width[3]);
     count_launch();
   }
   // ------------------------------------------------ ids
@@ -499,54 +597,11 @@ int run_launch_ws(const Plan& pl, const Want& w, const Layout& ly, char* ws, cud
     MP_CUDA_TRY(cudaGetLastError());
   }
 ids_done:
-  // ------------------------------------------------ reductions
-  if (ly.need_red) {
-    if (w.total) MP_CUDA_TRY(cudaMemsetAsync(w.total, 0, 8, st));
-    const bool lc_elem = D.lc && w.elem_mode;
-    LcHalo lh;
-    std::memset(&lh, 0, sizeof(lh));
-    if (lc_elem) lh = make_lc_halo(D, w);
-    if (def) {
-      MP_CUDA_TRY(cudaMemsetAsync(def, 0, ly.n_def * 8, st));
-      uint64_t work = 0;
-      for (int t = 0; t < D.k; ++t) {
-        const uint64_t lo_n = std::min<uint64_t>(lc_elem ? w.width[t] : 1, D.L[t]);
-        const uint64_t hi_n = std::min<uint64_t>(lc_elem ? w.width[t] : 1, D.L[t] - lo_n);
-        work += (lc_elem ? lo_n + hi_n : 2) * (D.npoints / D.L[t]);
-      }
-      const uint64_t blocks = std::max<uint64_t>(1, std::min<uint64_t>((work + kThreads - 1) / kThreads,
-                                                                         (uint64_t)sm_count() * 8));
-      if (lc_elem) {
-        k_lc_wslabs<<<(unsigned)blocks, kThreads, 0, st>>>(D, lh, w.face[0], w.face[1], w.face[2], w.face[3],
-                                                           w.width[0], w.width[1], w.width[2], w.width[3], def);
-        count_launch();
-      } else if (D.P <= kLcScanMax) {
-        LcRuns R;
-        std::memset(&R, 0, sizeof(R));
-        for (int t = 0; t + 1 < D.k; ++t) {
-          const bool crosses = D.lc_stride_mod[t] != 0 && w.face[t] != 0;
-          R.begin[t + 1] = R.begin[t] + (crosses ? 2 * (D.npoints / (D.L[t] * D.lc_stride[t])) : 0);
-        }
-        unsigned long long* defall = def + D.P;   // one extra word after the deficits
-        MP_CUDA_TRY(cudaMemsetAsync(defall, 0, 8, st));
-        const uint64_t runs = R.begin[D.k - 1];
-        if (runs) {
-          const uint64_t rb = std::max<uint64_t>(1, std::min<uint64_t>((runs + kThreads - 1) / kThreads,
-                                                                       (uint64_t)sm_count() * 8));
-          k_lc_runs<<<(unsigned)rb, kThreads, 0, st>>>(D, R, w.face[0], w.face[1], w.face[2], w.face[3], def, defall);
-          count_launch();
-        }
-        k_lc_scan<<<1, 1024, 0, st>>>(D, w.face[D.k - 1], def, defall);
-        count_launch();
-      } else {
-        k_lc_slabs<<<(unsigned)blocks, kThreads, 0, st>>>(D, w.face[0], w.face[1], w.face[2], w.face[3], def);
-        count_launch();
-      }
-    }
-    k_reduce<<<(D.P + kThreads - 1) / kThreads, kThreads, 0, st>>>(
-        D, T, H, X, (const uint64_t*)def, w.face[0], w.face[1], w.face[2], w.face[3], w.hist, w.recv,
-        (unsigned long long*)w.total, lh, lc_elem ? 1 : 0);
-    count_launch();
+  if (fk) {
+    MP_CUDA_TRY(cudaStreamWaitEvent(st, fk->join, 0));
+  } else {
+    int rc = reductions(st);
+    if (rc) return rc;
   }
   MP_CUDA_TRY(cudaGetLastError());
   return MP_OK;
