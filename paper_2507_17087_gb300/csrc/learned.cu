@@ -556,58 +556,125 @@ Pool g_pool_q, g_pool_s;   // query data; scores and selection
 
 Pool g_pool_img;   // feature tile images of the scoring kernels
 
-struct Prepared {
-  SearchSpace S;
-  QInfo Q;
-  const DeviceSpace* D = nullptr;   // the space's device copy (chain programs, factorisations, node tables)
-  const ChainProg* d_progs = nullptr;
-  const Fact* d_facts = nullptr;
-  float* d_chainfeat = nullptr;
-  uint16_t* d_fnode = nullptr;   // fibre-node table (k_fibre_nodes)
-  uint32_t* d_fdiv = nullptr;    // per factorisation: divisor indices of f0 and f0 f1
-  std::vector<unsigned long long> prim;   // primary (tiles) per factorisation
+// What the model reads of a candidate space besides the search's own copy,
+// built once per space: chain features, the fibre-node table and each
+// factorisation's divisor indices.  The 8 most recent spaces are kept.
+struct LearnedSpace {
+  std::shared_ptr<const SpaceCore> core;
+  char* mem = nullptr;
+  float* chainfeat = nullptr;
+  uint16_t* fnode = nullptr;
+  uint32_t* fdiv = nullptr;
+  uint32_t nd = 0;
+  int device = -1;
 };
+std::mutex g_lspace_mu;
+std::vector<std::shared_ptr<LearnedSpace>> g_lspaces;
 
-// Plans the query, uploads the chain programs and factorisations into the
-// query region (g_pool_q) and computes primaries, chain features and the
-// fibre-node table there.
-int prepare_query(const mp_search_query& q, Prepared& pq, cudaStream_t st) {
-  int rc = prepare(q, pq.S);
-  if (rc) return rc;
-  const size_t NC = pq.S.c->chains.size(), NF = pq.S.c->facts.size();
-  const uint32_t P = (uint32_t)q.procs;
+struct LearnedSpaceFree {
+  ~LearnedSpaceFree() {
+    for (auto& l : g_lspaces)
+      if (l->mem) cudaFree(l->mem);
+  }
+} g_lspace_free;
+
+int learned_space(const SearchSpace& S, const DeviceSpace& Dv, uint32_t P, cudaStream_t st,
+                  std::shared_ptr<LearnedSpace>* out) {
+  int device = 0;
+  MP_CUDA_TRY(cudaGetDevice(&device));
+  std::lock_guard<std::mutex> lk(g_lspace_mu);
+  for (size_t i = 0; i < g_lspaces.size(); ++i)
+    if (g_lspaces[i]->core == S.c) {
+      if (g_lspaces[i]->device != device) return MP_ENOTSUP;
+      auto hit = g_lspaces[i];
+      g_lspaces.erase(g_lspaces.begin() + (long)i);
+      g_lspaces.insert(g_lspaces.begin(), hit);
+      *out = hit;
+      return MP_OK;
+    }
+  const size_t NC = S.c->chains.size(), NF = S.c->facts.size();
   std::vector<uint32_t> D;
   for (uint32_t d = 1; d <= P; ++d)
     if (P % d == 0) D.push_back(d);
   const uint32_t nd = (uint32_t)D.size();
   std::vector<uint32_t> fdiv(NF);
   for (size_t i = 0; i < NF; ++i) {
-    const uint32_t f0 = (uint32_t)pq.S.c->facts[i][0], f01 = f0 * (uint32_t)pq.S.c->facts[i][1];
+    const uint32_t f0 = (uint32_t)S.c->facts[i][0], f01 = f0 * (uint32_t)S.c->facts[i][1];
     const uint32_t a = (uint32_t)(std::lower_bound(D.begin(), D.end(), f0) - D.begin());
     const uint32_t b = (uint32_t)(std::lower_bound(D.begin(), D.end(), f01) - D.begin());
     fdiv[i] = a | (b << 16);
   }
   const size_t W = 1 + 3 * (size_t)nd;
+  const size_t o_cf = 0, o_fn = o_cf + a256(NC * kChainFeat * 4), o_fd = o_fn + a256(NC * W * 2),
+               o_D = o_fd + a256(NF * 4), end = o_D + a256(nd * 4);
+  auto ls = std::make_shared<LearnedSpace>();
+  if (cudaMalloc(&ls->mem, end) != cudaSuccess) {
+    cudaGetLastError();
+    return MP_ENOMEM;
+  }
+  ls->core = S.c;
+  ls->chainfeat = (float*)(ls->mem + o_cf);
+  ls->fnode = (uint16_t*)(ls->mem + o_fn);
+  ls->fdiv = (uint32_t*)(ls->mem + o_fd);
+  ls->nd = nd;
+  ls->device = device;
+  uint32_t* d_D = (uint32_t*)(ls->mem + o_D);
+  bool ok = cudaMemcpyAsync(ls->fdiv, fdiv.data(), NF * 4, cudaMemcpyHostToDevice, st) == cudaSuccess &&
+            cudaMemcpyAsync(d_D, D.data(), nd * 4, cudaMemcpyHostToDevice, st) == cudaSuccess;
+  if (ok) {
+    k_chain_feats<<<(unsigned)((NC + 127) / 128), 128, 0, st>>>(Dv.progs, NC, P, ls->chainfeat);
+    k_fibre_nodes<<<(unsigned)((NC + 3) / 4), 128, 0, st>>>(Dv.progs, NC, P, d_D, nd, Dv.tab, Dv.Pp, ls->fnode);
+    count_launch(2);
+    ok = cudaGetLastError() == cudaSuccess && cudaStreamSynchronize(st) == cudaSuccess;
+  }
+  if (!ok) {
+    cudaGetLastError();
+    cudaFree(ls->mem);
+    return MP_ECUDA;
+  }
+  g_lspaces.insert(g_lspaces.begin(), ls);
+  if (g_lspaces.size() > 8) {
+    cudaFree(g_lspaces.back()->mem);   // waits for the device: no kernel still reads it
+    g_lspaces.back()->mem = nullptr;
+    g_lspaces.pop_back();
+  }
+  *out = ls;
+  return MP_OK;
+}
+
+struct Prepared {
+  SearchSpace S;
+  QInfo Q;
+  const DeviceSpace* D = nullptr;          // the space's device copy (chain programs, factorisations, node tables)
+  std::shared_ptr<LearnedSpace> L;         // the space's model inputs (chain features, fibre nodes, divisors)
+  const ChainProg* d_progs = nullptr;
+  const Fact* d_facts = nullptr;
+  const float* d_chainfeat = nullptr;
+  const uint16_t* d_fnode = nullptr;   // fibre-node table (k_fibre_nodes)
+  const uint32_t* d_fdiv = nullptr;    // per factorisation: divisor indices of f0 and f0 f1
+  std::vector<unsigned long long> prim;   // primary (tiles) per factorisation
+};
+
+// Plans the query: the space's device copies (built on its first use) and
+// the query's primaries per factorisation.
+int prepare_query(const mp_search_query& q, Prepared& pq, cudaStream_t st) {
+  int rc = prepare(q, pq.S);
+  if (rc) return rc;
+  const size_t NC = pq.S.c->chains.size(), NF = pq.S.c->facts.size();
+  const uint32_t P = (uint32_t)q.procs;
   if ((rc = device_space(*pq.S.c, st, &pq.D))) return rc;
+  if ((rc = learned_space(pq.S, *pq.D, P, st, &pq.L))) return rc;
   pq.d_progs = pq.D->progs;
   pq.d_facts = pq.D->facts;
-  const size_t o_cf = 0, o_pr = o_cf + a256(NC * kChainFeat * 4), o_fn = o_pr + a256(NF * 8),
-               o_fd = o_fn + a256(NC * W * 2), o_D = o_fd + a256(NF * 4), end = o_D + a256(nd * 4);
-  char* region = g_pool_q.get(std::max<size_t>(end, 64u << 20));
-  if (!region) return MP_ENOMEM;
-  pq.d_chainfeat = (float*)(region + o_cf);
-  pq.d_fnode = (uint16_t*)(region + o_fn);
-  pq.d_fdiv = (uint32_t*)(region + o_fd);
-  uint32_t* d_D = (uint32_t*)(region + o_D);
-  unsigned long long* d_prim = (unsigned long long*)(region + o_pr);
-  MP_CUDA_TRY(cudaMemcpyAsync(pq.d_fdiv, fdiv.data(), NF * 4, cudaMemcpyHostToDevice, st));
-  MP_CUDA_TRY(cudaMemcpyAsync(d_D, D.data(), nd * 4, cudaMemcpyHostToDevice, st));
-  k_chain_feats<<<(unsigned)((NC + 127) / 128), 128, 0, st>>>(pq.d_progs, NC, P, pq.d_chainfeat);
+  pq.d_chainfeat = pq.L->chainfeat;
+  pq.d_fnode = pq.L->fnode;
+  pq.d_fdiv = pq.L->fdiv;
+  const uint32_t nd = pq.L->nd;
+  unsigned long long* d_prim = (unsigned long long*)g_pool_q.get(std::max<size_t>(a256(NF * 8), 1u << 20));
+  if (!d_prim) return MP_ENOMEM;
   k_primaries<<<(unsigned)((NF + 127) / 128), 128, 0, st>>>(pq.d_facts, (uint32_t)NF, (uint32_t)q.M, (uint32_t)q.N,
                                                             (uint32_t)q.K, d_prim);
-  k_fibre_nodes<<<(unsigned)((NC + 3) / 4), 128, 0, st>>>(pq.d_progs, NC, P, d_D, nd, pq.D->tab, pq.D->Pp,
-                                                           pq.d_fnode);
-  count_launch(3);
+  count_launch();
   pq.prim.resize(NF);
   MP_CUDA_TRY(cudaMemcpyAsync(pq.prim.data(), d_prim, NF * 8, cudaMemcpyDeviceToHost, st));
   MP_CUDA_TRY(cudaStreamSynchronize(st));
