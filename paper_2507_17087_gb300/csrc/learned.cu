@@ -517,6 +517,13 @@ __global__ void k_topk_collect(const float* __restrict__ s, unsigned long long n
   }
 }
 
+// the scores of the first min(*n, cap) listed positions (n read on the device)
+__global__ void k_take_count(const float* __restrict__ s, const int64_t* __restrict__ idx,
+                             const unsigned* __restrict__ n, unsigned cap, float* __restrict__ out) {
+  const unsigned i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < cap && i < *n) out[i] = s[idx[i]];
+}
+
 // ------------------------------------------------------------ host side
 
 int sm_count_l() {
@@ -555,6 +562,27 @@ struct Pool {
 Pool g_pool_q, g_pool_s;   // query data; scores and selection
 
 Pool g_pool_img;   // feature tile images of the scoring kernels
+
+// Pinned host staging for the selection's small transfers (grows, never shrinks).
+struct HostPool {
+  char* p = nullptr;
+  size_t size = 0;
+  ~HostPool() {
+    if (p) cudaFreeHost(p);
+  }
+  char* get(size_t bytes) {
+    if (size >= bytes) return p;
+    if (p) cudaFreeHost(p);
+    p = nullptr;
+    size = 0;
+    if (cudaMallocHost(&p, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    size = bytes;
+    return p;
+  }
+} g_host_stage;
 
 // What the model reads of a candidate space besides the search's own copy,
 // built once per space: chain features, the fibre-node table and each
@@ -952,22 +980,37 @@ extern "C" int mp_learned_search(mp_mlp* h, const mp_search_query* query, int K,
     k_topk_collect<<<gb, 256, 0, st>>>(d_sc, ncand, d_thr, d_below, d_cnt, d_eq, d_cnt + 1, Kc, cap_eq);
     count_launch(2);
     MP_CUDA_TRY(cudaGetLastError());
-    unsigned cnt[2] = {0, 0};
-    MP_CUDA_TRY(cudaMemcpyAsync(cnt, d_cnt, 8, cudaMemcpyDeviceToHost, st));
+    // one round trip: the counts, the threshold bin's first entries with their
+    // scores and the positions below the threshold (a larger bin takes a second)
+    constexpr unsigned kEqFirst = 4096;
+    const size_t sb_cnt = 0, sb_eq = 256, sb_eqs = sb_eq + (size_t)kEqFirst * 8,
+                 sb_pos = sb_eqs + (size_t)kEqFirst * 4, sb_end = sb_pos + (size_t)Kmax * 8;
+    char* hs = g_host_stage.get(std::max<size_t>(sb_end, (size_t)Kmax * 20 + 256));
+    if (!hs) return MP_ENOMEM;
+    k_take_count<<<(kEqFirst + 255) / 256, 256, 0, st>>>(d_sc, d_eq, d_cnt + 1, std::min(kEqFirst, cap_eq), d_ye);
+    count_launch();
+    MP_CUDA_TRY(cudaMemcpyAsync(hs + sb_cnt, d_cnt, 8, cudaMemcpyDeviceToHost, st));
+    MP_CUDA_TRY(cudaMemcpyAsync(hs + sb_eq, d_eq, (size_t)std::min(kEqFirst, cap_eq) * 8, cudaMemcpyDeviceToHost, st));
+    MP_CUDA_TRY(cudaMemcpyAsync(hs + sb_eqs, d_ye, (size_t)std::min(kEqFirst, cap_eq) * 4, cudaMemcpyDeviceToHost, st));
+    MP_CUDA_TRY(cudaMemcpyAsync(hs + sb_pos, d_below, (size_t)Kc * 8, cudaMemcpyDeviceToHost, st));
     MP_CUDA_TRY(cudaStreamSynchronize(st));
+    const unsigned* cnt = (const unsigned*)(hs + sb_cnt);
     const unsigned nbelow = std::min(cnt[0], Kc), neq = std::min(cnt[1], cap_eq);
     // the threshold bin, ordered by (score, index) for a deterministic choice
     std::vector<int64_t> eq(neq);
     std::vector<float> eqs(neq);
-    if (neq) {
-      MP_CUDA_TRY(cudaMemcpyAsync(eq.data(), d_eq, (size_t)neq * 8, cudaMemcpyDeviceToHost, st));
-      k_take<<<(neq + 255) / 256, 256, 0, st>>>(d_sc, d_eq, (int)neq, d_ye);
+    const unsigned first = std::min(neq, kEqFirst);
+    std::memcpy(eq.data(), hs + sb_eq, (size_t)first * 8);
+    std::memcpy(eqs.data(), hs + sb_eqs, (size_t)first * 4);
+    pos.assign((const int64_t*)(hs + sb_pos), (const int64_t*)(hs + sb_pos) + nbelow);
+    if (neq > first) {
+      const unsigned rest = neq - first;
+      MP_CUDA_TRY(cudaMemcpyAsync(eq.data() + first, d_eq + first, (size_t)rest * 8, cudaMemcpyDeviceToHost, st));
+      k_take<<<(rest + 255) / 256, 256, 0, st>>>(d_sc, d_eq + first, (int)rest, d_ye + first);
       count_launch();
-      MP_CUDA_TRY(cudaMemcpyAsync(eqs.data(), d_ye, (size_t)neq * 4, cudaMemcpyDeviceToHost, st));
+      MP_CUDA_TRY(cudaMemcpyAsync(eqs.data() + first, d_ye + first, (size_t)rest * 4, cudaMemcpyDeviceToHost, st));
+      MP_CUDA_TRY(cudaStreamSynchronize(st));
     }
-    pos.assign(nbelow, 0);
-    if (nbelow) MP_CUDA_TRY(cudaMemcpyAsync(pos.data(), d_below, (size_t)nbelow * 8, cudaMemcpyDeviceToHost, st));
-    MP_CUDA_TRY(cudaStreamSynchronize(st));
     std::vector<uint32_t> ord(neq);
     std::iota(ord.begin(), ord.end(), 0u);
     std::sort(ord.begin(), ord.end(), [&](uint32_t a, uint32_t b) {
@@ -987,13 +1030,17 @@ extern "C" int mp_learned_search(mp_mlp* h, const mp_search_query* query, int K,
     MP_CUDA_TRY(cudaMemcpyAsync(d_sel, pos.data(), (size_t)nsel * 8, cudaMemcpyHostToDevice, st));
     k_take<<<(unsigned)((nsel + 255) / 256), 256, 0, st>>>(d_sc, d_sel, (int)nsel, d_y);
     count_launch();
-    pb.resize(nsel);
-    sb.resize(nsel);
-    yh.resize(nsel);
-    MP_CUDA_TRY(cudaMemcpyAsync(pb.data(), d_p, (size_t)nsel * 8, cudaMemcpyDeviceToHost, st));
-    MP_CUDA_TRY(cudaMemcpyAsync(sb.data(), d_s, (size_t)nsel * 8, cudaMemcpyDeviceToHost, st));
-    MP_CUDA_TRY(cudaMemcpyAsync(yh.data(), d_y, (size_t)nsel * 4, cudaMemcpyDeviceToHost, st));
-    MP_CUDA_TRY(cudaStreamSynchronize(st));
+    {
+      char* hp = g_host_stage.get((size_t)nsel * 20 + 256);
+      if (!hp) return MP_ENOMEM;
+      MP_CUDA_TRY(cudaMemcpyAsync(hp, d_p, (size_t)nsel * 8, cudaMemcpyDeviceToHost, st));
+      MP_CUDA_TRY(cudaMemcpyAsync(hp + (size_t)nsel * 8, d_s, (size_t)nsel * 8, cudaMemcpyDeviceToHost, st));
+      MP_CUDA_TRY(cudaMemcpyAsync(hp + (size_t)nsel * 16, d_y, (size_t)nsel * 4, cudaMemcpyDeviceToHost, st));
+      MP_CUDA_TRY(cudaStreamSynchronize(st));
+      pb.assign((const uint64_t*)hp, (const uint64_t*)hp + nsel);
+      sb.assign((const uint64_t*)(hp + (size_t)nsel * 8), (const uint64_t*)(hp + (size_t)nsel * 8) + nsel);
+      yh.assign((const float*)(hp + (size_t)nsel * 16), (const float*)(hp + (size_t)nsel * 16) + nsel);
+    }
     bi = 0;
     for (int64_t i = 1; i < nsel; ++i) {
       const bool less = pb[i] < pb[bi] || (pb[i] == pb[bi] && (sb[i] < sb[bi] || (sb[i] == sb[bi] && sel[i] < sel[bi])));
