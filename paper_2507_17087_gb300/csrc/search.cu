@@ -35,23 +35,64 @@ size_t align_up(size_t v) { return (v + 255) & ~size_t(255); }
 // full = 1: every candidate's secondary is scanned.  full = 0: candidates
 // whose (exact, closed-form) primary exceeds the minimum primary over all
 // factorisations cannot win the lexicographic argmin and are not scanned.
-__global__ void __launch_bounds__(256, 4) k_search(const ChainProg* __restrict__ progs, const Fact* __restrict__ facts, int nf,
+// PRE: the precounted fibre tables (full search; shared memory allows three
+// CTAs per SM, so the registers are bounded for three too).
+template <bool PRE>
+__global__ void __launch_bounds__(256, PRE ? 3 : 4) k_search(const ChainProg* __restrict__ progs, const Fact* __restrict__ facts, int nf,
                          uint32_t P, uint32_t E0, uint32_t E1, uint32_t E2, int words,
                          unsigned long long nchains, int full, unsigned long long ub,
                          const uint8_t* __restrict__ skip, const uint16_t* __restrict__ gtab, uint32_t Pp,
-                         Key* __restrict__ chain_best) {
+                         int npre, const uint32_t* __restrict__ pre_list, Key* __restrict__ chain_best) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ Key red[32];
+  __shared__ uint32_t s_pdiv[kPreMaxN], s_pm[kPreMaxN], s_poff[kPreMaxN + 1];
   uint32_t* bm = reinterpret_cast<uint32_t*>(smem_raw);
   uint16_t* tab = reinterpret_cast<uint16_t*>(smem_raw + (size_t)words * blockDim.x * 4);
+  // npre > 0: after the table, the precounted fibre counts of every divisor
+  // d = s_pdiv[k] <= kPreMaxDiv: the P / d blocks of d consecutive flat
+  // indices at s_poff[k], then the P / d residue classes modulo P / d
+  uint16_t* dtab = reinterpret_cast<uint16_t*>(smem_raw + (size_t)words * blockDim.x * 4 + (((size_t)P * 2 + 255) & ~(size_t)255));
   const uint32_t c = blockIdx.x;
   __shared__ ChainProg cp;
   if (threadIdx.x == 0) cp = progs[c];
+  for (int i = threadIdx.x; i < npre; i += blockDim.x) {
+    s_pdiv[i] = pre_list[i];
+    s_pm[i] = pre_list[npre + i];
+  }
+  for (int i = threadIdx.x; i <= npre; i += blockDim.x) s_poff[i] = pre_list[2 * npre + i];
   for (int w = 0; w < words; ++w) bm[w * blockDim.x + threadIdx.x] = 0;
   __syncthreads();
   if (gtab) load_table(gtab + (size_t)c * Pp, tab, Pp);
   else build_table(cp, tab, P);
   __syncthreads();
+  if (PRE && npre > 0) {
+    const uint32_t nitems = s_poff[npre];
+    for (uint32_t i = threadIdx.x; i < nitems; i += blockDim.x) {
+      int lo = 0, hi = npre;   // s_poff[lo] <= i < s_poff[hi]
+      while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (s_poff[mid] <= i) lo = mid;
+        else hi = mid;
+      }
+      const uint32_t d = s_pdiv[lo], m = s_pm[lo], local = i - s_poff[lo];
+      const bool blk = local < m;
+      const uint32_t base = blk ? local * d : local - m, stride = blk ? 1u : m;
+      dtab[i] = (uint16_t)fibre_distinct(tab, bm + threadIdx.x, blockDim.x, words, base, stride, d, d, d);
+    }
+    __syncthreads();
+  }
+  // the precounted table of divisor v (null when v is not precounted)
+  auto pre_of = [&](uint32_t v, bool res) -> const uint16_t* {
+    if (!PRE || npre == 0 || v > kPreMaxDiv) return nullptr;
+    int lo = 0, hi = npre;
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (s_pdiv[mid] <= v) lo = mid;
+      else hi = mid;
+    }
+    if (s_pdiv[lo] != v) return nullptr;
+    return dtab + s_poff[lo] + (res ? s_pm[lo] : 0u);
+  };
   const uint32_t E[3] = {E0, E1, E2};
   unsigned long long pmin = 0;
   if (!full) {
@@ -76,7 +117,10 @@ __global__ void __launch_bounds__(256, 4) k_search(const ChainProg* __restrict__
     k.p = primary_cost(E, f);
     if (!full && k.p > pmin) continue;   // uniform across the warp
     if (skip && skip[fr]) continue;
-    k.s = secondary_cost_warp(tab, wbm, blockDim.x, words, E, f, lane, ub);
+    // families 0 and 2 from the precounted fibres where every block holds tiles
+    const uint16_t* pre0 = E[0] >= f[0] ? pre_of(f[0], false) : nullptr;
+    const uint16_t* pre2 = E[2] >= f[2] ? pre_of(f[2], true) : nullptr;
+    k.s = secondary_cost_warp(tab, wbm, blockDim.x, words, E, f, lane, ub, pre0, pre2);
     k.idx = (unsigned long long)fr * nchains + c;
     if (key_less(k, best)) best = k;
   }
@@ -360,9 +404,33 @@ int exhaustive_search(const mp_search_query& q, mp_search_result* out, cudaStrea
   if (skip && skip->size() != NF) return MP_EINVAL;
   const DeviceSpace* D = nullptr;
   if ((rc = device_space(*S.c, st, &D))) return rc;
-  const size_t best_bytes = align_up(NC * sizeof(Key)) + align_up(sizeof(Key)) + align_up(NF);
+  // full search: the fibre counts of families 0 and 2 precounted per chain
+  // for the divisors up to kPreMaxDiv, when they fit in shared memory
+  std::vector<uint32_t> pre;
+  int npre = 0;
+  size_t smem = S.smem;
+  if (q.flags & MP_SEARCH_FULL) {
+    std::vector<uint32_t> dv, mv, ov(1, 0);
+    for (uint32_t d = 1; d <= (uint32_t)q.procs && d <= kPreMaxDiv; ++d)
+      if (q.procs % d == 0) {
+        dv.push_back(d);
+        mv.push_back((uint32_t)q.procs / d);
+        ov.push_back(ov.back() + 2 * ((uint32_t)q.procs / d));
+      }
+    const size_t need = S.smem + align_up((size_t)ov.back() * 2);
+    if ((int)dv.size() <= kPreMaxN && need <= (size_t)kSmemBudget) {
+      npre = (int)dv.size();
+      smem = need;
+      pre.insert(pre.end(), dv.begin(), dv.end());
+      pre.insert(pre.end(), mv.begin(), mv.end());
+      pre.insert(pre.end(), ov.begin(), ov.end());
+    }
+  }
+  const size_t best_bytes = align_up(NC * sizeof(Key)) + align_up(sizeof(Key)) + align_up(NF) + align_up(pre.size() * 4 + 4);
   char* rest = (char*)workspace(best_bytes, 2);
   if (!rest) return MP_ENOMEM;
+  uint32_t* d_pre = (uint32_t*)(rest + align_up(NC * sizeof(Key)) + align_up(sizeof(Key)) + align_up(NF));
+  if (npre) MP_CUDA_TRY(cudaMemcpyAsync(d_pre, pre.data(), pre.size() * 4, cudaMemcpyHostToDevice, st));
   Key* chain_best = (Key*)rest;
   Key* d_out = (Key*)(rest + align_up(NC * sizeof(Key)));
   uint8_t* d_skip = nullptr;
@@ -370,14 +438,16 @@ int exhaustive_search(const mp_search_query& q, mp_search_result* out, cudaStrea
     d_skip = (uint8_t*)(rest + align_up(NC * sizeof(Key)) + align_up(sizeof(Key)));
     MP_CUDA_TRY(cudaMemcpyAsync(d_skip, skip->data(), NF, cudaMemcpyHostToDevice, st));
   }
-  if (S.smem > 48 * 1024)
-    MP_CUDA_TRY(cudaFuncSetAttribute(k_search, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S.smem));
-  k_search<<<(unsigned)NC, S.threads, S.smem, st>>>(D->progs, D->facts, (int)S.c->facts.size(), (uint32_t)q.procs,
+  const void* kern = npre ? (const void*)k_search<true> : (const void*)k_search<false>;
+  if (smem > 48 * 1024)
+    MP_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  auto launch = npre ? k_search<true> : k_search<false>;
+  launch<<<(unsigned)NC, S.threads, smem, st>>>(D->progs, D->facts, (int)S.c->facts.size(), (uint32_t)q.procs,
                                                     (uint32_t)q.M, (uint32_t)q.N, (uint32_t)q.K, S.words, NC,
                                                     (q.flags & MP_SEARCH_FULL) ? 1 : 0,
                                                     (q.flags & MP_SEARCH_FULL) ? ~0ull : ub_secondary,
                                                     (q.flags & MP_SEARCH_FULL) ? nullptr : d_skip, D->tab, D->Pp,
-                                                    chain_best);
+                                                    npre, d_pre, chain_best);
   count_launch();
   k_search_final<<<1, 1024, 0, st>>>(chain_best, NC, d_out);
   count_launch();

@@ -14,6 +14,8 @@ constexpr int kMaxChainPrims = 12;
 
 constexpr int kSearchMaxProcs = 16384;
 constexpr int kSmemBudget = 200 * 1024;
+constexpr uint32_t kPreMaxDiv = 256;   // full search: fibre counts precounted for divisors up to this
+constexpr int kPreMaxN = 64;           // and for at most this many divisors
 
 struct ChainProg {
   int32_t nprim;
@@ -214,10 +216,16 @@ __device__ __forceinline__ unsigned long long warp_sum(unsigned long long v) {
 // Every lane returns the total.
 // ub: once the running total exceeds it the remaining families are skipped
 // and ~0 is returned (the caller only needs costs up to ub).
+// pre0 / pre2 (may be null): the distinct-node counts of family 0's fibres
+// (the blocks of f0 consecutive flat indices, by block) and of family 2's
+// (the residue classes modulo P / f2, by residue), counted once per chain
+// for every divisor and looked up here instead of scanned.
 __device__ __forceinline__ unsigned long long secondary_cost_warp(const uint16_t* __restrict__ tab, uint32_t* bm,
                                                                   int stride, int words, const uint32_t E[3],
                                                                   const uint32_t f[3], int lane,
-                                                                  unsigned long long ub = ~0ull) {
+                                                                  unsigned long long ub = ~0ull,
+                                                                  const uint16_t* __restrict__ pre0 = nullptr,
+                                                                  const uint16_t* __restrict__ pre2 = nullptr) {
   const uint32_t fstride[3] = {1u, f[0], f[0] * f[1]};
   uint32_t n[3];
   for (int t = 0; t < 3; ++t) n[t] = E[t] < f[t] ? E[t] : f[t];
@@ -227,7 +235,8 @@ __device__ __forceinline__ unsigned long long secondary_cost_warp(const uint16_t
     const int u = v == 0 ? 1 : 0;
     const int w = v == 2 ? 1 : 2;
     const uint32_t nfib = n[u] * n[w];
-    if (nfib >= 32) {
+    const uint16_t* pre = v == 0 ? pre0 : (v == 2 ? pre2 : nullptr);
+    if (nfib >= 32 || pre) {
       const uint32_t chunk = (nfib + 31) / 32;
       const uint32_t fb0 = lane * chunk, fb1 = min(nfib, fb0 + chunk);
       unsigned long long part = 0;
@@ -242,7 +251,8 @@ __device__ __forceinline__ unsigned long long secondary_cost_warp(const uint16_t
           const uint32_t rep_u = itu.rep;
           const uint32_t wt_u = itu.step();
           const uint32_t base = rep_u * fstride[u] + rep_w * fstride[w];
-          const uint32_t D = fibre_distinct(tab, bm + lane, stride, words, base, fstride[v], E[v], f[v], n[v]);
+          const uint32_t D = pre ? (uint32_t)pre[v == 0 ? rep_u + rep_w * f[1] : base]
+                                 : fibre_distinct(tab, bm + lane, stride, words, base, fstride[v], E[v], f[v], n[v]);
           part += (unsigned long long)wt_u * wt_w * (D - 1);
           if (++iu == n[u]) {
             iu = 0;
