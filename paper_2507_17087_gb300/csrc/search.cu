@@ -120,7 +120,7 @@ __global__ void __launch_bounds__(256, PRE ? 3 : 4) k_search(const ChainProg* __
     // families 0 and 2 from the precounted fibres where every block holds tiles
     const uint16_t* pre0 = E[0] >= f[0] ? pre_of(f[0], false) : nullptr;
     const uint16_t* pre2 = E[2] >= f[2] ? pre_of(f[2], true) : nullptr;
-    k.s = secondary_cost_warp(tab, wbm, blockDim.x, words, E, f, lane, ub, pre0, pre2);
+    k.s = secondary_cost_warp<!PRE>(tab, wbm, blockDim.x, words, E, f, lane, ub, pre0, pre2);
     k.idx = (unsigned long long)fr * nchains + c;
     if (key_less(k, best)) best = k;
   }

@@ -220,6 +220,9 @@ __device__ __forceinline__ unsigned long long warp_sum(unsigned long long v) {
 // (the blocks of f0 consecutive flat indices, by block) and of family 2's
 // (the residue classes modulo P / f2, by residue), counted once per chain
 // for every divisor and looked up here instead of scanned.
+// UNROLL: the three families unrolled (their extents in registers rather
+// than local memory); faster without the precounted tables, slower with them.
+template <bool UNROLL = false>
 __device__ __forceinline__ unsigned long long secondary_cost_warp(const uint16_t* __restrict__ tab, uint32_t* bm,
                                                                   int stride, int words, const uint32_t E[3],
                                                                   const uint32_t f[3], int lane,
@@ -230,6 +233,7 @@ __device__ __forceinline__ unsigned long long secondary_cost_warp(const uint16_t
   uint32_t n[3];
   for (int t = 0; t < 3; ++t) n[t] = E[t] < f[t] ? E[t] : f[t];
   unsigned long long sec = 0;
+#pragma unroll(UNROLL ? 3 : 1)
   for (int v = 0; v < 3; ++v) {
     if (n[v] <= 1) continue;
     const int u = v == 0 ? 1 : 0;
