@@ -504,10 +504,21 @@ int run_launch_ws(const Plan& pl, const Want& w, const Layout& ly, char* ws, cud
                                                                          w.width[1], w.width[2], w.width[3]);
     count_launch();
   }
+  // the caller's stream waits for the second stream on every way out of
+  // this function, so that a capture on it never ends with a fork open
+  struct Join {
+    const ForkStreams* fk;
+    cudaStream_t st;
+    bool armed;
+    ~Join() {
+      if (armed) cudaStreamWaitEvent(st, fk->join, 0);
+    }
+  } join{fk, st, false};
   if (fk) {
-    int rc = reductions(rs);
+    const int rc = reductions(rs);
+    join.armed = cudaEventRecord(fk->join, rs) == cudaSuccess;
     if (rc) return rc;
-    MP_CUDA_TRY(cudaEventRecord(fk->join, rs));
+    if (!join.armed) return MP_ECUDA;
   }
   if (ly.tab_total) {
     const uint64_t blocks = std::min<uint64_t>((ly.tab_total + kThreads - 1) / kThreads, (uint64_t)sm_count() * 16);
@@ -598,6 +609,7 @@ int run_launch_ws(const Plan& pl, const Want& w, const Layout& ly, char* ws, cud
   }
 ids_done:
   if (fk) {
+    join.armed = false;
     MP_CUDA_TRY(cudaStreamWaitEvent(st, fk->join, 0));
   } else {
     int rc = reductions(st);
