@@ -252,3 +252,51 @@ def test_linear_cyclic_deficits_in_closed_form(L, machine):
     chain = N.chain_from_draws(*machine, [rng.next() for _ in range(3)])
     face = [3 + t for t in range(len(L))]
     check_against_oracle(L, machine, chain, ("linear_cyclic",), face)
+
+
+@pytest.mark.parametrize("kind", ["block", "linear_cyclic"])
+def test_map_launch_captured_in_a_cuda_graph(kind):
+    # the call's kernels run on two streams (the reductions beside the id
+    # writer) and join before the call's work ends: captured into a caller's
+    # CUDA graph and replayed, it gives what the eager call gives
+    L, machine = (96, 40, 37), (6, 4)
+    cfg = W.scaled_launch(L, machine, kind, 77)
+    chain = N.chain_from_draws(*machine, cfg["draws"])
+    P = machine[0] * machine[1]
+    face = (8, 16, 4)
+
+    def outputs():
+        return (torch.full((math.prod(L),), -3, dtype=torch.int32, device="cuda"),
+                torch.full((P,), -3, dtype=torch.int64, device="cuda"),
+                torch.full((1,), -3, dtype=torch.int64, device="cuda"),
+                torch.full((P,), -3, dtype=torch.int64, device="cuda"))
+
+    want = outputs()
+    N.map_launch(L, machine, chain, cfg["dist"], ids=want[0], hist=want[1], face_bytes=face, total=want[2],
+                 recv=want[3])
+    torch.cuda.synchronize()
+    got = outputs()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):   # warm on the capture stream (workspace, second stream)
+        N.map_launch(L, machine, chain, cfg["dist"], ids=got[0], hist=got[1], face_bytes=face, total=got[2],
+                     recv=got[3], stream=s.cuda_stream)
+    torch.cuda.synchronize()
+    for t in got:
+        t.fill_(-3)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        N.map_launch(L, machine, chain, cfg["dist"], ids=got[0], hist=got[1], face_bytes=face, total=got[2],
+                     recv=got[3], stream=s.cuda_stream)
+    for t in got:
+        t.fill_(-3)
+    torch.cuda.synchronize()
+    g.replay()
+    torch.cuda.synchronize()
+    for a, b in zip(want, got):
+        assert torch.equal(a, b)
+    # and the oracle agrees with the eager call
+    ref = O.Launch(L, machine, chain, cfg["dist"])
+    rids, rhist = ref.map_points(threads=8)
+    assert np.array_equal(want[0].cpu().numpy(), rids)
+    assert np.array_equal(want[1].cpu().numpy().astype(np.uint64), rhist)
