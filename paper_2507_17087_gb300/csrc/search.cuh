@@ -170,38 +170,6 @@ __device__ __forceinline__ uint32_t fibre_distinct(const uint16_t* __restrict__ 
   return D;
 }
 
-// Secondary cost (tiles) of factorisation f for the chain tabulated in tab.
-__device__ __forceinline__ unsigned long long secondary_cost(const uint16_t* __restrict__ tab, uint32_t* bm, int nthr, int words,
-                                             const uint32_t E[3], const uint32_t f[3]) {
-  const uint32_t stride[3] = {1u, f[0], f[0] * f[1]};
-  uint32_t n[3];
-  for (int t = 0; t < 3; ++t) n[t] = E[t] < f[t] ? E[t] : f[t];
-  unsigned long long sec = 0;
-  for (int v = 0; v < 3; ++v) {
-    if (n[v] <= 1) continue;   // one block along the fibre: one owner
-    const int u = v == 0 ? 1 : 0;
-    const int w = v == 2 ? 1 : 2;
-    BlockIter iw;
-    iw.init(E[w], f[w]);
-    for (uint32_t a = 0; a < n[w]; ++a) {
-      const uint32_t rep_w = iw.rep;
-      const uint32_t wt_w = iw.step();
-      BlockIter iu;
-      iu.init(E[u], f[u]);
-      unsigned long long acc = 0;
-      for (uint32_t c = 0; c < n[u]; ++c) {
-        const uint32_t rep_u = iu.rep;
-        const uint32_t wt_u = iu.step();
-        const uint32_t base = rep_u * stride[u] + rep_w * stride[w];
-        const uint32_t D = fibre_distinct(tab, bm, nthr, words, base, stride[v], E[v], f[v], n[v]);
-        acc += (unsigned long long)wt_u * (D - 1);
-      }
-      sec += (unsigned long long)wt_w * acc;
-    }
-  }
-  return sec;
-}
-
 __device__ __forceinline__ unsigned long long warp_sum(unsigned long long v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
   return v;
