@@ -520,7 +520,7 @@ int enqueue(mp_batch& b, int32_t* ids, uint64_t* hist, uint64_t* halo, uint64_t*
 
 // Times the persistent id writer at a few tile sizes and keeps the fastest.
 int autotune(mp_batch& b, int32_t* ids, cudaStream_t st) {
-  const uint32_t cand[] = {2048, 8192, 32768};
+  const uint32_t cand[] = {8192, 32768, 65536, 131072};
   float best_ms = 1e30f;
   uint32_t best = cand[1];
   cudaEvent_t e0, e1;
