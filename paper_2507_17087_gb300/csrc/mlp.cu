@@ -37,7 +37,7 @@ __device__ __forceinline__ void stage_rows(uint8_t* dst, const __nv_bfloat16* __
 template <int NT>
 __global__ void __launch_bounds__(128) k_gemm_tn(const __nv_bfloat16* __restrict__ A,
                                                  const __nv_bfloat16* __restrict__ B, float* __restrict__ C,
-                                                 int M, int N, int K, int* __restrict__ status) {
+                                                 int M, int N, int K, int kcs, int* __restrict__ status) {
   extern __shared__ uint8_t smem_raw[];
   __shared__ uint64_t bar[2];
   __shared__ uint32_t tmem_slot;
@@ -63,10 +63,12 @@ __global__ void __launch_bounds__(128) k_gemm_tn(const __nv_bfloat16* __restrict
   const uint32_t tmem = tmem_slot;
   constexpr uint32_t idesc = tc::idesc_bf16(128, NT);
   bool ok = true;
-  const int nk = K / 64;
-  for (int kc = 0; kc < nk; ++kc) {
-    const int b = kc & 1;
-    if (kc >= 2) ok = ok && tc::mbar_wait(&bar[b], ((kc >> 1) - 1) & 1, kWaitLimit);
+  // split K: this CTA takes the 64-wide chunks [kc0, kc0 + n) (kcs per split)
+  const int nk_all = K / 64, kc0 = blockIdx.z * kcs;
+  const int nk = min(kcs, nk_all - kc0);
+  for (int j = 0; j < nk; ++j) {
+    const int b = j & 1, kc = kc0 + j;
+    if (j >= 2) ok = ok && tc::mbar_wait(&bar[b], ((j >> 1) - 1) & 1, kWaitLimit);
     stage_rows(bufA[b], A + (size_t)m0 * K, 128, K, kc * 64);
     stage_rows(bufB[b], B + (size_t)n0 * K, NT, K, kc * 64);
     tc::fence_proxy_async();
@@ -77,7 +79,7 @@ __global__ void __launch_bounds__(128) k_gemm_tn(const __nv_bfloat16* __restrict
 #pragma unroll
       for (int kk = 0; kk < 4; ++kk)
         tc::mma_bf16(tmem, tc::sdesc_sw128(a0 + kk * 32), tc::sdesc_sw128(b0 + kk * 32), idesc,
-                     (kc | kk) != 0);
+                     (j | kk) != 0);
       tc::mma_commit(&bar[b]);
     }
   }
@@ -93,11 +95,17 @@ __global__ void __launch_bounds__(128) k_gemm_tn(const __nv_bfloat16* __restrict
       tc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + c * 32, r);
       tc::tmem_ld_wait();
       float* dst = C + (size_t)row * N + n0 + c * 32;
+      if (gridDim.z > 1) {
+        // partial sums of the splits meet in C (zeroed before the launch)
 #pragma unroll
-      for (int j = 0; j < 32; j += 4)
-        *reinterpret_cast<float4*>(dst + j) =
-            make_float4(__uint_as_float(r[j]), __uint_as_float(r[j + 1]), __uint_as_float(r[j + 2]),
-                        __uint_as_float(r[j + 3]));
+        for (int j = 0; j < 32; ++j) atomicAdd(dst + j, __uint_as_float(r[j]));
+      } else {
+#pragma unroll
+        for (int j = 0; j < 32; j += 4)
+          *reinterpret_cast<float4*>(dst + j) =
+              make_float4(__uint_as_float(r[j]), __uint_as_float(r[j + 1]), __uint_as_float(r[j + 2]),
+                          __uint_as_float(r[j + 3]));
+      }
     }
   } else if (threadIdx.x == 0) {
     atomicExch(status, MP_ETIMEOUT);
@@ -114,8 +122,16 @@ int launch_gemm(const __nv_bfloat16* A, const __nv_bfloat16* B, float* C, int M,
                 cudaStream_t st) {
   const size_t sm = gemm_smem(NT);
   MP_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tn<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-  dim3 grid(M / 128, N / NT);
-  k_gemm_tn<NT><<<grid, 128, sm, st>>>(A, B, C, M, N, K, status);
+  // few output tiles over a long K (the weight gradients: K = the batch):
+  // split K over more CTAs, at least 4 chunks each, and add up in C
+  const int tiles = (M / 128) * (N / NT), nk = K / 64;
+  int splits = 1;
+  if (tiles < 64 && nk >= 8) splits = std::min(nk / 4, std::max(1, 128 / tiles));
+  const int kcs = (nk + splits - 1) / splits;
+  splits = (nk + kcs - 1) / kcs;
+  if (splits > 1) MP_CUDA_TRY(cudaMemsetAsync(C, 0, (size_t)M * N * sizeof(float), st));
+  dim3 grid(M / 128, N / NT, splits);
+  k_gemm_tn<NT><<<grid, 128, sm, st>>>(A, B, C, M, N, K, kcs, status);
   count_launch();
   MP_CUDA_TRY(cudaGetLastError());
   return MP_OK;
