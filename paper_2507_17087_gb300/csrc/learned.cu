@@ -255,20 +255,22 @@ __device__ __forceinline__ void epilogue_block(const uint32_t (&r)[32], int c, i
   }
 }
 
+// Column blocks [c0, c1) of 32 (of the tile's eight) of the rows this warp
+// reads from tensor memory.
 __device__ __forceinline__ void epilogue_rows(uint32_t tmem, uint32_t col0, const float* __restrict__ bias,
-                                              uint8_t* H) {
+                                              uint8_t* H, int c0 = 0, int c1 = 8) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int row = (warp & 3) * 32 + lane;
   const uint32_t t0 = tmem + ((uint32_t)((warp & 3) * 32) << 16) + col0;
   uint32_t ra[32], rb[32];
-  tc::tmem_ld32(t0, ra);
+  tc::tmem_ld32(t0 + c0 * 32, ra);
   tc::tmem_ld_wait();
 #pragma unroll 1
-  for (int c = 0; c < 8; c += 2) {
+  for (int c = c0; c < c1; c += 2) {
     tc::tmem_ld32(t0 + (c + 1) * 32, rb);
     epilogue_block(ra, c, row, bias, H);
     tc::tmem_ld_wait();
-    if (c + 2 < 8) tc::tmem_ld32(t0 + (c + 2) * 32, ra);
+    if (c + 2 < c1) tc::tmem_ld32(t0 + (c + 2) * 32, ra);
     epilogue_block(rb, c + 1, row, bias, H);
     tc::tmem_ld_wait();
   }
@@ -277,20 +279,20 @@ __device__ __forceinline__ void epilogue_rows(uint32_t tmem, uint32_t col0, cons
 // Output layer of one tile's row: relu(Z3 + b3) . w4 over 256 columns, the
 // loads pipelined as in epilogue_rows.
 __device__ __forceinline__ float output_row(uint32_t tmem, uint32_t col0, const float* __restrict__ b3,
-                                           const float* __restrict__ w4) {
+                                           const float* __restrict__ w4, int c0 = 0, int c1 = 8) {
   const int warp = threadIdx.x >> 5;
   const uint32_t t0 = tmem + ((uint32_t)((warp & 3) * 32) << 16) + col0;
   uint32_t ra[32], rb[32];
   float acc = 0.f;
-  tc::tmem_ld32(t0, ra);
+  tc::tmem_ld32(t0 + c0 * 32, ra);
   tc::tmem_ld_wait();
 #pragma unroll 1
-  for (int c = 0; c < 8; c += 2) {
+  for (int c = c0; c < c1; c += 2) {
     tc::tmem_ld32(t0 + (c + 1) * 32, rb);
 #pragma unroll
     for (int q = 0; q < 32; ++q) acc += fmaxf(__uint_as_float(ra[q]) + b3[c * 32 + q], 0.f) * w4[c * 32 + q];
     tc::tmem_ld_wait();
-    if (c + 2 < 8) tc::tmem_ld32(t0 + (c + 2) * 32, ra);
+    if (c + 2 < c1) tc::tmem_ld32(t0 + (c + 2) * 32, ra);
 #pragma unroll
     for (int q = 0; q < 32; ++q)
       acc += fmaxf(__uint_as_float(rb[q]) + b3[(c + 1) * 32 + q], 0.f) * w4[(c + 1) * 32 + q];
@@ -301,7 +303,11 @@ __device__ __forceinline__ float output_row(uint32_t tmem, uint32_t col0, const 
 
 constexpr size_t kMlpSmem = 2 * 65536 + 2 * mlpk::kWChunkBytes + 1024;
 
-__global__ void __launch_bounds__(256, 1) k_mlp_img(const uint8_t* __restrict__ img, uint32_t ntiles,
+// 16 warps: warp w serves tile (w >> 2) & 1, TMEM lanes 32 (w & 3) .. + 31 and
+// column blocks 4 (w >> 3) .. + 3 of the epilogues.
+constexpr int kMlpThreads = 512;
+
+__global__ void __launch_bounds__(kMlpThreads, 1) k_mlp_img(const uint8_t* __restrict__ img, uint32_t ntiles,
                                                     const uint8_t* __restrict__ Wimg, const float* __restrict__ P,
                                                     unsigned long long n, float* __restrict__ scores,
                                                     int* __restrict__ status) {
@@ -313,6 +319,7 @@ __global__ void __launch_bounds__(256, 1) k_mlp_img(const uint8_t* __restrict__ 
   __shared__ uint32_t tmem_slot;
   __shared__ int s_fail;
   __shared__ float sb[4][256];   // b1, b2, b3, w4
+  __shared__ float s_part[2][128];   // the output dot product's second half, per tile row
   uint8_t* base = smem_raw + ((1024 - (tc::smem_u32(smem_raw) & 1023)) & 1023);
   uint8_t* H[2] = {base, base + 65536};                                 // two tiles x four atoms
   uint8_t* Wb[2] = {base + 131072, base + 131072 + mlpk::kWChunkBytes};  // weight chunk buffers
@@ -428,17 +435,26 @@ __global__ void __launch_bounds__(256, 1) k_mlp_img(const uint8_t* __restrict__ 
       if (!ok) break;
       tc::fence_after_sync();
       if (threadIdx.x == 0) done = G + 1;
-      const uint32_t t = (uint32_t)warp >> 2;   // the tile this warp's epilogue serves
+      const uint32_t t = ((uint32_t)warp >> 2) & 1;   // the tile this warp's epilogue serves
+      const int hc = warp >> 3;                        // and the half of its columns
       if (j != 8) {
         // hidden layer 1 or 2 done: its activations become the next A operand
-        if (t < nt) epilogue_rows(tmem, t * 256, sb[j == 0 ? 0 : 1], H[t]);
+        if (t < nt) epilogue_rows(tmem, t * 256, sb[j == 0 ? 0 : 1], H[t], 4 * hc, 4 * hc + 4);
         tc::fence_proxy_async();
-      } else if (t < nt) {
-        // layer 3 and the output dot product
+      } else {
+        // layer 3 and the output dot product, each half of the columns by
+        // its own warp, added through shared memory
         const int row = (warp & 3) * 32 + lane;
-        const float acc = output_row(tmem, t * 256, sb[2], sb[3]);
-        const unsigned long long out = (unsigned long long)(tA + t) * 128 + row;
-        if (out < n) scores[out] = acc + b4;
+        float acc = 0.f;
+        if (t < nt) {
+          acc = output_row(tmem, t * 256, sb[2], sb[3], 4 * hc, 4 * hc + 4);
+          if (hc == 1) s_part[t][row] = acc;
+        }
+        __syncthreads();
+        if (t < nt && hc == 0) {
+          const unsigned long long out = (unsigned long long)(tA + t) * 128 + row;
+          if (out < n) scores[out] = acc + s_part[t][row] + b4;
+        }
       }
       tc::fence_before_sync();
       __syncthreads();
@@ -753,7 +769,7 @@ int score_candidates(mp_mlp* h, const Prepared& pq, const uint32_t* d_fl, uint64
     k_feat_img<<<ntiles, 128, 0, st>>>(pq.Q, pq.d_fnode, pq.d_fdiv, pq.d_facts, pq.d_chainfeat, d_fl, c0, n,
                                        img);
     const unsigned grid = (unsigned)std::min<uint64_t>((ntiles + 1) / 2, (uint64_t)sm_count_l());
-    k_mlp_img<<<grid, 256, kMlpSmem, st>>>(img, ntiles, h->Wimg, h->P, n, d_sc + c0, h->status);
+    k_mlp_img<<<grid, kMlpThreads, kMlpSmem, st>>>(img, ntiles, h->Wimg, h->P, n, d_sc + c0, h->status);
     count_launch(2);
     MP_CUDA_TRY(cudaGetLastError());
   }
