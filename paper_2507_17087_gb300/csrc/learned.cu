@@ -6,12 +6,12 @@
 //              along each final dimension)
 //   scoring    k_feat_img writes the candidates' features as swizzled BF16
 //              operand tiles (full occupancy hides the feature arithmetic's
-//              latency); k_mlp_img, one persistent CTA of 256 threads per
+//              latency); k_mlp_img, one persistent CTA of 512 threads per
 //              SM, bulk-copies two tiles and the nine weight chunk images
 //              (double-buffered) into shared memory and runs the three
 //              hidden layers as tcgen05 MMAs with FP32 accumulators in 512
-//              TMEM columns; warps 0-3 and 4-7 run the epilogues of the two
-//              tiles and the output dot product
+//              TMEM columns; its 16 warps run the epilogues (four per tile
+//              and half of its columns) and the output dot product
 //   top-K      65536-bin histogram of the order-preserving score keys, a
 //              threshold bin, and a compaction of the candidates at or below
 //   exact      the top-K are re-evaluated by the exact cost kernel; the
@@ -198,7 +198,8 @@ __global__ void k_features_idx(const __grid_constant__ QInfo Q, const uint16_t* 
 // copies them and the nine 32 KB weight chunk images into shared memory
 // (weights double-buffered, the next chunk in flight while the current
 // chunk's MMAs run), accumulates both tiles in 512 TMEM columns, and runs the
-// epilogues with warps 0-3 on the first tile and warps 4-7 on the second.
+// epilogues with warps 0-3 and 8-11 on the first tile (columns 0-127 and
+// 128-255), warps 4-7 and 12-15 on the second.
 
 constexpr uint32_t kTileBytes = 128 * 128;   // 128 rows x 64 BF16
 
