@@ -13,7 +13,8 @@
 // and owner(x) != owner(y) iff F(x) != F(y).
 // Kernels:
 //   k_resolve   T[F] for F < P (Fig. 4 inverses, last to first)        (a3)
-//   k_tables    c_t(x_t) for every coordinate of the tabled dimensions  (a2)
+//   k_prep      T and c_t(x_t) for every coordinate of the tabled
+//               dimensions in one launch (when ids want the tables) (a2-a3)
 //   k_ids       ids[lin] = T[base(row) + c_last(x_last)], 16-byte
 //               stores, one contiguous range per warp               (a1-a3)
 //   k_counts    per-dimension counts in closed form: H_t[j] points whose
@@ -37,17 +38,26 @@ __global__ void __launch_bounds__(kThreads) k_resolve(const __grid_constant__ Ma
   if (F < D.P) T[F] = resolve_F(D, D.prim, D.nprim, F);
 }
 
-__global__ void __launch_bounds__(kThreads) k_tables(const __grid_constant__ MapDesc D,
-                                                     const __grid_constant__ Tabs tabs, uint64_t total,
-                                                     uint32_t* __restrict__ ctab) {
+// The chain table and the c_t tables in one launch: flat final index e < P
+// resolves the chain, the rest are table entries (c_t(x) for every
+// coordinate x of the tabled dimensions).
+__global__ void __launch_bounds__(kThreads) k_prep(const __grid_constant__ MapDesc D,
+                                                   const __grid_constant__ Tabs tabs, uint64_t tab_total,
+                                                   uint32_t* __restrict__ T, uint32_t* __restrict__ ctab) {
+  const uint64_t total = (uint64_t)D.P + tab_total;
   for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
        e += (uint64_t)gridDim.x * blockDim.x) {
+    if (e < D.P) {
+      T[e] = resolve_F(D, D.prim, D.nprim, (uint32_t)e);
+      continue;
+    }
+    const uint64_t r = e - D.P;
     int t = -1;
     for (int u = 0; u < D.k; ++u)
-      if (tabs.has[u] && e >= tabs.off[u]) t = u;
+      if (tabs.has[u] && r >= tabs.off[u]) t = u;
     if (t < 0) continue;
-    const uint64_t x = e - tabs.off[t];
-    if (x < D.L[t]) ctab[e] = contrib(D, t, x);
+    const uint64_t x = r - tabs.off[t];
+    if (x < D.L[t]) ctab[r] = contrib(D, t, x);
   }
 }
 
@@ -439,7 +449,13 @@ int run_launch_ws(const Plan& pl, const Want& w, const Layout& ly, char* ws, cud
   unsigned long long* def = ly.n_def ? (unsigned long long*)(ws + ly.o_def) : nullptr;
 
   // ------------------------------------------------ tables
-  k_resolve<<<(D.P + kThreads - 1) / kThreads, kThreads, 0, st>>>(D, T);
+  if (ly.tab_total) {
+    const uint64_t work = (uint64_t)D.P + ly.tab_total;
+    const uint64_t blocks = std::min<uint64_t>((work + kThreads - 1) / kThreads, (uint64_t)sm_count() * 16);
+    k_prep<<<(unsigned)blocks, kThreads, 0, st>>>(D, tabs, ly.tab_total, T, ctab);
+  } else {
+    k_resolve<<<(D.P + kThreads - 1) / kThreads, kThreads, 0, st>>>(D, T);
+  }
   count_launch();
   // ------------------------------------------------ reductions (on rs)
   auto reductions = [&](cudaStream_t rs) -> int {
@@ -522,11 +538,6 @@ int run_launch_ws(const Plan& pl, const Want& w, const Layout& ly, char* ws, cud
     join.armed = cudaEventRecord(fk->join, rs) == cudaSuccess;
     if (rc) return rc;
     if (!join.armed) return MP_ECUDA;
-  }
-  if (ly.tab_total) {
-    const uint64_t blocks = std::min<uint64_t>((ly.tab_total + kThreads - 1) / kThreads, (uint64_t)sm_count() * 16);
-    k_tables<<<(unsigned)blocks, kThreads, 0, st>>>(D, tabs, ly.tab_total, ctab);
-    count_launch();
   }
   // ------------------------------------------------ ids
   if (w.ids) {
