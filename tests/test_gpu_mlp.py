@@ -16,7 +16,9 @@ pytestmark = pytest.mark.gpu
 
 
 @pytest.mark.parametrize("M,N_,K", [(128, 64, 64), (128, 256, 64), (256, 256, 256), (384, 128, 192),
-                                    (1024, 256, 4096), (128, 64, 1024)])
+                                    (1024, 256, 4096), (128, 64, 1024),
+                                    # K split over CTAs (few output tiles, long K), unevenly for K = 576
+                                    (256, 256, 4096), (256, 64, 4096), (128, 128, 576)])
 def test_gemm_bf16_against_float64(M, N_, K):
     g = torch.Generator(device="cpu").manual_seed(M * 7 + N_ * 3 + K)
     A = torch.randn(M, K, generator=g).to(torch.bfloat16).cuda()
