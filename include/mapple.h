@@ -26,6 +26,12 @@
  *    demand and is reused by later calls; it is freed at process exit.  Calls
  *    that run concurrently on different streams of one device must be
  *    serialised by the caller (the workspace is shared).
+ *  - A call that computes ids together with histograms or volumes runs the
+ *    reductions on a second stream (one per host thread and device, created
+ *    on first use) forked from `stream` after the chain table is built and
+ *    joined back onto `stream` before the call's work ends, on every return
+ *    path: the call stays ordered on `stream` and can be captured into a
+ *    CUDA graph on it (allocate the workspace by one call before capturing).
  *  - Processor ids are node-major: id = node * procs_per_node + proc, where
  *    (node, proc) is the index of Machine(GPU) = (nodes, procs_per_node)
  *    (Sec. 3.2, Fig. 3).
@@ -353,8 +359,11 @@ int mp_batch_info(const mp_batch* batch, uint64_t* total_ids, uint64_t* total_pr
  * query.  The kernels are captured into a CUDA graph on first use (and again
  * when the output pointers change) and replayed.  flags: MP_BATCH_AUTOTUNE
  * first times the persistent id writer at several tile sizes and keeps the
- * fastest; MP_BATCH_NO_GRAPH launches the kernels directly.  Asynchronous.
- * Runs of one batch must not overlap on the GPU (they share its pools). */
+ * fastest (tiles of 8,192 to 131,072 four-point groups); MP_BATCH_NO_GRAPH
+ * launches the kernels directly.  With ids and reductions both wanted, the
+ * reductions run on the batch's own second stream beside the id writer and
+ * join back onto `stream`.  Asynchronous.  Runs of one batch must not overlap
+ * on the GPU (they share its pools). */
 #define MP_BATCH_AUTOTUNE 1
 #define MP_BATCH_NO_GRAPH 2
 int mp_batch_run(mp_batch* batch, int32_t* ids, uint64_t* hist, uint64_t* halo, uint64_t* recv, int flags,
