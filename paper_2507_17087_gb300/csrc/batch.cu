@@ -60,10 +60,11 @@ struct QDesc : MapCore {
 };
 
 // the fused table's first dimension and length (0 when rows have no table)
-__host__ __device__ inline int fused_first(const QDesc& Q) { return Q.rsrc == R_TAB2 ? Q.fuse_m + 1 : Q.fuse_m; }
+__host__ __device__ inline bool two_level(const QDesc& Q) { return Q.rsrc == R_TAB2 || Q.rsrc == R_TAB2A; }
+__host__ __device__ inline int fused_first(const QDesc& Q) { return two_level(Q) ? Q.fuse_m + 1 : Q.fuse_m; }
 __host__ __device__ inline uint32_t fused_len(const QDesc& Q) {
   if (Q.mode != M_FUSED) return 0;
-  return Q.rsrc == R_TAB2 ? Q.Lin : (Q.rsrc <= R_TAB4 ? Q.Lf : 0);
+  return two_level(Q) ? Q.Lin : (Q.rsrc <= R_TAB4 ? Q.Lf : 0);
 }
 static_assert(sizeof(QDesc) % 16 == 0, "QDesc is copied in 16-byte words");
 
@@ -303,6 +304,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_b_ids(const QDesc* __restrict__
   ids_range_rows<SRC>(Q, Q.tabs, Ts, Cs, ctab, aux, Q.fuse_m, Q.Lf, Q.divLf, wb, we, lane, vec_ok, qids)
       switch (Q.rsrc) {
         case R_TAB2: MP_ROWS(R_TAB2); break;
+        case R_TAB2A: MP_ROWS(R_TAB2A); break;
         case R_TAB4: MP_ROWS(R_TAB4); break;
         case R_TAB: MP_ROWS(R_TAB); break;
         case R_BLOCK: MP_ROWS(R_BLOCK); break;
@@ -606,7 +608,7 @@ extern "C" int mp_batch_create(const mp_query* queries, int n, mp_batch** out) {
       if (Lf < kShortRow && m > 0 && Q.tabs.has[m - 1]) {
         // rows this short would change their base every few groups: the
         // next dimension joins the row through its own table
-        Q.rsrc = R_TAB2;
+        Q.rsrc = Lf % 4 == 0 ? R_TAB2A : R_TAB2;
         Q.Lin = (uint32_t)Lf;
         Q.divLin = make_div32((uint32_t)Lf);
         Q.fuse_m = m - 1;

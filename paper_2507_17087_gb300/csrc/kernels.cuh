@@ -366,7 +366,9 @@ __device__ __noinline__ uint32_t row_base_m(const MapCore& D, const Tabs& tabs, 
 //                   table's Lin points (dimensions m+1..k-1, too few for a
 //                   row of their own); x -> C2[x / Lin] + Cf[x % Lin], with
 //                   C2 dimension m's table in global memory
-enum RowSrc : int { R_TAB = 0, R_TAB4 = 1, R_BLOCK = 2, R_CYCLIC = 3, R_BCYC = 4, R_HIER = 5, R_TAB2 = 6 };
+//   R_TAB2A         R_TAB2 with Lin % 4 == 0: every group lies inside one
+//                   entry of C2 and reads its four Cf entries in one 16-byte load
+enum RowSrc : int { R_TAB = 0, R_TAB4 = 1, R_BLOCK = 2, R_CYCLIC = 3, R_BCYC = 4, R_HIER = 5, R_TAB2 = 6, R_TAB2A = 7 };
 
 // R_TAB2's second level (unused by the other row sources)
 struct RowAux {
@@ -379,7 +381,7 @@ template <int SRC>
 __device__ __forceinline__ uint32_t row_contrib(const MapCore& D, const uint32_t* __restrict__ Cf, const RowAux& A,
                                                 uint32_t x) {
   if (SRC == R_TAB || SRC == R_TAB4) return Cf[x];
-  if (SRC == R_TAB2) {
+  if (SRC == R_TAB2 || SRC == R_TAB2A) {
     uint32_t q, r;
     divmod32(x, A.divLin, q, r);
     return __ldg(A.C2 + q) + Cf[r];
@@ -456,6 +458,13 @@ __device__ __forceinline__ void ids_range_rows(const MapCore& D, const Tabs& tab
     } else if (SRC == R_TAB4) {
       const uint4 c = *reinterpret_cast<const uint4*>(Cf + x);
       v[0] = T[base + c.x]; v[1] = T[base + c.y]; v[2] = T[base + c.z]; v[3] = T[base + c.w];
+    } else if (SRC == R_TAB2A && x + 4 <= Lf) {
+      // x and Lin are multiples of 4: the group stays inside one entry of C2
+      uint32_t q0, r0;
+      divmod32(x, A.divLin, q0, r0);
+      const uint32_t c = base + __ldg(A.C2 + q0);
+      const uint4 f = *reinterpret_cast<const uint4*>(Cf + r0);
+      v[0] = T[c + f.x]; v[1] = T[c + f.y]; v[2] = T[c + f.z]; v[3] = T[c + f.w];
     } else if (SRC == R_TAB2 && x + 4 <= Lf && A.Lin >= 4) {
       // the group meets at most two entries of C2 (q0 and, when it crosses
       // a boundary of the inner table, q0 + 1 < L[m], the row going on)
