@@ -465,6 +465,31 @@ __device__ __forceinline__ void ids_range_rows(const MapCore& D, const Tabs& tab
       const uint32_t c = base + __ldg(A.C2 + q0);
       const uint4 f = *reinterpret_cast<const uint4*>(Cf + r0);
       v[0] = T[c + f.x]; v[1] = T[c + f.y]; v[2] = T[c + f.z]; v[3] = T[c + f.w];
+    } else if (SRC == R_CYCLIC && x + 4 <= Lf) {
+      // x mod s once, then one step per point
+      const Comp& c0 = D.comp[D.k - 1][0];
+      uint32_t q, a;
+      divmod32(x, c0.divs, q, a);
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        v[i] = T[base + a * c0.sigma];
+        a = a + 1 == c0.s ? 0u : a + 1;
+      }
+    } else if (SRC == R_BCYC && x + 4 <= Lf) {
+      // a group across blocks of b points: (x / b) mod s once, then the
+      // position inside the block and the block's residue step along
+      const Comp& c0 = D.comp[D.k - 1][0];
+      uint32_t blk, rb, q, a;
+      divmod32(x, c0.divb, blk, rb);
+      divmod32(blk, c0.divs, q, a);
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        v[i] = T[base + a * c0.sigma];
+        if (++rb == c0.b) {
+          rb = 0;
+          a = a + 1 == c0.s ? 0u : a + 1;
+        }
+      }
     } else if (SRC == R_TAB2 && x + 4 <= Lf && A.Lin >= 4) {
       // the group meets at most two entries of C2 (q0 and, when it crosses
       // a boundary of the inner table, q0 + 1 < L[m], the row going on)
