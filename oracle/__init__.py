@@ -69,6 +69,7 @@ def _load():
                 "or_owner_of": (I, launch + [V, I64, V]),
                 "or_map_range": (I, launch + [V, I64, I64, I, V, V]),
                 "or_comm_volume": (I, launch + [V, V, V, I]),
+                "or_map_launch": (I, launch + [V, V, V, V, V, I]),
                 "or_halo_elements": (I, launch + [V, V, V, V, I]),
                 "or_decompose_weighted": (I, [I64, I, V, V, I, V]),
                 "or_weighted_objective": (I, [I64, I, V, V, V, I, V]),
@@ -81,7 +82,7 @@ def _load():
                 "or_chain_from_draws": (I, [I, I, I, V, V]),
                 "or_matmul_cost": (I, [I64, I64, I64, I, I, V, I, V, I, V, V]),
                 "or_search": (I, [I64, I64, I64, I, I, I, I, V]),
-                "or_candidate_costs": (I, [I64, I64, I64, I, I, I, V, I64, V, V]),
+                "or_candidate_costs": (I, [I64, I64, I64, I, I, I, V, I64, V, V, I]),
                 "or_hier_costs": (I, [V, I, I, I, V, V, I, V, V, I, V, V]),
                 "or_hier_search": (I, [V, I, I, I, I, V, V, I, V]),
             }
@@ -217,6 +218,24 @@ class Launch:
         if rc:
             raise ValueError("invalid chain or distribution")
         return int(tot[0]), recv
+
+    def map_launch(self, face_bytes, ids=None, threads=1):
+        """ids, histogram, halo total and received bytes in one pass: every
+        point's owner evaluated once, each neighbour's owner looked up from
+        those ids.  `ids` may be a caller's int32 array of npoints."""
+        lib = _load()
+        fb = np.zeros(4, dtype=np.uint64)
+        fb[: self.k] = face_bytes
+        if ids is None:
+            ids = np.empty(self.npoints, dtype=np.int32)
+        assert ids.dtype == np.int32 and ids.size == self.npoints and ids.flags.c_contiguous
+        hist = np.zeros(self.P, dtype=np.uint64)
+        tot = np.zeros(1, dtype=np.uint64)
+        recv = np.zeros(self.P, dtype=np.uint64)
+        rc = lib.or_map_launch(*self._args(), _p(fb), _p(ids), _p(hist), _p(tot), _p(recv), threads)
+        if rc:
+            raise ValueError("invalid chain or distribution")
+        return ids, hist, int(tot[0]), recv
 
     def halo_elements(self, width, elem_bytes, want_recv=True, threads=1):
         """Anisotropic halo volume in elements: per element and
@@ -364,13 +383,13 @@ def search(M, N, K, machine, max_depth=3, threads=1):
             "primary": int(out[5]), "secondary": int(out[6]), "n_candidates": int(out[7])}
 
 
-def candidate_costs(M, N, K, machine, max_depth, indices):
+def candidate_costs(M, N, K, machine, max_depth, indices, threads=1):
     lib = _load()
     n, g = machine
     idx = np.ascontiguousarray(indices, dtype=np.int64)
     p = np.zeros(idx.shape[0], dtype=np.int64)
     s = np.zeros(idx.shape[0], dtype=np.int64)
-    if lib.or_candidate_costs(M, N, K, n, g, max_depth, _p(idx), idx.shape[0], _p(p), _p(s)):
+    if lib.or_candidate_costs(M, N, K, n, g, max_depth, _p(idx), idx.shape[0], _p(p), _p(s), threads):
         raise ValueError("bad candidate index")
     return p, s
 

@@ -454,9 +454,11 @@ void unravel(const Plan& pl, i64 lin, i64* x) {
   }
 }
 
+// fn(lo, hi, worker) over [0, n) in `threads` contiguous chunks; serial
+// below min_items (per-point loops: thread start-up outweighs small launches).
 template <class F>
-void parallel_for(i64 n, int threads, F fn) {
-  if (threads <= 1 || n < 4096) { fn(0, n, 0); return; }
+void parallel_for(i64 n, int threads, F fn, i64 min_items = 4096) {
+  if (threads <= 1 || n < min_items) { fn(0, n, 0); return; }
   std::vector<std::thread> th;
   i64 chunk = (n + threads - 1) / threads;
   for (int w = 0; w < threads; ++w) {
@@ -604,17 +606,33 @@ void matmul_cost_literal(i64 M, i64 N, i64 K, const ChainTable& tb, const i64* f
 // coordinates fall in the same pair of blocks touches the same set of owners
 // (the owner depends on a coordinate only through its block), so one fibre
 // per block pair is evaluated and weighted by the number of tiles in it.
-void matmul_cost_grouped(i64 M, i64 N, i64 K, const ChainTable& tb, const i64* f,
-                         i64 n_nodes, i128& prim, i128& sec) {
+//
+// The distinct block coordinates of each dimension and how many tiles fall in
+// each depend on the factorisation and the extents only, so they are counted
+// once per factorisation (BlockGroups) and shared by every chain.
+struct BlockGroups {
+  std::vector<std::vector<i64>> reps, wts;
+};
+
+BlockGroups block_groups(i64 M, i64 N, i64 K, const i64* f) {
   const i64 ext[3] = {M, N, K};
-  std::vector<std::vector<i64>> reps(3), wts(3);
+  BlockGroups bg;
+  bg.reps.resize(3);
+  bg.wts.resize(3);
   for (int t = 0; t < 3; ++t) {
     // distinct block coordinates of dimension t and how many tiles fall in each
     std::vector<i64> cnt(f[t], 0);
     for (i64 x = 0; x < ext[t]; ++x) cnt[blk(x, f[t], ext[t])]++;
     for (i64 a = 0; a < f[t]; ++a)
-      if (cnt[a] > 0) { reps[t].push_back(a); wts[t].push_back(cnt[a]); }
+      if (cnt[a] > 0) { bg.reps[t].push_back(a); bg.wts[t].push_back(cnt[a]); }
   }
+  return bg;
+}
+
+void matmul_cost_grouped(const BlockGroups& bg, const ChainTable& tb, const i64* f,
+                         i64 n_nodes, i128& prim, i128& sec) {
+  const std::vector<std::vector<i64>>& reps = bg.reps;
+  const std::vector<std::vector<i64>>& wts = bg.wts;
   prim = 0; sec = 0;
   std::vector<char> seen_node(n_nodes, 0);
   std::vector<i64> touched;
@@ -744,6 +762,75 @@ int or_map_range(const int64_t* L, int k, int n, int g, const int64_t* xf, int n
   return 0;
 }
 
+// ids, histogram and halo of one launch: the owner of every point is
+// evaluated once, as in or_map_points, and every directed pair (x, x + delta
+// e_t), delta = +-1, both points inside the launch, compares the two owners
+// from that array.  This is or_comm_volume's definition with the neighbour's
+// owner looked up instead of evaluated again (seven owner evaluations per
+// point are too slow for whole-batch checks).  ids may be NULL (kept
+// internally); hist, total and recv may be NULL.
+int or_map_launch(const int64_t* L, int k, int n, int g, const int64_t* xf, int nxf, int dist, int b,
+                  const uint64_t* face_bytes, int32_t* ids, uint64_t* hist, uint64_t* total,
+                  uint64_t* recv, int threads) {
+  Plan pl;
+  if (build_plan(pl, L, k, n, g, xf, nxf, dist, b)) return 1;
+  int T = threads < 1 ? 1 : threads;
+  std::vector<int32_t> own;
+  if (!ids) {
+    own.resize(pl.npoints);
+    ids = own.data();
+  }
+  parallel_for(pl.npoints, T, [&](i64 lo, i64 hi, int) {
+    i64 x[4];
+    for (i64 lin = lo; lin < hi; ++lin) {
+      unravel(pl, lin, x);
+      ids[lin] = (int32_t)owner_of_point(pl, x);
+    }
+  });
+  i64 stride[4];
+  stride[pl.k - 1] = 1;
+  for (int t = pl.k - 2; t >= 0; --t) stride[t] = stride[t + 1] * pl.L[t + 1];
+  std::vector<u64> tot(T, 0);
+  std::vector<std::vector<u64>> hpart(T), rpart(T);
+  parallel_for(pl.npoints, T, [&](i64 lo, i64 hi, int w) {
+    i64 x[4];
+    u64 mine = 0;
+    std::vector<u64> hv(hist ? pl.P : 0, 0), rv(recv ? pl.P : 0, 0);
+    for (i64 lin = lo; lin < hi; ++lin) {
+      const i64 me = ids[lin];
+      if (hist) hv[me]++;
+      unravel(pl, lin, x);
+      for (int t = 0; t < pl.k; ++t)
+        for (int delta = -1; delta <= 1; delta += 2) {
+          const i64 y = x[t] + delta;
+          if (y < 0 || y >= pl.L[t]) continue;
+          if (ids[lin + delta * stride[t]] != me) {
+            mine += face_bytes[t];
+            if (recv) rv[me] += face_bytes[t];
+          }
+        }
+    }
+    tot[w] = mine;
+    hpart[w] = std::move(hv);
+    rpart[w] = std::move(rv);
+  });
+  if (total) {
+    u64 s = 0;
+    for (int w = 0; w < T; ++w) s += tot[w];
+    *total = s;
+  }
+  for (i64 p = 0; p < pl.P; ++p) {
+    u64 hs = 0, rs = 0;
+    for (int w = 0; w < T; ++w) {
+      if (hist && !hpart[w].empty()) hs += hpart[w][p];
+      if (recv && !rpart[w].empty()) rs += rpart[w][p];
+    }
+    if (hist) hist[p] = hs;
+    if (recv) recv[p] = rs;
+  }
+  return 0;
+}
+
 // Owner of each listed linear point index (C-order).
 int or_owner_of(const int64_t* L, int k, int n, int g, const int64_t* xf, int nxf, int dist, int b,
                 const int64_t* lins, int64_t m, int32_t* ids_out) {
@@ -771,6 +858,8 @@ int or_comm_volume(const int64_t* L, int k, int n, int g, const int64_t* xf, int
   std::vector<std::vector<u64>> part(T, std::vector<u64>(recv ? pl.P : 0, 0));
   parallel_for(pl.npoints, T, [&](i64 lo, i64 hi, int w) {
     i64 x[4], y[4];
+    u64 mine = 0;
+    std::vector<u64> rv(recv ? pl.P : 0, 0);
     for (i64 lin = lo; lin < hi; ++lin) {
       unravel(pl, lin, x);
       i64 me = owner_of_point(pl, x);
@@ -781,11 +870,13 @@ int or_comm_volume(const int64_t* L, int k, int n, int g, const int64_t* xf, int
           if (y[t] < 0 || y[t] >= pl.L[t]) continue;
           i64 other = owner_of_point(pl, y);
           if (other != me) {
-            tot[w] += face_bytes[t];
-            if (recv) part[w][me] += face_bytes[t];
+            mine += face_bytes[t];
+            if (recv) rv[me] += face_bytes[t];
           }
         }
     }
+    tot[w] = mine;
+    if (recv) part[w] = std::move(rv);
   });
   u64 s = 0;
   for (int w = 0; w < T; ++w) s += tot[w];
@@ -820,6 +911,8 @@ int or_halo_elements(const int64_t* L, int k, int n, int g, const int64_t* xf, i
   std::vector<std::vector<u64>> part(T, std::vector<u64>(recv ? pl.P : 0, 0));
   parallel_for(pl.npoints, T, [&](i64 lo, i64 hi, int w) {
     i64 y[4], z[4];
+    u64 mine = 0;
+    std::vector<u64> rv(recv ? pl.P : 0, 0);
     std::vector<i64> seen;
     for (i64 lin = lo; lin < hi; ++lin) {
       unravel(pl, lin, y);
@@ -835,11 +928,13 @@ int or_halo_elements(const int64_t* L, int k, int n, int g, const int64_t* xf, i
           if (p == me) continue;
           if (std::find(seen.begin(), seen.end(), p) == seen.end()) seen.push_back(p);
         }
-        tot[w] += bytes[t] * (u64)seen.size();
+        mine += bytes[t] * (u64)seen.size();
         if (recv)
-          for (i64 p : seen) part[w][p] += bytes[t];
+          for (i64 p : seen) rv[p] += bytes[t];
       }
     }
+    tot[w] = mine;
+    if (recv) part[w] = std::move(rv);
   });
   u64 s = 0;
   for (int w = 0; w < T; ++w) s += tot[w];
@@ -1037,7 +1132,7 @@ int or_matmul_cost(int64_t M, int64_t N, int64_t K, int n, int g, const int64_t*
   ChainTable tb = chain_table(n, g, ch);
   i128 p, s;
   if (mode == 0) matmul_cost_literal(M, N, K, tb, f, p, s);
-  else matmul_cost_grouped(M, N, K, tb, f, n, p, s);
+  else matmul_cost_grouped(block_groups(M, N, K, f), tb, f, n, p, s);
   *primary = (int64_t)p;
   *secondary = (int64_t)s;
   return 0;
@@ -1054,6 +1149,10 @@ int or_search(int64_t M, int64_t N, int64_t K, int n, int g, int max_depth, int 
   auto chains = enum_chains(n, g, max_depth);
   i64 NC = (i64)chains.size();
   int T = threads < 1 ? 1 : threads;
+  std::vector<BlockGroups> bgs(fs.size());
+  parallel_for((i64)fs.size(), T, [&](i64 lo, i64 hi, int) {
+    for (i64 fr = lo; fr < hi; ++fr) bgs[fr] = block_groups(M, N, K, fs[fr].data());
+  }, 2);
   struct Best { i128 p, s; i64 idx; };
   std::vector<Best> best(T, Best{-1, -1, -1});
   parallel_for(NC, T, [&](i64 lo, i64 hi, int w) {
@@ -1061,15 +1160,14 @@ int or_search(int64_t M, int64_t N, int64_t K, int n, int g, int max_depth, int 
       ChainTable tb = chain_table(n, g, chains[c]);
       for (i64 fr = 0; fr < (i64)fs.size(); ++fr) {
         i128 p, s;
-        matmul_cost_grouped(M, N, K, tb, fs[fr].data(), n, p, s);
+        matmul_cost_grouped(bgs[fr], tb, fs[fr].data(), n, p, s);
         i64 idx = fr * NC + c;
         Best& b = best[w];
         if (b.idx < 0 || p < b.p || (p == b.p && (s < b.s || (s == b.s && idx < b.idx))))
           b = Best{p, s, idx};
       }
     }
-  }
-  );
+  }, 2);
   Best b = best[0];
   for (int w = 1; w < T; ++w) {
     const Best& o = best[w];
@@ -1229,19 +1327,28 @@ int or_hier_search(const int64_t* L, int k, int n, int g, int variant, const int
 
 // Cost of an explicit list of candidate indices (for sampled checks).
 int or_candidate_costs(int64_t M, int64_t N, int64_t K, int n, int g, int max_depth,
-                       const int64_t* idx, int64_t m, int64_t* primary, int64_t* secondary) {
+                       const int64_t* idx, int64_t m, int64_t* primary, int64_t* secondary,
+                       int threads) {
   auto fs = factorisations((i64)n * g, 3);
   auto chains = enum_chains(n, g, max_depth);
   i64 NC = (i64)chains.size();
+  std::vector<BlockGroups> bgs(fs.size());
+  std::vector<char> have(fs.size(), 0);
   for (int64_t e = 0; e < m; ++e) {
-    i64 fr = idx[e] / NC, c = idx[e] % NC;
-    if (idx[e] < 0 || fr >= (i64)fs.size()) return 1;
-    ChainTable tb = chain_table(n, g, chains[c]);
-    i128 p, s;
-    matmul_cost_grouped(M, N, K, tb, fs[fr].data(), n, p, s);
-    primary[e] = (int64_t)p;
-    secondary[e] = (int64_t)s;
+    if (idx[e] < 0 || idx[e] / NC >= (i64)fs.size()) return 1;
+    i64 fr = idx[e] / NC;
+    if (!have[fr]) { bgs[fr] = block_groups(M, N, K, fs[fr].data()); have[fr] = 1; }
   }
+  parallel_for(m, threads < 1 ? 1 : threads, [&](i64 lo, i64 hi, int) {
+    for (i64 e = lo; e < hi; ++e) {
+      i64 fr = idx[e] / NC, c = idx[e] % NC;
+      ChainTable tb = chain_table(n, g, chains[c]);
+      i128 p, s;
+      matmul_cost_grouped(bgs[fr], tb, fs[fr].data(), n, p, s);
+      primary[e] = (int64_t)p;
+      secondary[e] = (int64_t)s;
+    }
+  }, 64);
   return 0;
 }
 

@@ -340,6 +340,43 @@ def test_block_halo_closed_form_by_hand():
         assert launch.comm_volume([1] * len(L))[0] == want
 
 
+def test_map_launch_equals_per_pair_evaluation():
+    # the one-pass form (owners evaluated once, each neighbour's owner looked
+    # up) against map_points and against comm_volume, which evaluates the
+    # neighbour's owner again for every directed pair; all five
+    # distributions, threads or not
+    rng = W.rng(26)
+    for it in range(200):
+        L, machine, chain, dist = _random_launch(rng, max_points=5000)
+        launch = O.Launch(L, machine, chain, dist)
+        face = tuple(rng.randint(1, 9) for _ in L)
+        threads = 1 + it % 3
+        ids, hist, tot, recv = launch.map_launch(face, threads=threads)
+        rids, rhist = launch.map_points()
+        rtot, rrecv = launch.comm_volume(face)
+        assert np.array_equal(ids, rids) and np.array_equal(hist, rhist)
+        assert tot == rtot and np.array_equal(recv, rrecv), (L, machine, chain, dist)
+
+
+def test_map_launch_halo_by_numpy_neighbour_comparison():
+    # directed faces counted from the ids array with plain numpy slicing
+    rng = W.rng(27)
+    for _ in range(60):
+        L, machine, chain, dist = _random_launch(rng, max_points=4000)
+        launch = O.Launch(L, machine, chain, dist)
+        face = tuple(rng.randint(1, 9) for _ in L)
+        ids, _, tot, recv = launch.map_launch(face)
+        v = ids.reshape(L)
+        P = machine[0] * machine[1]
+        want = np.zeros(P, dtype=np.int64)
+        for t in range(len(L)):
+            a = np.take(v, np.arange(L[t] - 1), axis=t)
+            b = np.take(v, np.arange(1, L[t]), axis=t)
+            cross = a != b
+            want += face[t] * (np.bincount(a[cross], minlength=P) + np.bincount(b[cross], minlength=P))
+        assert np.array_equal(recv.astype(np.int64), want) and tot == int(want.sum())
+
+
 def test_halo_and_histogram_multiset_independent_of_chain():
     L, machine = (9, 7, 5), (4, 3)
     ref = None
@@ -478,6 +515,25 @@ def test_search_literal_brute_force_tiny():
             best = key if best is None or key < best else best
     res = O.search(M, N, K, (n, g), 2)
     assert (res["primary"], res["secondary"], res["index"]) == best
+
+
+def test_secondary_worked_by_hand():
+    # 4 x 2 x 2 tiles (M, N, K) on Machine(GPU) = (2 nodes, 2 GPUs), f = (2, 2, 1).
+    # Block coordinates: a0 = floor(2 i / 4) (i = 0,1 -> 0; i = 2,3 -> 1),
+    # a1 = j, a2 = 0; flat index b = a0 + 2 a1.  Flattening (node, gpu) with
+    # merge(0, 1) puts the node fastest (Sec. 5.2): node(b) = b mod 2,
+    # gpu(b) = b div 2.
+    #   A(i, k), 8 tiles, fibre over j: b in {a0, a0 + 2} -> 2 processors, 1 node
+    #   B(k, j), 4 tiles, fibre over i: b in {2j, 2j + 1} -> 2 processors, 2 nodes
+    #   C(i, j), 8 tiles, fibre over k: one block -> 1 processor, 1 node
+    # primary = 8 (2 - 1) + 4 (2 - 1) + 0 = 12; secondary = 0 + 4 (2 - 1) + 0 = 4.
+    # With swap(0, 1) first, the flattened space is (gpu, node) merged gpu
+    # fastest: node(b) = b div 2 = a1 = j.
+    #   A: nodes {0, 1} -> 8 (2 - 1) = 8;  B: node j only -> 0;  C: 0
+    # secondary = 8 (the primary does not depend on the chain).
+    for literal in (False, True):
+        assert O.matmul_cost(4, 2, 2, (2, 2), (), (2, 2, 1), literal=literal) == (12, 4)
+        assert O.matmul_cost(4, 2, 2, (2, 2), (("swap", 0, 1),), (2, 2, 1), literal=literal) == (12, 8)
 
 
 def test_secondary_depends_on_chain():
