@@ -34,9 +34,9 @@ from paper_2507_17087_gb300 import workloads as W  # noqa: E402
 METRIC = "points mapped/s"
 UNIT = "points/s"
 VARIANTS = ("block", "cyclic", "block_cyclic")
-# DRAM bytes (read + write) of one full-size id-writer launch from the ncu
-# capture summarised in profiles/k_ids_large_1024x1024x512.md (set to None
-# when the kernel changes, until it is captured again).
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one full-size
+# id-writer launch, from a separate ncu capture of this kernel (not measured
+# in this run; None once the kernel changes, until it is captured again).
 K_IDS_TRAFFIC_BYTES = 2086498560 + 46080
 
 
@@ -597,6 +597,8 @@ def main():
                        "l2": "outputs larger than L2 (2 GiB of ids per launch)"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
+                         "traffic_source": "ncu capture of one full-size k_ids launch (dram read + write "
+                                           "bytes), taken separately, not in this run",
                          "kernel": "k_ids (id writer)", "peak_source": f"{peak_kind} hbm_gbs",
                          "kernel_avg_ms": k_avg_ms, "algorithmic_bytes_per_launch": algo_bytes,
                          "note": "k_ids only writes, and hbm_gbs is a read + write copy: a write-only "

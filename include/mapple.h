@@ -62,11 +62,14 @@ enum mp_status {
 #define MP_MAX_XFORMS 64          /* transforms in one chain                   */
 #define MP_MAX_PROCS (1 << 26)    /* P = nodes * procs_per_node                */
 #define MP_MAX_HALO_WIDTH 16      /* halo width per dimension (mp_halo_volume)  */
+#define MP_MAX_EXTENT (1ll << 38) /* task extent bound: keeps the distributions'
+                                     products x * s below 2^64 (MP_ENOTSUP)   */
 
 /* ------------------------------------------------------------ data types */
 
 /* Index launch (task space): rank 1..4, extents ext[0..rank), C order (last
- * dimension fastest).  Point count prod(ext) must be < 2^62.  (Sec. 5.1's
+ * dimension fastest), each extent 1 .. MP_MAX_EXTENT - 1 (an extent >=
+ * MP_MAX_EXTENT is MP_ENOTSUP).  Point count prod(ext) must be < 2^62.  (Sec. 5.1's
  * ISpace / IPoint; Appendix A.1 task.ispace.) */
 typedef struct mp_space {
   int32_t rank;
@@ -144,8 +147,8 @@ typedef struct mp_dist {
  *   ids  : int32[prod(ext)] device or host, or NULL
  *   hist : uint64[P] device or host, or NULL (overwritten, not accumulated)
  * Errors: MP_EINVAL (invalid transform / distribution / extents),
- * MP_EOVERFLOW (prod(ext) >= 2^62), MP_ENOTSUP (P > MP_MAX_PROCS),
- * MP_ENOMEM, MP_ECUDA. */
+ * MP_EOVERFLOW (prod(ext) >= 2^62), MP_ENOTSUP (P > MP_MAX_PROCS, or an
+ * extent >= MP_MAX_EXTENT), MP_ENOMEM, MP_ECUDA. */
 int mp_map_points(const mp_space* space, const mp_machine* machine, const mp_xform* chain,
                   int n_xf, const mp_dist* dist, int32_t* ids, uint64_t* hist, void* stream);
 
@@ -262,7 +265,12 @@ int mp_map_launch(const mp_space* space, const mp_machine* machine, const mp_xfo
  *                every call.
  *   set-up     : the first call on a device looks up the array's device
  *                address (cudaGetSymbolAddress, with that device current); make
- *                that first call before any stream capture.
+ *                that first call before any stream capture.  The address is
+ *                kept for the life of the process: a cudaDeviceReset between
+ *                calls is not supported.
+ *   streams    : every kernel runs on `stream`, the reductions after the id
+ *                writer (mp_map_points would run them on a second stream); no
+ *                stream or event is created.
  *   concurrency: every call shares the one array, so calls that overlap on
  *                the GPU (other streams, other host threads) race; serialise
  *                them. */
@@ -551,6 +559,11 @@ const char* mp_last_error_detail(void);
 
 /* Number of kernel launches issued by this library in the calling process. */
 uint64_t mp_kernel_launches(void);
+
+/* Bytes of device workspace this library holds on the current device (the
+ * grow-only per-device scratch of the mapping calls; 0 before the first
+ * call).  Host only; lets a caller see whether a call allocated. */
+uint64_t mp_workspace_bytes(void);
 
 #ifdef __cplusplus
 }

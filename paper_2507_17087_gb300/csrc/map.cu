@@ -439,7 +439,7 @@ Layout make_layout(const MapDesc& D, const Want& w) {
 
 // Runs the kernels of one launch into device buffers, with the scratch at ws
 // (at least ly.bytes).
-int run_launch_ws(const Plan& pl, const Want& w, const Layout& ly, char* ws, cudaStream_t st) {
+int run_launch_ws(const Plan& pl, const Want& w, const Layout& ly, char* ws, cudaStream_t st, bool side_stream) {
   const MapDesc& D = pl.desc;
   const Tabs& tabs = ly.tabs;
   uint32_t* T = (uint32_t*)(ws + ly.o_T);
@@ -511,7 +511,7 @@ int run_launch_ws(const Plan& pl, const Want& w, const Layout& ly, char* ws, cud
   };
   // with ids wanted too, the counts and reductions (which read only the chain
   // table) run on a second stream beside the tables and the id writer
-  const ForkStreams* fk = w.ids && ly.need_red ? fork_streams() : nullptr;
+  const ForkStreams* fk = side_stream && w.ids && ly.need_red ? fork_streams() : nullptr;
   cudaStream_t rs = st;
   if (fk) {
     MP_CUDA_TRY(cudaEventRecord(fk->fork, st));
@@ -645,7 +645,7 @@ int run_launch(const Plan& pl, const Want& w, cudaStream_t st) {
   const Layout ly = make_layout(pl.desc, w);
   char* ws = (char*)workspace(ly.bytes, 0);
   if (!ws) return MP_ENOMEM;
-  return run_launch_ws(pl, w, ly, ws, st);
+  return run_launch_ws(pl, w, ly, ws, st, true);
 }
 
 // Resolves host/device outputs: device buffers are used directly, host
@@ -1109,5 +1109,6 @@ extern "C" int mp_map_points_noalloc(const mp_space* space, const mp_machine* ma
   char* ws = nullptr;
   rc = mp::noalloc_scratch(&ws);
   if (rc) return rc;
-  return mp::run_launch_ws(pl, w, ly, ws, (cudaStream_t)stream);
+  // everything on the caller's stream: no second stream or events are created
+  return mp::run_launch_ws(pl, w, ly, ws, (cudaStream_t)stream, false);
 }

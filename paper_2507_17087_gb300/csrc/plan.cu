@@ -11,7 +11,7 @@ namespace mp {
 
 namespace {
 
-constexpr int64_t kMaxExtent = int64_t(1) << 38;   // keeps x * s below 2^64
+constexpr int64_t kMaxExtent = MP_MAX_EXTENT;   // keeps x * s below 2^64
 constexpr int64_t kMaxPoints = int64_t(1) << 62;
 
 std::vector<int64_t> divisors_ascending(int64_t v) {

@@ -138,6 +138,18 @@ extern "C" int mp_set_kernel_timer(void* start_event, void* stop_event) {
 
 extern "C" uint64_t mp_descriptor_bytes(void) { return sizeof(mp::MapDesc); }
 
+extern "C" uint64_t mp_workspace_bytes(void) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= mp::kMaxDevices) {
+    cudaGetLastError();
+    return 0;
+  }
+  std::lock_guard<std::mutex> lock(mp::g_ws_mu);
+  uint64_t total = 0;
+  for (int s = 0; s < mp::kSlots; ++s) total += mp::g_ws[dev].size[s];
+  return total;
+}
+
 extern "C" int mp_debug_fail_allocations(int32_t n) {
   if (n < 0) return MP_EINVAL;
   mp::g_fail_allocs.store(n);

@@ -146,6 +146,7 @@ def lib():
                 "mp_strerror": (ctypes.c_char_p, [I]),
                 "mp_last_error_detail": (ctypes.c_char_p, []),
                 "mp_kernel_launches": (U64, []),
+                "mp_workspace_bytes": (U64, []),
                 "mp_set_kernel_timer": (I, [V, V]),
                 "mp_batch_create": (I, [V, I, V]),
                 "mp_batch_info": (I, [V, V, V, V, V, V]),
@@ -570,6 +571,11 @@ def candidate_costs(query, indices, primary, secondary, stream=None):
 
 def kernel_launches() -> int:
     return int(lib().mp_kernel_launches())
+
+
+def workspace_bytes() -> int:
+    """Device workspace the library holds on the current device."""
+    return int(lib().mp_workspace_bytes())
 
 
 def set_kernel_timer(start_event, stop_event):

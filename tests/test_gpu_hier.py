@@ -6,6 +6,7 @@ import math
 import pytest
 
 import oracle as O
+from hier_chains import hier_chain, node_chain
 from paper_2507_17087_gb300 import native as N
 from paper_2507_17087_gb300 import workloads as W
 
@@ -36,16 +37,15 @@ def test_fig5b_case():
 def test_large_launch_against_closed_forms():
     # 1024 x 1024 x 512 on 64 x 8, width 1: every candidate's volumes from
     # the oracle's closed form (block layouts: element count = face count)
+    # on the test's own chains for the two-level mapping
     L, machine, eb = (1024, 1024, 512), (64, 8), (8, 8, 8)
     got = N.hier_search(L, machine, "block", (1, 1, 1), eb)
     fa, fb = O.factorisations(64, 3), O.factorisations(8, 3)
     best = None
     for i, a in enumerate(fa):
-        ch, dist = N.hier_chain(a, (1, 1, 1), "block")
-        node_ch = ch[:2] + [("merge", 2, 3)]
-        p = O.Launch(L, (64, 1), node_ch, ("block",)).halo_closed_form(eb)
+        p = O.Launch(L, (64, 1), node_chain(3, a), ("block",)).halo_closed_form(eb)
         for j, b in enumerate(fb):
-            ch, dist = N.hier_chain(a, b, "block")
+            ch, dist = hier_chain(3, a, b, "block")
             s = O.Launch(L, machine, ch, dist).halo_closed_form(eb)
             key = (p, s, i * len(fb) + j)
             best = key if best is None or key < best else best

@@ -3,11 +3,13 @@
 Every case runs the CUDA engine through the C ABI and compares, element by
 element, with the oracle on the same seeded launch: ids and histograms are
 integers and must match bit-exactly; so must the halo totals and the
-per-processor received bytes.  At the 1024x1024x512 size the oracle checks
-sampled ids one by one, and the reductions are checked against plain PyTorch
-recomputations from the ids and against the oracle's closed form.
+per-processor received bytes.  At the 1024x1024x512 size the call the
+benchmark times is compared with the oracle in full: every id, the whole
+histogram, the halo total and the received bytes of every processor.
 """
+import itertools
 import math
+import os
 
 import numpy as np
 import pytest
@@ -21,6 +23,7 @@ pytestmark = pytest.mark.gpu
 
 DEV = "cuda"
 THREADS = 8
+CORES = os.cpu_count() or 8
 
 
 def gpu_run(L, machine, chain, dist, face):
@@ -117,7 +120,7 @@ def test_large_processor_count_uses_global_tables():
 def test_long_fastest_dimension_paths():
     # c_last from the HBM table (8192 < L_last <= 2^22) and computed (> 2^22)
     for L in [(3, 20011), ((1 << 22) + 5,)]:
-        for dist in [("block",), ("block_cyclic", 7)]:
+        for dist in [("block",), ("cyclic",), ("block_cyclic", 7)]:
             check_against_oracle(L, (5, 3), [("swap", 0, 1)], dist, [2] * len(L))
 
 
@@ -162,40 +165,77 @@ def test_invalid_arguments_write_nothing():
 
 @pytest.mark.parametrize("variant", ["block", "cyclic", "block_cyclic"])
 def test_full_size_1024x1024x512(variant):
+    # the call the benchmark times (ids, histogram, halo total and received
+    # bytes in one map_launch, on the current stream) at full size, compared
+    # element by element with the oracle: all 2^29 ids, the whole histogram,
+    # the halo total and every processor's received bytes, the neighbour's
+    # owner evaluated independently for every directed pair
     cfg = W.large_config(variant)
     L, machine, face = cfg["L"], cfg["machine"], cfg["face"]
     chain = N.chain_from_draws(*machine, cfg["draws"])
+    assert chain == O.chain_from_draws(*machine, cfg["draws"])
     P = machine[0] * machine[1]
     npts = math.prod(L)
-    ids = torch.empty(npts, dtype=torch.int32, device=DEV)
-    hist = torch.empty(P, dtype=torch.int64, device=DEV)
-    total = torch.empty(1, dtype=torch.int64, device=DEV)
-    recv = torch.empty(P, dtype=torch.int64, device=DEV)
-    N.map_points(L, machine, chain, cfg["dist"], ids=ids, hist=hist)
-    N.comm_volume(L, machine, chain, cfg["dist"], face, total=total, recv=recv)
+    ids = torch.full((npts,), -7, dtype=torch.int32, device=DEV)
+    hist = torch.full((P,), -7, dtype=torch.int64, device=DEV)
+    total = torch.full((1,), -7, dtype=torch.int64, device=DEV)
+    recv = torch.full((P,), -7, dtype=torch.int64, device=DEV)
+    N.map_launch(L, machine, chain, cfg["dist"], ids=ids, hist=hist, face_bytes=face, total=total, recv=recv,
+                 stream=torch.cuda.current_stream())
     torch.cuda.synchronize()
+    got_ids = ids.cpu().numpy()
+    got_hist, got_total, got_recv = hist.cpu().numpy(), int(total.item()), recv.cpu().numpy()
+    del ids
+    torch.cuda.empty_cache()
     ref = O.Launch(L, machine, chain, cfg["dist"])
-    # sampled ids against the oracle, point by point
-    g = torch.Generator().manual_seed(7)
-    lins = torch.randint(0, npts, (100000,), generator=g).numpy().astype(np.int64)
-    lins = np.concatenate([lins, np.arange(0, 4096), np.arange(npts - 4096, npts)])
-    got = ids[torch.from_numpy(lins).to(DEV)].cpu().numpy()
-    assert np.array_equal(got, ref.owner_of(lins))
-    # histogram: plain PyTorch bincount of the ids
-    assert torch.equal(torch.bincount(ids.long(), minlength=P), hist)
-    # halo total: the oracle's closed form
-    assert int(total.item()) == ref.halo_closed_form(face)
-    # per-processor received bytes: plain PyTorch neighbour comparison
-    v = ids.view(*L)
-    want = torch.zeros(P, dtype=torch.int64, device=DEV)
-    for t in range(3):
-        a = v.narrow(t, 0, L[t] - 1)
-        b = v.narrow(t, 1, L[t] - 1)
-        cross = a != b
-        want += face[t] * (torch.bincount(a[cross].long(), minlength=P) +
-                           torch.bincount(b[cross].long(), minlength=P))
-    assert torch.equal(want, recv)
-    assert int(recv.sum().item()) == int(total.item())
+    rids, rhist = ref.map_points(threads=CORES)
+    assert np.array_equal(got_ids, rids)
+    del rids, got_ids
+    assert np.array_equal(got_hist.astype(np.uint64), rhist)
+    rtot, rrecv = ref.comm_volume(face, threads=CORES)
+    assert got_total == rtot == ref.halo_closed_form(face)
+    assert np.array_equal(got_recv.astype(np.uint64), rrecv)
+
+
+def test_extent_limit():
+    # an extent of 2^38 or more is MP_ENOTSUP (the distributions' products
+    # x * s must stay below 2^64); nothing is written
+    hist = torch.full((6,), -3, dtype=torch.int64, device=DEV)
+    for L in [(1 << 38,), (2, 1 << 40)]:
+        with pytest.raises(N.MapleError) as e:
+            N.map_points(L, (2, 3), [], ("block",), hist=hist)
+        assert e.value.status == 6
+    assert (hist == -3).all()
+    # just below the limit, without ids: only the closed-form per-dimension
+    # counts run.  Histogram: every final index a owns prod_t H_t(a_t)
+    # points, H(a) = ceil((a+1) L / s) - ceil(a L / s) for block and
+    # floor((L - 1 - a) / s) + 1 for cyclic; halo total: the oracle's closed
+    # form; received bytes sum to it
+    for L, machine, dist in [(((1 << 38) - 1,), (2, 3), ("block",)), (((1 << 38) - 3,), (5, 1), ("cyclic",)),
+                             ((3, (1 << 38) - 5), (2, 4), ("block",)), ((7, (1 << 38) - 1), (3, 2), ("cyclic",))]:
+        P = machine[0] * machine[1]
+        face = [8] * len(L)
+        hist = torch.full((P,), -3, dtype=torch.int64, device=DEV)
+        total = torch.full((1,), -3, dtype=torch.int64, device=DEV)
+        recv = torch.full((P,), -3, dtype=torch.int64, device=DEV)
+        N.map_launch(L, machine, [], dist, hist=hist, face_bytes=face, total=total, recv=recv)
+        torch.cuda.synchronize()
+        ref = O.Launch(L, machine, [], dist)
+        shape = ref.final_shape()
+        a = np.array(list(itertools.product(*[range(v) for v in shape])), dtype=np.int64)
+        node, proc = ref.resolve(a)
+        want = np.zeros(P, dtype=np.int64)
+        for row, nd, pr in zip(a, node, proc):
+            cnt = 1
+            for t, at in enumerate(row):
+                if dist[0] == "block":
+                    cnt *= -(-(int(at) + 1) * L[t] // shape[t]) - -(-int(at) * L[t] // shape[t])
+                else:
+                    cnt *= (L[t] - 1 - int(at)) // shape[t] + 1
+            want[nd * machine[1] + pr] = cnt
+        assert hist.cpu().numpy().tolist() == want.tolist(), (L, dist)
+        assert int(total.item()) == ref.halo_closed_form(face), (L, dist)
+        assert int(recv.sum().item()) == int(total.item())
 
 
 def test_wide_index_launch_sampled():

@@ -165,9 +165,9 @@ def test_greedy_grid_matches_oracle():
 
 
 def test_hier_chain_matches_the_pinned_construction():
-    # the engine's two-level chains equal the oracle-pinned construction of
-    # tests/test_oracle_pins.py, and plan to the expected final spaces
-    import test_oracle_pins as T
+    # the engine's two-level chains equal the test-side construction (the
+    # one the oracle pins use), and plan to the expected final spaces
+    import hier_chains as T
     rng = W.rng(906)
     for _ in range(60):
         k = rng.randint(1, 4)

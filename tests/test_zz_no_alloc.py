@@ -42,13 +42,18 @@ def test_noalloc_matches_map_points_on_consecutive_calls():
         ref_ids = torch.empty(npts, dtype=torch.int32, device="cuda")
         ref_hist = torch.empty(P, dtype=torch.int64, device="cuda")
         N.map_points(L, machine, chain, dist, ids=ref_ids, hist=ref_hist)
-        for _ in range(2):
-            ids = torch.full((npts,), -1, dtype=torch.int32, device="cuda")
-            hist = torch.full((P,), -1, dtype=torch.int64, device="cuda")
+        outs = [(torch.full((npts,), -1, dtype=torch.int32, device="cuda"),
+                 torch.full((P,), -1, dtype=torch.int64, device="cuda")) for _ in range(2)]
+        torch.cuda.synchronize()
+        # nothing is allocated by the calls: neither the device's free memory
+        # nor the library's workspace changes around them
+        free0, ws0 = torch.cuda.mem_get_info()[0], N.workspace_bytes()
+        for ids, hist in outs:
             assert call_noalloc(L, machine, chain, dist, ids, hist) == 0
             torch.cuda.synchronize()
             assert torch.equal(ids, ref_ids)
             assert torch.equal(hist, ref_hist)
+        assert (torch.cuda.mem_get_info()[0], N.workspace_bytes()) == (free0, ws0)
 
 
 def test_noalloc_rejects_host_buffers_and_oversized_scratch():
