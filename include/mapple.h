@@ -408,11 +408,13 @@ int mp_mlp_set_params(mp_mlp* model, const float* params /* host */);
 /* params / grads: host float32[mp_mlp_num_params()] or NULL; grads are those
  * of the last training step. */
 int mp_mlp_get_params(const mp_mlp* model, float* params, float* grads);
-/* y[B] = model(X[B x 64]) with X bfloat16; device buffers, B % 128 == 0. */
+/* y[B] = model(X[B x 64]) with X bfloat16; device buffers, B % 128 == 0,
+ * B <= 2^26 (MP_ENOTSUP beyond). */
 int mp_mlp_forward(mp_mlp* model, const void* X, float* y, int B, void* stream);
 /* One Adam step (lr > 0) or gradients only (lr == 0) on the mean squared
  * error 0.5 mean (y - target)^2; *loss (host) receives the loss before the
- * step.  Device X (bfloat16 B x 64) and target (float32 B), B % 128 == 0. */
+ * step.  Device X (bfloat16 B x 64) and target (float32 B), B % 128 == 0,
+ * B <= 2^26. */
 int mp_mlp_train_step(mp_mlp* model, const void* X, const float* target, int B, float lr, float* loss,
                       void* stream);
 
@@ -420,7 +422,8 @@ int mp_mlp_train_step(mp_mlp* model, const void* X, const float* target, int B, 
  * candidates (half with the least primary cost, a quarter among the eight
  * lowest primaries, a quarter uniform) are evaluated exactly
  * (mp_candidate_costs), featurised, and the model takes `epochs` passes of
- * Adam over shuffled batches of `batch` (a multiple of 128).  Regression
+ * Adam over shuffled batches of `batch` (a multiple of 128), the step size
+ * following a cosine from lr down to 0.05 lr over the run.  Regression
  * target: 2 min(p / p_min - 1, 16) + log2(1 + s) / 8 with p, s the
  * candidate's primary / secondary cost in tiles and p_min the query's least
  * primary.  *final_loss: last batch loss. */
@@ -430,40 +433,64 @@ int mp_mlp_train_search(mp_mlp* model, const mp_search_query* queries, int n_que
 /* Learned decompose search.  Only candidates whose factorisation attains
  * the least primary cost can win the lexicographic argmin (the primary is
  * exact and closed-form), so the model scores those (fused tcgen05
- * inference; MP_LEARNED_SCORE_ALL scores every candidate) and the K best
- * scores are evaluated exactly.  Their argmin is returned if it is certified
- * (every candidate that could beat it was among those evaluated, or its
- * secondary cost reaches mp_secondary_lower_bound of every factorisation of
- * least primary cost) or if the
- * model's largest overestimation on them leaves a margin below the
- * selection threshold.  Otherwise the selection grows 8-fold in score order
- * (while it stays within 65536 candidates and a quarter of those scored) and
- * the rule is applied again; if it still fails, the exhaustive search runs.  MP_LEARNED_NO_FALLBACK
- * returns the argmin of the first K without growing or falling back.  The
- * returned costs are always exact.  K in [1, 65536].  Synchronous.
- * Phase times are host wall-clock milliseconds, each ending at a stream
- * synchronisation. */
+ * inference; MP_LEARNED_SCORE_ALL scores every candidate).  The K best
+ * scores, with the rest of the score-histogram bin the K-th falls in, are
+ * evaluated exactly, and their argmin is found, on the device (one round
+ * trip per selection).  It is returned when
+ *   1 every candidate of least primary cost was evaluated (exact),
+ *   2 its secondary reaches mp_secondary_lower_bound of every
+ *     factorisation of least primary cost (exact), or
+ *   3 the margin rule holds (a heuristic, calibrated by mp_mlp_calibrate):
+ *     every candidate left out scored at least tau, and tau exceeds the
+ *     winner's regression target by more than 1.25 x the calibrated
+ *     overestimation bound + 0.01.  An uncalibrated model (or a model that
+ *     produced a NaN / infinite score) gets no margin.
+ * Otherwise the selection grows 2-fold in score order (while it stays
+ * within 65536 candidates and half of those scored; each round evaluates
+ * only the candidates it adds) and the rules are applied again; if they
+ * still fail, the exhaustive search runs (exact).
+ * So the returned costs are always the exact costs of the returned
+ * candidate, and the candidate is the optimum under rules 1 and 2 and the
+ * fallback; under rule 3 it is the optimum unless the model overestimated a
+ * better candidate by more than its calibrated bound.
+ * MP_LEARNED_NO_FALLBACK returns the argmin of the first selection without
+ * growing or falling back.  K in [1, 65536].  Synchronous.
+ * Phase times: ms_prepare and ms_fallback are host wall-clock; ms_model and
+ * ms_exact are device time between events on the stream. */
 typedef struct mp_learned_stats {
   int64_t n_scored;         /* candidates scored by the model                     */
   int64_t n_exact;          /* candidate evaluations, summed over the rounds      */
   int64_t n_selected;       /* size of the last selection                         */
-  int32_t certified;        /* 1: every candidate that could win was evaluated;
-                               2: the winner reaches mp_secondary_lower_bound
-                               of every least-primary factorisation            */
+  int32_t certified;        /* how the result was accepted: 0 not (fallback or
+                               MP_LEARNED_NO_FALLBACK), 1 / 2 / 3 as above       */
   int32_t fallback;         /* 1: the exhaustive search ran                       */
   int32_t rounds;           /* selections evaluated (1 + growth steps)            */
   int32_t reserved;
-  double margin;            /* threshold - winner target - 1.5 * max overestimation */
+  double margin;            /* tau - winner target - rule bound (last selection)  */
   double max_overestimate;  /* largest score - target on the last selection        */
-  double ms_prepare;        /* candidate space, chain features, primaries          */
-  double ms_model;          /* fused scoring and the score histogram               */
-  double ms_exact;          /* selections and their exact costs                    */
-  double ms_fallback;       /* the exhaustive search, when it ran                  */
+  double margin_bound;      /* the rule bound used (infinite: not calibrated)     */
+  double ms_prepare;        /* candidate space, pool, lower bounds (host)         */
+  double ms_model;          /* fused scoring and the score histogram (device)     */
+  double ms_exact;          /* selections, exact costs, argmin (device)           */
+  double ms_wall;           /* scoring through the last selection (host)          */
+  double ms_fallback;       /* the exhaustive search, when it ran (host)          */
 } mp_learned_stats;
 #define MP_LEARNED_NO_FALLBACK 1
 #define MP_LEARNED_SCORE_ALL 2
 int mp_learned_search(mp_mlp* model, const mp_search_query* query, int K, int flags, mp_search_result* out,
                       mp_learned_stats* stats, void* stream);
+
+/* Calibrates the margin rule of mp_learned_search on queries held out of
+ * training.  For each query every candidate of least primary cost is scored
+ * and evaluated exactly, and the model's overestimation of its best-scored
+ * optimal candidate (least score among the candidates of least secondary,
+ * minus their regression target) is taken; the bound is the largest over
+ * the queries (*bound_out, host).  The model keeps it (and checkpoints
+ * carry it).  Synchronous. */
+int mp_mlp_calibrate(mp_mlp* model, const mp_search_query* queries, int n_queries, double* bound_out,
+                     void* stream);
+/* Sets the bound directly (INFINITY: no margin rule). */
+int mp_mlp_set_margin_bound(mp_mlp* model, double bound);
 
 /* Scores of every candidate of a query in index order (the fused scoring
  * kernel of mp_learned_search), and optionally their features (bfloat16,
@@ -530,11 +557,13 @@ uint64_t mp_descriptor_bytes(void);
 /* ------------------------------------------------------------ checkpoint, self-tests */
 
 /* Model checkpoint (training can resume from it): a binary file with a
- * versioned header -- 8 bytes "MAPLEMLP", uint32 format version (1), uint32
- * parameter count, int64 Adam step -- followed by the float32 parameters and
- * the two float32 Adam moment arrays.  mp_mlp_load rejects another magic,
- * version or parameter count (MP_EINVAL) and a short file (MP_EINVAL);
- * MP_ECUDA / file errors otherwise.  Synchronous. */
+ * versioned header -- 8 bytes "MAPLEMLP", uint32 format version (2), uint32
+ * parameter count, int64 Adam step, float64 margin bound (mp_mlp_calibrate;
+ * version 2 only) -- followed by the float32 parameters and the two float32
+ * Adam moment arrays.  mp_mlp_load reads versions 1 and 2 (a version-1 file
+ * leaves the model uncalibrated) and rejects another magic, version or
+ * parameter count (MP_EINVAL) and a short file (MP_EINVAL); MP_ECUDA / file
+ * errors otherwise.  Synchronous. */
 int mp_mlp_save(const mp_mlp* model, const char* path);
 int mp_mlp_load(mp_mlp* model, const char* path);
 

@@ -162,14 +162,6 @@ __device__ __forceinline__ float target_of(unsigned long long p_tiles, unsigned 
   return 2.f * fminf(pn, 16.f) + log2f(1.f + (float)s_tiles) / 8.f;
 }
 
-__global__ void k_primaries(const Fact* __restrict__ facts, uint32_t nf, uint32_t E0, uint32_t E1, uint32_t E2,
-                            unsigned long long* __restrict__ out) {
-  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= nf) return;
-  const uint32_t E[3] = {E0, E1, E2};
-  const uint32_t f[3] = {facts[i].f[0], facts[i].f[1], facts[i].f[2]};
-  out[i] = primary_cost(E, f);
-}
 
 // Features (BF16, row-major n x 64) of listed candidates; with exact costs
 // (bytes) also the regression targets.
@@ -481,64 +473,282 @@ __device__ __forceinline__ uint32_t order_key(float v) {
   return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
 }
 
-__global__ void k_topk_hist(const float* __restrict__ s, unsigned long long n, unsigned* __restrict__ hist) {
-  for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (unsigned long long)gridDim.x * blockDim.x)
-    atomicAdd(hist + (order_key(s[i]) >> 16), 1u);
+// The score of an order key: the inverse of order_key.
+__device__ __forceinline__ float key_value(uint32_t key) {
+  return __uint_as_float((key & 0x80000000u) ? (key ^ 0x80000000u) : ~key);
 }
 
-// smallest bin T whose cumulative count reaches K; out[0] = T, out[1] = count below T
-__global__ void __launch_bounds__(1024) k_topk_threshold(const unsigned* __restrict__ hist, unsigned K,
-                                                         unsigned* __restrict__ out) {
-  __shared__ unsigned part[1024];
-  const int t = threadIdx.x;   // 1024 threads x 64 bins
-  unsigned s = 0;
-  for (int i = 0; i < 64; ++i) s += hist[t * 64 + i];
-  part[t] = s;
+// Zeroes one selection's counters: the 65536 fine bins and 256 coarse bins
+// of the score histogram and `words` more counter words after them.
+__global__ void k_sel_init(unsigned* __restrict__ hist, unsigned words) {
+  const unsigned n = 65536 + 256 + words;
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) hist[i] = 0;
+}
+
+// 65536-bin histogram of the order keys' upper halves, and a 256-bin coarse
+// one of their top bytes (per CTA in shared memory first: the scores crowd
+// into a few coarse bins); nonfinite counts the NaN / infinite scores (a
+// model that produced one gets no margin)
+__global__ void k_topk_hist(const float* __restrict__ s, unsigned long long n, unsigned* __restrict__ hist,
+                            unsigned* __restrict__ coarse, unsigned* __restrict__ nonfinite) {
+  __shared__ unsigned c[256];
+  for (int i = threadIdx.x; i < 256; i += blockDim.x) c[i] = 0;
   __syncthreads();
-  for (int o = 1; o < 1024; o <<= 1) {
-    const unsigned v = t >= o ? part[t - o] : 0;
-    __syncthreads();
-    part[t] += v;
-    __syncthreads();
-  }
-  const unsigned before = t ? part[t - 1] : 0;
-  if (before < K && part[t] >= K) {
-    unsigned c = before;
-    for (int i = 0; i < 64; ++i) {
-      const unsigned h = hist[t * 64 + i];
-      if (c + h >= K) {
-        out[0] = t * 64 + i;
-        out[1] = c;
-        break;
-      }
-      c += h;
-    }
-  }
-}
-
-__global__ void k_topk_collect(const float* __restrict__ s, unsigned long long n, const unsigned* __restrict__ thr,
-                               int64_t* __restrict__ below, unsigned* __restrict__ nbelow, int64_t* __restrict__ eq,
-                               unsigned* __restrict__ neq, unsigned cap_below, unsigned cap_eq) {
-  const unsigned T = thr[0];
+  unsigned bad = 0;
   for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (unsigned long long)gridDim.x * blockDim.x) {
-    const unsigned b = order_key(s[i]) >> 16;
+    const float v = s[i];
+    const uint32_t key = order_key(v);
+    atomicAdd(hist + (key >> 16), 1u);
+    atomicAdd(c + (key >> 24), 1u);
+    bad += !isfinite(v);
+  }
+  if (bad) atomicAdd(nonfinite, bad);
+  __syncthreads();
+  for (int i = threadIdx.x; i < 256; i += blockDim.x)
+    if (c[i]) atomicAdd(coarse + i, c[i]);
+}
+
+// Inclusive prefix sum over a CTA of 256 threads (8 warps).
+__device__ __forceinline__ unsigned block_scan256(unsigned v, unsigned* warp_tot) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned y = __shfl_up_sync(0xFFFFFFFFu, v, o);
+    if (lane >= o) v += y;
+  }
+  if (lane == 31) warp_tot[warp] = v;
+  __syncthreads();
+  unsigned add = 0;
+  for (int w = 0; w < warp; ++w) add += warp_tot[w];
+  __syncthreads();
+  return v + add;
+}
+
+// Smallest bin T whose cumulative count reaches K, through the coarse
+// histogram (256 bins of 256 fine bins each) then the fine bins of the
+// chosen coarse bin.  out[0] = T, out[1] = count below T; out[2] = the first
+// bin not yet selected: 0, or with grow set one past the previous threshold
+// (out[0] on entry).  Also resets the collection's counters (cnt[0], cnt[1])
+// and its least left-out key (cnt[2]).  One CTA of 256 threads.
+__global__ void __launch_bounds__(256) k_topk_threshold(const unsigned* __restrict__ hist,
+                                                        const unsigned* __restrict__ coarse, unsigned K, int grow,
+                                                        unsigned* __restrict__ out, unsigned* __restrict__ cnt) {
+  __shared__ unsigned warp_tot[8];
+  __shared__ unsigned pick[2];
+  const unsigned t = threadIdx.x;
+  const unsigned prev = out[0];
+  if (t < 3) cnt[t] = t < 2 ? 0u : 0xFFFFFFFFu;   // the collection's counts and least left-out key
+  const unsigned cc = coarse[t];
+  const unsigned cum_c = block_scan256(cc, warp_tot);
+  if (cum_c - cc < K && cum_c >= K) {
+    pick[0] = t;
+    pick[1] = cum_c - cc;
+  }
+  __syncthreads();
+  const unsigned C = pick[0], base = pick[1];
+  const unsigned h = hist[C * 256 + t];
+  const unsigned cum = base + block_scan256(h, warp_tot);
+  if (cum - h < K && cum >= K) {
+    out[0] = C * 256 + t;
+    out[1] = cum - h;
+    out[2] = grow ? prev + 1 : 0;
+  }
+}
+
+// positions whose bin b has lo <= b < T (below) and b == T (eq), with
+// T = thr[0], lo = thr[2]: everything up to the threshold on the first
+// selection, only what is new on a growth round; and the least order key
+// among the positions left out (bins above T) into *key_out (one atomic per
+// warp; *key_out starts at ~0)
+__global__ void k_topk_collect(const float* __restrict__ s, unsigned long long n, const unsigned* __restrict__ thr,
+                               int64_t* __restrict__ below, unsigned* __restrict__ nbelow,
+                               int64_t* __restrict__ eq, unsigned* __restrict__ neq, unsigned cap_below,
+                               unsigned cap_eq, unsigned* __restrict__ key_out) {
+  const unsigned T = thr[0], lo = thr[2];
+  unsigned least = 0xFFFFFFFFu;
+  for (unsigned long long i0 = (unsigned long long)blockIdx.x * blockDim.x; i0 < n;
+       i0 += (unsigned long long)gridDim.x * blockDim.x) {
+    const unsigned long long i = i0 + threadIdx.x;
+    if (i >= n) break;
+    const uint32_t key = order_key(s[i]);
+    const unsigned b = key >> 16;
+    if (b > T) least = min(least, key);
+    if (b < lo || b > T) continue;
     if (b < T) {
       const unsigned k = atomicAdd(nbelow, 1u);
       if (k < cap_below) below[k] = (int64_t)i;
-    } else if (b == T) {
+    } else {
       const unsigned k = atomicAdd(neq, 1u);
       if (k < cap_eq) eq[k] = (int64_t)i;
     }
   }
+  least = __reduce_min_sync(0xFFFFFFFFu, least);
+  if ((threadIdx.x & 31) == 0 && least != 0xFFFFFFFFu) atomicMin(key_out, least);
 }
 
-// the scores of the first min(*n, cap) listed positions (n read on the device)
-__global__ void k_take_count(const float* __restrict__ s, const int64_t* __restrict__ idx,
-                             const unsigned* __restrict__ n, unsigned cap, float* __restrict__ out) {
-  const unsigned i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < cap && i < *n) out[i] = s[idx[i]];
+
+// Exact costs of a selection, one warp per selected candidate (warps stride
+// over the selection).  Each warp holds its candidate's chain table (Pp
+// uint16, copied from the space's cache) and its lanes' bitmaps (words x 32)
+// in its own part of shared memory, so no barrier spans the CTA; the cost is
+// the exhaustive search's warp routine.  The selection is the scored
+// positions listed in list_a (count *cnt_a, at most cap_a) followed by those
+// in list_b (*cnt_b, at most cap_b); with list_a null it is positions
+// 0 .. n_identity - 1.  A position maps to a candidate through the scored
+// factorisations (flist).  Outputs per entry, from entry out0 on (at most
+// out_cap entries in all): candidate index, primary and secondary (tiles),
+// score.
+__global__ void k_sel_costs(const ChainProg* __restrict__ progs, const Fact* __restrict__ facts,
+                            unsigned long long nchains, uint32_t P, uint32_t E0, uint32_t E1,
+                            uint32_t E2, int words, const uint16_t* __restrict__ gtab, uint32_t Pp,
+                            const uint32_t* __restrict__ flist, const int64_t* __restrict__ list_a,
+                            const unsigned* __restrict__ cnt_a, unsigned cap_a, const int64_t* __restrict__ list_b,
+                            const unsigned* __restrict__ cnt_b, unsigned cap_b, unsigned long long n_identity,
+                            const float* __restrict__ scores, unsigned long long out0, unsigned long long out_cap,
+                            int64_t* __restrict__ sel_idx, uint64_t* __restrict__ sel_p, uint64_t* __restrict__ sel_s,
+                            float* __restrict__ sel_y, int* __restrict__ status) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ uint64_t tab_bar[8];   // one per warp: its chain table's bulk copy
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const size_t per_warp = (size_t)Pp * 2 + (size_t)words * 32 * 4;   // Pp is a multiple of 8: 16-byte aligned
+  uint16_t* tab = reinterpret_cast<uint16_t*>(smem_raw + wib * per_warp);
+  uint32_t* bm = reinterpret_cast<uint32_t*>(smem_raw + wib * per_warp + (size_t)Pp * 2);
+  uint64_t* bar = &tab_bar[wib];
+  for (int w = 0; w < words; ++w) bm[w * 32 + lane] = 0;   // the routine leaves its bitmaps cleared
+  if (lane == 0) {
+    tc::mbar_init(bar, 1);
+    tc::fence_mbar_init();
+  }
+  __syncwarp();
+  uint32_t phase = 0;
+  unsigned long long na, n;
+  if (list_a) {
+    na = min(*cnt_a, cap_a);
+    n = na + min(*cnt_b, cap_b);
+  } else {
+    na = n = n_identity;
+  }
+  if (out0 >= out_cap) return;
+  n = min(n, out_cap - out0);   // entries beyond the arrays are dropped (the reduction sees the selection incomplete)
+  const uint32_t E[3] = {E0, E1, E2};
+  const unsigned long long nwarps = (unsigned long long)gridDim.x * (blockDim.x >> 5);
+  for (unsigned long long i = (unsigned long long)blockIdx.x * (blockDim.x >> 5) + wib; i < n; i += nwarps) {
+    const unsigned long long pos = !list_a ? i : (i < na ? (unsigned long long)list_a[i]
+                                                         : (unsigned long long)list_b[i - na]);
+    const unsigned long long j = pos / nchains, c = pos - j * nchains;
+    const unsigned long long fr = flist[j];
+    if (gtab) {
+      // the chain's cached table in one bulk copy (Pp * 2 bytes, 16-byte aligned rows)
+      if (lane == 0) {
+        tc::fence_proxy_async();   // the previous candidate's reads of tab come first
+        tc::mbar_expect_tx(bar, Pp * 2);
+        tc::bulk_g2s(tab, gtab + c * Pp, Pp * 2, bar);
+      }
+      const bool ok = __all_sync(0xFFFFFFFFu, tc::mbar_wait(bar, phase, kWaitLimit));
+      phase ^= 1;
+      if (!ok) {
+        if (lane == 0) atomicExch(status, MP_ETIMEOUT);
+        tc::mbar_wait(bar, phase ^ 1, kWaitLimit);   // the copy may still land: let it, then stop
+        return;
+      }
+    } else {   // the space's tables were too large to cache: resolve every flat index
+      const ChainProg cp = progs[c];
+      for (uint32_t b = lane; b < P; b += 32) tab[b] = (uint16_t)resolve_node(cp, b);
+      __syncwarp();
+    }
+    const uint32_t f[3] = {facts[fr].f[0], facts[fr].f[1], facts[fr].f[2]};
+    const unsigned long long sec = secondary_cost_warp<true>(tab, bm, 32, words, E, f, lane);
+    if (lane == 0) {
+      sel_idx[out0 + i] = (int64_t)(fr * nchains + c);
+      sel_p[out0 + i] = primary_cost(E, f);
+      sel_s[out0 + i] = sec;
+      sel_y[out0 + i] = scores[pos];
+    }
+    __syncwarp();   // the next candidate's table overwrites this one
+  }
+}
+
+// What the host reads back after a selection: the selection's argmin and
+// the acceptance test, decided on the device.
+struct SelResult {
+  int64_t idx;                 // winner's candidate index
+  unsigned long long p, s;     // winner's primary / secondary (tiles)
+  unsigned n;                  // selection size
+  int cert;                    // 0 none, 1 every threat evaluated, 2 lower bound, 3 margin rule
+  float tau;                   // the least score left out (infinite: none)
+  float y_best;                // the winner's regression target
+  float over;                  // largest score - target on the selection
+  float margin;                // tau - y_best - the calibrated bound (margin rule)
+  int complete;                // every entry at or below the threshold bin was evaluated
+  int pad;
+};
+
+// One CTA of 256 threads: argmin of (primary, secondary, index) over the
+// selection (the n_prev entries of earlier rounds and this round's new
+// ones), then the acceptance rule.  Certificates: (1) the selection
+// holds every candidate of least primary (threats_pmin of them), or (2) the
+// winner's secondary reaches min_lb, a lower bound on every least-primary
+// candidate's secondary.  Margin rule (heuristic): every candidate left out
+// scored at least tau; it can beat the winner only if the model
+// overestimated it by more than tau - y_best, which the calibrated bound
+// says does not happen (accepted when tau - y_best exceeds it).
+__global__ void __launch_bounds__(256) k_sel_reduce(const unsigned* __restrict__ cnt, unsigned cap_a,
+                                                      unsigned cap_b, unsigned n_prev, int prev_complete,
+                                                      unsigned out_cap, const unsigned* __restrict__ thr,
+                                                      const int64_t* __restrict__ sel_idx,
+                                                      const uint64_t* __restrict__ sel_p,
+                                                      const uint64_t* __restrict__ sel_s,
+                                                      const float* __restrict__ sel_y, unsigned long long pmin,
+                                                      unsigned long long min_lb, unsigned long long threats_pmin,
+                                                      float rule_bound, const unsigned* __restrict__ nonfinite,
+                                                      SelResult* __restrict__ out) {
+  __shared__ Key redk[32];
+  __shared__ float redo[32];
+  __shared__ unsigned redn[32];
+  const unsigned n_new = min(cnt[0], cap_a) + min(cnt[1], cap_b);
+  const unsigned n = min(n_prev + n_new, out_cap);
+  Key best{~0ull, ~0ull, ~0ull};
+  float over = -INFINITY;
+  unsigned n_pmin = 0;
+  for (unsigned i = threadIdx.x; i < n; i += blockDim.x) {
+    const Key k{sel_p[i], sel_s[i], (unsigned long long)sel_idx[i]};
+    if (key_less(k, best)) best = k;
+    over = fmaxf(over, sel_y[i] - target_of(k.p, k.s, pmin));
+    n_pmin += k.p == pmin;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    over = fmaxf(over, __shfl_down_sync(0xFFFFFFFFu, over, o));
+    n_pmin += __shfl_down_sync(0xFFFFFFFFu, n_pmin, o);
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) {
+    redo[warp] = over;
+    redn[warp] = n_pmin;
+  }
+  block_argmin(best, redk);   // synchronises the CTA; warp 0 holds the result
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+      over = fmaxf(over, redo[w]);
+      n_pmin += redn[w];
+    }
+    SelResult r;
+    r.idx = (int64_t)best.idx;
+    r.p = best.p;
+    r.s = best.s;
+    r.n = n;
+    r.complete = prev_complete && cnt[0] <= cap_a && cnt[1] <= cap_b && n_prev + n_new <= out_cap;
+    r.tau = cnt[2] == 0xFFFFFFFFu ? INFINITY : key_value(cnt[2]);   // the least score left out
+    r.y_best = target_of(best.p, best.s, pmin);
+    r.over = over;
+    r.margin = r.tau - r.y_best - rule_bound;
+    const bool at_pmin = n > 0 && best.p == pmin;
+    r.cert = 0;
+    if (at_pmin && n_pmin == threats_pmin) r.cert = 1;
+    else if (at_pmin && best.s <= min_lb) r.cert = 2;
+    else if (at_pmin && r.complete && *nonfinite == 0 && isfinite(rule_bound) && r.margin > 0.f) r.cert = 3;
+    r.pad = 0;
+    *out = r;
+  }
 }
 
 // ------------------------------------------------------------ host side
@@ -576,7 +786,7 @@ struct Pool {
   }
 };
 
-Pool g_pool_q, g_pool_s;   // query data; scores and selection
+Pool g_pool_s;   // scores and selection
 
 Pool g_pool_img;   // feature tile images of the scoring kernels
 
@@ -715,14 +925,14 @@ int prepare_query(const mp_search_query& q, Prepared& pq, cudaStream_t st) {
   pq.d_fnode = pq.L->fnode;
   pq.d_fdiv = pq.L->fdiv;
   const uint32_t nd = pq.L->nd;
-  unsigned long long* d_prim = (unsigned long long*)g_pool_q.get(std::max<size_t>(a256(NF * 8), 1u << 20));
-  if (!d_prim) return MP_ENOMEM;
-  k_primaries<<<(unsigned)((NF + 127) / 128), 128, 0, st>>>(pq.d_facts, (uint32_t)NF, (uint32_t)q.M, (uint32_t)q.N,
-                                                            (uint32_t)q.K, d_prim);
-  count_launch();
+  // primaries in closed form on the host (no device round trip)
+  const uint32_t E[3] = {(uint32_t)q.M, (uint32_t)q.N, (uint32_t)q.K};
   pq.prim.resize(NF);
-  MP_CUDA_TRY(cudaMemcpyAsync(pq.prim.data(), d_prim, NF * 8, cudaMemcpyDeviceToHost, st));
-  MP_CUDA_TRY(cudaStreamSynchronize(st));
+  for (size_t fr = 0; fr < NF; ++fr) {
+    const uint32_t f[3] = {(uint32_t)pq.S.c->facts[fr][0], (uint32_t)pq.S.c->facts[fr][1],
+                           (uint32_t)pq.S.c->facts[fr][2]};
+    pq.prim[fr] = primary_cost(E, f);
+  }
   QInfo& Q = pq.Q;
   std::memset(&Q, 0, sizeof(Q));
   Q.E[0] = (uint32_t)q.M;
@@ -793,10 +1003,6 @@ void mlpk_gather(const bf16* X, const float* T, const int64_t* perm, int B, bf16
   count_launch();
 }
 
-__global__ void k_take(const float* __restrict__ s, const int64_t* __restrict__ idx, int n, float* __restrict__ out) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) out[i] = s[idx[i]];
-}
 
 float host_target(unsigned long long p, unsigned long long sc, unsigned long long pmin) {
   const float pn = (float)((double)p / (double)std::max(pmin, 1ull) - 1.0);
@@ -875,13 +1081,18 @@ extern "C" int mp_mlp_train_search(mp_mlp* h, const mp_search_query* queries, in
   std::iota(perm.begin(), perm.end(), 0);
   int64_t* d_perm = nullptr;
   if (!rc && cudaMalloc(&d_perm, total * 8) != cudaSuccess) rc = MP_ENOMEM;
+  // the step size follows a cosine from lr down to 5% of it over the run
+  const double steps_total = (double)epochs * (double)(total / (size_t)batch);
+  double step_i = 0.0;
   for (int e = 0; e < epochs && !rc; ++e) {
     for (size_t i = total - 1; i > 0; --i) std::swap(perm[i], perm[splitmix(rng) % (i + 1)]);
     if (cudaMemcpyAsync(d_perm, perm.data(), total * 8, cudaMemcpyHostToDevice, st) != cudaSuccess) { rc = MP_ECUDA; break; }
     for (size_t b0 = 0; b0 + batch <= total && !rc; b0 += batch) {
       mp::lrn::mlpk_gather(X, T, d_perm + b0, batch, Xb, Tb, st);
       MP_CUDA_TRY(cudaMemsetAsync(h->status, 0, 4, st));
-      rc = mlpk::train_step(h, Xb, Tb, batch, lr, st);
+      const double cosine = 0.5 * (1.0 + std::cos(3.141592653589793 * step_i / std::max(steps_total, 1.0)));
+      step_i += 1.0;
+      rc = mlpk::train_step(h, Xb, Tb, batch, (float)(lr * (0.05 + 0.95 * cosine)), st);
     }
     float l = 0.f;
     cudaMemcpyAsync(&l, h->scalar, 4, cudaMemcpyDeviceToHost, st);
@@ -895,6 +1106,132 @@ extern "C" int mp_mlp_train_search(mp_mlp* h, const mp_search_query* queries, in
   if (final_loss) *final_loss = loss;
   return rc;
 }
+
+namespace mp {
+namespace lrn {
+
+// Counter words after the histograms that k_sel_init clears: cnt (4), nonfinite (1).
+constexpr unsigned kInitWords = 5;
+
+// Entries of the selection arrays: a selection of up to cap_a + cap_b
+// candidates plus the previous rounds' (at most as many again).
+size_t sel_capacity(unsigned cap_a, unsigned cap_b) { return 2 * ((size_t)cap_a + cap_b); }
+
+// Device buffers of one learned search (scores, histogram, selection).
+struct SelBufs {
+  float* sc;
+  unsigned *hist, *coarse, *thr, *cnt, *nonfinite;
+  int64_t *below, *eq, *sel_idx;
+  uint64_t *sel_p, *sel_s;
+  float* sel_y;
+  uint32_t* fl;
+  SelResult* res;
+};
+
+int sel_bufs(uint64_t ncand, unsigned cap_a, unsigned cap_b, size_t nfl, SelBufs& b) {
+  const size_t cap = sel_capacity(cap_a, cap_b);
+  // hist (65536 words), coarse (256 words), then the counters k_sel_init
+  // also clears (cnt, nonfinite: kInitWords); thr is kept across rounds
+  const size_t o_sc = 0, o_hist = a256(ncand * 4), o_coarse = o_hist + 65536 * 4, o_cnt = o_coarse + 256 * 4,
+               o_nf = o_cnt + 16, o_thr = o_hist + a256((65536 + 256 + kInitWords) * 4), o_below = o_thr + 256,
+               o_eq = o_below + a256((size_t)cap_a * 8),
+               o_idx = o_eq + a256((size_t)cap_b * 8), o_p = o_idx + a256(cap * 8), o_s = o_p + a256(cap * 8),
+               o_y = o_s + a256(cap * 8), o_fl = o_y + a256(cap * 4), o_res = o_fl + a256(nfl * 4),
+               end = o_res + 256;
+  char* w = g_pool_s.get(end);
+  if (!w) return MP_ENOMEM;
+  b.sc = (float*)(w + o_sc);
+  b.hist = (unsigned*)(w + o_hist);
+  b.coarse = (unsigned*)(w + o_coarse);
+  b.thr = (unsigned*)(w + o_thr);
+  b.cnt = (unsigned*)(w + o_cnt);
+  b.nonfinite = (unsigned*)(w + o_nf);
+  b.below = (int64_t*)(w + o_below);
+  b.eq = (int64_t*)(w + o_eq);
+  b.sel_idx = (int64_t*)(w + o_idx);
+  b.sel_p = (uint64_t*)(w + o_p);
+  b.sel_s = (uint64_t*)(w + o_s);
+  b.sel_y = (float*)(w + o_y);
+  b.fl = (uint32_t*)(w + o_fl);
+  b.res = (SelResult*)(w + o_res);
+  return MP_OK;
+}
+
+// Exact costs of the selection (or, with list_a null, of scored positions
+// 0 .. n_identity - 1) into b.sel_*.
+int launch_sel_costs(const mp_search_query& q, const Prepared& pq, const SelBufs& b, const int64_t* list_a,
+                     const unsigned* cnt_a, unsigned cap_a, const int64_t* list_b, const unsigned* cnt_b,
+                     unsigned cap_b, unsigned long long n_identity, unsigned long long out0,
+                     unsigned long long out_cap, int* status, cudaStream_t st) {
+  // one warp per candidate, each with its own chain table and bitmaps:
+  // up to 4 warps per CTA within about 100 KB of shared memory
+  const SearchSpace& S = pq.S;
+  const uint32_t Pp = (uint32_t)((q.procs + 7) & ~7);
+  const size_t per_warp = (size_t)Pp * 2 + (size_t)S.words * 32 * 4;
+  const int wpc = (int)std::max<size_t>(1, std::min<size_t>(4, (size_t)(100 * 1024) / per_warp));
+  const size_t smem = per_warp * wpc;
+  if (smem > 227 * 1024) return MP_ENOTSUP;
+  if (smem > 48 * 1024)
+    MP_CUDA_TRY(cudaFuncSetAttribute(k_sel_costs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = 0;
+  MP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sel_costs, 32 * wpc, smem));
+  const unsigned long long most = list_a ? (unsigned long long)cap_a + cap_b : n_identity;
+  const unsigned grid = (unsigned)std::max<unsigned long long>(
+      1, std::min<unsigned long long>((most + wpc - 1) / wpc,
+                                      (unsigned long long)sm_count_l() * std::max(per_sm, 1)));
+  k_sel_costs<<<grid, 32 * wpc, smem, st>>>(pq.d_progs, pq.d_facts, (unsigned long long)S.c->chains.size(),
+                                            (uint32_t)q.procs, (uint32_t)q.M, (uint32_t)q.N, (uint32_t)q.K, S.words,
+                                            pq.D->tab, Pp, b.fl, list_a,
+                                            cnt_a, cap_a, list_b, cnt_b, cap_b, n_identity, b.sc, out0, out_cap,
+                                            b.sel_idx, b.sel_p, b.sel_s, b.sel_y, status);
+  count_launch();
+  MP_CUDA_TRY(cudaGetLastError());
+  return MP_OK;
+}
+
+// Factorisations of least primary cost (or every one) and the scored pool.
+std::vector<uint32_t> pool_facts(const Prepared& pq, bool all) {
+  std::vector<uint32_t> flist;
+  for (uint64_t fr = 0; fr < pq.prim.size(); ++fr)
+    if (all || pq.prim[fr] == pq.Q.pmin) flist.push_back((uint32_t)fr);
+  return flist;
+}
+
+// Three timing events per host thread and device (created on first use).
+cudaEvent_t* phase_events() {
+  constexpr int kMaxDevices = 64;
+  struct Ev {
+    cudaEvent_t e[3] = {nullptr, nullptr, nullptr};
+    bool ok = false;
+    ~Ev() {
+      for (cudaEvent_t x : e)
+        if (x) cudaEventDestroy(x);
+    }
+  };
+  thread_local Ev per_device[kMaxDevices];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  Ev& v = per_device[dev];
+  if (!v.ok) {
+    v.ok = true;
+    for (cudaEvent_t& x : v.e) v.ok = v.ok && cudaEventCreate(&x) == cudaSuccess;
+    if (!v.ok) {
+      cudaGetLastError();
+      return nullptr;
+    }
+  }
+  return v.e;
+}
+
+// Margin rule: accepted when tau - y_best exceeds the calibrated bound with
+// this much head-room (relative, absolute).
+constexpr float kMarginScale = 1.25f, kMarginSlack = 0.01f;
+
+}  // namespace lrn
+}  // namespace mp
 
 extern "C" int mp_learned_search(mp_mlp* h, const mp_search_query* query, int K, int flags, mp_search_result* out,
                                  mp_learned_stats* stats, void* stream) {
@@ -915,55 +1252,17 @@ extern "C" int mp_learned_search(mp_mlp* h, const mp_search_query* query, int K,
   // the candidates that can win: every chain with a factorisation of least
   // primary cost (exact, closed form); MP_LEARNED_SCORE_ALL scores them all
   const bool all = (flags & MP_LEARNED_SCORE_ALL) != 0;
-  std::vector<uint32_t> flist;
-  for (uint64_t fr = 0; fr < NF; ++fr)
-    if (all || pq.prim[fr] == pq.Q.pmin) flist.push_back((uint32_t)fr);
+  const std::vector<uint32_t> flist = pool_facts(pq, all);
   const uint64_t ncand = NC * flist.size();
+  uint64_t n_pmin_facts = 0;
+  for (uint64_t fr = 0; fr < NF; ++fr) n_pmin_facts += pq.prim[fr] == pq.Q.pmin;
   // the selection grows by 8x (up to kMaxSel) while the acceptance rule fails
   const unsigned kMaxSel = 1u << 16;
-  const unsigned Kmax = (unsigned)std::min<uint64_t>(std::max<unsigned>((unsigned)K, kMaxSel), ncand);
-  const unsigned cap_eq = 1u << 16;
-  const size_t o_sc = 0, o_hist = a256(ncand * 4), o_thr = o_hist + a256(65536 * 4), o_cnt = o_thr + 256,
-               o_below = o_cnt + 256, o_eq = o_below + a256((size_t)Kmax * 8),
-               o_sel = o_eq + a256((size_t)cap_eq * 8), o_p = o_sel + a256((size_t)Kmax * 8),
-               o_s = o_p + a256((size_t)Kmax * 8), o_y = o_s + a256((size_t)Kmax * 8),
-               o_ye = o_y + a256((size_t)Kmax * 4), o_fl = o_ye + a256((size_t)cap_eq * 4),
-               end = o_fl + a256(flist.size() * 4);
-  char* w = g_pool_s.get(end);
-  if (!w) return MP_ENOMEM;
-  float* d_sc = (float*)(w + o_sc);
-  unsigned* d_hist = (unsigned*)(w + o_hist);
-  unsigned* d_thr = (unsigned*)(w + o_thr);
-  unsigned* d_cnt = (unsigned*)(w + o_cnt);
-  int64_t* d_below = (int64_t*)(w + o_below);
-  int64_t* d_eq = (int64_t*)(w + o_eq);
-  int64_t* d_sel = (int64_t*)(w + o_sel);
-  uint64_t* d_p = (uint64_t*)(w + o_p);
-  uint64_t* d_s = (uint64_t*)(w + o_s);
-  float* d_y = (float*)(w + o_y);
-  float* d_ye = (float*)(w + o_ye);
-  uint32_t* d_fl = (uint32_t*)(w + o_fl);
-  MP_CUDA_TRY(cudaMemcpyAsync(d_fl, flist.data(), flist.size() * 4, cudaMemcpyHostToDevice, st));
-  if (stats) stats->ms_prepare = ms_since(t_phase);
-  t_phase = clk::now();
-  // ---- score every candidate
-  MP_CUDA_TRY(cudaMemsetAsync(h->status, 0, 4, st));
-  if ((rc = score_candidates(h, pq, d_fl, ncand, d_sc, st))) return rc;
-  MP_CUDA_TRY(cudaMemsetAsync(d_hist, 0, 65536 * 4, st));
-  const unsigned gb = (unsigned)std::min<uint64_t>((ncand + 255) / 256, (uint64_t)sm_count_l() * 8);
-  k_topk_hist<<<gb, 256, 0, st>>>(d_sc, ncand, d_hist);
-  count_launch();
-  MP_CUDA_TRY(cudaGetLastError());
-  int status = 0;
-  MP_CUDA_TRY(cudaMemcpyAsync(&status, h->status, 4, cudaMemcpyDeviceToHost, st));
-  MP_CUDA_TRY(cudaStreamSynchronize(st));
-  if (status) return status;
-  if (stats) {
-    stats->ms_model = ms_since(t_phase);
-    stats->n_scored = (int64_t)ncand;
-  }
-  t_phase = clk::now();
-
+  const unsigned cap_a = (unsigned)std::min<uint64_t>(std::max<unsigned>((unsigned)K, kMaxSel), ncand);
+  const unsigned cap_b = 1u << 16;
+  SelBufs b;
+  if ((rc = sel_bufs(ncand, cap_a, cap_b, flist.size(), b))) return rc;
+  MP_CUDA_TRY(cudaMemcpyAsync(b.fl, flist.data(), flist.size() * 4, cudaMemcpyHostToDevice, st));
   // a lower bound on the secondary of every candidate that can win (the
   // least-primary factorisations); reaching it certifies the winner
   uint64_t min_lb = ~0ull;
@@ -972,160 +1271,100 @@ extern "C" int mp_learned_search(mp_mlp* h, const mp_search_query* query, int K,
     if (pq.prim[fr] == pq.Q.pmin) {
       const uint32_t f[3] = {(uint32_t)pq.S.c->facts[fr][0], (uint32_t)pq.S.c->facts[fr][1],
                              (uint32_t)pq.S.c->facts[fr][2]};
-      const uint64_t lb = secondary_lower_bound(pq.Q.E, f, pq.Q.n, pq.Q.g);
-      lb_of[fr] = lb;
-      if (lb < min_lb) min_lb = lb;
+      lb_of[fr] = secondary_lower_bound(pq.Q.E, f, pq.Q.n, pq.Q.g);
+      min_lb = std::min(min_lb, lb_of[fr]);
     }
-  // ---- the Kc best scores, evaluated exactly; Kc grows until accepted
-  auto key = [](float v) { return std::isnan(v) ? INFINITY : v; };   // NaN orders last
-  const unsigned long long tb = q.tile_bytes;
+  SelResult* hres = (SelResult*)g_host_stage.get(256);
+  if (!hres) return MP_ENOMEM;
+  int* hstatus = (int*)((char*)hres + 128);
+  if (stats) stats->ms_prepare = ms_since(t_phase);
+  t_phase = clk::now();
+  // phase boundaries on the stream (device time): scoring start, scores
+  // ranked, last selection reduced
+  cudaEvent_t* ev = stats ? phase_events() : nullptr;
+  if (stats && !ev) return MP_ECUDA;
+  if (ev) MP_CUDA_TRY(cudaEventRecord(ev[0], st));
+  // ---- score every candidate of the pool, histogram of the scores
+  MP_CUDA_TRY(cudaMemsetAsync(h->status, 0, 4, st));
+  k_sel_init<<<64, 256, 0, st>>>(b.hist, kInitWords);
+  count_launch();
+  if ((rc = score_candidates(h, pq, b.fl, ncand, b.sc, st))) return rc;
+  const unsigned gb = (unsigned)std::min<uint64_t>((ncand + 255) / 256, (uint64_t)sm_count_l() * 8);
+  k_topk_hist<<<gb, 256, 0, st>>>(b.sc, ncand, b.hist, b.coarse, b.nonfinite);
+  count_launch();
+  MP_CUDA_TRY(cudaGetLastError());
+  if (ev) MP_CUDA_TRY(cudaEventRecord(ev[1], st));
+  if (stats) stats->n_scored = (int64_t)ncand;
+  // ---- the Kc best scores (with the rest of the threshold bin), evaluated
+  // exactly and reduced on the device; one round trip per selection
+  const float rule_bound = std::isfinite(h->margin_bound) ? kMarginScale * std::max(0.f, (float)h->margin_bound) +
+                                                                kMarginSlack
+                                                          : INFINITY;
   unsigned Kc = (unsigned)std::min<uint64_t>((uint64_t)K, ncand);
-  std::vector<int64_t> sel, pos;
-  std::vector<uint64_t> pb, sb;
-  std::vector<float> yh;
-  int64_t bi = 0;
-  bool accept = false, certified = false;
-  int cert_kind_last = 0;
-  unsigned long long p_best_last = ~0ull, s_best_last = ~0ull;   // tiles
-  double margin = 0.0;
-  float over = 0.f;
+  const unsigned long long out_cap = sel_capacity(cap_a, cap_b);
+  SelResult r;
+  std::memset(&r, 0, sizeof(r));
+  r.complete = 1;
   int rounds = 0;
   for (;;) {
-    ++rounds;
-    MP_CUDA_TRY(cudaMemsetAsync(d_cnt, 0, 16, st));
-    k_topk_threshold<<<1, 1024, 0, st>>>(d_hist, Kc, d_thr);
-    k_topk_collect<<<gb, 256, 0, st>>>(d_sc, ncand, d_thr, d_below, d_cnt, d_eq, d_cnt + 1, Kc, cap_eq);
+    // a growth round evaluates only the candidates it adds (the bins past
+    // the previous threshold) and reduces them with the earlier ones
+    const unsigned n_prev = rounds ? r.n : 0;
+    const int prev_complete = r.complete;
+    k_topk_threshold<<<1, 256, 0, st>>>(b.hist, b.coarse, Kc, rounds ? 1 : 0, b.thr, b.cnt);
+    k_topk_collect<<<gb, 256, 0, st>>>(b.sc, ncand, b.thr, b.below, b.cnt, b.eq, b.cnt + 1, Kc, cap_b, b.cnt + 2);
     count_launch(2);
     MP_CUDA_TRY(cudaGetLastError());
-    // one round trip: the counts, the threshold bin's first entries with their
-    // scores and the positions below the threshold (a larger bin takes a second)
-    constexpr unsigned kEqFirst = 4096;
-    const size_t sb_cnt = 0, sb_eq = 256, sb_eqs = sb_eq + (size_t)kEqFirst * 8,
-                 sb_pos = sb_eqs + (size_t)kEqFirst * 4, sb_end = sb_pos + (size_t)Kmax * 8;
-    char* hs = g_host_stage.get(std::max<size_t>(sb_end, (size_t)Kmax * 20 + 256));
-    if (!hs) return MP_ENOMEM;
-    k_take_count<<<(kEqFirst + 255) / 256, 256, 0, st>>>(d_sc, d_eq, d_cnt + 1, std::min(kEqFirst, cap_eq), d_ye);
+    ++rounds;
+    if ((rc = launch_sel_costs(q, pq, b, b.below, b.cnt, Kc, b.eq, b.cnt + 1, cap_b, 0, n_prev, out_cap, h->status,
+                               st)))
+      return rc;
+    k_sel_reduce<<<1, 256, 0, st>>>(b.cnt, Kc, cap_b, n_prev, prev_complete, (unsigned)out_cap, b.thr, b.sel_idx,
+                                     b.sel_p, b.sel_s, b.sel_y, pq.Q.pmin, min_lb, NC * n_pmin_facts, rule_bound,
+                                     b.nonfinite, b.res);
     count_launch();
-    MP_CUDA_TRY(cudaMemcpyAsync(hs + sb_cnt, d_cnt, 8, cudaMemcpyDeviceToHost, st));
-    MP_CUDA_TRY(cudaMemcpyAsync(hs + sb_eq, d_eq, (size_t)std::min(kEqFirst, cap_eq) * 8, cudaMemcpyDeviceToHost, st));
-    MP_CUDA_TRY(cudaMemcpyAsync(hs + sb_eqs, d_ye, (size_t)std::min(kEqFirst, cap_eq) * 4, cudaMemcpyDeviceToHost, st));
-    MP_CUDA_TRY(cudaMemcpyAsync(hs + sb_pos, d_below, (size_t)Kc * 8, cudaMemcpyDeviceToHost, st));
+    MP_CUDA_TRY(cudaGetLastError());
+    if (ev) MP_CUDA_TRY(cudaEventRecord(ev[2], st));
+    MP_CUDA_TRY(cudaMemcpyAsync(hres, b.res, sizeof(SelResult), cudaMemcpyDeviceToHost, st));
+    MP_CUDA_TRY(cudaMemcpyAsync(hstatus, h->status, 4, cudaMemcpyDeviceToHost, st));
     MP_CUDA_TRY(cudaStreamSynchronize(st));
-    const unsigned* cnt = (const unsigned*)(hs + sb_cnt);
-    const unsigned nbelow = std::min(cnt[0], Kc), neq = std::min(cnt[1], cap_eq);
-    // the threshold bin, ordered by (score, index) for a deterministic choice
-    std::vector<int64_t> eq(neq);
-    std::vector<float> eqs(neq);
-    const unsigned first = std::min(neq, kEqFirst);
-    std::memcpy(eq.data(), hs + sb_eq, (size_t)first * 8);
-    std::memcpy(eqs.data(), hs + sb_eqs, (size_t)first * 4);
-    pos.assign((const int64_t*)(hs + sb_pos), (const int64_t*)(hs + sb_pos) + nbelow);
-    if (neq > first) {
-      const unsigned rest = neq - first;
-      MP_CUDA_TRY(cudaMemcpyAsync(eq.data() + first, d_eq + first, (size_t)rest * 8, cudaMemcpyDeviceToHost, st));
-      k_take<<<(rest + 255) / 256, 256, 0, st>>>(d_sc, d_eq + first, (int)rest, d_ye + first);
-      count_launch();
-      MP_CUDA_TRY(cudaMemcpyAsync(eqs.data() + first, d_ye + first, (size_t)rest * 4, cudaMemcpyDeviceToHost, st));
-      MP_CUDA_TRY(cudaStreamSynchronize(st));
-    }
-    std::vector<uint32_t> ord(neq);
-    std::iota(ord.begin(), ord.end(), 0u);
-    std::sort(ord.begin(), ord.end(), [&](uint32_t a, uint32_t b) {
-      const float ka = key(eqs[a]), kb = key(eqs[b]);
-      return ka < kb || (ka == kb && eq[a] < eq[b]);
-    });
-    for (uint32_t i = 0; i < neq && pos.size() < Kc; ++i) pos.push_back(eq[ord[i]]);
-    const int64_t nsel = (int64_t)pos.size();
-    if (nsel == 0) MP_CUDA_TRY(cudaErrorUnknown);   // the selection kernels produced nothing
-    sel = pos;   // positions in the scored list -> candidate indices
-    for (auto& v : sel) {
-      const uint64_t j = (uint64_t)v / NC;
-      v = (int64_t)((uint64_t)flist[j] * NC + ((uint64_t)v - j * NC));
-    }
-    MP_CUDA_TRY(cudaMemcpyAsync(d_sel, sel.data(), (size_t)nsel * 8, cudaMemcpyHostToDevice, st));
-    if ((rc = candidate_costs_dev(q, pq.S, *pq.D, d_sel, nsel, d_p, d_s, st))) return rc;
-    MP_CUDA_TRY(cudaMemcpyAsync(d_sel, pos.data(), (size_t)nsel * 8, cudaMemcpyHostToDevice, st));
-    k_take<<<(unsigned)((nsel + 255) / 256), 256, 0, st>>>(d_sc, d_sel, (int)nsel, d_y);
-    count_launch();
-    {
-      char* hp = g_host_stage.get((size_t)nsel * 20 + 256);
-      if (!hp) return MP_ENOMEM;
-      MP_CUDA_TRY(cudaMemcpyAsync(hp, d_p, (size_t)nsel * 8, cudaMemcpyDeviceToHost, st));
-      MP_CUDA_TRY(cudaMemcpyAsync(hp + (size_t)nsel * 8, d_s, (size_t)nsel * 8, cudaMemcpyDeviceToHost, st));
-      MP_CUDA_TRY(cudaMemcpyAsync(hp + (size_t)nsel * 16, d_y, (size_t)nsel * 4, cudaMemcpyDeviceToHost, st));
-      MP_CUDA_TRY(cudaStreamSynchronize(st));
-      pb.assign((const uint64_t*)hp, (const uint64_t*)hp + nsel);
-      sb.assign((const uint64_t*)(hp + (size_t)nsel * 8), (const uint64_t*)(hp + (size_t)nsel * 8) + nsel);
-      yh.assign((const float*)(hp + (size_t)nsel * 16), (const float*)(hp + (size_t)nsel * 16) + nsel);
-    }
-    bi = 0;
-    for (int64_t i = 1; i < nsel; ++i) {
-      const bool less = pb[i] < pb[bi] || (pb[i] == pb[bi] && (sb[i] < sb[bi] || (sb[i] == sb[bi] && sel[i] < sel[bi])));
-      if (less) bi = i;
-    }
-    const unsigned long long p_best = pb[bi] / tb;
-    // certificate: every candidate whose primary is no higher than the
-    // winner's was evaluated exactly
-    uint64_t threats = 0, threats_in = 0;
-    for (uint64_t fr = 0; fr < NF; ++fr)
-      if (pq.prim[fr] <= p_best) threats += NC;
-    for (int64_t i = 0; i < nsel; ++i)
-      if (pb[i] / tb <= p_best) ++threats_in;
-    certified = threats == threats_in;
-    int cert_kind = certified ? 1 : 0;
-    if (!certified && p_best == pq.Q.pmin && sb[bi] / tb <= min_lb) {
-      certified = true;   // no chain of any least-primary factorisation does better
-      cert_kind = 2;
-    }
-    // margin: a candidate left out scored at least tau (the largest selected
-    // score); it beats the winner only if its true target lies below the
-    // winner's, i.e. if the model overestimated it by more than
-    // tau - y_best.  The largest overestimation seen on the selection
-    // (times 1.5) bounds that.
-    float tau = -1e30f;
-    bool finite = true;
-    over = 0.f;
-    for (int64_t i = 0; i < nsel; ++i) {
-      const float yt = host_target(pb[i] / tb, sb[i] / tb, pq.Q.pmin);
-      finite = finite && std::isfinite(yh[i]);
-      over = std::max(over, yh[i] - yt);
-      tau = std::max(tau, yh[i]);
-    }
-    if (!finite) over = INFINITY;   // no margin from a model that returned NaN / inf
-    const float y_best = host_target(p_best, sb[bi] / tb, pq.Q.pmin);
-    margin = (double)tau - y_best - 1.5 * over - 1e-3;
-    cert_kind_last = cert_kind;
-    p_best_last = p_best;
-    s_best_last = sb[bi] / tb;
-    accept = certified || (p_best == pq.Q.pmin && margin > 0.0 && nsel == (int64_t)Kc);
-    if (stats) stats->n_exact += nsel;
-    if (accept || (flags & MP_LEARNED_NO_FALLBACK)) break;
-    // grow while the next selection stays a small part of the scored set;
-    // beyond that the exhaustive search (which shares each chain's table
-    // over its factorisations) is the cheaper way to an exact answer
-    const uint64_t next = (uint64_t)Kc * 8;
-    if (next > kMaxSel || next * 4 > ncand) break;
+    if (*hstatus) return *hstatus;
+    r = *hres;
+    if (r.n == 0) MP_CUDA_TRY(cudaErrorUnknown);   // the selection kernels produced nothing
+    if (stats) stats->n_exact += r.n;
+    if (r.cert || (flags & MP_LEARNED_NO_FALLBACK)) break;
+    // grow 2x while the selection stays within half of the scored set and
+    // complete; beyond that the exhaustive search (which shares each chain's
+    // table over its factorisations) is the cheaper way to an exact answer
+    const uint64_t next = (uint64_t)Kc * 2;
+    if (!r.complete || next > kMaxSel || next * 2 > ncand) break;
     Kc = (unsigned)next;
   }
   if (stats) {
-    stats->ms_exact = ms_since(t_phase);
-    stats->certified = cert_kind_last;
-    stats->margin = margin;
-    stats->max_overestimate = over;
+    float m = 0.f, e = 0.f;
+    MP_CUDA_TRY(cudaEventElapsedTime(&m, ev[0], ev[1]));
+    MP_CUDA_TRY(cudaEventElapsedTime(&e, ev[1], ev[2]));
+    stats->ms_model = m;
+    stats->ms_exact = e;
+    stats->ms_wall = ms_since(t_phase);
+    stats->certified = r.cert;
+    stats->margin = r.margin;
+    stats->max_overestimate = r.over;
+    stats->margin_bound = rule_bound;
     stats->rounds = rounds;
-    stats->n_selected = (int64_t)sel.size();
+    stats->n_selected = r.n;
   }
-  if (!accept && !(flags & MP_LEARNED_NO_FALLBACK)) {
+  if (!r.cert && !(flags & MP_LEARNED_NO_FALLBACK)) {
     t_phase = clk::now();
     mp_search_query qf = q;
     qf.flags = 0;
     // the selection's winner bounds the secondary the search must look for,
     // and factorisations whose lower bound lies above it need no scan
-    const bool bounded = p_best_last == pq.Q.pmin;
+    const bool bounded = r.p == pq.Q.pmin;
     std::vector<uint8_t> skip(NF, 0);
     if (bounded)
-      for (uint64_t fr = 0; fr < NF; ++fr) skip[fr] = pq.prim[fr] == pq.Q.pmin && lb_of[fr] > s_best_last;
-    rc = exhaustive_search(qf, out, st, bounded ? s_best_last : ~0ull, bounded ? &skip : nullptr);
+      for (uint64_t fr = 0; fr < NF; ++fr) skip[fr] = pq.prim[fr] == pq.Q.pmin && lb_of[fr] > r.s;
+    rc = exhaustive_search(qf, out, st, bounded ? r.s : ~0ull, bounded ? &skip : nullptr);
     if (stats) {
       stats->fallback = 1;
       stats->n_exact += out->n_candidates;
@@ -1135,7 +1374,7 @@ extern "C" int mp_learned_search(mp_mlp* h, const mp_search_query* query, int K,
   }
   // the winner of the selection
   std::memset(out, 0, sizeof(*out));
-  const uint64_t idx = (uint64_t)sel[bi], fr = idx / NC, c = idx % NC;
+  const uint64_t idx = (uint64_t)r.idx, fr = idx / NC, c = idx % NC;
   out->index = (int64_t)idx;
   for (int t = 0; t < 3; ++t) out->f[t] = pq.S.c->facts[fr][t];
   out->chain_rank = (int64_t)c;
@@ -1148,11 +1387,70 @@ extern "C" int mp_learned_search(mp_mlp* h, const mp_search_query* query, int K,
     x.j = op.op == P_SPLIT ? 0 : op.q;
     x.d = op.op == P_SPLIT ? op.d : 0;
   }
-  out->primary_bytes = pb[bi];
-  out->secondary_bytes = sb[bi];
+  out->primary_bytes = r.p * q.tile_bytes;
+  out->secondary_bytes = r.s * q.tile_bytes;
   out->n_chains = (int64_t)NC;
   out->n_factorisations = (int64_t)NF;
   out->n_candidates = (int64_t)(NC * NF);
+  return MP_OK;
+}
+
+// Calibration of the margin rule on queries held out of training: for each,
+// every candidate of least primary cost is scored and evaluated exactly;
+// the query's value is the model's overestimation of its best-scored optimal
+// candidate (least score among the candidates of least secondary, minus
+// their target).  A search misses the optimum under the margin rule only if
+// that value exceeds tau - y_best, so the largest value over the queries is
+// the bound the rule compares with.
+extern "C" int mp_mlp_calibrate(mp_mlp* h, const mp_search_query* queries, int n_queries, double* bound_out,
+                                void* stream) {
+  using namespace mp;
+  using namespace mp::lrn;
+  if (!h || !queries || n_queries < 1) return MP_EINVAL;
+  for (int i = 0; i < n_queries; ++i) {
+    const int rc = validate_query(queries[i]);
+    if (rc) return rc;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  double bound = -INFINITY;
+  std::vector<float> y;
+  std::vector<uint64_t> sec;
+  for (int qi = 0; qi < n_queries; ++qi) {
+    const mp_search_query& q = queries[qi];
+    Prepared pq;
+    int rc = prepare_query(q, pq, st);
+    if (rc) return rc;
+    const std::vector<uint32_t> flist = pool_facts(pq, false);
+    const uint64_t ncand = pq.S.c->chains.size() * flist.size();
+    SelBufs b;
+    if ((rc = sel_bufs(ncand, 1, (unsigned)std::min<uint64_t>(ncand, 0xFFFFFFFFull), flist.size(), b))) return rc;
+    MP_CUDA_TRY(cudaMemcpyAsync(b.fl, flist.data(), flist.size() * 4, cudaMemcpyHostToDevice, st));
+    MP_CUDA_TRY(cudaMemsetAsync(h->status, 0, 4, st));
+    if ((rc = score_candidates(h, pq, b.fl, ncand, b.sc, st))) return rc;
+    if ((rc = launch_sel_costs(q, pq, b, nullptr, nullptr, 0, nullptr, nullptr, 0, ncand, 0, ncand, h->status, st)))
+      return rc;
+    y.resize(ncand);
+    sec.resize(ncand);
+    int status = 0;
+    MP_CUDA_TRY(cudaMemcpyAsync(y.data(), b.sel_y, ncand * 4, cudaMemcpyDeviceToHost, st));
+    MP_CUDA_TRY(cudaMemcpyAsync(sec.data(), b.sel_s, ncand * 8, cudaMemcpyDeviceToHost, st));
+    MP_CUDA_TRY(cudaMemcpyAsync(&status, h->status, 4, cudaMemcpyDeviceToHost, st));
+    MP_CUDA_TRY(cudaStreamSynchronize(st));
+    if (status) return status;
+    const uint64_t s_opt = *std::min_element(sec.begin(), sec.end());
+    float best_score = INFINITY;
+    for (uint64_t i = 0; i < ncand; ++i)
+      if (sec[i] == s_opt) best_score = std::min(best_score, std::isnan(y[i]) ? INFINITY : y[i]);
+    bound = std::max(bound, (double)best_score - (double)host_target(pq.Q.pmin, s_opt, pq.Q.pmin));
+  }
+  h->margin_bound = std::isnan(bound) ? INFINITY : bound;
+  if (bound_out) *bound_out = h->margin_bound;
+  return MP_OK;
+}
+
+extern "C" int mp_mlp_set_margin_bound(mp_mlp* h, double bound) {
+  if (!h || std::isnan(bound)) return MP_EINVAL;
+  h->margin_bound = bound;
   return MP_OK;
 }
 

@@ -201,7 +201,7 @@ __global__ void __launch_bounds__(256) k_elem(const float* __restrict__ Z, const
   // KIND 2: [Z + bias > 0] * dy[r] * w4[c]       (output layer backward; aux = dy, aux2 = w4),
   //         colsum2 += relu(Z + bias) * dy[r]    (gradient of w4)
   __shared__ float tile[32][33];
-  const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
+  const int r0 = blockIdx.x * 32, c0 = blockIdx.y * 32;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8
   float csum = 0.f, csum2 = 0.f;
   for (int i = ty; i < 32; i += 8) {
@@ -238,7 +238,7 @@ __global__ void __launch_bounds__(256) k_elem(const float* __restrict__ Z, const
 __global__ void __launch_bounds__(256) k_transpose_bf16(const bf16* __restrict__ in, int R, int C,
                                                         bf16* __restrict__ out) {
   __shared__ bf16 tile[32][34];
-  const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
+  const int r0 = blockIdx.x * 32, c0 = blockIdx.y * 32;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   for (int i = ty; i < 32; i += 8)
     if (r0 + i < R && c0 + tx < C) tile[i][tx] = in[(size_t)(r0 + i) * C + c0 + tx];
@@ -356,19 +356,26 @@ int ensure_ws(mp_mlp* h, int B, Bufs& b) {
   return MP_OK;
 }
 
-dim3 tiles(int R, int C) { return dim3((C + 31) / 32, (R + 31) / 32); }
+// 32 x 32 tiles of an R x C array: rows on x (up to 2^31 - 1 blocks, any
+// batch), columns on y (C <= 256)
+dim3 tiles(int R, int C) { return dim3((R + 31) / 32, (C + 31) / 32); }
 
-// Forward through Z3 (and y); H1T / H2T only when training.
+// Forward through Z3 (and y); H1T / H2T only when training.  Every launch is
+// checked at once: a launch that fails (a grid too large, say) must not
+// leave the next kernels reading unwritten activations.
 int forward(mp_mlp* h, const bf16* X, int B, Bufs& b, bool train, const float* target, cudaStream_t st) {
   int rc;
   if ((rc = gemm_tn(X, h->W1b, b.Z1, B, DH, DIN, h->status, st))) return rc;
   k_elem<0><<<tiles(B, DH), 256, 0, st>>>(b.Z1, h->P + O_B1, nullptr, nullptr, B, DH, b.H1, train ? b.H1T : nullptr,
                                           nullptr, nullptr);
+  MP_CUDA_TRY(cudaGetLastError());
   if ((rc = gemm_tn(b.H1, h->W2b, b.Z2, B, DH, DH, h->status, st))) return rc;
   k_elem<0><<<tiles(B, DH), 256, 0, st>>>(b.Z2, h->P + O_B2, nullptr, nullptr, B, DH, b.H2, train ? b.H2T : nullptr,
                                           nullptr, nullptr);
+  MP_CUDA_TRY(cudaGetLastError());
   if ((rc = gemm_tn(b.H2, h->W3b, b.Z3, B, DH, DH, h->status, st))) return rc;
   k_output<<<(B * 32 + 255) / 256, 256, 0, st>>>(b.Z3, h->P, B, target, b.y, b.dy, h->scalar);
+  MP_CUDA_TRY(cudaGetLastError());
   count_launch(3);
   MP_CUDA_TRY(cudaGetLastError());
   return MP_OK;
@@ -381,20 +388,25 @@ int train_step(mp_mlp* h, const bf16* X, const float* target, int B, float lr, c
   MP_CUDA_TRY(cudaMemsetAsync(h->G, 0, NPARAM * 4, st));
   MP_CUDA_TRY(cudaMemsetAsync(h->scalar, 0, 4, st));
   k_transpose_bf16<<<tiles(B, DIN), 256, 0, st>>>(X, B, DIN, b.XT);
+  MP_CUDA_TRY(cudaGetLastError());
   count_launch();
   if ((rc = forward(h, X, B, b, true, target, st))) return rc;
   // output layer and layer 3
   k_sum<<<1, 256, 0, st>>>(b.dy, B, h->G + O_B4);
+  MP_CUDA_TRY(cudaGetLastError());
   k_elem<2><<<tiles(B, DH), 256, 0, st>>>(b.Z3, h->P + O_B3, b.dy, h->P + O_W4, B, DH, b.dZ3, b.dZ3T, h->G + O_B3,
                                           h->G + O_W4);
+  MP_CUDA_TRY(cudaGetLastError());
   count_launch(2);
   if ((rc = gemm_tn(b.dZ3T, b.H2T, h->G + O_W3, DH, DH, B, h->status, st))) return rc;
   if ((rc = gemm_tn(b.dZ3, h->W3T, b.dH, B, DH, DH, h->status, st))) return rc;
   k_elem<1><<<tiles(B, DH), 256, 0, st>>>(b.dH, h->P + O_B2, b.Z2, nullptr, B, DH, b.dZ2, b.dZ2T, h->G + O_B2, nullptr);
+  MP_CUDA_TRY(cudaGetLastError());
   count_launch();
   if ((rc = gemm_tn(b.dZ2T, b.H1T, h->G + O_W2, DH, DH, B, h->status, st))) return rc;
   if ((rc = gemm_tn(b.dZ2, h->W2T, b.dH, B, DH, DH, h->status, st))) return rc;
   k_elem<1><<<tiles(B, DH), 256, 0, st>>>(b.dH, h->P + O_B1, b.Z1, nullptr, B, DH, b.dZ1, b.dZ1T, h->G + O_B1, nullptr);
+  MP_CUDA_TRY(cudaGetLastError());
   count_launch();
   if ((rc = gemm_tn(b.dZ1T, b.XT, h->G + O_W1, DH, DIN, B, h->status, st))) return rc;
   if (lr > 0.f) {
@@ -402,7 +414,9 @@ int train_step(mp_mlp* h, const bf16* X, const float* target, int B, float lr, c
     const float b1 = 0.9f, b2 = 0.999f;
     const float c1 = 1.f - powf(b1, (float)h->step), c2 = 1.f - powf(b2, (float)h->step);
     k_adam<<<296, 256, 0, st>>>(h->P, h->G, h->M1, h->M2, NPARAM, lr, b1, b2, c1, c2, 1e-8f);
+    MP_CUDA_TRY(cudaGetLastError());
     k_refresh<<<256, 256, 0, st>>>(h->P, h->W1b, h->W2b, h->W3b, h->W2T, h->W3T, h->Wimg);
+    MP_CUDA_TRY(cudaGetLastError());
     count_launch(2);
   }
   MP_CUDA_TRY(cudaGetLastError());
@@ -501,6 +515,7 @@ extern "C" int mp_mlp_get_params(const mp_mlp* h, float* params, float* grads) {
 extern "C" int mp_mlp_forward(mp_mlp* h, const void* X, float* y, int B, void* stream) {
   using namespace mp::mlpk;
   if (!h || !X || !y || B <= 0 || B % 128) return MP_EINVAL;
+  if (B > kMaxRows) return MP_ENOTSUP;
   if (!mp::is_device_pointer(X) || !mp::is_device_pointer(y)) return MP_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
   Bufs b;
@@ -519,6 +534,7 @@ extern "C" int mp_mlp_train_step(mp_mlp* h, const void* X, const float* target, 
                                  void* stream) {
   using namespace mp::mlpk;
   if (!h || !X || !target || B <= 0 || B % 128) return MP_EINVAL;
+  if (B > kMaxRows) return MP_ENOTSUP;
   if (!mp::is_device_pointer(X) || !mp::is_device_pointer(target)) return MP_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
   MP_CUDA_TRY(cudaMemsetAsync(h->status, 0, 4, st));
@@ -540,7 +556,7 @@ namespace mlpk {
 namespace {
 
 constexpr char kMagic[8] = {'M', 'A', 'P', 'L', 'E', 'M', 'L', 'P'};
-constexpr uint32_t kFormat = 1;
+constexpr uint32_t kFormat = 2;   // 2: the margin bound follows the header (1: none)
 
 struct CkptHeader {
   char magic[8];
@@ -580,7 +596,9 @@ extern "C" int mp_mlp_save(const mp_mlp* h, const char* path) {
   hd.step = h->step;
   FILE* f = std::fopen(path, "wb");
   if (!f) return MP_EINVAL;
-  const bool ok = std::fwrite(&hd, sizeof(hd), 1, f) == 1 && std::fwrite(buf.data(), 4, buf.size(), f) == buf.size();
+  const double bound = h->margin_bound;
+  const bool ok = std::fwrite(&hd, sizeof(hd), 1, f) == 1 && std::fwrite(&bound, 8, 1, f) == 1 &&
+                  std::fwrite(buf.data(), 4, buf.size(), f) == buf.size();
   const bool closed = std::fclose(f) == 0;
   return ok && closed ? MP_OK : MP_EINVAL;
 }
@@ -592,11 +610,14 @@ extern "C" int mp_mlp_load(mp_mlp* h, const char* path) {
   if (!f) return MP_EINVAL;
   CkptHeader hd;
   std::vector<float> buf(3 * NPARAM);
-  const bool ok = std::fread(&hd, sizeof(hd), 1, f) == 1 && std::memcmp(hd.magic, kMagic, 8) == 0 &&
-                  hd.version == kFormat && hd.nparam == (uint32_t)NPARAM &&
-                  std::fread(buf.data(), 4, buf.size(), f) == buf.size();
+  double bound = __builtin_inf();
+  bool ok = std::fread(&hd, sizeof(hd), 1, f) == 1 && std::memcmp(hd.magic, kMagic, 8) == 0 &&
+            (hd.version == 1 || hd.version == kFormat) && hd.nparam == (uint32_t)NPARAM;
+  if (ok && hd.version >= 2) ok = std::fread(&bound, 8, 1, f) == 1;
+  ok = ok && std::fread(buf.data(), 4, buf.size(), f) == buf.size();
   std::fclose(f);
   if (!ok) return MP_EINVAL;
+  h->margin_bound = bound;
   MP_CUDA_TRY(cudaMemcpy(h->M1, buf.data() + NPARAM, NPARAM * 4, cudaMemcpyHostToDevice));
   MP_CUDA_TRY(cudaMemcpy(h->M2, buf.data() + 2 * NPARAM, NPARAM * 4, cudaMemcpyHostToDevice));
   h->step = (int)hd.step;

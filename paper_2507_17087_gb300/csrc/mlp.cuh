@@ -10,6 +10,7 @@ namespace mp {
 namespace mlpk {
 
 constexpr int DIN = 64, DH = 256;
+constexpr int kMaxRows = 1 << 26;   // rows of one forward / training batch (one warp per row in 32-bit indexing)
 constexpr size_t O_W1 = 0, O_B1 = O_W1 + DH * DIN, O_W2 = O_B1 + DH, O_B2 = O_W2 + DH * DH, O_W3 = O_B2 + DH,
                  O_B3 = O_W3 + DH * DH, O_W4 = O_B3 + DH, O_B4 = O_W4 + DH, NPARAM = O_B4 + 1;
 
@@ -46,6 +47,7 @@ struct mp_mlp {
   int* status = nullptr;
   float* scalar = nullptr;   // loss accumulator
   int step = 0;
+  double margin_bound = __builtin_inf();   // calibrated overestimation bound of the margin rule (none yet)
   // per-batch work buffers
   int ws_B = 0;
   void* ws = nullptr;

@@ -158,8 +158,6 @@ __global__ void k_candidate_costs(const ChainProg* __restrict__ progs, const Fac
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ ChainProg cp;
   __shared__ unsigned long long red[32];
-  uint32_t* bm = reinterpret_cast<uint32_t*>(smem_raw);
-  uint16_t* tab = reinterpret_cast<uint16_t*>(smem_raw + (size_t)words * blockDim.x * 4);
   const unsigned long long id = (unsigned long long)idx[blockIdx.x];
   if (idx[blockIdx.x] < 0 || id >= nchains * (unsigned long long)nf) {   // out of range: flag, no access
     if (threadIdx.x == 0) {
@@ -169,51 +167,10 @@ __global__ void k_candidate_costs(const ChainProg* __restrict__ progs, const Fac
     return;
   }
   const unsigned long long fr = id / nchains, c = id % nchains;
-  if (threadIdx.x == 0) cp = progs[c];
-  for (int w = 0; w < words; ++w) bm[w * blockDim.x + threadIdx.x] = 0;
-  __syncthreads();
-  if (gtab) load_table(gtab + (size_t)c * Pp, tab, Pp);
-  else build_table(cp, tab, P);
-  __syncthreads();
   const uint32_t E[3] = {E0, E1, E2};
-  const uint32_t f[3] = {facts[fr].f[0], facts[fr].f[1], facts[fr].f[2]};
-  const uint32_t stride[3] = {1u, f[0], f[0] * f[1]};
-  uint32_t n[3];
-  for (int t = 0; t < 3; ++t) n[t] = E[t] < f[t] ? E[t] : f[t];
-  unsigned long long sec = 0;
-  for (int v = 0; v < 3; ++v) {
-    if (n[v] <= 1) continue;
-    const int u = v == 0 ? 1 : 0;
-    const int w = v == 2 ? 1 : 2;
-    const uint32_t nfib = n[u] * n[w];
-    for (uint32_t fb = threadIdx.x; fb < nfib; fb += blockDim.x) {
-      const uint32_t iu = fb % n[u], iw = fb / n[u];
-      // representative and weight of block iu (iw) directly
-      auto rep_wt = [&](int t, uint32_t i, uint32_t& rep, uint32_t& wt) {
-        if (E[t] >= f[t]) {
-          rep = i;
-          const unsigned long long lo = ((unsigned long long)i * E[t] + f[t] - 1) / f[t];
-          const unsigned long long hi = ((unsigned long long)(i + 1) * E[t] + f[t] - 1) / f[t];
-          wt = (uint32_t)(hi - lo);
-        } else {
-          rep = (uint32_t)((unsigned long long)i * f[t] / E[t]);
-          wt = 1;
-        }
-      };
-      uint32_t ru, wu, rw, ww;
-      rep_wt(u, iu, ru, wu);
-      rep_wt(w, iw, rw, ww);
-      const uint32_t base = ru * stride[u] + rw * stride[w];
-      const uint32_t D = fibre_distinct(tab, bm + threadIdx.x, blockDim.x, words, base, stride[v], E[v], f[v], n[v]);
-      sec += (unsigned long long)wu * ww * (D - 1);
-    }
-  }
-  for (int o = 16; o > 0; o >>= 1) sec += __shfl_down_sync(0xFFFFFFFFu, sec, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = sec;
-  __syncthreads();
+  const unsigned long long s = candidate_secondary_block(progs, facts, fr, c, P, E, words, gtab, Pp, smem_raw, cp, red);
   if (threadIdx.x == 0) {
-    unsigned long long s = 0;
-    for (int w = 0; w < (int)((blockDim.x + 31) >> 5); ++w) s += red[w];
+    const uint32_t f[3] = {facts[fr].f[0], facts[fr].f[1], facts[fr].f[2]};
     prim_out[blockIdx.x] = primary_cost(E, f) * tile_bytes;
     sec_out[blockIdx.x] = s * tile_bytes;
   }

@@ -269,7 +269,7 @@ __device__ __forceinline__ unsigned long long secondary_cost_warp(const uint16_t
   return sec;
 }
 
-__device__ __forceinline__ unsigned long long primary_cost(const uint32_t E[3], const uint32_t f[3]) {
+__host__ __device__ __forceinline__ unsigned long long primary_cost(const uint32_t E[3], const uint32_t f[3]) {
   unsigned long long p = 0;
   for (int v = 0; v < 3; ++v) {
     const int u = v == 0 ? 1 : 0;
@@ -315,6 +315,67 @@ __device__ __forceinline__ void load_table(const uint16_t* __restrict__ row, uin
   for (uint32_t i = threadIdx.x; i < Pp / 8; i += blockDim.x) dst[i] = __ldg(src + i);
 }
 
+
+// Secondary cost (tiles) of candidate (factorisation fr, chain c), computed
+// by the whole CTA: the chain's node table in shared memory (copied from the
+// space's cache, or built), the fibres of the three families spread over the
+// threads, one bitmap per thread.  Every thread returns the total.
+// smem_raw: words * blockDim.x bitmap words, then the table (Pp uint16);
+// cp and red are the caller's __shared__ scratch.  Safe to call repeatedly
+// from one CTA (it synchronises before reusing its scratch).
+__device__ __forceinline__ unsigned long long candidate_secondary_block(
+    const ChainProg* __restrict__ progs, const Fact* __restrict__ facts, unsigned long long fr, unsigned long long c,
+    uint32_t P, const uint32_t E[3], int words, const uint16_t* __restrict__ gtab, uint32_t Pp,
+    unsigned char* smem_raw, ChainProg& cp, unsigned long long* red) {
+  uint32_t* bm = reinterpret_cast<uint32_t*>(smem_raw);
+  uint16_t* tab = reinterpret_cast<uint16_t*>(smem_raw + (size_t)words * blockDim.x * 4);
+  __syncthreads();
+  if (threadIdx.x == 0) cp = progs[c];
+  for (int w = 0; w < words; ++w) bm[w * blockDim.x + threadIdx.x] = 0;
+  __syncthreads();
+  if (gtab) load_table(gtab + (size_t)c * Pp, tab, Pp);
+  else build_table(cp, tab, P);
+  __syncthreads();
+  const uint32_t f[3] = {facts[fr].f[0], facts[fr].f[1], facts[fr].f[2]};
+  const uint32_t stride[3] = {1u, f[0], f[0] * f[1]};
+  uint32_t n[3];
+  for (int t = 0; t < 3; ++t) n[t] = E[t] < f[t] ? E[t] : f[t];
+  unsigned long long sec = 0;
+#pragma unroll   // constant family indices keep E, f, stride and n in registers
+  for (int v = 0; v < 3; ++v) {
+    if (n[v] <= 1) continue;
+    const int u = v == 0 ? 1 : 0;
+    const int w = v == 2 ? 1 : 2;
+    const uint32_t nfib = n[u] * n[w];
+    for (uint32_t fb = threadIdx.x; fb < nfib; fb += blockDim.x) {
+      const uint32_t iu = fb % n[u], iw = fb / n[u];
+      // representative and weight of block iu (iw) directly
+      auto rep_wt = [&](int t, uint32_t i, uint32_t& rep, uint32_t& wt) {
+        if (E[t] >= f[t]) {
+          rep = i;
+          const unsigned long long lo = ((unsigned long long)i * E[t] + f[t] - 1) / f[t];
+          const unsigned long long hi = ((unsigned long long)(i + 1) * E[t] + f[t] - 1) / f[t];
+          wt = (uint32_t)(hi - lo);
+        } else {
+          rep = (uint32_t)((unsigned long long)i * f[t] / E[t]);
+          wt = 1;
+        }
+      };
+      uint32_t ru, wu, rw, ww;
+      rep_wt(u, iu, ru, wu);
+      rep_wt(w, iw, rw, ww);
+      const uint32_t base = ru * stride[u] + rw * stride[w];
+      const uint32_t D = fibre_distinct(tab, bm + threadIdx.x, blockDim.x, words, base, stride[v], E[v], f[v], n[v]);
+      sec += (unsigned long long)wu * ww * (D - 1);
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) sec += __shfl_down_sync(0xFFFFFFFFu, sec, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = sec;
+  __syncthreads();
+  unsigned long long total = 0;
+  for (int w = 0; w < (int)((blockDim.x + 31) >> 5); ++w) total += red[w];
+  return total;
+}
 
 // ----------------------------------------------------------------- host side
 

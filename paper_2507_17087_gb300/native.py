@@ -162,6 +162,8 @@ def lib():
                 "mp_mlp_train_step": (I, [V, V, V, I, ctypes.c_float, V, V]),
                 "mp_mlp_train_search": (I, [V, V, I, I, I, I, ctypes.c_float, ctypes.c_uint64, V, V]),
                 "mp_learned_search": (I, [V, V, I, I, V, V, V]),
+                "mp_mlp_calibrate": (I, [V, V, I, V, V]),
+                "mp_mlp_set_margin_bound": (I, [V, ctypes.c_double]),
                 "mp_learned_scores": (I, [V, V, V, V, V, V]),
                 "mp_descriptor_bytes": (U64, []),
             }
@@ -677,8 +679,11 @@ class mp_learned_stats(ctypes.Structure):
     _fields_ = [("n_scored", ctypes.c_int64), ("n_exact", ctypes.c_int64), ("n_selected", ctypes.c_int64),
                 ("certified", ctypes.c_int32), ("fallback", ctypes.c_int32), ("rounds", ctypes.c_int32),
                 ("reserved", ctypes.c_int32), ("margin", ctypes.c_double), ("max_overestimate", ctypes.c_double),
-                ("ms_prepare", ctypes.c_double), ("ms_model", ctypes.c_double), ("ms_exact", ctypes.c_double),
-                ("ms_fallback", ctypes.c_double)]
+                ("margin_bound", ctypes.c_double), ("ms_prepare", ctypes.c_double), ("ms_model", ctypes.c_double),
+                ("ms_exact", ctypes.c_double), ("ms_wall", ctypes.c_double), ("ms_fallback", ctypes.c_double)]
+
+
+CERTIFIED = {0: "none", 1: "every threat evaluated", 2: "secondary lower bound", 3: "margin rule"}
 
 
 LEARNED_NO_FALLBACK = 1
@@ -747,10 +752,23 @@ class MLP:
         res = _search_result(out)
         res.update({"n_scored": st.n_scored, "n_exact": st.n_exact, "n_selected": st.n_selected,
                     "certified": int(st.certified), "fallback": bool(st.fallback), "rounds": st.rounds,
-                    "margin": st.margin, "max_overestimate": st.max_overestimate,
+                    "margin": st.margin, "max_overestimate": st.max_overestimate, "margin_bound": st.margin_bound,
                     "ms": {"prepare": st.ms_prepare, "model": st.ms_model, "exact": st.ms_exact,
-                           "fallback": st.ms_fallback}})
+                           "wall": st.ms_wall, "fallback": st.ms_fallback}})
         return res
+
+    def calibrate(self, queries, stream=None):
+        """Sets (and returns) the margin rule's overestimation bound from
+        queries held out of training (mp_mlp_calibrate)."""
+        qs = [_query(q) for q in queries]
+        arr = (mp_search_query * len(qs))(*qs)
+        bound = ctypes.c_double(0)
+        _check(lib().mp_mlp_calibrate(self._h, arr, len(qs), ctypes.byref(bound), _stream(stream)),
+               "mp_mlp_calibrate")
+        return bound.value
+
+    def set_margin_bound(self, bound):
+        _check(lib().mp_mlp_set_margin_bound(self._h, ctypes.c_double(bound)), "mp_mlp_set_margin_bound")
 
     def save(self, path):
         """Checkpoint: parameters, Adam moments and step (versioned header)."""

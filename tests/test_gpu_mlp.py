@@ -1,10 +1,14 @@
 """Tensor-core MLP kernels against the float64 reference (oracle/mlp.py).
 
 The GEMM is checked against a float64 product of the same bfloat16 values
-(FP32 accumulation: relative error well below 1e-4); the forward pass of the
-model against the float64 forward to 1e-2 relative (BF16 operands); the
-backward pass against the float64 gradients, which are themselves pinned to
-finite differences in tests/test_mlp_oracle.py.
+(FP32 accumulation: relative error well below 1e-4).  The forward pass and
+the fused scorer are checked element by element: every output y_i against
+the float64 forward y64_i, |y_i - y64_i| <= 1e-2 max(|y64_i|, floor), where
+the floor is a fixed fraction of the outputs' scale (an output near zero
+carries the absolute rounding error of its 256-term sums).  The backward
+pass is checked element by element against the float64 gradients with the
+engine's BF16 rounding points (the float64 gradients are themselves pinned
+to finite differences in tests/test_mlp_oracle.py).
 """
 import numpy as np
 import pytest
@@ -51,6 +55,16 @@ def rel(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
 
 
+def max_rel(a, ref, floor):
+    """max over elements of |a_i - ref_i| / max(|ref_i|, floor)."""
+    a, ref = np.asarray(a, dtype=np.float64), np.asarray(ref, dtype=np.float64)
+    return float((np.abs(a - ref) / np.maximum(np.abs(ref), floor)).max())
+
+
+def rms(v):
+    return float(np.sqrt(np.mean(np.square(v))))
+
+
 def test_forward_against_float64():
     model = N.MLP(seed=3)
     p = R.init_params(3)
@@ -59,11 +73,19 @@ def test_forward_against_float64():
         p[k] = rng.standard_normal(p[k].shape) * 0.1
     p["b4"] = np.array([0.2])
     model.set_params(p)
-    X = torch.from_numpy(rng.standard_normal((512, 64)).astype(np.float32)).to(torch.bfloat16).cuda()
-    y = torch.empty(512, dtype=torch.float32, device="cuda")
+    X = torch.from_numpy(rng.standard_normal((4096, 64)).astype(np.float32)).to(torch.bfloat16).cuda()
+    y = torch.empty(4096, dtype=torch.float32, device="cuda")
     model.forward(X, y)
-    ref, _ = R.forward(rounded_params(p), X.double().cpu().numpy())
-    assert rel(y.double().cpu().numpy(), ref) <= 1e-2
+    y = y.double().cpu().numpy()
+    xs = X.double().cpu().numpy()
+    # the float64 forward of the same BF16 inputs and weights, element by
+    # element (floor: the outputs' root mean square)
+    ref, _ = R.forward(rounded_params(p), xs)
+    assert max_rel(y, ref, rms(ref)) <= 1e-2
+    # with the engine's BF16 rounding points (the stored activations): only
+    # the FP32 accumulation order differs
+    ref, _ = R.forward(rounded_params(p), xs, rnd=bf16_round)
+    assert max_rel(y, ref, 1e-3 * np.abs(ref).max()) <= 1e-2
 
 
 def test_gradients_against_float64():
@@ -84,9 +106,12 @@ def test_gradients_against_float64():
     y, cache = R.forward(pr, xs, rnd=bf16_round)
     ref = R.backward(pr, cache, y, ts, rnd=bf16_round)
     assert abs(loss - R.loss(y, ts)) <= 1e-3 * abs(loss)
+    # element by element, floor: the root mean square of each block
     for k in ref:
-        assert rel(g[k], ref[k]) <= 1e-2, k
-    # pure float64: within the BF16 rounding of five stored operands
+        assert max_rel(g[k], ref[k], rms(ref[k])) <= 1e-2, k
+    # pure float64 (no rounding points): each gradient sums products of five
+    # BF16-rounded operands with cancellation, so only its norm is held to
+    # the BF16 budget
     y, cache = R.forward(pr, xs)
     ref = R.backward(pr, cache, y, ts)
     for k in ref:
@@ -118,42 +143,94 @@ def test_fused_scores_match_unfused_forward_and_float64():
     assert model.scores(q, scores, feats) == n
     y = torch.empty(npad, dtype=torch.float32, device="cuda")
     model.forward(feats, y)
-    assert rel(scores.double().cpu().numpy(), y[:n].double().cpu().numpy()) <= 1e-3
+    sc = scores.double().cpu().numpy()
+    unfused = y[:n].double().cpu().numpy()
+    assert max_rel(sc, unfused, 1e-3 * np.abs(unfused).max()) <= 1e-3
     ref, _ = R.forward(rounded_params(model.get_params()), feats[:n].double().cpu().numpy())
-    assert rel(scores.double().cpu().numpy(), ref) <= 1e-2
+    assert max_rel(sc, ref, rms(ref)) <= 1e-2
 
 
-def test_learned_search_trains_and_finds_the_optimum():
+def test_fused_scores_full_run_against_float64():
+    # every candidate of a P = 3600 query (3.79 M: seven full runs of 2^19
+    # candidates and a ragged last one, each through the feature and layer
+    # kernels) scored by a trained model, against the float64 forward of the
+    # kernel's own BF16 features, element by element; and the unfused forward
+    # of all 3.79 M feature rows (row tiles far beyond 65,535 x 32) against
+    # the fused scores
+    model = N.MLP(seed=11)
+    model.train_search(W.search_training_queries(128), samples_per_query=4096, epochs=4, batch=4096, lr=1e-3,
+                       seed=3)
+    q = [q for q in W.search_queries(16) if q["machine"][0] * q["machine"][1] == 3600][0]
+    n = 3787020
+    scores = torch.empty(n, dtype=torch.float32, device="cuda")
+    feats = torch.zeros((n + 127) // 128 * 128, 64, dtype=torch.bfloat16, device="cuda")
+    assert model.scores(q, scores, feats) == n
+    sc = scores.double().cpu().numpy()
+    F = feats[:n].double().cpu().numpy()
+    pr = rounded_params(model.get_params())
+    ref = np.empty(n)
+    for lo in range(0, n, 1 << 18):
+        ref[lo:lo + (1 << 18)], _ = R.forward(pr, F[lo:lo + (1 << 18)])
+    assert max_rel(sc, ref, 1.0) <= 1e-2
+    y = torch.empty(feats.shape[0], dtype=torch.float32, device="cuda")
+    model.forward(feats, y)
+    assert max_rel(y[:n].double().cpu().numpy(), sc, 1.0) <= 1e-4
+    model.close()
+
+
+def test_learned_search_gains_over_the_search_without_it():
+    # on 100 held-out queries: the trained, calibrated network against the
+    # same network untrained and against the exact search without a network
+    # (the primary-bound search).  Every returned cost is the exact cost of
+    # the returned candidate; results certified (every threat evaluated, or
+    # the secondary lower bound reached) or from the fallback are optimal;
+    # with the calibrated margin rule at least 99 % are; the trained model's
+    # top K alone hold the optimum far more often than the untrained one's
+    # (at least 90 % of the time), and it falls back to the exhaustive search
+    # far less often.
     model = N.MLP(seed=7)
-    train = W.search_training_queries(48)
-    loss0 = model.train_search(train[:4], samples_per_query=512, epochs=1, batch=512, lr=1e-3, seed=1)
-    loss = model.train_search(train, samples_per_query=4096, epochs=6, batch=4096, lr=1e-3, seed=2)
-    print(f"training loss {loss0:.4f} -> {loss:.4f}")
+    loss0 = model.train_search(W.search_training_queries(4), samples_per_query=512, epochs=1, batch=512, lr=1e-3,
+                               seed=1)
+    loss = model.train_search(W.search_training_queries(256), samples_per_query=4096, epochs=8, batch=4096, lr=1e-3,
+                              seed=2)
     assert np.isfinite(loss) and loss < loss0
-    evalq = W.search_queries(12, first_index=9000)
-    zero_regret = 0
+    bound = model.calibrate(W.search_training_queries(64, first_index=40000))
+    assert np.isfinite(bound)
+    untrained = N.MLP(seed=99)
+    assert untrained.learned_search(W.search_queries(1, first_index=9000)[0], K=1024)["margin_bound"] == np.inf
+    stats = {"trained": [0, 0, 0], "untrained": [0, 0, 0]}   # zero regret, top-K zero regret, fallbacks
+    evalq = W.search_queries(100, first_index=9000)
     for q in evalq:
         exact = N.decompose_search([q])[0]
-        got = model.learned_search(q, K=1024, fallback=True)
-        # exact with the fallback: the optimal cost tuple (among
-        # exact ties the index may differ unless the exhaustive search ran)
-        assert (got["primary_bytes"], got["secondary_bytes"]) == \
-            (exact["primary_bytes"], exact["secondary_bytes"])
-        if got["fallback"]:
-            assert got["index"] == exact["index"]
-        raw = model.learned_search(q, K=1024, fallback=False)
-        zero_regret += (raw["primary_bytes"], raw["secondary_bytes"]) == \
-            (exact["primary_bytes"], exact["secondary_bytes"])
-        # the model ranks the candidates of least primary cost, at most all
-        assert raw["n_exact"] <= 1024 and raw["n_scored"] <= exact["n_candidates"]
-    print(f"zero-regret without fallback: {zero_regret}/{len(evalq)}")
-    assert zero_regret >= len(evalq) // 2
+        want = (exact["primary_bytes"], exact["secondary_bytes"])
+        for name, m in (("trained", model), ("untrained", untrained)):
+            got = m.learned_search(q, K=1024, fallback=True)
+            cost = (got["primary_bytes"], got["secondary_bytes"])
+            p = np.zeros(1, dtype=np.uint64)
+            s = np.zeros(1, dtype=np.uint64)
+            N.candidate_costs(q, np.array([got["index"]], dtype=np.int64), p, s)
+            assert (int(p[0]), int(s[0])) == cost   # the returned costs are exact
+            if got["fallback"]:
+                assert got["index"] == exact["index"]
+            if got["fallback"] or got["certified"] in (1, 2):
+                assert cost == want, (name, q, got["certified"])
+            raw = m.learned_search(q, K=1024, fallback=False)
+            st = stats[name]
+            st[0] += cost == want
+            st[1] += (raw["primary_bytes"], raw["secondary_bytes"]) == want
+            st[2] += got["fallback"]
+    print("trained / untrained (zero regret, top-K zero regret, fallbacks):", stats, "bound", bound)
+    assert stats["trained"][0] >= 99   # the search as deployed (certificates, margin rule, fallback)
+    assert stats["trained"][1] >= 90 and stats["untrained"][1] <= stats["trained"][1] - 10
+    assert 2 * stats["trained"][2] < stats["untrained"][2]
     # scoring every candidate instead
     q = evalq[0]
     exact = N.decompose_search([q])[0]
     got = model.learned_search(q, K=1024, fallback=True, score_all=True)
     assert got["n_scored"] == exact["n_candidates"]
     assert (got["primary_bytes"], got["secondary_bytes"]) == (exact["primary_bytes"], exact["secondary_bytes"])
+    model.close()
+    untrained.close()
 
 
 def test_fibre_features_against_oracle_nodes():

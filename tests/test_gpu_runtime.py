@@ -74,13 +74,37 @@ def test_model_checkpoint_resumes_training(tmp_path):
     b.close()
 
 
+def test_checkpoint_carries_the_margin_bound(tmp_path):
+    # format 2 stores the calibrated margin bound after the header; a
+    # format-1 file (no bound) loads as an uncalibrated model
+    q = {"MNK": (64, 256, 16), "machine": (4, 8), "max_depth": 2, "tile_bytes": 512 * 512 * 4}
+    a = N.MLP(seed=23)
+    a.set_margin_bound(0.5)
+    path = tmp_path / "model.ckpt"
+    a.save(os.fspath(path))
+    b = N.MLP(seed=24)
+    b.load(os.fspath(path))
+    assert b.learned_search(q, K=64)["margin_bound"] == pytest.approx(1.25 * 0.5 + 0.01)
+    raw = bytearray(path.read_bytes())
+    v1 = raw[:8] + (1).to_bytes(4, "little") + raw[12:24] + raw[32:]   # version 1, bound dropped
+    p1 = tmp_path / "v1.ckpt"
+    p1.write_bytes(bytes(v1))
+    b.load(os.fspath(p1))
+    assert b.learned_search(q, K=64)["margin_bound"] == np.inf
+    pa, pb = a.get_params(), b.get_params()
+    for k in pa:
+        assert np.array_equal(pa[k], pb[k]), k
+    a.close()
+    b.close()
+
+
 def test_corrupt_checkpoints_rejected(tmp_path):
     a = N.MLP(seed=22)
     path = tmp_path / "model.ckpt"
     a.save(os.fspath(path))
     raw = bytearray(path.read_bytes())
     for mutate in (lambda r: r.__setitem__(0, ord("X")),            # magic
-                   lambda r: r.__setitem__(8, 2),                   # format version
+                   lambda r: r.__setitem__(8, 7),                   # format version
                    lambda r: r.__setitem__(12, r[12] ^ 1)):         # parameter count
         bad = bytearray(raw)
         mutate(bad)
