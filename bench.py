@@ -312,6 +312,50 @@ def extra_learned(N, W, torch, n_train=512, per_query=4096, epochs=8, n_eval=200
     return out
 
 
+# multiply-adds per training sample: forward 64*256 + 2*256*256, the three
+# weight gradients as many again, and the two hidden-layer input gradients
+# 2*256*256 (the output layer's 256 + 256 are left out)
+TRAIN_FLOP_PER_SAMPLE = 2 * (147456 + 147456 + 131072)
+
+
+def sustained_bf16_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["bf16_tflops_sustained"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 1700.0, "fallback"
+
+
+def extra_train(N, torch, dev, batch=4096, steps=300, warmup=10):
+    """Training steps of the learned cost model (forward, backward and Adam
+    on one batch of 4096 samples, every product on the tcgen05 GEMM):
+    samples/s, achieved TFLOP/s of the products and the fraction of the
+    sustained BF16 peak."""
+    g = torch.Generator(device="cpu").manual_seed(5)
+    X = torch.randn(batch, 64, generator=g).to(torch.bfloat16).to(dev)
+    t = torch.randn(batch, generator=g).to(dev)
+    m = N.MLP(seed=5)
+    for _ in range(warmup):
+        m.train_step(X, t, lr=1e-4)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        m.train_step(X, t, lr=1e-4)
+    e1.record()
+    torch.cuda.synchronize()
+    m.close()
+    ms = e0.elapsed_time(e1) / steps
+    tflops = TRAIN_FLOP_PER_SAMPLE * batch / (ms / 1e3) / 1e12
+    peak, kind = sustained_bf16_peak()
+    return {"metric": "training samples/s", "value": batch / (ms / 1e3), "unit": "samples/s", "batch": batch,
+            "ms_per_step": ms, "tflops": tflops, "peak_tflops": peak, "peak_source": f"{kind} bf16_tflops_sustained",
+            "frac_of_peak": tflops / peak, "flop_per_sample": TRAIN_FLOP_PER_SAMPLE,
+            "note": "each step synchronises once (it returns the loss), and its GEMMs are 128-row tiles "
+                    "of 4096 x 256 x {64, 256} and 256 x {64, 256} x 4096 products"}
+
+
 def extra_volume_study(N, W, torch, dev):
     """Decompose vs the greedy grid of Algorithm A1 on the paper's 180-config
     stencil grid: exact halo volume (width 1, 8-byte elements) of the block
@@ -505,7 +549,20 @@ def profile_case_batched(N, torch):
     b.close()
 
 
+def profile_case_train(N, torch):
+    """Training steps of the cost model on one batch of 4096 samples, five
+    times (every product through k_gemm_tn)."""
+    g = torch.Generator(device="cpu").manual_seed(5)
+    X = torch.randn(4096, 64, generator=g).to(torch.bfloat16).cuda()
+    t = torch.randn(4096, generator=g).cuda()
+    m = N.MLP(seed=5)
+    for _ in range(5):
+        m.train_step(X, t, lr=1e-4)
+    m.close()
+
+
 PROFILE_CASES = {"ids-small": profile_case_ids, "search": profile_case_search, "score": profile_case_score,
+                 "train-step": profile_case_train,
                  "score-features": profile_case_score_features, "batched": profile_case_batched}
 
 
@@ -654,6 +711,7 @@ def main():
             for key, fn in (("search", lambda: extra_search(N, W, torch)),
                             ("batched", lambda: extra_batched(N, W, torch, dev)),
                             ("learned", lambda: extra_learned(N, W, torch)),
+                            ("train", lambda: extra_train(N, torch, dev)),
                             ("volume_study", lambda: extra_volume_study(N, W, torch, dev)),
                             ("hier_search", lambda: extra_hier_search(N, W, torch)),
                             ("applications", lambda: extra_applications(N, W, torch, dev))):

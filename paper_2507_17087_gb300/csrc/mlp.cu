@@ -3,11 +3,16 @@
 // prunes the decompose search).
 //
 // k_gemm_tn: C[M x N] (FP32) = A[M x K] * B[N x K]^T with BF16 row-major
-// (K-major) operands.  One CTA of 128 threads computes a 128 x NT tile: the
-// K loop stages 64-wide chunks of A and B in shared memory with the 128-byte
-// swizzle (double-buffered), one thread issues four K=16 MMAs per chunk into
-// a tensor-memory accumulator and commits them to the chunk's mbarrier, and
-// the four warps read the accumulator back (32 rows each) for the epilogue.
+// (K-major) operands.  One CTA of 128 threads computes a 128 x NT tile: TMA
+// tensor copies bring 64-wide K chunks of A and B into shared memory in the
+// 128-byte swizzled layout the MMA reads (three stages, mbarrier transaction
+// counts), one thread issues four K=16 MMAs per chunk into a tensor-memory
+// accumulator and commits them to the stage's mbarrier (which frees it for
+// the chunk three ahead), and the four warps read the accumulator back (32
+// rows each) for the epilogue.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -24,68 +29,89 @@ namespace {
 
 constexpr uint32_t kWaitLimit = 1u << 26;   // mbarrier polls before a wait is abandoned
 
-__device__ __forceinline__ void stage_rows(uint8_t* dst, const __nv_bfloat16* __restrict__ src, int rows,
-                                           int ld, int k0) {
-  // rows x 64 elements (8 chunks of 16 bytes per row) into the swizzled tile
-  for (int i = threadIdx.x; i < rows * 8; i += blockDim.x) {
-    const int r = i >> 3, c = i & 7;
-    const uint4 v = __ldg(reinterpret_cast<const uint4*>(src + (size_t)r * ld + k0 + c * 8));
-    *reinterpret_cast<uint4*>(dst + tc::sw128_offset(r, c * 8)) = v;
-  }
-}
+constexpr int kGemmStages = 3;
 
 template <int NT>
-__global__ void __launch_bounds__(128) k_gemm_tn(const __nv_bfloat16* __restrict__ A,
-                                                 const __nv_bfloat16* __restrict__ B, float* __restrict__ C,
+__global__ void __launch_bounds__(128) k_gemm_tn(const __grid_constant__ CUtensorMap tmA,
+                                                 const __grid_constant__ CUtensorMap tmB, float* __restrict__ C,
                                                  int M, int N, int K, int kcs, int* __restrict__ status) {
   extern __shared__ uint8_t smem_raw[];
-  __shared__ uint64_t bar[2];
+  __shared__ uint64_t full[kGemmStages], empty[kGemmStages], done;
   __shared__ uint32_t tmem_slot;
+  __shared__ int s_fail;
   uint8_t* base = smem_raw + ((1024 - (tc::smem_u32(smem_raw) & 1023)) & 1023);
-  constexpr int ABYTES = 128 * 128, BBYTES = NT * 128;
-  uint8_t* bufA[2] = {base, base + ABYTES + BBYTES};
-  uint8_t* bufB[2] = {base + ABYTES, base + 2 * ABYTES + BBYTES};
+  constexpr uint32_t ABYTES = 128 * 128, BBYTES = NT * 128, SBYTES = ABYTES + BBYTES;   // multiples of 1024
   const int m0 = blockIdx.x * 128, n0 = blockIdx.y * NT;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // split K: this CTA takes the 64-wide chunks [kc0, kc0 + nk) (kcs per split)
+  const int kc0 = blockIdx.z * kcs;
+  const int nk = min(kcs, K / 64 - kc0);
 
   if (warp == 0) {
     tc::tmem_alloc(&tmem_slot, NT);
     tc::tmem_relinquish();
   }
   if (threadIdx.x == 0) {
-    tc::mbar_init(&bar[0], 1);
-    tc::mbar_init(&bar[1], 1);
+    s_fail = 0;
+    for (int s = 0; s < kGemmStages; ++s) {
+      tc::mbar_init(&full[s], 1);
+      tc::mbar_init(&empty[s], 1);
+    }
+    tc::mbar_init(&done, 1);
     tc::fence_mbar_init();
+    tc::prefetch_tmap(&tmA);
+    tc::prefetch_tmap(&tmB);
   }
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = tmem_slot;
   constexpr uint32_t idesc = tc::idesc_bf16(128, NT);
-  bool ok = true;
-  // split K: this CTA takes the 64-wide chunks [kc0, kc0 + n) (kcs per split)
-  const int nk_all = K / 64, kc0 = blockIdx.z * kcs;
-  const int nk = min(kcs, nk_all - kc0);
-  for (int j = 0; j < nk; ++j) {
-    const int b = j & 1, kc = kc0 + j;
-    if (j >= 2) ok = ok && tc::mbar_wait(&bar[b], ((j >> 1) - 1) & 1, kWaitLimit);
-    stage_rows(bufA[b], A + (size_t)m0 * K, 128, K, kc * 64);
-    stage_rows(bufB[b], B + (size_t)n0 * K, NT, K, kc * 64);
-    tc::fence_proxy_async();
-    __syncthreads();
-    if (threadIdx.x == 0) {
+  if (threadIdx.x == 0) {
+    // chunk j uses stage j % 3 for the (j / 3)-th time: its full / empty
+    // phases have parity (j / 3) & 1
+    auto load = [&](int j) {
+      const int s = j % kGemmStages;
+      uint8_t* a = base + s * SBYTES;
+      tc::mbar_expect_tx(&full[s], SBYTES);
+      tc::tma_load_2d(a, &tmA, (kc0 + j) * 64, m0, &full[s]);
+      tc::tma_load_2d(a + ABYTES, &tmB, (kc0 + j) * 64, n0, &full[s]);
+    };
+    int issued = 0, consumed = 0;
+    bool ok = true;
+    for (; issued < nk && issued < kGemmStages; ++issued) load(issued);
+    for (int j = 0; j < nk && ok; ++j) {
+      const int s = j % kGemmStages;
+      if (!tc::mbar_wait(&full[s], (j / kGemmStages) & 1, kWaitLimit)) {
+        ok = false;
+        break;
+      }
+      consumed = j + 1;
       tc::fence_after_sync();
-      const uint32_t a0 = tc::smem_u32(bufA[b]), b0 = tc::smem_u32(bufB[b]);
+      const uint32_t a0 = tc::smem_u32(base + s * SBYTES), b0 = a0 + ABYTES;
 #pragma unroll
       for (int kk = 0; kk < 4; ++kk)
-        tc::mma_bf16(tmem, tc::sdesc_sw128(a0 + kk * 32), tc::sdesc_sw128(b0 + kk * 32), idesc,
-                     (j | kk) != 0);
-      tc::mma_commit(&bar[b]);
+        tc::mma_bf16(tmem, tc::sdesc_sw128(a0 + kk * 32), tc::sdesc_sw128(b0 + kk * 32), idesc, (j | kk) != 0);
+      tc::mma_commit(&empty[s]);
+      // refill the stage of chunk j - 1 (its MMAs queue ahead of chunk j's)
+      if (j >= 1 && issued < nk) {
+        const int sp = (j - 1) % kGemmStages;
+        if (!tc::mbar_wait(&empty[sp], ((j - 1) / kGemmStages) & 1, kWaitLimit)) {
+          ok = false;
+          break;
+        }
+        load(issued++);
+      }
+    }
+    tc::mma_commit(&done);   // every MMA issued so far
+    if (!ok) {
+      s_fail = 1;
+      // copies still in flight land before the CTA goes on
+      for (int c = consumed; c < issued; ++c) tc::mbar_wait(&full[c % kGemmStages], (c / kGemmStages) & 1, kWaitLimit);
     }
   }
-  // the last commit covers every MMA issued before it
-  const int last = nk - 1;
-  ok = ok && tc::mbar_wait(&bar[last & 1], (last >> 1) & 1, kWaitLimit);
+  const bool mma_ok = tc::mbar_wait(&done, 0, kWaitLimit);
+  const bool ok = __syncthreads_and(mma_ok && !s_fail) != 0;
   tc::fence_after_sync();
   if (ok) {
     const int row = m0 + warp * 32 + lane;
@@ -115,7 +141,38 @@ __global__ void __launch_bounds__(128) k_gemm_tn(const __nv_bfloat16* __restrict
   if (warp == 0) tc::tmem_dealloc(tmem, NT);
 }
 
-size_t gemm_smem(int nt) { return 2 * (128 * 128 + (size_t)nt * 128) + 1024; }
+// cuTensorMapEncodeTiled from the driver, through the runtime (no link
+// against the driver library).
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess) {
+      cudaGetLastError();
+      return (PFN_cuTensorMapEncodeTiled_v12000) nullptr;
+    }
+    return (PFN_cuTensorMapEncodeTiled_v12000)p;
+  }();
+  return fn;
+}
+
+// Tensor map of a rows x K row-major BF16 matrix read in boxes of `box_rows`
+// rows by 64 columns (128 bytes), 128-byte swizzled into shared memory.
+int bf16_tile_map(CUtensorMap* map, const void* ptr, int rows, int K, int box_rows) {
+  const PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) return MP_ECUDA;
+  const cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)K * 2};
+  const cuuint32_t box[2] = {64, (cuuint32_t)box_rows};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims, strides, box, estr,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? MP_OK : MP_ECUDA;
+}
+
+size_t gemm_smem(int nt) { return kGemmStages * (128 * 128 + (size_t)nt * 128) + 1024; }
 
 template <int NT>
 int launch_gemm(const __nv_bfloat16* A, const __nv_bfloat16* B, float* C, int M, int N, int K, int* status,
@@ -123,15 +180,19 @@ int launch_gemm(const __nv_bfloat16* A, const __nv_bfloat16* B, float* C, int M,
   const size_t sm = gemm_smem(NT);
   MP_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tn<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
   // few output tiles over a long K (the weight gradients: K = the batch):
-  // split K over more CTAs, at least 4 chunks each, and add up in C
+  // split K over more CTAs, at least 8 chunks each, and add up in C
   const int tiles = (M / 128) * (N / NT), nk = K / 64;
   int splits = 1;
-  if (tiles < 64 && nk >= 8) splits = std::min(nk / 4, std::max(1, 128 / tiles));
+  if (tiles < 64 && nk >= 8) splits = std::min(nk / 8, std::max(1, 128 / tiles));
   const int kcs = (nk + splits - 1) / splits;
   splits = (nk + kcs - 1) / kcs;
   if (splits > 1) MP_CUDA_TRY(cudaMemsetAsync(C, 0, (size_t)M * N * sizeof(float), st));
+  CUtensorMap tmA, tmB;
+  int rc = bf16_tile_map(&tmA, A, M, K, 128);
+  if (!rc) rc = bf16_tile_map(&tmB, B, N, K, NT);
+  if (rc) return rc;
   dim3 grid(M / 128, N / NT, splits);
-  k_gemm_tn<NT><<<grid, 128, sm, st>>>(A, B, C, M, N, K, kcs, status);
+  k_gemm_tn<NT><<<grid, 128, sm, st>>>(tmA, tmB, C, M, N, K, kcs, status);
   count_launch();
   MP_CUDA_TRY(cudaGetLastError());
   return MP_OK;
@@ -145,9 +206,15 @@ int gemm_tn(const void* A, const void* B, float* C, int M, int N, int K, int* st
   if ((((uintptr_t)A) | ((uintptr_t)B) | ((uintptr_t)C)) & 15) return MP_EINVAL;
   const __nv_bfloat16* a = (const __nv_bfloat16*)A;
   const __nv_bfloat16* b = (const __nv_bfloat16*)B;
-  if (N % 256 == 0) return launch_gemm<256>(a, b, C, M, N, K, status, st);
-  if (N % 128 == 0) return launch_gemm<128>(a, b, C, M, N, K, status, st);
+  // the widest tile that still gives about a wave of CTAs (the training
+  // step's products are a few hundred MFLOP: 4096 x 256 at 128 x 256 tiles
+  // would occupy 32 of the SMs)
+  const int want = 128;
+  if (N % 256 == 0 && (M / 128) * (N / 256) >= want) return launch_gemm<256>(a, b, C, M, N, K, status, st);
+  if (N % 128 == 0 && (M / 128) * (N / 128) >= want) return launch_gemm<128>(a, b, C, M, N, K, status, st);
   if (N % 64 == 0) return launch_gemm<64>(a, b, C, M, N, K, status, st);
+  if (N % 128 == 0) return launch_gemm<128>(a, b, C, M, N, K, status, st);
+  if (N % 256 == 0) return launch_gemm<256>(a, b, C, M, N, K, status, st);
   return MP_EINVAL;
 }
 

@@ -60,6 +60,21 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
       : "memory");
 }
 
+// Tiled bulk tensor copy (TMA) of a 2-D box at coordinates (x, y) -- x the
+// innermost dimension, in elements -- from the tensor map's global tensor into
+// shared memory, completing on the barrier.  The map must live in parameter,
+// constant or global memory (a __grid_constant__ kernel parameter).
+__device__ __forceinline__ void tma_load_2d(void* dst, const void* tmap, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+      ::"r"(smem_u32(dst)), "l"(tmap), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void prefetch_tmap(const void* tmap) {
+  asm volatile("prefetch.tensormap [%0];" ::"l"(tmap) : "memory");
+}
+
 // ------------------------------------------------------------ tensor memory
 
 // Whole warp: allocate ncols (power of two >= 32) columns; the address is
