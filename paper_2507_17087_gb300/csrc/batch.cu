@@ -438,7 +438,7 @@ int upload_tiles(mp_batch& b, uint32_t tile_groups) {
   b.tile_groups = tile_groups;
   // launch shape of the persistent id writer: every resident CTA slot
   b.ids_smem = (size_t)((b.maxP + 3) & ~3u) * 4 + (size_t)b.maxC * 4;
-  if (b.ids_smem > 48 * 1024)
+  if (b.ids_smem > 40 * 1024)   // opt in with room for static shared memory
     MP_CUDA_TRY(cudaFuncSetAttribute(k_b_ids, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b.ids_smem));
   int per_sm = 0;
   MP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_b_ids, kThreads, b.ids_smem));

@@ -1171,7 +1171,7 @@ int launch_sel_costs(const mp_search_query& q, const Prepared& pq, const SelBufs
   const int wpc = (int)std::max<size_t>(1, std::min<size_t>(4, (size_t)(100 * 1024) / per_warp));
   const size_t smem = per_warp * wpc;
   if (smem > 227 * 1024) return MP_ENOTSUP;
-  if (smem > 48 * 1024)
+  if (smem > 40 * 1024)   // opt in with room for static shared memory
     MP_CUDA_TRY(cudaFuncSetAttribute(k_sel_costs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
   MP_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sel_costs, 32 * wpc, smem));

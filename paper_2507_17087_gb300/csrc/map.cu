@@ -567,7 +567,7 @@ int run_launch_ws(const Plan& pl, const Want& w, const Layout& ly, char* ws, cud
       return (unsigned)blocks;
     };
     auto go = [&](const void* kern, size_t sm, auto launch) {
-      if (sm > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      if (sm > 40 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
       uint64_t gpw = 0;
       const unsigned blocks = grid_for(kern, sm, gpw);
       launch(blocks, gpw);

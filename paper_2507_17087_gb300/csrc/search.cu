@@ -35,10 +35,10 @@ size_t align_up(size_t v) { return (v + 255) & ~size_t(255); }
 // full = 1: every candidate's secondary is scanned.  full = 0: candidates
 // whose (exact, closed-form) primary exceeds the minimum primary over all
 // factorisations cannot win the lexicographic argmin and are not scanned.
-// PRE: the precounted fibre tables (full search; shared memory allows three
-// CTAs per SM, so the registers are bounded for three too).
+// PRE: the precounted fibre tables (full search; one byte per fibre, so that
+// with the table and bitmaps four CTAs fit on an SM, as the registers do).
 template <bool PRE>
-__global__ void __launch_bounds__(256, PRE ? 3 : 4) k_search(const ChainProg* __restrict__ progs, const Fact* __restrict__ facts, int nf,
+__global__ void __launch_bounds__(256, 4) k_search(const ChainProg* __restrict__ progs, const Fact* __restrict__ facts, int nf,
                          uint32_t P, uint32_t E0, uint32_t E1, uint32_t E2, int words,
                          unsigned long long nchains, int full, unsigned long long ub,
                          const uint8_t* __restrict__ skip, const uint16_t* __restrict__ gtab, uint32_t Pp,
@@ -51,7 +51,7 @@ __global__ void __launch_bounds__(256, PRE ? 3 : 4) k_search(const ChainProg* __
   // npre > 0: after the table, the precounted fibre counts of every divisor
   // d = s_pdiv[k] <= kPreMaxDiv: the P / d blocks of d consecutive flat
   // indices at s_poff[k], then the P / d residue classes modulo P / d
-  uint16_t* dtab = reinterpret_cast<uint16_t*>(smem_raw + (size_t)words * blockDim.x * 4 + (((size_t)P * 2 + 255) & ~(size_t)255));
+  uint8_t* dtab = reinterpret_cast<uint8_t*>(smem_raw + (size_t)words * blockDim.x * 4 + (((size_t)P * 2 + 255) & ~(size_t)255));
   const uint32_t c = blockIdx.x;
   __shared__ ChainProg cp;
   if (threadIdx.x == 0) cp = progs[c];
@@ -77,12 +77,12 @@ __global__ void __launch_bounds__(256, PRE ? 3 : 4) k_search(const ChainProg* __
       const uint32_t d = s_pdiv[lo], m = s_pm[lo], local = i - s_poff[lo];
       const bool blk = local < m;
       const uint32_t base = blk ? local * d : local - m, stride = blk ? 1u : m;
-      dtab[i] = (uint16_t)fibre_distinct(tab, bm + threadIdx.x, blockDim.x, words, base, stride, d, d, d);
+      dtab[i] = (uint8_t)(fibre_distinct(tab, bm + threadIdx.x, blockDim.x, words, base, stride, d, d, d) - 1);
     }
     __syncthreads();
   }
   // the precounted table of divisor v (null when v is not precounted)
-  auto pre_of = [&](uint32_t v, bool res) -> const uint16_t* {
+  auto pre_of = [&](uint32_t v, bool res) -> const uint8_t* {
     if (!PRE || npre == 0 || v > kPreMaxDiv) return nullptr;
     int lo = 0, hi = npre;
     while (hi - lo > 1) {
@@ -118,8 +118,8 @@ __global__ void __launch_bounds__(256, PRE ? 3 : 4) k_search(const ChainProg* __
     if (!full && k.p > pmin) continue;   // uniform across the warp
     if (skip && skip[fr]) continue;
     // families 0 and 2 from the precounted fibres where every block holds tiles
-    const uint16_t* pre0 = E[0] >= f[0] ? pre_of(f[0], false) : nullptr;
-    const uint16_t* pre2 = E[2] >= f[2] ? pre_of(f[2], true) : nullptr;
+    const uint8_t* pre0 = E[0] >= f[0] ? pre_of(f[0], false) : nullptr;
+    const uint8_t* pre2 = E[2] >= f[2] ? pre_of(f[2], true) : nullptr;
     k.s = secondary_cost_warp<!PRE>(tab, wbm, blockDim.x, words, E, f, lane, ub, pre0, pre2);
     k.idx = (unsigned long long)fr * nchains + c;
     if (key_less(k, best)) best = k;
@@ -374,7 +374,7 @@ int exhaustive_search(const mp_search_query& q, mp_search_result* out, cudaStrea
         mv.push_back((uint32_t)q.procs / d);
         ov.push_back(ov.back() + 2 * ((uint32_t)q.procs / d));
       }
-    const size_t need = S.smem + align_up((size_t)ov.back() * 2);
+    const size_t need = S.smem + align_up((size_t)ov.back());
     if ((int)dv.size() <= kPreMaxN && need <= (size_t)kSmemBudget) {
       npre = (int)dv.size();
       smem = need;
@@ -396,7 +396,9 @@ int exhaustive_search(const mp_search_query& q, mp_search_result* out, cudaStrea
     MP_CUDA_TRY(cudaMemcpyAsync(d_skip, skip->data(), NF, cudaMemcpyHostToDevice, st));
   }
   const void* kern = npre ? (const void*)k_search<true> : (const void*)k_search<false>;
-  if (smem > 48 * 1024)
+  // the opt-in also covers dynamic memory just under 48 KB that the kernel's
+  // static shared memory takes past it
+  if (smem > 32 * 1024)
     MP_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   auto launch = npre ? k_search<true> : k_search<false>;
   launch<<<(unsigned)NC, S.threads, smem, st>>>(D->progs, D->facts, (int)S.c->facts.size(), (uint32_t)q.procs,
@@ -419,7 +421,7 @@ int exhaustive_search(const mp_search_query& q, mp_search_result* out, cudaStrea
 int candidate_costs_dev(const mp_search_query& q, const SearchSpace& S, const DeviceSpace& D, const int64_t* d_idx,
                         int64_t n, uint64_t* d_p, uint64_t* d_s, cudaStream_t st) {
   if (n <= 0) return MP_OK;
-  if (S.smem > 48 * 1024)
+  if (S.smem > 40 * 1024)   // opt in with room for static shared memory
     MP_CUDA_TRY(cudaFuncSetAttribute(k_candidate_costs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S.smem));
   k_candidate_costs<<<(unsigned)n, S.threads, S.smem, st>>>(D.progs, D.facts, (int)S.c->facts.size(), d_idx,
                                                              (unsigned long long)S.c->chains.size(), (uint32_t)q.procs,
@@ -476,7 +478,7 @@ extern "C" int mp_candidate_costs(const mp_search_query* query, const int64_t* i
   uint64_t* d_p = p_dev ? primary : (uint64_t*)(rest + ib);
   uint64_t* d_s = s_dev ? secondary : (uint64_t*)(rest + 2 * ib);
   if (!idx_dev) MP_CUDA_TRY(cudaMemcpyAsync(d_idx, host_idx.data(), n * 8, cudaMemcpyHostToDevice, st));
-  if (S.smem > 48 * 1024)
+  if (S.smem > 40 * 1024)   // opt in with room for static shared memory
     MP_CUDA_TRY(cudaFuncSetAttribute(k_candidate_costs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S.smem));
   k_candidate_costs<<<(unsigned)n, S.threads, S.smem, st>>>(D->progs, D->facts, (int)NF, d_idx, NC,
                                                              (uint32_t)query->procs, (uint32_t)query->M,

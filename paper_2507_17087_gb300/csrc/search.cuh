@@ -184,7 +184,8 @@ __device__ __forceinline__ unsigned long long warp_sum(unsigned long long v) {
 // Every lane returns the total.
 // ub: once the running total exceeds it the remaining families are skipped
 // and ~0 is returned (the caller only needs costs up to ub).
-// pre0 / pre2 (may be null): the distinct-node counts of family 0's fibres
+// pre0 / pre2 (may be null): the distinct-node counts minus one (a byte: a
+// precounted fibre has at most 256 points) of family 0's fibres
 // (the blocks of f0 consecutive flat indices, by block) and of family 2's
 // (the residue classes modulo P / f2, by residue), counted once per chain
 // for every divisor and looked up here instead of scanned.
@@ -195,8 +196,8 @@ __device__ __forceinline__ unsigned long long secondary_cost_warp(const uint16_t
                                                                   int stride, int words, const uint32_t E[3],
                                                                   const uint32_t f[3], int lane,
                                                                   unsigned long long ub = ~0ull,
-                                                                  const uint16_t* __restrict__ pre0 = nullptr,
-                                                                  const uint16_t* __restrict__ pre2 = nullptr) {
+                                                                  const uint8_t* __restrict__ pre0 = nullptr,
+                                                                  const uint8_t* __restrict__ pre2 = nullptr) {
   const uint32_t fstride[3] = {1u, f[0], f[0] * f[1]};
   uint32_t n[3];
   for (int t = 0; t < 3; ++t) n[t] = E[t] < f[t] ? E[t] : f[t];
@@ -207,7 +208,7 @@ __device__ __forceinline__ unsigned long long secondary_cost_warp(const uint16_t
     const int u = v == 0 ? 1 : 0;
     const int w = v == 2 ? 1 : 2;
     const uint32_t nfib = n[u] * n[w];
-    const uint16_t* pre = v == 0 ? pre0 : (v == 2 ? pre2 : nullptr);
+    const uint8_t* pre = v == 0 ? pre0 : (v == 2 ? pre2 : nullptr);
     if (nfib >= 32 || pre) {
       const uint32_t chunk = (nfib + 31) / 32;
       const uint32_t fb0 = lane * chunk, fb1 = min(nfib, fb0 + chunk);
@@ -223,7 +224,7 @@ __device__ __forceinline__ unsigned long long secondary_cost_warp(const uint16_t
           const uint32_t rep_u = itu.rep;
           const uint32_t wt_u = itu.step();
           const uint32_t base = rep_u * fstride[u] + rep_w * fstride[w];
-          const uint32_t D = pre ? (uint32_t)pre[v == 0 ? rep_u + rep_w * f[1] : base]
+          const uint32_t D = pre ? (uint32_t)pre[v == 0 ? rep_u + rep_w * f[1] : base] + 1u
                                  : fibre_distinct(tab, bm + lane, stride, words, base, fstride[v], E[v], f[v], n[v]);
           part += (unsigned long long)wt_u * wt_w * (D - 1);
           if (++iu == n[u]) {
