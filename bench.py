@@ -561,8 +561,22 @@ def profile_case_train(N, torch):
     m.close()
 
 
+def profile_case_learned(N, torch):
+    """A briefly trained and calibrated model, then the learned search
+    (exact costs of the top 1024, no fallback) on six held-out queries,
+    twice each (the first builds each candidate space)."""
+    m = N.MLP(seed=11)
+    m.train_search(W.search_training_queries(64), samples_per_query=2048, epochs=2, batch=4096, lr=2e-3, seed=3)
+    m.calibrate(W.search_training_queries(16, first_index=40000))
+    for q in W.search_queries(6, first_index=9000):
+        N.decompose_search([q])
+        for _ in range(2):
+            m.learned_search(q, K=1024, fallback=False)
+    m.close()
+
+
 PROFILE_CASES = {"ids-small": profile_case_ids, "search": profile_case_search, "score": profile_case_score,
-                 "train-step": profile_case_train,
+                 "train-step": profile_case_train, "learned": profile_case_learned,
                  "score-features": profile_case_score_features, "batched": profile_case_batched}
 
 

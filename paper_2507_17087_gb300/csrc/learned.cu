@@ -478,31 +478,41 @@ __device__ __forceinline__ float key_value(uint32_t key) {
   return __uint_as_float((key & 0x80000000u) ? (key ^ 0x80000000u) : ~key);
 }
 
-// Zeroes one selection's counters: the 65536 bins of the score histogram
-// and `words` more counter words after them.
+// Zeroes one selection's counters: the 65536 fine and 256 coarse bins of the
+// score histogram and `words` more counter words after them.
 __global__ void k_sel_init(unsigned* __restrict__ hist, unsigned words) {
-  const unsigned n = 65536 + words;
+  const unsigned n = 65536 + 256 + words;
   for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) hist[i] = 0;
 }
 
-// 65536-bin histogram of the order keys' upper halves; the lanes of a warp
-// that fall into one bin add once (the scores crowd into few bins);
-// nonfinite counts the NaN / infinite scores (a model that produced one
-// gets no margin)
+// 65536-bin histogram of the order keys' upper halves and a 256-bin coarse
+// one of their top bytes (per CTA in shared memory, then added to the
+// global one).  The scores crowd into few bins, so the lanes of a warp that
+// share a bin add once; nonfinite counts the NaN / infinite scores (a model
+// that produced one gets no margin).
 __global__ void k_topk_hist(const float* __restrict__ s, unsigned long long n, unsigned* __restrict__ hist,
-                            unsigned* __restrict__ nonfinite) {
+                            unsigned* __restrict__ coarse, unsigned* __restrict__ nonfinite) {
+  __shared__ unsigned c[256];
+  for (int i = threadIdx.x; i < 256; i += blockDim.x) c[i] = 0;
+  __syncthreads();
+  const unsigned lane = threadIdx.x & 31;
   unsigned bad = 0;
   for (unsigned long long i0 = (unsigned long long)blockIdx.x * blockDim.x; i0 < n;
        i0 += (unsigned long long)gridDim.x * blockDim.x) {
     const unsigned long long i = i0 + threadIdx.x;
     const bool in = i < n;
     const float v = in ? s[i] : 0.f;
-    const unsigned bin = in ? order_key(v) >> 16 : 0xFFFFFFFFu;
-    const unsigned peers = __match_any_sync(0xFFFFFFFFu, bin);
-    if (in && (threadIdx.x & 31) == (unsigned)(__ffs(peers) - 1)) atomicAdd(hist + bin, (unsigned)__popc(peers));
+    const uint32_t key = order_key(v);
+    const unsigned fine = in ? key >> 16 : 0xFFFFFFFFu, top = in ? key >> 24 : 0xFFFFFFFFu;
+    const unsigned pf = __match_any_sync(0xFFFFFFFFu, fine), pt = __match_any_sync(0xFFFFFFFFu, top);
+    if (in && lane == (unsigned)(__ffs(pf) - 1)) atomicAdd(hist + fine, (unsigned)__popc(pf));
+    if (in && lane == (unsigned)(__ffs(pt) - 1)) atomicAdd(c + top, (unsigned)__popc(pt));
     bad += in && !isfinite(v);
   }
   if (bad) atomicAdd(nonfinite, bad);
+  __syncthreads();
+  for (int i = threadIdx.x; i < 256; i += blockDim.x)
+    if (c[i]) atomicAdd(coarse + i, c[i]);
 }
 
 // Inclusive prefix sum over a CTA of 256 threads (8 warps).
@@ -520,28 +530,20 @@ __device__ __forceinline__ unsigned block_scan256(unsigned v, unsigned* warp_tot
   return v + add;
 }
 
-// Smallest bin T whose cumulative count reaches K, through coarse bins (sums
-// of 256 fine bins, formed here) then the fine bins of the chosen one.  out[0] = T, out[1] = count below T; out[2] = the first
+// Smallest bin T whose cumulative count reaches K, through the coarse
+// histogram (256 bins of 256 fine bins each) then the fine bins of the
+// chosen coarse bin.  out[0] = T, out[1] = count below T; out[2] = the first
 // bin not yet selected: 0, or with grow set one past the previous threshold
 // (out[0] on entry).  Also resets the collection's counters (cnt[0], cnt[1])
 // and its least left-out key (cnt[2]).  One CTA of 256 threads.
-__global__ void __launch_bounds__(256) k_topk_threshold(const unsigned* __restrict__ hist, unsigned K, int grow,
+__global__ void __launch_bounds__(256) k_topk_threshold(const unsigned* __restrict__ hist,
+                                                        const unsigned* __restrict__ coarse, unsigned K, int grow,
                                                         unsigned* __restrict__ out, unsigned* __restrict__ cnt) {
   __shared__ unsigned warp_tot[8];
   __shared__ unsigned pick[2];
-  __shared__ unsigned coarse[256];
   const unsigned t = threadIdx.x;
   const unsigned prev = out[0];
   if (t < 3) cnt[t] = t < 2 ? 0u : 0xFFFFFFFFu;   // the collection's counts and least left-out key
-  // coarse bins: warp w sums fine bins 256 b .. 256 b + 255 for b = w, w + 8, ...
-  const unsigned lane = t & 31, warp = t >> 5;
-  for (unsigned b = warp; b < 256; b += 8) {
-    unsigned v = 0;
-    for (unsigned j = lane; j < 256; j += 32) v += hist[b * 256 + j];
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
-    if (lane == 0) coarse[b] = v;
-  }
-  __syncthreads();
   const unsigned cc = coarse[t];
   const unsigned cum_c = block_scan256(cc, warp_tot);
   if (cum_c - cc < K && cum_c >= K) {
@@ -1124,7 +1126,7 @@ size_t sel_capacity(unsigned cap_a, unsigned cap_b) { return 2 * ((size_t)cap_a 
 // Device buffers of one learned search (scores, histogram, selection).
 struct SelBufs {
   float* sc;
-  unsigned *hist, *thr, *cnt, *nonfinite;
+  unsigned *hist, *coarse, *thr, *cnt, *nonfinite;
   int64_t *below, *eq, *sel_idx;
   uint64_t *sel_p, *sel_s;
   float* sel_y;
@@ -1134,10 +1136,10 @@ struct SelBufs {
 
 int sel_bufs(uint64_t ncand, unsigned cap_a, unsigned cap_b, size_t nfl, SelBufs& b) {
   const size_t cap = sel_capacity(cap_a, cap_b);
-  // hist (65536 words), then the counters k_sel_init also clears (cnt,
-  // nonfinite: kInitWords); thr is kept across rounds
-  const size_t o_sc = 0, o_hist = a256(ncand * 4), o_cnt = o_hist + 65536 * 4, o_nf = o_cnt + 16,
-               o_thr = o_hist + a256((65536 + kInitWords) * 4), o_below = o_thr + 256,
+  // hist (65536 words), coarse (256 words), then the counters k_sel_init
+  // also clears (cnt, nonfinite: kInitWords); thr is kept across rounds
+  const size_t o_sc = 0, o_hist = a256(ncand * 4), o_coarse = o_hist + 65536 * 4, o_cnt = o_coarse + 256 * 4,
+               o_nf = o_cnt + 16, o_thr = o_hist + a256((65536 + 256 + kInitWords) * 4), o_below = o_thr + 256,
                o_eq = o_below + a256((size_t)cap_a * 8),
                o_idx = o_eq + a256((size_t)cap_b * 8), o_p = o_idx + a256(cap * 8), o_s = o_p + a256(cap * 8),
                o_y = o_s + a256(cap * 8), o_fl = o_y + a256(cap * 4), o_res = o_fl + a256(nfl * 4),
@@ -1146,6 +1148,7 @@ int sel_bufs(uint64_t ncand, unsigned cap_a, unsigned cap_b, size_t nfl, SelBufs
   if (!w) return MP_ENOMEM;
   b.sc = (float*)(w + o_sc);
   b.hist = (unsigned*)(w + o_hist);
+  b.coarse = (unsigned*)(w + o_coarse);
   b.thr = (unsigned*)(w + o_thr);
   b.cnt = (unsigned*)(w + o_cnt);
   b.nonfinite = (unsigned*)(w + o_nf);
@@ -1293,7 +1296,7 @@ extern "C" int mp_learned_search(mp_mlp* h, const mp_search_query* query, int K,
   count_launch();
   if ((rc = score_candidates(h, pq, b.fl, ncand, b.sc, st))) return rc;
   const unsigned gb = (unsigned)std::min<uint64_t>((ncand + 255) / 256, (uint64_t)sm_count_l() * 8);
-  k_topk_hist<<<gb, 256, 0, st>>>(b.sc, ncand, b.hist, b.nonfinite);
+  k_topk_hist<<<gb, 256, 0, st>>>(b.sc, ncand, b.hist, b.coarse, b.nonfinite);
   count_launch();
   MP_CUDA_TRY(cudaGetLastError());
   if (ev) MP_CUDA_TRY(cudaEventRecord(ev[1], st));
@@ -1314,7 +1317,7 @@ extern "C" int mp_learned_search(mp_mlp* h, const mp_search_query* query, int K,
     // the previous threshold) and reduces them with the earlier ones
     const unsigned n_prev = rounds ? r.n : 0;
     const int prev_complete = r.complete;
-    k_topk_threshold<<<1, 256, 0, st>>>(b.hist, Kc, rounds ? 1 : 0, b.thr, b.cnt);
+    k_topk_threshold<<<1, 256, 0, st>>>(b.hist, b.coarse, Kc, rounds ? 1 : 0, b.thr, b.cnt);
     k_topk_collect<<<gb, 256, 0, st>>>(b.sc, ncand, b.thr, b.below, b.cnt, b.eq, b.cnt + 1, Kc, cap_b, b.cnt + 2);
     count_launch(2);
     MP_CUDA_TRY(cudaGetLastError());
