@@ -663,7 +663,7 @@ __global__ void k_sel_costs(const ChainProg* __restrict__ progs, const Fact* __r
       __syncwarp();
     }
     const uint32_t f[3] = {facts[fr].f[0], facts[fr].f[1], facts[fr].f[2]};
-    const unsigned long long sec = secondary_cost_warp<true>(tab, bm, 32, words, E, f, lane);
+    const unsigned long long sec = secondary_cost_warp<true, true>(tab, bm, 32, words, E, f, lane);
     if (lane == 0) {
       sel_idx[out0 + i] = (int64_t)(fr * nchains + c);
       sel_p[out0 + i] = primary_cost(E, f);

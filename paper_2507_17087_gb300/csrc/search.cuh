@@ -118,14 +118,21 @@ struct BlockIter {
 
 // Distinct nodes along one fibre (count of nodes seen), bitmap per thread in
 // shared memory (word w of thread t at bm[w * nthr + t]).
+// ROT: the scan begins with element `start` (< n) and wraps round to it (the
+// count does not depend on the order); threads that scan neighbouring fibres
+// at power-of-two strides then start at different elements, so that their
+// table reads fall into different shared-memory banks.
+template <bool ROT = false>
 __device__ __forceinline__ uint32_t fibre_distinct(const uint16_t* __restrict__ tab, uint32_t* bm, int nthr,
                                                    int words, uint32_t base, uint32_t stride, uint32_t E,
-                                                   uint32_t f, uint32_t n) {
+                                                   uint32_t f, uint32_t n, uint32_t start = 0) {
   if (E >= f) {
-    // every block holds tiles: the fibre's blocks are 0 .. n - 1 in order
-    const uint16_t* p = tab + base;
+    // every block holds tiles: the fibre's blocks are 0 .. n - 1
+    const uint16_t* p0 = tab + base;
+    const uint16_t* p = ROT ? p0 + start * stride : p0;
+    uint32_t j = start;
     uint32_t D = 0;
-    for (uint32_t iv = 0; iv < n; ++iv, p += stride) {
+    for (uint32_t iv = 0; iv < n; ++iv) {
       const uint32_t node = *p;
       uint32_t* wp = bm + (node >> 5) * nthr;
       const uint32_t bit = 1u << (node & 31);
@@ -134,11 +141,17 @@ __device__ __forceinline__ uint32_t fibre_distinct(const uint16_t* __restrict__ 
         *wp = word | bit;
         ++D;
       }
+      if (ROT && ++j == n) {
+        j = 0;
+        p = p0;
+      } else {
+        p += stride;
+      }
     }
     if ((uint32_t)words <= n) {
       for (int w = 0; w < words; ++w) bm[w * nthr] = 0;
     } else {
-      p = tab + base;
+      p = p0;
       for (uint32_t iv = 0; iv < n; ++iv, p += stride) bm[(*p >> 5) * nthr] = 0;
     }
     return D;
@@ -191,7 +204,11 @@ __device__ __forceinline__ unsigned long long warp_sum(unsigned long long v) {
 // for every divisor and looked up here instead of scanned.
 // UNROLL: the three families unrolled (their extents in registers rather
 // than local memory); faster without the precounted tables, slower with them.
-template <bool UNROLL = false>
+// ROT: each lane starts its fibre scans at element lane mod n (spreads the
+// table reads over shared-memory banks when the lanes' fibres lie a power of
+// two apart; measured faster for the learned search's one-candidate warps,
+// slower in the full search, whose warps share one table).
+template <bool UNROLL = false, bool ROT = false>
 __device__ __forceinline__ unsigned long long secondary_cost_warp(const uint16_t* __restrict__ tab, uint32_t* bm,
                                                                   int stride, int words, const uint32_t E[3],
                                                                   const uint32_t f[3], int lane,
@@ -210,6 +227,7 @@ __device__ __forceinline__ unsigned long long secondary_cost_warp(const uint16_t
     const uint32_t nfib = n[u] * n[w];
     const uint8_t* pre = v == 0 ? pre0 : (v == 2 ? pre2 : nullptr);
     if (nfib >= 32 || pre) {
+      const uint32_t rot = ROT ? (uint32_t)lane % n[v] : 0u;
       const uint32_t chunk = (nfib + 31) / 32;
       const uint32_t fb0 = lane * chunk, fb1 = min(nfib, fb0 + chunk);
       unsigned long long part = 0;
@@ -225,7 +243,8 @@ __device__ __forceinline__ unsigned long long secondary_cost_warp(const uint16_t
           const uint32_t wt_u = itu.step();
           const uint32_t base = rep_u * fstride[u] + rep_w * fstride[w];
           const uint32_t D = pre ? (uint32_t)pre[v == 0 ? rep_u + rep_w * f[1] : base] + 1u
-                                 : fibre_distinct(tab, bm + lane, stride, words, base, fstride[v], E[v], f[v], n[v]);
+                                 : fibre_distinct<ROT>(tab, bm + lane, stride, words, base, fstride[v], E[v], f[v],
+                                                       n[v], rot);
           part += (unsigned long long)wt_u * wt_w * (D - 1);
           if (++iu == n[u]) {
             iu = 0;
