@@ -158,8 +158,10 @@ __device__ __forceinline__ void candidate_features(const QInfo& Q, const uint16_
 // second term varies, over a range of a few units).
 __device__ __forceinline__ float target_of(unsigned long long p_tiles, unsigned long long s_tiles,
                                            unsigned long long pmin) {
+  const float sec = log2f(1.f + (float)s_tiles) / 8.f;
+  if (p_tiles == pmin) return sec;   // the same value (2 * 0 + sec) without a double division
   const float pn = (float)((double)p_tiles / (double)max(pmin, 1ull) - 1.0);
-  return 2.f * fminf(pn, 16.f) + log2f(1.f + (float)s_tiles) / 8.f;
+  return 2.f * fminf(pn, 16.f) + sec;
 }
 
 
@@ -1268,7 +1270,12 @@ extern "C" int mp_learned_search(mp_mlp* h, const mp_search_query* query, int K,
   const unsigned cap_b = 1u << 16;
   SelBufs b;
   if ((rc = sel_bufs(ncand, cap_a, cap_b, flist.size(), b))) return rc;
-  MP_CUDA_TRY(cudaMemcpyAsync(b.fl, flist.data(), flist.size() * 4, cudaMemcpyHostToDevice, st));
+  // host staging (pinned): the result record, the status word, then the
+  // scored factorisations (copied asynchronously from there)
+  char* stage = g_host_stage.get(256 + flist.size() * 4);
+  if (!stage) return MP_ENOMEM;
+  std::memcpy(stage + 256, flist.data(), flist.size() * 4);
+  MP_CUDA_TRY(cudaMemcpyAsync(b.fl, stage + 256, flist.size() * 4, cudaMemcpyHostToDevice, st));
   // a lower bound on the secondary of every candidate that can win (the
   // least-primary factorisations); reaching it certifies the winner
   uint64_t min_lb = ~0ull;
@@ -1280,9 +1287,8 @@ extern "C" int mp_learned_search(mp_mlp* h, const mp_search_query* query, int K,
       lb_of[fr] = secondary_lower_bound(pq.Q.E, f, pq.Q.n, pq.Q.g);
       min_lb = std::min(min_lb, lb_of[fr]);
     }
-  SelResult* hres = (SelResult*)g_host_stage.get(256);
-  if (!hres) return MP_ENOMEM;
-  int* hstatus = (int*)((char*)hres + 128);
+  SelResult* hres = (SelResult*)stage;
+  int* hstatus = (int*)(stage + 128);
   if (stats) stats->ms_prepare = ms_since(t_phase);
   t_phase = clk::now();
   // phase boundaries on the stream (device time): scoring start, scores
