@@ -244,6 +244,34 @@ def test_learned_search_gains_over_the_search_without_it():
     untrained.close()
 
 
+def test_learned_search_edge_cases():
+    # pools smaller than K (every candidate of least primary evaluated: the
+    # first certificate), K = 1, one node, one processor per node; every
+    # result's cost tuple equals the exact search's, and the exhaustive
+    # oracle's on the small machines
+    model = N.MLP(seed=12)
+    model.train_search(W.search_training_queries(8), samples_per_query=1024, epochs=2, batch=1024, lr=1e-3, seed=4)
+    cases = [{"MNK": (16, 8, 64), "machine": (2, 4), "max_depth": 2},
+             {"MNK": (64, 64, 1), "machine": (1, 8), "max_depth": 1},
+             {"MNK": (5, 7, 3), "machine": (6, 1), "max_depth": 2},
+             {"MNK": (256, 1024, 256), "machine": (16, 8), "max_depth": 2}]
+    for q in cases:
+        q = dict(q, tile_bytes=512 * 512 * 4)
+        exact = N.decompose_search([q])[0]
+        want = (exact["primary_bytes"], exact["secondary_bytes"])
+        for K in (1, 64, 65536):
+            got = model.learned_search(q, K=K, fallback=True)
+            assert (got["primary_bytes"], got["secondary_bytes"]) == want, (q, K)
+            if K >= got["n_scored"]:
+                assert got["certified"] == 1 and not got["fallback"]
+        if q["machine"][0] * q["machine"][1] <= 16:
+            ref = O.search(*q["MNK"], q["machine"], q["max_depth"], threads=8)
+            assert want == (ref["primary"] * q["tile_bytes"], ref["secondary"] * q["tile_bytes"])
+    with pytest.raises(N.MapleError):
+        model.learned_search(cases[0] | {"tile_bytes": 512 * 512 * 4}, K=0)
+    model.close()
+
+
 def test_fibre_features_against_oracle_nodes():
     # features 53..58 of a candidate (factorisation f, chain c): whether the
     # node changes one step along each fibre, and how many distinct nodes its
