@@ -6,12 +6,14 @@
 //              along each final dimension)
 //   scoring    k_feat_img writes the candidates' features as swizzled BF16
 //              operand tiles (full occupancy hides the feature arithmetic's
-//              latency); k_mlp_img, one persistent CTA of 512 threads per
-//              SM, bulk-copies two tiles and the nine weight chunk images
-//              (double-buffered) into shared memory and runs the three
-//              hidden layers as tcgen05 MMAs with FP32 accumulators in 512
-//              TMEM columns; its 16 warps run the epilogues (four per tile
-//              and half of its columns) and the output dot product
+//              latency); k_mlp_img, one persistent CTA per SM, runs the three
+//              hidden layers of two tiles at a time as tcgen05 MMAs with FP32
+//              accumulators in 512 TMEM columns: a copy warp streams the
+//              weights in 16 KB slices through a five-deep ring, one MMA
+//              warp per tile issues, and 16 epilogue warps apply bias and
+//              ReLU (and the output dot product) by halves of the columns,
+//              each half's epilogue under the other half's (and the other
+//              tile's) MMAs
 //   top-K      65536-bin histogram of the order-preserving score keys, a
 //              threshold bin, and a compaction of the candidates at or below
 //   exact      the top-K are re-evaluated by the exact cost kernel; the
@@ -187,13 +189,8 @@ __global__ void k_features_idx(const __grid_constant__ QInfo Q, const uint16_t* 
 // operand images (one 16 KB K-major, 128-byte swizzled tile of 128 rows per
 // 128 candidates; rows past the end are zero) at full occupancy, where the
 // latency of the feature arithmetic (chain walks, table loads) hides behind
-// many resident warps.  k_mlp_img then runs the three layers on those tiles:
-// a persistent CTA per SM takes two tiles (256 candidates) per pass, bulk-
-// copies them and the nine 32 KB weight chunk images into shared memory
-// (weights double-buffered, the next chunk in flight while the current
-// chunk's MMAs run), accumulates both tiles in 512 TMEM columns, and runs the
-// epilogues with warps 0-3 and 8-11 on the first tile (columns 0-127 and
-// 128-255), warps 4-7 and 12-15 on the second.
+// many resident warps.  k_mlp_img then runs the three layers on those tiles,
+// two per pass (256 candidates), in a persistent CTA per SM.
 
 constexpr uint32_t kTileBytes = 128 * 128;   // 128 rows x 64 BF16
 
@@ -229,98 +226,121 @@ __global__ void __launch_bounds__(128) k_feat_img(const __grid_constant__ QInfo 
   }
 }
 
-// Epilogue of one tile's hidden layer: rows 32 (w % 4) + lane of the tile,
-// all 256 columns of its accumulator (TMEM columns col0 ..), bias and ReLU,
-// BF16 into the tile's activation atoms.  The next 32 columns are loaded from
-// tensor memory while the current ones are converted.
-__device__ __forceinline__ void epilogue_block(const uint32_t (&r)[32], int c, int row,
-                                               const float* __restrict__ bias, uint8_t* H) {
-  uint8_t* atom = H + (c >> 1) * 16384;
-#pragma unroll
-  for (int j = 0; j < 32; j += 8) {
-    uint32_t w[4];
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      const float a = fmaxf(__uint_as_float(r[j + 2 * e]) + bias[c * 32 + j + 2 * e], 0.f);
-      const float b = fmaxf(__uint_as_float(r[j + 2 * e + 1]) + bias[c * 32 + j + 2 * e + 1], 0.f);
-      __nv_bfloat162 h2 = __floats2bfloat162_rn(a, b);
-      w[e] = *reinterpret_cast<uint32_t*>(&h2);
-    }
-    *reinterpret_cast<uint4*>(atom + tc::sw128_offset(row, (c & 1) * 32 + j)) = make_uint4(w[0], w[1], w[2], w[3]);
+// The layer kernel streams the weights in slices of half a chunk (the 128
+// output features of one half by 64 K): 18 per pass of two tiles, through a
+// ring of kSlots 16 KB buffers.  Layer 1 is slices (chunk 0, half 0) and
+// (chunk 0, half 1); layers 2 and 3 take the four K chunks of half 0, then
+// those of half 1.  So half 0 of a layer's accumulators is complete while half
+// 1 is still being multiplied: its epilogue (writing activation atoms 0 and 1)
+// runs under those MMAs, and the next layer's first two K chunks, which read
+// only atoms 0 and 1, run under half 1's epilogue.
+constexpr int kSlots = 5;
+constexpr uint32_t kSliceBytes = 16384;
+constexpr int kSlices = 2 * mlpk::kWChunks;
+constexpr size_t kMlpSmem = 2 * 65536 + kSlots * kSliceBytes + 1024;
+
+// 16 epilogue warps (warp w: tile (w >> 2) & 1, TMEM lanes 32 (w & 3) .. + 31,
+// activation atom w >> 3 of each half), one MMA warp per tile (their MMAs
+// interleave on the tensor pipe, so one tile's waits hide behind the other
+// tile's MMAs) and the copy warp.  19 warps put five on three of the SM's four
+// register-file quarters: 96 registers a thread at most.
+constexpr int kEpiWarps = 16;
+constexpr int kMmaWarp = kEpiWarps, kCopyWarp = kEpiWarps + 2;   // MMA warps kMmaWarp + t
+constexpr int kMlpThreads = (kEpiWarps + 3) * 32;
+
+// Slice s (0 .. 17) of a pass: layer l (0 .. 2), K chunk k and half h.
+__host__ __device__ __forceinline__ void slice_of(int s, int& l, int& k, int& h) {
+  if (s < 2) {
+    l = 0;
+    k = 0;
+    h = s;
+    return;
   }
+  l = 1 + (s - 2) / 8;
+  h = ((s - 2) % 8) >> 2;
+  k = (s - 2) & 3;
 }
 
-// Column blocks [c0, c1) of 32 (of the tile's eight) of the rows this warp
-// reads from tensor memory.
-__device__ __forceinline__ void epilogue_rows(uint32_t tmem, uint32_t col0, const float* __restrict__ bias,
-                                              uint8_t* H, int c0 = 0, int c1 = 8) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int row = (warp & 3) * 32 + lane;
-  const uint32_t t0 = tmem + ((uint32_t)((warp & 3) * 32) << 16) + col0;
-  uint32_t ra[32], rb[32];
-  tc::tmem_ld32(t0 + c0 * 32, ra);
-  tc::tmem_ld_wait();
+// Per tile t, every barrier but the ring's completes once per pass (phase
+// parity = pass parity): xfull[t] (tile t's features landed in its atom 0),
+// accfull[t][l][h] (tile t's MMA warp commit: half h of layer l
+// accumulated), infree[t][l - 1] (commit: layer l >= 1's MMAs that read
+// atoms 0 and 1 done), actready[t][l][h] (tile t's 256 epilogue threads: half
+// h of layer l's activations written), accfree[t][h] (256 threads: half h of
+// layer 3 read from TMEM), part[t * 4 + q] (32 threads: the output's second
+// partial sum written).  A ring buffer is refilled once both MMA warps
+// committed its slice (empty: two arrivals).
+struct LayerBars {
+  uint64_t full[kSlots], empty[kSlots];
+  uint64_t xfull[2], drain[2];
+  uint64_t accfull[2][3][2];
+  uint64_t infree[2][2];
+  uint64_t actready[2][2][2];
+  uint64_t accfree[2][2];
+  uint64_t part[8];
+};
+
+// A bounded wait that also gives up early once another role has failed.
+__device__ __forceinline__ bool wait_or_fail(uint64_t* bar, uint32_t parity, volatile int* fail) {
 #pragma unroll 1
-  for (int c = c0; c < c1; c += 2) {
-    tc::tmem_ld32(t0 + (c + 1) * 32, rb);
-    epilogue_block(ra, c, row, bias, H);
-    tc::tmem_ld_wait();
-    if (c + 2 < c1) tc::tmem_ld32(t0 + (c + 2) * 32, ra);
-    epilogue_block(rb, c + 1, row, bias, H);
-    tc::tmem_ld_wait();
+  for (int i = 0; i < 64; ++i) {
+    if (tc::mbar_wait(bar, parity, kWaitLimit / 64)) return true;
+    if (*fail) return false;
   }
+  *fail = 1;
+  return false;
 }
 
-// Output layer of one tile's row: relu(Z3 + b3) . w4 over 256 columns, the
-// loads pipelined as in epilogue_rows.
-__device__ __forceinline__ float output_row(uint32_t tmem, uint32_t col0, const float* __restrict__ b3,
-                                           const float* __restrict__ w4, int c0 = 0, int c1 = 8) {
-  const int warp = threadIdx.x >> 5;
-  const uint32_t t0 = tmem + ((uint32_t)((warp & 3) * 32) << 16) + col0;
-  uint32_t ra[32], rb[32];
-  float acc = 0.f;
-  tc::tmem_ld32(t0 + c0 * 32, ra);
-  tc::tmem_ld_wait();
-#pragma unroll 1
-  for (int c = c0; c < c1; c += 2) {
-    tc::tmem_ld32(t0 + (c + 1) * 32, rb);
-#pragma unroll
-    for (int q = 0; q < 32; ++q) acc += fmaxf(__uint_as_float(ra[q]) + b3[c * 32 + q], 0.f) * w4[c * 32 + q];
-    tc::tmem_ld_wait();
-    if (c + 2 < c1) tc::tmem_ld32(t0 + (c + 2) * 32, ra);
-#pragma unroll
-    for (int q = 0; q < 32; ++q)
-      acc += fmaxf(__uint_as_float(rb[q]) + b3[(c + 1) * 32 + q], 0.f) * w4[(c + 1) * 32 + q];
-    tc::tmem_ld_wait();
-  }
-  return acc;
+// Packed FP32 pairs (one instruction for two lanes, each rounded as the
+// scalar operation would round it) and the ReLU-clamping BF16 conversion.
+__device__ __forceinline__ unsigned long long f2_pack(uint32_t lo, uint32_t hi) {
+  unsigned long long v;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(v) : "r"(lo), "r"(hi));
+  return v;
 }
-
-constexpr size_t kMlpSmem = 2 * 65536 + 2 * mlpk::kWChunkBytes + 1024;
-
-// 16 warps: warp w serves tile (w >> 2) & 1, TMEM lanes 32 (w & 3) .. + 31 and
-// column blocks 4 (w >> 3) .. + 3 of the epilogues.
-constexpr int kMlpThreads = 512;
+__device__ __forceinline__ unsigned long long f2_add(unsigned long long a, unsigned long long b) {
+  unsigned long long d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ unsigned long long f2_fma(unsigned long long a, unsigned long long b,
+                                                     unsigned long long c) {
+  unsigned long long d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+// BF16 pair of max(lo, 0) and max(hi, 0), lo in the low half
+__device__ __forceinline__ uint32_t relu_bf16x2(unsigned long long v) {
+  uint32_t d;
+  asm("{\n\t.reg .b32 lo, hi;\n\t"
+      "mov.b64 {lo, hi}, %1;\n\t"
+      "cvt.rn.relu.bf16x2.f32 %0, hi, lo;\n\t}"
+      : "=r"(d)
+      : "l"(v));
+  return d;
+}
+__device__ __forceinline__ unsigned long long f2_relu(unsigned long long v) {
+  uint32_t lo, hi;
+  asm("mov.b64 {%0, %1}, %2;" : "=r"(lo), "=r"(hi) : "l"(v));
+  return f2_pack(__float_as_uint(fmaxf(__uint_as_float(lo), 0.f)), __float_as_uint(fmaxf(__uint_as_float(hi), 0.f)));
+}
 
 __global__ void __launch_bounds__(kMlpThreads, 1) k_mlp_img(const uint8_t* __restrict__ img, uint32_t ntiles,
                                                     const uint8_t* __restrict__ Wimg, const float* __restrict__ P,
                                                     unsigned long long n, float* __restrict__ scores,
                                                     int* __restrict__ status) {
   extern __shared__ uint8_t smem_raw[];
-  // wbar[b]: weight chunk landed in buffer b; cbar[b]: the MMAs that read
-  // buffer b completed.  Chunk G uses buffer G & 1, and is the (G >> 1)-th
-  // use of it, so every wait's phase parity follows from G.
-  __shared__ uint64_t wbar[2], cbar[2], xbar;
+  __shared__ LayerBars bars;
   __shared__ uint32_t tmem_slot;
-  __shared__ int s_fail;
-  __shared__ float sb[4][256];   // b1, b2, b3, w4
-  __shared__ float s_part[2][128];   // the output dot product's second half, per tile row
+  __shared__ volatile int s_fail;
+  __shared__ uint32_t s_consumed[2], s_xwaited[2];   // per MMA warp: slices and feature tiles seen landed
+  __shared__ __align__(16) float sb[4][256];   // b1, b2, b3, w4
+  __shared__ float s_part[2][2][128];          // [pass parity][tile][row]: the output's second partial sum
   uint8_t* base = smem_raw + ((1024 - (tc::smem_u32(smem_raw) & 1023)) & 1023);
-  uint8_t* H[2] = {base, base + 65536};                                 // two tiles x four atoms
-  uint8_t* Wb[2] = {base + 131072, base + 131072 + mlpk::kWChunkBytes};  // weight chunk buffers
+  // tile t's four 16 KB activation atoms at base + t * 65536 (atom 0 holds X in layer 1)
+  uint8_t* ring = base + 131072;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t npass = ntiles > 2 * blockIdx.x ? (ntiles - 2 * blockIdx.x + 2 * gridDim.x - 1) / (2 * gridDim.x) : 0;
-  const uint32_t total_chunks = npass * mlpk::kWChunks;
   for (int i = threadIdx.x; i < 256; i += blockDim.x) {
     sb[0][i] = __ldg(P + mlpk::O_B1 + i);
     sb[1][i] = __ldg(P + mlpk::O_B2 + i);
@@ -334,134 +354,210 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_mlp_img(const uint8_t* __res
   }
   if (threadIdx.x == 0) {
     s_fail = 0;
-    for (int b = 0; b < 2; ++b) {
-      tc::mbar_init(&wbar[b], 1);
-      tc::mbar_init(&cbar[b], 1);
+    for (int i = 0; i < kSlots; ++i) {
+      tc::mbar_init(&bars.full[i], 1);
+      tc::mbar_init(&bars.empty[i], 2);
     }
-    tc::mbar_init(&xbar, 1);
+    for (int t = 0; t < 2; ++t) {
+      s_consumed[t] = 0;
+      s_xwaited[t] = 0;
+      tc::mbar_init(&bars.xfull[t], 1);
+      tc::mbar_init(&bars.drain[t], 1);
+      for (int i = 0; i < 2; ++i) {
+        tc::mbar_init(&bars.infree[t][i], 1);
+        tc::mbar_init(&bars.accfree[t][i], kEpiWarps / 2 * 32);
+        for (int l = 0; l < 3; ++l) tc::mbar_init(&bars.accfull[t][l][i], 1);
+        for (int h = 0; h < 2; ++h) tc::mbar_init(&bars.actready[t][i][h], kEpiWarps / 2 * 32);
+      }
+    }
+    for (int i = 0; i < 8; ++i) tc::mbar_init(&bars.part[i], 32);
     tc::fence_mbar_init();
-    // the first two weight chunks
-    for (uint32_t c = 0; c < 2 && c < total_chunks; ++c) {
-      tc::mbar_expect_tx(&wbar[c], (uint32_t)mlpk::kWChunkBytes);
-      tc::bulk_g2s(Wb[c], Wimg + (size_t)c * mlpk::kWChunkBytes, (uint32_t)mlpk::kWChunkBytes, &wbar[c]);
-    }
   }
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = tmem_slot;
-  constexpr uint32_t idesc = tc::idesc_bf16(128, 256);
-  uint32_t xphase = 0;
-  uint32_t G = 0;          // weight chunks consumed so far (the same in every thread)
-  uint32_t landed = 0;     // thread 0: chunks seen landed
-  uint32_t issued = total_chunks < 2 ? total_chunks : 2;   // thread 0: chunk copies issued
-  uint32_t committed = 0;  // thread 0: chunks whose MMAs were issued
-  uint32_t done = 0;       // thread 0: chunks whose MMAs were seen complete
-  bool x_pending = false;  // a tile copy not yet seen landed
-  bool ok = true;
-  for (uint32_t pass = 0; pass < npass && ok; ++pass) {
-    const uint32_t tA = 2 * (blockIdx.x + pass * gridDim.x);
-    const uint32_t nt = tA + 1 < ntiles ? 2 : 1;
-    if (threadIdx.x == 0 && pass == 0) {
-      // later passes' tiles were copied during the previous pass
-      tc::mbar_expect_tx(&xbar, nt * kTileBytes);
-      for (uint32_t t = 0; t < nt; ++t) tc::bulk_g2s(H[t], img + (size_t)(tA + t) * kTileBytes, kTileBytes, &xbar);
+  uint32_t x_issued[2] = {0, 0}, issued = 0;   // copy thread: feature tiles and slices whose copies were issued
+  if (warp == kCopyWarp) {
+    if (lane == 0) {
+      for (uint32_t pass = 0; pass < npass && !s_fail; ++pass) {
+        // each feature tile goes into its atom 0 once the previous pass's
+        // layer 3 has read it; a missing second tile (odd count, last pass)
+        // completes its barrier with a plain arrival
+        const uint32_t tA = 2 * (blockIdx.x + pass * gridDim.x);
+        const uint32_t nt = tA + 1 < ntiles ? 2 : 1;
+        bool xok = true;
+        for (uint32_t t = 0; t < 2 && xok; ++t) {
+          if (pass > 0 && !(xok = wait_or_fail(&bars.infree[t][1], (pass - 1) & 1, &s_fail))) break;
+          if (t < nt) {
+            tc::mbar_expect_tx(&bars.xfull[t], kTileBytes);
+            tc::bulk_g2s(base + t * 65536, img + (size_t)(tA + t) * kTileBytes, kTileBytes, &bars.xfull[t]);
+          } else {
+            tc::mbar_arrive(&bars.xfull[t]);
+          }
+          ++x_issued[t];
+        }
+        if (!xok) break;
+        bool ok = true;
+        for (int s = 0; s < kSlices; ++s) {
+          const uint32_t G = pass * kSlices + s, slot = G % kSlots, use = G / kSlots;
+          if (use >= 1 && !wait_or_fail(&bars.empty[slot], (use - 1) & 1, &s_fail)) {
+            ok = false;
+            break;
+          }
+          int l, k, h;
+          slice_of(s, l, k, h);
+          const int chunk = l == 0 ? 0 : 1 + 4 * (l - 1) + k;
+          tc::mbar_expect_tx(&bars.full[slot], kSliceBytes);
+          tc::bulk_g2s(ring + slot * kSliceBytes, Wimg + (size_t)chunk * mlpk::kWChunkBytes + h * kSliceBytes,
+                       kSliceBytes, &bars.full[slot]);
+          ++issued;
+        }
+        if (!ok) break;
+      }
     }
-    x_pending = true;
-    // every wait's outcome is agreed on by the whole CTA before it goes on
-    ok = __syncthreads_and(tc::mbar_wait(&xbar, xphase, kWaitLimit)) != 0;
-    if (!ok) break;
-    x_pending = false;
-    xphase ^= 1;
-    for (int j = 0; j < mlpk::kWChunks; ++j, ++G) {
-      const uint32_t b = G & 1;
-      // A operand: atom kc of each tile (X for layer 1)
-      const uint32_t kc = j == 0 ? 0 : (uint32_t)((j - 1) & 3);
-      const bool first = j == 0 || kc == 0;
-      if (threadIdx.x == 0 && !s_fail) {
-        // issue this chunk's MMAs as soon as its weights are in; they queue
-        // behind the previous chunk's on the tensor pipe
-        if (!tc::mbar_wait(&wbar[b], (G >> 1) & 1, kWaitLimit)) {
-          s_fail = 1;
-        } else {
-          ++landed;
+  } else if (warp == kMmaWarp || warp == kMmaWarp + 1) {
+    if (lane == 0) {
+      const uint32_t t = warp - kMmaWarp;   // this warp's tile
+      constexpr uint32_t idesc = tc::idesc_bf16(128, 128);
+      // operand descriptors of the tile's atom 0 and of ring buffer 0; the
+      // others are byte offsets / 16 added to the start-address field
+      const uint64_t adesc0 = tc::sdesc_sw128(tc::smem_u32(base + t * 65536));
+      const uint64_t bdesc0 = tc::sdesc_sw128(tc::smem_u32(ring));
+      const uint32_t dt = tmem + t * 256;
+      uint32_t slot = 0, fphase = 0;   // ring buffer of the next slice and its fill's phase parity
+      uint32_t consumed = 0, xwaited = 0;
+      for (uint32_t pass = 0; pass < npass && !s_fail; ++pass) {
+        const uint32_t ph = pass & 1;
+        const uint32_t tA = 2 * (blockIdx.x + pass * gridDim.x);
+        // a missing second tile still takes part in the barriers, without MMAs
+        const bool live = tA + t < ntiles;
+        if (!wait_or_fail(&bars.xfull[t], ph, &s_fail)) break;
+        xwaited = pass + 1;
+        bool ok = true;
+        // the slice schedule unrolled: layer, K chunk and half are constants
+#pragma unroll
+        for (int s = 0; s < kSlices; ++s) {
+          int l, k, h;
+          slice_of(s, l, k, h);
+          // layer 1 overwrites the accumulators the previous pass's output
+          // layer read; layers 2 and 3 read the activation atoms 2h' + (0, 1)
+          // of the layer before (half 0's slices of K chunks 0 and 2 wait)
+          if (l == 0 && pass > 0) ok = wait_or_fail(&bars.accfree[t][h], ph ^ 1, &s_fail);
+          if (ok && l >= 1 && h == 0 && (k & 1) == 0)
+            ok = wait_or_fail(&bars.actready[t][l - 1][k >> 1], ph, &s_fail);
+          if (ok) ok = wait_or_fail(&bars.full[slot], fphase, &s_fail);
+          if (!ok) break;
+          ++consumed;
           tc::fence_after_sync();
-          for (uint32_t t = 0; t < nt; ++t) {
-            const uint32_t a_addr = tc::smem_u32(H[t] + kc * 16384), b_addr = tc::smem_u32(Wb[b]);
+          if (live) {
+            const uint64_t bd = bdesc0 + slot * (kSliceBytes >> 4);
+            const uint64_t ad = adesc0 + ((k * 16384) >> 4);
 #pragma unroll
             for (int kk = 0; kk < 4; ++kk)
-              tc::mma_bf16(tmem + t * 256, tc::sdesc_sw128(a_addr + kk * 32), tc::sdesc_sw128(b_addr + kk * 32),
-                           idesc, (first && kk == 0) ? 0u : 1u);
+              tc::mma_bf16(dt + h * 128, ad + 2 * kk, bd + 2 * kk, idesc, (k == 0 && kk == 0) ? 0u : 1u);
           }
-          tc::mma_commit(&cbar[b]);
-          ++committed;
-          // the previous chunk's buffer is free once its MMAs completed: the
-          // next chunk goes into it
-          if (G >= 1) {
-            if (!tc::mbar_wait(&cbar[b ^ 1], ((G - 1) >> 1) & 1, kWaitLimit)) {
-              s_fail = 1;
-            } else {
-              done = G;
-              if (j == 6 && pass + 1 < npass) {
-                // chunk 5 (layer 3's first, the last reader of atom 0) is
-                // done: the next pass's tiles go into atom 0 now
-                const uint32_t tN = 2 * (blockIdx.x + (pass + 1) * gridDim.x);
-                const uint32_t ntN = tN + 1 < ntiles ? 2 : 1;
-                tc::mbar_expect_tx(&xbar, ntN * kTileBytes);
-                for (uint32_t u = 0; u < ntN; ++u)
-                  tc::bulk_g2s(H[u], img + (size_t)(tN + u) * kTileBytes, kTileBytes, &xbar);
-                x_pending = true;
-              }
-              if (G + 1 < total_chunks) {
-                ++issued;
-                tc::mbar_expect_tx(&wbar[b ^ 1], (uint32_t)mlpk::kWChunkBytes);
-                tc::bulk_g2s(Wb[b ^ 1], Wimg + (size_t)((G + 1) % mlpk::kWChunks) * mlpk::kWChunkBytes,
-                             (uint32_t)mlpk::kWChunkBytes, &wbar[b ^ 1]);
-              }
+          tc::mma_commit(&bars.empty[slot]);
+          if (l == 0 || k == 3) tc::mma_commit(&bars.accfull[t][l][h]);
+          if (l >= 1 && h == 1 && k == 1) tc::mma_commit(&bars.infree[t][l - 1]);
+          if (++slot == kSlots) {
+            slot = 0;
+            fphase ^= 1;
+          }
+        }
+        if (!ok) break;
+      }
+      s_consumed[t] = consumed;
+      s_xwaited[t] = xwaited;
+      // every MMA issued has completed before the CTA goes on
+      tc::mma_commit(&bars.drain[t]);
+      if (!tc::mbar_wait(&bars.drain[t], 0, kWaitLimit)) s_fail = 1;
+    }
+  } else {
+    const uint32_t t = ((uint32_t)warp >> 2) & 1, q = warp & 3, a = warp >> 3;
+    const uint32_t row = q * 32 + lane;
+    const uint32_t t0 = tmem + ((q * 32) << 16) + t * 256 + a * 64;
+    bool ok = true;
+    for (uint32_t pass = 0; pass < npass && ok; ++pass) {
+      const uint32_t ph = pass & 1;
+      unsigned long long acc2 = 0;   // the output layer's partial dot product (even, odd columns)
+      for (int l = 0; l < 3 && ok; ++l) {
+        for (int h = 0; h < 2; ++h) {
+          if (!(ok = wait_or_fail(&bars.accfull[t][l][h], ph, &s_fail))) break;
+          tc::fence_after_sync();
+          const int c0 = h * 128 + a * 64;   // this warp's first column
+          // the 64 columns in two loads of 32 (one 32-register buffer)
+          uint32_t r[32];
+          if (l == 2) {
+            // relu(z + b3) . w4 over the 64 columns, even and odd columns in
+            // the two lanes of a packed pair
+            const unsigned long long* b3 = reinterpret_cast<const unsigned long long*>(sb[2] + c0);
+            const unsigned long long* w4 = reinterpret_cast<const unsigned long long*>(sb[3] + c0);
+#pragma unroll
+            for (int part = 0; part < 2; ++part) {
+              tc::tmem_ld32(t0 + h * 128 + 32 * part, r);
+              tc::tmem_ld_wait();
+#pragma unroll
+              for (int j = 0; j < 16; ++j)
+                acc2 = f2_fma(f2_relu(f2_add(f2_pack(r[2 * j], r[2 * j + 1]), b3[16 * part + j])), w4[16 * part + j],
+                              acc2);
             }
+            tc::fence_before_sync();
+            tc::mbar_arrive(&bars.accfree[t][h]);
+            continue;
           }
+          // bias, ReLU, BF16 pairs of the 64 columns
+          const unsigned long long* bias = reinterpret_cast<const unsigned long long*>(sb[l] + c0);
+          uint32_t w[32];
+#pragma unroll
+          for (int part = 0; part < 2; ++part) {
+            tc::tmem_ld32(t0 + h * 128 + 32 * part, r);
+            tc::tmem_ld_wait();
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+              w[16 * part + j] = relu_bf16x2(f2_add(f2_pack(r[2 * j], r[2 * j + 1]), bias[16 * part + j]));
+          }
+          // atoms 0 and 1 are this layer's input too: wait until its MMAs
+          // that read them are done (layer 1: all of them)
+          if (h == 0 && !(ok = wait_or_fail(l == 0 ? &bars.accfull[t][0][1] : &bars.infree[t][0], ph, &s_fail)))
+            break;
+          uint8_t* atom = base + t * 65536 + (2 * h + a) * 16384;
+#pragma unroll
+          for (int j = 0; j < 8; ++j)
+            *reinterpret_cast<uint4*>(atom + tc::sw128_offset(row, 8 * j)) =
+                make_uint4(w[4 * j], w[4 * j + 1], w[4 * j + 2], w[4 * j + 3]);
+          tc::fence_proxy_async();
+          tc::fence_before_sync();
+          tc::mbar_arrive(&bars.actready[t][l][h]);
         }
       }
-      if (j != 0 && j != 4 && j != 8) continue;
-      // a layer is complete: everyone waits for this chunk's MMAs
-      const bool mma_done = tc::mbar_wait(&cbar[b], (G >> 1) & 1, kWaitLimit);
-      __syncthreads();   // s_fail as thread 0 left it
-      ok = __syncthreads_and(mma_done && !s_fail) != 0;
       if (!ok) break;
-      tc::fence_after_sync();
-      if (threadIdx.x == 0) done = G + 1;
-      const uint32_t t = ((uint32_t)warp >> 2) & 1;   // the tile this warp's epilogue serves
-      const int hc = warp >> 3;                        // and the half of its columns
-      if (j != 8) {
-        // hidden layer 1 or 2 done: its activations become the next A operand
-        if (t < nt) epilogue_rows(tmem, t * 256, sb[j == 0 ? 0 : 1], H[t], 4 * hc, 4 * hc + 4);
-        tc::fence_proxy_async();
+      // the two warps of a (tile, lane quarter) add their halves of the dot
+      // product; the second writes, the first adds and stores the score
+      const uint32_t tA = 2 * (blockIdx.x + pass * gridDim.x);
+      const uint32_t nt = tA + 1 < ntiles ? 2 : 1;
+      uint32_t a_even, a_odd;
+      asm("mov.b64 {%0, %1}, %2;" : "=r"(a_even), "=r"(a_odd) : "l"(acc2));
+      const float acc = __uint_as_float(a_even) + __uint_as_float(a_odd);
+      if (a == 1) {
+        s_part[ph][t][row] = acc;
+        tc::mbar_arrive(&bars.part[t * 4 + q]);
       } else {
-        // layer 3 and the output dot product, each half of the columns by
-        // its own warp, added through shared memory
-        const int row = (warp & 3) * 32 + lane;
-        float acc = 0.f;
-        if (t < nt) {
-          acc = output_row(tmem, t * 256, sb[2], sb[3], 4 * hc, 4 * hc + 4);
-          if (hc == 1) s_part[t][row] = acc;
-        }
-        __syncthreads();
-        if (t < nt && hc == 0) {
-          const unsigned long long out = (unsigned long long)(tA + t) * 128 + row;
-          if (out < n) scores[out] = acc + s_part[t][row] + b4;
-        }
+        if (!(ok = wait_or_fail(&bars.part[t * 4 + q], ph, &s_fail))) break;
+        const unsigned long long out = (unsigned long long)(tA + t) * 128 + row;
+        if (t < nt && out < n) scores[out] = acc + s_part[ph][t][row] + b4;
       }
-      tc::fence_before_sync();
-      __syncthreads();
     }
   }
-  if (!ok && threadIdx.x == 0) {
+  __syncthreads();
+  if (warp == kCopyWarp && lane == 0 && s_fail) {
+    // copies issued but not seen landed by both MMA warps (at most one per
+    // ring buffer, and one feature tile each) complete before the CTA exits
+    for (uint32_t G = min(s_consumed[0], s_consumed[1]); G < issued; ++G)
+      tc::mbar_wait(&bars.full[G % kSlots], (G / kSlots) & 1, kWaitLimit);
+    for (int t = 0; t < 2; ++t)
+      if (x_issued[t] > s_xwaited[t]) tc::mbar_wait(&bars.xfull[t], (x_issued[t] - 1) & 1, kWaitLimit);
     atomicExch(status, MP_ETIMEOUT);
-    // before the CTA exits: the chunk copies issued but not seen landed, the
-    // MMAs issued but not seen complete, and a tile copy in flight
-    for (uint32_t c = landed; c < issued; ++c) tc::mbar_wait(&wbar[c & 1], (c >> 1) & 1, kWaitLimit);
-    for (uint32_t c = done; c < committed; ++c) tc::mbar_wait(&cbar[c & 1], (c >> 1) & 1, kWaitLimit);
-    if (x_pending) tc::mbar_wait(&xbar, xphase, kWaitLimit);
   }
   tc::fence_before_sync();
   __syncthreads();
