@@ -229,11 +229,11 @@ __global__ void __launch_bounds__(128) k_feat_img(const __grid_constant__ QInfo 
 // The layer kernel streams the weights in slices of half a chunk (the 128
 // output features of one half by 64 K): 18 per pass of two tiles, through a
 // ring of kSlots 16 KB buffers.  Layer 1 is slices (chunk 0, half 0) and
-// (chunk 0, half 1); layers 2 and 3 take the four K chunks of half 0, then
-// those of half 1.  So half 0 of a layer's accumulators is complete while half
-// 1 is still being multiplied: its epilogue (writing activation atoms 0 and 1)
-// runs under those MMAs, and the next layer's first two K chunks, which read
-// only atoms 0 and 1, run under half 1's epilogue.
+// (chunk 0, half 1); layers 2 and 3 take K chunks 0 and 1 of half 0, the same
+// of half 1, then K chunks 2 and 3 of half 0 and of half 1.  So the layer's
+// reads of activation atoms 0 and 1 are done before half 0 is complete (its
+// epilogue writes them at once), half 0's epilogue runs under half 1's last
+// MMAs, and the next layer starts on atom 0 while half 1's epilogue runs.
 constexpr int kSlots = 5;
 constexpr uint32_t kSliceBytes = 16384;
 constexpr int kSlices = 2 * mlpk::kWChunks;
@@ -257,27 +257,33 @@ __host__ __device__ __forceinline__ void slice_of(int s, int& l, int& k, int& h)
     return;
   }
   l = 1 + (s - 2) / 8;
-  h = ((s - 2) % 8) >> 2;
-  k = (s - 2) & 3;
+  const int r = (s - 2) % 8;
+  h = (r >> 1) & 1;
+  k = (r & 1) + 2 * (r >> 2);
 }
 
 // Per tile t, every barrier but the ring's completes once per pass (phase
 // parity = pass parity): xfull[t] (tile t's features landed in its atom 0),
 // accfull[t][l][h] (tile t's MMA warp commit: half h of layer l
-// accumulated), infree[t][l - 1] (commit: layer l >= 1's MMAs that read
-// atoms 0 and 1 done), actready[t][l][h] (tile t's 256 epilogue threads: half
-// h of layer l's activations written), accfree[t][h] (256 threads: half h of
-// layer 3 read from TMEM), part[t * 4 + q] (32 threads: the output's second
-// partial sum written).  A ring buffer is refilled once both MMA warps
-// committed its slice (empty: two arrivals).
+// accumulated), infree[t] (commit: layer 3's MMAs that read atoms 0 and 1
+// done), part[t * 4 + q] (32 threads: the output's second partial sum
+// written).  A ring buffer is refilled once both MMA warps committed its slice
+// (empty: two arrivals).  The MMA warps wait on counters instead (eight
+// epilogue warps add one per pass to each of tile t's): landed (slices whose
+// weights landed, published in order by the copy warp), tfree[t][l][h] (half h
+// of layer l's accumulators read from TMEM), ready[t][l][k] (activation atom k
+// of layer l written).
 struct LayerBars {
   uint64_t full[kSlots], empty[kSlots];
   uint64_t xfull[2], drain[2];
   uint64_t accfull[2][3][2];
-  uint64_t infree[2][2];
-  uint64_t actready[2][2][2];
-  uint64_t accfree[2][2];
+  uint64_t infree[2];
   uint64_t part[8];
+};
+struct LayerCounts {
+  uint32_t landed;
+  uint32_t tfree[2][3][2];
+  uint32_t ready[2][2][4];
 };
 
 // A bounded wait that also gives up early once another role has failed.
@@ -319,6 +325,39 @@ __device__ __forceinline__ uint32_t relu_bf16x2(unsigned long long v) {
       : "l"(v));
   return d;
 }
+// Shared-memory event counters: a release add (or store) by the signalling
+// thread; the waiting one polls with relaxed loads and fences once the count
+// is reached.  A completed mbarrier phase takes
+// about 200 cycles to observe, an acquire load of a counter a fraction of
+// that, so the MMA warps, whose waits sit between the tensor pipe's work,
+// wait on counters; the barriers stay where the hardware signals them (bulk
+// copies, MMA commits).
+__device__ __forceinline__ uint32_t ld_relaxed(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.relaxed.cta.shared::cta.u32 %0, [%1];" : "=r"(v) : "r"(tc::smem_u32(p)) : "memory");
+  return v;
+}
+__device__ __forceinline__ void red_release_add(uint32_t* p, uint32_t v) {
+  asm volatile("red.release.cta.shared::cta.add.u32 [%0], %1;" ::"r"(tc::smem_u32(p)), "r"(v) : "memory");
+}
+__device__ __forceinline__ void st_release(uint32_t* p, uint32_t v) {
+  asm volatile("st.release.cta.shared::cta.u32 [%0], %1;" ::"r"(tc::smem_u32(p)), "r"(v) : "memory");
+}
+// Waits (bounded) until the counter reaches target; gives up early once
+// another role has failed.
+__device__ __forceinline__ bool wait_count(const uint32_t* p, uint32_t target, volatile int* fail) {
+#pragma unroll 1
+  for (uint32_t i = 0; i < kWaitLimit; ++i) {
+    if (ld_relaxed(p) >= target) {
+      asm volatile("fence.acq_rel.cta;" ::: "memory");   // with the load: an acquire
+      return true;
+    }
+    if ((i & 1023) == 1023 && *fail) return false;
+  }
+  *fail = 1;
+  return false;
+}
+
 __device__ __forceinline__ unsigned long long f2_relu(unsigned long long v) {
   uint32_t lo, hi;
   asm("mov.b64 {%0, %1}, %2;" : "=r"(lo), "=r"(hi) : "l"(v));
@@ -333,7 +372,8 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_mlp_img(const uint8_t* __res
   __shared__ LayerBars bars;
   __shared__ uint32_t tmem_slot;
   __shared__ volatile int s_fail;
-  __shared__ uint32_t s_consumed[2], s_xwaited[2];   // per MMA warp: slices and feature tiles seen landed
+  __shared__ LayerCounts cnt;
+  __shared__ uint32_t s_xwaited[2];   // per MMA warp: feature tiles seen landed
   __shared__ __align__(16) float sb[4][256];   // b1, b2, b3, w4
   __shared__ float s_part[2][2][128];          // [pass parity][tile][row]: the output's second partial sum
   uint8_t* base = smem_raw + ((1024 - (tc::smem_u32(smem_raw) & 1023)) & 1023);
@@ -358,16 +398,18 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_mlp_img(const uint8_t* __res
       tc::mbar_init(&bars.full[i], 1);
       tc::mbar_init(&bars.empty[i], 2);
     }
+    cnt.landed = 0;
     for (int t = 0; t < 2; ++t) {
-      s_consumed[t] = 0;
       s_xwaited[t] = 0;
       tc::mbar_init(&bars.xfull[t], 1);
       tc::mbar_init(&bars.drain[t], 1);
+      tc::mbar_init(&bars.infree[t], 1);
       for (int i = 0; i < 2; ++i) {
-        tc::mbar_init(&bars.infree[t][i], 1);
-        tc::mbar_init(&bars.accfree[t][i], kEpiWarps / 2 * 32);
-        for (int l = 0; l < 3; ++l) tc::mbar_init(&bars.accfull[t][l][i], 1);
-        for (int h = 0; h < 2; ++h) tc::mbar_init(&bars.actready[t][i][h], kEpiWarps / 2 * 32);
+        for (int l = 0; l < 3; ++l) {
+          tc::mbar_init(&bars.accfull[t][l][i], 1);
+          cnt.tfree[t][l][i] = 0;
+        }
+        for (int k = 0; k < 4; ++k) cnt.ready[t][i][k] = 0;
       }
     }
     for (int i = 0; i < 8; ++i) tc::mbar_init(&bars.part[i], 32);
@@ -377,18 +419,34 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_mlp_img(const uint8_t* __res
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = tmem_slot;
-  uint32_t x_issued[2] = {0, 0}, issued = 0;   // copy thread: feature tiles and slices whose copies were issued
+  // copy thread: feature tiles and slices whose copies were issued, slices published as landed
+  uint32_t x_issued[2] = {0, 0}, issued = 0, pub = 0;
   if (warp == kCopyWarp) {
     if (lane == 0) {
-      for (uint32_t pass = 0; pass < npass && !s_fail; ++pass) {
+      // slices are published (cnt.landed) in order as their copies land;
+      // every wait of this thread keeps publishing meanwhile
+      auto publish = [&]() {
+        while (pub < issued && tc::mbar_test(&bars.full[pub % kSlots], (pub / kSlots) & 1)) st_release(&cnt.landed, ++pub);
+      };
+      auto wait_publishing = [&](uint64_t* bar, uint32_t parity) -> bool {
+#pragma unroll 1
+        for (uint32_t i = 0; i < kWaitLimit; ++i) {
+          if (tc::mbar_test(bar, parity)) return true;
+          publish();
+          if ((i & 255) == 255 && s_fail) return false;
+        }
+        s_fail = 1;
+        return false;
+      };
+      bool ok = true;
+      for (uint32_t pass = 0; pass < npass && ok && !s_fail; ++pass) {
         // each feature tile goes into its atom 0 once the previous pass's
         // layer 3 has read it; a missing second tile (odd count, last pass)
         // completes its barrier with a plain arrival
         const uint32_t tA = 2 * (blockIdx.x + pass * gridDim.x);
         const uint32_t nt = tA + 1 < ntiles ? 2 : 1;
-        bool xok = true;
-        for (uint32_t t = 0; t < 2 && xok; ++t) {
-          if (pass > 0 && !(xok = wait_or_fail(&bars.infree[t][1], (pass - 1) & 1, &s_fail))) break;
+        for (uint32_t t = 0; t < 2 && ok; ++t) {
+          if (pass > 0 && !(ok = wait_publishing(&bars.infree[t], (pass - 1) & 1))) break;
           if (t < nt) {
             tc::mbar_expect_tx(&bars.xfull[t], kTileBytes);
             tc::bulk_g2s(base + t * 65536, img + (size_t)(tA + t) * kTileBytes, kTileBytes, &bars.xfull[t]);
@@ -397,14 +455,9 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_mlp_img(const uint8_t* __res
           }
           ++x_issued[t];
         }
-        if (!xok) break;
-        bool ok = true;
-        for (int s = 0; s < kSlices; ++s) {
+        for (int s = 0; s < kSlices && ok; ++s) {
           const uint32_t G = pass * kSlices + s, slot = G % kSlots, use = G / kSlots;
-          if (use >= 1 && !wait_or_fail(&bars.empty[slot], (use - 1) & 1, &s_fail)) {
-            ok = false;
-            break;
-          }
+          if (use >= 1 && !(ok = wait_publishing(&bars.empty[slot], (use - 1) & 1))) break;
           int l, k, h;
           slice_of(s, l, k, h);
           const int chunk = l == 0 ? 0 : 1 + 4 * (l - 1) + k;
@@ -412,8 +465,15 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_mlp_img(const uint8_t* __res
           tc::bulk_g2s(ring + slot * kSliceBytes, Wimg + (size_t)chunk * mlpk::kWChunkBytes + h * kSliceBytes,
                        kSliceBytes, &bars.full[slot]);
           ++issued;
+          publish();
         }
-        if (!ok) break;
+      }
+      // the last slices
+#pragma unroll 1
+      for (uint32_t i = 0; ok && pub < issued; ++i) {
+        publish();
+        if (i == kWaitLimit) s_fail = 1;
+        if (s_fail) break;
       }
     }
   } else if (warp == kMmaWarp || warp == kMmaWarp + 1) {
@@ -425,7 +485,7 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_mlp_img(const uint8_t* __res
       const uint64_t adesc0 = tc::sdesc_sw128(tc::smem_u32(base + t * 65536));
       const uint64_t bdesc0 = tc::sdesc_sw128(tc::smem_u32(ring));
       const uint32_t dt = tmem + t * 256;
-      uint32_t slot = 0, fphase = 0;   // ring buffer of the next slice and its fill's phase parity
+      uint32_t slot = 0;   // ring buffer of the next slice
       uint32_t consumed = 0, xwaited = 0;
       for (uint32_t pass = 0; pass < npass && !s_fail; ++pass) {
         const uint32_t ph = pass & 1;
@@ -441,12 +501,13 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_mlp_img(const uint8_t* __res
           int l, k, h;
           slice_of(s, l, k, h);
           // layer 1 overwrites the accumulators the previous pass's output
-          // layer read; layers 2 and 3 read the activation atoms 2h' + (0, 1)
-          // of the layer before (half 0's slices of K chunks 0 and 2 wait)
-          if (l == 0 && pass > 0) ok = wait_or_fail(&bars.accfree[t][h], ph ^ 1, &s_fail);
-          if (ok && l >= 1 && h == 0 && (k & 1) == 0)
-            ok = wait_or_fail(&bars.actready[t][l - 1][k >> 1], ph, &s_fail);
-          if (ok) ok = wait_or_fail(&bars.full[slot], fphase, &s_fail);
+          // layer read; in layers 2 and 3 half 0's slices wait for the atom
+          // they read (atom 0's written after half 0's TMEM was read), half
+          // 1's first slice for half 1's TMEM read
+          if (l == 0 && pass > 0) ok = wait_count(&cnt.tfree[t][2][h], 8 * pass, &s_fail);
+          if (ok && l >= 1 && h == 0) ok = wait_count(&cnt.ready[t][l - 1][k], 8 * (pass + 1), &s_fail);
+          if (ok && l >= 1 && h == 1 && k == 0) ok = wait_count(&cnt.tfree[t][l - 1][1], 8 * (pass + 1), &s_fail);
+          if (ok) ok = wait_count(&cnt.landed, consumed + 1, &s_fail);
           if (!ok) break;
           ++consumed;
           tc::fence_after_sync();
@@ -459,15 +520,11 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_mlp_img(const uint8_t* __res
           }
           tc::mma_commit(&bars.empty[slot]);
           if (l == 0 || k == 3) tc::mma_commit(&bars.accfull[t][l][h]);
-          if (l >= 1 && h == 1 && k == 1) tc::mma_commit(&bars.infree[t][l - 1]);
-          if (++slot == kSlots) {
-            slot = 0;
-            fphase ^= 1;
-          }
+          if (l == 2 && h == 1 && k == 1) tc::mma_commit(&bars.infree[t]);
+          if (++slot == kSlots) slot = 0;
         }
         if (!ok) break;
       }
-      s_consumed[t] = consumed;
       s_xwaited[t] = xwaited;
       // every MMA issued has completed before the CTA goes on
       tc::mma_commit(&bars.drain[t]);
@@ -476,7 +533,7 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_mlp_img(const uint8_t* __res
   } else {
     const uint32_t t = ((uint32_t)warp >> 2) & 1, q = warp & 3, a = warp >> 3;
     const uint32_t row = q * 32 + lane;
-    const uint32_t t0 = tmem + ((q * 32) << 16) + t * 256 + a * 64;
+    const uint32_t tq = tmem + ((q * 32) << 16) + t * 256;   // this warp's TMEM lanes, the tile's columns
     bool ok = true;
     for (uint32_t pass = 0; pass < npass && ok; ++pass) {
       const uint32_t ph = pass & 1;
@@ -485,50 +542,50 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_mlp_img(const uint8_t* __res
         for (int h = 0; h < 2; ++h) {
           if (!(ok = wait_or_fail(&bars.accfull[t][l][h], ph, &s_fail))) break;
           tc::fence_after_sync();
-          const int c0 = h * 128 + a * 64;   // this warp's first column
-          // the 64 columns in two loads of 32 (one 32-register buffer)
-          uint32_t r[32];
+          // this warp's columns of atoms 2h and 2h + 1 (warp a: columns
+          // 32a .. 32a + 31 of each) are read from TMEM first, and the half's
+          // TMEM is released; then each atom is finished and published
+          uint32_t r0[32], r1[32];
+          const int c0 = h * 128 + a * 32, c1 = c0 + 64;
+          tc::tmem_ld32(tq + c0, r0);
+          tc::tmem_ld32(tq + c1, r1);
+          tc::tmem_ld_wait();
+          tc::fence_before_sync();
+          __syncwarp();
+          if (lane == 0) red_release_add(&cnt.tfree[t][l][h], 1);
           if (l == 2) {
-            // relu(z + b3) . w4 over the 64 columns, even and odd columns in
-            // the two lanes of a packed pair
-            const unsigned long long* b3 = reinterpret_cast<const unsigned long long*>(sb[2] + c0);
-            const unsigned long long* w4 = reinterpret_cast<const unsigned long long*>(sb[3] + c0);
-#pragma unroll
-            for (int part = 0; part < 2; ++part) {
-              tc::tmem_ld32(t0 + h * 128 + 32 * part, r);
-              tc::tmem_ld_wait();
-#pragma unroll
-              for (int j = 0; j < 16; ++j)
-                acc2 = f2_fma(f2_relu(f2_add(f2_pack(r[2 * j], r[2 * j + 1]), b3[16 * part + j])), w4[16 * part + j],
-                              acc2);
-            }
-            tc::fence_before_sync();
-            tc::mbar_arrive(&bars.accfree[t][h]);
-            continue;
-          }
-          // bias, ReLU, BF16 pairs of the 64 columns
-          const unsigned long long* bias = reinterpret_cast<const unsigned long long*>(sb[l] + c0);
-          uint32_t w[32];
-#pragma unroll
-          for (int part = 0; part < 2; ++part) {
-            tc::tmem_ld32(t0 + h * 128 + 32 * part, r);
-            tc::tmem_ld_wait();
+            // relu(z + b3) . w4, even and odd columns in the two lanes of a
+            // packed pair
+            const unsigned long long* b3 = reinterpret_cast<const unsigned long long*>(sb[2]);
+            const unsigned long long* w4 = reinterpret_cast<const unsigned long long*>(sb[3]);
 #pragma unroll
             for (int j = 0; j < 16; ++j)
-              w[16 * part + j] = relu_bf16x2(f2_add(f2_pack(r[2 * j], r[2 * j + 1]), bias[16 * part + j]));
-          }
-          // atoms 0 and 1 are this layer's input too: wait until its MMAs
-          // that read them are done (layer 1: all of them)
-          if (h == 0 && !(ok = wait_or_fail(l == 0 ? &bars.accfull[t][0][1] : &bars.infree[t][0], ph, &s_fail)))
-            break;
-          uint8_t* atom = base + t * 65536 + (2 * h + a) * 16384;
+              acc2 = f2_fma(f2_relu(f2_add(f2_pack(r0[2 * j], r0[2 * j + 1]), b3[c0 / 2 + j])), w4[c0 / 2 + j], acc2);
 #pragma unroll
-          for (int j = 0; j < 8; ++j)
-            *reinterpret_cast<uint4*>(atom + tc::sw128_offset(row, 8 * j)) =
-                make_uint4(w[4 * j], w[4 * j + 1], w[4 * j + 2], w[4 * j + 3]);
-          tc::fence_proxy_async();
-          tc::fence_before_sync();
-          tc::mbar_arrive(&bars.actready[t][l][h]);
+            for (int j = 0; j < 16; ++j)
+              acc2 = f2_fma(f2_relu(f2_add(f2_pack(r1[2 * j], r1[2 * j + 1]), b3[c1 / 2 + j])), w4[c1 / 2 + j], acc2);
+            continue;
+          }
+          // layer 1's half 0 goes where its input (atom 0) is: wait for the
+          // layer's last MMAs
+          if (l == 0 && h == 0 && !(ok = wait_or_fail(&bars.accfull[t][0][1], ph, &s_fail))) break;
+#pragma unroll
+          for (int i = 0; i < 2; ++i) {
+            // bias, ReLU, BF16 pairs of the 32 columns
+            const unsigned long long* bias = reinterpret_cast<const unsigned long long*>(sb[l] + (i ? c1 : c0));
+            const uint32_t* r = i ? r1 : r0;
+            uint32_t w[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) w[j] = relu_bf16x2(f2_add(f2_pack(r[2 * j], r[2 * j + 1]), bias[j]));
+            uint8_t* atom = base + t * 65536 + (2 * h + i) * 16384;
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+              *reinterpret_cast<uint4*>(atom + tc::sw128_offset(row, 8 * (4 * a + j))) =
+                  make_uint4(w[4 * j], w[4 * j + 1], w[4 * j + 2], w[4 * j + 3]);
+            tc::fence_proxy_async();
+            __syncwarp();
+            if (lane == 0) red_release_add(&cnt.ready[t][l][2 * h + i], 1);
+          }
         }
       }
       if (!ok) break;
@@ -551,9 +608,9 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_mlp_img(const uint8_t* __res
   }
   __syncthreads();
   if (warp == kCopyWarp && lane == 0 && s_fail) {
-    // copies issued but not seen landed by both MMA warps (at most one per
-    // ring buffer, and one feature tile each) complete before the CTA exits
-    for (uint32_t G = min(s_consumed[0], s_consumed[1]); G < issued; ++G)
+    // copies issued but not seen landed (at most one per ring buffer, and
+    // one feature tile each) complete before the CTA exits
+    for (uint32_t G = pub; G < issued; ++G)
       tc::mbar_wait(&bars.full[G % kSlots], (G / kSlots) & 1, kWaitLimit);
     for (int t = 0; t < 2; ++t)
       if (x_issued[t] > s_xwaited[t]) tc::mbar_wait(&bars.xfull[t], (x_issued[t] - 1) & 1, kWaitLimit);
