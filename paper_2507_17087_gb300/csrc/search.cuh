@@ -227,28 +227,34 @@ __device__ __forceinline__ unsigned long long secondary_cost_warp(const uint16_t
     const uint32_t nfib = n[u] * n[w];
     const uint8_t* pre = v == 0 ? pre0 : (v == 2 ? pre2 : nullptr);
     if (nfib >= 32 || pre) {
-      const uint32_t rot = ROT ? (uint32_t)lane % n[v] : 0u;
+      // the family's extents as scalars (not re-read from the arrays around
+      // the fibre scans' shared-memory stores)
+      const uint32_t Eu = E[u], fu = f[u], nu = n[u], su = fstride[u], sw = fstride[w];
+      const uint32_t Ev = E[v], fv = f[v], nv = n[v], sv = fstride[v], f1 = f[1];
+      const uint32_t rot = ROT ? (uint32_t)lane % nv : 0u;
       const uint32_t chunk = (nfib + 31) / 32;
       const uint32_t fb0 = lane * chunk, fb1 = min(nfib, fb0 + chunk);
       unsigned long long part = 0;
       if (fb0 < fb1) {
-        uint32_t iu = fb0 % n[u];
+        uint32_t iu = fb0 % nu;
         BlockIter itu, itw;
-        itu.seek(E[u], f[u], iu);
-        itw.seek(E[w], f[w], fb0 / n[u]);
+        itu.seek(Eu, fu, iu);
+        itw.seek(E[w], f[w], fb0 / nu);
         uint32_t rep_w = itw.rep;
         uint32_t wt_w = itw.step();
         for (uint32_t fb = fb0; fb < fb1; ++fb) {
           const uint32_t rep_u = itu.rep;
           const uint32_t wt_u = itu.step();
-          const uint32_t base = rep_u * fstride[u] + rep_w * fstride[w];
-          const uint32_t D = pre ? (uint32_t)pre[v == 0 ? rep_u + rep_w * f[1] : base] + 1u
-                                 : fibre_distinct<ROT>(tab, bm + lane, stride, words, base, fstride[v], E[v], f[v],
-                                                       n[v], rot);
+          const uint32_t base = rep_u * su + rep_w * sw;
+          const uint32_t D = pre ? (uint32_t)pre[v == 0 ? rep_u + rep_w * f1 : base] + 1u
+                                 : fibre_distinct<ROT>(tab, bm + lane, stride, words, base, sv, Ev, fv, nv, rot);
           part += (unsigned long long)wt_u * wt_w * (D - 1);
-          if (++iu == n[u]) {
+          if (++iu == nu) {
+            // back to block 0: the quotient and remainder stay, the running
+            // remainder and the representative restart at 0
             iu = 0;
-            itu.seek(E[u], f[u], 0);
+            itu.r = 0;
+            itu.rep = 0;
             rep_w = itw.rep;
             wt_w = itw.step();
           }
@@ -258,10 +264,12 @@ __device__ __forceinline__ unsigned long long secondary_cost_warp(const uint16_t
     } else {
       BlockIter itu, itw;
       itw.seek(E[w], f[w], 0);
+      itu.seek(E[u], f[u], 0);
       for (uint32_t iw = 0; iw < n[w]; ++iw) {
         const uint32_t rep_w = itw.rep;
         const uint32_t wt_w = itw.step();
-        itu.seek(E[u], f[u], 0);
+        itu.r = 0;
+        itu.rep = 0;
         for (uint32_t iu = 0; iu < n[u]; ++iu) {
           const uint32_t rep_u = itu.rep;
           const uint32_t wt_u = itu.step();
