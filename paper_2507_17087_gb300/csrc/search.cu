@@ -35,10 +35,11 @@ size_t align_up(size_t v) { return (v + 255) & ~size_t(255); }
 // full = 1: every candidate's secondary is scanned.  full = 0: candidates
 // whose (exact, closed-form) primary exceeds the minimum primary over all
 // factorisations cannot win the lexicographic argmin and are not scanned.
-// PRE: the precounted fibre tables (full search; one byte per fibre, so that
-// with the table and bitmaps four CTAs fit on an SM, as the registers do).
+// PRE: the precounted fibre tables (full search; one byte per fibre).  The
+// full search runs three CTAs per SM at 80 registers (faster than four at 64,
+// which spill); the primary-bound search, with few candidates per CTA, four.
 template <bool PRE>
-__global__ void __launch_bounds__(256, 4) k_search(const ChainProg* __restrict__ progs, const Fact* __restrict__ facts, int nf,
+__global__ void __launch_bounds__(256, PRE ? 3 : 4) k_search(const ChainProg* __restrict__ progs, const Fact* __restrict__ facts, int nf,
                          uint32_t P, uint32_t E0, uint32_t E1, uint32_t E2, int words,
                          unsigned long long nchains, int full, unsigned long long ub,
                          const uint8_t* __restrict__ skip, const uint16_t* __restrict__ gtab, uint32_t Pp,
