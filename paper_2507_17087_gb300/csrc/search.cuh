@@ -192,8 +192,8 @@ __device__ __forceinline__ unsigned long long warp_sum(unsigned long long v) {
 // computed by one warp.  Families with at least 32 fibres: lane l scans a
 // contiguous share of them with its own bitmap (word w of lane l at
 // bm[w * stride + l]).  Families with fewer fibres: the fibres are scanned
-// one at a time, the lanes splitting the elements over one shared bitmap
-// (lane 0's) with atomic ORs, the distinct count being its population.
+// one at a time, the lanes splitting the elements, each into its own bitmap;
+// the distinct count is the population of the lanes' bitmaps ORed together.
 // Every lane returns the total.
 // ub: once the running total exceeds it the remaining families are skipped
 // and ~0 is returned (the caller only needs costs up to ub).
@@ -262,6 +262,17 @@ __device__ __forceinline__ unsigned long long secondary_cost_warp(const uint16_t
       }
       sec += warp_sum(part);
     } else {
+      // few, long fibres: the lanes split each fibre's points, each marking
+      // its own bitmap column, and the warp ORs the columns word by word
+      const uint32_t Ev = E[v], fv = f[v], nv = n[v], sv = fstride[v], su = fstride[u], sw = fstride[w];
+      // block coordinate of the lane's point iv = lane + 32 t: floor(iv fv / Ev)
+      // when Ev < fv (iv when Ev >= fv), stepped by 32 points through its
+      // remainder (iv fv < 2^19: P <= 2^14)
+      const bool dense = Ev >= fv;
+      const uint32_t Q = dense ? 32u : 32u * fv / Ev, R = dense ? 0u : 32u * fv % Ev;
+      const uint32_t rep0 = dense ? (uint32_t)lane : (uint32_t)lane * fv / Ev;
+      const uint32_t rem0 = dense ? 0u : (uint32_t)lane * fv % Ev;
+      uint32_t* col = bm + lane;
       BlockIter itu, itw;
       itw.seek(E[w], f[w], 0);
       itu.seek(E[u], f[u], 0);
@@ -273,21 +284,26 @@ __device__ __forceinline__ unsigned long long secondary_cost_warp(const uint16_t
         for (uint32_t iu = 0; iu < n[u]; ++iu) {
           const uint32_t rep_u = itu.rep;
           const uint32_t wt_u = itu.step();
-          const uint32_t base = rep_u * fstride[u] + rep_w * fstride[w];
-          for (uint32_t iv = lane; iv < n[v]; iv += 32) {
-            const uint32_t rep_v =
-                E[v] >= f[v] ? iv : (uint32_t)((unsigned long long)iv * f[v] / E[v]);
-            const uint32_t node = tab[base + rep_v * fstride[v]];
-            atomicOr(bm + (node >> 5) * stride, 1u << (node & 31));
+          const uint32_t base = rep_u * su + rep_w * sw;
+          uint32_t rep = rep0, rem = rem0;
+          for (uint32_t iv = lane; iv < nv; iv += 32) {
+            const uint32_t node = tab[base + rep * sv];
+            uint32_t* wp = col + (node >> 5) * stride;
+            const uint32_t bit = 1u << (node & 31);
+            const uint32_t word = *wp;
+            if (!(word & bit)) *wp = word | bit;
+            rep += Q;
+            rem += R;
+            if (rem >= Ev) {
+              rem -= Ev;
+              ++rep;
+            }
           }
-          __syncwarp();
-          unsigned long long cnt = 0;
-          for (int k = lane; k < words; k += 32) {
-            cnt += __popc(bm[k * stride]);
-            bm[k * stride] = 0;
+          uint32_t D = 0;
+          for (int k = 0; k < words; ++k) {
+            D += __popc(__reduce_or_sync(0xFFFFFFFFu, col[k * stride]));
+            col[k * stride] = 0;
           }
-          const unsigned long long D = warp_sum(cnt);
-          __syncwarp();
           sec += (unsigned long long)wt_u * wt_w * (D - 1);
         }
       }
