@@ -684,13 +684,17 @@ def main():
 
     e2e_step()
     per_step_launches = N.kernel_launches() - launches_before
-    if dist:
-        dist.barrier()
-    t0 = time.perf_counter()
-    for _ in range(args.e2e_steps):
-        e2e_step()
-    e2e_s = time.perf_counter() - t0
-    e2e_s = max_over_ranks(e2e_s, dist, dev)
+    # three trials of the same steps, the median reported (a host-link hiccup
+    # during one trial does not set the number)
+    trials = []
+    for _ in range(3):
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            e2e_step()
+        trials.append(max_over_ranks(time.perf_counter() - t0, dist, dev))
+    e2e_s = sorted(trials)[1]
     e2e_value = 3 * npts * args.e2e_steps * world / e2e_s
     d2h = 3 * (npts * 4 + P * 8 + 8 + P * 8)
     h2d = per_step_launches * N.descriptor_bytes()
@@ -717,7 +721,9 @@ def main():
                          "kernel_avg_ms": k_avg_ms, "algorithmic_bytes_per_launch": algo_bytes,
                          "note": "k_ids only writes, and hbm_gbs is a read + write copy: a write-only "
                                  "2 GiB fill moves 7.2-7.75 TB/s on the same GPUs"},
-            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "timing": "median of 3 trials of %d steps (host wall clock)" % args.e2e_steps,
+                    "trial_values": [3 * npts * args.e2e_steps * world / t for t in trials]},
             "gpu_launches": gpu_launches,
             "clocks": clocks,
         }
