@@ -433,27 +433,31 @@ __device__ __forceinline__ void ids_range_rows(const MapCore& D, const Tabs& tab
   // R_BLOCK / R_BCYC: the run [run_lo, run_hi) of the last dimension with
   // one final coordinate (block, or block of b points) that holds x, with
   // contribution rc; a group inside it has one id, looked up once
+  // (only where runs can hold a group: blocks of at least 4 points)
   constexpr bool RUNS = SRC == R_BLOCK || SRC == R_BCYC;
   const Comp& cl = D.comp[D.k - 1][0];
+  const bool use_runs = RUNS && (SRC == R_BCYC ? cl.b >= 4 : cl.L >= 4 * (uint64_t)cl.s);
   uint32_t rc = 0, run_lo = 1, run_hi = 0;
   for (; g < gend; g += 32, lin0 += 128) {
     const int cnt = N - lin0 < 4 ? (int)(N - lin0) : 4;
     uint32_t v[4] = {0, 0, 0, 0};
-    if (RUNS && (x < run_lo || x >= run_hi)) {
-      rc = row_contrib<SRC>(D, Cf, A, x);
+    if (use_runs && (x < run_lo || x >= run_hi)) {
       uint64_t lo, hi;
       if (SRC == R_BLOCK) {
-        const uint64_t a = rc / cl.sigma;
-        lo = (a * cl.L + cl.s - 1) / cl.s;
-        hi = ((a + 1) * cl.L + cl.s - 1) / cl.s;
+        // block a of x: points [ceil(a L / s), ceil((a + 1) L / s))
+        const uint32_t a = cl.narrow ? div32(x * cl.s, cl.divL32) : (uint32_t)div64((uint64_t)x * cl.s, cl.divL);
+        rc = a * cl.sigma;
+        lo = div64((uint64_t)a * cl.L + cl.s - 1, cl.divs64);
+        hi = div64((uint64_t)(a + 1) * cl.L + cl.s - 1, cl.divs64);
       } else {
-        lo = (uint64_t)(x / cl.b) * cl.b;
+        rc = row_contrib<SRC>(D, Cf, A, x);
+        lo = (uint64_t)div32(x, cl.divb) * cl.b;
         hi = lo + cl.b;
       }
       run_lo = (uint32_t)lo;
       run_hi = (uint32_t)(hi < Lf ? hi : Lf);
     }
-    if (RUNS && x + 4 <= run_hi) {
+    if (use_runs && x + 4 <= run_hi) {
       v[0] = v[1] = v[2] = v[3] = T[base + rc];
     } else if (SRC == R_TAB4) {
       const uint4 c = *reinterpret_cast<const uint4*>(Cf + x);
