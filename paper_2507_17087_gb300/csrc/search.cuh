@@ -235,7 +235,26 @@ __device__ __forceinline__ unsigned long long secondary_cost_warp(const uint16_t
       const uint32_t chunk = (nfib + 31) / 32;
       const uint32_t fb0 = lane * chunk, fb1 = min(nfib, fb0 + chunk);
       unsigned long long part = 0;
-      if (fb0 < fb1) {
+      if (fb0 < fb1 && pre && Eu >= fu && E[w] >= f[w]) {
+        // precounted, every block of u and w holds tiles: fibre fb's count is
+        // at pre[fb] (family 0: rep_u + f1 rep_w, family 2: rep_u + f0 rep_w,
+        // and rep = block index), so the lane reads its bytes in order
+        uint32_t iu = fb0 % nu;
+        BlockIter itu, itw;
+        itu.seek(Eu, fu, iu);
+        itw.seek(E[w], f[w], fb0 / nu);
+        uint32_t wt_w = itw.step();
+        for (uint32_t fb = fb0; fb < fb1; ++fb) {
+          const uint32_t wt_u = itu.step();
+          part += (unsigned long long)wt_u * wt_w * pre[fb];
+          if (++iu == nu) {
+            iu = 0;
+            itu.r = 0;
+            itu.rep = 0;
+            wt_w = itw.step();
+          }
+        }
+      } else if (fb0 < fb1) {
         uint32_t iu = fb0 % nu;
         BlockIter itu, itw;
         itu.seek(Eu, fu, iu);
