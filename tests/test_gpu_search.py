@@ -57,6 +57,24 @@ def test_worked_shapes():
     assert N.decompose_search([q])[0]["index"] == oracle_best(q)["index"]
 
 
+def test_search_kernel_paths():
+    # shapes that take the search kernels' special paths, exhaustively against
+    # the oracle, with and without the primary bound: extents below their
+    # factors (blocks holding one tile or none), uneven blocks (A or A + 1
+    # tiles), families with fewer than 32 long fibres, precounted families
+    # read by fibre number
+    shapes = [((5, 1000, 7), (90, 8)), ((250, 333, 97), (45, 16)), ((3, 3, 3), (64, 1)),
+              ((1000, 2, 1000), (30, 24)), ((64, 4096, 2), (8, 8))]
+    for (MNK, machine), depth in zip(shapes, (3, 3, 3, 3, 3)):
+        q = {"MNK": MNK, "machine": machine, "max_depth": depth, "tile_bytes": TILE}
+        ref = oracle_best(q, threads=CORES)
+        for full in (False, True):
+            got = N.decompose_search([q], full=full)[0]
+            assert (got["index"], got["f"]) == (ref["index"], ref["f"]), (q, full, got, ref)
+            assert got["primary_bytes"] == ref["primary"] * TILE
+            assert got["secondary_bytes"] == ref["secondary"] * TILE
+
+
 @pytest.mark.parametrize("qi", range(8))
 def test_matmul_queries_full_size(qi):
     # every full-size query (P = 512, 2520, 3600, 4096; up to 3.79 M
