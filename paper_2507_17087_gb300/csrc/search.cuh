@@ -81,20 +81,27 @@ struct BlockIter {
     r = 0;
     rep = 0;
   }
-  // positions the iterator at block index i (a few divisions, once)
+  // positions the iterator at block index i (a few divisions, once; 32-bit
+  // ones when the product fits)
   __device__ __forceinline__ void seek(uint32_t E, uint32_t f, uint32_t i) {
     big = E >= f;
     if (big) {
-      A = E / f; B = E % f; m = f;
+      A = E / f; B = E - A * f; m = f;
+      // r = ceil(i E / f) f - i E = (f - (i E mod f)) mod f
       const unsigned long long ie = (unsigned long long)i * E;
-      const unsigned long long c = (ie + f - 1) / f;   // ceil(i E / f)
-      r = (uint32_t)(c * f - ie);
+      const uint32_t rem = (ie >> 32) ? (uint32_t)(ie % f) : (uint32_t)ie % f;
+      r = rem ? f - rem : 0u;
       rep = i;
     } else {
-      A = f / E; B = f % E; m = E;
+      A = f / E; B = f - A * E; m = E;
       const unsigned long long iF = (unsigned long long)i * f;
-      rep = (uint32_t)(iF / E);
-      r = (uint32_t)(iF % E);
+      if (iF >> 32) {
+        rep = (uint32_t)(iF / E);
+        r = (uint32_t)(iF - (unsigned long long)rep * E);
+      } else {
+        rep = (uint32_t)iF / E;
+        r = (uint32_t)iF - rep * E;
+      }
     }
   }
   // returns the weight of the current representative and advances
@@ -239,10 +246,11 @@ __device__ __forceinline__ unsigned long long secondary_cost_warp(const uint16_t
         // precounted, every block of u and w holds tiles: fibre fb's count is
         // at pre[fb] (family 0: rep_u + f1 rep_w, family 2: rep_u + f0 rep_w,
         // and rep = block index), so the lane reads its bytes in order
-        uint32_t iu = fb0 % nu;
+        const uint32_t row0 = fb0 / nu;
+        uint32_t iu = fb0 - row0 * nu;
         BlockIter itu, itw;
         itu.seek(Eu, fu, iu);
-        itw.seek(E[w], f[w], fb0 / nu);
+        itw.seek(E[w], f[w], row0);
         uint32_t wt_w = itw.step();
         for (uint32_t fb = fb0; fb < fb1; ++fb) {
           const uint32_t wt_u = itu.step();
@@ -255,10 +263,11 @@ __device__ __forceinline__ unsigned long long secondary_cost_warp(const uint16_t
           }
         }
       } else if (fb0 < fb1) {
-        uint32_t iu = fb0 % nu;
+        const uint32_t row0 = fb0 / nu;
+        uint32_t iu = fb0 - row0 * nu;
         BlockIter itu, itw;
         itu.seek(Eu, fu, iu);
-        itw.seek(E[w], f[w], fb0 / nu);
+        itw.seek(E[w], f[w], row0);
         uint32_t rep_w = itw.rep;
         uint32_t wt_w = itw.step();
         for (uint32_t fb = fb0; fb < fb1; ++fb) {
