@@ -327,6 +327,53 @@ def sustained_bf16_peak():
         return 1700.0, "fallback"
 
 
+SCORE_FLOP_PER_CANDIDATE = 2 * (64 * 256 + 2 * 256 * 256 + 256)
+
+
+def burst_bf16_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["bf16_tflops"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 1900.0, "fallback"
+
+
+def extra_scorer(N, W, torch, dev, reps=7):
+    """The learned scorer's layer kernel (k_mlp_img: three tcgen05 layers and
+    the output dot product) timed alone with CUDA events around one full
+    launch of 2^19 candidates (the first run of scoring every candidate of the
+    P = 3600 search query, by a briefly trained model): TFLOP/s and the
+    fraction of the measured BF16 burst peak (the kernel is timed alone)."""
+    q = _search_query_3600()
+    m = N.MLP(seed=11)
+    m.train_search(W.search_training_queries(16), samples_per_query=1024, epochs=1, batch=1024, lr=1e-3, seed=3)
+    nf, nc = N.search_space(q["machine"][0] * q["machine"][1], q["machine"][1], q["max_depth"])
+    scores = torch.empty(nf * nc, dtype=torch.float32, device=dev)
+    m.scores(q, scores)   # warm: the candidate space and the scoring buffers
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()   # once here, so that torch reads them after the library records them again
+        b.record()
+        torch.cuda.synchronize()
+        N.set_layer_timer(a, b)
+        m.scores(q, scores)
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    m.close()
+    med = sorted(ms)[len(ms) // 2]
+    cands = 1 << 19
+    tflops = cands * SCORE_FLOP_PER_CANDIDATE / (med * 1e-3) / 1e12
+    peak, src = burst_bf16_peak()
+    return {"metric": "layer kernel TFLOP/s (BF16)", "value": tflops, "unit": "TFLOP/s", "frac_of_peak": tflops / peak,
+            "peak_tflops": peak, "peak_source": f"{src} bf16_tflops (burst)", "ms_per_launch": med,
+            "ms_launches": ms, "candidates_per_launch": cands, "flop_per_candidate": SCORE_FLOP_PER_CANDIDATE,
+            "workload": "every candidate of the P = 3600 matmul search query (256 x 1024 x 4096 tiles on 450 x 8), "
+                        "first run of 2^19"}
+
+
 def extra_train(N, torch, dev, batch=4096, steps=300, warmup=10):
     """Training steps of the learned cost model (forward, backward and Adam
     on one batch of 4096 samples, every product on the tcgen05 GEMM):
@@ -732,6 +779,7 @@ def main():
                             ("batched", lambda: extra_batched(N, W, torch, dev)),
                             ("learned", lambda: extra_learned(N, W, torch)),
                             ("train", lambda: extra_train(N, torch, dev)),
+                            ("scorer", lambda: extra_scorer(N, W, torch, dev)),
                             ("volume_study", lambda: extra_volume_study(N, W, torch, dev)),
                             ("hier_search", lambda: extra_hier_search(N, W, torch)),
                             ("applications", lambda: extra_applications(N, W, torch, dev))):

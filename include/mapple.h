@@ -550,6 +550,12 @@ int mp_greedy_grid(int64_t d, int32_t k, int64_t* out);
  * with CUDA events. */
 int mp_set_kernel_timer(void* start_event, void* stop_event);
 
+/* The same for the learned scorer's layer kernel (the three tcgen05 layers
+ * and the output dot product, one launch per run of at most 2^19 scored
+ * candidates): the next launch records `start_event` before it and
+ * `stop_event` after it on the call's stream; one-shot; NULL disables. */
+int mp_set_layer_timer(void* start_event, void* stop_event);
+
 /* Bytes of launch description one kernel launch carries to the device as
  * parameters (the host-to-device input of a mapping call). */
 uint64_t mp_descriptor_bytes(void);

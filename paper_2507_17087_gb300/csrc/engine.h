@@ -200,6 +200,9 @@ void count_launch(uint64_t n = 1);
 // One-shot events around the dominant kernel (mp_set_kernel_timer).
 void timer_begin(cudaStream_t st);
 void timer_end(cudaStream_t st);
+// the same one-shot pair around the next launch of the learned scorer's layer kernel
+void layer_timer_begin(cudaStream_t st);
+void layer_timer_end(cudaStream_t st);
 
 }  // namespace mp
 

@@ -1141,7 +1141,9 @@ int score_candidates(mp_mlp* h, const Prepared& pq, const uint32_t* d_fl, uint64
     k_feat_img<<<ntiles, 128, 0, st>>>(pq.Q, pq.d_fnode, pq.d_fdiv, pq.d_facts, pq.d_chainfeat, d_fl, c0, n,
                                        img);
     const unsigned grid = (unsigned)std::min<uint64_t>((ntiles + 1) / 2, (uint64_t)sm_count_l());
+    layer_timer_begin(st);
     k_mlp_img<<<grid, kMlpThreads, kMlpSmem, st>>>(img, ntiles, h->Wimg, h->P, n, d_sc + c0, h->status);
+    layer_timer_end(st);
     count_launch(2);
     MP_CUDA_TRY(cudaGetLastError());
   }

@@ -99,6 +99,8 @@ void record_cuda_error(cudaError_t e, const char* file, int line) {
 namespace {
 cudaEvent_t g_t0 = nullptr, g_t1 = nullptr;
 bool g_armed = false;
+cudaEvent_t g_lt0 = nullptr, g_lt1 = nullptr;   // the learned scorer's layer kernel
+bool g_larmed = false;
 }  // namespace
 
 void timer_begin(cudaStream_t st) {
@@ -108,6 +110,15 @@ void timer_begin(cudaStream_t st) {
 void timer_end(cudaStream_t st) {
   if (g_armed && g_t1) cudaEventRecord(g_t1, st);
   g_armed = false;
+}
+
+void layer_timer_begin(cudaStream_t st) {
+  if (g_larmed && g_lt0) cudaEventRecord(g_lt0, st);
+}
+
+void layer_timer_end(cudaStream_t st) {
+  if (g_larmed && g_lt1) cudaEventRecord(g_lt1, st);
+  g_larmed = false;
 }
 
 }  // namespace mp
@@ -133,6 +144,13 @@ extern "C" int mp_set_kernel_timer(void* start_event, void* stop_event) {
   mp::g_t0 = (cudaEvent_t)start_event;
   mp::g_t1 = (cudaEvent_t)stop_event;
   mp::g_armed = start_event && stop_event;
+  return MP_OK;
+}
+
+extern "C" int mp_set_layer_timer(void* start_event, void* stop_event) {
+  mp::g_lt0 = (cudaEvent_t)start_event;
+  mp::g_lt1 = (cudaEvent_t)stop_event;
+  mp::g_larmed = start_event && stop_event;
   return MP_OK;
 }
 

@@ -148,6 +148,7 @@ def lib():
                 "mp_kernel_launches": (U64, []),
                 "mp_workspace_bytes": (U64, []),
                 "mp_set_kernel_timer": (I, [V, V]),
+                "mp_set_layer_timer": (I, [V, V]),
                 "mp_batch_create": (I, [V, I, V]),
                 "mp_batch_info": (I, [V, V, V, V, V, V]),
                 "mp_batch_run": (I, [V, V, V, V, V, I, V]),
@@ -584,6 +585,12 @@ def set_kernel_timer(start_event, stop_event):
     """Time the next id-writer kernel with two cudaEvent_t handles (or torch events)."""
     h = lambda e: None if e is None else (e.cuda_event if hasattr(e, "cuda_event") else int(e))
     _check(lib().mp_set_kernel_timer(h(start_event), h(stop_event)), "mp_set_kernel_timer")
+
+
+def set_layer_timer(start_event, stop_event):
+    """Time the learned scorer's next layer-kernel launch (mp_set_layer_timer)."""
+    h = lambda e: None if e is None else (e.cuda_event if hasattr(e, "cuda_event") else int(e))
+    _check(lib().mp_set_layer_timer(h(start_event), h(stop_event)), "mp_set_layer_timer")
 
 
 def descriptor_bytes() -> int:

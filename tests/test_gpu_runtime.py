@@ -138,3 +138,39 @@ def test_persisted_autotune_choice(tmp_path):
     assert torch.equal(ids1, ids2)
     b1.close()
     b2.close()
+
+
+def test_kernel_timers_are_one_shot_and_record_on_the_call_stream():
+    # the id writer's and the layer kernel's measurement hooks: armed, the
+    # next launch records both events (a positive elapsed time); then they
+    # disarm themselves, so a second call does not record them again
+    def events():
+        # recorded once here, so that torch will read them after the library
+        # records them again
+        e = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+        for x in e:
+            x.record()
+        torch.cuda.synchronize()
+        return e
+
+    a, b = events()
+    ids = torch.empty(64 * 64, dtype=torch.int32, device="cuda")
+    N.set_kernel_timer(a, b)
+    N.map_points((64, 64), (2, 4), [("merge", 0, 1)], ("block",), ids=ids)
+    torch.cuda.synchronize()
+    assert a.elapsed_time(b) > 0
+    model = N.MLP(seed=2)
+    q = {"MNK": (64, 64, 64), "machine": (4, 4), "max_depth": 2, "tile_bytes": 512 * 512 * 4}
+    nf, nc = N.search_space(16, 4, 2)
+    scores = torch.empty(nf * nc, dtype=torch.float32, device="cuda")
+    c, d = events()
+    N.set_layer_timer(c, d)
+    assert model.scores(q, scores) == nf * nc
+    torch.cuda.synchronize()
+    t1 = c.elapsed_time(d)
+    assert t1 > 0
+    model.scores(q, scores)
+    N.map_points((64, 64), (2, 4), [("merge", 0, 1)], ("block",), ids=ids)
+    torch.cuda.synchronize()
+    assert c.elapsed_time(d) == t1
+    model.close()
